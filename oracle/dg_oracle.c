@@ -1,0 +1,1198 @@
+/*
+ * dg_oracle.c -- plain FP64 CPU oracle for the flagged Euler / NS-LES DGSEM residual.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the benchmark's
+ * CPU-baseline leg. The CUDA library never links, includes or calls it, and it shares no
+ * code with that library. Everything here is deliberately direct: no blocking, no fusion,
+ * no reordering beyond what the discretisation states.
+ *
+ * Discretisation (arXiv 2403.05463, App. B, Eqs. NS2-NS5) on Gauss-Lobatto nodes:
+ *   weak form per element, integrated with the tensor-product quadrature,
+ *     w J dq/dt = sum_d (1/w_{i_d}) sum_m w_m D_{m i_d} Ftil^d_m  -  sum_faces (1/w_end) H*
+ *   with Ftil^d the contravariant (Ja^d-weighted) total flux F_e - F_v,turb and H* the
+ *   area-weighted outward numerical flux F_e* - F_v* on each face (projected from the
+ *   mortar when the two sides have different orders).
+ * Sec. 2.3: Euler elements omit every viscous/turbulent term; convective terms everywhere;
+ * faces couple with Roe (convective) and BR1 (viscous). Reading for an Euler/NS face: the
+ * single-valued BR1 flux is the average of the NS side's viscous flux and zero.
+ */
+#include "dg_oracle.h"
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXN 15
+#define OR_MAXG 4
+
+static __thread char g_err[512];
+static void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+const char* or_error(void) { return g_err; }
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------------------
+ * 1D: Gauss-Lobatto-Legendre nodes and weights, differentiation, interpolation,
+ * L2 projection. (Quadrature of App. B, last paragraph; Gauss-Lobatto variant.)
+ * ---------------------------------------------------------------------------------- */
+
+/* Legendre polynomials L_{N-1}, L_N, L_{N+1} at x by the three-term recurrence
+ * (k+1) L_{k+1} = (2k+1) x L_k - k L_{k-1}, L_0 = 1, L_1 = x. */
+static void legendre3(int N, double x, double* Lm1, double* L0, double* Lp1) {
+  double lkm1 = 0.0, lk = 1.0; /* L_{-1} (unused), L_0 */
+  double lkp1 = x;             /* L_1 */
+  for (int k = 1; k <= N; ++k) {
+    lkm1 = lk;
+    lk = lkp1;
+    lkp1 = ((2.0 * k + 1.0) * x * lk - k * lkm1) / (k + 1.0);
+  }
+  /* after the loop: lkm1 = L_{N-1}, lk = L_N, lkp1 = L_{N+1} */
+  *Lm1 = lkm1;
+  *L0 = lk;
+  *Lp1 = lkp1;
+}
+
+int or_lgl(int N, double* x, double* w) {
+  if (N < 1 || N > OR_MAXN) {
+    set_err("order %d outside 1..%d", N, OR_MAXN);
+    return -1;
+  }
+  x[0] = -1.0;
+  x[N] = 1.0;
+  /* interior nodes: roots of L_{N+1} - L_{N-1} (proportional to (1-x^2) L'_N);
+   * Newton from Chebyshev-Gauss-Lobatto guesses, d/dx (L_{N+1}-L_{N-1}) = (2N+1) L_N. */
+  for (int j = 1; j < N; ++j) {
+    double xj = -cos(M_PI * j / N);
+    for (int it = 0; it < 200; ++it) {
+      double lm1, l0, lp1;
+      legendre3(N, xj, &lm1, &l0, &lp1);
+      double dx = (lp1 - lm1) / ((2.0 * N + 1.0) * l0);
+      xj -= dx;
+      if (fabs(dx) <= 1e-17) break;
+    }
+    x[j] = xj;
+  }
+  /* enforce the exact symmetry of the node set */
+  for (int j = 0; j < (N + 1) / 2; ++j) {
+    double s = 0.5 * (x[N - j] - x[j]);
+    x[j] = -s;
+    x[N - j] = s;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  for (int j = 0; j <= N; ++j) {
+    double lm1, l0, lp1;
+    legendre3(N, x[j], &lm1, &l0, &lp1);
+    w[j] = 2.0 / (N * (N + 1.0) * l0 * l0);
+  }
+  return 0;
+}
+
+/* Lagrange basis l_j(y) on nodes xs[0..n-1] by the product formula. */
+static double lagrange(int n, const double* xs, int j, double y) {
+  double v = 1.0;
+  for (int k = 0; k < n; ++k)
+    if (k != j) v *= (y - xs[k]) / (xs[j] - xs[k]);
+  return v;
+}
+
+int or_dmat(int N, double* D) {
+  double x[OR_MAXN + 1], w[OR_MAXN + 1], lam[OR_MAXN + 1];
+  if (or_lgl(N, x, w)) return -1;
+  int n = N + 1;
+  /* barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k) */
+  for (int j = 0; j < n; ++j) {
+    double p = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) p *= (x[j] - x[k]);
+    lam[j] = 1.0 / p;
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+      s += D[i * n + j];
+    }
+    D[i * n + i] = -s;
+  }
+  return 0;
+}
+
+int or_interp_lgl(int Ns, int Nd, double* I) {
+  double xs[OR_MAXN + 1], ws[OR_MAXN + 1], xd[OR_MAXN + 1], wd[OR_MAXN + 1];
+  if (or_lgl(Ns, xs, ws) || or_lgl(Nd, xd, wd)) return -1;
+  for (int i = 0; i <= Nd; ++i)
+    for (int j = 0; j <= Ns; ++j) I[i * (Ns + 1) + j] = lagrange(Ns + 1, xs, j, xd[i]);
+  return 0;
+}
+
+/* Solve A X = B in place (A n x n, B n x m, row-major) by Gauss-Jordan with partial
+ * pivoting. Returns -1 if A is singular. */
+static int gauss_jordan(int n, double* A, int m, double* B) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+    if (fabs(A[piv * n + c]) < 1e-300) return -1;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) {
+        double t = A[c * n + k];
+        A[c * n + k] = A[piv * n + k];
+        A[piv * n + k] = t;
+      }
+      for (int k = 0; k < m; ++k) {
+        double t = B[c * m + k];
+        B[c * m + k] = B[piv * m + k];
+        B[piv * m + k] = t;
+      }
+    }
+    double d = A[c * n + c];
+    for (int k = 0; k < n; ++k) A[c * n + k] /= d;
+    for (int k = 0; k < m; ++k) B[c * m + k] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      for (int k = 0; k < m; ++k) B[r * m + k] -= f * B[c * m + k];
+    }
+  }
+  return 0;
+}
+
+/* L2 projection from the degree-Nh polynomial given at its Gauss-Lobatto nodes onto
+ * degree Nl <= Nh: P = M_l^{-1} I^T W_h, where I interpolates Nl -> Nh nodes and
+ * M_l = I^T W_h I is the exact mass matrix (Nh-point Lobatto quadrature is exact for
+ * degree 2 Nl <= 2 Nh - 1 when Nh > Nl). For Nh == Nl, P is the identity. */
+int or_project_lgl(int Nh, int Nl, double* P) {
+  int nh = Nh + 1, nl = Nl + 1;
+  if (Nl > Nh) {
+    set_err("projection needs Nl <= Nh");
+    return -1;
+  }
+  if (Nh == Nl) {
+    for (int i = 0; i < nl; ++i)
+      for (int j = 0; j < nh; ++j) P[i * nh + j] = (i == j) ? 1.0 : 0.0;
+    return 0;
+  }
+  double xh[OR_MAXN + 1], wh[OR_MAXN + 1];
+  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  double M[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  if (or_lgl(Nh, xh, wh) || or_interp_lgl(Nl, Nh, I)) return -1;
+  for (int a = 0; a < nl; ++a)
+    for (int b = 0; b < nl; ++b) {
+      double s = 0.0;
+      for (int j = 0; j < nh; ++j) s += I[j * nl + a] * wh[j] * I[j * nl + b];
+      M[a * nl + b] = s;
+    }
+  for (int a = 0; a < nl; ++a)
+    for (int j = 0; j < nh; ++j) P[a * nh + j] = I[j * nl + a] * wh[j];
+  if (gauss_jordan(nl, M, nh, P)) {
+    set_err("singular mass matrix");
+    return -1;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Pointwise physics (App. A in artificial-compressibility form, rho = 1).
+ *   F_e in direction x_k: (c0^2 u_k, u u_k + p e_1k, v u_k + p e_2k, w u_k + p e_3k)
+ *   tau = (nu + nu_t)(G + G^T) - 2/3 (nu + nu_t) tr(G) I,  G_ck = d u_c / d x_k
+ * ---------------------------------------------------------------------------------- */
+
+void or_normal_flux(const double q[4], const double nh[3], double c0sq, double out[4]) {
+  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+  out[0] = c0sq * un;
+  for (int c = 0; c < 3; ++c) out[1 + c] = q[1 + c] * un + q[0] * nh[c];
+}
+
+/* A = d F_n / d q, rows/cols ordered (p, u, v, w). */
+void or_flux_jacobian(const double q[4], const double nh[3], double c0sq, double A[16]) {
+  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+  memset(A, 0, 16 * sizeof(double));
+  for (int c = 0; c < 3; ++c) A[0 * 4 + 1 + c] = c0sq * nh[c];
+  for (int r = 0; r < 3; ++r) {
+    A[(1 + r) * 4 + 0] = nh[r];
+    for (int c = 0; c < 3; ++c) A[(1 + r) * 4 + 1 + c] = q[1 + r] * nh[c] + (r == c ? un : 0.0);
+  }
+}
+
+/* |A| = R |Lambda| R^{-1} from the explicit eigen-decomposition of A:
+ *   lambda = u_n (twice, eigenvectors (0, t) with t tangent to the face),
+ *   lambda = u_n +- sqrt(u_n^2 + c0^2), eigenvectors with n . u_hat = 1,
+ *     p_hat = lambda - 2 u_n, u_hat = (n p_hat + u) / (lambda - u_n).
+ * R^{-1} is formed numerically (Gauss-Jordan), not from a closed form. */
+int or_abs_jacobian(const double q[4], const double nh[3], double c0sq, double absA[16]) {
+  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+  double a = sqrt(un * un + c0sq);
+  double lam[4] = {un, un, un + a, un - a};
+  /* tangent vectors: t1 = normalize(e x n) with e the axis least aligned with n */
+  int ax = 0;
+  if (fabs(nh[1]) < fabs(nh[ax])) ax = 1;
+  if (fabs(nh[2]) < fabs(nh[ax])) ax = 2;
+  double e[3] = {0, 0, 0};
+  e[ax] = 1.0;
+  double t1[3] = {e[1] * nh[2] - e[2] * nh[1], e[2] * nh[0] - e[0] * nh[2], e[0] * nh[1] - e[1] * nh[0]};
+  double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int c = 0; c < 3; ++c) t1[c] /= l1;
+  double t2[3] = {nh[1] * t1[2] - nh[2] * t1[1], nh[2] * t1[0] - nh[0] * t1[2], nh[0] * t1[1] - nh[1] * t1[0]};
+  double R[16], Rinv[16], Rw[16];
+  /* column k of R = eigenvector k */
+  for (int r = 0; r < 4; ++r) R[r * 4 + 0] = (r == 0) ? 0.0 : t1[r - 1];
+  for (int r = 0; r < 4; ++r) R[r * 4 + 1] = (r == 0) ? 0.0 : t2[r - 1];
+  for (int k = 2; k < 4; ++k) {
+    double ph = lam[k] - 2.0 * un;
+    R[0 * 4 + k] = ph;
+    for (int c = 0; c < 3; ++c) R[(1 + c) * 4 + k] = (nh[c] * ph + q[1 + c]) / (lam[k] - un);
+  }
+  memcpy(Rw, R, sizeof R);
+  for (int i = 0; i < 16; ++i) Rinv[i] = (i % 5 == 0) ? 1.0 : 0.0;
+  if (gauss_jordan(4, Rw, 4, Rinv)) {
+    set_err("singular eigenvector matrix");
+    return -1;
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += R[i * 4 + k] * fabs(lam[k]) * Rinv[k * 4 + j];
+      absA[i * 4 + j] = s;
+    }
+  return 0;
+}
+
+/* Convective numerical flux through a face with unit normal nh pointing from the
+ * qm side to the qp side (Sec. 2.3: Roe; LLF as the alternative flux). */
+int or_riemann(const double qm[4], const double qp[4], const double nh[3], const or_params* prm,
+               double out[4]) {
+  double fm[4], fp[4];
+  or_normal_flux(qm, nh, prm->c0sq, fm);
+  or_normal_flux(qp, nh, prm->c0sq, fp);
+  if (prm->riemann == 0) {
+    double qb[4], absA[16];
+    for (int v = 0; v < 4; ++v) qb[v] = 0.5 * (qm[v] + qp[v]);
+    if (or_abs_jacobian(qb, nh, prm->c0sq, absA)) return -1;
+    for (int v = 0; v < 4; ++v) {
+      double d = 0.0;
+      for (int k = 0; k < 4; ++k) d += absA[v * 4 + k] * (qp[k] - qm[k]);
+      out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * d;
+    }
+  } else {
+    double unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+    double unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
+    double sm = fabs(unm) + sqrt(unm * unm + prm->c0sq);
+    double sp = fabs(unp) + sqrt(unp * unp + prm->c0sq);
+    double s = sm > sp ? sm : sp;
+    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * s * (qp[v] - qm[v]);
+  }
+  return 0;
+}
+
+/* LES eddy viscosity (App. A, Eq. for the Vreman model; Smagorinsky as the alternative
+ * closure): G[c*3+k] = d u_c / d x_k, delta the filter width. */
+double or_eddy_viscosity(const double G[9], double delta, const or_params* prm) {
+  if (prm->closure == 0) {
+    double ss = 0.0;
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.5 * (G[c * 3 + k] + G[k * 3 + c]);
+        ss += s * s;
+      }
+    double cd = prm->cs * delta;
+    return cd * cd * sqrt(2.0 * ss);
+  }
+  /* Vreman: alpha_ij = d u_j / d x_i, beta_ij = delta^2 alpha_mi alpha_mj */
+  double al[3][3], aa = 0.0, be[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      al[i][j] = G[j * 3 + i];
+      aa += al[i][j] * al[i][j];
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < 3; ++m) s += al[m][i] * al[m][j];
+      be[i][j] = delta * delta * s;
+    }
+  double B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] - be[0][2] * be[0][2] +
+             be[1][1] * be[2][2] - be[1][2] * be[1][2];
+  if (aa < 1e-300 || B <= 0.0) return 0.0;
+  return prm->cv * sqrt(B / aa);
+}
+
+/* Low-storage third-order Runge-Kutta (Sec. 2.3 cites a low-storage explicit RK3; the
+ * Williamson 2N-storage coefficients are used):  g <- A_s g + dt R(q),  q <- q + B_s g. */
+static const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+double or_rk3_linear(double z) {
+  double y = 1.0, g = 0.0;
+  for (int s = 0; s < 3; ++s) {
+    g = (s == 0 ? 0.0 : RK_A[s] * g) + z * y;
+    y = y + RK_B[s] * g;
+  }
+  return y;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Mesh
+ * ---------------------------------------------------------------------------------- */
+
+typedef struct {
+  double x[OR_MAXN + 1], w[OR_MAXN + 1], D[(OR_MAXN + 1) * (OR_MAXN + 1)];
+} op1d;
+
+struct or_mesh {
+  int64_t ne, total;
+  int g;
+  int8_t* N;
+  uint8_t* flag;
+  int64_t* off;
+  double* gx;     /* [ne][(g+1)^3][3] */
+  int64_t* nb_e;  /* [ne][6]: neighbour element, -1 at a boundary */
+  int8_t* nb_f;   /* [ne][6]: neighbour local face */
+  int8_t* nb_o;   /* [ne][6]: orientation code mapping neighbour face coords to mine */
+  int8_t* bc;     /* [ne][6]: boundary tag (-1 interior) */
+  double* vscale; /* [ne] */
+  or_params p;
+  op1d op[OR_MAXN + 1];
+};
+
+int64_t or_total_nodes(const or_mesh* m) { return m->total; }
+const int64_t* or_offsets(const or_mesh* m) { return m->off; }
+
+/* Local faces: f = 2 d + s on the plane xi_d = (s ? +1 : -1). Face coordinates (a, b) run
+ * along the two remaining directions in increasing order. */
+static void face_dirs(int d, int* t0, int* t1) {
+  *t0 = (d == 0) ? 1 : 0;
+  *t1 = (d == 2) ? 1 : 2;
+}
+static int64_t face_node(int f, int N, int a, int b) {
+  int d = f >> 1, s = f & 1, t0, t1, ijk[3];
+  face_dirs(d, &t0, &t1);
+  ijk[d] = s ? N : 0;
+  ijk[t0] = a;
+  ijk[t1] = b;
+  int n = N + 1;
+  return ijk[0] + (int64_t)n * (ijk[1] + (int64_t)n * ijk[2]);
+}
+static int face_corner(int f, int ca, int cb) {
+  int d = f >> 1, s = f & 1, t0, t1, c[3];
+  face_dirs(d, &t0, &t1);
+  c[d] = s;
+  c[t0] = ca;
+  c[t1] = cb;
+  return c[0] + 2 * c[1] + 4 * c[2];
+}
+/* Orientation code o = swap | flip_a << 1 | flip_b << 2 maps neighbour face coords
+ * (a1, b1) at order M to mine: (x, y) = swap ? (b1, a1) : (a1, b1); a0 = flip_a ? M - x : x;
+ * b0 = flip_b ? M - y : y. */
+static void orient_map(int o, int M, int a1, int b1, int* a0, int* b0) {
+  int x = (o & 1) ? b1 : a1, y = (o & 1) ? a1 : b1;
+  *a0 = (o & 2) ? M - x : x;
+  *b0 = (o & 4) ? M - y : y;
+}
+
+typedef struct {
+  int64_t k[4];
+  int64_t e;
+  int f;
+} face_rec;
+
+static int cmp_face(const void* A, const void* B) {
+  const face_rec* a = (const face_rec*)A;
+  const face_rec* b = (const face_rec*)B;
+  for (int i = 0; i < 4; ++i)
+    if (a->k[i] != b->k[i]) return a->k[i] < b->k[i] ? -1 : 1;
+  if (a->e != b->e) return a->e < b->e ? -1 : 1;
+  return a->f - b->f;
+}
+
+void or_destroy(or_mesh* m) {
+  if (!m) return;
+  free(m->N);
+  free(m->flag);
+  free(m->off);
+  free(m->gx);
+  free(m->nb_e);
+  free(m->nb_f);
+  free(m->nb_o);
+  free(m->bc);
+  free(m->vscale);
+  free(m);
+}
+
+or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const double* gxyz, const int8_t* bc_tag,
+                   const int8_t* order, const uint8_t* flag, const or_params* prm) {
+  if (ne <= 0 || !hex || !gxyz || !order || !flag || !prm) {
+    set_err("bad arguments");
+    return NULL;
+  }
+  if (g < 1 || g > OR_MAXG) {
+    set_err("geometry degree %d unsupported", g);
+    return NULL;
+  }
+  or_mesh* m = (or_mesh*)calloc(1, sizeof(or_mesh));
+  m->ne = ne;
+  m->g = g;
+  m->p = *prm;
+  for (int N = 1; N <= OR_MAXN; ++N) {
+    or_lgl(N, m->op[N].x, m->op[N].w);
+    or_dmat(N, m->op[N].D);
+  }
+  int ng = g + 1, ng3 = ng * ng * ng;
+  m->N = (int8_t*)malloc(ne);
+  m->flag = (uint8_t*)malloc(ne);
+  m->off = (int64_t*)malloc(sizeof(int64_t) * (ne + 1));
+  m->gx = (double*)malloc(sizeof(double) * ne * ng3 * 3);
+  m->nb_e = (int64_t*)malloc(sizeof(int64_t) * ne * 6);
+  m->nb_f = (int8_t*)malloc(ne * 6);
+  m->nb_o = (int8_t*)malloc(ne * 6);
+  m->bc = (int8_t*)malloc(ne * 6);
+  m->vscale = (double*)malloc(sizeof(double) * ne);
+  memcpy(m->gx, gxyz, sizeof(double) * ne * ng3 * 3);
+  m->off[0] = 0;
+  for (int64_t e = 0; e < ne; ++e) {
+    if (order[e] < 1 || order[e] > OR_MAXN || order[e] < g) {
+      set_err("element %lld: order %d invalid (geometry degree %d)", (long long)e, order[e], g);
+      or_destroy(m);
+      return NULL;
+    }
+    if (flag[e] > 1) {
+      set_err("element %lld: flag %d invalid", (long long)e, flag[e]);
+      or_destroy(m);
+      return NULL;
+    }
+    m->N[e] = order[e];
+    m->flag[e] = flag[e];
+    m->vscale[e] = 1.0;
+    int n = order[e] + 1;
+    m->off[e + 1] = m->off[e] + (int64_t)n * n * n;
+    for (int f = 0; f < 6; ++f) {
+      m->nb_e[e * 6 + f] = -1;
+      m->nb_f[e * 6 + f] = -1;
+      m->nb_o[e * 6 + f] = 0;
+      m->bc[e * 6 + f] = bc_tag ? bc_tag[e * 6 + f] : -1;
+    }
+  }
+  m->total = m->off[ne];
+
+  /* face matching by the sorted corner vertex ids */
+  face_rec* rec = (face_rec*)malloc(sizeof(face_rec) * ne * 6);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      face_rec* r = &rec[e * 6 + f];
+      for (int c = 0; c < 4; ++c) r->k[c] = hex[e * 8 + face_corner(f, c & 1, c >> 1)];
+      for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j) {
+          if (r->k[i] == r->k[j]) {
+            set_err("element %lld face %d has repeated vertex ids", (long long)e, f);
+            free(rec);
+            or_destroy(m);
+            return NULL;
+          }
+          if (r->k[j] < r->k[i]) {
+            int64_t t = r->k[i];
+            r->k[i] = r->k[j];
+            r->k[j] = t;
+          }
+        }
+      r->e = e;
+      r->f = f;
+    }
+  qsort(rec, (size_t)ne * 6, sizeof(face_rec), cmp_face);
+  int64_t i = 0;
+  while (i < ne * 6) {
+    int64_t j = i + 1;
+    while (j < ne * 6 && memcmp(rec[j].k, rec[i].k, sizeof rec[i].k) == 0) ++j;
+    if (j - i > 2) {
+      set_err("a face is shared by more than two elements");
+      free(rec);
+      or_destroy(m);
+      return NULL;
+    }
+    if (j - i == 1) {
+      if (m->bc[rec[i].e * 6 + rec[i].f] < 1) {
+        set_err("element %lld face %d is unmatched and has no boundary tag", (long long)rec[i].e, rec[i].f);
+        free(rec);
+        or_destroy(m);
+        return NULL;
+      }
+    } else {
+      for (int s = 0; s < 2; ++s) {
+        int64_t e0 = rec[i + s].e, e1 = rec[i + 1 - s].e;
+        int f0 = rec[i + s].f, f1 = rec[i + 1 - s].f;
+        if (m->bc[e0 * 6 + f0] >= 1) {
+          set_err("element %lld face %d is interior but carries a boundary tag", (long long)e0, f0);
+          free(rec);
+          or_destroy(m);
+          return NULL;
+        }
+        int found = -1;
+        for (int o = 0; o < 8 && found < 0; ++o) {
+          int ok = 1;
+          for (int cb = 0; cb < 2 && ok; ++cb)
+            for (int ca = 0; ca < 2 && ok; ++ca) {
+              int a0, b0;
+              orient_map(o, 1, ca, cb, &a0, &b0);
+              if (hex[e1 * 8 + face_corner(f1, ca, cb)] != hex[e0 * 8 + face_corner(f0, a0, b0)]) ok = 0;
+            }
+          if (ok) found = o;
+        }
+        if (found < 0) {
+          set_err("no orientation matches element %lld face %d", (long long)e0, f0);
+          free(rec);
+          or_destroy(m);
+          return NULL;
+        }
+        m->nb_e[e0 * 6 + f0] = e1;
+        m->nb_f[e0 * 6 + f0] = (int8_t)f1;
+        m->nb_o[e0 * 6 + f0] = (int8_t)found;
+      }
+    }
+    i = j;
+  }
+  free(rec);
+  return m;
+}
+
+int or_set_visc_scale(or_mesh* m, const double* scale) {
+  for (int64_t e = 0; e < m->ne; ++e) m->vscale[e] = scale ? scale[e] : 1.0;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Geometry (App. B: transfinite polynomial map x(xi), Jacobian J, contravariant metric).
+ * Metric terms in the curl (conservative) form, computed at the geometry degree g and
+ * interpolated to the element's nodes (exact because N >= g):
+ *   Ja^i_n = - e_i . curl_xi ( I^g( X_l grad_xi X_m ) ),  (n, m, l) cyclic.
+ * J = det(dX/dxi) of the degree-g map at the element's nodes.
+ * ---------------------------------------------------------------------------------- */
+
+/* derivative along direction k of a field on an n^3 tensor grid with matrix D (n x n) */
+static void deriv3(int n, const double* D, int k, const double* u, double* du) {
+  for (int c = 0; c < n; ++c)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        int ijk[3] = {a, b, c};
+        double s = 0.0;
+        for (int mm = 0; mm < n; ++mm) {
+          int src[3] = {a, b, c};
+          src[k] = mm;
+          s += D[ijk[k] * n + mm] * u[src[0] + n * (src[1] + n * src[2])];
+        }
+        du[a + n * (b + n * c)] = s;
+      }
+}
+
+/* tensor interpolation from an ns^3 grid to an nd^3 grid with I (nd x ns) */
+static void interp3(int ns, int nd, const double* I, const double* u, double* out) {
+  for (int k = 0; k < nd; ++k)
+    for (int j = 0; j < nd; ++j)
+      for (int i = 0; i < nd; ++i) {
+        double s = 0.0;
+        for (int c = 0; c < ns; ++c)
+          for (int b = 0; b < ns; ++b)
+            for (int a = 0; a < ns; ++a)
+              s += I[i * ns + a] * I[j * ns + b] * I[k * ns + c] * u[a + ns * (b + ns * c)];
+        out[i + nd * (j + nd * k)] = s;
+      }
+}
+
+int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja) {
+  int g = m->g, ng = g + 1, ng3 = ng * ng * ng;
+  int N = m->N[e], n = N + 1, n3 = n * n * n;
+  const double* Dg = m->op[g].D;
+  double I[(OR_MAXN + 1) * (OR_MAXG + 1)];
+  or_interp_lgl(g, N, I);
+  double X[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+  double dX[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+  for (int p = 0; p < ng3; ++p)
+    for (int c = 0; c < 3; ++c) X[c][p] = m->gx[(e * ng3 + p) * 3 + c];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) deriv3(ng, Dg, k, X[c], dX[c][k]);
+  /* J at the element nodes */
+  double* dXn = (double*)malloc(sizeof(double) * 9 * n3);
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) interp3(ng, n, I, dX[c][k], dXn + (c * 3 + k) * n3);
+  for (int p = 0; p < n3; ++p) {
+    double a[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 3; ++k) a[c][k] = dXn[(c * 3 + k) * n3 + p];
+    J[p] = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+           a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  }
+  free(dXn);
+  /* curl form at degree g */
+  for (int nn = 0; nn < 3; ++nn) {
+    int mm = (nn + 1) % 3, ll = (nn + 2) % 3;
+    double v[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    double dv[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    for (int k = 0; k < 3; ++k)
+      for (int p = 0; p < ng3; ++p) v[k][p] = X[ll][p] * dX[mm][k][p];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) deriv3(ng, Dg, d, v[k], dv[k][d]); /* dv[k][d] = d v_k / d xi_d */
+    double curl[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    for (int p = 0; p < ng3; ++p) {
+      curl[0][p] = dv[2][1][p] - dv[1][2][p];
+      curl[1][p] = dv[0][2][p] - dv[2][0][p];
+      curl[2][p] = dv[1][0][p] - dv[0][1][p];
+    }
+    for (int i = 0; i < 3; ++i) {
+      double neg[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+      for (int p = 0; p < ng3; ++p) neg[p] = -curl[i][p];
+      interp3(ng, n, I, neg, Ja + (i * 3 + nn) * n3);
+    }
+  }
+  return 0;
+}
+
+int or_node_coords(const or_mesh* m, double* xyz) {
+  int g = m->g, ng = g + 1, ng3 = ng * ng * ng;
+  for (int64_t e = 0; e < m->ne; ++e) {
+    int N = m->N[e], n = N + 1, n3 = n * n * n;
+    double I[(OR_MAXN + 1) * (OR_MAXG + 1)];
+    or_interp_lgl(g, N, I);
+    double X[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    double* out = (double*)malloc(sizeof(double) * n3);
+    for (int c = 0; c < 3; ++c) {
+      for (int p = 0; p < ng3; ++p) X[p] = m->gx[(e * ng3 + p) * 3 + c];
+      interp3(ng, n, I, X, out);
+      for (int p = 0; p < n3; ++p) xyz[c * m->total + m->off[e] + p] = out[p];
+    }
+    free(out);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Residual machinery
+ * ---------------------------------------------------------------------------------- */
+
+typedef struct {
+  double* J;   /* [n3] */
+  double* Ja;  /* [3][3][n3] */
+  double delta;
+} geo_t;
+
+typedef struct {
+  const or_mesh* m;
+  const double* q;
+  geo_t* geo;    /* per element, J == NULL if not computed */
+  double** G;    /* per element gradient [3][3][n3], NULL if not computed */
+} work_t;
+
+static void compute_geo(const or_mesh* m, int64_t e, geo_t* gt) {
+  int n = m->N[e] + 1, n3 = n * n * n;
+  gt->J = (double*)malloc(sizeof(double) * n3);
+  gt->Ja = (double*)malloc(sizeof(double) * 9 * n3);
+  or_element_geometry(m, e, gt->J, gt->Ja);
+  const double* w = m->op[m->N[e]].w;
+  double V = 0.0;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) V += w[i] * w[j] * w[k] * gt->J[i + n * (j + n * k)];
+  /* filter width: cube root of the element volume over the nodes per direction */
+  gt->delta = cbrt(V) / n;
+}
+
+/* 2D tensor interpolation on a face: ns^2 -> nd^2 with I (nd x ns) */
+static void interp2(int ns, int nd, const double* I, const double* u, double* out) {
+  for (int b = 0; b < nd; ++b)
+    for (int a = 0; a < nd; ++a) {
+      double s = 0.0;
+      for (int bb = 0; bb < ns; ++bb)
+        for (int aa = 0; aa < ns; ++aa) s += I[a * ns + aa] * I[b * ns + bb] * u[aa + ns * bb];
+      out[a + nd * b] = s;
+    }
+}
+
+/* outward area-weighted normal S = sigma Ja^d at the face nodes of element e, face f */
+static void face_S(const or_mesh* m, const geo_t* gt, int64_t e, int f, double* S /*[3][n2]*/) {
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  int d = f >> 1;
+  double sg = (f & 1) ? 1.0 : -1.0;
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      int64_t p = face_node(f, N, a, b);
+      for (int c = 0; c < 3; ++c) S[c * n2 + a + n * b] = sg * gt->Ja[(d * 3 + c) * n3 + p];
+    }
+}
+
+static void face_q(const or_mesh* m, const double* q, int64_t e, int f, double* T /*[4][n2]*/) {
+  int N = m->N[e], n = N + 1, n2 = n * n;
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      int64_t p = m->off[e] + face_node(f, N, a, b);
+      for (int v = 0; v < 4; ++v) T[v * n2 + a + n * b] = q[v * m->total + p];
+    }
+}
+
+/* viscous stress at one node of an NS element */
+static void stress(const or_mesh* m, const geo_t* gt, const double* G, int64_t e, int n3, int64_t p,
+                   double tau[3][3]) {
+  double Gp[9];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) Gp[c * 3 + k] = G[(c * 3 + k) * n3 + p];
+  double nut = or_eddy_viscosity(Gp, gt->delta, &m->p);
+  double mu = (m->p.nu + nut) * m->vscale[e];
+  double tr = Gp[0] + Gp[4] + Gp[8];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) tau[c][k] = mu * (Gp[c * 3 + k] + Gp[k * 3 + c]) - (c == k ? 2.0 / 3.0 * mu * tr : 0.0);
+}
+
+/* area-weighted outward viscous flux trace tau . S of element e on face f (zero for Euler) */
+static void face_fv(const work_t* W, int64_t e, int f, double* Fv /*[3][n2]*/) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  if (!m->flag[e]) {
+    memset(Fv, 0, sizeof(double) * 3 * n2);
+    return;
+  }
+  const geo_t* gt = &W->geo[e];
+  double* S = (double*)malloc(sizeof(double) * 3 * n2);
+  face_S(m, gt, e, f, S);
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      int64_t p = face_node(f, N, a, b);
+      double tau[3][3];
+      stress(m, gt, W->G[e], e, n3, p, tau);
+      for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s += tau[c][k] * S[k * n2 + a + n * b];
+        Fv[c * n2 + a + n * b] = s;
+      }
+    }
+  free(S);
+}
+
+static void ghost_state(const or_mesh* m, int tag, const double* qin, double* qg) {
+  if (tag == 1) { /* inflow: prescribed velocity, interior pressure */
+    qg[0] = qin[0];
+    for (int c = 0; c < 3; ++c) qg[1 + c] = m->p.inflow[1 + c];
+  } else { /* outflow: interior velocity, zero pressure */
+    qg[0] = 0.0;
+    for (int c = 0; c < 3; ++c) qg[1 + c] = qin[1 + c];
+  }
+}
+
+/* Mortar data of face (e, f) in e's face coordinates at order M = max(N_e, N_nbr):
+ * my trace, the neighbour trace (or ghost), my S interpolated. */
+typedef struct {
+  int M, nm;          /* mortar order, my order */
+  double* qm;         /* [4][(M+1)^2] */
+  double* qp;         /* [4][(M+1)^2] */
+  double* S;          /* [3][(M+1)^2] */
+  int64_t nbr;        /* -1 at a boundary */
+  int nf, no, tag;
+} mortar_t;
+
+static void mortar_free(mortar_t* mt) {
+  free(mt->qm);
+  free(mt->qp);
+  free(mt->S);
+}
+
+/* interpolate a neighbour face field (order Nn) to the mortar order M and rotate it into
+ * my face coordinates */
+static void nbr_to_mortar(int Nn, int M, int o, int nvar, const double* src, double* dst) {
+  int nn = Nn + 1, nM = M + 1, nM2 = nM * nM;
+  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_interp_lgl(Nn, M, I);
+  double* tmp = (double*)malloc(sizeof(double) * nM2);
+  for (int v = 0; v < nvar; ++v) {
+    interp2(nn, nM, I, src + v * nn * nn, tmp);
+    for (int b1 = 0; b1 < nM; ++b1)
+      for (int a1 = 0; a1 < nM; ++a1) {
+        int a0, b0;
+        orient_map(o, M, a1, b1, &a0, &b0);
+        dst[v * nM2 + a0 + nM * b0] = tmp[a1 + nM * b1];
+      }
+  }
+  free(tmp);
+}
+
+static void mine_to_mortar(int Nm, int M, int nvar, const double* src, double* dst) {
+  int nm = Nm + 1, nM = M + 1;
+  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_interp_lgl(Nm, M, I);
+  for (int v = 0; v < nvar; ++v) interp2(nm, nM, I, src + v * nm * nm, dst + v * nM * nM);
+}
+
+/* project a mortar field (order M, my coordinates) to my order */
+static void mortar_to_mine(int M, int Nm, int nvar, const double* src, double* dst) {
+  int nm = Nm + 1, nM = M + 1;
+  double P[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_project_lgl(M, Nm, P);
+  for (int v = 0; v < nvar; ++v) interp2(nM, nm, P, src + v * nM * nM, dst + v * nm * nm);
+}
+
+static void mortar_build(const work_t* W, int64_t e, int f, mortar_t* mt) {
+  const or_mesh* m = W->m;
+  int Nm = m->N[e], nm = Nm + 1;
+  int64_t nb = m->nb_e[e * 6 + f];
+  int Nn = nb >= 0 ? m->N[nb] : Nm;
+  int M = Nm > Nn ? Nm : Nn, nM = M + 1, nM2 = nM * nM;
+  mt->M = M;
+  mt->nm = Nm;
+  mt->nbr = nb;
+  mt->nf = m->nb_f[e * 6 + f];
+  mt->no = m->nb_o[e * 6 + f];
+  mt->tag = m->bc[e * 6 + f];
+  mt->qm = (double*)malloc(sizeof(double) * 4 * nM2);
+  mt->qp = (double*)malloc(sizeof(double) * 4 * nM2);
+  mt->S = (double*)malloc(sizeof(double) * 3 * nM2);
+  double* tq = (double*)malloc(sizeof(double) * 4 * nm * nm);
+  double* tS = (double*)malloc(sizeof(double) * 3 * nm * nm);
+  face_q(m, W->q, e, f, tq);
+  face_S(m, &W->geo[e], e, f, tS);
+  mine_to_mortar(Nm, M, 4, tq, mt->qm);
+  mine_to_mortar(Nm, M, 3, tS, mt->S);
+  if (nb >= 0) {
+    int nn = Nn + 1;
+    double* tn = (double*)malloc(sizeof(double) * 4 * nn * nn);
+    face_q(m, W->q, nb, mt->nf, tn);
+    nbr_to_mortar(Nn, M, mt->no, 4, tn, mt->qp);
+    free(tn);
+  } else {
+    for (int p = 0; p < nM2; ++p) {
+      double qi[4], qg[4];
+      for (int v = 0; v < 4; ++v) qi[v] = mt->qm[v * nM2 + p];
+      ghost_state(m, mt->tag, qi, qg);
+      for (int v = 0; v < 4; ++v) mt->qp[v * nM2 + p] = qg[v];
+    }
+  }
+  free(tq);
+  free(tS);
+}
+
+/* BR1 lifting data on face (e, f): projected u*_c S_k, shape [3][3][n2] */
+static void face_ustar(const work_t* W, int64_t e, int f, double* LU) {
+  mortar_t mt;
+  mortar_build(W, e, f, &mt);
+  int nM = mt.M + 1, nM2 = nM * nM;
+  double* U = (double*)malloc(sizeof(double) * 9 * nM2);
+  for (int p = 0; p < nM2; ++p)
+    for (int c = 0; c < 3; ++c) {
+      double us = 0.5 * (mt.qm[(1 + c) * nM2 + p] + mt.qp[(1 + c) * nM2 + p]);
+      for (int k = 0; k < 3; ++k) U[(c * 3 + k) * nM2 + p] = us * mt.S[k * nM2 + p];
+    }
+  mortar_to_mine(mt.M, mt.nm, 9, U, LU);
+  free(U);
+  mortar_free(&mt);
+}
+
+/* Total numerical flux on face (e, f): projected (F_e* - F_v*) . S (my outward), [4][n2] */
+static int face_hstar(const work_t* W, int64_t e, int f, double* LH) {
+  const or_mesh* m = W->m;
+  mortar_t mt;
+  mortar_build(W, e, f, &mt);
+  int nM = mt.M + 1, nM2 = nM * nM, nm = mt.nm + 1, nm2 = nm * nm;
+  double* H = (double*)malloc(sizeof(double) * 4 * nM2);
+  double* Fvm = (double*)calloc(3 * nM2, sizeof(double));
+  double* Fvp = (double*)calloc(3 * nM2, sizeof(double));
+  int any_visc = m->flag[e] || (mt.nbr >= 0 && m->flag[mt.nbr]);
+  if (any_visc) {
+    double* t = (double*)malloc(sizeof(double) * 3 * nm2);
+    face_fv(W, e, f, t);
+    mine_to_mortar(mt.nm, mt.M, 3, t, Fvm);
+    free(t);
+    if (mt.nbr >= 0) {
+      int nn = m->N[mt.nbr] + 1;
+      double* tn = (double*)malloc(sizeof(double) * 3 * nn * nn);
+      face_fv(W, mt.nbr, mt.nf, tn);
+      nbr_to_mortar(m->N[mt.nbr], mt.M, mt.no, 3, tn, Fvp);
+      free(tn);
+    } else {
+      /* boundary: the ghost carries the interior viscous flux, pointing the other way */
+      for (int i = 0; i < 3 * nM2; ++i) Fvp[i] = -Fvm[i];
+    }
+  }
+  int rc = 0;
+  for (int p = 0; p < nM2; ++p) {
+    double S[3] = {mt.S[p], mt.S[nM2 + p], mt.S[2 * nM2 + p]};
+    double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    double nh[3] = {S[0] / s, S[1] / s, S[2] / s};
+    double qm[4], qp[4], Fs[4];
+    for (int v = 0; v < 4; ++v) {
+      qm[v] = mt.qm[v * nM2 + p];
+      qp[v] = mt.qp[v * nM2 + p];
+    }
+    if (or_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
+    H[p] = Fs[0] * s;
+    for (int c = 0; c < 3; ++c) {
+      double fv = 0.5 * (Fvm[c * nM2 + p] - Fvp[c * nM2 + p]);
+      H[(1 + c) * nM2 + p] = Fs[1 + c] * s - fv;
+    }
+  }
+  mortar_to_mine(mt.M, mt.nm, 4, H, LH);
+  free(H);
+  free(Fvm);
+  free(Fvp);
+  mortar_free(&mt);
+  return rc;
+}
+
+/* BR1 gradient, weak form (integrated by parts, Bassi-Rebay 1):
+ *   w J G_ck = -sum_d (w/w_{i_d}) sum_m w_m D_{m i_d} (u_c Ja^d_k)_m + face terms u*_c S_k */
+static void element_gradient(const work_t* W, int64_t e, double* G) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  const double* w = m->op[N].w;
+  const double* D = m->op[N].D;
+  const geo_t* gt = &W->geo[e];
+  const double* q = W->q;
+  int64_t o = m->off[e];
+  memset(G, 0, sizeof(double) * 9 * n3);
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) {
+      double* Gck = G + (c * 3 + k) * n3;
+      for (int kk = 0; kk < n; ++kk)
+        for (int jj = 0; jj < n; ++jj)
+          for (int ii = 0; ii < n; ++ii) {
+            int ijk[3] = {ii, jj, kk};
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              double sd = 0.0;
+              for (int mm = 0; mm < n; ++mm) {
+                int src[3] = {ii, jj, kk};
+                src[d] = mm;
+                int64_t ps = src[0] + n * (src[1] + n * src[2]);
+                sd += w[mm] * D[mm * n + ijk[d]] * q[(1 + c) * m->total + o + ps] * gt->Ja[(d * 3 + k) * n3 + ps];
+              }
+              s -= sd / w[ijk[d]];
+            }
+            Gck[ii + n * (jj + n * kk)] = s;
+          }
+    }
+  double* LU = (double*)malloc(sizeof(double) * 9 * n2);
+  for (int f = 0; f < 6; ++f) {
+    face_ustar(W, e, f, LU);
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        int64_t p = face_node(f, N, a, b);
+        for (int ck = 0; ck < 9; ++ck) G[ck * n3 + p] += LU[ck * n2 + a + n * b] / w[0];
+      }
+  }
+  free(LU);
+  for (int ck = 0; ck < 9; ++ck)
+    for (int p = 0; p < n3; ++p) G[ck * n3 + p] /= gt->J[p];
+}
+
+int or_element_gradient(const or_mesh* m, const double* q, int64_t e, double* G) {
+  if (e < 0 || e >= m->ne) return -1;
+  work_t W;
+  W.m = m;
+  W.q = q;
+  W.geo = (geo_t*)calloc(m->ne, sizeof(geo_t));
+  W.G = NULL;
+  compute_geo(m, e, &W.geo[e]);
+  element_gradient(&W, e, G);
+  free(W.geo[e].J);
+  free(W.geo[e].Ja);
+  free(W.geo);
+  return 0;
+}
+
+/* Residual of one element, weak form (App. B, Eq. NS4 with the viscous terms integrated
+ * by parts under BR1):
+ *   w J R = sum_d (w / w_{i_d}) sum_m w_m D_{m i_d} Ftil^d_m - w_face H*  */
+static int element_residual(const work_t* W, int64_t e, double* R) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  const double* w = m->op[N].w;
+  const double* D = m->op[N].D;
+  const geo_t* gt = &W->geo[e];
+  const double* q = W->q;
+  int64_t o = m->off[e], T = m->total;
+  double c0sq = m->p.c0sq;
+  /* contravariant total flux Ftil[d][v][p] = sum_k Ja^d_k (F_e - F_v)_{v,k} */
+  double* Ft = (double*)malloc(sizeof(double) * 12 * n3);
+  for (int p = 0; p < n3; ++p) {
+    double qq[4];
+    for (int v = 0; v < 4; ++v) qq[v] = q[v * T + o + p];
+    double F[4][3];
+    for (int k = 0; k < 3; ++k) {
+      F[0][k] = c0sq * qq[1 + k];
+      for (int c = 0; c < 3; ++c) F[1 + c][k] = qq[1 + c] * qq[1 + k] + (c == k ? qq[0] : 0.0);
+    }
+    if (m->flag[e]) {
+      double tau[3][3];
+      stress(m, gt, W->G[e], e, n3, p, tau);
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 3; ++k) F[1 + c][k] -= tau[c][k];
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 4; ++v) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s += gt->Ja[(d * 3 + k) * n3 + p] * F[v][k];
+        Ft[(d * 4 + v) * n3 + p] = s;
+      }
+  }
+  double* JR = (double*)calloc(4 * n3, sizeof(double));
+  for (int v = 0; v < 4; ++v)
+    for (int kk = 0; kk < n; ++kk)
+      for (int jj = 0; jj < n; ++jj)
+        for (int ii = 0; ii < n; ++ii) {
+          int ijk[3] = {ii, jj, kk};
+          double s = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            double sd = 0.0;
+            for (int mm = 0; mm < n; ++mm) {
+              int src[3] = {ii, jj, kk};
+              src[d] = mm;
+              sd += w[mm] * D[mm * n + ijk[d]] * Ft[(d * 4 + v) * n3 + src[0] + n * (src[1] + n * src[2])];
+            }
+            s += sd / w[ijk[d]];
+          }
+          JR[v * n3 + ii + n * (jj + n * kk)] = s;
+        }
+  double* LH = (double*)malloc(sizeof(double) * 4 * n2);
+  int rc = 0;
+  for (int f = 0; f < 6; ++f) {
+    if (face_hstar(W, e, f, LH)) rc = -1;
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        int64_t p = face_node(f, N, a, b);
+        for (int v = 0; v < 4; ++v) JR[v * n3 + p] -= LH[v * n2 + a + n * b] / w[0];
+      }
+  }
+  for (int v = 0; v < 4; ++v)
+    for (int p = 0; p < n3; ++p) R[v * T + o + p] = JR[v * n3 + p] / gt->J[p];
+  free(LH);
+  free(JR);
+  free(Ft);
+  return rc;
+}
+
+static void free_work(work_t* W) {
+  for (int64_t e = 0; e < W->m->ne; ++e) {
+    free(W->geo[e].J);
+    free(W->geo[e].Ja);
+    if (W->G) free(W->G[e]);
+  }
+  free(W->geo);
+  free(W->G);
+}
+
+int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, const int64_t* sel) {
+  int64_t ne = m->ne;
+  /* elements whose residual is wanted */
+  uint8_t* want = (uint8_t*)calloc(ne, 1);
+  if (sel) {
+    for (int64_t i = 0; i < n_sel; ++i) {
+      if (sel[i] < 0 || sel[i] >= ne) {
+        free(want);
+        set_err("selected element out of range");
+        return -1;
+      }
+      want[sel[i]] = 1;
+    }
+  } else {
+    memset(want, 1, ne);
+  }
+  /* geometry is needed on the wanted elements and their face neighbours; gradients on
+   * the NS elements among them */
+  uint8_t* need = (uint8_t*)calloc(ne, 1);
+  for (int64_t e = 0; e < ne; ++e)
+    if (want[e]) {
+      need[e] = 1;
+      for (int f = 0; f < 6; ++f)
+        if (m->nb_e[e * 6 + f] >= 0) need[m->nb_e[e * 6 + f]] = 1;
+    }
+  work_t W;
+  W.m = m;
+  W.q = q;
+  W.geo = (geo_t*)calloc(ne, sizeof(geo_t));
+  W.G = (double**)calloc(ne, sizeof(double*));
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * ne);
+  int64_t nl = 0;
+  for (int64_t e = 0; e < ne; ++e)
+    if (need[e]) list[nl++] = e;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < nl; ++i) compute_geo(m, list[i], &W.geo[list[i]]);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < nl; ++i) {
+    int64_t e = list[i];
+    if (!m->flag[e]) continue;
+    int n = m->N[e] + 1;
+    W.G[e] = (double*)malloc(sizeof(double) * 9 * n * n * n);
+    element_gradient(&W, e, W.G[e]);
+  }
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(| : rc)
+  for (int64_t e = 0; e < ne; ++e)
+    if (want[e]) rc |= element_residual(&W, e, R) ? 1 : 0;
+  free(list);
+  free_work(&W);
+  free(need);
+  free(want);
+  if (rc) {
+    set_err("Riemann solver failed");
+    return -1;
+  }
+  return 0;
+}
+
+int or_rk_step(const or_mesh* m, double* q, double* g, double dt, int nsteps) {
+  int64_t T4 = 4 * m->total;
+  double* R = (double*)malloc(sizeof(double) * T4);
+  for (int st = 0; st < nsteps; ++st)
+    for (int s = 0; s < 3; ++s) {
+      if (or_residual(m, q, R, 0, NULL)) {
+        free(R);
+        return -1;
+      }
+      for (int64_t i = 0; i < T4; ++i) {
+        g[i] = (s == 0 ? 0.0 : RK_A[s] * g[i]) + dt * R[i];
+        q[i] = q[i] + RK_B[s] * g[i];
+      }
+    }
+  free(R);
+  return 0;
+}
+
+int or_conservation(const or_mesh* m, const double* R, double out[4]) {
+  int64_t ne = m->ne;
+  double* part = (double*)calloc(4 * ne, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t e = 0; e < ne; ++e) {
+    geo_t gt;
+    compute_geo(m, e, &gt);
+    int N = m->N[e], n = N + 1;
+    const double* w = m->op[N].w;
+    for (int v = 0; v < 4; ++v) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            int64_t p = i + n * (j + n * k);
+            s += w[i] * w[j] * w[k] * gt.J[p] * R[v * m->total + m->off[e] + p];
+          }
+      part[v * ne + e] = s;
+    }
+    free(gt.J);
+    free(gt.Ja);
+  }
+  for (int v = 0; v < 4; ++v) {
+    double s = 0.0;
+    for (int64_t e = 0; e < ne; ++e) s += part[v * ne + e];
+    out[v] = s;
+  }
+  free(part);
+  return 0;
+}

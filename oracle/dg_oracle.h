@@ -1,0 +1,87 @@
+/*
+ * dg_oracle.h -- plain FP64 CPU oracle for the flagged Euler / NS-LES DGSEM residual.
+ *
+ * TEST INFRASTRUCTURE ONLY. This library exists so that tests, the smoke check and the
+ * CPU-baseline leg of the benchmark can compare the CUDA path against an independent,
+ * slow, obviously correct evaluation of the method. Nothing in the product links it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * Method (Otmani et al., arXiv 2403.05463):
+ *   - Sec. 2.3: each hexahedral element is flagged inviscid (Euler: convective terms only)
+ *     or viscous/turbulent (full Navier-Stokes + LES eddy viscosity); elements couple only
+ *     through interface numerical fluxes (Roe for convection, BR1 for viscous terms).
+ *   - App. A: governing equations u_t + div F_e = div F_v,turb with the stress tensor
+ *     tau = (mu+mu_t)(grad v + grad v^T) - 2/3 (mu+mu_t) I div v and the Vreman model.
+ *     Read here in artificial-compressibility form with rho = 1, state q = (p, u, v, w).
+ *   - App. B, Eqs. NS2-NS5: DGSEM on curvilinear hexahedra, weak form with the
+ *     convective numerical flux on element faces, tensor-product Gauss quadrature
+ *     (Gauss-Lobatto nodes here).
+ *   - Sec. 2.3 (last paragraph): low-storage explicit third-order Runge-Kutta.
+ *
+ * Layout: q and R are SoA [4][total_nodes]; element e occupies nodes
+ * [offset[e], offset[e] + (N_e+1)^3) with xi_1 fastest, then xi_2, then xi_3.
+ */
+#ifndef DG_ORACLE_H
+#define DG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double nu;        /* kinematic viscosity 1/Re                                  */
+  double c0sq;      /* artificial-compressibility wave speed squared             */
+  double cs;        /* Smagorinsky constant                                      */
+  double cv;        /* Vreman constant (paper: 0.07)                             */
+  int closure;      /* 0 Smagorinsky, 1 Vreman                                   */
+  int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                             */
+  double inflow[4]; /* ghost state used at inflow faces (velocity part)          */
+} or_params;
+
+typedef struct or_mesh or_mesh;
+
+/* 1D building blocks (Gauss-Lobatto-Legendre nodes on [-1,1]). */
+int or_lgl(int N, double* x, double* w);                  /* x[N+1], w[N+1]          */
+int or_dmat(int N, double* D);                            /* D[(N+1)*(N+1)] row-major */
+int or_interp_lgl(int Ns, int Nd, double* I);             /* I[(Nd+1)][(Ns+1)]        */
+int or_project_lgl(int Nh, int Nl, double* P);            /* P[(Nl+1)][(Nh+1)]        */
+
+/* Pointwise building blocks. n_hat must be a unit vector. */
+void or_normal_flux(const double q[4], const double n_hat[3], double c0sq, double out[4]);
+void or_flux_jacobian(const double q[4], const double n_hat[3], double c0sq, double A[16]);
+int or_abs_jacobian(const double q[4], const double n_hat[3], double c0sq, double absA[16]);
+int or_riemann(const double qm[4], const double qp[4], const double n_hat[3],
+               const or_params* prm, double out[4]);
+double or_eddy_viscosity(const double G[9], double delta, const or_params* prm);
+double or_rk3_linear(double z);   /* amplification of one RK3 step on y' = lambda y, z = lambda dt */
+
+/* Mesh + discretisation. Returns NULL on error (see or_error()). */
+or_mesh* or_create(int64_t n_elem, const int64_t* hex, int geom_degree, const double* geom_xyz,
+                   const int8_t* bc_tag, const int8_t* order, const uint8_t* flag,
+                   const or_params* prm);
+void or_destroy(or_mesh* m);
+const char* or_error(void);
+int64_t or_total_nodes(const or_mesh* m);
+const int64_t* or_offsets(const or_mesh* m);
+int or_node_coords(const or_mesh* m, double* xyz);   /* [3][total_nodes] */
+/* Per-element multiplier on (nu + nu_t) in NS elements (test hook; default 1). */
+int or_set_visc_scale(or_mesh* m, const double* scale);
+/* Element geometry: J[n^3], Ja[3][3][n^3] (Ja[i][c] = J dxi_i/dx_c). */
+int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja);
+/* BR1 velocity gradient of one NS element: G[3][3][n^3], G[c][k] = d u_c / d x_k. */
+int or_element_gradient(const or_mesh* m, const double* q, int64_t e, double* G);
+/* Residual R = dq/dt. sel == NULL: every element; otherwise only the listed ones are
+ * written (the other entries of R are left untouched). */
+int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, const int64_t* sel);
+/* nsteps low-storage RK3 steps in place on q, g. */
+int or_rk_step(const or_mesh* m, double* q, double* g, double dt, int nsteps);
+/* out[v] = sum_e sum_nodes w_i w_j w_k J R_v. */
+int or_conservation(const or_mesh* m, const double* R, double out[4]);
+/* Number of OpenMP threads the oracle uses. */
+int or_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,264 @@
+"""ctypes binding of the FP64 CPU oracle (``dg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module. It never imports the product package and the
+product never imports it.
+
+The oracle evaluates the residual of the flagged Euler / NS-LES DGSEM of arXiv 2403.05463
+(Sec. 2.3, App. A, App. B) in plain FP64, weak form, element by element.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "dg_oracle.c")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, -O2). Returns the library path."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    stale = (not os.path.exists(LIB_PATH)) or os.path.getmtime(LIB_PATH) < max(
+        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "dg_oracle.h")))
+    if force or stale:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
+               "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
+                ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
+                ("inflow", ctypes.c_double * 4)]
+
+
+_P = ctypes.POINTER
+_d = _P(ctypes.c_double)
+_i64 = _P(ctypes.c_int64)
+_i8 = _P(ctypes.c_int8)
+_u8 = _P(ctypes.c_uint8)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.or_lgl.argtypes = [ctypes.c_int, _d, _d]
+            L.or_dmat.argtypes = [ctypes.c_int, _d]
+            L.or_interp_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
+            L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
+            L.or_normal_flux.argtypes = [_d, _d, ctypes.c_double, _d]
+            L.or_normal_flux.restype = None
+            L.or_flux_jacobian.argtypes = [_d, _d, ctypes.c_double, _d]
+            L.or_flux_jacobian.restype = None
+            L.or_abs_jacobian.argtypes = [_d, _d, ctypes.c_double, _d]
+            L.or_riemann.argtypes = [_d, _d, _d, _P(Params), _d]
+            L.or_eddy_viscosity.argtypes = [_d, ctypes.c_double, _P(Params)]
+            L.or_eddy_viscosity.restype = ctypes.c_double
+            L.or_rk3_linear.argtypes = [ctypes.c_double]
+            L.or_rk3_linear.restype = ctypes.c_double
+            L.or_create.argtypes = [ctypes.c_int64, _i64, ctypes.c_int, _d, _i8, _i8, _u8, _P(Params)]
+            L.or_create.restype = ctypes.c_void_p
+            L.or_destroy.argtypes = [ctypes.c_void_p]
+            L.or_destroy.restype = None
+            L.or_error.restype = ctypes.c_char_p
+            L.or_total_nodes.argtypes = [ctypes.c_void_p]
+            L.or_total_nodes.restype = ctypes.c_int64
+            L.or_offsets.argtypes = [ctypes.c_void_p]
+            L.or_offsets.restype = _i64
+            L.or_node_coords.argtypes = [ctypes.c_void_p, _d]
+            L.or_set_visc_scale.argtypes = [ctypes.c_void_p, _d]
+            L.or_element_geometry.argtypes = [ctypes.c_void_p, ctypes.c_int64, _d, _d]
+            L.or_element_gradient.argtypes = [ctypes.c_void_p, _d, ctypes.c_int64, _d]
+            L.or_residual.argtypes = [ctypes.c_void_p, _d, _d, ctypes.c_int64, _i64]
+            L.or_rk_step.argtypes = [ctypes.c_void_p, _d, _d, ctypes.c_double, ctypes.c_int]
+            L.or_conservation.argtypes = [ctypes.c_void_p, _d, _d]
+            L.or_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0)):
+    p = Params()
+    p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
+    p.closure, p.riemann = closure, riemann
+    for i in range(4):
+        p.inflow[i] = inflow[i]
+    return p
+
+
+# ---- 1D operators --------------------------------------------------------------------
+
+def lgl(N):
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if lib().or_lgl(N, _ptr(x, _d), _ptr(w, _d)):
+        raise ValueError(lib().or_error().decode())
+    return x, w
+
+
+def dmat(N):
+    D = np.zeros((N + 1, N + 1))
+    if lib().or_dmat(N, _ptr(D, _d)):
+        raise ValueError(lib().or_error().decode())
+    return D
+
+
+def interp(Ns, Nd):
+    I = np.zeros((Nd + 1, Ns + 1))
+    if lib().or_interp_lgl(Ns, Nd, _ptr(I, _d)):
+        raise ValueError(lib().or_error().decode())
+    return I
+
+
+def project(Nh, Nl):
+    P = np.zeros((Nl + 1, Nh + 1))
+    if lib().or_project_lgl(Nh, Nl, _ptr(P, _d)):
+        raise ValueError(lib().or_error().decode())
+    return P
+
+
+# ---- pointwise -----------------------------------------------------------------------
+
+def normal_flux(q, n, c0sq):
+    out = np.zeros(4)
+    lib().or_normal_flux(_ptr(_f64(q), _d), _ptr(_f64(n), _d), c0sq, _ptr(out, _d))
+    return out
+
+
+def flux_jacobian(q, n, c0sq):
+    A = np.zeros((4, 4))
+    lib().or_flux_jacobian(_ptr(_f64(q), _d), _ptr(_f64(n), _d), c0sq, _ptr(A, _d))
+    return A
+
+
+def abs_jacobian(q, n, c0sq):
+    A = np.zeros((4, 4))
+    if lib().or_abs_jacobian(_ptr(_f64(q), _d), _ptr(_f64(n), _d), c0sq, _ptr(A, _d)):
+        raise ValueError(lib().or_error().decode())
+    return A
+
+
+def riemann(qm, qp, n, prm):
+    out = np.zeros(4)
+    if lib().or_riemann(_ptr(_f64(qm), _d), _ptr(_f64(qp), _d), _ptr(_f64(n), _d), ctypes.byref(prm),
+                        _ptr(out, _d)):
+        raise ValueError(lib().or_error().decode())
+    return out
+
+
+def eddy_viscosity(G, delta, prm):
+    return lib().or_eddy_viscosity(_ptr(_f64(np.asarray(G).reshape(9)), _d), delta, ctypes.byref(prm))
+
+
+def rk3_linear(z):
+    return lib().or_rk3_linear(z)
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+# ---- mesh ----------------------------------------------------------------------------
+
+class Mesh:
+    """FP64 oracle discretisation of one mesh (orders, flags and parameters fixed)."""
+
+    def __init__(self, hex, geom_xyz, geom_degree, orders, flags, prm, bc_tag=None):
+        L = lib()
+        self.hex = np.ascontiguousarray(hex, dtype=np.int64)
+        self.ne = self.hex.shape[0]
+        gx = _f64(geom_xyz)
+        orders = np.ascontiguousarray(orders, dtype=np.int8)
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        bc = None if bc_tag is None else np.ascontiguousarray(bc_tag, dtype=np.int8)
+        self.prm = prm
+        self.orders = orders.copy()
+        self.flags = flags.copy()
+        h = L.or_create(self.ne, _ptr(self.hex, _i64), geom_degree, _ptr(gx, _d),
+                        None if bc is None else _ptr(bc, _i8), _ptr(orders, _i8), _ptr(flags, _u8),
+                        ctypes.byref(prm))
+        if not h:
+            raise ValueError(L.or_error().decode())
+        self.h = h
+        self.total = L.or_total_nodes(h)
+        offp = L.or_offsets(h)
+        self.offsets = np.ctypeslib.as_array(offp, shape=(self.ne + 1,)).copy()
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().or_destroy(h)
+            self.h = None
+
+    def node_coords(self):
+        xyz = np.zeros((3, self.total))
+        lib().or_node_coords(self.h, _ptr(xyz, _d))
+        return xyz
+
+    def set_visc_scale(self, scale):
+        s = None if scale is None else _f64(scale)
+        lib().or_set_visc_scale(self.h, None if s is None else _ptr(s, _d))
+
+    def element_geometry(self, e):
+        n = int(self.orders[e]) + 1
+        J = np.zeros(n ** 3)
+        Ja = np.zeros((3, 3, n ** 3))
+        lib().or_element_geometry(self.h, e, _ptr(J, _d), _ptr(Ja, _d))
+        return J, Ja
+
+    def element_gradient(self, q, e):
+        n = int(self.orders[e]) + 1
+        G = np.zeros((3, 3, n ** 3))
+        q = _f64(q)
+        lib().or_element_gradient(self.h, _ptr(q, _d), e, _ptr(G, _d))
+        return G
+
+    def residual(self, q, sel=None, out=None):
+        q = _f64(q)
+        assert q.shape == (4, self.total)
+        R = np.zeros((4, self.total)) if out is None else out
+        if sel is None:
+            rc = lib().or_residual(self.h, _ptr(q, _d), _ptr(R, _d), 0, None)
+        else:
+            s = np.ascontiguousarray(sel, dtype=np.int64)
+            rc = lib().or_residual(self.h, _ptr(q, _d), _ptr(R, _d), s.size, _ptr(s, _i64))
+        if rc:
+            raise RuntimeError(lib().or_error().decode())
+        return R
+
+    def rk_step(self, q, g, dt, nsteps=1):
+        assert q.dtype == np.float64 and g.dtype == np.float64 and q.flags.c_contiguous and g.flags.c_contiguous
+        if lib().or_rk_step(self.h, _ptr(q, _d), _ptr(g, _d), dt, nsteps):
+            raise RuntimeError(lib().or_error().decode())
+
+    def conservation(self, R):
+        out = np.zeros(4)
+        R = _f64(R)
+        lib().or_conservation(self.h, _ptr(R, _d), _ptr(out, _d))
+        return out
+
+    def element_nodes(self, e):
+        return slice(int(self.offsets[e]), int(self.offsets[e + 1]))

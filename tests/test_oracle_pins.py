@@ -1,0 +1,449 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (no GPU needed).
+
+Each test checks the oracle against something other than itself: closed forms, library
+routines (numpy eigen-decomposition, Legendre series), a symbolic evaluation of the PDE,
+or an invariant of the discretisation (free stream, conservation, Euler == NS with nu = 0,
+invariance under local re-numbering).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2403_05463_gb300 import workloads as wl
+
+
+# ---- 1D operators (App. B quadrature, Gauss-Lobatto) ---------------------------------
+
+CLOSED_FORM_LGL = {
+    1: ([-1.0, 1.0], [1.0, 1.0]),
+    2: ([-1.0, 0.0, 1.0], [1 / 3, 4 / 3, 1 / 3]),
+    3: ([-1.0, -1 / math.sqrt(5), 1 / math.sqrt(5), 1.0], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+    4: ([-1.0, -math.sqrt(3 / 7), 0.0, math.sqrt(3 / 7), 1.0], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+}
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_lgl_closed_forms(N):
+    x, w = orc.lgl(N)
+    xr, wr = CLOSED_FORM_LGL[N]
+    np.testing.assert_allclose(x, xr, atol=1e-15)
+    np.testing.assert_allclose(w, wr, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", range(1, 16))
+def test_lgl_quadrature_degree(N):
+    x, w = orc.lgl(N)
+    assert abs(w.sum() - 2.0) < 1e-13
+    for k in range(2 * N):  # exact up to degree 2N-1
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs((w * x ** k).sum() - exact) < 1e-13, (N, k)
+    k = 2 * N  # and not beyond (pins Lobatto rather than Gauss points)
+    assert abs((w * x ** k).sum() - 2.0 / (k + 1)) > 1e-10
+
+
+@pytest.mark.parametrize("N", range(1, 13))
+def test_dmat_exact_on_polynomials(N):
+    x, _ = orc.lgl(N)
+    D = orc.dmat(N)
+    assert np.abs(D.sum(axis=1)).max() < 1e-12
+    for k in range(1, N + 1):
+        np.testing.assert_allclose(D @ x ** k, k * x ** (k - 1), atol=1e-11 * k * N)
+
+
+@pytest.mark.parametrize("Ns,Nd", [(2, 5), (3, 3), (4, 7), (6, 2), (1, 4)])
+def test_interpolation_exact(Ns, Nd):
+    xs, _ = orc.lgl(Ns)
+    xd, _ = orc.lgl(Nd)
+    I = orc.interp(Ns, Nd)
+    rng = np.random.default_rng(0)
+    c = rng.normal(size=Ns + 1)
+    np.testing.assert_allclose(I @ np.polyval(c, xs), np.polyval(c, xd), atol=1e-12)
+
+
+@pytest.mark.parametrize("Nh,Nl", [(3, 2), (5, 3), (7, 6), (7, 2), (4, 4)])
+def test_projection_is_l2_projection(Nh, Nl):
+    from numpy.polynomial import legendre as leg
+    xh, _ = orc.lgl(Nh)
+    xl, _ = orc.lgl(Nl)
+    P = orc.project(Nh, Nl)
+    # identity on interpolated low-order polynomials
+    np.testing.assert_allclose(P @ orc.interp(Nl, Nh), np.eye(Nl + 1), atol=1e-12)
+    # equals truncation of the Legendre series (numpy's Legendre fit)
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=Nh + 1)
+    coef = leg.legfit(xh, f, Nh)
+    ref = leg.legval(xl, coef[:Nl + 1])
+    np.testing.assert_allclose(P @ f, ref, atol=1e-12)
+
+
+# ---- pointwise physics (App. A, Sec. 2.3 Roe flux) -----------------------------------
+
+def _rand_state(rng):
+    return np.array([rng.normal(), 1.0 + rng.normal() * 0.5, rng.normal() * 0.5, rng.normal() * 0.5])
+
+
+def _rand_normal(rng):
+    n = rng.normal(size=3)
+    return n / np.linalg.norm(n)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_roe_consistency_and_roe_property(seed):
+    rng = np.random.default_rng(seed)
+    prm = orc.params(c0sq=25.0)
+    qm, qp, n = _rand_state(rng), _rand_state(rng), _rand_normal(rng)
+    # consistency F*(q, q) = F_n(q)
+    np.testing.assert_allclose(orc.riemann(qm, qm, n, prm), orc.normal_flux(qm, n, 25.0), atol=1e-13)
+    # F_n(q) by hand: (c0^2 u.n, u u.n + p n)
+    un = qm[1:] @ n
+    np.testing.assert_allclose(orc.normal_flux(qm, n, 25.0), np.r_[25.0 * un, qm[1:] * un + qm[0] * n], atol=1e-14)
+    # Roe property: A(mean) (q+ - q-) = F(q+) - F(q-) for the quadratic flux
+    A = orc.flux_jacobian(0.5 * (qm + qp), n, 25.0)
+    np.testing.assert_allclose(A @ (qp - qm), orc.normal_flux(qp, n, 25.0) - orc.normal_flux(qm, n, 25.0),
+                               atol=1e-12)
+    # Jacobian against central finite differences of the flux
+    Afd = np.zeros((4, 4))
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = 1e-6
+        Afd[:, k] = (orc.normal_flux(qm + e, n, 25.0) - orc.normal_flux(qm - e, n, 25.0)) / 2e-6
+    np.testing.assert_allclose(orc.flux_jacobian(qm, n, 25.0), Afd, atol=1e-8)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_abs_jacobian_matches_numpy_eig(seed):
+    rng = np.random.default_rng(10 + seed)
+    q, n = _rand_state(rng), _rand_normal(rng)
+    A = orc.flux_jacobian(q, n, 25.0)
+    lam, V = np.linalg.eig(A)
+    ref = (V @ np.diag(np.abs(lam)) @ np.linalg.inv(V)).real
+    absA = orc.abs_jacobian(q, n, 25.0)
+    np.testing.assert_allclose(absA, ref, atol=1e-11)
+    np.testing.assert_allclose(absA @ absA, A @ A, atol=1e-10)
+    # eigenvalues u_n (twice), u_n +- sqrt(u_n^2 + c0^2)
+    un = q[1:] @ n
+    ev = np.sort(lam.real)
+    np.testing.assert_allclose(ev, np.sort([un, un, un + math.sqrt(un * un + 25), un - math.sqrt(un * un + 25)]),
+                               atol=1e-12)
+
+
+def test_roe_upwinding_along_positive_wave():
+    rng = np.random.default_rng(3)
+    qb, n = _rand_state(rng), _rand_normal(rng)
+    A = orc.flux_jacobian(qb, n, 25.0)
+    lam, V = np.linalg.eig(A)
+    k = int(np.argmax(lam.real))  # fast positive wave
+    dq = 1e-3 * V[:, k].real
+    qm, qp = qb - 0.5 * dq, qb + 0.5 * dq
+    prm = orc.params(c0sq=25.0)
+    # only the left state is seen through a right-running wave
+    np.testing.assert_allclose(orc.riemann(qm, qp, n, prm), orc.normal_flux(qm, n, 25.0), atol=1e-12)
+    k = int(np.argmin(lam.real))
+    dq = 1e-3 * V[:, k].real
+    qm, qp = qb - 0.5 * dq, qb + 0.5 * dq
+    np.testing.assert_allclose(orc.riemann(qm, qp, n, prm), orc.normal_flux(qp, n, 25.0), atol=1e-12)
+
+
+def test_llf_consistency_and_symmetry():
+    rng = np.random.default_rng(4)
+    prm = orc.params(c0sq=25.0, riemann=1)
+    qm, qp, n = _rand_state(rng), _rand_state(rng), _rand_normal(rng)
+    np.testing.assert_allclose(orc.riemann(qm, qm, n, prm), orc.normal_flux(qm, n, 25.0), atol=1e-13)
+    np.testing.assert_allclose(orc.riemann(qm, qp, n, prm), -orc.riemann(qp, qm, -n, prm), atol=1e-13)
+    prm0 = orc.params(c0sq=25.0)
+    np.testing.assert_allclose(orc.riemann(qm, qp, n, prm0), -orc.riemann(qp, qm, -n, prm0), atol=1e-12)
+
+
+def test_eddy_viscosity_closed_forms():
+    delta, g = 0.3, 2.5
+    smag = orc.params(cs=0.1, closure=0)
+    vrem = orc.params(cv=0.07, closure=1)
+    shear = np.zeros((3, 3))
+    shear[0, 1] = g  # u = g y
+    assert abs(orc.eddy_viscosity(shear, delta, smag) - (0.1 * delta) ** 2 * g) < 1e-15
+    assert orc.eddy_viscosity(shear, delta, vrem) == 0.0  # Vreman vanishes in pure shear
+    a = 1.7
+    strain = np.diag([a, -a, 0.0])
+    assert abs(orc.eddy_viscosity(strain, delta, smag) - (0.1 * delta) ** 2 * 2 * a) < 1e-14
+    assert abs(orc.eddy_viscosity(strain, delta, vrem) - 0.07 * delta ** 2 * a / math.sqrt(2)) < 1e-14
+    assert orc.eddy_viscosity(np.zeros((3, 3)), delta, vrem) == 0.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_eddy_viscosity_random_against_invariants(seed):
+    rng = np.random.default_rng(seed)
+    G = rng.normal(size=(3, 3))
+    delta = 0.2
+    S = 0.5 * (G + G.T)
+    ref_s = (0.1 * delta) ** 2 * math.sqrt(2 * (S * S).sum())
+    assert abs(orc.eddy_viscosity(G, delta, orc.params(cs=0.1)) - ref_s) < 1e-14
+    alpha = G.T  # alpha_ij = d u_j / d x_i
+    beta = delta ** 2 * alpha.T @ alpha
+    Bb = 0.5 * (np.trace(beta) ** 2 - np.trace(beta @ beta))  # second invariant of beta
+    ref_v = 0.07 * math.sqrt(Bb / (alpha * alpha).sum())
+    assert abs(orc.eddy_viscosity(G, delta, orc.params(cv=0.07, closure=1)) - ref_v) < 1e-14
+
+
+@pytest.mark.parametrize("z", [-0.1, -1.0, -2.3, 0.5, 1.0])
+def test_rk3_amplification(z):
+    assert abs(orc.rk3_linear(z) - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
+
+
+# ---- mesh-level invariants -------------------------------------------------------------
+
+def _mesh(w, **kw):
+    m = w.mesh
+    return orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**w.params), m.bc_tag)
+
+
+def _small_padapt(n=3, seed=0, orders=(2, 5), rotate=True):
+    w = wl.padapt_32x32x32(n=n, amp=0.05)
+    rng = np.random.default_rng(seed)
+    E = n ** 3
+    orders = rng.integers(orders[0], orders[1] + 1, size=E).astype(np.int8)
+    flags = rng.integers(0, 2, size=E).astype(np.uint8)
+    mesh = w.mesh
+    if rotate:
+        mesh, _ = wl.rotate_elements(mesh, seed + 100)
+    import dataclasses
+    return dataclasses.replace(w, mesh=mesh, orders=orders, flags=flags)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_free_stream_curved_mixed_orders(seed):
+    w = _small_padapt(seed=seed)
+    M = _mesh(w)
+    q = np.zeros((4, M.total))
+    q[0], q[1], q[2], q[3] = 0.3, 1.0, -0.5, 0.25
+    R = M.residual(q)
+    assert np.abs(R).max() < 1e-11, np.abs(R).max()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_conservation_periodic_mixed(seed):
+    w = _small_padapt(seed=seed)
+    M = _mesh(w)
+    xyz = M.node_coords()
+    q = w.state(xyz)
+    q[0] += 0.1 * np.sin(2 * np.pi * xyz[0])
+    R = M.residual(q)
+    c = M.conservation(R)
+    _, scale = _weighted_abs(M, R)
+    assert np.abs(c).max() < 1e-12 * scale, (c, scale)
+
+
+def _weighted_abs(M, R):
+    tot = np.zeros(4)
+    for e in range(M.ne):
+        J, _ = M.element_geometry(e)
+        N = int(M.orders[e])
+        _, wq = orc.lgl(N)
+        w3 = np.einsum("k,j,i->kji", wq, wq, wq).ravel()
+        tot += np.abs(R[:, M.element_nodes(e)]) @ (w3 * J)
+    return tot, tot.max()
+
+
+def test_conservation_tgv_uniform():
+    w = wl.tgv_4x4x4_n3()
+    M = _mesh(w)
+    q = w.state(M.node_coords())
+    R = M.residual(q)
+    _, scale = _weighted_abs(M, R)
+    assert np.abs(M.conservation(R)).max() < 1e-13 * scale
+
+
+def test_euler_equals_ns_without_viscosity():
+    w = _small_padapt(seed=3)
+    xyz = None
+    p = dict(w.params, nu=0.0, cs=0.0)
+    m = w.mesh
+    E = w.n_elem
+    A = orc.Mesh(m.hex, m.geom, 2, w.orders, np.ones(E, np.uint8), orc.params(**p))
+    B = orc.Mesh(m.hex, m.geom, 2, w.orders, np.zeros(E, np.uint8), orc.params(**p))
+    xyz = A.node_coords()
+    q = w.state(xyz)
+    Ra, Rb = A.residual(q), B.residual(q)
+    assert np.abs(Ra - Rb).max() <= 1e-13 * np.abs(Rb).max()
+
+
+def test_mixed_equals_all_ns_with_zero_viscosity_in_euler_elements():
+    # Sec. 2.3 reading: the Euler/NS face carries the average of the NS viscous flux and 0.
+    w = _small_padapt(seed=4)
+    m = w.mesh
+    prm = orc.params(**dict(w.params, nu=1e-2))
+    mixed = orc.Mesh(m.hex, m.geom, 2, w.orders, w.flags, prm)
+    alls = orc.Mesh(m.hex, m.geom, 2, w.orders, np.ones(w.n_elem, np.uint8), prm)
+    alls.set_visc_scale(w.flags.astype(np.float64))
+    q = w.state(mixed.node_coords())
+    Rm, Ra = mixed.residual(q), alls.residual(q)
+    assert np.abs(Rm - Ra).max() <= 1e-13 * np.abs(Ra).max()
+    # and the viscous terms do matter: plain all-NS differs
+    alls.set_visc_scale(None)
+    assert np.abs(alls.residual(q) - Rm).max() > 1e-6
+
+
+def test_orientation_invariance():
+    w = _small_padapt(seed=5, rotate=False)
+    rmesh, rot_of = wl.rotate_elements(w.mesh, 77)
+    prm = orc.params(**dict(w.params, nu=1e-2))
+    A = orc.Mesh(w.mesh.hex, w.mesh.geom, 2, w.orders, w.flags, prm)
+    B = orc.Mesh(rmesh.hex, rmesh.geom, 2, w.orders, w.flags, prm)
+    xa, xb = A.node_coords(), B.node_coords()
+    qa = w.state(xa)
+    # same physical field on the re-numbered mesh: permute node values element by element
+    perm = np.zeros(A.total, dtype=np.int64)
+    for e in range(A.ne):
+        n = int(w.orders[e]) + 1
+        idx = wl.rotation_index_map(wl.CUBE_ROTATIONS[rot_of[e]], n)
+        perm[B.offsets[e]:B.offsets[e + 1]] = A.offsets[e] + idx
+    np.testing.assert_allclose(xb, xa[:, perm], atol=1e-13)
+    Ra = A.residual(qa)
+    Rb = B.residual(qa[:, perm])
+    assert np.abs(Rb - Ra[:, perm]).max() <= 1e-12 * np.abs(Ra).max()
+
+
+def test_inflow_outflow_free_stream():
+    w = wl.wake_16x16x16_n4(n=3, order=3)
+    M = _mesh(w)
+    q = np.zeros((4, M.total))
+    q[1] = 1.0
+    R = M.residual(q)
+    assert np.abs(R).max() < 1e-12
+
+
+def test_affine_gradient_exact_for_quadratics():
+    # BR1 lifting vanishes for continuous fields; D is exact for degree <= N on affine maps
+    rng = np.random.default_rng(8)
+    n = 3
+    b = np.linspace(0, 1, n + 1)
+    A = np.array([[1.0, 0.3, 0.0], [0.1, 0.9, 0.2], [0.0, -0.2, 1.1]])
+    mesh = wl.box_mesh(n, n, n, b, b, b, warp=lambda x, y, z: tuple(A @ np.stack([x, y, z])))
+    E = n ** 3
+    M = orc.Mesh(mesh.hex, mesh.geom, 1, np.full(E, 3, np.int8), np.ones(E, np.uint8), orc.params())
+    xyz = M.node_coords()
+    C = rng.normal(size=(3, 3))
+    H = rng.normal(size=(3, 3))
+    q = np.zeros((4, M.total))
+    # u_c = C_c . x + x . H x  (quadratic, non-periodic -> only interior elements are exact)
+    for c in range(3):
+        q[1 + c] = C[c] @ xyz + 0.1 * (xyz[c] ** 2)
+    e = 13  # the central element of the 3^3 mesh
+    G = M.element_gradient(q, e)
+    x = xyz[:, M.element_nodes(e)]
+    for c in range(3):
+        for k in range(3):
+            ref = C[c, k] + (0.2 * x[c] if c == k else 0.0)
+            np.testing.assert_allclose(G[c, k], ref, atol=1e-11)
+
+
+def _tgv_exact_residual(xyz, nu, c0sq):
+    """R = -div(u u + p I) + div(tau), R_p = -c0^2 div u for the Taylor-Green field,
+    evaluated symbolically (sympy) from the PDE of App. A (rho = 1)."""
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    u = [sp.sin(x) * sp.cos(y) * sp.cos(z), -sp.cos(x) * sp.sin(y) * sp.cos(z), sp.Integer(0)]
+    p = (sp.cos(2 * x) + sp.cos(2 * y)) * (sp.cos(2 * z) + 2) / 16
+    X = [x, y, z]
+    G = [[sp.diff(u[c], X[k]) for k in range(3)] for c in range(3)]
+    div = G[0][0] + G[1][1] + G[2][2]
+    tau = [[nu * (G[c][k] + G[k][c]) - (sp.Rational(2, 3) * nu * div if c == k else 0) for k in range(3)]
+           for c in range(3)]
+    R = [-c0sq * div]
+    for c in range(3):
+        R.append(sum(-sp.diff(u[c] * u[k] + (p if c == k else 0), X[k]) + sp.diff(tau[c][k], X[k])
+                     for k in range(3)))
+    f = sp.lambdify((x, y, z), R, "numpy")
+    out = f(xyz[0], xyz[1], xyz[2])
+    return np.array([np.broadcast_to(np.asarray(o, dtype=float), xyz[0].shape) for o in out])
+
+
+def test_spectral_convergence_tgv():
+    pytest.importorskip("sympy")
+    errs = []
+    for N in range(2, 8):
+        w = wl.tgv_4x4x4_n3(order=N)
+        prm = orc.params(**dict(w.params, nu=0.01, cs=0.0))
+        M = orc.Mesh(w.mesh.hex, w.mesh.geom, 1, w.orders, w.flags, prm)
+        xyz = M.node_coords()
+        q = w.state(xyz)
+        R = M.residual(q)
+        Rex = _tgv_exact_residual(xyz, 0.01, 25.0)
+        errs.append(np.sqrt(((R - Rex) ** 2).sum() / (Rex ** 2).sum()))
+    errs = np.array(errs)
+    assert np.all(np.diff(np.log(errs)) < -0.5), errs  # decays geometrically with N
+    assert errs[-1] < 5e-4, errs
+
+
+@pytest.mark.slow
+def test_rk3_temporal_order():
+    w = wl.tgv_4x4x4_n3(order=3)
+    M = _mesh(w)
+    q0 = w.state(M.node_coords())
+    T = 0.2
+
+    def run(nsteps):
+        q = q0.copy()
+        g = np.zeros_like(q)
+        M.rk_step(q, g, T / nsteps, nsteps)
+        return q
+
+    ref = run(160)
+    e = [np.abs(run(k) - ref).max() for k in (10, 20, 40)]
+    slopes = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(slopes > 2.7), (e, slopes)
+
+
+def _tgv_eddy_divergence(xyz, delta, closure, C):
+    """div(tau_t) for the Taylor-Green field with the eddy viscosity of App. A (Vreman) or
+    Smagorinsky, evaluated symbolically; tau_t = nu_t (G + G^T) (div u = 0)."""
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    u = [sp.sin(x) * sp.cos(y) * sp.cos(z), -sp.cos(x) * sp.sin(y) * sp.cos(z), sp.Integer(0)]
+    X = [x, y, z]
+    G = sp.Matrix(3, 3, lambda c, k: sp.diff(u[c], X[k]))
+    if closure == 0:
+        S = (G + G.T) / 2
+        nut = (C * delta) ** 2 * sp.sqrt(2 * sum(S[i, j] ** 2 for i in range(3) for j in range(3)))
+    else:
+        al = G.T
+        be = delta ** 2 * al.T * al
+        B = (be[0, 0] * be[1, 1] - be[0, 1] ** 2 + be[0, 0] * be[2, 2] - be[0, 2] ** 2
+             + be[1, 1] * be[2, 2] - be[1, 2] ** 2)
+        nut = C * sp.sqrt(B / sum(al[i, j] ** 2 for i in range(3) for j in range(3)))
+    R = [sp.Integer(0)] + [sum(sp.diff(nut * (G[c, k] + G[k, c]), X[k]) for k in range(3)) for c in range(3)]
+    f = sp.lambdify((x, y, z), R, "numpy")
+    out = f(xyz[0], xyz[1], xyz[2])
+    return np.array([np.broadcast_to(np.asarray(o, dtype=float), xyz[0].shape) for o in out])
+
+
+def _les_error(closure, ne, N):
+    w = wl.tgv_4x4x4_n3(n_elem_dir=ne, order=N)
+    base = dict(w.params, nu=0.0, cs=0.0, cv=0.0, closure=closure)
+    les = dict(base, cs=0.5, cv=0.5)
+    M0 = orc.Mesh(w.mesh.hex, w.mesh.geom, 1, w.orders, w.flags, orc.params(**base))
+    M1 = orc.Mesh(w.mesh.hex, w.mesh.geom, 1, w.orders, w.flags, orc.params(**les))
+    xyz = M0.node_coords()
+    q = w.state(xyz)
+    dR = M1.residual(q) - M0.residual(q)
+    delta = (2 * np.pi / ne) / (N + 1)  # cube root of the element volume over nodes per direction
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ref = _tgv_eddy_divergence(xyz, delta, closure, 0.5)
+    ok = np.isfinite(ref).all(axis=0)  # the symbolic Vreman form is 0/0 where B_beta = 0
+    assert ok.mean() > 0.9
+    return np.sqrt(((dR - ref)[:, ok] ** 2).sum() / (ref[:, ok] ** 2).sum())
+
+
+def test_smagorinsky_term_matches_symbolic_divergence():
+    pytest.importorskip("sympy")
+    assert _les_error(0, 4, 7) < 0.015
+    assert _les_error(0, 4, 9) < 0.008
+
+
+def test_vreman_term_converges_to_symbolic_divergence():
+    # Vreman's nu_t is not smooth for this field (B_beta vanishes on surfaces), so the
+    # DG divergence converges slowly; pin the trend under h-refinement.
+    pytest.importorskip("sympy")
+    e1, e2 = _les_error(1, 4, 7), _les_error(1, 8, 7)
+    assert e1 < 0.4 and e2 < 0.65 * e1, (e1, e2)
