@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Throughput of the flagged Euler / NS-LES DGSEM Runge-Kutta step on GB300.
+
+One benchmark step = one low-storage RK3 step = three residual evaluations + updates over the
+whole mesh (every phase of the hot path: traces, viscous pass on NS elements, inviscid pass,
+surface terms, FP64 update). The metric is DOF-updates/s per RK stage:
+    value = n_ranks * DOF * 3 / (time per step),  DOF = sum_e (N_e + 1)^3.
+
+Default workload: 64^3 stretched hexahedra, N = 4 (32.8 M DOF), 25% NS + Smagorinsky,
+synthetic turbulence on u = 1 (the large mixed configuration). Its state (q and g: 2.1 GB)
+is larger than L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (plain FP64 C, OpenMP) on the host cores on a bounded
+sample of the same workload, in the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("DOF-updates/s per RK stage (mixed Euler/NS-LES vs all-NS; FP32-TC vs FP64) at stated error")
+UNIT = "DOF-updates/s"
+THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+                 0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed_64x64x64_n4")
+    ap.add_argument("--precision", default=os.environ.get("DG_BENCH_PRECISION", "fp64"), choices=["fp64", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
+    ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
+    return ap.parse_args()
+
+
+# ---- clocks --------------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[3], 16)
+            except ValueError:
+                continue
+            for b, name in THROTTLE_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---- distributed -----------------------------------------------------------------------------
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU oracle baseline ---------------------------------------------------------------------
+
+def oracle_rate(w, q_host, budget_s=12.0, seed=0):
+    """The FP64 oracle as it stands, on the host cores: residual of a random sample of
+    elements (each needs its neighbours' BR1 gradients too), DOF of the sample / wall time."""
+    import numpy as np
+    from oracle import oracle as orc
+    m = w.mesh
+    M = orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**w.params), m.bc_tag)
+    rng = np.random.default_rng(seed)
+    n3 = (w.orders.astype(np.int64) + 1) ** 3
+    R = np.zeros_like(q_host)
+
+    def timed(k):
+        sel = np.sort(rng.choice(w.n_elem, size=min(k, w.n_elem), replace=False))
+        t0 = time.perf_counter()
+        M.residual(q_host, sel=sel, out=R)
+        return float(n3[sel].sum()), time.perf_counter() - t0, sel.size
+
+    dof, dt, _ = timed(256)
+    k = int(min(w.n_elem, max(256, 256 * budget_s / max(dt, 1e-3))))
+    dof, dt, k = timed(k)
+    return {"value": dof / dt, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"one FP64 residual of {k} randomly sampled elements of {w.name} "
+                      f"({int(dof)} DOF, {dt:.1f} s; neighbours' gradients included in the time)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_2403_05463_gb300 import workloads as wl
+    w = wl.WORKLOADS[args.workload]()
+    m = w.mesh
+    M = orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**w.params), m.bc_tag)
+    xyz = M.node_coords()
+    q = w.state(xyz)
+    del xyz
+    n3 = (w.orders.astype(np.int64) + 1) ** 3
+    rng = np.random.default_rng(1)
+    R = np.zeros_like(q)
+    # size one step (one stage on a sample) so that warmup + steps fit in about two minutes
+    sel = rng.choice(w.n_elem, 128, replace=False)
+    t0 = time.perf_counter()
+    M.residual(q, sel=sel, out=R)
+    per_elem = (time.perf_counter() - t0) / sel.size
+    k = int(max(64, min(w.n_elem, 100.0 / max(1, args.steps + args.warmup) / max(per_elem, 1e-6))))
+    times, dofs = [], []
+    for i in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(w.n_elem, k, replace=False))
+        t0 = time.perf_counter()
+        M.residual(q, sel=sel, out=R)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            dofs.append(float(n3[sel].sum()))
+    value = sum(dofs) / sum(times)
+    ms = 1e3 * sum(times) / len(times)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "n_elem": int(w.n_elem), "dof": int(w.total_nodes),
+                      "ns_fraction": w.ns_fraction, "step": f"one residual (one RK stage) of {k} sampled elements"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                            "sample": f"{k} randomly sampled elements per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---- GPU -------------------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2403_05463_gb300 import dg, workloads as wl
+
+    world, rank, local = dist_setup()
+    w = wl.WORKLOADS[args.workload]() if args.n is None else wl.WORKLOADS[args.workload](n=args.n)
+    S = dg.Solver.from_workload(w, precision=args.precision, device=local)
+    dof = S.total_nodes
+    xyz = S.node_coords()
+    q = w.state_fn(xyz, None, None) if args.workload == "mixed_64x64x64_n4" else \
+        torch.from_numpy(w.state(xyz.cpu().numpy())).cuda()
+    q = q.contiguous()
+    del xyz
+    q0 = q.clone()
+    g = torch.zeros_like(q)
+    dt = w.dt
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.rk_step(q, g, dt, 1, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = allmax(world, ms)
+    value = world * dof * 3 / (ms_max * 1e-3)
+    S.check_device()
+    launches = S.launches_per_step * args.steps
+
+    # roofline of the dominant phase (CUDA events between the phases, same stream)
+    q.copy_(q0)
+    ph_ms = S.phase_times(q, g, dt, reps=6, stream=stream)
+    ph_bytes = S.phase_bytes()
+    dom = max(ph_ms, key=lambda k: ph_ms[k])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach = ph_bytes[dom] / (ph_ms[dom] * 1e-3) / 1e9
+    step_bytes = 3 * sum(ph_bytes.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None,
+                "step_frac": step_bytes / (ms_max * 1e-3) / 1e9 / hbm}
+    phases = {k: {"ms": ph_ms[k], "algorithmic_gb": ph_bytes[k] / 1e9,
+                  "gbs": (ph_bytes[k] / (ph_ms[k] * 1e-3) / 1e9) if ph_ms[k] > 0 else None} for k in ph_ms}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": w.name, "n_elem": int(w.n_elem), "order": int(w.orders.max()), "dof": int(dof),
+                      "ns_fraction": w.ns_fraction, "precision": args.precision, "stages_per_step": 3,
+                      "state": "FP64 q, g resident in HBM; FP64 RK accumulation",
+                      "l2": f"inputs larger than L2 (q + g = {2 * q.numel() * 8 / 1e9:.2f} GB per rank)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": roofline, "phases": phases, "gpu_launches": launches, "clocks": clk}
+
+    if not args.no_extras:
+        # mixed vs all-NS and all-Euler on the same mesh and GPU
+        cmp = {}
+        for name, fl in (("all_ns", np.ones(w.n_elem, np.uint8)), ("all_euler", np.zeros(w.n_elem, np.uint8))):
+            S.set_flags(fl)
+            q.copy_(q0)
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            cmp[name] = {"ms_per_step": a.elapsed_time(b) / 5, "value": dof * 3 / (a.elapsed_time(b) / 5 * 1e-3)}
+        S.set_flags(w.flags)
+        f = w.ns_fraction
+        bar = f * cmp["all_ns"]["ms_per_step"] + (1 - f) * cmp["all_euler"]["ms_per_step"]
+        cmp["mixed_ms_per_step"] = ms
+        cmp["bar_ms_per_step"] = bar
+        cmp["speedup_vs_all_ns"] = cmp["all_ns"]["ms_per_step"] / ms
+        cmp["meets_bar"] = ms <= bar
+        out["comparison"] = cmp
+        # end to end through the C ABI with host buffers (pinned), copies inside the timing
+        qh = q0.cpu().pin_memory()
+        gh = torch.zeros_like(qh).pin_memory()
+        S.rk_step_host(qh, gh, dt, 1, stream=stream)
+        n_e2e = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            S.rk_step_host(qh, gh, dt, 1, stream=stream)
+        t_e2e = (time.perf_counter() - t0) / n_e2e
+        t_e2e = allmax(world, t_e2e)
+        nbytes = 2 * qh.numel() * 8
+        out["e2e"] = {"value": world * dof * 3 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3}
+        if rank == 0 and world == 1:
+            try:
+                out["cpu_baseline"] = oracle_rate(w, q0.cpu().numpy())
+            except Exception as exc:  # the baseline is context, never the product path
+                out["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle", "cores": None,
+                                       "sample": f"not measured: {exc}"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) flagged Euler / NS-LES DGSEM residual library.
+ *
+ * The library evaluates the explicit-time-step spatial residual of a nodal
+ * Gauss-Lobatto DGSEM discretisation of incompressible flow in artificial-compressibility
+ * form and advances it with a low-storage third-order Runge-Kutta scheme, after
+ *   Otmani, Mateo-Gabin, Rubio, Ferrer, arXiv 2403.05463:
+ *   - Sec. 2.3 (viscous/turbulent-inviscid interactions): every hexahedral element carries a
+ *     flag; flag 0 solves the Euler equations (convective terms only), flag 1 the full
+ *     Navier-Stokes equations with an LES eddy viscosity. Neighbours couple only through
+ *     interface numerical fluxes: Roe for the convective part, BR1 for the viscous part.
+ *   - App. A: u_t + div F_e = div F_v,turb with tau = (nu + nu_t)(grad v + grad v^T)
+ *     - 2/3 (nu + nu_t) I div v, the Vreman closure (Smagorinsky selectable).
+ *   - App. B, Eqs. NS2-NS5: DGSEM on curvilinear hexahedra (transfinite map, Jacobian J,
+ *     contravariant fluxes), numerical flux on faces, tensor-product quadrature.
+ *   - Sec. 2.3 (last paragraph): low-storage explicit third-order Runge-Kutta.
+ *   - Sec. 1/4: local p-adaptation, one polynomial order per element, p-nonconforming faces.
+ *
+ * State: q = (p, u, v, w), rho = 1. All state arrays are FP64, structure-of-arrays
+ * [4][total_nodes]: variable v of global node i lives at q[v * total_nodes + i]. Element e
+ * owns nodes [elem_offset[e], elem_offset[e] + (N_e + 1)^3), lexicographic with xi_1
+ * fastest, then xi_2, then xi_3 (see dg_get_layout).
+ *
+ * Errors: every entry point returns a dg_status; none aborts. dg_last_error() gives a
+ * thread-local message for the last failing call on that thread. Calls that take a stream
+ * are asynchronous with respect to the host; device-side faults found by a kernel (a
+ * non-positive Jacobian, a bounded wait that timed out) land in a device error word that
+ * dg_check_device() and dg_conservation() read.
+ *
+ * Ownership: descriptors and host arrays passed in are copied; the caller keeps them.
+ * Device arrays (q, g, R, xyz) are caller-owned, FP64, contiguous; the library never frees
+ * them. Library-owned buffers (traces, geometry, tables) are freed by dg_destroy.
+ */
+#ifndef DG_H
+#define DG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,         /* invalid argument (null pointer, out-of-range value)      */
+  DG_ERR_MESH = 2,        /* inconsistent mesh (unmatched face, bad orientation, J<=0) */
+  DG_ERR_CUDA = 3,        /* a CUDA runtime call failed                                */
+  DG_ERR_OOM = 4,         /* device allocation failed                                  */
+  DG_ERR_UNSUPPORTED = 5, /* valid input outside what this build implements            */
+  DG_ERR_STATE = 6,       /* call out of order                                         */
+  DG_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up                        */
+  DG_ERR_DEVICE = 8       /* a kernel reported a fault in the device error word        */
+} dg_status;
+
+/* Mesh description (App. B: curvilinear hexahedra given by a polynomial map). */
+typedef struct {
+  int64_t n_elem;
+  /* [n_elem][8] vertex ids, corner c = c1 + 2 c2 + 4 c3 sits at xi = (2c1-1, 2c2-1, 2c3-1).
+   * Faces match by their four corner ids; periodic faces are those whose corners share ids.
+   * The orientation of a shared face is derived from the corner ids (all 8 are supported). */
+  const int64_t* hex;
+  /* Geometry degree g (1 trilinear, 2 quadratic) and [n_elem][(g+1)^3][3] node coordinates at
+   * the Gauss-Lobatto points of degree g (i.e. {-1,1} or {-1,0,1}), xi_1 fastest. Orders must
+   * satisfy N_e >= g. */
+  int geom_degree;
+  const double* geom_xyz;
+  /* [n_elem][6] boundary tag per local face f = 2 d + s (plane xi_{d+1} = s ? +1 : -1):
+   * -1 interior or periodic, 1 inflow (velocity from dg_params.inflow, interior pressure),
+   * 2 outflow (interior velocity, zero pressure). NULL means every face is interior. */
+  const int8_t* bc_tag;
+} dg_mesh_desc;
+
+/* Physical and numerical parameters (App. A, Sec. 2.3). */
+typedef struct {
+  double nu;        /* kinematic viscosity 1/Re                                        */
+  double c0sq;      /* artificial-compressibility wave speed squared                   */
+  double cs;        /* Smagorinsky constant                                            */
+  double cv;        /* Vreman constant (the paper uses 0.07)                           */
+  int closure;      /* 0 Smagorinsky, 1 Vreman                                         */
+  int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                                   */
+  int precision;    /* 0 FP64 throughout; 1 FP32 element/face arithmetic with FP64 state,
+                       traces and Runge-Kutta accumulation                              */
+  int reserved;     /* must be 0                                                       */
+  double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
+} dg_params;
+
+/* Build the mesh topology (face matching, orientations, periodic pairs), the geometry
+ * (curl-form metric terms at the geometry degree, Kopriva 2006) and upload everything to
+ * `device`. Orders default to 3 (or the geometry degree if larger) and flags to 1 (NS).
+ * Returns DG_ERR_MESH for an unmatched face without a boundary tag, a face shared by more
+ * than two elements, repeated corner ids on one face or a non-positive Jacobian. */
+dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int device, dg_ctx** out);
+
+/* Per-element polynomial order N_e in 1..7 (host array, length n_elem; Sec. 4 local
+ * p-adaptation). Faces between different orders become mortars (interpolation to the
+ * larger order, exact L2 projection back). Re-lays out the state: previous q/g/R arrays
+ * no longer match the layout. */
+dg_status dg_set_orders(dg_ctx* ctx, const int8_t* orders);
+
+/* Per-element flag (host array, length n_elem): 0 Euler, 1 Navier-Stokes + LES (Sec. 2.3).
+ * Does not change the layout. */
+dg_status dg_set_element_flags(dg_ctx* ctx, const uint8_t* flags);
+
+/* Replace the parameters (same validation as dg_create_mesh). */
+dg_status dg_set_params(dg_ctx* ctx, const dg_params* params);
+
+/* total_nodes = sum_e (N_e + 1)^3; *elem_offset points to a library-owned host array of
+ * n_elem + 1 offsets, valid until the next dg_set_orders or dg_destroy. */
+dg_status dg_get_layout(const dg_ctx* ctx, int64_t* total_nodes, const int64_t** elem_offset);
+
+/* Physical coordinates of every node, device array [3][total_nodes]. */
+dg_status dg_node_coords(dg_ctx* ctx, double* xyz_dev, void* stream);
+
+/* R = dq/dt (App. B, Eq. NS4 with the BR1 viscous terms) for device arrays q, R of shape
+ * [4][total_nodes] (they must not overlap). Asynchronous on `stream` (a cudaStream_t,
+ * NULL = default stream). */
+dg_status dg_residual(dg_ctx* ctx, const double* q_dev, double* R_dev, void* stream);
+
+/* nsteps steps of the Williamson 2N-storage RK3 in place on device arrays q and g
+ * ([4][total_nodes] each): per stage s, g <- A_s g + dt R(q), q <- q + B_s g, with
+ * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15) (g need not be initialised: A_1 = 0
+ * overwrites it). One step is captured once as a CUDA graph per (q, g, dt) and replayed.
+ * t is the time at the start (the residual has no explicit time dependence). */
+dg_status dg_rk_step(dg_ctx* ctx, double* q_dev, double* g_dev, double t, double dt, int nsteps,
+                     void* stream);
+
+/* Host-buffer variants: copy the host arrays to library-owned device buffers, compute on
+ * `stream`, copy the result back and synchronise the stream before returning. */
+dg_status dg_residual_host(dg_ctx* ctx, const double* q_host, double* R_host, void* stream);
+dg_status dg_rk_step_host(dg_ctx* ctx, double* q_host, double* g_host, double t, double dt, int nsteps,
+                          void* stream);
+
+/* out_host[v] = sum_e sum_nodes w_i w_j w_k J R_v (FP64, deterministic order). Synchronises
+ * the stream and also reports a pending device error. On a periodic mesh the exact
+ * discretisation conserves every variable, so these sums vanish to rounding. */
+dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double out_host[4], void* stream);
+
+/* Synchronise `stream`, then read and clear the device error word. */
+dg_status dg_check_device(dg_ctx* ctx, void* stream);
+
+/* Phases of one residual evaluation / Runge-Kutta stage, in launch order. */
+#define DG_NPHASES 5 /* 0 traces, 1 mortar lifting, 2 viscous, 3 mortar flux, 4 inviscid+update */
+
+/* Tracing: run `reps` Runge-Kutta stages (stage index cycling 0, 1, 2) in place on q, g with
+ * CUDA events recorded on `stream` between the phases, synchronise, and return the mean
+ * time of each phase in milliseconds (a phase with no work reports 0). Advances q and g
+ * exactly like dg_rk_step. */
+dg_status dg_phase_times(dg_ctx* ctx, double* q_dev, double* g_dev, double dt, int reps,
+                         double out_ms[DG_NPHASES], void* stream);
+
+/* Algorithmic DRAM bytes of each phase of one Runge-Kutta stage on the current mesh, orders
+ * and flags: every value a phase must read or write once (state, traces, viscous buffers,
+ * metric terms), none re-read. The roofline of a phase is these bytes over its time. */
+dg_status dg_phase_bytes(const dg_ctx* ctx, double out_bytes[DG_NPHASES]);
+
+/* Number of kernel launches the last dg_residual / one dg_rk_step step issued. */
+int dg_launches_per_residual(const dg_ctx* ctx);
+int dg_launches_per_step(const dg_ctx* ctx);
+
+/* Thread-local message describing the last failure on this thread. */
+const char* dg_last_error(void);
+
+/* Free every library-owned buffer. NULL is allowed. */
+void dg_destroy(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

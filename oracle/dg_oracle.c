@@ -26,6 +26,20 @@
 #include <omp.h>
 #endif
 
+#if defined(OR_EXTENDED) && OR_EXTENDED
+#define SQRT sqrtl
+#define FABS fabsl
+#define COS cosl
+#define CBRT cbrtl
+#define PI_R 3.141592653589793238462643383279502884L
+#else
+#define SQRT sqrt
+#define FABS fabs
+#define COS cos
+#define CBRT cbrt
+#define PI_R M_PI
+#endif
+
 #define OR_MAXN 15
 #define OR_MAXG 4
 
@@ -53,9 +67,9 @@ int or_num_threads(void) {
 
 /* Legendre polynomials L_{N-1}, L_N, L_{N+1} at x by the three-term recurrence
  * (k+1) L_{k+1} = (2k+1) x L_k - k L_{k-1}, L_0 = 1, L_1 = x. */
-static void legendre3(int N, double x, double* Lm1, double* L0, double* Lp1) {
-  double lkm1 = 0.0, lk = 1.0; /* L_{-1} (unused), L_0 */
-  double lkp1 = x;             /* L_1 */
+static void legendre3(int N, or_real x, or_real* Lm1, or_real* L0, or_real* Lp1) {
+  or_real lkm1 = 0.0, lk = 1.0; /* L_{-1} (unused), L_0 */
+  or_real lkp1 = x;             /* L_1 */
   for (int k = 1; k <= N; ++k) {
     lkm1 = lk;
     lk = lkp1;
@@ -67,7 +81,7 @@ static void legendre3(int N, double x, double* Lm1, double* L0, double* Lp1) {
   *Lp1 = lkp1;
 }
 
-int or_lgl(int N, double* x, double* w) {
+int or_lgl(int N, or_real* x, or_real* w) {
   if (N < 1 || N > OR_MAXN) {
     set_err("order %d outside 1..%d", N, OR_MAXN);
     return -1;
@@ -77,25 +91,25 @@ int or_lgl(int N, double* x, double* w) {
   /* interior nodes: roots of L_{N+1} - L_{N-1} (proportional to (1-x^2) L'_N);
    * Newton from Chebyshev-Gauss-Lobatto guesses, d/dx (L_{N+1}-L_{N-1}) = (2N+1) L_N. */
   for (int j = 1; j < N; ++j) {
-    double xj = -cos(M_PI * j / N);
+    or_real xj = -COS(PI_R * j / N);
     for (int it = 0; it < 200; ++it) {
-      double lm1, l0, lp1;
+      or_real lm1, l0, lp1;
       legendre3(N, xj, &lm1, &l0, &lp1);
-      double dx = (lp1 - lm1) / ((2.0 * N + 1.0) * l0);
+      or_real dx = (lp1 - lm1) / ((2.0 * N + 1.0) * l0);
       xj -= dx;
-      if (fabs(dx) <= 1e-17) break;
+      if (FABS(dx) <= 1e-17) break;
     }
     x[j] = xj;
   }
   /* enforce the exact symmetry of the node set */
   for (int j = 0; j < (N + 1) / 2; ++j) {
-    double s = 0.5 * (x[N - j] - x[j]);
+    or_real s = 0.5 * (x[N - j] - x[j]);
     x[j] = -s;
     x[N - j] = s;
   }
   if (N % 2 == 0) x[N / 2] = 0.0;
   for (int j = 0; j <= N; ++j) {
-    double lm1, l0, lp1;
+    or_real lm1, l0, lp1;
     legendre3(N, x[j], &lm1, &l0, &lp1);
     w[j] = 2.0 / (N * (N + 1.0) * l0 * l0);
   }
@@ -103,26 +117,26 @@ int or_lgl(int N, double* x, double* w) {
 }
 
 /* Lagrange basis l_j(y) on nodes xs[0..n-1] by the product formula. */
-static double lagrange(int n, const double* xs, int j, double y) {
-  double v = 1.0;
+static or_real lagrange(int n, const or_real* xs, int j, or_real y) {
+  or_real v = 1.0;
   for (int k = 0; k < n; ++k)
     if (k != j) v *= (y - xs[k]) / (xs[j] - xs[k]);
   return v;
 }
 
-int or_dmat(int N, double* D) {
-  double x[OR_MAXN + 1], w[OR_MAXN + 1], lam[OR_MAXN + 1];
+int or_dmat(int N, or_real* D) {
+  or_real x[OR_MAXN + 1], w[OR_MAXN + 1], lam[OR_MAXN + 1];
   if (or_lgl(N, x, w)) return -1;
   int n = N + 1;
   /* barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k) */
   for (int j = 0; j < n; ++j) {
-    double p = 1.0;
+    or_real p = 1.0;
     for (int k = 0; k < n; ++k)
       if (k != j) p *= (x[j] - x[k]);
     lam[j] = 1.0 / p;
   }
   for (int i = 0; i < n; ++i) {
-    double s = 0.0;
+    or_real s = 0.0;
     for (int j = 0; j < n; ++j) {
       if (j == i) continue;
       D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
@@ -133,8 +147,8 @@ int or_dmat(int N, double* D) {
   return 0;
 }
 
-int or_interp_lgl(int Ns, int Nd, double* I) {
-  double xs[OR_MAXN + 1], ws[OR_MAXN + 1], xd[OR_MAXN + 1], wd[OR_MAXN + 1];
+int or_interp_lgl(int Ns, int Nd, or_real* I) {
+  or_real xs[OR_MAXN + 1], ws[OR_MAXN + 1], xd[OR_MAXN + 1], wd[OR_MAXN + 1];
   if (or_lgl(Ns, xs, ws) || or_lgl(Nd, xd, wd)) return -1;
   for (int i = 0; i <= Nd; ++i)
     for (int j = 0; j <= Ns; ++j) I[i * (Ns + 1) + j] = lagrange(Ns + 1, xs, j, xd[i]);
@@ -143,30 +157,30 @@ int or_interp_lgl(int Ns, int Nd, double* I) {
 
 /* Solve A X = B in place (A n x n, B n x m, row-major) by Gauss-Jordan with partial
  * pivoting. Returns -1 if A is singular. */
-static int gauss_jordan(int n, double* A, int m, double* B) {
+static int gauss_jordan(int n, or_real* A, int m, or_real* B) {
   for (int c = 0; c < n; ++c) {
     int piv = c;
     for (int r = c + 1; r < n; ++r)
-      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
-    if (fabs(A[piv * n + c]) < 1e-300) return -1;
+      if (FABS(A[r * n + c]) > FABS(A[piv * n + c])) piv = r;
+    if (FABS(A[piv * n + c]) < 1e-300) return -1;
     if (piv != c) {
       for (int k = 0; k < n; ++k) {
-        double t = A[c * n + k];
+        or_real t = A[c * n + k];
         A[c * n + k] = A[piv * n + k];
         A[piv * n + k] = t;
       }
       for (int k = 0; k < m; ++k) {
-        double t = B[c * m + k];
+        or_real t = B[c * m + k];
         B[c * m + k] = B[piv * m + k];
         B[piv * m + k] = t;
       }
     }
-    double d = A[c * n + c];
+    or_real d = A[c * n + c];
     for (int k = 0; k < n; ++k) A[c * n + k] /= d;
     for (int k = 0; k < m; ++k) B[c * m + k] /= d;
     for (int r = 0; r < n; ++r) {
       if (r == c) continue;
-      double f = A[r * n + c];
+      or_real f = A[r * n + c];
       if (f == 0.0) continue;
       for (int k = 0; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
       for (int k = 0; k < m; ++k) B[r * m + k] -= f * B[c * m + k];
@@ -179,7 +193,7 @@ static int gauss_jordan(int n, double* A, int m, double* B) {
  * degree Nl <= Nh: P = M_l^{-1} I^T W_h, where I interpolates Nl -> Nh nodes and
  * M_l = I^T W_h I is the exact mass matrix (Nh-point Lobatto quadrature is exact for
  * degree 2 Nl <= 2 Nh - 1 when Nh > Nl). For Nh == Nl, P is the identity. */
-int or_project_lgl(int Nh, int Nl, double* P) {
+int or_project_lgl(int Nh, int Nl, or_real* P) {
   int nh = Nh + 1, nl = Nl + 1;
   if (Nl > Nh) {
     set_err("projection needs Nl <= Nh");
@@ -190,13 +204,13 @@ int or_project_lgl(int Nh, int Nl, double* P) {
       for (int j = 0; j < nh; ++j) P[i * nh + j] = (i == j) ? 1.0 : 0.0;
     return 0;
   }
-  double xh[OR_MAXN + 1], wh[OR_MAXN + 1];
-  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
-  double M[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real xh[OR_MAXN + 1], wh[OR_MAXN + 1];
+  or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real M[(OR_MAXN + 1) * (OR_MAXN + 1)];
   if (or_lgl(Nh, xh, wh) || or_interp_lgl(Nl, Nh, I)) return -1;
   for (int a = 0; a < nl; ++a)
     for (int b = 0; b < nl; ++b) {
-      double s = 0.0;
+      or_real s = 0.0;
       for (int j = 0; j < nh; ++j) s += I[j * nl + a] * wh[j] * I[j * nl + b];
       M[a * nl + b] = s;
     }
@@ -215,16 +229,16 @@ int or_project_lgl(int Nh, int Nl, double* P) {
  *   tau = (nu + nu_t)(G + G^T) - 2/3 (nu + nu_t) tr(G) I,  G_ck = d u_c / d x_k
  * ---------------------------------------------------------------------------------- */
 
-void or_normal_flux(const double q[4], const double nh[3], double c0sq, double out[4]) {
-  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+void or_normal_flux(const or_real q[4], const or_real nh[3], or_real c0sq, or_real out[4]) {
+  or_real un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
   out[0] = c0sq * un;
   for (int c = 0; c < 3; ++c) out[1 + c] = q[1 + c] * un + q[0] * nh[c];
 }
 
 /* A = d F_n / d q, rows/cols ordered (p, u, v, w). */
-void or_flux_jacobian(const double q[4], const double nh[3], double c0sq, double A[16]) {
-  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
-  memset(A, 0, 16 * sizeof(double));
+void or_flux_jacobian(const or_real q[4], const or_real nh[3], or_real c0sq, or_real A[16]) {
+  or_real un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+  memset(A, 0, 16 * sizeof(or_real));
   for (int c = 0; c < 3; ++c) A[0 * 4 + 1 + c] = c0sq * nh[c];
   for (int r = 0; r < 3; ++r) {
     A[(1 + r) * 4 + 0] = nh[r];
@@ -234,29 +248,29 @@ void or_flux_jacobian(const double q[4], const double nh[3], double c0sq, double
 
 /* |A| = R |Lambda| R^{-1} from the explicit eigen-decomposition of A:
  *   lambda = u_n (twice, eigenvectors (0, t) with t tangent to the face),
- *   lambda = u_n +- sqrt(u_n^2 + c0^2), eigenvectors with n . u_hat = 1,
+ *   lambda = u_n +- SQRT(u_n^2 + c0^2), eigenvectors with n . u_hat = 1,
  *     p_hat = lambda - 2 u_n, u_hat = (n p_hat + u) / (lambda - u_n).
  * R^{-1} is formed numerically (Gauss-Jordan), not from a closed form. */
-int or_abs_jacobian(const double q[4], const double nh[3], double c0sq, double absA[16]) {
-  double un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
-  double a = sqrt(un * un + c0sq);
-  double lam[4] = {un, un, un + a, un - a};
+int or_abs_jacobian(const or_real q[4], const or_real nh[3], or_real c0sq, or_real absA[16]) {
+  or_real un = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+  or_real a = SQRT(un * un + c0sq);
+  or_real lam[4] = {un, un, un + a, un - a};
   /* tangent vectors: t1 = normalize(e x n) with e the axis least aligned with n */
   int ax = 0;
-  if (fabs(nh[1]) < fabs(nh[ax])) ax = 1;
-  if (fabs(nh[2]) < fabs(nh[ax])) ax = 2;
-  double e[3] = {0, 0, 0};
+  if (FABS(nh[1]) < FABS(nh[ax])) ax = 1;
+  if (FABS(nh[2]) < FABS(nh[ax])) ax = 2;
+  or_real e[3] = {0, 0, 0};
   e[ax] = 1.0;
-  double t1[3] = {e[1] * nh[2] - e[2] * nh[1], e[2] * nh[0] - e[0] * nh[2], e[0] * nh[1] - e[1] * nh[0]};
-  double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  or_real t1[3] = {e[1] * nh[2] - e[2] * nh[1], e[2] * nh[0] - e[0] * nh[2], e[0] * nh[1] - e[1] * nh[0]};
+  or_real l1 = SQRT(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
   for (int c = 0; c < 3; ++c) t1[c] /= l1;
-  double t2[3] = {nh[1] * t1[2] - nh[2] * t1[1], nh[2] * t1[0] - nh[0] * t1[2], nh[0] * t1[1] - nh[1] * t1[0]};
-  double R[16], Rinv[16], Rw[16];
+  or_real t2[3] = {nh[1] * t1[2] - nh[2] * t1[1], nh[2] * t1[0] - nh[0] * t1[2], nh[0] * t1[1] - nh[1] * t1[0]};
+  or_real R[16], Rinv[16], Rw[16];
   /* column k of R = eigenvector k */
   for (int r = 0; r < 4; ++r) R[r * 4 + 0] = (r == 0) ? 0.0 : t1[r - 1];
   for (int r = 0; r < 4; ++r) R[r * 4 + 1] = (r == 0) ? 0.0 : t2[r - 1];
   for (int k = 2; k < 4; ++k) {
-    double ph = lam[k] - 2.0 * un;
+    or_real ph = lam[k] - 2.0 * un;
     R[0 * 4 + k] = ph;
     for (int c = 0; c < 3; ++c) R[(1 + c) * 4 + k] = (nh[c] * ph + q[1 + c]) / (lam[k] - un);
   }
@@ -268,8 +282,8 @@ int or_abs_jacobian(const double q[4], const double nh[3], double c0sq, double a
   }
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < 4; ++k) s += R[i * 4 + k] * fabs(lam[k]) * Rinv[k * 4 + j];
+      or_real s = 0.0;
+      for (int k = 0; k < 4; ++k) s += R[i * 4 + k] * FABS(lam[k]) * Rinv[k * 4 + j];
       absA[i * 4 + j] = s;
     }
   return 0;
@@ -277,26 +291,26 @@ int or_abs_jacobian(const double q[4], const double nh[3], double c0sq, double a
 
 /* Convective numerical flux through a face with unit normal nh pointing from the
  * qm side to the qp side (Sec. 2.3: Roe; LLF as the alternative flux). */
-int or_riemann(const double qm[4], const double qp[4], const double nh[3], const or_params* prm,
-               double out[4]) {
-  double fm[4], fp[4];
+int or_riemann(const or_real qm[4], const or_real qp[4], const or_real nh[3], const or_params* prm,
+               or_real out[4]) {
+  or_real fm[4], fp[4];
   or_normal_flux(qm, nh, prm->c0sq, fm);
   or_normal_flux(qp, nh, prm->c0sq, fp);
   if (prm->riemann == 0) {
-    double qb[4], absA[16];
+    or_real qb[4], absA[16];
     for (int v = 0; v < 4; ++v) qb[v] = 0.5 * (qm[v] + qp[v]);
     if (or_abs_jacobian(qb, nh, prm->c0sq, absA)) return -1;
     for (int v = 0; v < 4; ++v) {
-      double d = 0.0;
+      or_real d = 0.0;
       for (int k = 0; k < 4; ++k) d += absA[v * 4 + k] * (qp[k] - qm[k]);
       out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * d;
     }
   } else {
-    double unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
-    double unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
-    double sm = fabs(unm) + sqrt(unm * unm + prm->c0sq);
-    double sp = fabs(unp) + sqrt(unp * unp + prm->c0sq);
-    double s = sm > sp ? sm : sp;
+    or_real unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+    or_real unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
+    or_real sm = FABS(unm) + SQRT(unm * unm + prm->c0sq);
+    or_real sp = FABS(unp) + SQRT(unp * unp + prm->c0sq);
+    or_real s = sm > sp ? sm : sp;
     for (int v = 0; v < 4; ++v) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * s * (qp[v] - qm[v]);
   }
   return 0;
@@ -304,19 +318,19 @@ int or_riemann(const double qm[4], const double qp[4], const double nh[3], const
 
 /* LES eddy viscosity (App. A, Eq. for the Vreman model; Smagorinsky as the alternative
  * closure): G[c*3+k] = d u_c / d x_k, delta the filter width. */
-double or_eddy_viscosity(const double G[9], double delta, const or_params* prm) {
+or_real or_eddy_viscosity(const or_real G[9], or_real delta, const or_params* prm) {
   if (prm->closure == 0) {
-    double ss = 0.0;
+    or_real ss = 0.0;
     for (int c = 0; c < 3; ++c)
       for (int k = 0; k < 3; ++k) {
-        double s = 0.5 * (G[c * 3 + k] + G[k * 3 + c]);
+        or_real s = 0.5 * (G[c * 3 + k] + G[k * 3 + c]);
         ss += s * s;
       }
-    double cd = prm->cs * delta;
-    return cd * cd * sqrt(2.0 * ss);
+    or_real cd = prm->cs * delta;
+    return cd * cd * SQRT(2.0 * ss);
   }
   /* Vreman: alpha_ij = d u_j / d x_i, beta_ij = delta^2 alpha_mi alpha_mj */
-  double al[3][3], aa = 0.0, be[3][3];
+  or_real al[3][3], aa = 0.0, be[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       al[i][j] = G[j * 3 + i];
@@ -324,23 +338,23 @@ double or_eddy_viscosity(const double G[9], double delta, const or_params* prm) 
     }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
+      or_real s = 0.0;
       for (int m = 0; m < 3; ++m) s += al[m][i] * al[m][j];
       be[i][j] = delta * delta * s;
     }
-  double B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] - be[0][2] * be[0][2] +
+  or_real B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] - be[0][2] * be[0][2] +
              be[1][1] * be[2][2] - be[1][2] * be[1][2];
   if (aa < 1e-300 || B <= 0.0) return 0.0;
-  return prm->cv * sqrt(B / aa);
+  return prm->cv * SQRT(B / aa);
 }
 
 /* Low-storage third-order Runge-Kutta (Sec. 2.3 cites a low-storage explicit RK3; the
  * Williamson 2N-storage coefficients are used):  g <- A_s g + dt R(q),  q <- q + B_s g. */
-static const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
-static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+static const or_real RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+static const or_real RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 
-double or_rk3_linear(double z) {
-  double y = 1.0, g = 0.0;
+or_real or_rk3_linear(or_real z) {
+  or_real y = 1.0, g = 0.0;
   for (int s = 0; s < 3; ++s) {
     g = (s == 0 ? 0.0 : RK_A[s] * g) + z * y;
     y = y + RK_B[s] * g;
@@ -353,7 +367,7 @@ double or_rk3_linear(double z) {
  * ---------------------------------------------------------------------------------- */
 
 typedef struct {
-  double x[OR_MAXN + 1], w[OR_MAXN + 1], D[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real x[OR_MAXN + 1], w[OR_MAXN + 1], D[(OR_MAXN + 1) * (OR_MAXN + 1)];
 } op1d;
 
 struct or_mesh {
@@ -362,12 +376,12 @@ struct or_mesh {
   int8_t* N;
   uint8_t* flag;
   int64_t* off;
-  double* gx;     /* [ne][(g+1)^3][3] */
+  or_real* gx;     /* [ne][(g+1)^3][3] */
   int64_t* nb_e;  /* [ne][6]: neighbour element, -1 at a boundary */
   int8_t* nb_f;   /* [ne][6]: neighbour local face */
   int8_t* nb_o;   /* [ne][6]: orientation code mapping neighbour face coords to mine */
   int8_t* bc;     /* [ne][6]: boundary tag (-1 interior) */
-  double* vscale; /* [ne] */
+  or_real* vscale; /* [ne] */
   or_params p;
   op1d op[OR_MAXN + 1];
 };
@@ -436,7 +450,7 @@ void or_destroy(or_mesh* m) {
   free(m);
 }
 
-or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const double* gxyz, const int8_t* bc_tag,
+or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const or_real* gxyz, const int8_t* bc_tag,
                    const int8_t* order, const uint8_t* flag, const or_params* prm) {
   if (ne <= 0 || !hex || !gxyz || !order || !flag || !prm) {
     set_err("bad arguments");
@@ -458,13 +472,13 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const double* gxyz, co
   m->N = (int8_t*)malloc(ne);
   m->flag = (uint8_t*)malloc(ne);
   m->off = (int64_t*)malloc(sizeof(int64_t) * (ne + 1));
-  m->gx = (double*)malloc(sizeof(double) * ne * ng3 * 3);
+  m->gx = (or_real*)malloc(sizeof(or_real) * ne * ng3 * 3);
   m->nb_e = (int64_t*)malloc(sizeof(int64_t) * ne * 6);
   m->nb_f = (int8_t*)malloc(ne * 6);
   m->nb_o = (int8_t*)malloc(ne * 6);
   m->bc = (int8_t*)malloc(ne * 6);
-  m->vscale = (double*)malloc(sizeof(double) * ne);
-  memcpy(m->gx, gxyz, sizeof(double) * ne * ng3 * 3);
+  m->vscale = (or_real*)malloc(sizeof(or_real) * ne);
+  memcpy(m->gx, gxyz, sizeof(or_real) * ne * ng3 * 3);
   m->off[0] = 0;
   for (int64_t e = 0; e < ne; ++e) {
     if (order[e] < 1 || order[e] > OR_MAXN || order[e] < g) {
@@ -570,7 +584,7 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const double* gxyz, co
   return m;
 }
 
-int or_set_visc_scale(or_mesh* m, const double* scale) {
+int or_set_visc_scale(or_mesh* m, const or_real* scale) {
   for (int64_t e = 0; e < m->ne; ++e) m->vscale[e] = scale ? scale[e] : 1.0;
   return 0;
 }
@@ -584,12 +598,12 @@ int or_set_visc_scale(or_mesh* m, const double* scale) {
  * ---------------------------------------------------------------------------------- */
 
 /* derivative along direction k of a field on an n^3 tensor grid with matrix D (n x n) */
-static void deriv3(int n, const double* D, int k, const double* u, double* du) {
+static void deriv3(int n, const or_real* D, int k, const or_real* u, or_real* du) {
   for (int c = 0; c < n; ++c)
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
         int ijk[3] = {a, b, c};
-        double s = 0.0;
+        or_real s = 0.0;
         for (int mm = 0; mm < n; ++mm) {
           int src[3] = {a, b, c};
           src[k] = mm;
@@ -600,11 +614,11 @@ static void deriv3(int n, const double* D, int k, const double* u, double* du) {
 }
 
 /* tensor interpolation from an ns^3 grid to an nd^3 grid with I (nd x ns) */
-static void interp3(int ns, int nd, const double* I, const double* u, double* out) {
+static void interp3(int ns, int nd, const or_real* I, const or_real* u, or_real* out) {
   for (int k = 0; k < nd; ++k)
     for (int j = 0; j < nd; ++j)
       for (int i = 0; i < nd; ++i) {
-        double s = 0.0;
+        or_real s = 0.0;
         for (int c = 0; c < ns; ++c)
           for (int b = 0; b < ns; ++b)
             for (int a = 0; a < ns; ++a)
@@ -613,24 +627,24 @@ static void interp3(int ns, int nd, const double* I, const double* u, double* ou
       }
 }
 
-int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja) {
+int or_element_geometry(const or_mesh* m, int64_t e, or_real* J, or_real* Ja) {
   int g = m->g, ng = g + 1, ng3 = ng * ng * ng;
   int N = m->N[e], n = N + 1, n3 = n * n * n;
-  const double* Dg = m->op[g].D;
-  double I[(OR_MAXN + 1) * (OR_MAXG + 1)];
+  const or_real* Dg = m->op[g].D;
+  or_real I[(OR_MAXN + 1) * (OR_MAXG + 1)];
   or_interp_lgl(g, N, I);
-  double X[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
-  double dX[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+  or_real X[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+  or_real dX[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
   for (int p = 0; p < ng3; ++p)
     for (int c = 0; c < 3; ++c) X[c][p] = m->gx[(e * ng3 + p) * 3 + c];
   for (int c = 0; c < 3; ++c)
     for (int k = 0; k < 3; ++k) deriv3(ng, Dg, k, X[c], dX[c][k]);
   /* J at the element nodes */
-  double* dXn = (double*)malloc(sizeof(double) * 9 * n3);
+  or_real* dXn = (or_real*)malloc(sizeof(or_real) * 9 * n3);
   for (int c = 0; c < 3; ++c)
     for (int k = 0; k < 3; ++k) interp3(ng, n, I, dX[c][k], dXn + (c * 3 + k) * n3);
   for (int p = 0; p < n3; ++p) {
-    double a[3][3];
+    or_real a[3][3];
     for (int c = 0; c < 3; ++c)
       for (int k = 0; k < 3; ++k) a[c][k] = dXn[(c * 3 + k) * n3 + p];
     J[p] = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
@@ -640,20 +654,20 @@ int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja) {
   /* curl form at degree g */
   for (int nn = 0; nn < 3; ++nn) {
     int mm = (nn + 1) % 3, ll = (nn + 2) % 3;
-    double v[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
-    double dv[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    or_real v[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    or_real dv[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
     for (int k = 0; k < 3; ++k)
       for (int p = 0; p < ng3; ++p) v[k][p] = X[ll][p] * dX[mm][k][p];
     for (int k = 0; k < 3; ++k)
       for (int d = 0; d < 3; ++d) deriv3(ng, Dg, d, v[k], dv[k][d]); /* dv[k][d] = d v_k / d xi_d */
-    double curl[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    or_real curl[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
     for (int p = 0; p < ng3; ++p) {
       curl[0][p] = dv[2][1][p] - dv[1][2][p];
       curl[1][p] = dv[0][2][p] - dv[2][0][p];
       curl[2][p] = dv[1][0][p] - dv[0][1][p];
     }
     for (int i = 0; i < 3; ++i) {
-      double neg[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+      or_real neg[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
       for (int p = 0; p < ng3; ++p) neg[p] = -curl[i][p];
       interp3(ng, n, I, neg, Ja + (i * 3 + nn) * n3);
     }
@@ -661,14 +675,14 @@ int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja) {
   return 0;
 }
 
-int or_node_coords(const or_mesh* m, double* xyz) {
+int or_node_coords(const or_mesh* m, or_real* xyz) {
   int g = m->g, ng = g + 1, ng3 = ng * ng * ng;
   for (int64_t e = 0; e < m->ne; ++e) {
     int N = m->N[e], n = N + 1, n3 = n * n * n;
-    double I[(OR_MAXN + 1) * (OR_MAXG + 1)];
+    or_real I[(OR_MAXN + 1) * (OR_MAXG + 1)];
     or_interp_lgl(g, N, I);
-    double X[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
-    double* out = (double*)malloc(sizeof(double) * n3);
+    or_real X[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
+    or_real* out = (or_real*)malloc(sizeof(or_real) * n3);
     for (int c = 0; c < 3; ++c) {
       for (int p = 0; p < ng3; ++p) X[p] = m->gx[(e * ng3 + p) * 3 + c];
       interp3(ng, n, I, X, out);
@@ -684,37 +698,37 @@ int or_node_coords(const or_mesh* m, double* xyz) {
  * ---------------------------------------------------------------------------------- */
 
 typedef struct {
-  double* J;   /* [n3] */
-  double* Ja;  /* [3][3][n3] */
-  double delta;
+  or_real* J;   /* [n3] */
+  or_real* Ja;  /* [3][3][n3] */
+  or_real delta;
 } geo_t;
 
 typedef struct {
   const or_mesh* m;
-  const double* q;
+  const or_real* q;
   geo_t* geo;    /* per element, J == NULL if not computed */
-  double** G;    /* per element gradient [3][3][n3], NULL if not computed */
+  or_real** G;    /* per element gradient [3][3][n3], NULL if not computed */
 } work_t;
 
 static void compute_geo(const or_mesh* m, int64_t e, geo_t* gt) {
   int n = m->N[e] + 1, n3 = n * n * n;
-  gt->J = (double*)malloc(sizeof(double) * n3);
-  gt->Ja = (double*)malloc(sizeof(double) * 9 * n3);
+  gt->J = (or_real*)malloc(sizeof(or_real) * n3);
+  gt->Ja = (or_real*)malloc(sizeof(or_real) * 9 * n3);
   or_element_geometry(m, e, gt->J, gt->Ja);
-  const double* w = m->op[m->N[e]].w;
-  double V = 0.0;
+  const or_real* w = m->op[m->N[e]].w;
+  or_real V = 0.0;
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i) V += w[i] * w[j] * w[k] * gt->J[i + n * (j + n * k)];
   /* filter width: cube root of the element volume over the nodes per direction */
-  gt->delta = cbrt(V) / n;
+  gt->delta = CBRT(V) / n;
 }
 
 /* 2D tensor interpolation on a face: ns^2 -> nd^2 with I (nd x ns) */
-static void interp2(int ns, int nd, const double* I, const double* u, double* out) {
+static void interp2(int ns, int nd, const or_real* I, const or_real* u, or_real* out) {
   for (int b = 0; b < nd; ++b)
     for (int a = 0; a < nd; ++a) {
-      double s = 0.0;
+      or_real s = 0.0;
       for (int bb = 0; bb < ns; ++bb)
         for (int aa = 0; aa < ns; ++aa) s += I[a * ns + aa] * I[b * ns + bb] * u[aa + ns * bb];
       out[a + nd * b] = s;
@@ -722,10 +736,10 @@ static void interp2(int ns, int nd, const double* I, const double* u, double* ou
 }
 
 /* outward area-weighted normal S = sigma Ja^d at the face nodes of element e, face f */
-static void face_S(const or_mesh* m, const geo_t* gt, int64_t e, int f, double* S /*[3][n2]*/) {
+static void face_S(const or_mesh* m, const geo_t* gt, int64_t e, int f, or_real* S /*[3][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
   int d = f >> 1;
-  double sg = (f & 1) ? 1.0 : -1.0;
+  or_real sg = (f & 1) ? 1.0 : -1.0;
   for (int b = 0; b < n; ++b)
     for (int a = 0; a < n; ++a) {
       int64_t p = face_node(f, N, a, b);
@@ -733,7 +747,7 @@ static void face_S(const or_mesh* m, const geo_t* gt, int64_t e, int f, double* 
     }
 }
 
-static void face_q(const or_mesh* m, const double* q, int64_t e, int f, double* T /*[4][n2]*/) {
+static void face_q(const or_mesh* m, const or_real* q, int64_t e, int f, or_real* T /*[4][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n;
   for (int b = 0; b < n; ++b)
     for (int a = 0; a < n; ++a) {
@@ -743,36 +757,36 @@ static void face_q(const or_mesh* m, const double* q, int64_t e, int f, double* 
 }
 
 /* viscous stress at one node of an NS element */
-static void stress(const or_mesh* m, const geo_t* gt, const double* G, int64_t e, int n3, int64_t p,
-                   double tau[3][3]) {
-  double Gp[9];
+static void stress(const or_mesh* m, const geo_t* gt, const or_real* G, int64_t e, int n3, int64_t p,
+                   or_real tau[3][3]) {
+  or_real Gp[9];
   for (int c = 0; c < 3; ++c)
     for (int k = 0; k < 3; ++k) Gp[c * 3 + k] = G[(c * 3 + k) * n3 + p];
-  double nut = or_eddy_viscosity(Gp, gt->delta, &m->p);
-  double mu = (m->p.nu + nut) * m->vscale[e];
-  double tr = Gp[0] + Gp[4] + Gp[8];
+  or_real nut = or_eddy_viscosity(Gp, gt->delta, &m->p);
+  or_real mu = (m->p.nu + nut) * m->vscale[e];
+  or_real tr = Gp[0] + Gp[4] + Gp[8];
   for (int c = 0; c < 3; ++c)
     for (int k = 0; k < 3; ++k) tau[c][k] = mu * (Gp[c * 3 + k] + Gp[k * 3 + c]) - (c == k ? 2.0 / 3.0 * mu * tr : 0.0);
 }
 
 /* area-weighted outward viscous flux trace tau . S of element e on face f (zero for Euler) */
-static void face_fv(const work_t* W, int64_t e, int f, double* Fv /*[3][n2]*/) {
+static void face_fv(const work_t* W, int64_t e, int f, or_real* Fv /*[3][n2]*/) {
   const or_mesh* m = W->m;
   int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
   if (!m->flag[e]) {
-    memset(Fv, 0, sizeof(double) * 3 * n2);
+    memset(Fv, 0, sizeof(or_real) * 3 * n2);
     return;
   }
   const geo_t* gt = &W->geo[e];
-  double* S = (double*)malloc(sizeof(double) * 3 * n2);
+  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
   face_S(m, gt, e, f, S);
   for (int b = 0; b < n; ++b)
     for (int a = 0; a < n; ++a) {
       int64_t p = face_node(f, N, a, b);
-      double tau[3][3];
+      or_real tau[3][3];
       stress(m, gt, W->G[e], e, n3, p, tau);
       for (int c = 0; c < 3; ++c) {
-        double s = 0.0;
+        or_real s = 0.0;
         for (int k = 0; k < 3; ++k) s += tau[c][k] * S[k * n2 + a + n * b];
         Fv[c * n2 + a + n * b] = s;
       }
@@ -780,7 +794,7 @@ static void face_fv(const work_t* W, int64_t e, int f, double* Fv /*[3][n2]*/) {
   free(S);
 }
 
-static void ghost_state(const or_mesh* m, int tag, const double* qin, double* qg) {
+static void ghost_state(const or_mesh* m, int tag, const or_real* qin, or_real* qg) {
   if (tag == 1) { /* inflow: prescribed velocity, interior pressure */
     qg[0] = qin[0];
     for (int c = 0; c < 3; ++c) qg[1 + c] = m->p.inflow[1 + c];
@@ -794,9 +808,9 @@ static void ghost_state(const or_mesh* m, int tag, const double* qin, double* qg
  * my trace, the neighbour trace (or ghost), my S interpolated. */
 typedef struct {
   int M, nm;          /* mortar order, my order */
-  double* qm;         /* [4][(M+1)^2] */
-  double* qp;         /* [4][(M+1)^2] */
-  double* S;          /* [3][(M+1)^2] */
+  or_real* qm;         /* [4][(M+1)^2] */
+  or_real* qp;         /* [4][(M+1)^2] */
+  or_real* S;          /* [3][(M+1)^2] */
   int64_t nbr;        /* -1 at a boundary */
   int nf, no, tag;
 } mortar_t;
@@ -809,11 +823,11 @@ static void mortar_free(mortar_t* mt) {
 
 /* interpolate a neighbour face field (order Nn) to the mortar order M and rotate it into
  * my face coordinates */
-static void nbr_to_mortar(int Nn, int M, int o, int nvar, const double* src, double* dst) {
+static void nbr_to_mortar(int Nn, int M, int o, int nvar, const or_real* src, or_real* dst) {
   int nn = Nn + 1, nM = M + 1, nM2 = nM * nM;
-  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
   or_interp_lgl(Nn, M, I);
-  double* tmp = (double*)malloc(sizeof(double) * nM2);
+  or_real* tmp = (or_real*)malloc(sizeof(or_real) * nM2);
   for (int v = 0; v < nvar; ++v) {
     interp2(nn, nM, I, src + v * nn * nn, tmp);
     for (int b1 = 0; b1 < nM; ++b1)
@@ -826,17 +840,17 @@ static void nbr_to_mortar(int Nn, int M, int o, int nvar, const double* src, dou
   free(tmp);
 }
 
-static void mine_to_mortar(int Nm, int M, int nvar, const double* src, double* dst) {
+static void mine_to_mortar(int Nm, int M, int nvar, const or_real* src, or_real* dst) {
   int nm = Nm + 1, nM = M + 1;
-  double I[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
   or_interp_lgl(Nm, M, I);
   for (int v = 0; v < nvar; ++v) interp2(nm, nM, I, src + v * nm * nm, dst + v * nM * nM);
 }
 
 /* project a mortar field (order M, my coordinates) to my order */
-static void mortar_to_mine(int M, int Nm, int nvar, const double* src, double* dst) {
+static void mortar_to_mine(int M, int Nm, int nvar, const or_real* src, or_real* dst) {
   int nm = Nm + 1, nM = M + 1;
-  double P[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real P[(OR_MAXN + 1) * (OR_MAXN + 1)];
   or_project_lgl(M, Nm, P);
   for (int v = 0; v < nvar; ++v) interp2(nM, nm, P, src + v * nM * nM, dst + v * nm * nm);
 }
@@ -853,24 +867,24 @@ static void mortar_build(const work_t* W, int64_t e, int f, mortar_t* mt) {
   mt->nf = m->nb_f[e * 6 + f];
   mt->no = m->nb_o[e * 6 + f];
   mt->tag = m->bc[e * 6 + f];
-  mt->qm = (double*)malloc(sizeof(double) * 4 * nM2);
-  mt->qp = (double*)malloc(sizeof(double) * 4 * nM2);
-  mt->S = (double*)malloc(sizeof(double) * 3 * nM2);
-  double* tq = (double*)malloc(sizeof(double) * 4 * nm * nm);
-  double* tS = (double*)malloc(sizeof(double) * 3 * nm * nm);
+  mt->qm = (or_real*)malloc(sizeof(or_real) * 4 * nM2);
+  mt->qp = (or_real*)malloc(sizeof(or_real) * 4 * nM2);
+  mt->S = (or_real*)malloc(sizeof(or_real) * 3 * nM2);
+  or_real* tq = (or_real*)malloc(sizeof(or_real) * 4 * nm * nm);
+  or_real* tS = (or_real*)malloc(sizeof(or_real) * 3 * nm * nm);
   face_q(m, W->q, e, f, tq);
   face_S(m, &W->geo[e], e, f, tS);
   mine_to_mortar(Nm, M, 4, tq, mt->qm);
   mine_to_mortar(Nm, M, 3, tS, mt->S);
   if (nb >= 0) {
     int nn = Nn + 1;
-    double* tn = (double*)malloc(sizeof(double) * 4 * nn * nn);
+    or_real* tn = (or_real*)malloc(sizeof(or_real) * 4 * nn * nn);
     face_q(m, W->q, nb, mt->nf, tn);
     nbr_to_mortar(Nn, M, mt->no, 4, tn, mt->qp);
     free(tn);
   } else {
     for (int p = 0; p < nM2; ++p) {
-      double qi[4], qg[4];
+      or_real qi[4], qg[4];
       for (int v = 0; v < 4; ++v) qi[v] = mt->qm[v * nM2 + p];
       ghost_state(m, mt->tag, qi, qg);
       for (int v = 0; v < 4; ++v) mt->qp[v * nM2 + p] = qg[v];
@@ -881,14 +895,14 @@ static void mortar_build(const work_t* W, int64_t e, int f, mortar_t* mt) {
 }
 
 /* BR1 lifting data on face (e, f): projected u*_c S_k, shape [3][3][n2] */
-static void face_ustar(const work_t* W, int64_t e, int f, double* LU) {
+static void face_ustar(const work_t* W, int64_t e, int f, or_real* LU) {
   mortar_t mt;
   mortar_build(W, e, f, &mt);
   int nM = mt.M + 1, nM2 = nM * nM;
-  double* U = (double*)malloc(sizeof(double) * 9 * nM2);
+  or_real* U = (or_real*)malloc(sizeof(or_real) * 9 * nM2);
   for (int p = 0; p < nM2; ++p)
     for (int c = 0; c < 3; ++c) {
-      double us = 0.5 * (mt.qm[(1 + c) * nM2 + p] + mt.qp[(1 + c) * nM2 + p]);
+      or_real us = 0.5 * (mt.qm[(1 + c) * nM2 + p] + mt.qp[(1 + c) * nM2 + p]);
       for (int k = 0; k < 3; ++k) U[(c * 3 + k) * nM2 + p] = us * mt.S[k * nM2 + p];
     }
   mortar_to_mine(mt.M, mt.nm, 9, U, LU);
@@ -897,23 +911,23 @@ static void face_ustar(const work_t* W, int64_t e, int f, double* LU) {
 }
 
 /* Total numerical flux on face (e, f): projected (F_e* - F_v*) . S (my outward), [4][n2] */
-static int face_hstar(const work_t* W, int64_t e, int f, double* LH) {
+static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
   const or_mesh* m = W->m;
   mortar_t mt;
   mortar_build(W, e, f, &mt);
   int nM = mt.M + 1, nM2 = nM * nM, nm = mt.nm + 1, nm2 = nm * nm;
-  double* H = (double*)malloc(sizeof(double) * 4 * nM2);
-  double* Fvm = (double*)calloc(3 * nM2, sizeof(double));
-  double* Fvp = (double*)calloc(3 * nM2, sizeof(double));
+  or_real* H = (or_real*)malloc(sizeof(or_real) * 4 * nM2);
+  or_real* Fvm = (or_real*)calloc(3 * nM2, sizeof(or_real));
+  or_real* Fvp = (or_real*)calloc(3 * nM2, sizeof(or_real));
   int any_visc = m->flag[e] || (mt.nbr >= 0 && m->flag[mt.nbr]);
   if (any_visc) {
-    double* t = (double*)malloc(sizeof(double) * 3 * nm2);
+    or_real* t = (or_real*)malloc(sizeof(or_real) * 3 * nm2);
     face_fv(W, e, f, t);
     mine_to_mortar(mt.nm, mt.M, 3, t, Fvm);
     free(t);
     if (mt.nbr >= 0) {
       int nn = m->N[mt.nbr] + 1;
-      double* tn = (double*)malloc(sizeof(double) * 3 * nn * nn);
+      or_real* tn = (or_real*)malloc(sizeof(or_real) * 3 * nn * nn);
       face_fv(W, mt.nbr, mt.nf, tn);
       nbr_to_mortar(m->N[mt.nbr], mt.M, mt.no, 3, tn, Fvp);
       free(tn);
@@ -924,10 +938,10 @@ static int face_hstar(const work_t* W, int64_t e, int f, double* LH) {
   }
   int rc = 0;
   for (int p = 0; p < nM2; ++p) {
-    double S[3] = {mt.S[p], mt.S[nM2 + p], mt.S[2 * nM2 + p]};
-    double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-    double nh[3] = {S[0] / s, S[1] / s, S[2] / s};
-    double qm[4], qp[4], Fs[4];
+    or_real S[3] = {mt.S[p], mt.S[nM2 + p], mt.S[2 * nM2 + p]};
+    or_real s = SQRT(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    or_real nh[3] = {S[0] / s, S[1] / s, S[2] / s};
+    or_real qm[4], qp[4], Fs[4];
     for (int v = 0; v < 4; ++v) {
       qm[v] = mt.qm[v * nM2 + p];
       qp[v] = mt.qp[v * nM2 + p];
@@ -935,7 +949,7 @@ static int face_hstar(const work_t* W, int64_t e, int f, double* LH) {
     if (or_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
     H[p] = Fs[0] * s;
     for (int c = 0; c < 3; ++c) {
-      double fv = 0.5 * (Fvm[c * nM2 + p] - Fvp[c * nM2 + p]);
+      or_real fv = 0.5 * (Fvm[c * nM2 + p] - Fvp[c * nM2 + p]);
       H[(1 + c) * nM2 + p] = Fs[1 + c] * s - fv;
     }
   }
@@ -949,25 +963,25 @@ static int face_hstar(const work_t* W, int64_t e, int f, double* LH) {
 
 /* BR1 gradient, weak form (integrated by parts, Bassi-Rebay 1):
  *   w J G_ck = -sum_d (w/w_{i_d}) sum_m w_m D_{m i_d} (u_c Ja^d_k)_m + face terms u*_c S_k */
-static void element_gradient(const work_t* W, int64_t e, double* G) {
+static void element_gradient(const work_t* W, int64_t e, or_real* G) {
   const or_mesh* m = W->m;
   int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
-  const double* w = m->op[N].w;
-  const double* D = m->op[N].D;
+  const or_real* w = m->op[N].w;
+  const or_real* D = m->op[N].D;
   const geo_t* gt = &W->geo[e];
-  const double* q = W->q;
+  const or_real* q = W->q;
   int64_t o = m->off[e];
-  memset(G, 0, sizeof(double) * 9 * n3);
+  memset(G, 0, sizeof(or_real) * 9 * n3);
   for (int c = 0; c < 3; ++c)
     for (int k = 0; k < 3; ++k) {
-      double* Gck = G + (c * 3 + k) * n3;
+      or_real* Gck = G + (c * 3 + k) * n3;
       for (int kk = 0; kk < n; ++kk)
         for (int jj = 0; jj < n; ++jj)
           for (int ii = 0; ii < n; ++ii) {
             int ijk[3] = {ii, jj, kk};
-            double s = 0.0;
+            or_real s = 0.0;
             for (int d = 0; d < 3; ++d) {
-              double sd = 0.0;
+              or_real sd = 0.0;
               for (int mm = 0; mm < n; ++mm) {
                 int src[3] = {ii, jj, kk};
                 src[d] = mm;
@@ -979,7 +993,7 @@ static void element_gradient(const work_t* W, int64_t e, double* G) {
             Gck[ii + n * (jj + n * kk)] = s;
           }
     }
-  double* LU = (double*)malloc(sizeof(double) * 9 * n2);
+  or_real* LU = (or_real*)malloc(sizeof(or_real) * 9 * n2);
   for (int f = 0; f < 6; ++f) {
     face_ustar(W, e, f, LU);
     for (int b = 0; b < n; ++b)
@@ -993,7 +1007,7 @@ static void element_gradient(const work_t* W, int64_t e, double* G) {
     for (int p = 0; p < n3; ++p) G[ck * n3 + p] /= gt->J[p];
 }
 
-int or_element_gradient(const or_mesh* m, const double* q, int64_t e, double* G) {
+int or_element_gradient(const or_mesh* m, const or_real* q, int64_t e, or_real* G) {
   if (e < 0 || e >= m->ne) return -1;
   work_t W;
   W.m = m;
@@ -1011,47 +1025,47 @@ int or_element_gradient(const or_mesh* m, const double* q, int64_t e, double* G)
 /* Residual of one element, weak form (App. B, Eq. NS4 with the viscous terms integrated
  * by parts under BR1):
  *   w J R = sum_d (w / w_{i_d}) sum_m w_m D_{m i_d} Ftil^d_m - w_face H*  */
-static int element_residual(const work_t* W, int64_t e, double* R) {
+static int element_residual(const work_t* W, int64_t e, or_real* R) {
   const or_mesh* m = W->m;
   int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
-  const double* w = m->op[N].w;
-  const double* D = m->op[N].D;
+  const or_real* w = m->op[N].w;
+  const or_real* D = m->op[N].D;
   const geo_t* gt = &W->geo[e];
-  const double* q = W->q;
+  const or_real* q = W->q;
   int64_t o = m->off[e], T = m->total;
-  double c0sq = m->p.c0sq;
+  or_real c0sq = m->p.c0sq;
   /* contravariant total flux Ftil[d][v][p] = sum_k Ja^d_k (F_e - F_v)_{v,k} */
-  double* Ft = (double*)malloc(sizeof(double) * 12 * n3);
+  or_real* Ft = (or_real*)malloc(sizeof(or_real) * 12 * n3);
   for (int p = 0; p < n3; ++p) {
-    double qq[4];
+    or_real qq[4];
     for (int v = 0; v < 4; ++v) qq[v] = q[v * T + o + p];
-    double F[4][3];
+    or_real F[4][3];
     for (int k = 0; k < 3; ++k) {
       F[0][k] = c0sq * qq[1 + k];
       for (int c = 0; c < 3; ++c) F[1 + c][k] = qq[1 + c] * qq[1 + k] + (c == k ? qq[0] : 0.0);
     }
     if (m->flag[e]) {
-      double tau[3][3];
+      or_real tau[3][3];
       stress(m, gt, W->G[e], e, n3, p, tau);
       for (int c = 0; c < 3; ++c)
         for (int k = 0; k < 3; ++k) F[1 + c][k] -= tau[c][k];
     }
     for (int d = 0; d < 3; ++d)
       for (int v = 0; v < 4; ++v) {
-        double s = 0.0;
+        or_real s = 0.0;
         for (int k = 0; k < 3; ++k) s += gt->Ja[(d * 3 + k) * n3 + p] * F[v][k];
         Ft[(d * 4 + v) * n3 + p] = s;
       }
   }
-  double* JR = (double*)calloc(4 * n3, sizeof(double));
+  or_real* JR = (or_real*)calloc(4 * n3, sizeof(or_real));
   for (int v = 0; v < 4; ++v)
     for (int kk = 0; kk < n; ++kk)
       for (int jj = 0; jj < n; ++jj)
         for (int ii = 0; ii < n; ++ii) {
           int ijk[3] = {ii, jj, kk};
-          double s = 0.0;
+          or_real s = 0.0;
           for (int d = 0; d < 3; ++d) {
-            double sd = 0.0;
+            or_real sd = 0.0;
             for (int mm = 0; mm < n; ++mm) {
               int src[3] = {ii, jj, kk};
               src[d] = mm;
@@ -1061,7 +1075,7 @@ static int element_residual(const work_t* W, int64_t e, double* R) {
           }
           JR[v * n3 + ii + n * (jj + n * kk)] = s;
         }
-  double* LH = (double*)malloc(sizeof(double) * 4 * n2);
+  or_real* LH = (or_real*)malloc(sizeof(or_real) * 4 * n2);
   int rc = 0;
   for (int f = 0; f < 6; ++f) {
     if (face_hstar(W, e, f, LH)) rc = -1;
@@ -1089,7 +1103,7 @@ static void free_work(work_t* W) {
   free(W->G);
 }
 
-int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, const int64_t* sel) {
+int or_residual(const or_mesh* m, const or_real* q, or_real* R, int64_t n_sel, const int64_t* sel) {
   int64_t ne = m->ne;
   /* elements whose residual is wanted */
   uint8_t* want = (uint8_t*)calloc(ne, 1);
@@ -1118,7 +1132,7 @@ int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, con
   W.m = m;
   W.q = q;
   W.geo = (geo_t*)calloc(ne, sizeof(geo_t));
-  W.G = (double**)calloc(ne, sizeof(double*));
+  W.G = (or_real**)calloc(ne, sizeof(or_real*));
   int64_t* list = (int64_t*)malloc(sizeof(int64_t) * ne);
   int64_t nl = 0;
   for (int64_t e = 0; e < ne; ++e)
@@ -1130,7 +1144,7 @@ int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, con
     int64_t e = list[i];
     if (!m->flag[e]) continue;
     int n = m->N[e] + 1;
-    W.G[e] = (double*)malloc(sizeof(double) * 9 * n * n * n);
+    W.G[e] = (or_real*)malloc(sizeof(or_real) * 9 * n * n * n);
     element_gradient(&W, e, W.G[e]);
   }
   int rc = 0;
@@ -1148,9 +1162,9 @@ int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, con
   return 0;
 }
 
-int or_rk_step(const or_mesh* m, double* q, double* g, double dt, int nsteps) {
+int or_rk_step(const or_mesh* m, or_real* q, or_real* g, or_real dt, int nsteps) {
   int64_t T4 = 4 * m->total;
-  double* R = (double*)malloc(sizeof(double) * T4);
+  or_real* R = (or_real*)malloc(sizeof(or_real) * T4);
   for (int st = 0; st < nsteps; ++st)
     for (int s = 0; s < 3; ++s) {
       if (or_residual(m, q, R, 0, NULL)) {
@@ -1166,17 +1180,17 @@ int or_rk_step(const or_mesh* m, double* q, double* g, double dt, int nsteps) {
   return 0;
 }
 
-int or_conservation(const or_mesh* m, const double* R, double out[4]) {
+int or_conservation(const or_mesh* m, const or_real* R, or_real out[4]) {
   int64_t ne = m->ne;
-  double* part = (double*)calloc(4 * ne, sizeof(double));
+  or_real* part = (or_real*)calloc(4 * ne, sizeof(or_real));
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t e = 0; e < ne; ++e) {
     geo_t gt;
     compute_geo(m, e, &gt);
     int N = m->N[e], n = N + 1;
-    const double* w = m->op[N].w;
+    const or_real* w = m->op[N].w;
     for (int v = 0; v < 4; ++v) {
-      double s = 0.0;
+      or_real s = 0.0;
       for (int k = 0; k < n; ++k)
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
@@ -1189,7 +1203,7 @@ int or_conservation(const or_mesh* m, const double* R, double out[4]) {
     free(gt.Ja);
   }
   for (int v = 0; v < 4; ++v) {
-    double s = 0.0;
+    or_real s = 0.0;
     for (int64_t e = 0; e < ne; ++e) s += part[v * ne + e];
     out[v] = s;
   }

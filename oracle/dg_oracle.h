@@ -25,59 +25,68 @@
 #define DG_ORACLE_H
 #include <stdint.h>
 
+/* Floating-point type of the oracle: FP64 by default. Built with -DOR_EXTENDED=1 it computes
+ * in long double (x87 80-bit on x86-64, IEEE binary128 on AArch64); that build only serves
+ * parity checks whose FP64 conditioning is too poor to verify an FP64 tolerance. */
+#if defined(OR_EXTENDED) && OR_EXTENDED
+typedef long double or_real;
+#else
+typedef double or_real;
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
 typedef struct {
-  double nu;        /* kinematic viscosity 1/Re                                  */
-  double c0sq;      /* artificial-compressibility wave speed squared             */
-  double cs;        /* Smagorinsky constant                                      */
-  double cv;        /* Vreman constant (paper: 0.07)                             */
+  or_real nu;        /* kinematic viscosity 1/Re                                  */
+  or_real c0sq;      /* artificial-compressibility wave speed squared             */
+  or_real cs;        /* Smagorinsky constant                                      */
+  or_real cv;        /* Vreman constant (paper: 0.07)                             */
   int closure;      /* 0 Smagorinsky, 1 Vreman                                   */
   int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                             */
-  double inflow[4]; /* ghost state used at inflow faces (velocity part)          */
+  or_real inflow[4]; /* ghost state used at inflow faces (velocity part)          */
 } or_params;
 
 typedef struct or_mesh or_mesh;
 
 /* 1D building blocks (Gauss-Lobatto-Legendre nodes on [-1,1]). */
-int or_lgl(int N, double* x, double* w);                  /* x[N+1], w[N+1]          */
-int or_dmat(int N, double* D);                            /* D[(N+1)*(N+1)] row-major */
-int or_interp_lgl(int Ns, int Nd, double* I);             /* I[(Nd+1)][(Ns+1)]        */
-int or_project_lgl(int Nh, int Nl, double* P);            /* P[(Nl+1)][(Nh+1)]        */
+int or_lgl(int N, or_real* x, or_real* w);                  /* x[N+1], w[N+1]          */
+int or_dmat(int N, or_real* D);                            /* D[(N+1)*(N+1)] row-major */
+int or_interp_lgl(int Ns, int Nd, or_real* I);             /* I[(Nd+1)][(Ns+1)]        */
+int or_project_lgl(int Nh, int Nl, or_real* P);            /* P[(Nl+1)][(Nh+1)]        */
 
 /* Pointwise building blocks. n_hat must be a unit vector. */
-void or_normal_flux(const double q[4], const double n_hat[3], double c0sq, double out[4]);
-void or_flux_jacobian(const double q[4], const double n_hat[3], double c0sq, double A[16]);
-int or_abs_jacobian(const double q[4], const double n_hat[3], double c0sq, double absA[16]);
-int or_riemann(const double qm[4], const double qp[4], const double n_hat[3],
-               const or_params* prm, double out[4]);
-double or_eddy_viscosity(const double G[9], double delta, const or_params* prm);
-double or_rk3_linear(double z);   /* amplification of one RK3 step on y' = lambda y, z = lambda dt */
+void or_normal_flux(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real out[4]);
+void or_flux_jacobian(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real A[16]);
+int or_abs_jacobian(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real absA[16]);
+int or_riemann(const or_real qm[4], const or_real qp[4], const or_real n_hat[3],
+               const or_params* prm, or_real out[4]);
+or_real or_eddy_viscosity(const or_real G[9], or_real delta, const or_params* prm);
+or_real or_rk3_linear(or_real z);   /* amplification of one RK3 step on y' = lambda y, z = lambda dt */
 
 /* Mesh + discretisation. Returns NULL on error (see or_error()). */
-or_mesh* or_create(int64_t n_elem, const int64_t* hex, int geom_degree, const double* geom_xyz,
+or_mesh* or_create(int64_t n_elem, const int64_t* hex, int geom_degree, const or_real* geom_xyz,
                    const int8_t* bc_tag, const int8_t* order, const uint8_t* flag,
                    const or_params* prm);
 void or_destroy(or_mesh* m);
 const char* or_error(void);
 int64_t or_total_nodes(const or_mesh* m);
 const int64_t* or_offsets(const or_mesh* m);
-int or_node_coords(const or_mesh* m, double* xyz);   /* [3][total_nodes] */
+int or_node_coords(const or_mesh* m, or_real* xyz);   /* [3][total_nodes] */
 /* Per-element multiplier on (nu + nu_t) in NS elements (test hook; default 1). */
-int or_set_visc_scale(or_mesh* m, const double* scale);
+int or_set_visc_scale(or_mesh* m, const or_real* scale);
 /* Element geometry: J[n^3], Ja[3][3][n^3] (Ja[i][c] = J dxi_i/dx_c). */
-int or_element_geometry(const or_mesh* m, int64_t e, double* J, double* Ja);
+int or_element_geometry(const or_mesh* m, int64_t e, or_real* J, or_real* Ja);
 /* BR1 velocity gradient of one NS element: G[3][3][n^3], G[c][k] = d u_c / d x_k. */
-int or_element_gradient(const or_mesh* m, const double* q, int64_t e, double* G);
+int or_element_gradient(const or_mesh* m, const or_real* q, int64_t e, or_real* G);
 /* Residual R = dq/dt. sel == NULL: every element; otherwise only the listed ones are
  * written (the other entries of R are left untouched). */
-int or_residual(const or_mesh* m, const double* q, double* R, int64_t n_sel, const int64_t* sel);
+int or_residual(const or_mesh* m, const or_real* q, or_real* R, int64_t n_sel, const int64_t* sel);
 /* nsteps low-storage RK3 steps in place on q, g. */
-int or_rk_step(const or_mesh* m, double* q, double* g, double dt, int nsteps);
+int or_rk_step(const or_mesh* m, or_real* q, or_real* g, or_real dt, int nsteps);
 /* out[v] = sum_e sum_nodes w_i w_j w_k J R_v. */
-int or_conservation(const or_mesh* m, const double* R, double out[4]);
+int or_conservation(const or_mesh* m, const or_real* R, or_real out[4]);
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);
 

@@ -20,58 +20,70 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "dg_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+LIB_PATH_EXT = os.path.join(BUILD_DIR, "liboracle_ext.so")
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP, -O2). Returns the library path."""
+    """Compile the oracle with gcc (OpenMP, -O2): the FP64 library and the extended-precision
+    one (long double; only for checks whose FP64 conditioning is too poor). Returns the FP64
+    library path."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    stale = (not os.path.exists(LIB_PATH)) or os.path.getmtime(LIB_PATH) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "dg_oracle.h")))
-    if force or stale:
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
-               "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB_PATH)
+    for path, extra in ((LIB_PATH, []), (LIB_PATH_EXT, ["-DOR_EXTENDED=1"])):
+        stale = (not os.path.exists(path)) or os.path.getmtime(path) < max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "dg_oracle.h")))
+        if force or stale:
+            tmp = path + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE", *extra,
+                   "-o", tmp, SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, path)
     return LIB_PATH
 
 
-class Params(ctypes.Structure):
-    _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
-                ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("inflow", ctypes.c_double * 4)]
-
-
 _P = ctypes.POINTER
-_d = _P(ctypes.c_double)
 _i64 = _P(ctypes.c_int64)
 _i8 = _P(ctypes.c_int8)
 _u8 = _P(ctypes.c_uint8)
 
 
-def lib():
-    global _lib
+def _params_type(real):
+    class P(ctypes.Structure):
+        _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
+                    ("riemann", ctypes.c_int), ("inflow", real * 4)]
+    return P
+
+
+Params = _params_type(ctypes.c_double)
+ParamsExt = _params_type(ctypes.c_longdouble)
+_d = _P(ctypes.c_double)
+
+
+def lib(extended: bool = False):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if extended not in _libs:
+            build()
+            real = ctypes.c_longdouble if extended else ctypes.c_double
+            Pt = ParamsExt if extended else Params
+            _d = _P(real)
+            L = ctypes.CDLL(LIB_PATH_EXT if extended else LIB_PATH)
             L.or_lgl.argtypes = [ctypes.c_int, _d, _d]
             L.or_dmat.argtypes = [ctypes.c_int, _d]
             L.or_interp_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
-            L.or_normal_flux.argtypes = [_d, _d, ctypes.c_double, _d]
+            L.or_normal_flux.argtypes = [_d, _d, real, _d]
             L.or_normal_flux.restype = None
-            L.or_flux_jacobian.argtypes = [_d, _d, ctypes.c_double, _d]
+            L.or_flux_jacobian.argtypes = [_d, _d, real, _d]
             L.or_flux_jacobian.restype = None
-            L.or_abs_jacobian.argtypes = [_d, _d, ctypes.c_double, _d]
-            L.or_riemann.argtypes = [_d, _d, _d, _P(Params), _d]
-            L.or_eddy_viscosity.argtypes = [_d, ctypes.c_double, _P(Params)]
-            L.or_eddy_viscosity.restype = ctypes.c_double
-            L.or_rk3_linear.argtypes = [ctypes.c_double]
-            L.or_rk3_linear.restype = ctypes.c_double
-            L.or_create.argtypes = [ctypes.c_int64, _i64, ctypes.c_int, _d, _i8, _i8, _u8, _P(Params)]
+            L.or_abs_jacobian.argtypes = [_d, _d, real, _d]
+            L.or_riemann.argtypes = [_d, _d, _d, _P(Pt), _d]
+            L.or_eddy_viscosity.argtypes = [_d, real, _P(Pt)]
+            L.or_eddy_viscosity.restype = real
+            L.or_rk3_linear.argtypes = [real]
+            L.or_rk3_linear.restype = real
+            L.or_create.argtypes = [ctypes.c_int64, _i64, ctypes.c_int, _d, _i8, _i8, _u8, _P(Pt)]
             L.or_create.restype = ctypes.c_void_p
             L.or_destroy.argtypes = [ctypes.c_void_p]
             L.or_destroy.restype = None
@@ -85,11 +97,11 @@ def lib():
             L.or_element_geometry.argtypes = [ctypes.c_void_p, ctypes.c_int64, _d, _d]
             L.or_element_gradient.argtypes = [ctypes.c_void_p, _d, ctypes.c_int64, _d]
             L.or_residual.argtypes = [ctypes.c_void_p, _d, _d, ctypes.c_int64, _i64]
-            L.or_rk_step.argtypes = [ctypes.c_void_p, _d, _d, ctypes.c_double, ctypes.c_int]
+            L.or_rk_step.argtypes = [ctypes.c_void_p, _d, _d, real, ctypes.c_int]
             L.or_conservation.argtypes = [ctypes.c_void_p, _d, _d]
             L.or_num_threads.restype = ctypes.c_int
-            _lib = L
-    return _lib
+            _libs[extended] = L
+    return _libs[extended]
 
 
 def _ptr(a, t):
@@ -184,20 +196,36 @@ def num_threads():
 # ---- mesh ----------------------------------------------------------------------------
 
 class Mesh:
-    """FP64 oracle discretisation of one mesh (orders, flags and parameters fixed)."""
+    """Oracle discretisation of one mesh (orders, flags and parameters fixed).
 
-    def __init__(self, hex, geom_xyz, geom_degree, orders, flags, prm, bc_tag=None):
-        L = lib()
+    extended=True evaluates in long double (inputs are widened, results rounded to FP64);
+    the default is the FP64 oracle."""
+
+    def __init__(self, hex, geom_xyz, geom_degree, orders, flags, prm, bc_tag=None, extended=False):
+        self.extended = bool(extended)
+        L = self._L = lib(self.extended)
+        self._real = np.longdouble if self.extended else np.float64
+        self._ptr_t = _P(ctypes.c_longdouble if self.extended else ctypes.c_double)
+        if self.extended:
+            p2 = ParamsExt()
+            for name, _ in Params._fields_:
+                v = getattr(prm, name)
+                if name == "inflow":
+                    for i in range(4):
+                        p2.inflow[i] = v[i]
+                else:
+                    setattr(p2, name, v)
+            prm = p2
         self.hex = np.ascontiguousarray(hex, dtype=np.int64)
         self.ne = self.hex.shape[0]
-        gx = _f64(geom_xyz)
+        gx = self._r(geom_xyz)
         orders = np.ascontiguousarray(orders, dtype=np.int8)
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
         bc = None if bc_tag is None else np.ascontiguousarray(bc_tag, dtype=np.int8)
         self.prm = prm
         self.orders = orders.copy()
         self.flags = flags.copy()
-        h = L.or_create(self.ne, _ptr(self.hex, _i64), geom_degree, _ptr(gx, _d),
+        h = L.or_create(self.ne, _ptr(self.hex, _i64), geom_degree, _ptr(gx, self._ptr_t),
                         None if bc is None else _ptr(bc, _i8), _ptr(orders, _i8), _ptr(flags, _u8),
                         ctypes.byref(prm))
         if not h:
@@ -210,55 +238,70 @@ class Mesh:
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().or_destroy(h)
+            self._L.or_destroy(h)
             self.h = None
 
+    def _r(self, a):
+        return np.ascontiguousarray(a, dtype=self._real)
+
     def node_coords(self):
-        xyz = np.zeros((3, self.total))
-        lib().or_node_coords(self.h, _ptr(xyz, _d))
-        return xyz
+        xyz = np.zeros((3, self.total), dtype=self._real)
+        self._L.or_node_coords(self.h, _ptr(xyz, self._ptr_t))
+        return xyz.astype(np.float64)
 
     def set_visc_scale(self, scale):
-        s = None if scale is None else _f64(scale)
-        lib().or_set_visc_scale(self.h, None if s is None else _ptr(s, _d))
+        s = None if scale is None else self._r(scale)
+        self._L.or_set_visc_scale(self.h, None if s is None else _ptr(s, self._ptr_t))
 
     def element_geometry(self, e):
         n = int(self.orders[e]) + 1
-        J = np.zeros(n ** 3)
-        Ja = np.zeros((3, 3, n ** 3))
-        lib().or_element_geometry(self.h, e, _ptr(J, _d), _ptr(Ja, _d))
-        return J, Ja
+        J = np.zeros(n ** 3, dtype=self._real)
+        Ja = np.zeros((3, 3, n ** 3), dtype=self._real)
+        self._L.or_element_geometry(self.h, e, _ptr(J, self._ptr_t), _ptr(Ja, self._ptr_t))
+        return J.astype(np.float64), Ja.astype(np.float64)
 
     def element_gradient(self, q, e):
         n = int(self.orders[e]) + 1
-        G = np.zeros((3, 3, n ** 3))
-        q = _f64(q)
-        lib().or_element_gradient(self.h, _ptr(q, _d), e, _ptr(G, _d))
-        return G
+        G = np.zeros((3, 3, n ** 3), dtype=self._real)
+        q = self._r(q)
+        self._L.or_element_gradient(self.h, _ptr(q, self._ptr_t), e, _ptr(G, self._ptr_t))
+        return G.astype(np.float64)
 
     def residual(self, q, sel=None, out=None):
-        q = _f64(q)
+        q = self._r(q)
         assert q.shape == (4, self.total)
-        R = np.zeros((4, self.total)) if out is None else out
+        R = np.zeros((4, self.total), dtype=self._real)
         if sel is None:
-            rc = lib().or_residual(self.h, _ptr(q, _d), _ptr(R, _d), 0, None)
+            rc = self._L.or_residual(self.h, _ptr(q, self._ptr_t), _ptr(R, self._ptr_t), 0, None)
         else:
             s = np.ascontiguousarray(sel, dtype=np.int64)
-            rc = lib().or_residual(self.h, _ptr(q, _d), _ptr(R, _d), s.size, _ptr(s, _i64))
+            rc = self._L.or_residual(self.h, _ptr(q, self._ptr_t), _ptr(R, self._ptr_t), s.size, _ptr(s, _i64))
         if rc:
-            raise RuntimeError(lib().or_error().decode())
-        return R
+            raise RuntimeError(self._L.or_error().decode())
+        if out is None:
+            return R.astype(np.float64)
+        if sel is None:
+            out[...] = R
+        else:
+            idx = np.concatenate([np.arange(self.offsets[e], self.offsets[e + 1]) for e in np.asarray(sel)])
+            out[:, idx] = R[:, idx]
+        return out
 
     def rk_step(self, q, g, dt, nsteps=1):
+        """In place on FP64 arrays q, g (the extended oracle works on widened copies)."""
         assert q.dtype == np.float64 and g.dtype == np.float64 and q.flags.c_contiguous and g.flags.c_contiguous
-        if lib().or_rk_step(self.h, _ptr(q, _d), _ptr(g, _d), dt, nsteps):
-            raise RuntimeError(lib().or_error().decode())
+        qr, gr = self._r(q), self._r(g)
+        if self._L.or_rk_step(self.h, _ptr(qr, self._ptr_t), _ptr(gr, self._ptr_t), dt, nsteps):
+            raise RuntimeError(self._L.or_error().decode())
+        if self.extended:
+            q[...] = qr
+            g[...] = gr
 
     def conservation(self, R):
-        out = np.zeros(4)
-        R = _f64(R)
-        lib().or_conservation(self.h, _ptr(R, _d), _ptr(out, _d))
-        return out
+        out = np.zeros(4, dtype=self._real)
+        R = self._r(R)
+        self._L.or_conservation(self.h, _ptr(R, self._ptr_t), _ptr(out, self._ptr_t))
+        return out.astype(np.float64)
 
     def element_nodes(self, e):
         return slice(int(self.offsets[e]), int(self.offsets[e + 1]))

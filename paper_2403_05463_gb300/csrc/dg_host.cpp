@@ -1,0 +1,1119 @@
+// dg_host.cpp -- host side of the C ABI (include/dg.h): mesh ingestion, face matching and
+// orientation, geometry (curl-form metrics), per-order buckets, device buffers, launch
+// sequencing and CUDA-graph capture of the Runge-Kutta step.
+#include "../../include/dg.h"
+#include "dg_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace dgk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dg_status fail(dg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e__ = (call);                                                           \
+    if (e__ != cudaSuccess)                                                             \
+      return fail(e__ == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e__));                                      \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// 1D Gauss-Lobatto operators. Interior nodes: zeros of P_N', found by Newton iteration with
+// P_N'' from Legendre's equation (1-x^2) P'' = 2x P' - N(N+1) P. D by the closed form for
+// Lobatto points (Canuto et al. 2006, Sec. 2.3), interpolation in barycentric form and the
+// L2 projection by truncating the Legendre expansion.
+// ---------------------------------------------------------------------------------------
+void legendre_and_derivative(int N, double x, double& P, double& dP) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (N == 0) { P = 1.0; dP = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    double d2 = d0 + (2 * k + 1) * p1;  // P'_{k+1} = P'_{k-1} + (2k+1) P_k
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  P = p1;
+  dP = d1;
+}
+
+struct Rule {
+  int N;
+  std::vector<double> x, w, D;  // D row-major n x n
+};
+
+Rule make_rule(int N) {
+  Rule r;
+  r.N = N;
+  const int n = N + 1;
+  r.x.assign(n, 0.0);
+  r.w.assign(n, 0.0);
+  r.x[0] = -1.0;
+  r.x[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double x = -std::cos(M_PI * j / N);  // Chebyshev-Lobatto starting guess
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_and_derivative(N, x, P, dP);
+      double d2P = (2.0 * x * dP - N * (N + 1.0) * P) / (1.0 - x * x);
+      double dx = dP / d2P;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    r.x[j] = x;
+  }
+  for (int j = 0; j <= N / 2; ++j) {  // symmetrise
+    double m = 0.5 * (r.x[N - j] - r.x[j]);
+    r.x[j] = -m;
+    r.x[N - j] = m;
+  }
+  if (N % 2 == 0) r.x[N / 2] = 0.0;
+  std::vector<double> PN(n);
+  for (int j = 0; j < n; ++j) {
+    double P, dP;
+    legendre_and_derivative(N, r.x[j], P, dP);
+    PN[j] = P;
+    r.w[j] = 2.0 / (N * (N + 1.0) * P * P);
+  }
+  r.D.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (i != j) r.D[i * n + j] = PN[i] / (PN[j] * (r.x[i] - r.x[j]));
+    }
+  r.D[0] = -N * (N + 1.0) / 4.0;
+  r.D[N * n + N] = N * (N + 1.0) / 4.0;
+  return r;
+}
+
+// barycentric Lagrange interpolation matrix from nodes xs to points xd: I[i][j]
+std::vector<double> interp_matrix(const std::vector<double>& xs, const std::vector<double>& xd) {
+  const int ns = (int)xs.size(), nd = (int)xd.size();
+  std::vector<double> lam(ns, 1.0), I(nd * ns, 0.0);
+  for (int j = 0; j < ns; ++j)
+    for (int k = 0; k < ns; ++k)
+      if (k != j) lam[j] /= (xs[j] - xs[k]);
+  for (int i = 0; i < nd; ++i) {
+    int hit = -1;
+    for (int j = 0; j < ns; ++j)
+      if (xd[i] == xs[j]) hit = j;
+    if (hit >= 0) {
+      I[i * ns + hit] = 1.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int j = 0; j < ns; ++j) den += lam[j] / (xd[i] - xs[j]);
+    for (int j = 0; j < ns; ++j) I[i * ns + j] = lam[j] / (xd[i] - xs[j]) / den;
+  }
+  return I;
+}
+
+// L2 projection of a degree-Nh polynomial (values at its Lobatto nodes) onto degree Nl:
+// Legendre coefficients by the Nh-point Lobatto quadrature (exact for the modes kept,
+// degree k + Nh <= 2 Nh - 1 for k < Nh), truncation, evaluation at the Nl nodes.
+std::vector<double> projection_matrix(const Rule& hi, const Rule& lo) {
+  const int nh = hi.N + 1, nl = lo.N + 1;
+  std::vector<double> P(nl * nh, 0.0);
+  if (hi.N == lo.N) {
+    for (int i = 0; i < nl; ++i) P[i * nh + i] = 1.0;
+    return P;
+  }
+  auto leg = [](int k, double x) {
+    double P, dP;
+    legendre_and_derivative(k, x, P, dP);
+    return P;
+  };
+  for (int i = 0; i < nl; ++i)
+    for (int j = 0; j < nh; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= lo.N; ++k) s += (k + 0.5) * leg(k, hi.x[j]) * leg(k, lo.x[i]);
+      P[i * nh + j] = s * hi.w[j];
+    }
+  return P;
+}
+
+struct OpTables {
+  Rule rule[NP];
+  std::vector<double> interp, proj;  // [(a*NP+b)*NP*NP + i*NP + j]
+  OpTables() {
+    for (int N = 1; N <= MAXN; ++N) rule[N] = make_rule(N);
+    interp.assign(NP * NP * NP * NP, 0.0);
+    proj.assign(NP * NP * NP * NP, 0.0);
+    for (int a = 1; a <= MAXN; ++a)
+      for (int b = 1; b <= MAXN; ++b) {
+        auto I = interp_matrix(rule[a].x, rule[b].x);
+        for (int i = 0; i <= b; ++i)
+          for (int j = 0; j <= a; ++j) interp[(a * NP + b) * NP * NP + i * NP + j] = I[i * (a + 1) + j];
+        if (b <= a) {
+          auto P = projection_matrix(rule[a], rule[b]);
+          for (int i = 0; i <= b; ++i)
+            for (int j = 0; j <= a; ++j) proj[(a * NP + b) * NP * NP + i * NP + j] = P[i * (a + 1) + j];
+        }
+      }
+  }
+};
+
+const OpTables& ops() {
+  static OpTables t;
+  return t;
+}
+
+// face f = 2d+s: tangential directions and hexahedron corner of face corner (ca, cb)
+void tangents(int d, int& t0, int& t1) {
+  t0 = d == 0 ? 1 : 0;
+  t1 = d == 2 ? 1 : 2;
+}
+int face_corner_index(int f, int ca, int cb) {
+  int d = f >> 1, t0, t1, c[3];
+  tangents(d, t0, t1);
+  c[d] = f & 1;
+  c[t0] = ca;
+  c[t1] = cb;
+  return c[0] + 2 * c[1] + 4 * c[2];
+}
+void orient_fwd(int o, int M, int a1, int b1, int& a0, int& b0) {
+  int x = (o & 1) ? b1 : a1, y = (o & 1) ? a1 : b1;
+  a0 = (o & 2) ? M - x : x;
+  b0 = (o & 4) ? M - y : y;
+}
+
+struct Key4 {
+  int64_t k[4];
+  bool operator==(const Key4& o) const { return std::memcmp(k, o.k, sizeof k) == 0; }
+};
+struct Key4Hash {
+  size_t operator()(const Key4& a) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < 4; ++i) {
+      h ^= (uint64_t)a.k[i] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  const double* q = nullptr;
+  const double* g = nullptr;
+  double dt = 0.0;
+  uint64_t version = 0;
+};
+
+struct dg_ctx {
+  int device = 0;
+  int64_t ne = 0;
+  int gdeg = 1;
+  std::vector<int64_t> hex;
+  std::vector<double> gnodes;   // [E][(g+1)^3][3]
+  std::vector<int8_t> bc;       // [E][6]
+  dg_params prm{};
+  std::vector<int8_t> order;
+  std::vector<uint8_t> flag;
+  std::vector<int64_t> off, troff;
+  int64_t total = 0, tr_total = 0;
+  // topology (order independent)
+  std::vector<int32_t> nb;      // [E*6] neighbour or -1
+  std::vector<uint8_t> nbf, nbo;
+  // device
+  std::map<std::string, DevBuf> buf;
+  DevMesh M{};
+  std::vector<Bucket> all_buckets;  // per (N, curved): every element
+  std::vector<Bucket> ns_buckets;   // per (N, curved): NS elements
+  std::vector<Bucket> ord_buckets;  // per N (traces, coordinates, sums)
+  int32_t* mortar_all = nullptr;    // device slots e*6+f of every mortar face
+  int n_mortar_all = 0;
+  int32_t* mortar_ns = nullptr;     // mortar slots of NS elements (lifting)
+  int n_mortar_ns = 0;
+  std::vector<ElemConst> ec;
+  bool any_curved = false;
+  cudaStream_t cap_stream = nullptr;
+  GraphCache graph;
+  uint64_t version = 1;
+  int launches_residual = 0, launches_step = 0;
+  // host-variant staging
+  double* stage_q = nullptr;
+  double* stage_r = nullptr;
+  double* partial = nullptr;
+  std::vector<double> partial_host;
+};
+
+namespace {
+
+void free_buf(dg_ctx* c, const std::string& name) {
+  auto it = c->buf.find(name);
+  if (it != c->buf.end()) {
+    cudaFree(it->second.p);
+    c->buf.erase(it);
+  }
+}
+
+template <typename T>
+dg_status dev_alloc(dg_ctx* c, const std::string& name, size_t count, T** out) {
+  free_buf(c, name);
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(DG_ERR_OOM, "cudaMalloc(%s, %zu bytes): %s", name.c_str(), bytes, cudaGetErrorString(e));
+  c->buf[name] = DevBuf{p, bytes};
+  *out = (T*)p;
+  return DG_OK;
+}
+
+template <typename T>
+dg_status dev_upload(dg_ctx* c, const std::string& name, const std::vector<T>& v, T** out) {
+  dg_status st = dev_alloc(c, name, v.size(), out);
+  if (st != DG_OK) return st;
+  if (!v.empty()) CU(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+dg_status check_params(const dg_params* p) {
+  if (!p) return fail(DG_ERR_ARG, "params is NULL");
+  if (!(p->c0sq > 0.0) || !(p->nu >= 0.0) || !(p->cs >= 0.0) || !(p->cv >= 0.0))
+    return fail(DG_ERR_ARG, "need c0sq > 0 and nu, cs, cv >= 0");
+  if (p->closure < 0 || p->closure > 1) return fail(DG_ERR_ARG, "closure must be 0 or 1");
+  if (p->riemann < 0 || p->riemann > 1) return fail(DG_ERR_ARG, "riemann must be 0 or 1");
+  if (p->precision < 0 || p->precision > 1) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
+  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
+  return DG_OK;
+}
+
+void apply_params(dg_ctx* c) {
+  c->M.nu = c->prm.nu;
+  c->M.c0sq = c->prm.c0sq;
+  c->M.cs = c->prm.cs;
+  c->M.cv = c->prm.cv;
+  c->M.closure = c->prm.closure;
+  c->M.riemann = c->prm.riemann;
+  for (int i = 0; i < 4; ++i) c->M.inflow[i] = c->prm.inflow[i];
+  c->version++;
+}
+
+// Geometry of element e at order N. Affine (parallelepiped) elements: Ja^d = a_{d+1} x a_{d+2}
+// with a_d = dX/dxi_d (constant). Otherwise the curl form of the metric identities
+// (Kopriva 2006) at the geometry degree g, interpolated to the element's nodes.
+struct ElemGeo {
+  bool affine;
+  double Ja[9], J;                  // affine
+  std::vector<double> Jan, Jn;      // curved: [9][n3], [n3]
+};
+
+bool is_affine(const dg_ctx* c, int64_t e, double a[3][3], double x0[3]) {
+  const int g = c->gdeg, ng = g + 1, ng3 = ng * ng * ng;
+  const double* X = &c->gnodes[(size_t)e * ng3 * 3];
+  auto node = [&](int i, int j, int k) { return X + 3 * (i + ng * (j + ng * k)); };
+  const double* p0 = node(0, 0, 0);
+  const double* px = node(g, 0, 0);
+  const double* py = node(0, g, 0);
+  const double* pz = node(0, 0, g);
+  double scale = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    x0[k] = p0[k];
+    a[0][k] = 0.5 * (px[k] - p0[k]);
+    a[1][k] = 0.5 * (py[k] - p0[k]);
+    a[2][k] = 0.5 * (pz[k] - p0[k]);
+    scale = std::max({scale, std::fabs(a[0][k]), std::fabs(a[1][k]), std::fabs(a[2][k])});
+  }
+  const std::vector<double>& t = ops().rule[std::max(g, 1)].x;  // reference points of degree g
+  for (int kk = 0; kk < ng; ++kk)
+    for (int jj = 0; jj < ng; ++jj)
+      for (int ii = 0; ii < ng; ++ii) {
+        const double* p = node(ii, jj, kk);
+        for (int k = 0; k < 3; ++k) {
+          double ref = x0[k] + (t[ii] + 1.0) * a[0][k] + (t[jj] + 1.0) * a[1][k] + (t[kk] + 1.0) * a[2][k];
+          if (std::fabs(p[k] - ref) > 1e-13 * scale) return false;
+        }
+      }
+  return true;
+}
+
+void cross(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void elem_geometry(const dg_ctx* c, int64_t e, int N, ElemGeo& G) {
+  double a[3][3], x0[3];
+  const int g = c->gdeg, ng = g + 1, ng3 = ng * ng * ng;
+  if (is_affine(c, e, a, x0)) {
+    G.affine = true;
+    double t[3];
+    cross(a[1], a[2], t);
+    for (int k = 0; k < 3; ++k) G.Ja[0 * 3 + k] = t[k];
+    cross(a[2], a[0], t);
+    for (int k = 0; k < 3; ++k) G.Ja[1 * 3 + k] = t[k];
+    cross(a[0], a[1], t);
+    for (int k = 0; k < 3; ++k) G.Ja[2 * 3 + k] = t[k];
+    G.J = a[0][0] * G.Ja[0] + a[0][1] * G.Ja[1] + a[0][2] * G.Ja[2];
+    return;
+  }
+  G.affine = false;
+  const Rule& rg = ops().rule[g];
+  const Rule& rn = ops().rule[N];
+  const int n = N + 1, n3 = n * n * n;
+  const double* X = &c->gnodes[(size_t)e * ng3 * 3];
+  // derivative along direction d on the ng^3 grid
+  auto deriv = [&](const std::vector<double>& u, int d) {
+    std::vector<double> out(ng3, 0.0);
+    for (int k = 0; k < ng; ++k)
+      for (int j = 0; j < ng; ++j)
+        for (int i = 0; i < ng; ++i) {
+          int idx[3] = {i, j, k};
+          double acc = 0.0;
+          for (int m = 0; m < ng; ++m) {
+            int q[3] = {i, j, k};
+            q[d] = m;
+            acc += rg.D[idx[d] * ng + m] * u[q[0] + ng * (q[1] + ng * q[2])];
+          }
+          out[i + ng * (j + ng * k)] = acc;
+        }
+    return out;
+  };
+  std::vector<double> I = interp_matrix(rg.x, rn.x);  // n x ng
+  auto to_nodes = [&](const std::vector<double>& u) {
+    // separable interpolation, one direction at a time
+    std::vector<double> t1(n * ng * ng), t2(n * n * ng), out(n3);
+    for (int k = 0; k < ng; ++k)
+      for (int j = 0; j < ng; ++j)
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int m = 0; m < ng; ++m) s += I[i * ng + m] * u[m + ng * (j + ng * k)];
+          t1[i + n * (j + ng * k)] = s;
+        }
+    for (int k = 0; k < ng; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int m = 0; m < ng; ++m) s += I[j * ng + m] * t1[i + n * (m + ng * k)];
+          t2[i + n * (j + n * k)] = s;
+        }
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int m = 0; m < ng; ++m) s += I[k * ng + m] * t2[i + n * (j + n * m)];
+          out[i + n * (j + n * k)] = s;
+        }
+    return out;
+  };
+  std::vector<double> Xc[3];
+  for (int k = 0; k < 3; ++k) {
+    Xc[k].resize(ng3);
+    for (int p = 0; p < ng3; ++p) Xc[k][p] = X[3 * p + k];
+  }
+  std::vector<double> dX[3][3];  // dX[k][d] = d X_k / d xi_d
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) dX[k][d] = deriv(Xc[k], d);
+  // J at the nodes
+  std::vector<double> dXn[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) dXn[k][d] = to_nodes(dX[k][d]);
+  G.Jn.assign(n3, 0.0);
+  for (int p = 0; p < n3; ++p) {
+    double m[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) m[k][d] = dXn[k][d][p];
+    G.Jn[p] = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+              m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  }
+  // curl form: Ja^i_k = -(curl_xi v^k)_i with v^k_d = X_l dX_m/dxi_d, (k, m, l) cyclic
+  G.Jan.assign(9 * n3, 0.0);
+  for (int k = 0; k < 3; ++k) {
+    const int m = (k + 1) % 3, l = (k + 2) % 3;
+    std::vector<double> v[3];
+    for (int d = 0; d < 3; ++d) {
+      v[d].resize(ng3);
+      for (int p = 0; p < ng3; ++p) v[d][p] = Xc[l][p] * dX[m][d][p];
+    }
+    // (curl v)_0 = d1 v2 - d2 v1, (curl v)_1 = d2 v0 - d0 v2, (curl v)_2 = d0 v1 - d1 v0
+    for (int i = 0; i < 3; ++i) {
+      const int j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+      std::vector<double> a1 = deriv(v[j2], j1), a2 = deriv(v[j1], j2), w(ng3);
+      for (int p = 0; p < ng3; ++p) w[p] = -(a1[p] - a2[p]);
+      std::vector<double> wn = to_nodes(w);
+      for (int p = 0; p < n3; ++p) G.Jan[(i * 3 + k) * n3 + p] = wn[p];
+    }
+  }
+}
+
+void destroy_graph(dg_ctx* c) {
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  c->graph = GraphCache{};
+}
+
+void build_buckets(const std::vector<int32_t>& elems, const std::vector<int8_t>& order,
+                   const std::vector<ElemConst>& ec, bool split_curved,
+                   std::vector<std::vector<int32_t>>& lists, std::vector<std::pair<int, bool>>& keys) {
+  std::map<std::pair<int, bool>, std::vector<int32_t>> m;
+  for (int32_t e : elems) m[{order[e], split_curved && ec[e].curved != 0.0}].push_back(e);
+  lists.clear();
+  keys.clear();
+  for (auto& kv : m) {
+    keys.push_back(kv.first);
+    lists.push_back(kv.second);
+  }
+}
+
+dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector<int32_t>& elems, bool split_curved,
+                         bool ns, std::vector<Bucket>& out) {
+  std::vector<std::vector<int32_t>> lists;
+  std::vector<std::pair<int, bool>> keys;
+  build_buckets(elems, c->order, c->ec, split_curved, lists, keys);
+  out.clear();
+  for (size_t i = 0; i < lists.size(); ++i) {
+    Bucket b;
+    b.N = keys[i].first;
+    b.curved = keys[i].second;
+    b.ns = ns;
+    b.count = (int)lists[i].size();
+    dg_status st = dev_upload(c, prefix + std::to_string(i), lists[i], &b.list);
+    if (st != DG_OK) return st;
+    out.push_back(b);
+  }
+  return DG_OK;
+}
+
+// flag-dependent tables: links' neighbour flags, NS buckets, mortar lifting slots
+dg_status rebuild_flags(dg_ctx* c) {
+  std::vector<FaceLink> link(c->ne * 6);
+  std::vector<int32_t> mall, mns, ns_elems;
+  for (int64_t e = 0; e < c->ne; ++e) {
+    if (c->flag[e]) ns_elems.push_back((int32_t)e);
+    for (int f = 0; f < 6; ++f) {
+      FaceLink L{};
+      int32_t nb = c->nb[e * 6 + f];
+      L.nbr = nb;
+      if (nb >= 0) {
+        L.nface = c->nbf[e * 6 + f];
+        L.orient = c->nbo[e * 6 + f];
+        L.kind = c->order[nb] == c->order[e] ? FK_CONF : FK_MORTAR;
+        L.nflag = c->flag[nb];
+        if (L.kind == FK_MORTAR) {
+          mall.push_back((int32_t)(e * 6 + f));
+          if (c->flag[e]) mns.push_back((int32_t)(e * 6 + f));
+        }
+      } else {
+        L.nbr = -1;
+        L.kind = c->bc[e * 6 + f] == 1 ? FK_INFLOW : FK_OUTFLOW;
+      }
+      link[e * 6 + f] = L;
+    }
+  }
+  FaceLink* dl;
+  dg_status st = dev_upload(c, "link", link, &dl);
+  if (st != DG_OK) return st;
+  c->M.link = dl;
+  uint8_t* df;
+  if ((st = dev_upload(c, "flag", c->flag, &df)) != DG_OK) return st;
+  c->M.flag = df;
+  if ((st = dev_upload(c, "mortar_all", mall, &c->mortar_all)) != DG_OK) return st;
+  c->n_mortar_all = (int)mall.size();
+  if ((st = dev_upload(c, "mortar_ns", mns, &c->mortar_ns)) != DG_OK) return st;
+  c->n_mortar_ns = (int)mns.size();
+  for (auto it = c->buf.begin(); it != c->buf.end();) {
+    if (it->first.rfind("nsb", 0) == 0) {
+      cudaFree(it->second.p);
+      it = c->buf.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  if ((st = upload_buckets(c, "nsb", ns_elems, true, true, c->ns_buckets)) != DG_OK) return st;
+  // viscous traces of Euler elements are never written: keep them at zero
+  if (c->M.Tv) CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
+  c->version++;
+  destroy_graph(c);
+  return DG_OK;
+}
+
+// order-dependent layout, geometry, buffers
+dg_status rebuild_orders(dg_ctx* c) {
+  const int64_t E = c->ne;
+  c->off.assign(E + 1, 0);
+  c->troff.assign(E + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int n = c->order[e] + 1;
+    c->off[e + 1] = c->off[e] + (int64_t)n * n * n;
+    c->troff[e + 1] = c->troff[e] + 6LL * n * n;
+  }
+  c->total = c->off[E];
+  c->tr_total = c->troff[E];
+  if (c->total * 4 > INT64_C(1) << 40) return fail(DG_ERR_UNSUPPORTED, "mesh too large");
+  // geometry
+  c->ec.assign(E, ElemConst{});
+  std::vector<double> geo;
+  c->any_curved = false;
+  std::vector<ElemGeo> curved_geo;
+  std::vector<int64_t> curved_ids;
+  for (int64_t e = 0; e < E; ++e) {
+    ElemGeo G;
+    const int N = c->order[e], n = N + 1, n3 = n * n * n;
+    elem_geometry(c, e, N, G);
+    ElemConst& k = c->ec[e];
+    const Rule& r = ops().rule[N];
+    double vol = 0.0;
+    if (G.affine) {
+      if (!(G.J > 0.0)) return fail(DG_ERR_MESH, "element %lld has a non-positive Jacobian", (long long)e);
+      for (int i = 0; i < 9; ++i) k.Ja[i] = G.Ja[i];
+      k.J = G.J;
+      k.invJ = 1.0 / G.J;
+      k.curved = 0.0;
+      vol = 8.0 * G.J;
+    } else {
+      for (int p = 0; p < n3; ++p) {
+        if (!(G.Jn[p] > 0.0)) return fail(DG_ERR_MESH, "element %lld has a non-positive Jacobian", (long long)e);
+        vol += r.w[p % n] * r.w[(p / n) % n] * r.w[p / (n * n)] * G.Jn[p];
+      }
+      k.curved = 1.0;
+      c->any_curved = true;
+      curved_ids.push_back(e);
+      curved_geo.push_back(std::move(G));
+    }
+    k.delta = std::cbrt(vol) / n;
+  }
+  if (c->any_curved) {
+    geo.assign((size_t)10 * c->total, 0.0);
+    for (size_t i = 0; i < curved_ids.size(); ++i) {
+      const int64_t e = curved_ids[i];
+      const int n = c->order[e] + 1, n3 = n * n * n;
+      const ElemGeo& G = curved_geo[i];
+      for (int k = 0; k < 9; ++k)
+        for (int p = 0; p < n3; ++p) geo[(size_t)k * c->total + c->off[e] + p] = G.Jan[k * n3 + p];
+      for (int p = 0; p < n3; ++p) geo[(size_t)9 * c->total + c->off[e] + p] = G.Jn[p];
+    }
+  }
+  dg_status st;
+  int64_t* d64;
+  if ((st = dev_upload(c, "elem_off", c->off, &d64)) != DG_OK) return st;
+  c->M.elem_off = d64;
+  if ((st = dev_upload(c, "tr_off", c->troff, &d64)) != DG_OK) return st;
+  c->M.tr_off = d64;
+  int8_t* d8;
+  if ((st = dev_upload(c, "order", c->order, &d8)) != DG_OK) return st;
+  c->M.order = d8;
+  ElemConst* dec;
+  if ((st = dev_upload(c, "ec", c->ec, &dec)) != DG_OK) return st;
+  c->M.ec = dec;
+  double* dgeo = nullptr;
+  if (c->any_curved) {
+    if ((st = dev_upload(c, "geo", geo, &dgeo)) != DG_OK) return st;
+  } else {
+    free_buf(c, "geo");
+  }
+  c->M.geo = dgeo;
+  c->M.n_elem = E;
+  c->M.total = c->total;
+  c->M.tr_total = c->tr_total;
+  if ((st = dev_alloc(c, "Tq", 4 * c->tr_total, &c->M.Tq)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "Tv", 3 * c->tr_total, &c->M.Tv)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "rv", 3 * c->total, &c->M.rv)) != DG_OK) return st;
+  bool has_mortar = false;
+  for (int64_t s = 0; s < E * 6 && !has_mortar; ++s)
+    has_mortar = c->nb[s] >= 0 && c->order[c->nb[s]] != c->order[s / 6];
+  const int64_t mort = has_mortar ? c->tr_total : 0;
+  if ((st = dev_alloc(c, "LU", 9 * mort, &c->M.LU)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "LH", 4 * mort, &c->M.LH)) != DG_OK) return st;
+  CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
+  if ((st = dev_alloc(c, "partial", 4 * E, &c->partial)) != DG_OK) return st;
+  c->partial_host.assign(4 * E, 0.0);
+  free_buf(c, "stage_q");
+  free_buf(c, "stage_r");
+  c->stage_q = c->stage_r = nullptr;
+  // buckets over all elements
+  for (auto it = c->buf.begin(); it != c->buf.end();) {
+    if (it->first.rfind("allb", 0) == 0 || it->first.rfind("ordb", 0) == 0) {
+      cudaFree(it->second.p);
+      it = c->buf.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  std::vector<int32_t> every(E);
+  for (int64_t e = 0; e < E; ++e) every[e] = (int32_t)e;
+  if ((st = upload_buckets(c, "allb", every, true, false, c->all_buckets)) != DG_OK) return st;
+  if ((st = upload_buckets(c, "ordb", every, false, false, c->ord_buckets)) != DG_OK) return st;
+  return rebuild_flags(c);
+}
+
+// one phase of a residual evaluation (mode RESIDUAL) or of an RK stage (mode RK) on stream s
+dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage, double dt,
+                      cudaStream_t s, int* nlaunch) {
+  int nl = 0;
+  switch (phase) {
+    case 0:
+      for (const Bucket& b : c->ord_buckets) {
+        CU(launch_traces(c->M, b, q, s));
+        ++nl;
+      }
+      break;
+    case 1:
+      if (c->n_mortar_ns) {
+        CU(launch_mortar_lift(c->M, c->mortar_ns, c->n_mortar_ns, s));
+        ++nl;
+      }
+      break;
+    case 2:
+      for (const Bucket& b : c->ns_buckets) {
+        CU(launch_viscous(c->M, b, q, c->prm.precision, s));
+        ++nl;
+      }
+      break;
+    case 3:
+      if (c->n_mortar_all) {
+        CU(launch_mortar_flux(c->M, c->mortar_all, c->n_mortar_all, s));
+        ++nl;
+      }
+      break;
+    default:
+      for (const Bucket& b : c->all_buckets) {
+        CU(launch_inviscid(c->M, b, q, out, g, mode, stage, dt, c->prm.precision, s));
+        ++nl;
+      }
+  }
+  if (nlaunch) *nlaunch += nl;
+  return DG_OK;
+}
+
+dg_status issue_stage(dg_ctx* c, const double* q, double* out, double* g, int mode, int stage, double dt,
+                      cudaStream_t s, int* nlaunch) {
+  for (int ph = 0; ph < DG_NPHASES; ++ph) {
+    dg_status st = issue_phase(c, ph, q, out, g, mode, stage, dt, s, nlaunch);
+    if (st != DG_OK) return st;
+  }
+  return DG_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int device, dg_ctx** out) {
+  if (!out) return fail(DG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !mesh->hex || !mesh->geom_xyz) return fail(DG_ERR_ARG, "mesh, hex or geom_xyz is NULL");
+  if (mesh->n_elem <= 0 || mesh->n_elem > INT32_MAX / 6) return fail(DG_ERR_ARG, "n_elem out of range");
+  if (mesh->geom_degree < 1 || mesh->geom_degree > 2) return fail(DG_ERR_UNSUPPORTED, "geometry degree must be 1 or 2");
+  dg_status st = check_params(params);
+  if (st != DG_OK) return st;
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(DG_ERR_ARG, "device %d not present (%d devices)", device, ndev);
+  CU(cudaSetDevice(device));
+  dg_ctx* c = new dg_ctx();
+  c->device = device;
+  c->ne = mesh->n_elem;
+  c->gdeg = mesh->geom_degree;
+  const int ng3 = (c->gdeg + 1) * (c->gdeg + 1) * (c->gdeg + 1);
+  c->hex.assign(mesh->hex, mesh->hex + c->ne * 8);
+  c->gnodes.assign(mesh->geom_xyz, mesh->geom_xyz + c->ne * ng3 * 3);
+  c->bc.assign(c->ne * 6, -1);
+  if (mesh->bc_tag) c->bc.assign(mesh->bc_tag, mesh->bc_tag + c->ne * 6);
+  c->prm = *params;
+  // face matching on sorted corner ids
+  c->nb.assign(c->ne * 6, -1);
+  c->nbf.assign(c->ne * 6, 0);
+  c->nbo.assign(c->ne * 6, 0);
+  std::unordered_map<Key4, std::vector<int64_t>, Key4Hash> faces;
+  faces.reserve((size_t)c->ne * 4);
+  for (int64_t e = 0; e < c->ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      Key4 k;
+      for (int i = 0; i < 4; ++i) k.k[i] = c->hex[e * 8 + face_corner_index(f, i & 1, i >> 1)];
+      std::sort(k.k, k.k + 4);
+      for (int i = 0; i < 3; ++i)
+        if (k.k[i] == k.k[i + 1]) {
+          delete c;
+          return fail(DG_ERR_MESH, "element %lld face %d repeats a vertex id", (long long)e, f);
+        }
+      faces[k].push_back(e * 6 + f);
+    }
+  for (auto& kv : faces) {
+    const auto& v = kv.second;
+    if (v.size() > 2) {
+      delete c;
+      return fail(DG_ERR_MESH, "a face is shared by %zu elements", v.size());
+    }
+    if (v.size() == 1) {
+      int64_t s = v[0];
+      if (c->bc[s] != 1 && c->bc[s] != 2) {
+        delete c;
+        return fail(DG_ERR_MESH, "element %lld face %d is unmatched and has no boundary tag", (long long)(s / 6),
+                    (int)(s % 6));
+      }
+      continue;
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int64_t s0 = v[side], s1 = v[1 - side];
+      const int64_t e0 = s0 / 6, e1 = s1 / 6;
+      const int f0 = (int)(s0 % 6), f1 = (int)(s1 % 6);
+      if (c->bc[s0] >= 1) {
+        delete c;
+        return fail(DG_ERR_MESH, "element %lld face %d is interior but tagged as boundary", (long long)e0, f0);
+      }
+      int found = -1;
+      for (int o = 0; o < 8 && found < 0; ++o) {
+        bool ok = true;
+        for (int cb = 0; cb < 2 && ok; ++cb)
+          for (int ca = 0; ca < 2 && ok; ++ca) {
+            int a0, b0;
+            orient_fwd(o, 1, ca, cb, a0, b0);
+            ok = c->hex[e1 * 8 + face_corner_index(f1, ca, cb)] == c->hex[e0 * 8 + face_corner_index(f0, a0, b0)];
+          }
+        if (ok) found = o;
+      }
+      if (found < 0) {
+        delete c;
+        return fail(DG_ERR_MESH, "no orientation matches element %lld face %d", (long long)e0, f0);
+      }
+      c->nb[s0] = (int32_t)e1;
+      c->nbf[s0] = (uint8_t)f1;
+      c->nbo[s0] = (uint8_t)found;
+    }
+  }
+  // constants, default orders and flags
+  Ops1D o1{};
+  const OpTables& T = ops();
+  for (int N = 1; N <= MAXN; ++N) {
+    const int n = N + 1;
+    for (int i = 0; i < n * n; ++i) o1.D[N][i] = T.rule[N].D[i];
+    for (int i = 0; i < n; ++i) {
+      o1.w[N][i] = T.rule[N].w[i];
+      o1.x[N][i] = T.rule[N].x[i];
+    }
+  }
+  cudaError_t ce = upload_ops(o1);
+  if (ce == cudaSuccess) ce = prepare_kernels();
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) {
+    delete c;
+    return fail(DG_ERR_CUDA, "CUDA setup failed: %s", cudaGetErrorString(ce));
+  }
+  double* dtab = nullptr;
+  if ((st = dev_upload(c, "interp", T.interp, &dtab)) != DG_OK) {
+    dg_destroy(c);
+    return st;
+  }
+  c->M.interp = dtab;
+  if ((st = dev_upload(c, "proj", T.proj, &dtab)) != DG_OK) {
+    dg_destroy(c);
+    return st;
+  }
+  c->M.proj = dtab;
+  int* derr;
+  if ((st = dev_alloc(c, "err", 4, &derr)) != DG_OK) {
+    dg_destroy(c);
+    return st;
+  }
+  cudaMemset(derr, 0, 16);
+  c->M.err = derr;
+  apply_params(c);
+  c->order.assign(c->ne, (int8_t)std::max(3, c->gdeg));
+  c->flag.assign(c->ne, 1);
+  if ((st = rebuild_orders(c)) != DG_OK) {
+    dg_destroy(c);
+    return st;
+  }
+  *out = c;
+  return DG_OK;
+}
+
+dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
+  if (!c || !orders) return fail(DG_ERR_ARG, "NULL argument");
+  for (int64_t e = 0; e < c->ne; ++e)
+    if (orders[e] < 1 || orders[e] > MAXN || orders[e] < c->gdeg)
+      return fail(DG_ERR_ARG, "element %lld: order %d outside %d..%d", (long long)e, orders[e], std::max(1, c->gdeg), MAXN);
+  CU(cudaSetDevice(c->device));
+  std::vector<int8_t> old = c->order;
+  c->order.assign(orders, orders + c->ne);
+  dg_status st = rebuild_orders(c);
+  if (st != DG_OK) {
+    c->order = old;
+    std::string msg = g_last_error;
+    rebuild_orders(c);
+    g_last_error = msg;
+  }
+  return st;
+}
+
+dg_status dg_set_element_flags(dg_ctx* c, const uint8_t* flags) {
+  if (!c || !flags) return fail(DG_ERR_ARG, "NULL argument");
+  for (int64_t e = 0; e < c->ne; ++e)
+    if (flags[e] > 1) return fail(DG_ERR_ARG, "element %lld: flag %d is not 0 or 1", (long long)e, flags[e]);
+  CU(cudaSetDevice(c->device));
+  c->flag.assign(flags, flags + c->ne);
+  return rebuild_flags(c);
+}
+
+dg_status dg_set_params(dg_ctx* c, const dg_params* params) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  dg_status st = check_params(params);
+  if (st != DG_OK) return st;
+  c->prm = *params;
+  apply_params(c);
+  destroy_graph(c);
+  return DG_OK;
+}
+
+dg_status dg_get_layout(const dg_ctx* c, int64_t* total_nodes, const int64_t** elem_offset) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (total_nodes) *total_nodes = c->total;
+  if (elem_offset) *elem_offset = c->off.data();
+  return DG_OK;
+}
+
+dg_status dg_node_coords(dg_ctx* c, double* xyz, void* stream) {
+  if (!c || !xyz) return fail(DG_ERR_ARG, "NULL argument");
+  CU(cudaSetDevice(c->device));
+  double* gn;
+  dg_status st = dev_upload(c, "gnodes", c->gnodes, &gn);
+  if (st != DG_OK) return st;
+  for (const Bucket& b : c->ord_buckets) CU(launch_node_coords(c->M, gn, c->gdeg, b, xyz, (cudaStream_t)stream));
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  free_buf(c, "gnodes");
+  return DG_OK;
+}
+
+dg_status dg_residual(dg_ctx* c, const double* q, double* R, void* stream) {
+  if (!c || !q || !R) return fail(DG_ERR_ARG, "NULL argument");
+  const size_t bytes = sizeof(double) * 4 * c->total;
+  if (overlaps(q, bytes, R, bytes)) return fail(DG_ERR_ARG, "q and R overlap");
+  CU(cudaSetDevice(c->device));
+  int nl = 0;
+  dg_status st = issue_stage(c, q, R, nullptr, MODE_RESIDUAL, 0, 0.0, (cudaStream_t)stream, &nl);
+  c->launches_residual = nl;
+  return st;
+}
+
+dg_status dg_rk_step(dg_ctx* c, double* q, double* g, double t, double dt, int nsteps, void* stream) {
+  (void)t;
+  if (!c || !q || !g) return fail(DG_ERR_ARG, "NULL argument");
+  if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps < 0");
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt is not finite");
+  const size_t bytes = sizeof(double) * 4 * c->total;
+  if (overlaps(q, bytes, g, bytes)) return fail(DG_ERR_ARG, "q and g overlap");
+  if (nsteps == 0) return DG_OK;
+  CU(cudaSetDevice(c->device));
+  GraphCache& G = c->graph;
+  if (!G.exec || G.q != q || G.g != g || G.dt != dt || G.version != c->version) {
+    destroy_graph(c);
+    CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    dg_status st = DG_OK;
+    for (int s = 0; s < 3 && st == DG_OK; ++s) st = issue_stage(c, q, q, g, MODE_RK, s, dt, c->cap_stream, &nl);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return fail(DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      G.exec = nullptr;
+      return fail(DG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    G.q = q;
+    G.g = g;
+    G.dt = dt;
+    G.version = c->version;
+    c->launches_step = nl;
+  }
+  for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(G.exec, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+static dg_status ensure_staging(dg_ctx* c) {
+  dg_status st = DG_OK;
+  if (!c->stage_q) st = dev_alloc(c, "stage_q", 4 * c->total, &c->stage_q);
+  if (st == DG_OK && !c->stage_r) st = dev_alloc(c, "stage_r", 4 * c->total, &c->stage_r);
+  return st;
+}
+
+dg_status dg_residual_host(dg_ctx* c, const double* q_host, double* R_host, void* stream) {
+  if (!c || !q_host || !R_host) return fail(DG_ERR_ARG, "NULL argument");
+  CU(cudaSetDevice(c->device));
+  dg_status st = ensure_staging(c);
+  if (st != DG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * 4 * c->total;
+  CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
+  if ((st = dg_residual(c, c->stage_q, c->stage_r, stream)) != DG_OK) return st;
+  CU(cudaMemcpyAsync(R_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+dg_status dg_rk_step_host(dg_ctx* c, double* q_host, double* g_host, double t, double dt, int nsteps, void* stream) {
+  if (!c || !q_host || !g_host) return fail(DG_ERR_ARG, "NULL argument");
+  CU(cudaSetDevice(c->device));
+  dg_status st = ensure_staging(c);
+  if (st != DG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * 4 * c->total;
+  CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(c->stage_r, g_host, bytes, cudaMemcpyHostToDevice, s));
+  if ((st = dg_rk_step(c, c->stage_q, c->stage_r, t, dt, nsteps, stream)) != DG_OK) return st;
+  CU(cudaMemcpyAsync(q_host, c->stage_q, bytes, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(g_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+dg_status dg_check_device(dg_ctx* c, void* stream) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  int h[4] = {0, 0, 0, 0};
+  CU(cudaMemcpy(h, c->M.err, sizeof h, cudaMemcpyDeviceToHost));
+  if (h[0] != 0) {
+    CU(cudaMemset(c->M.err, 0, sizeof h));
+    if (h[0] == DG_ERR_TIMEOUT) return fail(DG_ERR_TIMEOUT, "a device-side wait timed out (site %d)", h[1]);
+    return fail(DG_ERR_DEVICE, "device error %d at site %d", h[0], h[1]);
+  }
+  return DG_OK;
+}
+
+dg_status dg_conservation(dg_ctx* c, const double* R, double out[4], void* stream) {
+  if (!c || !R || !out) return fail(DG_ERR_ARG, "NULL argument");
+  CU(cudaSetDevice(c->device));
+  for (const Bucket& b : c->ord_buckets) CU(launch_conservation(c->M, b, R, c->partial, (cudaStream_t)stream));
+  CU(cudaMemcpyAsync(c->partial_host.data(), c->partial, sizeof(double) * 4 * c->ne, cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
+  dg_status st = dg_check_device(c, stream);
+  if (st != DG_OK) return st;
+  for (int v = 0; v < 4; ++v) {
+    double s = 0.0;
+    for (int64_t e = 0; e < c->ne; ++e) s += c->partial_host[v * c->ne + e];
+    out[v] = s;
+  }
+  return DG_OK;
+}
+
+dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, double out_ms[DG_NPHASES],
+                         void* stream) {
+  if (!c || !q || !g || !out_ms) return fail(DG_ERR_ARG, "NULL argument");
+  if (reps <= 0) return fail(DG_ERR_ARG, "reps must be positive");
+  CU(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[DG_NPHASES + 1];
+  for (auto& e : ev) CU(cudaEventCreate(&e));
+  double acc[DG_NPHASES] = {0, 0, 0, 0, 0};
+  dg_status st = DG_OK;
+  for (int r = 0; r < reps && st == DG_OK; ++r) {
+    CU(cudaEventRecord(ev[0], s));
+    for (int ph = 0; ph < DG_NPHASES && st == DG_OK; ++ph) {
+      st = issue_phase(c, ph, q, q, g, MODE_RK, r % 3, dt, s, nullptr);
+      CU(cudaEventRecord(ev[ph + 1], s));
+    }
+    CU(cudaEventSynchronize(ev[DG_NPHASES]));
+    for (int ph = 0; ph < DG_NPHASES; ++ph) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+      acc[ph] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != DG_OK) return st;
+  for (int ph = 0; ph < DG_NPHASES; ++ph) out_ms[ph] = acc[ph] / reps;
+  return DG_OK;
+}
+
+dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
+  if (!c || !out) return fail(DG_ERR_ARG, "NULL argument");
+  const double d = 8.0;
+  double b[DG_NPHASES] = {0, 0, 0, 0, 0};
+  for (int64_t e = 0; e < c->ne; ++e) {
+    const double n = c->order[e] + 1, n2 = n * n, n3 = n2 * n;
+    const bool ns = c->flag[e] != 0;
+    const double geo = c->ec[e].curved != 0.0 ? 10.0 * n3 * d : 14.0 * d;
+    b[0] += 2.0 * 4.0 * 6.0 * n2 * d;  // read q at the face nodes, write the traces
+    double inv = 16.0 * n3 * d + geo;   // q, g read and written
+    if (ns) {
+      b[2] += 3.0 * n3 * d + geo + 3.0 * n3 * d + 18.0 * n2 * d;  // u in, rv and Tv out
+      inv += 3.0 * n3 * d;                                       // rv in
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int32_t nb = c->nb[e * 6 + f];
+      if (nb < 0) continue;
+      const double nn = c->order[nb] + 1;
+      const bool nbns = c->flag[nb] != 0;
+      if (c->order[nb] == c->order[e]) {
+        if (ns) b[2] += 3.0 * n2 * d;                  // neighbour velocity trace
+        inv += 4.0 * n2 * d;                            // neighbour q trace
+        if (ns) inv += 3.0 * n2 * d;                    // own viscous trace
+        if (nbns) inv += 3.0 * n2 * d;                  // neighbour viscous trace
+      } else {
+        if (ns) {
+          b[1] += 3.0 * (n2 + nn * nn) * d + 9.0 * n2 * d;  // both velocity traces in, lifting out
+          b[2] += 9.0 * n2 * d;                             // lifting in
+        }
+        b[3] += 4.0 * (n2 + nn * nn) * d + (ns ? 3.0 * n2 * d : 0.0) + (nbns ? 3.0 * nn * nn * d : 0.0) +
+                4.0 * n2 * d;
+        inv += 4.0 * n2 * d + (ns ? 3.0 * n2 * d : 0.0);   // projected flux, own viscous trace
+      }
+    }
+    b[4] += inv;
+  }
+  for (int ph = 0; ph < DG_NPHASES; ++ph) out[ph] = b[ph];
+  return DG_OK;
+}
+
+int dg_launches_per_residual(const dg_ctx* c) { return c ? c->launches_residual : 0; }
+int dg_launches_per_step(const dg_ctx* c) { return c ? c->launches_step : 0; }
+
+void dg_destroy(dg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  destroy_graph(c);
+  for (auto& kv : c->buf) cudaFree(kv.second.p);
+  c->buf.clear();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// dg_internal.h -- data shared between the host library (dg_host.cpp) and the kernels.
+// Not part of the public C ABI (include/dg.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgk {
+
+constexpr int MAXN = 7;        // largest polynomial order with a kernel instantiation
+constexpr int NP = MAXN + 1;   // table stride
+
+// Kind of coupling behind one local face of an element.
+enum FaceKind : uint8_t {
+  FK_CONF = 0,     // same order on both sides: the flux is evaluated node by node, in place
+  FK_MORTAR = 1,   // different orders: flux on the mortar of the larger order, projected back
+  FK_INFLOW = 2,   // ghost state: prescribed velocity, interior pressure
+  FK_OUTFLOW = 3,  // ghost state: interior velocity, zero pressure
+};
+
+// One entry per (element, local face). Local face f = 2 d + s lies on xi_{d+1} = s ? +1 : -1;
+// its face coordinates (a, b) run along the two other directions in increasing order.
+struct FaceLink {
+  int32_t nbr;     // neighbour element, -1 on a boundary
+  uint8_t nface;   // neighbour's local face
+  uint8_t orient;  // swap | flip_a << 1 | flip_b << 2: neighbour (a1, b1) -> mine
+  uint8_t kind;    // FaceKind
+  uint8_t nflag;   // neighbour flag (0 Euler, 1 NS)
+};
+
+// Per-element constants. Affine elements carry their constant metric here; curved elements
+// read per-node metric terms from DevMesh::geo.
+struct ElemConst {
+  double Ja[9];    // Ja[d*3+k] = J d xi_d / d x_k (affine only)
+  double J, invJ;  // affine only
+  double delta;    // LES filter width: cube root of the element volume / (N + 1)
+  double curved;   // 1.0: metric terms per node in DevMesh::geo; 0.0: affine (Ja above)
+};
+
+// Everything a kernel needs, passed by value.
+struct DevMesh {
+  int64_t n_elem, total, tr_total;
+  const int64_t* elem_off;   // [E+1] node offsets
+  const int64_t* tr_off;     // [E+1] face-trace offsets: element e's 6 faces x n^2 nodes
+  const int8_t* order;       // [E]
+  const uint8_t* flag;       // [E]
+  const FaceLink* link;      // [E*6]
+  const ElemConst* ec;       // [E]
+  const double* geo;         // curved elements: [10][total] = Ja[9] (d*3+k) then J
+  double* Tq;                // [4][tr_total] face traces of q (FP64)
+  double* Tv;                // [3][tr_total] outward viscous flux traces tau . S (NS elements)
+  double* rv;                // [3][total]    J * viscous volume divergence (NS elements)
+  double* LU;                // [9][tr_total] projected BR1 lifting u*_c S_k on mortar faces
+  double* LH;                // [4][tr_total] projected total flux (F_e* - F_v*) . S on mortars
+  const double* interp;      // [(Ns*NP+Nd)*NP*NP + i*NP + j]: Lagrange interpolation Ns -> Nd
+  const double* proj;        // [(Nh*NP+Nl)*NP*NP + i*NP + j]: L2 projection Nh -> Nl
+  int* err;                  // device error word
+  double nu, c0sq, cs, cv;
+  int closure, riemann;
+  double inflow[4];
+};
+
+// 1D Gauss-Lobatto operators for N = 1..MAXN (uploaded to constant memory).
+struct Ops1D {
+  double D[NP][NP * NP];  // D[N][i*n+m]
+  double w[NP][NP];       // w[N][i]
+  double x[NP][NP];       // x[N][i]
+};
+
+// Element lists of one kernel launch.
+struct Bucket {
+  int N;
+  bool curved;
+  bool ns;            // true: only NS elements (viscous pass)
+  int32_t* list;      // device
+  int count;
+};
+
+enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };
+
+// Launchers (dg_kernels.cu). All return cudaGetLastError() of their launches.
+cudaError_t upload_ops(const Ops1D& ops);
+cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
+cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
+cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, int precision,
+                           cudaStream_t s);
+cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, double* out,
+                            double* g, int mode, int stage, double dt, int precision,
+                            cudaStream_t s);
+cudaError_t launch_node_coords(const DevMesh& M, const double* geom_nodes, int geom_degree,
+                               const Bucket& b, double* xyz, cudaStream_t s);
+cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R,
+                                double* partial, cudaStream_t s);
+cudaError_t prepare_kernels();
+
+}  // namespace dgk

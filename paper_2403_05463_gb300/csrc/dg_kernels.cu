@@ -1,0 +1,803 @@
+// dg_kernels.cu -- sm_103a kernels of the flagged Euler / NS-LES DGSEM residual (FP64 path).
+//
+// Per residual evaluation (one Runge-Kutta stage):
+//   traces   : every element copies q at its 6 n^2 face nodes into a face-major trace buffer
+//              (neighbours read only traces, never q, so the last pass may update q in place).
+//   mortar_lift (p-nonconforming faces of NS elements): BR1 lifting u* S projected from the
+//              mortar of the larger order.
+//   viscous  (NS elements only, Sec. 2.3): BR1 gradient of the velocity, eddy viscosity,
+//              stress, contravariant viscous flux, its divergence (stored as J r_v) and the
+//              outward viscous flux traces tau . S on the 6 faces.
+//   mortar_flux: total projected flux (F_e* - F_v*) . S on p-nonconforming faces.
+//   inviscid (all elements): contravariant Euler flux, its divergence by sum-factorised
+//              derivative contractions staged in shared memory, surface terms (Roe/LLF
+//              fluctuation on conforming faces, BR1 average of viscous traces), + J r_v,
+//              then R = (1/J)(...) or the in-place low-storage RK3 update.
+// Strong form on Gauss-Lobatto nodes (equal to the weak form of App. B, Eq. NS4, by the
+// summation-by-parts property of the Lobatto quadrature):
+//   J R = -sum_d D_d (Ftil_e^d - Ftil_v^d) - sum_faces (1/w_end) [(F_e* - F_v*) . S - (Ftil_e - Ftil_v)_out]
+#include "dg_internal.h"
+
+#include <cstdio>
+
+namespace dgk {
+
+__constant__ Ops1D c_ops;
+
+// Williamson 2N-storage RK3 (the paper's low-storage third-order scheme, Sec. 2.3).
+__constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+__constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+template <int N>
+struct Shape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
+  static constexpr int EPB = (256 / n3) > 0 ? (256 / n3) : 1;   // elements per block
+  static constexpr int threads = ((EPB * n3 + 31) / 32) * 32;
+};
+
+// volume node of face f = 2d+s at face coordinates (a, b)
+__host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
+  int d = f >> 1, fix = (f & 1) ? n - 1 : 0;
+  if (d == 0) return fix + n * (a + n * b);
+  if (d == 1) return a + n * (fix + n * b);
+  return a + n * (b + n * fix);
+}
+
+// my face coordinates (a, b) at order N -> neighbour's (a1, b1)
+__device__ __forceinline__ void inv_orient(int o, int N, int a, int b, int& a1, int& b1) {
+  int x = (o & 2) ? N - a : a;
+  int y = (o & 4) ? N - b : b;
+  if (o & 1) { a1 = y; b1 = x; } else { a1 = x; b1 = y; }
+}
+
+// neighbour face coordinates (a1, b1) at order M -> mine
+__device__ __forceinline__ void fwd_orient(int o, int M, int a1, int b1, int& a0, int& b0) {
+  int x = (o & 1) ? b1 : a1, y = (o & 1) ? a1 : b1;
+  a0 = (o & 2) ? M - x : x;
+  b0 = (o & 4) ? M - y : y;
+}
+
+// y = A(ub) x for the artificial-compressibility flux Jacobian in direction nh
+__device__ __forceinline__ void ac_jac_apply(const double ub[3], double un, const double nh[3],
+                                             double c0sq, const double x[4], double y[4]) {
+  double nx = nh[0] * x[1] + nh[1] * x[2] + nh[2] * x[3];
+  y[0] = c0sq * nx;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) y[1 + c] = nh[c] * x[0] + ub[c] * nx + un * x[1 + c];
+}
+
+// Fluctuation A^-(qbar) dq = (F* - F_n(q-)) for Roe (riemann == 0): the flux is quadratic,
+// so F(q+) - F(q-) = A(qbar) dq exactly with qbar the arithmetic mean, and |A| is the
+// quadratic polynomial in A that matches |lambda| on the three distinct eigenvalues
+// u_n - a, u_n, u_n + a (a = sqrt(u_n^2 + c0^2)). For LLF: 1/2 (A dq - lambda_max dq).
+__device__ __forceinline__ void flux_fluct(const double qm[4], const double qp[4], const double nh[3],
+                                           double c0sq, int riemann, double out[4]) {
+  double dq[4], ub[3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) dq[v] = qp[v] - qm[v];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (qm[1 + c] + qp[1 + c]);
+  double un = ub[0] * nh[0] + ub[1] * nh[1] + ub[2] * nh[2];
+  double y1[4];
+  ac_jac_apply(ub, un, nh, c0sq, dq, y1);
+  if (riemann == 0) {
+    double y2[4];
+    ac_jac_apply(ub, un, nh, c0sq, y1, y2);
+    double a = sqrt(un * un + c0sq);
+    double aun = fabs(un);
+    double lm = un - a, l0 = un;
+    double d1 = (aun + un - a) / a;        // divided difference of |.| on (lm, l0)
+    double d2 = (a - aun) / (a * a);       // second divided difference on (lm, l0, lp)
+    double k0 = -lm - d1 * lm + d2 * lm * l0;
+    double k1 = d1 - d2 * (lm + l0);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - (k0 * dq[v] + k1 * y1[v] + d2 * y2[v]));
+  } else {
+    double unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+    double unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
+    double lam = fmax(fabs(unm) + sqrt(unm * unm + c0sq), fabs(unp) + sqrt(unp * unp + c0sq));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - lam * dq[v]);
+  }
+}
+
+// Full numerical flux F*(q-, q+) (mortar faces): F_n(q-) + fluctuation.
+__device__ __forceinline__ void flux_full(const double qm[4], const double qp[4], const double nh[3],
+                                          double c0sq, int riemann, double out[4]) {
+  double fl[4];
+  flux_fluct(qm, qp, nh, c0sq, riemann, fl);
+  double un = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+  out[0] = c0sq * un + fl[0];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[1 + c] = qm[1 + c] * un + qm[0] * nh[c] + fl[1 + c];
+}
+
+// LES eddy viscosity from G[c][k] = d u_c / d x_k (App. A: Vreman; Smagorinsky alternative).
+__device__ __forceinline__ double eddy_visc(const double G[3][3], double delta, int closure, double cs,
+                                            double cv) {
+  if (closure == 0) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.5 * (G[c][k] + G[k][c]);
+        s2 += s * s;
+      }
+    double l = cs * delta;
+    return l * l * sqrt(2.0 * s2);
+  }
+  // Vreman: alpha_ij = d u_j / d x_i = G[j][i]; beta = delta^2 alpha^T alpha
+  double aa = 0.0, b[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      aa += G[j][i] * G[j][i];
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) s += G[i][m] * G[j][m];  // alpha_mi alpha_mj = G[i][m] G[j][m]
+      b[i][j] = delta * delta * s;
+    }
+  double B = b[0][0] * b[1][1] - b[0][1] * b[0][1] + b[0][0] * b[2][2] - b[0][2] * b[0][2] +
+             b[1][1] * b[2][2] - b[1][2] * b[1][2];
+  if (aa < 1e-300 || B <= 0.0) return 0.0;
+  return cv * sqrt(B / aa);
+}
+
+// ---------------------------------------------------------------------------------------
+// traces
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void k_traces(DevMesh M, const int32_t* __restrict__ list, int count,
+                         const double* __restrict__ q) {
+  constexpr int n = N + 1, n2 = n * n, per = 6 * n2;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)count * per) return;
+  int le = (int)(gid / per), r = (int)(gid % per);
+  int f = r / n2, ab = r % n2;
+  int e = list[le];
+  int64_t src = M.elem_off[e] + face_node(f, n, ab % n, ab / n);
+  int64_t dst = M.tr_off[e] + f * n2 + ab;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) M.Tq[v * M.tr_total + dst] = __ldg(&q[v * M.total + src]);
+}
+
+// ---------------------------------------------------------------------------------------
+// viscous pass (NS elements)
+// ---------------------------------------------------------------------------------------
+template <int N, bool CURVED>
+__global__ void __launch_bounds__(Shape<N>::threads) k_viscous(DevMesh M, const int32_t* __restrict__ list,
+                                                               int count, const double* __restrict__ q) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ double sm[];
+  double* sD = sm;                                // n*n
+  double* sU = sD + NP * NP;                      // EPB * 3 * n3
+  double* sJa = sU + EPB * 3 * n3;                // EPB * 9 * n3 (curved only)
+  double* sF = sJa + (CURVED ? EPB * 9 * n3 : 0); // EPB * 9 * n3
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_ops.D[N][t];
+  int le = tid / n3, p = tid % n3;
+  const int slot = blockIdx.x * EPB + le;
+  const bool active = (le < EPB) && (slot < count);
+  if (le >= EPB) le = EPB - 1;
+  const int e = active ? list[slot] : 0;
+  const int64_t off = active ? M.elem_off[e] : 0;
+  double* U = sU + le * 3 * n3;
+  double* JA = sJa + le * 9 * n3;
+  double* F = sF + le * 9 * n3;
+  double Ja[9], invJ = 0.0, u[3] = {0.0, 0.0, 0.0};
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u[c] = __ldg(&q[(1 + c) * M.total + off + p]);
+      U[c * n3 + p] = u[c];
+    }
+    if (CURVED) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        Ja[k] = __ldg(&M.geo[k * M.total + off + p]);
+        JA[k * n3 + p] = Ja[k];
+      }
+      invJ = 1.0 / __ldg(&M.geo[9 * M.total + off + p]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
+      invJ = M.ec[e].invJ;
+    }
+  }
+  __syncthreads();
+  const int ii[3] = {p % n, (p / n) % n, p / n2};
+  const int str[3] = {1, n, n2};
+  double G[3][3];
+  if (active) {
+    // volume part: J G_ck = sum_d D_d (Ja^d_k u_c)
+    if (!CURVED) {
+      double du[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int base = p - ii[d] * str[d];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          double dm = sD[ii[d] * n + m];
+          int pm = base + m * str[d];
+          s0 += dm * U[pm];
+          s1 += dm * U[n3 + pm];
+          s2 += dm * U[2 * n3 + pm];
+        }
+        du[0][d] = s0;
+        du[1][d] = s1;
+        du[2][d] = s2;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[c][k] = Ja[k] * du[c][0] + Ja[3 + k] * du[c][1] + Ja[6 + k] * du[c][2];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[c][k] = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int base = p - ii[d] * str[d];
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          double dm = sD[ii[d] * n + m];
+          int pm = base + m * str[d];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            double dj = dm * JA[(d * 3 + k) * n3 + pm];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) G[c][k] += dj * U[c * n3 + pm];
+          }
+        }
+      }
+    }
+    // BR1 lifting on the faces this node lies on: (1/w_end) (u* - u) S
+    const double invw = 1.0 / c_ops.w[N][0];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (ii[d] != 0 && ii[d] != N) continue;
+      const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+      const double sg = side ? 1.0 : -1.0;
+      const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+      const FaceLink L = M.link[e * 6 + f];
+      double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+      if (L.kind == FK_MORTAR) {
+        const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) G[c][k] += invw * (M.LU[(c * 3 + k) * M.tr_total + ms] - u[c] * Sv[k]);
+      } else {
+        double jump[3] = {0.0, 0.0, 0.0};
+        if (L.kind == FK_CONF) {
+          int a1, b1;
+          inv_orient(L.orient, N, a, b, a1, b1);
+          const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) jump[c] = M.Tq[(1 + c) * M.tr_total + ns] - u[c];
+        } else if (L.kind == FK_INFLOW) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) jump[c] = M.inflow[1 + c] - u[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) G[c][k] += invw * 0.5 * jump[c] * Sv[k];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[c][k] *= invJ;
+    // eddy viscosity and stress
+    const double mu = M.nu + eddy_visc(G, M.ec[e].delta, M.closure, M.cs, M.cv);
+    const double tr = G[0][0] + G[1][1] + G[2][2];
+    double tau[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tau[c][k] = mu * (G[c][k] + G[k][c]) - (c == k ? (2.0 / 3.0) * mu * tr : 0.0);
+    // contravariant viscous flux Fv^d_c = sum_k Ja^d_k tau_ck
+    double Fv[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Fv[d][c] = Ja[d * 3] * tau[c][0] + Ja[d * 3 + 1] * tau[c][1] + Ja[d * 3 + 2] * tau[c][2];
+        F[(d * 3 + c) * n3 + p] = Fv[d][c];
+      }
+    // outward viscous flux traces tau . S = sigma Fv^d
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (ii[d] != 0 && ii[d] != N) continue;
+      const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+      const double sg = side ? 1.0 : -1.0;
+      const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+      const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) M.Tv[c * M.tr_total + ms] = sg * Fv[d][c];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // J r_v = sum_d D_d Fv^d
+    double V[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int base = p - ii[d] * str[d];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        double dm = sD[ii[d] * n + m];
+        int pm = base + m * str[d];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) V[c] += dm * F[(d * 3 + c) * n3 + pm];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M.rv[c * M.total + off + p] = V[c];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// inviscid pass + assembly + (optional) RK update
+// ---------------------------------------------------------------------------------------
+template <int N, bool CURVED, int MODE>
+__global__ void __launch_bounds__(Shape<N>::threads)
+    k_inviscid(DevMesh M, const int32_t* __restrict__ list, int count, const double* qin, double* out,
+               double* g, int stage, double dt) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sF = sD + NP * NP;  // EPB * 12 * n3: Ftil_e[d][v]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_ops.D[N][t];
+  int le = tid / n3, p = tid % n3;
+  const int slot = blockIdx.x * EPB + le;
+  const bool active = (le < EPB) && (slot < count);
+  if (le >= EPB) le = EPB - 1;
+  const int e = active ? list[slot] : 0;
+  const int64_t off = active ? M.elem_off[e] : 0;
+  double* F = sF + le * 12 * n3;
+  double qq[4] = {0.0, 0.0, 0.0, 0.0}, Ja[9], invJ = 0.0, fl[4][3];
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qq[v] = qin[v * M.total + off + p];
+    if (CURVED) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = __ldg(&M.geo[k * M.total + off + p]);
+      invJ = 1.0 / __ldg(&M.geo[9 * M.total + off + p]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
+      invJ = M.ec[e].invJ;
+    }
+    // physical Euler flux f_v,k
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      fl[0][k] = M.c0sq * qq[1 + k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fl[1 + c][k] = qq[1 + c] * qq[1 + k] + (c == k ? qq[0] : 0.0);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        F[(d * 4 + v) * n3 + p] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int ii[3] = {p % n, (p / n) % n, p / n2};
+  const int str[3] = {1, n, n2};
+  double JR[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int base = p - ii[d] * str[d];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      double dm = sD[ii[d] * n + m];
+      int pm = base + m * str[d];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) JR[v] -= dm * F[(d * 4 + v) * n3 + pm];
+    }
+  }
+  const bool ns = M.flag[e] != 0;
+  if (ns) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) JR[1 + c] += M.rv[c * M.total + off + p];
+  }
+  const double invw = 1.0 / c_ops.w[N][0];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (ii[d] != 0 && ii[d] != N) continue;
+    const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+    const double sg = side ? 1.0 : -1.0;
+    const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+    const FaceLink L = M.link[e * 6 + f];
+    const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+    const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+    if (L.kind == FK_MORTAR) {
+      // projected (F_e* - F_v*) . S from the mortar, minus the own outward flux
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double own = Sv[0] * fl[v][0] + Sv[1] * fl[v][1] + Sv[2] * fl[v][2];
+        if (v > 0 && ns) own -= M.Tv[(v - 1) * M.tr_total + ms];
+        JR[v] -= invw * (M.LH[v * M.tr_total + ms] - own);
+      }
+      continue;
+    }
+    const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+    const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+    double qp[4];
+    int64_t nsl = 0;
+    if (L.kind == FK_CONF) {
+      int a1, b1;
+      inv_orient(L.orient, N, a, b, a1, b1);
+      nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) qp[v] = M.Tq[v * M.tr_total + nsl];
+    } else if (L.kind == FK_INFLOW) {
+      qp[0] = qq[0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qp[1 + c] = M.inflow[1 + c];
+    } else {
+      qp[0] = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qp[1 + c] = qq[1 + c];
+    }
+    double fx[4];
+    flux_fluct(qq, qp, nh, M.c0sq, M.riemann, fx);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) JR[v] -= invw * s * fx[v];
+    if (L.kind == FK_CONF && (ns || L.nflag)) {
+      // BR1: F_v* . S - Ftil_v,out = -1/2 (tau_own . S_own + tau_nbr . S_nbr)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double t = 0.0;
+        if (ns) t += M.Tv[c * M.tr_total + ms];
+        if (L.nflag) t += M.Tv[c * M.tr_total + nsl];
+        JR[1 + c] -= invw * 0.5 * t;
+      }
+    }
+  }
+  if (MODE == MODE_RESIDUAL) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v * M.total + off + p] = JR[v] * invJ;
+  } else {
+    const double A = c_rkA[stage], B = c_rkB[stage];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t ix = v * M.total + off + p;
+      double gi = dt * (JR[v] * invJ);
+      if (stage > 0) gi += A * g[ix];
+      g[ix] = gi;
+      out[ix] = qq[v] + B * gi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// mortars (p-nonconforming faces): one block per (element, face) slot
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ const double* interp_tab(const DevMesh& M, int Ns, int Nd) {
+  return M.interp + (Ns * NP + Nd) * NP * NP;
+}
+__device__ __forceinline__ const double* proj_tab(const DevMesh& M, int Nh, int Nl) {
+  return M.proj + (Nh * NP + Nl) * NP * NP;
+}
+
+// 2D tensor application on a face: dst[a + nd b] = sum T[a][aa] T[b][bb] src[aa + ns bb]
+__device__ __forceinline__ double tensor2(const double* T, int ns, int a, int b, const double* src) {
+  double s = 0.0;
+  for (int bb = 0; bb < ns; ++bb) {
+    double t = 0.0;
+    for (int aa = 0; aa < ns; ++aa) t += T[a * NP + aa] * src[aa + ns * bb];
+    s += T[b * NP + bb] * t;
+  }
+  return s;
+}
+
+__device__ __forceinline__ void node_metric(const DevMesh& M, int e, int64_t node, double Ja[9]) {
+  if (M.ec[e].curved != 0.0) {
+    for (int k = 0; k < 9; ++k) Ja[k] = M.geo[k * M.total + node];
+  } else {
+    for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
+  }
+}
+
+// loads my face field (nvar from `src` planes, stride tr_total) and S at my face nodes
+struct MortarSmem {
+  double mine[7][NP * NP];   // my trace at my order
+  double nbr[7][NP * NP];    // neighbour trace at its order
+  double mM[7][NP * NP];     // mine on the mortar
+  double nM[7][NP * NP];     // neighbour on the mortar (my coordinates)
+  double Sm[3][NP * NP];     // my S at my nodes
+  double SM[3][NP * NP];     // S on the mortar
+  double H[9][NP * NP];      // mortar result
+};
+
+__global__ void k_mortar_lift(DevMesh M, const int32_t* __restrict__ slots, int count) {
+  __shared__ MortarSmem sm;
+  if (blockIdx.x >= count) return;
+  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
+  const FaceLink L = M.link[es];
+  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
+  const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
+  const int d = f >> 1;
+  const double sg = (f & 1) ? 1.0 : -1.0;
+  const int t = threadIdx.x;
+  if (t < nm * nm) {
+    int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
+    double Ja[9];
+    node_metric(M, e, node, Ja);
+    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
+    for (int c = 0; c < 3; ++c) sm.mine[c][t] = M.Tq[(1 + c) * M.tr_total + M.tr_off[e] + f * nm * nm + t];
+  }
+  if (t < nn * nn)
+    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = M.Tq[(1 + c) * M.tr_total + M.tr_off[L.nbr] + L.nface * nn * nn + t];
+  __syncthreads();
+  if (t < nM * nM) {
+    const int a = t % nM, b = t / nM;
+    const double* Im = interp_tab(M, Nm, Mo);
+    const double* In = interp_tab(M, Nn, Mo);
+    for (int c = 0; c < 3; ++c) sm.mM[c][t] = tensor2(Im, nm, a, b, sm.mine[c]);
+    for (int k = 0; k < 3; ++k) sm.SM[k][t] = tensor2(Im, nm, a, b, sm.Sm[k]);
+    int a0, b0;
+    fwd_orient(L.orient, Mo, a, b, a0, b0);  // (a, b) are neighbour mortar coordinates here
+    for (int c = 0; c < 3; ++c) sm.nM[c][a0 + nM * b0] = tensor2(In, nn, a, b, sm.nbr[c]);
+  }
+  __syncthreads();
+  if (t < nM * nM)
+    for (int c = 0; c < 3; ++c) {
+      double us = 0.5 * (sm.mM[c][t] + sm.nM[c][t]);
+      for (int k = 0; k < 3; ++k) sm.H[c * 3 + k][t] = us * sm.SM[k][t];
+    }
+  __syncthreads();
+  if (t < nm * nm) {
+    const double* P = proj_tab(M, Mo, Nm);
+    const int a = t % nm, b = t / nm;
+    for (int ck = 0; ck < 9; ++ck)
+      M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = tensor2(P, nM, a, b, sm.H[ck]);
+  }
+}
+
+__global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int count) {
+  __shared__ MortarSmem sm;
+  if (blockIdx.x >= count) return;
+  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
+  const FaceLink L = M.link[es];
+  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
+  const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
+  const int d = f >> 1;
+  const double sg = (f & 1) ? 1.0 : -1.0;
+  const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
+  const int t = threadIdx.x;
+  // planes 0..3: q, 4..6: outward viscous traces
+  if (t < nm * nm) {
+    int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
+    double Ja[9];
+    node_metric(M, e, node, Ja);
+    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
+    const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
+    for (int v = 0; v < 4; ++v) sm.mine[v][t] = M.Tq[v * M.tr_total + s0];
+    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? M.Tv[c * M.tr_total + s0] : 0.0;
+  }
+  if (t < nn * nn) {
+    const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
+    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = M.Tq[v * M.tr_total + s1];
+    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? M.Tv[c * M.tr_total + s1] : 0.0;
+  }
+  __syncthreads();
+  if (t < nM * nM) {
+    const int a = t % nM, b = t / nM;
+    const double* Im = interp_tab(M, Nm, Mo);
+    const double* In = interp_tab(M, Nn, Mo);
+    for (int v = 0; v < 7; ++v) sm.mM[v][t] = tensor2(Im, nm, a, b, sm.mine[v]);
+    for (int k = 0; k < 3; ++k) sm.SM[k][t] = tensor2(Im, nm, a, b, sm.Sm[k]);
+    int a0, b0;
+    fwd_orient(L.orient, Mo, a, b, a0, b0);
+    for (int v = 0; v < 7; ++v) sm.nM[v][a0 + nM * b0] = tensor2(In, nn, a, b, sm.nbr[v]);
+  }
+  __syncthreads();
+  if (t < nM * nM) {
+    const double Sv[3] = {sm.SM[0][t], sm.SM[1][t], sm.SM[2][t]};
+    const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+    const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+    double qm[4], qp[4], Fs[4];
+    for (int v = 0; v < 4; ++v) {
+      qm[v] = sm.mM[v][t];
+      qp[v] = sm.nM[v][t];
+    }
+    flux_full(qm, qp, nh, M.c0sq, M.riemann, Fs);
+    sm.H[0][t] = s * Fs[0];
+    for (int c = 0; c < 3; ++c) sm.H[1 + c][t] = s * Fs[1 + c] - 0.5 * (sm.mM[4 + c][t] - sm.nM[4 + c][t]);
+  }
+  __syncthreads();
+  if (t < nm * nm) {
+    const double* P = proj_tab(M, Mo, Nm);
+    const int a = t % nm, b = t / nm;
+    for (int v = 0; v < 4; ++v)
+      M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = tensor2(P, nM, a, b, sm.H[v]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// node coordinates and conservation sums (not on the hot path)
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void k_node_coords(DevMesh M, const int32_t* __restrict__ list, int count, const double* gn,
+                              int gdeg, double* xyz) {
+  constexpr int n = N + 1, n3 = n * n * n;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)count * n3) return;
+  const int e = list[gid / n3], p = (int)(gid % n3);
+  const int i = p % n, j = (p / n) % n, k = p / (n * n);
+  const int ng = gdeg + 1, ng3 = ng * ng * ng;
+  const double* I = M.interp + (gdeg * NP + N) * NP * NP;
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (int cc = 0; cc < ng; ++cc)
+      for (int bb = 0; bb < ng; ++bb)
+        for (int aa = 0; aa < ng; ++aa)
+          s += I[i * NP + aa] * I[j * NP + bb] * I[k * NP + cc] * gn[((int64_t)e * ng3 + aa + ng * (bb + ng * cc)) * 3 + c];
+    xyz[c * M.total + M.elem_off[e] + p] = s;
+  }
+}
+
+template <int N>
+__global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int count, const double* R,
+                               double* partial) {
+  constexpr int n = N + 1, n3 = n * n * n;
+  int le = blockIdx.x * blockDim.x + threadIdx.x;
+  if (le >= count) return;
+  const int e = list[le];
+  const int64_t off = M.elem_off[e];
+  const bool curved = M.ec[e].curved != 0.0;
+  for (int v = 0; v < 4; ++v) {
+    double s = 0.0;
+    for (int p = 0; p < n3; ++p) {
+      const double w = c_ops.w[N][p % n] * c_ops.w[N][(p / n) % n] * c_ops.w[N][p / (n * n)];
+      const double J = curved ? M.geo[9 * M.total + off + p] : M.ec[e].J;
+      s += w * J * R[v * M.total + off + p];
+    }
+    partial[v * M.n_elem + e] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------------------
+cudaError_t upload_ops(const Ops1D& ops) { return cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D)); }
+
+template <int N, bool C>
+static size_t visc_smem() {
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * (3 + (C ? 9 : 0) + 9) * Shape<N>::n3);
+}
+template <int N>
+static size_t inv_smem() {
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * 12 * Shape<N>::n3);
+}
+
+template <int N>
+static cudaError_t prep_n() {
+  cudaError_t r;
+  if ((r = cudaFuncSetAttribute(k_viscous<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)visc_smem<N, false>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)visc_smem<N, true>())) != cudaSuccess) return r;
+  const int is = (int)inv_smem<N>();
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  return cudaSuccess;
+}
+
+cudaError_t prepare_kernels() {
+  cudaError_t r;
+  if ((r = prep_n<1>()) != cudaSuccess) return r;
+  if ((r = prep_n<2>()) != cudaSuccess) return r;
+  if ((r = prep_n<3>()) != cudaSuccess) return r;
+  if ((r = prep_n<4>()) != cudaSuccess) return r;
+  if ((r = prep_n<5>()) != cudaSuccess) return r;
+  if ((r = prep_n<6>()) != cudaSuccess) return r;
+  if ((r = prep_n<7>()) != cudaSuccess) return r;
+  return cudaSuccess;
+}
+
+#define DG_DISPATCH_N(NVAR, ...)                                  \
+  switch (NVAR) {                                                 \
+    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;         \
+    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;         \
+    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;         \
+    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;         \
+    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;         \
+    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;         \
+    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;         \
+    default: return cudaErrorInvalidValue;                        \
+  }
+
+cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_DISPATCH_N(b.N, {
+    const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
+    const int thr = 256;
+    k_traces<NN><<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(M, b.list, b.count, q);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s) {
+  (void)precision;
+  if (b.count == 0) return cudaSuccess;
+  DG_DISPATCH_N(b.N, {
+    using SH = Shape<NN>;
+    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+    if (b.curved)
+      k_viscous<NN, true><<<grid, SH::threads, visc_smem<NN, true>(), s>>>(M, b.list, b.count, q);
+    else
+      k_viscous<NN, false><<<grid, SH::threads, visc_smem<NN, false>(), s>>>(M, b.list, b.count, q);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                            int mode, int stage, double dt, int precision, cudaStream_t s) {
+  (void)precision;
+  if (b.count == 0) return cudaSuccess;
+  DG_DISPATCH_N(b.N, {
+    using SH = Shape<NN>;
+    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+    const size_t sm = inv_smem<NN>();
+    if (mode == MODE_RESIDUAL) {
+      if (b.curved)
+        k_inviscid<NN, true, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+      else
+        k_inviscid<NN, false, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+    } else {
+      if (b.curved)
+        k_inviscid<NN, true, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+      else
+        k_inviscid<NN, false, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_mortar_lift<<<count, 64, 0, s>>>(M, slots, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_mortar_flux<<<count, 64, 0, s>>>(M, slots, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_coords(const DevMesh& M, const double* gn, int gdeg, const Bucket& b, double* xyz,
+                               cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_DISPATCH_N(b.N, {
+    const int64_t tot = (int64_t)b.count * (NN + 1) * (NN + 1) * (NN + 1);
+    k_node_coords<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, gn, gdeg, xyz);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, double* partial,
+                                cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_DISPATCH_N(b.N, {
+    k_conservation<NN><<<(unsigned)((b.count + 127) / 128), 128, 0, s>>>(M, b.list, b.count, R, partial);
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

@@ -1,0 +1,268 @@
+"""ctypes binding of libdgflag.so (include/dg.h): argument marshalling only.
+
+Every step of the residual and of the Runge-Kutta update runs in the library's CUDA
+kernels; PyTorch only provides device memory and streams. There is no fallback: if the
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdgflag.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "dg.h")
+
+DG_OK = 0
+STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA", 4: "DG_ERR_OOM",
+          5: "DG_ERR_UNSUPPORTED", 6: "DG_ERR_STATE", 7: "DG_ERR_TIMEOUT", 8: "DG_ERR_DEVICE"}
+
+PRECISION = {"fp64": 0, "fp32": 1}
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("hex", ctypes.POINTER(ctypes.c_int64)),
+                ("geom_degree", ctypes.c_int), ("geom_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("bc_tag", ctypes.POINTER(ctypes.c_int8))]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
+                ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def header_symbols():
+    """Names of the functions include/dg.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z_]+)\s*\(", text)))
+
+
+def load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.dg_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.c_int,
+                                     ctypes.POINTER(_vp)]
+        L.dg_set_orders.argtypes = [_vp, ctypes.POINTER(ctypes.c_int8)]
+        L.dg_set_element_flags.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint8)]
+        L.dg_set_params.argtypes = [_vp, ctypes.POINTER(Params)]
+        L.dg_get_layout.argtypes = [_vp, _i64p, ctypes.POINTER(_i64p)]
+        L.dg_node_coords.argtypes = [_vp, _vp, _vp]
+        L.dg_residual.argtypes = [_vp, _vp, _vp, _vp]
+        L.dg_rk_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]
+        L.dg_residual_host.argtypes = [_vp, _vp, _vp, _vp]
+        L.dg_rk_step_host.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]
+        L.dg_conservation.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+        L.dg_check_device.argtypes = [_vp, _vp]
+        L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
+        L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        L.dg_launches_per_residual.argtypes = [_vp]
+        L.dg_launches_per_step.argtypes = [_vp]
+        L.dg_last_error.restype = ctypes.c_char_p
+        L.dg_destroy.argtypes = [_vp]
+        L.dg_destroy.restype = None
+        for name in header_symbols():
+            if name not in ("dg_last_error", "dg_destroy") and not name.startswith("dg_launches"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(status):
+    if status != DG_OK:
+        raise DGError(status, load().dg_last_error().decode())
+
+
+def make_params(p: dict, precision=0) -> Params:
+    out = Params()
+    out.nu, out.c0sq, out.cs, out.cv = p["nu"], p["c0sq"], p["cs"], p["cv"]
+    out.closure, out.riemann = int(p.get("closure", 0)), int(p.get("riemann", 0))
+    out.precision = PRECISION.get(precision, precision) if isinstance(precision, str) else int(precision)
+    out.reserved = 0
+    for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
+        out.inflow[i] = v
+    return out
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One mesh on one GPU: orders, flags and parameters can be changed in place."""
+
+    def __init__(self, hex, geom, geom_degree, params: dict, orders=None, flags=None, bc_tag=None,
+                 precision=0, device=0):
+        L = load()
+        self._hex = np.ascontiguousarray(hex, dtype=np.int64)
+        self._geom = np.ascontiguousarray(geom, dtype=np.float64)
+        self._bc = None if bc_tag is None else np.ascontiguousarray(bc_tag, dtype=np.int8)
+        d = MeshDesc()
+        d.n_elem = self._hex.shape[0]
+        d.hex = self._hex.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.geom_degree = int(geom_degree)
+        d.geom_xyz = self._geom.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.bc_tag = None if self._bc is None else self._bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+        self.params = dict(params)
+        self.precision = precision
+        self._prm = make_params(self.params, precision)
+        h = ctypes.c_void_p()
+        _check(L.dg_create_mesh(ctypes.byref(d), ctypes.byref(self._prm), int(device), ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        self.n_elem = d.n_elem
+        if orders is not None:
+            self.set_orders(orders)
+        if flags is not None:
+            self.set_flags(flags)
+
+    @classmethod
+    def from_workload(cls, w, precision=0, device=0, params=None):
+        m = w.mesh
+        return cls(m.hex, m.geom, m.geom_degree, params or w.params, w.orders, w.flags, m.bc_tag,
+                   precision=precision, device=device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- configuration ----------------------------------------------------------------
+    def set_orders(self, orders):
+        o = np.ascontiguousarray(orders, dtype=np.int8)
+        assert o.size == self.n_elem
+        _check(load().dg_set_orders(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))))
+
+    def set_flags(self, flags):
+        f = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert f.size == self.n_elem
+        _check(load().dg_set_element_flags(self.h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def set_params(self, params: dict = None, precision=None):
+        if params is not None:
+            self.params = dict(params)
+        if precision is not None:
+            self.precision = precision
+        self._prm = make_params(self.params, self.precision)
+        _check(load().dg_set_params(self.h, ctypes.byref(self._prm)))
+
+    @property
+    def total_nodes(self) -> int:
+        t = ctypes.c_int64()
+        _check(load().dg_get_layout(self.h, ctypes.byref(t), None))
+        return t.value
+
+    @property
+    def offsets(self) -> np.ndarray:
+        t = ctypes.c_int64()
+        p = _i64p()
+        _check(load().dg_get_layout(self.h, ctypes.byref(t), ctypes.byref(p)))
+        return np.ctypeslib.as_array(p, shape=(self.n_elem + 1,)).copy()
+
+    # ---- compute ----------------------------------------------------------------------
+    def node_coords(self):
+        import torch
+        xyz = torch.empty((3, self.total_nodes), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(load().dg_node_coords(self.h, _dev_ptr(xyz, "xyz"), _stream_handle(None)))
+        return xyz
+
+    def residual(self, q, R=None, stream=None):
+        import torch
+        if R is None:
+            R = torch.empty_like(q)
+        _check(load().dg_residual(self.h, _dev_ptr(q, "q"), _dev_ptr(R, "R"), _stream_handle(stream)))
+        return R
+
+    def rk_step(self, q, g, dt, nsteps=1, t=0.0, stream=None):
+        _check(load().dg_rk_step(self.h, _dev_ptr(q, "q"), _dev_ptr(g, "g"), float(t), float(dt), int(nsteps),
+                                 _stream_handle(stream)))
+
+    def residual_host(self, q, R, stream=None):
+        """q, R: host arrays (numpy or pinned CPU tensors), float64 [4][total]."""
+        _check(load().dg_residual_host(self.h, _host_ptr(q), _host_ptr(R), _stream_handle(stream)))
+
+    def rk_step_host(self, q, g, dt, nsteps=1, t=0.0, stream=None):
+        _check(load().dg_rk_step_host(self.h, _host_ptr(q), _host_ptr(g), float(t), float(dt), int(nsteps),
+                                      _stream_handle(stream)))
+
+    def conservation(self, R, stream=None):
+        out = (ctypes.c_double * 4)()
+        _check(load().dg_conservation(self.h, _dev_ptr(R, "R"), out, _stream_handle(stream)))
+        return np.array(list(out))
+
+    PHASES = ("traces", "mortar_lift", "viscous", "mortar_flux", "inviscid_update")
+
+    def phase_times(self, q, g, dt, reps=3, stream=None):
+        """Mean milliseconds per phase over `reps` RK stages (advances q, g)."""
+        out = (ctypes.c_double * 5)()
+        _check(load().dg_phase_times(self.h, _dev_ptr(q, "q"), _dev_ptr(g, "g"), float(dt), int(reps), out,
+                                     _stream_handle(stream)))
+        return dict(zip(self.PHASES, list(out)))
+
+    def phase_bytes(self):
+        out = (ctypes.c_double * 5)()
+        _check(load().dg_phase_bytes(self.h, out))
+        return dict(zip(self.PHASES, list(out)))
+
+    def check_device(self, stream=None):
+        _check(load().dg_check_device(self.h, _stream_handle(stream)))
+
+    @property
+    def launches_per_residual(self):
+        return load().dg_launches_per_residual(self.h)
+
+    @property
+    def launches_per_step(self):
+        return load().dg_launches_per_step(self.h)
+
+
+def _host_ptr(a):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("host array must be C-contiguous float64")
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous():
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("host array must be a float64 numpy array or CPU tensor")

@@ -266,6 +266,16 @@ def kraichnan_modes(seed, lengths, nmodes=64, kmin=None, kmax=None, rms=0.05):
 
 
 def fourier_velocity(modes: FourierModes, xyz, chunk=1 << 22):
+    """Velocity of the Fourier modes at points xyz [3][T] (numpy array or torch tensor)."""
+    if hasattr(xyz, "device") and hasattr(xyz, "dtype") and not isinstance(xyz, np.ndarray):
+        import torch
+        k = torch.as_tensor(modes.k, dtype=xyz.dtype, device=xyz.device)
+        amp = torch.as_tensor(modes.amp, dtype=xyz.dtype, device=xyz.device)
+        ph = torch.as_tensor(modes.phase, dtype=xyz.dtype, device=xyz.device)
+        out = torch.zeros((3, xyz.shape[1]), dtype=xyz.dtype, device=xyz.device)
+        for m in range(k.shape[0]):
+            out += amp[m][:, None] * torch.cos(k[m] @ xyz + ph[m])[None, :]
+        return out
     x = np.asarray(xyz)
     out = np.zeros((3, x.shape[1]))
     for s in range(0, x.shape[1], chunk):
@@ -427,8 +437,12 @@ def mixed_64x64x64_n4(n=64, order=4, y_wall=0.2, r_wake=0.4, all_ns=False, all_e
     modes = kraichnan_modes(seed, (8.0, 4.0, 4.0), nmodes=64, kmin=2 * np.pi / 4.0, kmax=np.pi * n / 4.0)
 
     def state(xyz, e, l):
-        q = np.zeros((4, xyz.shape[1]))
-        q[1:] = fourier_velocity(modes, xyz)
+        v = fourier_velocity(modes, xyz)
+        if isinstance(v, np.ndarray):
+            q = np.zeros((4, v.shape[1]))
+        else:
+            q = v.new_zeros((4, v.shape[1]))
+        q[1:] = v
         q[1] += 1.0
         return q
 
