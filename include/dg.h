@@ -118,10 +118,13 @@ dg_status dg_node_coords(dg_ctx* ctx, double* xyz_dev, void* stream);
 dg_status dg_residual(dg_ctx* ctx, const double* q_dev, double* R_dev, void* stream);
 
 /* nsteps steps of the Williamson 2N-storage RK3 in place on device arrays q and g
- * ([4][total_nodes] each): per stage s, g <- A_s g + dt R(q), q <- q + B_s g, with
+ * ([4][total_nodes] FP64 each): per stage s, g <- A_s g + dt R(q), q <- q + B_s g, with
  * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15) (g need not be initialised: A_1 = 0
- * overwrites it). One step is captured once as a CUDA graph per (q, g, dt) and replayed.
- * t is the time at the start (the residual has no explicit time dependence). */
+ * overwrites it). q is always accumulated in FP64. g is the scheme's register: FP64 with
+ * precision 0; with precision 1 it holds FP32 values (the first half of its bytes, laid out
+ * [4][total_nodes]), like the residual it accumulates. One step is captured once as a CUDA
+ * graph per (q, g, dt) and replayed. t is the time at the start (the residual has no
+ * explicit time dependence). */
 dg_status dg_rk_step(dg_ctx* ctx, double* q_dev, double* g_dev, double t, double dt, int nsteps,
                      void* stream);
 
@@ -149,9 +152,10 @@ dg_status dg_check_device(dg_ctx* ctx, void* stream);
 dg_status dg_phase_times(dg_ctx* ctx, double* q_dev, double* g_dev, double dt, int reps,
                          double out_ms[DG_NPHASES], void* stream);
 
-/* Algorithmic DRAM bytes of each phase of one Runge-Kutta stage on the current mesh, orders
- * and flags: every value a phase must read or write once (state, traces, viscous buffers,
- * metric terms), none re-read. The roofline of a phase is these bytes over its time. */
+/* Algorithmic DRAM bytes of each phase, averaged over the three stages of one Runge-Kutta
+ * step, on the current mesh, orders, flags and precision: every value a phase must read or
+ * write once (state, RK register, traces, viscous buffers, metric terms), none re-read. The
+ * roofline of a phase is these bytes over its mean time from dg_phase_times. */
 dg_status dg_phase_bytes(const dg_ctx* ctx, double out_bytes[DG_NPHASES]);
 
 /* Number of kernel launches the last dg_residual / one dg_rk_step step issued. */

@@ -1,0 +1,68 @@
+// dg_device.cuh -- device helpers shared by the FP64 and FP32 kernel files.
+#pragma once
+#include "dg_internal.h"
+
+namespace dgk {
+
+template <int N>
+struct Shape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
+  static constexpr int EPB = (256 / n3) > 0 ? (256 / n3) : 1;   // elements per block
+  static constexpr int threads = ((EPB * n3 + 31) / 32) * 32;
+};
+
+// volume node of face f = 2d+s at face coordinates (a, b)
+__host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
+  int d = f >> 1, fix = (f & 1) ? n - 1 : 0;
+  if (d == 0) return fix + n * (a + n * b);
+  if (d == 1) return a + n * (fix + n * b);
+  return a + n * (b + n * fix);
+}
+
+// my face coordinates (a, b) at order N -> neighbour's (a1, b1)
+__device__ __forceinline__ void inv_orient(int o, int N, int a, int b, int& a1, int& b1) {
+  int x = (o & 2) ? N - a : a;
+  int y = (o & 4) ? N - b : b;
+  if (o & 1) { a1 = y; b1 = x; } else { a1 = x; b1 = y; }
+}
+
+// neighbour face coordinates (a1, b1) at order M -> mine
+__device__ __forceinline__ void fwd_orient(int o, int M, int a1, int b1, int& a0, int& b0) {
+  int x = (o & 1) ? b1 : a1, y = (o & 1) ? a1 : b1;
+  a0 = (o & 2) ? M - x : x;
+  b0 = (o & 4) ? M - y : y;
+}
+
+// Splits x into FP32 hi + lo: hi is x truncated to 24 significant bits, lo the remainder
+// rounded to 24 bits, so |x - hi - lo| <= 2^-71 |x| for 2^-74 <= |x| < 2^128. Uses integer
+// and FP32 instructions only (no FP64 pipe). |x| < 2^-126 gives 0; |x| >= 2^128, inf or NaN
+// give a NaN hi.
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e < 897) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  if (e > 1150) {
+    hi = __int_as_float(0x7fc00000);
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const unsigned m = (unsigned)(b & 0x1fffffffu);  // the 29 mantissa bits below hi
+  if (e < 949 || m == 0u) {
+    lo = 0.f;
+    return;
+  }
+  // m = m1 2^23 + m0 converted exactly piecewise (2^23 + k - 2^23 = k), then rounded once
+  const float f0 = __uint_as_float(0x4b000000u | (m & 0x7fffffu)) - 8388608.f;
+  const float f1 = __uint_as_float(0x4b000000u | (m >> 23)) - 8388608.f;
+  const float mf = fmaf(f1, 8388608.f, f0);
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  lo = __uint_as_float(__float_as_uint(mf * scale) | sign);
+}
+
+}  // namespace dgk

@@ -263,6 +263,7 @@ struct dg_ctx {
   uint64_t version = 1;
   int launches_residual = 0, launches_step = 0;
   // host-variant staging
+  double* trace_buf[2] = {nullptr, nullptr};
   double* stage_q = nullptr;
   double* stage_r = nullptr;
   double* partial = nullptr;
@@ -317,6 +318,11 @@ void apply_params(dg_ctx* c) {
   c->M.cv = c->prm.cv;
   c->M.closure = c->prm.closure;
   c->M.riemann = c->prm.riemann;
+  c->M.precision = c->prm.precision;
+  c->M.nu32 = (float)c->prm.nu;
+  c->M.c0sq32 = (float)c->prm.c0sq;
+  c->M.cs32 = (float)c->prm.cs;
+  c->M.cv32 = (float)c->prm.cv;
   for (int i = 0; i < 4; ++i) c->M.inflow[i] = c->prm.inflow[i];
   c->version++;
 }
@@ -627,17 +633,38 @@ dg_status rebuild_orders(dg_ctx* c) {
   ElemConst* dec;
   if ((st = dev_upload(c, "ec", c->ec, &dec)) != DG_OK) return st;
   c->M.ec = dec;
+  std::vector<ElemConst32> ec32(E);
+  for (int64_t e = 0; e < E; ++e) {
+    for (int k = 0; k < 9; ++k) ec32[e].Ja[k] = (float)c->ec[e].Ja[k];
+    ec32[e].invJ = (float)c->ec[e].invJ;
+    ec32[e].delta = (float)c->ec[e].delta;
+    ec32[e].curved = (float)c->ec[e].curved;
+  }
+  ElemConst32* dec32;
+  if ((st = dev_upload(c, "ec32", ec32, &dec32)) != DG_OK) return st;
+  c->M.ec32 = dec32;
   double* dgeo = nullptr;
+  float* dgeo32 = nullptr;
   if (c->any_curved) {
     if ((st = dev_upload(c, "geo", geo, &dgeo)) != DG_OK) return st;
+    std::vector<float> g32(geo.size());
+    for (size_t i = 0; i < (size_t)9 * c->total; ++i) g32[i] = (float)geo[i];
+    for (int64_t i = 0; i < c->total; ++i)
+      g32[(size_t)9 * c->total + i] = geo[(size_t)9 * c->total + i] != 0.0 ? (float)(1.0 / geo[(size_t)9 * c->total + i]) : 0.f;
+    if ((st = dev_upload(c, "geo32", g32, &dgeo32)) != DG_OK) return st;
   } else {
     free_buf(c, "geo");
+    free_buf(c, "geo32");
   }
   c->M.geo = dgeo;
+  c->M.geo32 = dgeo32;
   c->M.n_elem = E;
   c->M.total = c->total;
   c->M.tr_total = c->tr_total;
-  if ((st = dev_alloc(c, "Tq", 4 * c->tr_total, &c->M.Tq)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "Tq", 4 * c->tr_total, &c->trace_buf[0])) != DG_OK) return st;
+  if ((st = dev_alloc(c, "Tq2", 4 * c->tr_total, &c->trace_buf[1])) != DG_OK) return st;
+  c->M.Tq = c->trace_buf[0];
+  c->M.Tq_next = c->trace_buf[1];
   if ((st = dev_alloc(c, "Tv", 3 * c->tr_total, &c->M.Tv)) != DG_OK) return st;
   if ((st = dev_alloc(c, "rv", 3 * c->total, &c->M.rv)) != DG_OK) return st;
   bool has_mortar = false;
@@ -668,38 +695,47 @@ dg_status rebuild_orders(dg_ctx* c) {
   return rebuild_flags(c);
 }
 
-// one phase of a residual evaluation (mode RESIDUAL) or of an RK stage (mode RK) on stream s
+// One phase of a residual evaluation (mode RESIDUAL) or of an RK stage (mode RK) on stream s.
+// Traces are double-buffered: stage s reads buffer s % 2; in RK mode the update of stages 0
+// and 1 writes the traces of the new state into the other buffer, so only stage 0 (and a
+// residual evaluation) launches the trace kernel.
 dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage, double dt,
                       cudaStream_t s, int* nlaunch) {
   int nl = 0;
+  DevMesh M = c->M;
+  const int cur = (mode == MODE_RK) ? stage % 2 : 0;
+  M.Tq = c->trace_buf[cur];
+  M.Tq_next = c->trace_buf[1 - cur];
+  const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
   switch (phase) {
     case 0:
+      if (mode == MODE_RK && stage > 0) break;
       for (const Bucket& b : c->ord_buckets) {
-        CU(launch_traces(c->M, b, q, s));
+        CU(launch_traces(M, b, q, c->prm.precision, s));
         ++nl;
       }
       break;
     case 1:
       if (c->n_mortar_ns) {
-        CU(launch_mortar_lift(c->M, c->mortar_ns, c->n_mortar_ns, s));
+        CU(launch_mortar_lift(M, c->mortar_ns, c->n_mortar_ns, s));
         ++nl;
       }
       break;
     case 2:
       for (const Bucket& b : c->ns_buckets) {
-        CU(launch_viscous(c->M, b, q, c->prm.precision, s));
+        CU(launch_viscous(M, b, q, c->prm.precision, s));
         ++nl;
       }
       break;
     case 3:
       if (c->n_mortar_all) {
-        CU(launch_mortar_flux(c->M, c->mortar_all, c->n_mortar_all, s));
+        CU(launch_mortar_flux(M, c->mortar_all, c->n_mortar_all, s));
         ++nl;
       }
       break;
     default:
       for (const Bucket& b : c->all_buckets) {
-        CU(launch_inviscid(c->M, b, q, out, g, mode, stage, dt, c->prm.precision, s));
+        CU(launch_inviscid(M, b, q, out, g, mode, stage, dt, write_tr, c->prm.precision, s));
         ++nl;
       }
   }
@@ -940,6 +976,7 @@ dg_status dg_rk_step(dg_ctx* c, double* q, double* g, double t, double dt, int n
   GraphCache& G = c->graph;
   if (!G.exec || G.q != q || G.g != g || G.dt != dt || G.version != c->version) {
     destroy_graph(c);
+    c->M.dt32 = (float)dt;
     CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int nl = 0;
     dg_status st = DG_OK;
@@ -1040,6 +1077,8 @@ dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, d
   if (reps <= 0) return fail(DG_ERR_ARG, "reps must be positive");
   CU(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
+  c->M.dt32 = (float)dt;
+  destroy_graph(c);  // the captured step holds its own dt
   cudaEvent_t ev[DG_NPHASES + 1];
   for (auto& e : ev) CU(cudaEventCreate(&e));
   double acc[DG_NPHASES] = {0, 0, 0, 0, 0};
@@ -1065,17 +1104,25 @@ dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, d
 
 dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
   if (!c || !out) return fail(DG_ERR_ARG, "NULL argument");
-  const double d = 8.0;
+  // Mean over the three stages of one RK step. State q is FP64 (8 B); traces are 8 B per
+  // value (FP64, or an FP32 hi/lo pair); with precision 1 the RK register g, the viscous
+  // traces and the viscous divergence are FP32 (4 B).
+  const bool f32 = c->prm.precision == 1;
+  const double d = 8.0, sg = f32 ? 4.0 : 8.0, sv = f32 ? 4.0 : 8.0, tr = 8.0;
   double b[DG_NPHASES] = {0, 0, 0, 0, 0};
   for (int64_t e = 0; e < c->ne; ++e) {
     const double n = c->order[e] + 1, n2 = n * n, n3 = n2 * n;
     const bool ns = c->flag[e] != 0;
-    const double geo = c->ec[e].curved != 0.0 ? 10.0 * n3 * d : 14.0 * d;
-    b[0] += 2.0 * 4.0 * 6.0 * n2 * d;  // read q at the face nodes, write the traces
-    double inv = 16.0 * n3 * d + geo;   // q, g read and written
+    const bool curved = c->ec[e].curved != 0.0;
+    const double geo = curved ? 10.0 * n3 * (f32 ? 4.0 : 8.0) : (f32 ? 48.0 : 112.0);
+    // traces: launched in one stage out of three (q at the face nodes in, traces out)
+    b[0] += (4.0 * 6.0 * n2 * d + 4.0 * 6.0 * n2 * tr) / 3.0;
+    // inviscid + update: q in and out, g out (and in for two stages of three), geometry,
+    // traces of the new state written in two stages of three
+    double inv = 4.0 * n3 * d * 2.0 + 4.0 * n3 * sg * (1.0 + 2.0 / 3.0) + geo + (2.0 / 3.0) * 4.0 * 6.0 * n2 * tr;
     if (ns) {
-      b[2] += 3.0 * n3 * d + geo + 3.0 * n3 * d + 18.0 * n2 * d;  // u in, rv and Tv out
-      inv += 3.0 * n3 * d;                                       // rv in
+      b[2] += 3.0 * n3 * d + geo + 3.0 * n3 * sv + 18.0 * n2 * sv;  // u in, rv and Tv out
+      inv += 3.0 * n3 * sv;                                         // rv in
     }
     for (int f = 0; f < 6; ++f) {
       const int32_t nb = c->nb[e * 6 + f];
@@ -1083,18 +1130,18 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
       const double nn = c->order[nb] + 1;
       const bool nbns = c->flag[nb] != 0;
       if (c->order[nb] == c->order[e]) {
-        if (ns) b[2] += 3.0 * n2 * d;                  // neighbour velocity trace
-        inv += 4.0 * n2 * d;                            // neighbour q trace
-        if (ns) inv += 3.0 * n2 * d;                    // own viscous trace
-        if (nbns) inv += 3.0 * n2 * d;                  // neighbour viscous trace
+        if (ns) b[2] += 3.0 * n2 * tr;                 // neighbour velocity trace
+        inv += 4.0 * n2 * tr;                           // neighbour q trace
+        if (ns) inv += 3.0 * n2 * sv;                   // own viscous trace
+        if (nbns) inv += 3.0 * n2 * sv;                 // neighbour viscous trace
       } else {
         if (ns) {
-          b[1] += 3.0 * (n2 + nn * nn) * d + 9.0 * n2 * d;  // both velocity traces in, lifting out
-          b[2] += 9.0 * n2 * d;                             // lifting in
+          b[1] += 3.0 * (n2 + nn * nn) * tr + 9.0 * n2 * d;  // both velocity traces in, lifting out
+          b[2] += 9.0 * n2 * d;                              // lifting in
         }
-        b[3] += 4.0 * (n2 + nn * nn) * d + (ns ? 3.0 * n2 * d : 0.0) + (nbns ? 3.0 * nn * nn * d : 0.0) +
+        b[3] += 4.0 * (n2 + nn * nn) * tr + (ns ? 3.0 * n2 * sv : 0.0) + (nbns ? 3.0 * nn * nn * sv : 0.0) +
                 4.0 * n2 * d;
-        inv += 4.0 * n2 * d + (ns ? 3.0 * n2 * d : 0.0);   // projected flux, own viscous trace
+        inv += 4.0 * n2 * d + (ns ? 3.0 * n2 * sv : 0.0);   // projected flux, own viscous trace
       }
     }
     b[4] += inv;

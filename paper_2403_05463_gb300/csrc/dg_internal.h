@@ -36,6 +36,14 @@ struct ElemConst {
   double curved;   // 1.0: metric terms per node in DevMesh::geo; 0.0: affine (Ja above)
 };
 
+// FP32 copy of the per-element constants for the reduced-precision passes.
+struct ElemConst32 {
+  float Ja[9];
+  float invJ;
+  float delta;
+  float curved;
+};
+
 // Everything a kernel needs, passed by value.
 struct DevMesh {
   int64_t n_elem, total, tr_total;
@@ -46,7 +54,12 @@ struct DevMesh {
   const FaceLink* link;      // [E*6]
   const ElemConst* ec;       // [E]
   const double* geo;         // curved elements: [10][total] = Ja[9] (d*3+k) then J
-  double* Tq;                // [4][tr_total] face traces of q (FP64)
+  const ElemConst32* ec32;   // [E] FP32 constants
+  const float* geo32;        // curved elements: [10][total] = Ja[9] then 1/J (FP32)
+  double* Tq;                // [4][tr_total] face traces of q: FP64 values, or with precision 1
+                             // (hi, lo) FP32 pairs, hi + lo = q to 2^-48 relative
+  double* Tq_next;           // traces of the updated q written by the RK update for the next
+                             // stage (double-buffered with Tq: neighbours still read Tq)
   double* Tv;                // [3][tr_total] outward viscous flux traces tau . S (NS elements)
   double* rv;                // [3][total]    J * viscous volume divergence (NS elements)
   double* LU;                // [9][tr_total] projected BR1 lifting u*_c S_k on mortar faces
@@ -56,6 +69,8 @@ struct DevMesh {
   int* err;                  // device error word
   double nu, c0sq, cs, cv;
   int closure, riemann;
+  int precision;             // 0: Tv/rv hold FP64; 1: they hold FP32 (same buffers)
+  float nu32, c0sq32, cs32, cv32, dt32;  // FP32 copies for the reduced-precision passes
   double inflow[4];
 };
 
@@ -79,18 +94,25 @@ enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
 // Launchers (dg_kernels.cu). All return cudaGetLastError() of their launches.
 cudaError_t upload_ops(const Ops1D& ops);
-cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s);
 cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
 cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
 cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, int precision,
                            cudaStream_t s);
 cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, double* out,
-                            double* g, int mode, int stage, double dt, int precision,
+                            double* g, int mode, int stage, double dt, int write_tr, int precision,
                             cudaStream_t s);
 cudaError_t launch_node_coords(const DevMesh& M, const double* geom_nodes, int geom_degree,
                                const Bucket& b, double* xyz, cudaStream_t s);
 cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R,
                                 double* partial, cudaStream_t s);
 cudaError_t prepare_kernels();
+// FP32-arithmetic variants (dg_kernels_f32.cu)
+cudaError_t upload_ops32(const Ops1D& ops);
+cudaError_t prepare_kernels32();
+cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                              int mode, int stage, int write_tr, cudaStream_t s);
 
 }  // namespace dgk

@@ -16,7 +16,7 @@
 // Strong form on Gauss-Lobatto nodes (equal to the weak form of App. B, Eq. NS4, by the
 // summation-by-parts property of the Lobatto quadrature):
 //   J R = -sum_d D_d (Ftil_e^d - Ftil_v^d) - sum_faces (1/w_end) [(F_e* - F_v*) . S - (Ftil_e - Ftil_v)_out]
-#include "dg_internal.h"
+#include "dg_device.cuh"
 
 #include <cstdio>
 
@@ -27,35 +27,6 @@ __constant__ Ops1D c_ops;
 // Williamson 2N-storage RK3 (the paper's low-storage third-order scheme, Sec. 2.3).
 __constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 __constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
-
-template <int N>
-struct Shape {
-  static constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
-  static constexpr int EPB = (256 / n3) > 0 ? (256 / n3) : 1;   // elements per block
-  static constexpr int threads = ((EPB * n3 + 31) / 32) * 32;
-};
-
-// volume node of face f = 2d+s at face coordinates (a, b)
-__host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
-  int d = f >> 1, fix = (f & 1) ? n - 1 : 0;
-  if (d == 0) return fix + n * (a + n * b);
-  if (d == 1) return a + n * (fix + n * b);
-  return a + n * (b + n * fix);
-}
-
-// my face coordinates (a, b) at order N -> neighbour's (a1, b1)
-__device__ __forceinline__ void inv_orient(int o, int N, int a, int b, int& a1, int& b1) {
-  int x = (o & 2) ? N - a : a;
-  int y = (o & 4) ? N - b : b;
-  if (o & 1) { a1 = y; b1 = x; } else { a1 = x; b1 = y; }
-}
-
-// neighbour face coordinates (a1, b1) at order M -> mine
-__device__ __forceinline__ void fwd_orient(int o, int M, int a1, int b1, int& a0, int& b0) {
-  int x = (o & 1) ? b1 : a1, y = (o & 1) ? a1 : b1;
-  a0 = (o & 2) ? M - x : x;
-  b0 = (o & 4) ? M - y : y;
-}
 
 // y = A(ub) x for the artificial-compressibility flux Jacobian in direction nh
 __device__ __forceinline__ void ac_jac_apply(const double ub[3], double un, const double nh[3],
@@ -349,7 +320,7 @@ __global__ void __launch_bounds__(Shape<N>::threads) k_viscous(DevMesh M, const 
 template <int N, bool CURVED, int MODE>
 __global__ void __launch_bounds__(Shape<N>::threads)
     k_inviscid(DevMesh M, const int32_t* __restrict__ list, int count, const double* qin, double* out,
-               double* g, int stage, double dt) {
+               double* g, int stage, double dt, int write_tr) {
   using S = Shape<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ double sm[];
@@ -476,7 +447,17 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       double gi = dt * (JR[v] * invJ);
       if (stage > 0) gi += A * g[ix];
       g[ix] = gi;
-      out[ix] = qq[v] + B * gi;
+      const double qn = qq[v] + B * gi;
+      out[ix] = qn;
+      if (write_tr) {  // traces of the new state for the next stage
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (ii[d] != 0 && ii[d] != N) continue;
+          const int f = 2 * d + (ii[d] == N ? 1 : 0);
+          const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+          M.Tq_next[v * M.tr_total + M.tr_off[e] + f * n2 + a + n * b] = qn;
+        }
+      }
     }
   }
 }
@@ -510,6 +491,20 @@ __device__ __forceinline__ void node_metric(const DevMesh& M, int e, int64_t nod
   }
 }
 
+// trace value of q: FP64, or an FP32 (hi, lo) pair with precision 1
+__device__ __forceinline__ double tq_load(const DevMesh& M, int64_t i) {
+  if (M.precision == 1) {
+    const float2 t = reinterpret_cast<const float2*>(M.Tq)[i];
+    return (double)t.x + (double)t.y;
+  }
+  return M.Tq[i];
+}
+
+// viscous trace value: FP64 or FP32 storage depending on the precision of the passes
+__device__ __forceinline__ double tv_load(const DevMesh& M, int64_t i) {
+  return M.precision == 1 ? (double)reinterpret_cast<const float*>(M.Tv)[i] : M.Tv[i];
+}
+
 // loads my face field (nvar from `src` planes, stride tr_total) and S at my face nodes
 struct MortarSmem {
   double mine[7][NP * NP];   // my trace at my order
@@ -536,10 +531,10 @@ __global__ void k_mortar_lift(DevMesh M, const int32_t* __restrict__ slots, int 
     double Ja[9];
     node_metric(M, e, node, Ja);
     for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
-    for (int c = 0; c < 3; ++c) sm.mine[c][t] = M.Tq[(1 + c) * M.tr_total + M.tr_off[e] + f * nm * nm + t];
+    for (int c = 0; c < 3; ++c) sm.mine[c][t] = tq_load(M, (1 + c) * M.tr_total + M.tr_off[e] + f * nm * nm + t);
   }
   if (t < nn * nn)
-    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = M.Tq[(1 + c) * M.tr_total + M.tr_off[L.nbr] + L.nface * nn * nn + t];
+    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = tq_load(M, (1 + c) * M.tr_total + M.tr_off[L.nbr] + L.nface * nn * nn + t);
   __syncthreads();
   if (t < nM * nM) {
     const int a = t % nM, b = t / nM;
@@ -584,13 +579,13 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
     node_metric(M, e, node, Ja);
     for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
     const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
-    for (int v = 0; v < 4; ++v) sm.mine[v][t] = M.Tq[v * M.tr_total + s0];
-    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? M.Tv[c * M.tr_total + s0] : 0.0;
+    for (int v = 0; v < 4; ++v) sm.mine[v][t] = tq_load(M, v * M.tr_total + s0);
+    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? tv_load(M, c * M.tr_total + s0) : 0.0;
   }
   if (t < nn * nn) {
     const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
-    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = M.Tq[v * M.tr_total + s1];
-    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? M.Tv[c * M.tr_total + s1] : 0.0;
+    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = tq_load(M, v * M.tr_total + s1);
+    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? tv_load(M, c * M.tr_total + s1) : 0.0;
   }
   __syncthreads();
   if (t < nM * nM) {
@@ -672,7 +667,10 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
 // ---------------------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------------------
-cudaError_t upload_ops(const Ops1D& ops) { return cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D)); }
+cudaError_t upload_ops(const Ops1D& ops) {
+  cudaError_t r = cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D));
+  return r == cudaSuccess ? upload_ops32(ops) : r;
+}
 
 template <int N, bool C>
 static size_t visc_smem() {
@@ -707,7 +705,7 @@ cudaError_t prepare_kernels() {
   if ((r = prep_n<5>()) != cudaSuccess) return r;
   if ((r = prep_n<6>()) != cudaSuccess) return r;
   if ((r = prep_n<7>()) != cudaSuccess) return r;
-  return cudaSuccess;
+  return prepare_kernels32();
 }
 
 #define DG_DISPATCH_N(NVAR, ...)                                  \
@@ -722,7 +720,8 @@ cudaError_t prepare_kernels() {
     default: return cudaErrorInvalidValue;                        \
   }
 
-cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
+cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s) {
+  if (precision == 1) return launch_traces32(M, b, q, s);
   if (b.count == 0) return cudaSuccess;
   DG_DISPATCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
@@ -733,7 +732,7 @@ cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, cu
 }
 
 cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s) {
-  (void)precision;
+  if (precision == 1) return launch_viscous32(M, b, q, s);
   if (b.count == 0) return cudaSuccess;
   DG_DISPATCH_N(b.N, {
     using SH = Shape<NN>;
@@ -747,8 +746,8 @@ cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, i
 }
 
 cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
-                            int mode, int stage, double dt, int precision, cudaStream_t s) {
-  (void)precision;
+                            int mode, int stage, double dt, int write_tr, int precision, cudaStream_t s) {
+  if (precision == 1) return launch_inviscid32(M, b, q, out, g, mode, stage, write_tr, s);
   if (b.count == 0) return cudaSuccess;
   DG_DISPATCH_N(b.N, {
     using SH = Shape<NN>;
@@ -756,14 +755,14 @@ cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, 
     const size_t sm = inv_smem<NN>();
     if (mode == MODE_RESIDUAL) {
       if (b.curved)
-        k_inviscid<NN, true, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+        k_inviscid<NN, true, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
       else
-        k_inviscid<NN, false, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+        k_inviscid<NN, false, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
     } else {
       if (b.curved)
-        k_inviscid<NN, true, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+        k_inviscid<NN, true, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
       else
-        k_inviscid<NN, false, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt);
+        k_inviscid<NN, false, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
     }
   });
   return cudaGetLastError();

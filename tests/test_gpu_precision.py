@@ -1,0 +1,111 @@
+"""Reduced-precision path (FP32 arithmetic, FP64 state/traces/RK accumulation) against the
+FP64 oracle: every result reports its relative L2 error (printed, and appended to
+gpurun_out/precision_errors.jsonl when that folder exists) and must stay within its
+regression bound below.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from helpers import gpu_solver, oracle_mesh, oracle_state, rel_l2, small_mixed, to_dev
+from paper_2403_05463_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+# Regression bounds per case, about 3x the measured FP32 error. The error is set by the
+# conditioning of the residual (largest for R_p = -c0^2 div u of divergence-free fields,
+# where c0^2 |u| |D| / |R_p| is 1e2..1e4); the 1e-6 target holds only where that is small.
+BOUNDS = {
+    "tgv_4x4x4_n3": 3e-5, "wake_16x16x16_n4": 1e-6, "tgv_8x8x8_n5_slab30": 6e-6,
+    "padapt_6x6x6_curved": 1.5e-5, "tgv_5x5x5_n1_vreman_llf": 1e-6, "tgv_5x5x5_n2_vreman_llf": 5e-6,
+    "tgv_5x5x5_n6_vreman_llf": 3e-4, "tgv_5x5x5_n7_vreman_llf": 3e-4,
+    "tgv_4x4x4_n3_rk3_10_steps_update": 7e-6, "mixed_64x64x64_n4_sampled": 1e-4,
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _record(name, err):
+    print(f"{name}: FP32 relative L2 error vs FP64 oracle = {err:.3e}")
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(d):
+        with open(os.path.join(d, "precision_errors.jsonl"), "a") as f:
+            f.write(json.dumps({"case": name, "rel_l2": err}) + "\n")
+
+
+def _fp32_error(w, params=None):
+    M = oracle_mesh(w, params)
+    q = oracle_state(w, M)
+    R_ref = M.residual(q)
+    S = gpu_solver(w, precision=1, params=params)
+    R = S.residual(to_dev(q)).cpu().numpy()
+    return rel_l2(R, R_ref)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("tgv_4x4x4_n3", lambda: wl.tgv_4x4x4_n3()),
+    ("wake_16x16x16_n4", lambda: wl.wake_16x16x16_n4()),
+    ("tgv_8x8x8_n5_slab30", lambda: wl.tgv_32x32x32_n5(n=8)),
+    ("padapt_6x6x6_curved", lambda: wl.padapt_32x32x32(n=6)),
+])
+def test_fp32_residual_error(name, make):
+    err = _fp32_error(make())
+    _record(name, err)
+    assert err <= BOUNDS[name], err
+
+
+def test_fp32_every_order_and_vreman_llf():
+    for N in (1, 2, 6, 7):
+        w = small_mixed(wl.tgv_4x4x4_n3(n_elem_dir=5, order=N), seed=20 + N)
+        err = _fp32_error(w, params=dict(w.params, nu=1e-2, closure=1, riemann=1))
+        _record(f"tgv_5x5x5_n{N}_vreman_llf", err)
+        assert err <= BOUNDS[f"tgv_5x5x5_n{N}_vreman_llf"], (N, err)
+
+
+def test_fp32_rk3_ten_steps():
+    w = wl.tgv_4x4x4_n3()
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    q0 = q.copy()
+    g = np.zeros_like(q)
+    qd, gd = to_dev(q), to_dev(g)
+    S = gpu_solver(w, precision=1)
+    S.rk_step(qd, gd, w.dt, w.steps)
+    M.rk_step(q, g, w.dt, w.steps)
+    err = rel_l2(qd.cpu().numpy() - q0, q - q0)  # error of the state change over 10 steps
+    _record("tgv_4x4x4_n3_rk3_10_steps_update", err)
+    assert err <= BOUNDS["tgv_4x4x4_n3_rk3_10_steps_update"]
+
+
+def test_fp32_mixed_full_size_sampled():
+    import torch
+    from test_gpu_parity import _fourier_torch
+    from oracle import oracle as orc
+    w = wl.mixed_64x64x64_n4()
+    M = oracle_mesh(w)
+    xyz = torch.from_numpy(M.node_coords()).cuda()
+    q = torch.zeros((4, M.total), dtype=torch.float64, device="cuda")
+    q[1:] = _fourier_torch(w, xyz)
+    q[1] += 1.0
+    del xyz
+    S = gpu_solver(w, precision=1)
+    R = S.residual(q).cpu().numpy()
+    qh = q.cpu().numpy()
+    rng = np.random.default_rng(1)
+    sel = np.concatenate([rng.choice(np.flatnonzero(w.flags), 24, replace=False),
+                          rng.choice(np.flatnonzero(w.flags == 0), 24, replace=False)])
+    m = w.mesh
+    Mx = orc.Mesh(m.hex, m.geom, 1, w.orders, w.flags, orc.params(**w.params), m.bc_tag, extended=True)
+    Rx = np.zeros_like(qh)
+    Mx.residual(qh, sel=sel, out=Rx)
+    idx = np.concatenate([np.arange(M.offsets[e], M.offsets[e + 1]) for e in sel])
+    err = rel_l2(R[:, idx], Rx[:, idx])
+    _record("mixed_64x64x64_n4_sampled", err)
+    assert err <= BOUNDS["mixed_64x64x64_n4_sampled"]
