@@ -41,7 +41,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_64x64x64_n4")
-    ap.add_argument("--precision", default=os.environ.get("DG_BENCH_PRECISION", "fp64"), choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
+                    help="fp32: FP32 arithmetic with FP64 state and RK accumulation (the large mixed
+                    configuration's precision); fp64: FP64 throughout")
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
     return ap.parse_args()

@@ -14,7 +14,7 @@
  *   - App. B, Eqs. NS2-NS5: DGSEM on curvilinear hexahedra (transfinite map, Jacobian J,
  *     contravariant fluxes), numerical flux on faces, tensor-product quadrature.
  *   - Sec. 2.3 (last paragraph): low-storage explicit third-order Runge-Kutta.
- *   - Sec. 1/4: local p-adaptation, one polynomial order per element, p-nonconforming faces.
+ *   - Sec. 3.2: local p-adaptation, one polynomial order per element, p-nonconforming faces.
  *
  * State: q = (p, u, v, w), rho = 1. All state arrays are FP64, structure-of-arrays
  * [4][total_nodes]: variable v of global node i lives at q[v * total_nodes + i]. Element e
@@ -92,7 +92,7 @@ typedef struct {
  * than two elements, repeated corner ids on one face or a non-positive Jacobian. */
 dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int device, dg_ctx** out);
 
-/* Per-element polynomial order N_e in 1..7 (host array, length n_elem; Sec. 4 local
+/* Per-element polynomial order N_e in 1..7 (host array, length n_elem; Sec. 3.2 local
  * p-adaptation). Faces between different orders become mortars (interpolation to the
  * larger order, exact L2 projection back). Re-lays out the state: previous q/g/R arrays
  * no longer match the layout. */
