@@ -42,8 +42,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_64x64x64_n4")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
-                    help="fp32: FP32 arithmetic with FP64 state and RK accumulation (the large mixed
-                    configuration's precision); fp64: FP64 throughout")
+                    help="fp32: FP32 arithmetic with FP64 state and FP64 accumulation of q (the large "
+                         "mixed configuration's precision); fp64: FP64 throughout")
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
     return ap.parse_args()

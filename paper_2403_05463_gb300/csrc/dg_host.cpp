@@ -257,6 +257,7 @@ struct dg_ctx {
   int32_t* mortar_ns = nullptr;     // mortar slots of NS elements (lifting)
   int n_mortar_ns = 0;
   std::vector<ElemConst> ec;
+  std::vector<uint8_t> geo_kind;  // 0 axis-aligned box, 1 affine, 2 curved
   bool any_curved = false;
   cudaStream_t cap_stream = nullptr;
   GraphCache graph;
@@ -481,10 +482,10 @@ void destroy_graph(dg_ctx* c) {
 }
 
 void build_buckets(const std::vector<int32_t>& elems, const std::vector<int8_t>& order,
-                   const std::vector<ElemConst>& ec, bool split_curved,
-                   std::vector<std::vector<int32_t>>& lists, std::vector<std::pair<int, bool>>& keys) {
-  std::map<std::pair<int, bool>, std::vector<int32_t>> m;
-  for (int32_t e : elems) m[{order[e], split_curved && ec[e].curved != 0.0}].push_back(e);
+                   const std::vector<uint8_t>& geo_kind, bool split_geo,
+                   std::vector<std::vector<int32_t>>& lists, std::vector<std::pair<int, int>>& keys) {
+  std::map<std::pair<int, int>, std::vector<int32_t>> m;
+  for (int32_t e : elems) m[{order[e], split_geo ? (int)geo_kind[e] : 1}].push_back(e);
   lists.clear();
   keys.clear();
   for (auto& kv : m) {
@@ -496,13 +497,14 @@ void build_buckets(const std::vector<int32_t>& elems, const std::vector<int8_t>&
 dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector<int32_t>& elems, bool split_curved,
                          bool ns, std::vector<Bucket>& out) {
   std::vector<std::vector<int32_t>> lists;
-  std::vector<std::pair<int, bool>> keys;
-  build_buckets(elems, c->order, c->ec, split_curved, lists, keys);
+  std::vector<std::pair<int, int>> keys;
+  build_buckets(elems, c->order, c->geo_kind, split_curved, lists, keys);
   out.clear();
   for (size_t i = 0; i < lists.size(); ++i) {
     Bucket b;
     b.N = keys[i].first;
-    b.curved = keys[i].second;
+    b.geo = keys[i].second;
+    b.curved = b.geo == 2;
     b.ns = ns;
     b.count = (int)lists[i].size();
     dg_status st = dev_upload(c, prefix + std::to_string(i), lists[i], &b.list);
@@ -527,6 +529,10 @@ dg_status rebuild_flags(dg_ctx* c) {
         L.orient = c->nbo[e * 6 + f];
         L.kind = c->order[nb] == c->order[e] ? FK_CONF : FK_MORTAR;
         L.nflag = c->flag[nb];
+        const int64_t nn1 = c->order[nb] + 1;
+        L.nslot = c->troff[nb] + (int64_t)L.nface * nn1 * nn1;
+        if (L.nslot < 0 || L.nslot + nn1 * nn1 > c->tr_total)
+          return fail(DG_ERR_MESH, "internal: trace slot of element %lld face %d out of range", (long long)e, f);
         if (L.kind == FK_MORTAR) {
           mall.push_back((int32_t)(e * 6 + f));
           if (c->flag[e]) mns.push_back((int32_t)(e * 6 + f));
@@ -580,6 +586,7 @@ dg_status rebuild_orders(dg_ctx* c) {
   if (c->total * 4 > INT64_C(1) << 40) return fail(DG_ERR_UNSUPPORTED, "mesh too large");
   // geometry
   c->ec.assign(E, ElemConst{});
+  c->geo_kind.assign(E, 1);
   std::vector<double> geo;
   c->any_curved = false;
   std::vector<ElemGeo> curved_geo;
@@ -597,6 +604,19 @@ dg_status rebuild_orders(dg_ctx* c) {
       k.J = G.J;
       k.invJ = 1.0 / G.J;
       k.curved = 0.0;
+      // axis-aligned box: diagonal metric with positive entries
+      double mx = 0.0, off_diag = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          mx = std::max(mx, std::fabs(G.Ja[i * 3 + j]));
+          if (i != j) off_diag = std::max(off_diag, std::fabs(G.Ja[i * 3 + j]));
+        }
+      if (off_diag <= 1e-14 * mx && G.Ja[0] > 0.0 && G.Ja[4] > 0.0 && G.Ja[8] > 0.0) {
+        c->geo_kind[e] = 0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            if (i != j) k.Ja[i * 3 + j] = 0.0;
+      }
       vol = 8.0 * G.J;
     } else {
       for (int p = 0; p < n3; ++p) {
@@ -604,6 +624,7 @@ dg_status rebuild_orders(dg_ctx* c) {
         vol += r.w[p % n] * r.w[(p / n) % n] * r.w[p / (n * n)] * G.Jn[p];
       }
       k.curved = 1.0;
+      c->geo_kind[e] = 2;
       c->any_curved = true;
       curved_ids.push_back(e);
       curved_geo.push_back(std::move(G));

@@ -25,7 +25,9 @@ struct FaceLink {
   uint8_t orient;  // swap | flip_a << 1 | flip_b << 2: neighbour (a1, b1) -> mine
   uint8_t kind;    // FaceKind
   uint8_t nflag;   // neighbour flag (0 Euler, 1 NS)
+  int64_t nslot;   // first trace slot of the neighbour's face: tr_off[nbr] + nface n_nbr^2
 };
+static_assert(sizeof(FaceLink) == 16, "FaceLink layout is shared by host and device");
 
 // Per-element constants. Affine elements carry their constant metric here; curved elements
 // read per-node metric terms from DevMesh::geo.
@@ -34,6 +36,7 @@ struct ElemConst {
   double J, invJ;  // affine only
   double delta;    // LES filter width: cube root of the element volume / (N + 1)
   double curved;   // 1.0: metric terms per node in DevMesh::geo; 0.0: affine (Ja above)
+  // (the geometry kind used for bucketing -- box, affine, curved -- is kept on the host)
 };
 
 // FP32 copy of the per-element constants for the reduced-precision passes.
@@ -84,7 +87,8 @@ struct Ops1D {
 // Element lists of one kernel launch.
 struct Bucket {
   int N;
-  bool curved;
+  int geo;            // 0 axis-aligned box, 1 affine, 2 curved
+  bool curved;        // geo == 2
   bool ns;            // true: only NS elements (viscous pass)
   int32_t* list;      // device
   int count;

@@ -68,3 +68,11 @@ def test_kraichnan_modes_are_divergence_free_and_scaled():
     L = np.array([8.0, 4.0, 4.0])
     n = m.k * L / (2 * np.pi)
     assert np.abs(n - np.round(n)).max() < 1e-9  # periodic on the box
+
+
+def test_bench_and_entry_compile():
+    import py_compile
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for f in ("bench.py", "__graft_entry__.py"):
+        py_compile.compile(os.path.join(root, f), doraise=True)
