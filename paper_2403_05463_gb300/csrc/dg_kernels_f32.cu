@@ -431,8 +431,9 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 }
 
 // shared-memory layout of k_inviscid32 (floats), per element of the block:
-//   F  [12 n3]  contravariant flux deviations; after the contraction: face terms [6][4][n2]
-//   Q  [8 n3]   hi/lo of q; after the face phase: hi/lo of the updated q
+//   F  [3][n3] float4   contravariant flux deviations (4 variables packed); after the
+//                       contraction: face terms [6][n2] float4
+//   Q  [2][n3] float4   hi, lo of q; after the face phase: hi, lo of the updated q
 //   NT [48 n2]  neighbours' q traces (hi, lo)[6][4][n2] (neighbour face coordinates)
 //   NV [18 n2]  neighbours' viscous traces [6][3][n2];  OV [18 n2] own viscous traces
 //   EC [16]     element constants (Ja, 1/J, delta, kind)
@@ -503,8 +504,9 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
   const bool ns = active && M.flag[e] != 0;
   float* base = sE + le * PE;
   float* F = base + L32::oF;
-  float* QH = base + L32::oQ;
-  float* QL = QH + 4 * n3;
+  float4* F4 = reinterpret_cast<float4*>(F);
+  float4* QH4 = reinterpret_cast<float4*>(base + L32::oQ);
+  float4* QL4 = QH4 + n3;
   float* EC = base + L32::oEC;
   double* QD = reinterpret_cast<double*>(base + L32::oQD);
   const int ii[3] = {p % n, (p / n) % n, p / n2};
@@ -521,18 +523,17 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
     }
     const ElemConst32& ec = M.ec32[e];
     for (int k = p; k < 12; k += n3) EC[k] = k < 9 ? ec.Ja[k] : (k == 9 ? ec.invJ : (k == 10 ? ec.delta : ec.curved));
-    float dq[4], qr32[4];
+    float dq[4], qr32[4], h[4], l[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float h, l;
       const double qv = qin[v * M.total + off + p];
       QD[v * n3 + p] = qv;
-      split_hilo(qv, h, l);
-      QH[v * n3 + p] = h;
-      QL[v * n3 + p] = l;
+      split_hilo(qv, h[v], l[v]);
       qr32[v] = hi_part(qin[v * M.total + off]);  // any per-element constant serves as reference
-      dq[v] = (h - qr32[v]) + l;
+      dq[v] = (h[v] - qr32[v]) + l[v];
     }
+    QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
+    QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
     float fl[4][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -544,9 +545,10 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
     if (GEO == 0) {
       invJ = ec.invJ;
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) F[(d * 4 + v) * n3 + p] = ec.Ja[d * 4] * fl[v][d];
+      for (int d = 0; d < 3; ++d) {
+        const float j = ec.Ja[d * 4];
+        F4[d * n3 + p] = make_float4(j * fl[0][d], j * fl[1][d], j * fl[2][d], j * fl[3][d]);
+      }
     } else {
       float Ja[9];
       if (GEO == 2) {
@@ -559,10 +561,12 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
         invJ = ec.invJ;
       }
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d) {
+        float c4[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          F[(d * 4 + v) * n3 + p] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+        for (int v = 0; v < 4; ++v) c4[v] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+        F4[d * n3 + p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+      }
     }
   }
   cp_async_wait_all();
@@ -577,9 +581,11 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 #pragma unroll
       for (int m = 0; m < n; ++m) {
         const float dm = sD[ii[d] * n + m];
-        const int pm = bs + m * str[d];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) JR[v] -= dm * F[(d * 4 + v) * n3 + pm];
+        const float4 f4 = F4[d * n3 + bs + m * str[d]];
+        JR[0] -= dm * f4.x;
+        JR[1] -= dm * f4.y;
+        JR[2] -= dm * f4.z;
+        JR[3] -= dm * f4.w;
       }
     }
 #pragma unroll
@@ -636,14 +642,10 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
       const float s = GEO == 0 ? fabsf(E2[d * 4]) : sqrtf(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
       const float is = 1.f / s;
       const float nh[3] = {Sv[0] * is, Sv[1] * is, Sv[2] * is};
-      const float* QH2 = b2 + L32::oQ;
-      const float* QL2 = QH2 + 4 * n3;
-      float qh[4], ql[4], dqf[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        qh[v] = QH2[v * n3 + pv];
-        ql[v] = QL2[v * n3 + pv];
-      }
+      const float4 h4 = reinterpret_cast<const float4*>(b2 + L32::oQ)[pv];
+      const float4 l4 = reinterpret_cast<const float4*>(b2 + L32::oQ)[n3 + pv];
+      const float qh[4] = {h4.x, h4.y, h4.z, h4.w}, ql[4] = {l4.x, l4.y, l4.z, l4.w};
+      float dqf[4];
       int nab = 0;
       if (L.kind == FK_CONF) {
         int a1, b1;
@@ -693,22 +695,22 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
         }
       }
     }
-    float* SC = b2 + L32::oF;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) SC[(f * 4 + v) * n2 + ab] = term[v];
+    reinterpret_cast<float4*>(b2 + L32::oF)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
   }
   __syncthreads();
   // ---- assembly and update (node phase) -------------------------------------------------
   const bool on_face = ii[0] == 0 || ii[0] == N || ii[1] == 0 || ii[1] == N || ii[2] == 0 || ii[2] == N;
   if (active) {
-    const float* SC = F;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (ii[d] != 0 && ii[d] != N) continue;
       const int f = 2 * d + (ii[d] == N ? 1 : 0);
       const int a = d == 0 ? ii[1] : ii[0], bb = d == 2 ? ii[1] : ii[2];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) JR[v] -= invw * SC[(f * 4 + v) * n2 + a + n * bb];
+      const float4 sc = F4[f * n2 + a + n * bb];
+      JR[0] -= invw * sc.x;
+      JR[1] -= invw * sc.y;
+      JR[2] -= invw * sc.z;
+      JR[3] -= invw * sc.w;
     }
     if (MODE == MODE_RESIDUAL) {
 #pragma unroll
@@ -718,6 +720,7 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
       const float A = c32_rkA32[stage];
       const double B = c32_rkB[stage];
       const float dtf = M.dt32;
+      float h[4], l[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int64_t ix = v * M.total + off + p;
@@ -725,12 +728,11 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
         g32[ix] = gi;
         const double qn = fma(B, (double)gi, QD[v * n3 + p]);
         out[ix] = qn;
-        if (write_tr && on_face) {
-          float h, l;
-          split_hilo(qn, h, l);
-          QH[v * n3 + p] = h;
-          QL[v * n3 + p] = l;
-        }
+        if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
+      }
+      if (write_tr && on_face) {
+        QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
+        QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
       }
     }
   }
@@ -742,11 +744,14 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
       const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
       if (ebase + le2 >= count) continue;
       const int e2 = list[ebase + le2];
-      const float* QH2 = sE + le2 * PE + L32::oQ;
+      const float4* Q2 = reinterpret_cast<const float4*>(sE + le2 * PE + L32::oQ);
       const int pv = face_node(f, n, ab % n, ab / n);
       const int64_t dst = M.tr_off[e2] + f * n2 + ab;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Tn[v * M.tr_total + dst] = make_float2(QH2[v * n3 + pv], QH2[(4 + v) * n3 + pv]);
+      const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
+      Tn[dst] = make_float2(h4.x, l4.x);
+      Tn[M.tr_total + dst] = make_float2(h4.y, l4.y);
+      Tn[2 * M.tr_total + dst] = make_float2(h4.z, l4.z);
+      Tn[3 * M.tr_total + dst] = make_float2(h4.w, l4.w);
     }
   }
 }
