@@ -29,7 +29,10 @@
  *
  * Ownership: descriptors and host arrays passed in are copied; the caller keeps them.
  * Device arrays (q, g, R, xyz) are caller-owned, FP64, contiguous; the library never frees
- * them. Library-owned buffers (traces, geometry, tables) are freed by dg_destroy.
+ * them. Library-owned buffers (traces, geometry, tables) are freed by dg_destroy. The
+ * reduced-precision path reads q with bulk copies of whole 16-byte blocks, so the 16-byte
+ * blocks containing q's first and last bytes must be readable (true for any cudaMalloc or
+ * PyTorch CUDA allocation).
  */
 #ifndef DG_H
 #define DG_H

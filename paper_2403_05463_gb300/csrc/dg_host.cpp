@@ -249,7 +249,8 @@ struct dg_ctx {
   // device
   std::map<std::string, DevBuf> buf;
   DevMesh M{};
-  std::vector<Bucket> all_buckets;  // per (N, curved): every element
+  std::vector<Bucket> all_buckets;  // per (N, geometry kind): every element
+  std::vector<std::vector<int32_t>> all_lists;  // host copies of the all_buckets lists
   std::vector<Bucket> ns_buckets;   // per (N, curved): NS elements
   std::vector<Bucket> ord_buckets;  // per N (traces, coordinates, sums)
   int32_t* mortar_all = nullptr;    // device slots e*6+f of every mortar face
@@ -284,7 +285,8 @@ void free_buf(dg_ctx* c, const std::string& name) {
 template <typename T>
 dg_status dev_alloc(dg_ctx* c, const std::string& name, size_t count, T** out) {
   free_buf(c, name);
-  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  // 256 bytes of slack: bulk copies read whole 16-byte blocks around the wanted range
+  size_t bytes = count * sizeof(T) + 256;
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) return fail(DG_ERR_OOM, "cudaMalloc(%s, %zu bytes): %s", name.c_str(), bytes, cudaGetErrorString(e));
@@ -495,7 +497,7 @@ void build_buckets(const std::vector<int32_t>& elems, const std::vector<int8_t>&
 }
 
 dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector<int32_t>& elems, bool split_curved,
-                         bool ns, std::vector<Bucket>& out) {
+                         bool ns, std::vector<Bucket>& out, std::vector<std::vector<int32_t>>* host_lists = nullptr) {
   std::vector<std::vector<int32_t>> lists;
   std::vector<std::pair<int, int>> keys;
   build_buckets(elems, c->order, c->geo_kind, split_curved, lists, keys);
@@ -509,8 +511,21 @@ dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector
     b.count = (int)lists[i].size();
     dg_status st = dev_upload(c, prefix + std::to_string(i), lists[i], &b.list);
     if (st != DG_OK) return st;
+    if (host_lists) {
+      std::vector<int64_t> bo(lists[i].size()), bt(lists[i].size());
+      for (size_t j = 0; j < lists[i].size(); ++j) {
+        bo[j] = c->off[lists[i][j]];
+        bt[j] = c->troff[lists[i][j]];
+      }
+      int64_t* d;
+      if ((st = dev_upload(c, prefix + "o" + std::to_string(i), bo, &d)) != DG_OK) return st;
+      b.boff = d;
+      if ((st = dev_upload(c, prefix + "t" + std::to_string(i), bt, &d)) != DG_OK) return st;
+      b.btr = d;
+    }
     out.push_back(b);
   }
+  if (host_lists) *host_lists = lists;
   return DG_OK;
 }
 
@@ -548,6 +563,31 @@ dg_status rebuild_flags(dg_ctx* c) {
   dg_status st = dev_upload(c, "link", link, &dl);
   if (st != DG_OK) return st;
   c->M.link = dl;
+  // per-entry link and flag tables of the all-element buckets
+  for (size_t i = 0; i < c->all_buckets.size() && i < c->all_lists.size(); ++i) {
+    const std::vector<int32_t>& L = c->all_lists[i];
+    std::vector<FaceLink> bl(L.size() * 6);
+    std::vector<uint8_t> bf(L.size());
+    std::vector<EntryMeta> bm(L.size());
+    for (size_t j = 0; j < L.size(); ++j) {
+      for (int f = 0; f < 6; ++f) bl[j * 6 + f] = link[(size_t)L[j] * 6 + f];
+      bf[j] = c->flag[L[j]];
+      bm[j].off = c->off[L[j]];
+      bm[j].troff = c->troff[L[j]];
+      bm[j].elem = L[j];
+      bm[j].flag = c->flag[L[j]];
+      bm[j].pad = 0;
+    }
+    FaceLink* dbl;
+    uint8_t* dbf;
+    EntryMeta* dbm;
+    if ((st = dev_upload(c, "allbl" + std::to_string(i), bl, &dbl)) != DG_OK) return st;
+    if ((st = dev_upload(c, "allbf" + std::to_string(i), bf, &dbf)) != DG_OK) return st;
+    if ((st = dev_upload(c, "allbm" + std::to_string(i), bm, &dbm)) != DG_OK) return st;
+    c->all_buckets[i].blink = dbl;
+    c->all_buckets[i].bflag = dbf;
+    c->all_buckets[i].bmeta = dbm;
+  }
   uint8_t* df;
   if ((st = dev_upload(c, "flag", c->flag, &df)) != DG_OK) return st;
   c->M.flag = df;
@@ -711,7 +751,7 @@ dg_status rebuild_orders(dg_ctx* c) {
   }
   std::vector<int32_t> every(E);
   for (int64_t e = 0; e < E; ++e) every[e] = (int32_t)e;
-  if ((st = upload_buckets(c, "allb", every, true, false, c->all_buckets)) != DG_OK) return st;
+  if ((st = upload_buckets(c, "allb", every, true, false, c->all_buckets, &c->all_lists)) != DG_OK) return st;
   if ((st = upload_buckets(c, "ordb", every, false, false, c->ord_buckets)) != DG_OK) return st;
   return rebuild_flags(c);
 }

@@ -8,6 +8,7 @@ namespace dgk {
 
 constexpr int MAXN = 7;        // largest polynomial order with a kernel instantiation
 constexpr int NP = MAXN + 1;   // table stride
+constexpr int kErrTimeout = 7;  // DG_ERR_TIMEOUT in the device error word
 
 // Kind of coupling behind one local face of an element.
 enum FaceKind : uint8_t {
@@ -84,14 +85,31 @@ struct Ops1D {
   double x[NP][NP];       // x[N][i]
 };
 
+// Per-entry record of a bucket (32 bytes, copied whole into shared memory by the
+// pipelined inviscid pass).
+struct EntryMeta {
+  int64_t off;    // node offset of the element
+  int64_t troff;  // first face-trace slot of the element
+  int32_t elem;   // element id
+  int32_t flag;   // 0 Euler, 1 NS
+  int64_t pad;
+};
+static_assert(sizeof(EntryMeta) == 32, "EntryMeta is copied in 16-byte blocks");
+
 // Element lists of one kernel launch.
 struct Bucket {
   int N;
   int geo;            // 0 axis-aligned box, 1 affine, 2 curved
   bool curved;        // geo == 2
   bool ns;            // true: only NS elements (viscous pass)
-  int32_t* list;      // device
+  int32_t* list;      // device: element ids
   int count;
+  // per-entry tables in bucket order (device), for the pipelined inviscid pass
+  const int64_t* boff = nullptr;    // node offset of the entry's element
+  const int64_t* btr = nullptr;     // first face-trace slot of the entry's element
+  const FaceLink* blink = nullptr;  // the element's 6 face links
+  const uint8_t* bflag = nullptr;   // the element's flag
+  const EntryMeta* bmeta = nullptr; // the entry's record
 };
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };

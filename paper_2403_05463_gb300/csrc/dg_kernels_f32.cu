@@ -430,329 +430,533 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
   }
 }
 
-// shared-memory layout of k_inviscid32 (floats), per element of the block:
-//   F  [3][n3] float4   contravariant flux deviations (4 variables packed); after the
-//                       contraction: face terms [6][n2] float4
-//   Q  [2][n3] float4   hi, lo of q; after the face phase: hi, lo of the updated q
-//   NT [48 n2]  neighbours' q traces (hi, lo)[6][4][n2] (neighbour face coordinates)
-//   NV [18 n2]  neighbours' viscous traces [6][3][n2];  OV [18 n2] own viscous traces
-//   EC [16]     element constants (Ja, 1/J, delta, kind)
-//   QD [4 n3]   the exact FP64 state (doubles) for the update
-// then the block's face links.
+// ---------------------------------------------------------------------------------------
+// inviscid pass, persistent, TMA-staged
+// ---------------------------------------------------------------------------------------
+// Each block loops over tiles of EPB elements. While it computes tile i from one shared input
+// buffer, warp 0 fetches tile i+1 into the other buffer with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier): per element the four planes
+// of its FP64 state, every conforming face's neighbour trace planes, the neighbours' and its
+// own viscous traces, its constants and its face links — about 50 copies instead of ~2000
+// thread-level copies. A bulk copy needs 16-byte-aligned ends, so each copy covers the
+// 16-byte-aligned superset of its range and the offset of the first wanted byte is kept in
+// a small table. Per element (bytes):
+//   QD [4] slots of a16(8 n3 + 16) | NT [6][4] slots of a16(8 n2 + 16) |
+//   NV [6][3] slots of a16(4 n2 + 16) | OV [3] slots of a16(24 n2 + 16) | LK 96 | EC 48 |
+//   MT 32 (EntryMeta) | SH 64 (byte offsets of the slots' first wanted byte)
 template <int N>
-struct InvSmem32 {
+struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
-  static constexpr int oF = 0, oQ = 12 * n3, oNT = oQ + 8 * n3, oNV = oNT + 48 * n2, oOV = oNV + 18 * n2,
-                       oEC = oOV + 18 * n2, oQD = oEC + 16, per_elem = oQD + 8 * n3;
-  static constexpr size_t bytes = sizeof(float) * (NP * NP + EPB * per_elem) + sizeof(FaceLink) * EPB * 6;
+  static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
+  static constexpr int SQD = a16(8 * n3 + 16), SNT = a16(8 * n2 + 16), SNV = a16(4 * n2 + 16),
+                       SOV = a16(24 * n2 + 16);
+  static constexpr int iQD = 0, iNT = 4 * SQD, iNV = iNT + 24 * SNT, iOV = iNV + 18 * SNV, iLK = iOV + 3 * SOV,
+                       iEC = iLK + 96, iMT = iEC + 48, iSH = iMT + 32, in_elem = a16(iSH + 64);
+  static constexpr int ITEMS = 50;  // copies per element: 4 QD, 24 NT, 18 NV, 3 OV, EC
+  static constexpr int wF = 0, wQ = 48 * n3, work_elem = 80 * n3;
+  static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
+  static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
 };
 
-// Geometry kinds of a bucket: 0 axis-aligned box (diagonal constant metric), 1 affine
-// (constant metric), 2 curved (metric per node).
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// global load whose issue point the compiler keeps (used to prefetch values needed much later)
+__device__ __forceinline__ float ld_early(const float* p) {
+  float v;
+  asm volatile("ld.global.f32 %0, [%1];\n" : "=f"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void mbar_init(void* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(void* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(void* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, void* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One bulk copy of a tile element, item k (see TmaSmem32), described from the element's record
+// and links already in shared memory: returns false if the item does not apply. src/len give
+// the wanted bytes, slot the element-relative destination, sh_index the shift-table entry.
+template <int N>
+__device__ __forceinline__ bool tma_item(const DevMesh& M, const double* qin, const EntryMeta& mt,
+                                         const FaceLink* lk, int k, const char*& src, int& len, int& slot,
+                                         int& sh_index) {
+  using P = TmaSmem32<N>;
+  constexpr int n2 = P::n2, n3 = P::n3;
+  if (k < 4) {
+    src = reinterpret_cast<const char*>(qin + (int64_t)k * M.total + mt.off);
+    len = 8 * n3;
+    slot = P::iQD + k * P::SQD;
+    sh_index = k;
+    return true;
+  }
+  if (k < 28) {
+    const int f = (k - 4) / 4, v = (k - 4) % 4;
+    const FaceLink& L = lk[f];
+    if (L.kind != FK_CONF) return false;
+    src = reinterpret_cast<const char*>(M.Tq + (int64_t)v * M.tr_total + L.nslot);
+    len = 8 * n2;
+    slot = P::iNT + (k - 4) * P::SNT;
+    sh_index = k;
+    return true;
+  }
+  if (k < 46) {
+    const int f = (k - 28) / 3, c = (k - 28) % 3;
+    const FaceLink& L = lk[f];
+    if (L.kind != FK_CONF || !L.nflag) return false;
+    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + (int64_t)c * M.tr_total + L.nslot);
+    len = 4 * n2;
+    slot = P::iNV + (k - 28) * P::SNV;
+    sh_index = k;
+    return true;
+  }
+  if (k < 49) {
+    if (!mt.flag) return false;
+    const int c = k - 46;
+    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + (int64_t)c * M.tr_total + mt.troff);
+    len = 4 * 6 * n2;
+    slot = P::iOV + c * P::SOV;
+    sh_index = k;
+    return true;
+  }
+  src = reinterpret_cast<const char*>(&M.ec32[mt.elem]);
+  len = 48;
+  slot = P::iEC;
+  sh_index = -1;
+  return true;
+}
+
+// The producer warp fills buffer IN with tile `tile`, completion on `bar` (32 arrivals):
+// (1) each element's record and face links, with independent loads, into the buffer's MT/LK
+// slots; (2) the copy plan from those, the shift table, the expected byte count; (3) the bulk
+// copies.
+template <int N>
+__device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, const double* qin, int tile, char* IN,
+                                          void* bar) {
+  using P = TmaSmem32<N>;
+  constexpr int EPB = P::EPB;
+  const int lane = threadIdx.x & 31;
+  for (int r = lane; r < EPB * 7; r += 32) {
+    const int le = r / 7, k = r % 7, i = tile * EPB + le;
+    if (i >= B.count) continue;
+    char* base = IN + le * P::in_elem;
+    if (k == 0)
+      *reinterpret_cast<EntryMeta*>(base + P::iMT) = B.bmeta[i];
+    else
+      reinterpret_cast<FaceLink*>(base + P::iLK)[k - 1] = B.blink[(int64_t)i * 6 + (k - 1)];
+  }
+  __syncwarp();
+  unsigned total = 0;
+  for (int it = lane; it < EPB * P::ITEMS; it += 32) {
+    const int le = it / P::ITEMS, k = it % P::ITEMS;
+    if (tile * EPB + le >= B.count) continue;
+    char* base = IN + le * P::in_elem;
+    const char* src;
+    int len, slot, sh;
+    if (!tma_item<N>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
+                     reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
+      continue;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t s0 = a & ~(uintptr_t)15, e0 = (a + len + 15) & ~(uintptr_t)15;
+    total += (unsigned)(e0 - s0);
+    if (sh >= 0) reinterpret_cast<unsigned char*>(base + P::iSH)[sh] = (unsigned char)(a - s0);
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_arrive_expect_tx(bar, total);
+  for (int it = lane; it < EPB * P::ITEMS; it += 32) {
+    const int le = it / P::ITEMS, k = it % P::ITEMS;
+    if (tile * EPB + le >= B.count) continue;
+    char* base = IN + le * P::in_elem;
+    const char* src;
+    int len, slot, sh;
+    if (!tma_item<N>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
+                     reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
+      continue;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t s0 = a & ~(uintptr_t)15, e0 = (a + len + 15) & ~(uintptr_t)15;
+    bulk_copy_g2s(base + slot, reinterpret_cast<const void*>(s0), (unsigned)(e0 - s0), bar);
+  }
+}
+
+// bounded wait on an mbarrier phase: false if it did not complete within the limit
+__device__ __forceinline__ bool mbar_wait_bounded(void* bar, unsigned parity) {
+  bool ok = false;
+  for (int spin = 0; spin < (1 << 22) && !ok; ++spin) ok = mbar_try_wait(bar, parity);
+  return ok;
+}
+__device__ __forceinline__ void mbar_arrive(void* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier 1 among the consumer threads only (the producer warp never joins it)
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+// OR of `pred` over the consumer threads (barrier 2)
+__device__ __forceinline__ bool consumer_any(bool pred, int nthreads) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+template <int N>
+struct TmaMinBlocks {
+  static constexpr int value = N == 4 ? 3 : (N == 5 ? 4 : (N == 1 || N == 7 ? 1 : 2));
+};
+
+// Warp-specialised: threads [0, Shape<N>::threads) compute (one per node, as elsewhere), the
+// last warp only fetches tiles. Input buffer b is handed over through full[b] (the copies'
+// bytes) and returned through empty[b] (one arrival per consumer warp).
 template <int N, int GEO, int MODE>
-__global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
-    k_inviscid32(DevMesh M, const int32_t* __restrict__ list, int count, const double* qin, double* out, double* g,
-                 int stage, int write_tr) {
+__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+    k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
   using S = Shape<N>;
-  using L32 = InvSmem32<N>;
-  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB, PE = L32::per_elem;
-  extern __shared__ float smf[];
-  float* sD = smf;
-  float* sE = sD + NP * NP;
-  FaceLink* sL = reinterpret_cast<FaceLink*>(sE + EPB * PE);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int ebase = blockIdx.x * EPB;
-  const float* Tvf = reinterpret_cast<const float*>(M.Tv);
+  using P = TmaSmem32<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ __align__(128) char smc[];
+  void* bar0 = smc + P::oBAR;        // full[0]
+  void* bar1 = smc + P::oBAR + 8;    // full[1]
+  void* ebar0 = smc + P::oBAR + 16;  // empty[0]
+  void* ebar1 = smc + P::oBAR + 24;  // empty[1]
+  constexpr int NC = Shape<N>::threads;  // consumer threads
+  float* sD = reinterpret_cast<float*>(smc + P::oD);
+  char* const IN0 = smc + P::oIN0;
+  char* const IN1 = smc + P::oIN1;
+  char* W = smc + P::oW;
+  const int tid = threadIdx.x, nthr = NC;
+  const int ntiles = (B.count + EPB - 1) / EPB;
   const float* rvf = reinterpret_cast<const float*>(M.rv);
   float* g32 = reinterpret_cast<float*>(g);
-  const float2* Tq2 = reinterpret_cast<const float2*>(M.Tq);
   const float c0sq = M.c0sq32;
   const float invw = c_ops32.w0inv[N];
   for (int t = tid; t < n2; t += nthr) sD[t] = c_ops32.D[N][t];
-  // stage the neighbours' traces (and the viscous traces) of every conforming face
-  for (int t = tid; t < EPB * 6 * n2; t += nthr) {
-    const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
-    if (ebase + le2 >= count) continue;
-    const int e2 = list[ebase + le2];
-    const FaceLink L = M.link[e2 * 6 + f];
-    if (ab == 0) sL[le2 * 6 + f] = L;
-    float* base = sE + le2 * PE;
-    if (L.kind == FK_CONF) {
-      const int64_t src = L.nslot + ab;
-      float2* nt = reinterpret_cast<float2*>(base + L32::oNT);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) cp_async8(&nt[(f * 4 + v) * n2 + ab], &Tq2[v * M.tr_total + src]);
-      if (L.nflag) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async4(&base[L32::oNV + (f * 3 + c) * n2 + ab], &Tvf[c * M.tr_total + src]);
-      }
-    }
-    if (M.flag[e2]) {
-      const int64_t own = M.tr_off[e2] + f * n2 + ab;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async4(&base[L32::oOV + (f * 3 + c) * n2 + ab], &Tvf[c * M.tr_total + own]);
-    }
+  if (tid == 0) {
+    mbar_init(bar0, 32);
+    mbar_init(bar1, 32);
+    mbar_init(ebar0, NC / 32);
+    mbar_init(ebar1, NC / 32);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // ---- node phase: state, flux deviations --------------------------------------------
+  __syncthreads();
+  if (tid >= NC) {
+    // ---- producer warp ----------------------------------------------------------------
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1))) {
+        if (tid == NC) {
+          atomicCAS(&M.err[0], 0, kErrTimeout);
+          atomicCAS(&M.err[1], 0, 2);
+        }
+        return;
+      }
+      tma_stage<N>(M, B, qin, tile, b ? IN1 : IN0, b ? bar1 : bar0);
+    }
+    return;
+  }
   int le = tid / n3;
   const int p = tid % n3;
-  const int slot = ebase + le;
-  const bool active = (le < EPB) && (slot < count);
-  if (le >= EPB) le = EPB - 1;
-  const int e = active ? list[slot] : 0;
-  const int64_t off = active ? M.elem_off[e] : 0;
-  const bool ns = active && M.flag[e] != 0;
-  float* base = sE + le * PE;
-  float* F = base + L32::oF;
-  float4* F4 = reinterpret_cast<float4*>(F);
-  float4* QH4 = reinterpret_cast<float4*>(base + L32::oQ);
-  float4* QL4 = QH4 + n3;
-  float* EC = base + L32::oEC;
-  double* QD = reinterpret_cast<double*>(base + L32::oQD);
+  const bool lane_ok = le < EPB;
+  if (!lane_ok) le = EPB - 1;
   const int ii[3] = {p % n, (p / n) % n, p / n2};
-  float invJ = 0.f;
-  float gold[4] = {0.f, 0.f, 0.f, 0.f}, rvp[3] = {0.f, 0.f, 0.f};
-  if (active) {
-    if (MODE == MODE_RK && stage > 0) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) gold[v] = g32[v * M.total + off + p];
-    }
-    if (ns) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) rvp[c] = rvf[c * M.total + off + p];
-    }
-    const ElemConst32& ec = M.ec32[e];
-    for (int k = p; k < 12; k += n3) EC[k] = k < 9 ? ec.Ja[k] : (k == 9 ? ec.invJ : (k == 10 ? ec.delta : ec.curved));
-    float dq[4], qr32[4], h[4], l[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const double qv = qin[v * M.total + off + p];
-      QD[v * n3 + p] = qv;
-      split_hilo(qv, h[v], l[v]);
-      qr32[v] = hi_part(qin[v * M.total + off]);  // any per-element constant serves as reference
-      dq[v] = (h[v] - qr32[v]) + l[v];
-    }
-    QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
-    QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
-    float fl[4][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      fl[0][k] = c0sq * dq[1 + k];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        fl[1 + c][k] = qr32[1 + c] * dq[1 + k] + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
-    }
-    if (GEO == 0) {
-      invJ = ec.invJ;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float j = ec.Ja[d * 4];
-        F4[d * n3 + p] = make_float4(j * fl[0][d], j * fl[1][d], j * fl[2][d], j * fl[3][d]);
-      }
-    } else {
-      float Ja[9];
-      if (GEO == 2) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Ja[k] = __ldg(&M.geo32[k * M.total + off + p]);
-        invJ = __ldg(&M.geo32[9 * M.total + off + p]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Ja[k] = ec.Ja[k];
-        invJ = ec.invJ;
-      }
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float c4[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) c4[v] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
-        F4[d * n3 + p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
-      }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // ---- volume: J R = -sum_d D_d Ftil^d ------------------------------------------------
-  float JR[4] = {0.f, 0.f, 0.f, 0.f};
-  if (active) {
-    const int str[3] = {1, n, n2};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int bs = p - ii[d] * str[d];
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        const float dm = sD[ii[d] * n + m];
-        const float4 f4 = F4[d * n3 + bs + m * str[d]];
-        JR[0] -= dm * f4.x;
-        JR[1] -= dm * f4.y;
-        JR[2] -= dm * f4.z;
-        JR[3] -= dm * f4.w;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
-  }
-  __syncthreads();  // F is reused for the face terms below
-  // ---- faces, one thread per (element, face, face node) -------------------------------
-  for (int t = tid; t < EPB * 6 * n2; t += nthr) {
-    const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
-    if (ebase + le2 >= count) continue;
-    const int e2 = list[ebase + le2];
-    const FaceLink L = sL[le2 * 6 + f];
-    float* b2 = sE + le2 * PE;
-    const float* E2 = b2 + L32::oEC;
-    const int d = f >> 1;
-    const float sg = (f & 1) ? 1.f : -1.f;
-    const int a = ab % n, bb = ab / n;
-    const int pv = face_node(f, n, a, bb);
-    const bool ns2 = M.flag[e2] != 0;
-    float term[4];
-    if (L.kind == FK_MORTAR) {
-      const int64_t node = M.elem_off[e2] + pv;
-      const int64_t ms = M.tr_off[e2] + f * n2 + ab;
-      double Sd[3], qq[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) qq[v] = qin[v * M.total + node];
-      if (GEO == 2) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Sd[k] = sg * M.geo[(d * 3 + k) * M.total + node];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Sd[k] = sg * M.ec[e2].Ja[d * 3 + k];
-      }
-      const double un = qq[1] * Sd[0] + qq[2] * Sd[1] + qq[3] * Sd[2];
-      term[0] = (float)(M.LH[ms] - M.c0sq * un);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double own = qq[1 + c] * un + qq[0] * Sd[c];
-        term[1 + c] = (float)(M.LH[(1 + c) * M.tr_total + ms] - own) + (ns2 ? b2[L32::oOV + (f * 3 + c) * n2 + ab] : 0.f);
-      }
-    } else {
-      float Sv[3];
-      if (GEO == 2) {
-        const int64_t node = M.elem_off[e2] + pv;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Sv[k] = sg * __ldg(&M.geo32[(d * 3 + k) * M.total + node]);
-      } else if (GEO == 1) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Sv[k] = sg * E2[d * 3 + k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Sv[k] = (k == d) ? sg * E2[d * 4] : 0.f;
-      }
-      const float s = GEO == 0 ? fabsf(E2[d * 4]) : sqrtf(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
-      const float is = 1.f / s;
-      const float nh[3] = {Sv[0] * is, Sv[1] * is, Sv[2] * is};
-      const float4 h4 = reinterpret_cast<const float4*>(b2 + L32::oQ)[pv];
-      const float4 l4 = reinterpret_cast<const float4*>(b2 + L32::oQ)[n3 + pv];
-      const float qh[4] = {h4.x, h4.y, h4.z, h4.w}, ql[4] = {l4.x, l4.y, l4.z, l4.w};
-      float dqf[4];
-      int nab = 0;
-      if (L.kind == FK_CONF) {
-        int a1, b1;
-        inv_orient(L.orient, N, a, bb, a1, b1);
-        nab = a1 + n * b1;
-        const float2* nt = reinterpret_cast<const float2*>(b2 + L32::oNT);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float2 tq = nt[(f * 4 + v) * n2 + nab];
-          dqf[v] = (tq.x - qh[v]) + (tq.y - ql[v]);
-        }
-      } else if (L.kind == FK_INFLOW) {
-        dqf[0] = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float ih, il;
-          split_hilo(M.inflow[1 + c], ih, il);
-          dqf[1 + c] = (ih - qh[1 + c]) + (il - ql[1 + c]);
-        }
-      } else {
-        dqf[0] = -(qh[0] + ql[0]);
-        dqf[1] = dqf[2] = dqf[3] = 0.f;
-      }
-      float ub[3], um[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        um[c] = qh[1 + c] + ql[1 + c];
-        ub[c] = um[c] + 0.5f * dqf[1 + c];
-      }
-      float fx[4];
-      if (GEO == 0) {
-        flux_fluct32_axis(dqf, ub, um, d, sg, c0sq, M.riemann, fx);
-      } else {
-        const float unm = um[0] * nh[0] + um[1] * nh[1] + um[2] * nh[2];
-        const float unp = unm + dqf[1] * nh[0] + dqf[2] * nh[1] + dqf[3] * nh[2];
-        flux_fluct32(dqf, ub, nh, c0sq, M.riemann, unm, unp, fx);
-      }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) term[v] = s * fx[v];
-      if (L.kind == FK_CONF && (ns2 || L.nflag)) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float tv = 0.f;
-          if (ns2) tv += b2[L32::oOV + (f * 3 + c) * n2 + ab];
-          if (L.nflag) tv += b2[L32::oNV + (f * 3 + c) * n2 + nab];
-          term[1 + c] += 0.5f * tv;
-        }
-      }
-    }
-    reinterpret_cast<float4*>(b2 + L32::oF)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
-  }
-  __syncthreads();
-  // ---- assembly and update (node phase) -------------------------------------------------
   const bool on_face = ii[0] == 0 || ii[0] == N || ii[1] == 0 || ii[1] == N || ii[2] == 0 || ii[2] == N;
-  if (active) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (ii[d] != 0 && ii[d] != N) continue;
-      const int f = 2 * d + (ii[d] == N ? 1 : 0);
-      const int a = d == 0 ? ii[1] : ii[0], bb = d == 2 ? ii[1] : ii[2];
-      const float4 sc = F4[f * n2 + a + n * bb];
-      JR[0] -= invw * sc.x;
-      JR[1] -= invw * sc.y;
-      JR[2] -= invw * sc.z;
-      JR[3] -= invw * sc.w;
+  float4* F4 = reinterpret_cast<float4*>(W + le * P::work_elem + P::wF);
+  float4* QH4 = reinterpret_cast<float4*>(W + le * P::work_elem + P::wQ);
+  float4* QL4 = QH4 + n3;
+  // ---- consumer threads ----------------------------------------------------------------
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int cur = it & 1;
+    const int i = tile * EPB + le;
+    const bool active = lane_ok && i < B.count;
+    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1));
+    if (consumer_any(!ok, NC)) {
+      if (tid == 0) {
+        atomicCAS(&M.err[0], 0, kErrTimeout);
+        atomicCAS(&M.err[1], 0, 1);
+      }
+      return;
     }
-    if (MODE == MODE_RESIDUAL) {
+    char* IN = cur ? IN1 : IN0;
+    const char* INe = IN + le * P::in_elem;
+    const EntryMeta* MT = reinterpret_cast<const EntryMeta*>(INe + P::iMT);
+    // prefetch what this node needs only at the end of the tile
+    int64_t off = 0;
+    float gold[4] = {0.f, 0.f, 0.f, 0.f}, rvp[3] = {0.f, 0.f, 0.f};
+    if (active) {
+      off = MT->off;
+      if (MODE == MODE_RK && stage > 0) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) out[v * M.total + off + p] = (double)(JR[v] * invJ);
-    } else {
-      // g <- A g + dt R in FP32 (the RK register of this path); q <- q + B g in FP64
-      const float A = c32_rkA32[stage];
-      const double B = c32_rkB[stage];
-      const float dtf = M.dt32;
-      float h[4], l[4];
+        for (int v = 0; v < 4; ++v) gold[v] = ld_early(&g32[v * M.total + off + p]);
+      }
+      if (MT->flag) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rvp[c] = ld_early(&rvf[c * M.total + off + p]);
+      }
+    }
+    const unsigned char* SH = reinterpret_cast<const unsigned char*>(INe + P::iSH);
+    const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
+    float invJ = 0.f;
+    // ---- node phase: split state, flux deviations --------------------------------------
+    if (active) {
+      float dq[4], qr32[4], h[4], l[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const int64_t ix = v * M.total + off + p;
-        const float gi = fmaf(A, gold[v], JR[v] * invJ * dtf);
-        g32[ix] = gi;
-        const double qn = fma(B, (double)gi, QD[v * n3 + p]);
-        out[ix] = qn;
-        if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
+        const double* QDv = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v]);
+        split_hilo(QDv[p], h[v], l[v]);
+        qr32[v] = hi_part(QDv[0]);  // any per-element constant serves as reference
+        dq[v] = (h[v] - qr32[v]) + l[v];
       }
-      if (write_tr && on_face) {
-        QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
-        QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
+      QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
+      QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
+      float fl[4][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        fl[0][k] = c0sq * dq[1 + k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          fl[1 + c][k] = qr32[1 + c] * dq[1 + k] + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
+      }
+      if (GEO == 0) {
+        invJ = EC->invJ;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float j = EC->Ja[d * 4];
+          F4[d * n3 + p] = make_float4(j * fl[0][d], j * fl[1][d], j * fl[2][d], j * fl[3][d]);
+        }
+      } else {
+        float Ja[9];
+        if (GEO == 2) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Ja[k] = __ldg(&M.geo32[k * M.total + off + p]);
+          invJ = __ldg(&M.geo32[9 * M.total + off + p]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Ja[k] = EC->Ja[k];
+          invJ = EC->invJ;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          float c4[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) c4[v] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+          F4[d * n3 + p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        }
       }
     }
-  }
-  if (MODE == MODE_RK && write_tr) {
-    __syncthreads();
-    // traces of the new state for the next stage, one thread per face slot (coalesced)
-    float2* Tn = reinterpret_cast<float2*>(M.Tq_next);
+    consumer_sync(NC);
+    // ---- volume: J R = -sum_d D_d Ftil^d ----------------------------------------------
+    float JR[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+      const int str[3] = {1, n, n2};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int bs = p - ii[d] * str[d];
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const float dm = sD[ii[d] * n + m];
+          const float4 f4 = F4[d * n3 + bs + m * str[d]];
+          JR[0] -= dm * f4.x;
+          JR[1] -= dm * f4.y;
+          JR[2] -= dm * f4.z;
+          JR[3] -= dm * f4.w;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
+    }
+    consumer_sync(NC);  // F is reused for the face terms below
+    // ---- faces, one thread per (element, face, face node) -----------------------------
     for (int t = tid; t < EPB * 6 * n2; t += nthr) {
       const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
-      if (ebase + le2 >= count) continue;
-      const int e2 = list[ebase + le2];
-      const float4* Q2 = reinterpret_cast<const float4*>(sE + le2 * PE + L32::oQ);
-      const int pv = face_node(f, n, ab % n, ab / n);
-      const int64_t dst = M.tr_off[e2] + f * n2 + ab;
-      const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
-      Tn[dst] = make_float2(h4.x, l4.x);
-      Tn[M.tr_total + dst] = make_float2(h4.y, l4.y);
-      Tn[2 * M.tr_total + dst] = make_float2(h4.z, l4.z);
-      Tn[3 * M.tr_total + dst] = make_float2(h4.w, l4.w);
+      const int i2 = tile * EPB + le2;
+      if (i2 >= B.count) continue;
+      const char* I2 = IN + le2 * P::in_elem;
+      const unsigned char* SH2 = reinterpret_cast<const unsigned char*>(I2 + P::iSH);
+      const FaceLink L = reinterpret_cast<const FaceLink*>(I2 + P::iLK)[f];
+      const ElemConst32* E2 = reinterpret_cast<const ElemConst32*>(I2 + P::iEC);
+      const EntryMeta* MT2 = reinterpret_cast<const EntryMeta*>(I2 + P::iMT);
+      char* W2 = W + le2 * P::work_elem;
+      const int d = f >> 1;
+      const float sg = (f & 1) ? 1.f : -1.f;
+      const int a = ab % n, bb = ab / n;
+      const int pv = face_node(f, n, a, bb);
+      const bool ns2 = MT2->flag != 0;
+      float term[4];
+      if (L.kind == FK_MORTAR) {
+        const int64_t node = MT2->off + pv;
+        const int64_t ms = MT2->troff + f * n2 + ab;
+        const int e2 = MT2->elem;
+        double Sd[3], qq[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qq[v] = reinterpret_cast<const double*>(I2 + P::iQD + v * P::SQD + SH2[v])[pv];
+        if (GEO == 2) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sd[k] = sg * M.geo[(d * 3 + k) * M.total + node];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sd[k] = sg * M.ec[e2].Ja[d * 3 + k];
+        }
+        const double un = qq[1] * Sd[0] + qq[2] * Sd[1] + qq[3] * Sd[2];
+        term[0] = (float)(M.LH[ms] - M.c0sq * un);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double own = qq[1 + c] * un + qq[0] * Sd[c];
+          float t2 = (float)(M.LH[(1 + c) * M.tr_total + ms] - own);
+          if (ns2) t2 += reinterpret_cast<const float*>(I2 + P::iOV + c * P::SOV + SH2[46 + c])[f * n2 + ab];
+          term[1 + c] = t2;
+        }
+      } else {
+        float Sv[3];
+        if (GEO == 2) {
+          const int64_t node = MT2->off + pv;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sv[k] = sg * __ldg(&M.geo32[(d * 3 + k) * M.total + node]);
+        } else if (GEO == 1) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sv[k] = sg * E2->Ja[d * 3 + k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sv[k] = (k == d) ? sg * E2->Ja[d * 4] : 0.f;
+        }
+        const float s = GEO == 0 ? fabsf(E2->Ja[d * 4]) : sqrtf(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+        const float is = 1.f / s;
+        const float nh[3] = {Sv[0] * is, Sv[1] * is, Sv[2] * is};
+        const float4 h4 = reinterpret_cast<const float4*>(W2 + P::wQ)[pv];
+        const float4 l4 = reinterpret_cast<const float4*>(W2 + P::wQ)[n3 + pv];
+        const float qh[4] = {h4.x, h4.y, h4.z, h4.w}, ql[4] = {l4.x, l4.y, l4.z, l4.w};
+        float dqf[4];
+        int nab = 0;
+        if (L.kind == FK_CONF) {
+          int a1, b1;
+          inv_orient(L.orient, N, a, bb, a1, b1);
+          nab = a1 + n * b1;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int sl = 4 + f * 4 + v;
+            const float2 tq = reinterpret_cast<const float2*>(I2 + P::iNT + (f * 4 + v) * P::SNT + SH2[sl])[nab];
+            dqf[v] = (tq.x - qh[v]) + (tq.y - ql[v]);
+          }
+        } else if (L.kind == FK_INFLOW) {
+          dqf[0] = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float ih, il;
+            split_hilo(M.inflow[1 + c], ih, il);
+            dqf[1 + c] = (ih - qh[1 + c]) + (il - ql[1 + c]);
+          }
+        } else {
+          dqf[0] = -(qh[0] + ql[0]);
+          dqf[1] = dqf[2] = dqf[3] = 0.f;
+        }
+        float ub[3], um[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          um[c] = qh[1 + c] + ql[1 + c];
+          ub[c] = um[c] + 0.5f * dqf[1 + c];
+        }
+        float fx[4];
+        if (GEO == 0) {
+          flux_fluct32_axis(dqf, ub, um, d, sg, c0sq, M.riemann, fx);
+        } else {
+          const float unm = um[0] * nh[0] + um[1] * nh[1] + um[2] * nh[2];
+          const float unp = unm + dqf[1] * nh[0] + dqf[2] * nh[1] + dqf[3] * nh[2];
+          flux_fluct32(dqf, ub, nh, c0sq, M.riemann, unm, unp, fx);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) term[v] = s * fx[v];
+        if (L.kind == FK_CONF && (ns2 || L.nflag)) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float tv = 0.f;
+            if (ns2) tv += reinterpret_cast<const float*>(I2 + P::iOV + c * P::SOV + SH2[46 + c])[f * n2 + ab];
+            if (L.nflag)
+              tv += reinterpret_cast<const float*>(I2 + P::iNV + (f * 3 + c) * P::SNV + SH2[28 + f * 3 + c])[nab];
+            term[1 + c] += 0.5f * tv;
+          }
+        }
+      }
+      reinterpret_cast<float4*>(W2 + P::wF)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
     }
+    consumer_sync(NC);
+    // ---- assembly and update ------------------------------------------------------------
+    if (active) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (ii[d] != 0 && ii[d] != N) continue;
+        const int f = 2 * d + (ii[d] == N ? 1 : 0);
+        const int a = d == 0 ? ii[1] : ii[0], bb = d == 2 ? ii[1] : ii[2];
+        const float4 sc = F4[f * n2 + a + n * bb];
+        JR[0] -= invw * sc.x;
+        JR[1] -= invw * sc.y;
+        JR[2] -= invw * sc.z;
+        JR[3] -= invw * sc.w;
+      }
+      if (MODE == MODE_RESIDUAL) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[v * M.total + off + p] = (double)(JR[v] * invJ);
+      } else {
+        // g <- A g + dt R in FP32 (the RK register of this path); q <- q + B g in FP64
+        const float A = c32_rkA32[stage];
+        const double Bc = c32_rkB[stage];
+        const float dtf = M.dt32;
+        float h[4], l[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int64_t ix = v * M.total + off + p;
+          const float gi = fmaf(A, gold[v], JR[v] * invJ * dtf);
+          g32[ix] = gi;
+          const double qo = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v])[p];
+          const double qn = fma(Bc, (double)gi, qo);
+          out[ix] = qn;
+          if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
+        }
+        if (write_tr && on_face) {
+          QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
+          QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
+        }
+      }
+    }
+    if (MODE == MODE_RK && write_tr) {
+      consumer_sync(NC);
+      // traces of the new state for the next stage, one thread per face slot (coalesced)
+      float2* Tn = reinterpret_cast<float2*>(M.Tq_next);
+      for (int t = tid; t < EPB * 6 * n2; t += nthr) {
+        const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
+        const int i2 = tile * EPB + le2;
+        if (i2 >= B.count) continue;
+        const float4* Q2 = reinterpret_cast<const float4*>(W + le2 * P::work_elem + P::wQ);
+        const int pv = face_node(f, n, ab % n, ab / n);
+        const int64_t dst = reinterpret_cast<const EntryMeta*>(IN + le2 * P::in_elem + P::iMT)->troff + f * n2 + ab;
+        const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
+        Tn[dst] = make_float2(h4.x, l4.x);
+        Tn[M.tr_total + dst] = make_float2(h4.y, l4.y);
+        Tn[2 * M.tr_total + dst] = make_float2(h4.z, l4.z);
+        Tn[3 * M.tr_total + dst] = make_float2(h4.w, l4.w);
+      }
+    }
+    consumer_sync(NC);  // work buffers are reused by the next tile
+    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);  // this input buffer may be refilled
   }
 }
 
@@ -772,10 +976,6 @@ template <int N, int GEO>
 static size_t visc_smem32() {
   return ViscSmem32<N, GEO>::bytes;
 }
-template <int N>
-static size_t inv_smem32() {
-  return InvSmem32<N>::bytes;
-}
 
 template <int N>
 static cudaError_t prep32_n() {
@@ -786,13 +986,13 @@ static cudaError_t prep32_n() {
                                 (int)visc_smem32<N, 1>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 2>())) != cudaSuccess) return r;
-  const int is = (int)inv_smem32<N>();
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 0, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 1, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 2, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 0, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 1, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32<N, 2, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  const int ps = (int)TmaSmem32<N>::bytes;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
   return cudaSuccess;
 }
 
@@ -844,31 +1044,45 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
   return cudaGetLastError();
 }
 
+// grid of the persistent kernel: every resident block slot of the GPU, at most one per tile
+template <int N, int GEO, int MODE>
+static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                               int stage, int write_tr, cudaStream_t s) {
+  static int per_sm = -1, sms = 0;
+  const size_t sm = TmaSmem32<N>::bytes;
+  if (per_sm < 0) {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE>,
+                                                                  Shape<N>::threads + 32, sm);
+    if (r != cudaSuccess) return r;
+    int dev = 0;
+    if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntiles = (b.count + Shape<N>::EPB - 1) / Shape<N>::EPB;
+  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
+  k_inviscid32t<N, GEO, MODE><<<grid, Shape<N>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g, int mode,
                               int stage, int write_tr, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
+  if (!b.boff || !b.btr || !b.blink || !b.bflag || !b.bmeta) return cudaErrorInvalidValue;
   DG32_DISPATCH_N(b.N, {
-    using SH = Shape<NN>;
-    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
-    const size_t sm = inv_smem32<NN>();
-    const int geo = b.geo;
+    cudaError_t r;
     if (mode == MODE_RESIDUAL) {
-      if (geo == 0)
-        k_inviscid32<NN, 0, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
-      else if (geo == 1)
-        k_inviscid32<NN, 1, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
-      else
-        k_inviscid32<NN, 2, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
+      if (b.geo == 0) r = launch_pipe<NN, 0, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
+      else if (b.geo == 1) r = launch_pipe<NN, 1, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
+      else r = launch_pipe<NN, 2, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
     } else {
-      if (geo == 0)
-        k_inviscid32<NN, 0, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
-      else if (geo == 1)
-        k_inviscid32<NN, 1, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
-      else
-        k_inviscid32<NN, 2, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, write_tr);
+      if (b.geo == 0) r = launch_pipe<NN, 0, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
+      else if (b.geo == 1) r = launch_pipe<NN, 1, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
+      else r = launch_pipe<NN, 2, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
     }
+    return r;
   });
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace dgk

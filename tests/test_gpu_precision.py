@@ -22,6 +22,7 @@ BOUNDS = {
     "padapt_6x6x6_curved": 1.5e-5, "tgv_5x5x5_n1_vreman_llf": 1e-6, "tgv_5x5x5_n2_vreman_llf": 5e-6,
     "tgv_5x5x5_n6_vreman_llf": 3e-4, "tgv_5x5x5_n7_vreman_llf": 3e-4,
     "tgv_4x4x4_n3_rk3_10_steps_update": 7e-6, "mixed_64x64x64_n4_sampled": 1e-4,
+    "tgv_5x5x5_rotated_affine_mixed_orders": 1e-4,
 }
 
 
@@ -67,6 +68,18 @@ def test_fp32_every_order_and_vreman_llf():
         err = _fp32_error(w, params=dict(w.params, nu=1e-2, closure=1, riemann=1))
         _record(f"tgv_5x5x5_n{N}_vreman_llf", err)
         assert err <= BOUNDS[f"tgv_5x5x5_n{N}_vreman_llf"], (N, err)
+
+
+def test_fp32_rotated_affine_mixed_orders():
+    # re-oriented elements: general affine metric (not diagonal), every face orientation,
+    # mortars between orders 2..5
+    import dataclasses
+    w = wl.tgv_4x4x4_n3(n_elem_dir=5, order=3)
+    mesh, _ = wl.rotate_elements(w.mesh, 11)
+    w = small_mixed(dataclasses.replace(w, mesh=mesh), seed=12, orders=(2, 5))
+    err = _fp32_error(w, params=dict(w.params, nu=1e-2))
+    _record("tgv_5x5x5_rotated_affine_mixed_orders", err)
+    assert err <= BOUNDS["tgv_5x5x5_rotated_affine_mixed_orders"]
 
 
 def test_fp32_rk3_ten_steps():
