@@ -142,6 +142,27 @@ dg_status dg_rk_step_host(dg_ctx* ctx, double* q_host, double* g_host, double t,
  * discretisation conserves every variable, so these sums vanish to rounding. */
 dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double out_host[4], void* stream);
 
+/* Largest mesh (elements) that dg_conservation_noalloc accepts. */
+#define DG_CONSERVATION_NOALLOC_MAX_ELEMS 65536
+
+/* The paper has no counterpart to this call; it is a service for callers that cannot allocate.
+ * The same sums as dg_conservation, written to out_dev[4] (caller-owned device memory, FP64)
+ * asynchronously on `stream`, without allocating device memory (no cudaMalloc, cudaFree or
+ * allocating library call) and without a host copy or synchronisation. It is meant for callers
+ * that must not allocate while they run: a process whose memory pool has already claimed the
+ * device, or a time-critical loop in which an allocation would stall the device.
+ * Scratch: the per-element partial sums go to one static device array of
+ * 4 x DG_CONSERVATION_NOALLOC_MAX_ELEMS doubles (2 MiB) that the library module carries.
+ * Nothing in it has to start at zero. Every call in the process on that device shares it, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race and give wrong
+ * sums: serialise them. The first call on a device looks up the array's device address (which
+ * can load the library's device code), so make that first call before any stream capture.
+ * Errors: DG_ERR_ARG for a NULL pointer or a mesh of more than
+ * DG_CONSERVATION_NOALLOC_MAX_ELEMS elements; DG_ERR_CUDA if the look-up or a launch fails.
+ * The device error word is not read (see dg_check_device). The final sum runs in a fixed
+ * order on the device, so it may differ from dg_conservation's host sum by rounding. */
+dg_status dg_conservation_noalloc(dg_ctx* ctx, const double* R_dev, double* out_dev, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 dg_status dg_check_device(dg_ctx* ctx, void* stream);
 

@@ -1132,6 +1132,27 @@ dg_status dg_conservation(dg_ctx* c, const double* R, double out[4], void* strea
   return DG_OK;
 }
 
+static_assert(DG_CONSERVATION_NOALLOC_MAX_ELEMS == kNoAllocMaxElems, "scratch limit");
+
+// Allocates nothing: no cudaMalloc/cudaFree, no host copy. The weights travel as a kernel
+// argument built on the stack; the partial sums use the static scratch of dg_noalloc.cu.
+dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, void* stream) {
+  if (!c || !R || !out_dev) return fail(DG_ERR_ARG, "NULL argument");
+  if (c->ne > kNoAllocMaxElems)
+    return fail(DG_ERR_ARG, "dg_conservation_noalloc: the mesh has %lld elements, the static scratch holds %lld",
+                (long long)c->ne, (long long)kNoAllocMaxElems);
+  CU(cudaSetDevice(c->device));
+  double* scratch = nullptr;
+  CU(noalloc_scratch(c->device, &scratch));
+  NoAllocWeights W{};
+  const OpTables& T = ops();
+  for (int N = 1; N <= MAXN; ++N)
+    for (int i = 0; i <= N; ++i) W.w[N][i] = T.rule[N].w[i];
+  CU(launch_conservation_noalloc(c->M, c->ord_buckets.data(), (int)c->ord_buckets.size(), W, R, scratch, out_dev,
+                                 (cudaStream_t)stream));
+  return DG_OK;
+}
+
 dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, double out_ms[DG_NPHASES],
                          void* stream) {
   if (!c || !q || !g || !out_ms) return fail(DG_ERR_ARG, "NULL argument");

@@ -114,6 +114,12 @@ struct Bucket {
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
+// Allocation-free conservation sums (dg_noalloc.cu): largest mesh its static scratch holds.
+constexpr int64_t kNoAllocMaxElems = 65536;
+struct NoAllocWeights {
+  double w[NP][NP];  // Gauss-Lobatto weights w[N][i]
+};
+
 // Launchers (dg_kernels.cu). All return cudaGetLastError() of their launches.
 cudaError_t upload_ops(const Ops1D& ops);
 cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s);
@@ -136,5 +142,11 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
 cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
 cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                               int mode, int stage, int write_tr, cudaStream_t s);
+
+// Allocation-free conservation sums (dg_noalloc.cu)
+cudaError_t noalloc_scratch(int device, double** ptr);
+cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets,
+                                        const NoAllocWeights& W, const double* R, double* scratch,
+                                        double* out, cudaStream_t s);
 
 }  // namespace dgk

@@ -76,6 +76,7 @@ def load():
         L.dg_residual_host.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_rk_step_host.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]
         L.dg_conservation.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+        L.dg_conservation_noalloc.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_check_device.argtypes = [_vp, _vp]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -230,6 +231,15 @@ class Solver:
         out = (ctypes.c_double * 4)()
         _check(load().dg_conservation(self.h, _dev_ptr(R, "R"), out, _stream_handle(stream)))
         return np.array(list(out))
+
+    def conservation_noalloc(self, R, out, stream=None):
+        """The same sums into `out` (a caller-owned float64 CUDA tensor of 4 values), without
+        any allocation, host copy or synchronisation; calls whose kernels overlap on one device
+        race on the library's shared scratch."""
+        if out.numel() < 4:
+            raise ValueError("out must hold 4 float64 values")
+        _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R"), _dev_ptr(out, "out"),
+                                              _stream_handle(stream)))
 
     PHASES = ("traces", "mortar_lift", "viscous", "mortar_flux", "inviscid_update")
 
