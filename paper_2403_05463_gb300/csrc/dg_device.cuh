@@ -34,35 +34,21 @@ __device__ __forceinline__ void fwd_orient(int o, int M, int a1, int b1, int& a0
 }
 
 // Splits x into FP32 hi + lo: hi is x truncated to 24 significant bits, lo the remainder
-// rounded to 24 bits, so |x - hi - lo| <= 2^-71 |x| for 2^-74 <= |x| < 2^128. Uses integer
-// and FP32 instructions only (no FP64 pipe). |x| < 2^-126 gives 0; |x| >= 2^128, inf or NaN
-// give a NaN hi.
+// rounded to 24 bits, so |x - hi - lo| <= 2^-48 |x| for 2^-74 <= |x| < 2^128. Uses integer
+// and FP32 instructions only (no FP64 pipe), without branches: the 29 mantissa bits below hi
+// are converted to FP32 with one rounding (integer-to-float conversion) and scaled by a power
+// of two. |x| < 2^-126 gives 0; |x| >= 2^128, inf or NaN give a NaN hi.
 __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ffu);
-  if (e < 897) {
-    hi = 0.f;
-    lo = 0.f;
-    return;
-  }
-  if (e > 1150) {
-    hi = __int_as_float(0x7fc00000);
-    lo = 0.f;
-    return;
-  }
-  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-  const unsigned m = (unsigned)(b & 0x1fffffffu);  // the 29 mantissa bits below hi
-  if (e < 949 || m == 0u) {
-    lo = 0.f;
-    return;
-  }
-  // m = m1 2^23 + m0 converted exactly piecewise (2^23 + k - 2^23 = k), then rounded once
-  const float f0 = __uint_as_float(0x4b000000u | (m & 0x7fffffu)) - 8388608.f;
-  const float f1 = __uint_as_float(0x4b000000u | (m >> 23)) - 8388608.f;
-  const float mf = fmaf(f1, 8388608.f, f0);
-  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
-  lo = __uint_as_float(__float_as_uint(mf * scale) | sign);
+  const unsigned top = (unsigned)(b >> 32);
+  const unsigned sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7ffu);
+  const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  hi = e < 897 ? 0.f : (e > 1150 ? __int_as_float(0x7fc00000) : h);
+  const unsigned m = (unsigned)(b & 0x1fffffffu);
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075), for e >= 949
+  const float l = __uint_as_float(__float_as_uint(__uint2float_rn(m) * scale) | sign);
+  lo = (e < 949 || e > 1150) ? 0.f : l;
 }
 
 }  // namespace dgk

@@ -44,8 +44,8 @@ __device__ __forceinline__ void flux_fluct32(const float dq[4], const float ub[3
   if (riemann == 0) {
     float y2[4];
     jac_apply32(ub, un, nh, c0sq, y1, y2);
-    float a = sqrtf(un * un + c0sq);
-    float ia = 1.0f / a;
+    const float ia = rsqrtf(un * un + c0sq);  // 1/a, a^2 = un^2 + c0^2 >= c0^2 > 0
+    const float a = (un * un + c0sq) * ia;
     float aun = fabsf(un);
     float lm = un - a;
     float d1 = (aun + un - a) * ia;
@@ -81,8 +81,8 @@ __device__ __forceinline__ void flux_fluct32_axis(const float dq[4], const float
     y2[0] = c0sq * nx2;
 #pragma unroll
     for (int c = 0; c < 3; ++c) y2[1 + c] = ub[c] * nx2 + un * y1[1 + c] + (c == d ? sg * y1[0] : 0.f);
-    const float a = sqrtf(un * un + c0sq);
-    const float ia = 1.0f / a;
+    const float ia = rsqrtf(un * un + c0sq);
+    const float a = (un * un + c0sq) * ia;
     const float aun = fabsf(un);
     const float lm = un - a;
     const float d1 = (aun + un - a) * ia;
@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 // ---------------------------------------------------------------------------------------
 // inviscid pass, persistent, TMA-staged
 // ---------------------------------------------------------------------------------------
-// Each block loops over tiles of EPB elements. While it computes tile i from one shared input
-// buffer, warp 0 fetches tile i+1 into the other buffer with bulk asynchronous copies
+// Each block loops over tiles of EPB elements. While its consumer warps compute tile i from one
+// shared input buffer, the producer warp fetches tile i+1 into the other buffer with bulk asynchronous copies
 // (cp.async.bulk, completion counted in bytes on an mbarrier): per element the four planes
 // of its FP64 state, every conforming face's neighbour trace planes, the neighbours' and its
 // own viscous traces, its constants and its face links — about 50 copies instead of ~2000
@@ -683,6 +683,16 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   float4* F4 = reinterpret_cast<float4*>(W + le * P::work_elem + P::wF);
   float4* QH4 = reinterpret_cast<float4*>(W + le * P::work_elem + P::wQ);
   float4* QL4 = QH4 + n3;
+  // This thread's (element, face, face node) items of the face and trace-write phases, the
+  // same in every tile: le2 | f << 5 | a << 8 | b << 11 | pv << 14, or -1.
+  constexpr int NFI = EPB * 6 * n2, FR = (NFI + NC - 1) / NC;
+  int fdesc[FR];
+#pragma unroll
+  for (int r = 0; r < FR; ++r) {
+    const int t = tid + r * NC;
+    const int le2 = t / (6 * n2), rr = t % (6 * n2), f = rr / n2, ab = rr % n2;
+    fdesc[r] = t < NFI ? (le2 | f << 5 | (ab % n) << 8 | (ab / n) << 11 | face_node(f, n, ab % n, ab / n) << 14) : -1;
+  }
   // ---- consumer threads ----------------------------------------------------------------
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -787,10 +797,13 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     }
     consumer_sync(NC);  // F is reused for the face terms below
     // ---- faces, one thread per (element, face, face node) -----------------------------
-    for (int t = tid; t < EPB * 6 * n2; t += nthr) {
-      const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
-      const int i2 = tile * EPB + le2;
-      if (i2 >= B.count) continue;
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+      const int fd = fdesc[r];
+      if (fd < 0) break;
+      const int le2 = fd & 31, f = (fd >> 5) & 7, a = (fd >> 8) & 7, bb = (fd >> 11) & 7, pv = fd >> 14;
+      const int ab = a + n * bb;
+      if (tile * EPB + le2 >= B.count) continue;
       const char* I2 = IN + le2 * P::in_elem;
       const unsigned char* SH2 = reinterpret_cast<const unsigned char*>(I2 + P::iSH);
       const FaceLink L = reinterpret_cast<const FaceLink*>(I2 + P::iLK)[f];
@@ -799,8 +812,6 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
       char* W2 = W + le2 * P::work_elem;
       const int d = f >> 1;
       const float sg = (f & 1) ? 1.f : -1.f;
-      const int a = ab % n, bb = ab / n;
-      const int pv = face_node(f, n, a, bb);
       const bool ns2 = MT2->flag != 0;
       float term[4];
       if (L.kind == FK_MORTAR) {
@@ -839,8 +850,9 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 #pragma unroll
           for (int k = 0; k < 3; ++k) Sv[k] = (k == d) ? sg * E2->Ja[d * 4] : 0.f;
         }
-        const float s = GEO == 0 ? fabsf(E2->Ja[d * 4]) : sqrtf(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
-        const float is = 1.f / s;
+        const float ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
+        const float is = GEO == 0 ? 0.f : rsqrtf(ss);  // face area element S = |Sv| > 0
+        const float s = GEO == 0 ? fabsf(E2->Ja[d * 4]) : ss * is;
         const float nh[3] = {Sv[0] * is, Sv[1] * is, Sv[2] * is};
         const float4 h4 = reinterpret_cast<const float4*>(W2 + P::wQ)[pv];
         const float4 l4 = reinterpret_cast<const float4*>(W2 + P::wQ)[n3 + pv];
@@ -941,12 +953,14 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
       consumer_sync(NC);
       // traces of the new state for the next stage, one thread per face slot (coalesced)
       float2* Tn = reinterpret_cast<float2*>(M.Tq_next);
-      for (int t = tid; t < EPB * 6 * n2; t += nthr) {
-        const int le2 = t / (6 * n2), r = t % (6 * n2), f = r / n2, ab = r % n2;
-        const int i2 = tile * EPB + le2;
-        if (i2 >= B.count) continue;
+#pragma unroll
+      for (int r = 0; r < FR; ++r) {
+        const int fd = fdesc[r];
+        if (fd < 0) break;
+        const int le2 = fd & 31, f = (fd >> 5) & 7, pv = fd >> 14;
+        const int ab = ((fd >> 8) & 7) + n * ((fd >> 11) & 7);
+        if (tile * EPB + le2 >= B.count) continue;
         const float4* Q2 = reinterpret_cast<const float4*>(W + le2 * P::work_elem + P::wQ);
-        const int pv = face_node(f, n, ab % n, ab / n);
         const int64_t dst = reinterpret_cast<const EntryMeta*>(IN + le2 * P::in_elem + P::iMT)->troff + f * n2 + ab;
         const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
         Tn[dst] = make_float2(h4.x, l4.x);
