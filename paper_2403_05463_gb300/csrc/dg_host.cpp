@@ -529,6 +529,38 @@ dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector
   return DG_OK;
 }
 
+// Per-entry tables of a set of buckets, in bucket order: the element's 6 face links, its flag
+// and its 32-byte record (read by the pipelined passes instead of chasing the element id).
+dg_status upload_entry_tables(dg_ctx* c, const std::string& prefix, const std::vector<std::vector<int32_t>>& lists,
+                              const std::vector<FaceLink>& link, std::vector<Bucket>& buckets) {
+  dg_status st = DG_OK;
+  for (size_t i = 0; i < buckets.size() && i < lists.size(); ++i) {
+    const std::vector<int32_t>& L = lists[i];
+    std::vector<FaceLink> bl(L.size() * 6);
+    std::vector<uint8_t> bf(L.size());
+    std::vector<EntryMeta> bm(L.size());
+    for (size_t j = 0; j < L.size(); ++j) {
+      for (int f = 0; f < 6; ++f) bl[j * 6 + f] = link[(size_t)L[j] * 6 + f];
+      bf[j] = c->flag[L[j]];
+      bm[j].off = c->off[L[j]];
+      bm[j].troff = c->troff[L[j]];
+      bm[j].elem = L[j];
+      bm[j].flag = c->flag[L[j]];
+      bm[j].pad = 0;
+    }
+    FaceLink* dbl;
+    uint8_t* dbf;
+    EntryMeta* dbm;
+    if ((st = dev_upload(c, prefix + "l" + std::to_string(i), bl, &dbl)) != DG_OK) return st;
+    if ((st = dev_upload(c, prefix + "f" + std::to_string(i), bf, &dbf)) != DG_OK) return st;
+    if ((st = dev_upload(c, prefix + "m" + std::to_string(i), bm, &dbm)) != DG_OK) return st;
+    buckets[i].blink = dbl;
+    buckets[i].bflag = dbf;
+    buckets[i].bmeta = dbm;
+  }
+  return st;
+}
+
 // flag-dependent tables: links' neighbour flags, NS buckets, mortar lifting slots
 dg_status rebuild_flags(dg_ctx* c) {
   std::vector<FaceLink> link(c->ne * 6);
@@ -564,30 +596,7 @@ dg_status rebuild_flags(dg_ctx* c) {
   if (st != DG_OK) return st;
   c->M.link = dl;
   // per-entry link and flag tables of the all-element buckets
-  for (size_t i = 0; i < c->all_buckets.size() && i < c->all_lists.size(); ++i) {
-    const std::vector<int32_t>& L = c->all_lists[i];
-    std::vector<FaceLink> bl(L.size() * 6);
-    std::vector<uint8_t> bf(L.size());
-    std::vector<EntryMeta> bm(L.size());
-    for (size_t j = 0; j < L.size(); ++j) {
-      for (int f = 0; f < 6; ++f) bl[j * 6 + f] = link[(size_t)L[j] * 6 + f];
-      bf[j] = c->flag[L[j]];
-      bm[j].off = c->off[L[j]];
-      bm[j].troff = c->troff[L[j]];
-      bm[j].elem = L[j];
-      bm[j].flag = c->flag[L[j]];
-      bm[j].pad = 0;
-    }
-    FaceLink* dbl;
-    uint8_t* dbf;
-    EntryMeta* dbm;
-    if ((st = dev_upload(c, "allbl" + std::to_string(i), bl, &dbl)) != DG_OK) return st;
-    if ((st = dev_upload(c, "allbf" + std::to_string(i), bf, &dbf)) != DG_OK) return st;
-    if ((st = dev_upload(c, "allbm" + std::to_string(i), bm, &dbm)) != DG_OK) return st;
-    c->all_buckets[i].blink = dbl;
-    c->all_buckets[i].bflag = dbf;
-    c->all_buckets[i].bmeta = dbm;
-  }
+  if ((st = upload_entry_tables(c, "allb", c->all_lists, link, c->all_buckets)) != DG_OK) return st;
   uint8_t* df;
   if ((st = dev_upload(c, "flag", c->flag, &df)) != DG_OK) return st;
   c->M.flag = df;
@@ -603,7 +612,9 @@ dg_status rebuild_flags(dg_ctx* c) {
       ++it;
     }
   }
-  if ((st = upload_buckets(c, "nsb", ns_elems, true, true, c->ns_buckets)) != DG_OK) return st;
+  std::vector<std::vector<int32_t>> ns_lists;
+  if ((st = upload_buckets(c, "nsb", ns_elems, true, true, c->ns_buckets, &ns_lists)) != DG_OK) return st;
+  if ((st = upload_entry_tables(c, "nsbx", ns_lists, link, c->ns_buckets)) != DG_OK) return st;
   // viscous traces of Euler elements are never written: keep them at zero
   if (c->M.Tv) CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
   c->version++;

@@ -60,11 +60,13 @@ struct DevMesh {
   const double* geo;         // curved elements: [10][total] = Ja[9] (d*3+k) then J
   const ElemConst32* ec32;   // [E] FP32 constants
   const float* geo32;        // curved elements: [10][total] = Ja[9] then 1/J (FP32)
-  double* Tq;                // [4][tr_total] face traces of q: FP64 values, or with precision 1
-                             // (hi, lo) FP32 pairs, hi + lo = q to 2^-48 relative
+  double* Tq;                // face traces of q: FP64 [4][tr_total], or with precision 1 FP32
+                             // (hi, lo) pairs, hi + lo = q to 2^-48 relative, interleaved per
+                             // slot [tr_total][4] (one 32-byte record per face node)
   double* Tq_next;           // traces of the updated q written by the RK update for the next
                              // stage (double-buffered with Tq: neighbours still read Tq)
-  double* Tv;                // [3][tr_total] outward viscous flux traces tau . S (NS elements)
+  double* Tv;                // outward viscous flux traces tau . S (NS elements): FP64
+                             // [3][tr_total], or with precision 1 FP32 [tr_total][3]
   double* rv;                // [3][total]    J * viscous volume divergence (NS elements)
   double* LU;                // [9][tr_total] projected BR1 lifting u*_c S_k on mortar faces
   double* LH;                // [4][tr_total] projected total flux (F_e* - F_v*) . S on mortars

@@ -491,18 +491,19 @@ __device__ __forceinline__ void node_metric(const DevMesh& M, int e, int64_t nod
   }
 }
 
-// trace value of q: FP64, or an FP32 (hi, lo) pair with precision 1
-__device__ __forceinline__ double tq_load(const DevMesh& M, int64_t i) {
+// trace value of variable v at trace slot `slot`: FP64 planes [4][tr_total], or with precision 1
+// FP32 (hi, lo) pairs interleaved per slot, [tr_total][4]
+__device__ __forceinline__ double tq_load(const DevMesh& M, int v, int64_t slot) {
   if (M.precision == 1) {
-    const float2 t = reinterpret_cast<const float2*>(M.Tq)[i];
+    const float2 t = reinterpret_cast<const float2*>(M.Tq)[slot * 4 + v];
     return (double)t.x + (double)t.y;
   }
-  return M.Tq[i];
+  return M.Tq[v * M.tr_total + slot];
 }
 
-// viscous trace value: FP64 or FP32 storage depending on the precision of the passes
-__device__ __forceinline__ double tv_load(const DevMesh& M, int64_t i) {
-  return M.precision == 1 ? (double)reinterpret_cast<const float*>(M.Tv)[i] : M.Tv[i];
+// viscous trace component c at `slot`: FP64 planes [3][tr_total], or FP32 [tr_total][3]
+__device__ __forceinline__ double tv_load(const DevMesh& M, int c, int64_t slot) {
+  return M.precision == 1 ? (double)reinterpret_cast<const float*>(M.Tv)[slot * 3 + c] : M.Tv[c * M.tr_total + slot];
 }
 
 // loads my face field (nvar from `src` planes, stride tr_total) and S at my face nodes
@@ -531,10 +532,10 @@ __global__ void k_mortar_lift(DevMesh M, const int32_t* __restrict__ slots, int 
     double Ja[9];
     node_metric(M, e, node, Ja);
     for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
-    for (int c = 0; c < 3; ++c) sm.mine[c][t] = tq_load(M, (1 + c) * M.tr_total + M.tr_off[e] + f * nm * nm + t);
+    for (int c = 0; c < 3; ++c) sm.mine[c][t] = tq_load(M, 1 + c, M.tr_off[e] + f * nm * nm + t);
   }
   if (t < nn * nn)
-    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = tq_load(M, (1 + c) * M.tr_total + M.tr_off[L.nbr] + L.nface * nn * nn + t);
+    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = tq_load(M, 1 + c, M.tr_off[L.nbr] + L.nface * nn * nn + t);
   __syncthreads();
   if (t < nM * nM) {
     const int a = t % nM, b = t / nM;
@@ -579,13 +580,13 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
     node_metric(M, e, node, Ja);
     for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
     const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
-    for (int v = 0; v < 4; ++v) sm.mine[v][t] = tq_load(M, v * M.tr_total + s0);
-    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? tv_load(M, c * M.tr_total + s0) : 0.0;
+    for (int v = 0; v < 4; ++v) sm.mine[v][t] = tq_load(M, v, s0);
+    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? tv_load(M, c, s0) : 0.0;
   }
   if (t < nn * nn) {
     const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
-    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = tq_load(M, v * M.tr_total + s1);
-    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? tv_load(M, c * M.tr_total + s1) : 0.0;
+    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = tq_load(M, v, s1);
+    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? tv_load(M, c, s1) : 0.0;
   }
   __syncthreads();
   if (t < nM * nM) {

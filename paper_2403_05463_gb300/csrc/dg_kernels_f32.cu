@@ -129,10 +129,6 @@ __device__ __forceinline__ float eddy_visc32(const float G[3][3], float delta, i
   return cv * sqrtf(B / aa);
 }
 
-__device__ __forceinline__ float2 tq2(const DevMesh& M, int64_t i) {
-  return reinterpret_cast<const float2*>(M.Tq)[i];
-}
-
 // FP32 geometry of element e at node p (affine: element constants; curved: per node)
 template <bool CURVED>
 __device__ __forceinline__ void metric32(const DevMesh& M, int e, int64_t node, float Ja[9], float& invJ) {
@@ -149,7 +145,7 @@ __device__ __forceinline__ void metric32(const DevMesh& M, int e, int64_t node, 
 }
 
 // ---------------------------------------------------------------------------------------
-// traces as (hi, lo) FP32 pairs
+// traces as (hi, lo) FP32 pairs, one 32-byte record (p, u, v, w) per face node
 // ---------------------------------------------------------------------------------------
 template <int N>
 __global__ void k_traces32(DevMesh M, const int32_t* __restrict__ list, int count, const double* __restrict__ q) {
@@ -161,13 +157,12 @@ __global__ void k_traces32(DevMesh M, const int32_t* __restrict__ list, int coun
   const int e = list[le];
   const int64_t src = M.elem_off[e] + face_node(f, n, ab % n, ab / n);
   const int64_t dst = M.tr_off[e] + f * n2 + ab;
-  float2* T = reinterpret_cast<float2*>(M.Tq);
+  float h[4], l[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    float2 t;
-    split_hilo(__ldg(&q[v * M.total + src]), t.x, t.y);
-    T[v * M.tr_total + dst] = t;
-  }
+  for (int v = 0; v < 4; ++v) split_hilo(__ldg(&q[v * M.total + src]), h[v], l[v]);
+  float4* T = reinterpret_cast<float4*>(M.Tq) + 2 * dst;
+  T[0] = make_float4(h[0], l[0], h[1], l[1]);
+  T[1] = make_float4(h[2], l[2], h[3], l[3]);
 }
 
 // Minimum resident blocks per SM for the register cap (four 256-thread blocks: 64 registers).
@@ -236,7 +231,7 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
     const int64_t src = L.nslot + ab;
     float2* nu = reinterpret_cast<float2*>(sE + le2 * PE + LV::oNU);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cp_async8(&nu[(f * 3 + c) * n2 + ab], &Tq2[(1 + c) * M.tr_total + src]);
+    for (int c = 0; c < 3; ++c) cp_async8(&nu[(f * 3 + c) * n2 + ab], &Tq2[src * 4 + 1 + c]);
   }
   int le = tid / n3;
   const int p = tid % n3;
@@ -408,7 +403,7 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
       const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
       const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Tvf[c * M.tr_total + ms] = sg * Fv[d][c];
+      for (int c = 0; c < 3; ++c) Tvf[ms * 3 + c] = sg * Fv[d][c];
     }
   }
   __syncthreads();
@@ -436,23 +431,23 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 // Each block loops over tiles of EPB elements. While its consumer warps compute tile i from one
 // shared input buffer, the producer warp fetches tile i+1 into the other buffer with bulk asynchronous copies
 // (cp.async.bulk, completion counted in bytes on an mbarrier): per element the four planes
-// of its FP64 state, every conforming face's neighbour trace planes, the neighbours' and its
-// own viscous traces, its constants and its face links — about 50 copies instead of ~2000
-// thread-level copies. A bulk copy needs 16-byte-aligned ends, so each copy covers the
-// 16-byte-aligned superset of its range and the offset of the first wanted byte is kept in
-// a small table. Per element (bytes):
-//   QD [4] slots of a16(8 n3 + 16) | NT [6][4] slots of a16(8 n2 + 16) |
-//   NV [6][3] slots of a16(4 n2 + 16) | OV [3] slots of a16(24 n2 + 16) | LK 96 | EC 48 |
-//   MT 32 (EntryMeta) | SH 64 (byte offsets of the slots' first wanted byte)
+// of its FP64 state, every conforming face's neighbour traces (one 32-byte record per face
+// node), the neighbours' and its own viscous traces (12 bytes per face node) and its
+// constants — at most 18 copies instead of ~2000 thread-level copies. A bulk copy needs
+// 16-byte-aligned ends, so each copy covers the 16-byte-aligned superset of its range and the
+// offset of the first wanted byte is kept in a small table. Per element (bytes):
+//   QD [4] slots of a16(8 n3 + 16) | NT [6] slots of a16(32 n2 + 16) |
+//   NV [6] slots of a16(12 n2 + 16) | OV a16(72 n2 + 16) | LK 96 | EC 48 |
+//   MT 32 (EntryMeta) | SH 32 (byte offsets of the slots' first wanted byte)
 template <int N>
 struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
-  static constexpr int SQD = a16(8 * n3 + 16), SNT = a16(8 * n2 + 16), SNV = a16(4 * n2 + 16),
-                       SOV = a16(24 * n2 + 16);
-  static constexpr int iQD = 0, iNT = 4 * SQD, iNV = iNT + 24 * SNT, iOV = iNV + 18 * SNV, iLK = iOV + 3 * SOV,
-                       iEC = iLK + 96, iMT = iEC + 48, iSH = iMT + 32, in_elem = a16(iSH + 64);
-  static constexpr int ITEMS = 50;  // copies per element: 4 QD, 24 NT, 18 NV, 3 OV, EC
+  static constexpr int SQD = a16(8 * n3 + 16), SNT = a16(32 * n2 + 16), SNV = a16(12 * n2 + 16),
+                       SOV = a16(72 * n2 + 16);
+  static constexpr int iQD = 0, iNT = 4 * SQD, iNV = iNT + 6 * SNT, iOV = iNV + 6 * SNV, iLK = iOV + SOV,
+                       iEC = iLK + 96, iMT = iEC + 48, iSH = iMT + 32, in_elem = a16(iSH + 32);
+  static constexpr int ITEMS = 18;  // copies per element: 4 QD, 6 NT, 6 NV, OV, EC
   static constexpr int wF = 0, wQ = 48 * n3, work_elem = 80 * n3;
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
@@ -507,32 +502,29 @@ __device__ __forceinline__ bool tma_item(const DevMesh& M, const double* qin, co
     sh_index = k;
     return true;
   }
-  if (k < 28) {
-    const int f = (k - 4) / 4, v = (k - 4) % 4;
-    const FaceLink& L = lk[f];
+  if (k < 10) {
+    const FaceLink& L = lk[k - 4];
     if (L.kind != FK_CONF) return false;
-    src = reinterpret_cast<const char*>(M.Tq + (int64_t)v * M.tr_total + L.nslot);
-    len = 8 * n2;
+    src = reinterpret_cast<const char*>(M.Tq + L.nslot * 4);  // 4 (hi, lo) pairs = 4 doubles
+    len = 32 * n2;
     slot = P::iNT + (k - 4) * P::SNT;
     sh_index = k;
     return true;
   }
-  if (k < 46) {
-    const int f = (k - 28) / 3, c = (k - 28) % 3;
-    const FaceLink& L = lk[f];
+  if (k < 16) {
+    const FaceLink& L = lk[k - 10];
     if (L.kind != FK_CONF || !L.nflag) return false;
-    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + (int64_t)c * M.tr_total + L.nslot);
-    len = 4 * n2;
-    slot = P::iNV + (k - 28) * P::SNV;
+    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + L.nslot * 3);
+    len = 12 * n2;
+    slot = P::iNV + (k - 10) * P::SNV;
     sh_index = k;
     return true;
   }
-  if (k < 49) {
+  if (k == 16) {
     if (!mt.flag) return false;
-    const int c = k - 46;
-    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + (int64_t)c * M.tr_total + mt.troff);
-    len = 4 * 6 * n2;
-    slot = P::iOV + c * P::SOV;
+    src = reinterpret_cast<const char*>(reinterpret_cast<const float*>(M.Tv) + mt.troff * 3);
+    len = 72 * n2;
+    slot = P::iOV;
     sh_index = k;
     return true;
   }
@@ -543,26 +535,63 @@ __device__ __forceinline__ bool tma_item(const DevMesh& M, const double* qin, co
   return true;
 }
 
-// The producer warp fills buffer IN with tile `tile`, completion on `bar` (32 arrivals):
-// (1) each element's record and face links, with independent loads, into the buffer's MT/LK
-// slots; (2) the copy plan from those, the shift table, the expected byte count; (3) the bulk
-// copies.
+// The records of one tile, held in the producer warp's registers between the time they are
+// loaded and the time the tile's input buffer is free: record r = lane + 32 j of the tile's
+// EPB x 7 records (k = r % 7 = 0: the element's 32-byte EntryMeta, 1..6: its face links).
+template <int N>
+struct TileRecs {
+  static constexpr int R = (Shape<N>::EPB * 7 + 31) / 32;
+  uint4 a[R], b[R];
+};
+
+template <int N>
+__device__ __forceinline__ void load_recs(const Bucket& B, int tile, TileRecs<N>& T) {
+  constexpr int EPB = Shape<N>::EPB;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < TileRecs<N>::R; ++j) {
+    const int r = lane + 32 * j, le = r / 7, k = r % 7, i = tile * EPB + le;
+    if (r < EPB * 7 && i < B.count) {
+      if (k == 0) {
+        const uint4* m = reinterpret_cast<const uint4*>(&B.bmeta[i]);
+        T.a[j] = m[0];
+        T.b[j] = m[1];
+      } else {
+        T.a[j] = *reinterpret_cast<const uint4*>(&B.blink[(int64_t)i * 6 + (k - 1)]);
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_recs(const Bucket& B, int tile, const TileRecs<N>& T, char* IN) {
+  using P = TmaSmem32<N>;
+  constexpr int EPB = Shape<N>::EPB;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < TileRecs<N>::R; ++j) {
+    const int r = lane + 32 * j, le = r / 7, k = r % 7, i = tile * EPB + le;
+    if (r < EPB * 7 && i < B.count) {
+      char* base = IN + le * P::in_elem;
+      if (k == 0) {
+        reinterpret_cast<uint4*>(base + P::iMT)[0] = T.a[j];
+        reinterpret_cast<uint4*>(base + P::iMT)[1] = T.b[j];
+      } else {
+        reinterpret_cast<uint4*>(base + P::iLK)[k - 1] = T.a[j];
+      }
+    }
+  }
+}
+
+// The producer warp fills buffer IN with tile `tile`, completion on `bar` (32 arrivals), from
+// the records already in the buffer's MT/LK slots: the copy plan, the shift table and the
+// expected byte count, then the bulk copies.
 template <int N>
 __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, const double* qin, int tile, char* IN,
                                           void* bar) {
   using P = TmaSmem32<N>;
   constexpr int EPB = P::EPB;
   const int lane = threadIdx.x & 31;
-  for (int r = lane; r < EPB * 7; r += 32) {
-    const int le = r / 7, k = r % 7, i = tile * EPB + le;
-    if (i >= B.count) continue;
-    char* base = IN + le * P::in_elem;
-    if (k == 0)
-      *reinterpret_cast<EntryMeta*>(base + P::iMT) = B.bmeta[i];
-    else
-      reinterpret_cast<FaceLink*>(base + P::iLK)[k - 1] = B.blink[(int64_t)i * 6 + (k - 1)];
-  }
-  __syncwarp();
   unsigned total = 0;
   for (int it = lane; it < EPB * P::ITEMS; it += 32) {
     const int le = it / P::ITEMS, k = it % P::ITEMS;
@@ -660,6 +689,10 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   __syncthreads();
   if (tid >= NC) {
     // ---- producer warp ----------------------------------------------------------------
+    // the records of the next tile are loaded one tile ahead, so their latency is hidden
+    // behind the wait for a free buffer and the copies of the current tile
+    TileRecs<N> recs;
+    if ((int)blockIdx.x < ntiles) load_recs<N>(B, blockIdx.x, recs);
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
@@ -670,7 +703,11 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         }
         return;
       }
-      tma_stage<N>(M, B, qin, tile, b ? IN1 : IN0, b ? bar1 : bar0);
+      char* IN = b ? IN1 : IN0;
+      store_recs<N>(B, tile, recs, IN);
+      if (tile + (int)gridDim.x < ntiles) load_recs<N>(B, tile + gridDim.x, recs);
+      __syncwarp();
+      tma_stage<N>(M, B, qin, tile, IN, b ? bar1 : bar0);
     }
     return;
   }
@@ -834,7 +871,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         for (int c = 0; c < 3; ++c) {
           const double own = qq[1 + c] * un + qq[0] * Sd[c];
           float t2 = (float)(M.LH[(1 + c) * M.tr_total + ms] - own);
-          if (ns2) t2 += reinterpret_cast<const float*>(I2 + P::iOV + c * P::SOV + SH2[46 + c])[f * n2 + ab];
+          if (ns2) t2 += reinterpret_cast<const float*>(I2 + P::iOV + SH2[16])[(f * n2 + ab) * 3 + c];
           term[1 + c] = t2;
         }
       } else {
@@ -863,12 +900,13 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
           int a1, b1;
           inv_orient(L.orient, N, a, bb, a1, b1);
           nab = a1 + n * b1;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int sl = 4 + f * 4 + v;
-            const float2 tq = reinterpret_cast<const float2*>(I2 + P::iNT + (f * 4 + v) * P::SNT + SH2[sl])[nab];
-            dqf[v] = (tq.x - qh[v]) + (tq.y - ql[v]);
-          }
+          // the neighbour's 32-byte record (p, u, v, w as hi, lo); 16-byte aligned, no shift
+          const float4* tr = reinterpret_cast<const float4*>(I2 + P::iNT + f * P::SNT) + 2 * nab;
+          const float4 t01 = tr[0], t23 = tr[1];
+          dqf[0] = (t01.x - qh[0]) + (t01.y - ql[0]);
+          dqf[1] = (t01.z - qh[1]) + (t01.w - ql[1]);
+          dqf[2] = (t23.x - qh[2]) + (t23.y - ql[2]);
+          dqf[3] = (t23.z - qh[3]) + (t23.w - ql[3]);
         } else if (L.kind == FK_INFLOW) {
           dqf[0] = 0.f;
 #pragma unroll
@@ -901,9 +939,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             float tv = 0.f;
-            if (ns2) tv += reinterpret_cast<const float*>(I2 + P::iOV + c * P::SOV + SH2[46 + c])[f * n2 + ab];
-            if (L.nflag)
-              tv += reinterpret_cast<const float*>(I2 + P::iNV + (f * 3 + c) * P::SNV + SH2[28 + f * 3 + c])[nab];
+            if (ns2) tv += reinterpret_cast<const float*>(I2 + P::iOV + SH2[16])[(f * n2 + ab) * 3 + c];
+            if (L.nflag) tv += reinterpret_cast<const float*>(I2 + P::iNV + f * P::SNV + SH2[10 + f])[nab * 3 + c];
             term[1 + c] += 0.5f * tv;
           }
         }
@@ -952,7 +989,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     if (MODE == MODE_RK && write_tr) {
       consumer_sync(NC);
       // traces of the new state for the next stage, one thread per face slot (coalesced)
-      float2* Tn = reinterpret_cast<float2*>(M.Tq_next);
+      float4* Tn = reinterpret_cast<float4*>(M.Tq_next);
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
         const int fd = fdesc[r];
@@ -963,10 +1000,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         const float4* Q2 = reinterpret_cast<const float4*>(W + le2 * P::work_elem + P::wQ);
         const int64_t dst = reinterpret_cast<const EntryMeta*>(IN + le2 * P::in_elem + P::iMT)->troff + f * n2 + ab;
         const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
-        Tn[dst] = make_float2(h4.x, l4.x);
-        Tn[M.tr_total + dst] = make_float2(h4.y, l4.y);
-        Tn[2 * M.tr_total + dst] = make_float2(h4.z, l4.z);
-        Tn[3 * M.tr_total + dst] = make_float2(h4.w, l4.w);
+        Tn[2 * dst] = make_float4(h4.x, l4.x, h4.y, l4.y);
+        Tn[2 * dst + 1] = make_float4(h4.z, l4.z, h4.w, l4.w);
       }
     }
     consumer_sync(NC);  // work buffers are reused by the next tile
