@@ -51,4 +51,17 @@ __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
   lo = (e < 949 || e > 1150) ? 0.f : l;
 }
 
+// Exact FP32 -> FP64 widening with integer instructions only (GB300 runs FP32<->FP64
+// conversions on the FP64 pipe, 1/64 of the FP32 rate): the exponent is re-biased from 127 to
+// 1023 and the 23-bit mantissa moved to the top of the 52-bit field. FP32 subnormals
+// (|x| < 2^-126) become a signed zero; infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const unsigned ew = e == 0xffu ? 0x7ffu : e + 896u;
+  const unsigned hi = e == 0u ? sign : (sign | (ew << 20) | (m >> 3));
+  const unsigned lo = e == 0u ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 }  // namespace dgk

@@ -535,6 +535,50 @@ __device__ __forceinline__ bool tma_item(const DevMesh& M, const double* qin, co
   return true;
 }
 
+// Shared-memory layout of the pipelined viscous pass (box and affine elements), per element
+// (bytes): QV [3] slots of a16(8 n3 + 16) (velocity planes) | NT [6] slots of a16(32 n2 + 16)
+// (neighbours' trace records) | LK 96 | EC 48 | MT 32 | SH 32; work: U [3 n3] velocity
+// deviations and F [9 n3] contravariant viscous fluxes (floats).
+template <int N>
+struct ViscTmaSmem32 {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
+  static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
+  static constexpr int SQV = a16(8 * n3 + 16), SNT = a16(32 * n2 + 16);
+  static constexpr int iQV = 0, iNT = 3 * SQV, iLK = iNT + 6 * SNT, iEC = iLK + 96, iMT = iEC + 48,
+                       iSH = iMT + 32, in_elem = a16(iSH + 32);
+  static constexpr int ITEMS = 10;  // copies per element: 3 QV, 6 NT, EC
+  static constexpr int wU = 0, wF = 12 * n3, work_elem = a16(48 * n3);
+  static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
+  static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
+};
+
+template <int N>
+__device__ __forceinline__ bool vtma_item(const DevMesh& M, const double* q, const EntryMeta& mt, const FaceLink* lk,
+                                          int k, const char*& src, int& len, int& slot, int& sh_index) {
+  using P = ViscTmaSmem32<N>;
+  if (k < 3) {
+    src = reinterpret_cast<const char*>(q + (int64_t)(1 + k) * M.total + mt.off);
+    len = 8 * P::n3;
+    slot = P::iQV + k * P::SQV;
+    sh_index = k;
+    return true;
+  }
+  if (k < 9) {
+    const FaceLink& L = lk[k - 3];
+    if (L.kind != FK_CONF) return false;
+    src = reinterpret_cast<const char*>(M.Tq + L.nslot * 4);
+    len = 32 * P::n2;
+    slot = P::iNT + (k - 3) * P::SNT;
+    sh_index = k;
+    return true;
+  }
+  src = reinterpret_cast<const char*>(&M.ec32[mt.elem]);
+  len = 48;
+  slot = P::iEC;
+  sh_index = -1;
+  return true;
+}
+
 // The records of one tile, held in the producer warp's registers between the time they are
 // loaded and the time the tile's input buffer is free: record r = lane + 32 j of the tile's
 // EPB x 7 records (k = r % 7 = 0: the element's 32-byte EntryMeta, 1..6: its face links).
@@ -563,9 +607,8 @@ __device__ __forceinline__ void load_recs(const Bucket& B, int tile, TileRecs<N>
   }
 }
 
-template <int N>
+template <int N, class P>
 __device__ __forceinline__ void store_recs(const Bucket& B, int tile, const TileRecs<N>& T, char* IN) {
-  using P = TmaSmem32<N>;
   constexpr int EPB = Shape<N>::EPB;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -585,11 +628,21 @@ __device__ __forceinline__ void store_recs(const Bucket& B, int tile, const Tile
 
 // The producer warp fills buffer IN with tile `tile`, completion on `bar` (32 arrivals), from
 // the records already in the buffer's MT/LK slots: the copy plan, the shift table and the
-// expected byte count, then the bulk copies.
-template <int N>
+// expected byte count, then the bulk copies. P is the shared-memory layout, VISC selects the
+// viscous pass's copies (velocity planes, neighbour trace records, constants).
+template <int N, class P, bool VISC>
+__device__ __forceinline__ bool stage_item(const DevMesh& M, const double* qin, const EntryMeta& mt,
+                                           const FaceLink* lk, int k, const char*& src, int& len, int& slot,
+                                           int& sh) {
+  if constexpr (VISC)
+    return vtma_item<N>(M, qin, mt, lk, k, src, len, slot, sh);
+  else
+    return tma_item<N>(M, qin, mt, lk, k, src, len, slot, sh);
+}
+
+template <int N, class P, bool VISC>
 __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, const double* qin, int tile, char* IN,
                                           void* bar) {
-  using P = TmaSmem32<N>;
   constexpr int EPB = P::EPB;
   const int lane = threadIdx.x & 31;
   unsigned total = 0;
@@ -599,8 +652,8 @@ __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, con
     char* base = IN + le * P::in_elem;
     const char* src;
     int len, slot, sh;
-    if (!tma_item<N>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
-                     reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
+    if (!stage_item<N, P, VISC>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
+                                reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
       continue;
     const uintptr_t a = reinterpret_cast<uintptr_t>(src);
     const uintptr_t s0 = a & ~(uintptr_t)15, e0 = (a + len + 15) & ~(uintptr_t)15;
@@ -615,8 +668,8 @@ __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, con
     char* base = IN + le * P::in_elem;
     const char* src;
     int len, slot, sh;
-    if (!tma_item<N>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
-                     reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
+    if (!stage_item<N, P, VISC>(M, qin, *reinterpret_cast<const EntryMeta*>(base + P::iMT),
+                                reinterpret_cast<const FaceLink*>(base + P::iLK), k, src, len, slot, sh))
       continue;
     const uintptr_t a = reinterpret_cast<uintptr_t>(src);
     const uintptr_t s0 = a & ~(uintptr_t)15, e0 = (a + len + 15) & ~(uintptr_t)15;
@@ -704,10 +757,10 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         return;
       }
       char* IN = b ? IN1 : IN0;
-      store_recs<N>(B, tile, recs, IN);
+      store_recs<N, P>(B, tile, recs, IN);
       if (tile + (int)gridDim.x < ntiles) load_recs<N>(B, tile + gridDim.x, recs);
       __syncwarp();
-      tma_stage<N>(M, B, qin, tile, IN, b ? bar1 : bar0);
+      tma_stage<N, P, false>(M, B, qin, tile, IN, b ? bar1 : bar0);
     }
     return;
   }
@@ -976,7 +1029,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
           const float gi = fmaf(A, gold[v], JR[v] * invJ * dtf);
           g32[ix] = gi;
           const double qo = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v])[p];
-          const double qn = fma(Bc, (double)gi, qo);
+          const double qn = fma(Bc, widen_f32(gi), qo);
           out[ix] = qn;
           if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
         }
@@ -1010,6 +1063,236 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 }
 
 // ---------------------------------------------------------------------------------------
+// viscous pass, persistent, TMA-staged (box and affine elements)
+// ---------------------------------------------------------------------------------------
+// The same producer/consumer scheme as the inviscid pass: the last warp stages each tile's
+// velocity planes, neighbour trace records and constants; the consumer threads (one per node)
+// compute the BR1 gradient with its lifting, the eddy viscosity, tau and the contravariant
+// viscous fluxes, write the viscous face traces, and release the input buffer before the
+// divergence. Two consumer barriers per tile: U is written before the first and read before
+// the second; F is written between them and read after the second, and the next tile writes F
+// only after its first barrier.
+template <int N, int GEO>
+__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+    k_viscous32t(DevMesh M, Bucket B, const double* q) {
+  using S = Shape<N>;
+  using P = ViscTmaSmem32<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  constexpr int NC = Shape<N>::threads;  // consumer threads
+  extern __shared__ __align__(128) char smc[];
+  void* bar0 = smc + P::oBAR;
+  void* bar1 = smc + P::oBAR + 8;
+  void* ebar0 = smc + P::oBAR + 16;
+  void* ebar1 = smc + P::oBAR + 24;
+  float* sD = reinterpret_cast<float*>(smc + P::oD);
+  char* const IN0 = smc + P::oIN0;
+  char* const IN1 = smc + P::oIN1;
+  char* W = smc + P::oW;
+  const int tid = threadIdx.x;
+  const int ntiles = (B.count + EPB - 1) / EPB;
+  float* Tvf = reinterpret_cast<float*>(M.Tv);
+  float* rvf = reinterpret_cast<float*>(M.rv);
+  for (int t = tid; t < n2; t += NC) sD[t] = c_ops32.D[N][t];
+  if (tid == 0) {
+    mbar_init(bar0, 32);
+    mbar_init(bar1, 32);
+    mbar_init(ebar0, NC / 32);
+    mbar_init(ebar1, NC / 32);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid >= NC) {
+    // ---- producer warp ----------------------------------------------------------------
+    TileRecs<N> recs;
+    if ((int)blockIdx.x < ntiles) load_recs<N>(B, blockIdx.x, recs);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1))) {
+        if (tid == NC) {
+          atomicCAS(&M.err[0], 0, kErrTimeout);
+          atomicCAS(&M.err[1], 0, 4);
+        }
+        return;
+      }
+      char* IN = b ? IN1 : IN0;
+      store_recs<N, P>(B, tile, recs, IN);
+      if (tile + (int)gridDim.x < ntiles) load_recs<N>(B, tile + gridDim.x, recs);
+      __syncwarp();
+      tma_stage<N, P, true>(M, B, q, tile, IN, b ? bar1 : bar0);
+    }
+    return;
+  }
+  int le = tid / n3;
+  const int p = tid % n3;
+  const bool lane_ok = le < EPB;
+  if (!lane_ok) le = EPB - 1;
+  const int ii[3] = {p % n, (p / n) % n, p / n2};
+  const int str[3] = {1, n, n2};
+  float* U = reinterpret_cast<float*>(W + le * P::work_elem + P::wU);
+  float* F = reinterpret_cast<float*>(W + le * P::work_elem + P::wF);
+  const float invw = c_ops32.w0inv[N];
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int cur = it & 1;
+    const bool active = lane_ok && tile * EPB + le < B.count;
+    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1));
+    if (consumer_any(!ok, NC)) {
+      if (tid == 0) {
+        atomicCAS(&M.err[0], 0, kErrTimeout);
+        atomicCAS(&M.err[1], 0, 3);
+      }
+      return;
+    }
+    const char* INe = (cur ? IN1 : IN0) + le * P::in_elem;
+    const EntryMeta* MT = reinterpret_cast<const EntryMeta*>(INe + P::iMT);
+    const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
+    const unsigned char* SH = reinterpret_cast<const unsigned char*>(INe + P::iSH);
+    int64_t off = 0, troff = 0;
+    int e = 0;
+    float Ja[9], invJ = 0.f, delta = 0.f;
+    float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+    if (active) {
+      off = MT->off;
+      troff = MT->troff;
+      e = MT->elem;
+      delta = EC->delta;
+      invJ = EC->invJ;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = EC->Ja[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double* QV = reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c]);
+        split_hilo(QV[p], uh[c], ul[c]);
+        U[c * n3 + p] = (uh[c] - hi_part(QV[0])) + ul[c];  // deviation from the element's first node
+      }
+    }
+    consumer_sync(NC);
+    if (active) {
+      float G[3][3];
+      {
+        float du[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int bs = p - ii[d] * str[d];
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            const float dm = sD[ii[d] * n + m];
+            const int pm = bs + m * str[d];
+            s0 += dm * U[pm];
+            s1 += dm * U[n3 + pm];
+            s2 += dm * U[2 * n3 + pm];
+          }
+          du[0][d] = s0;
+          du[1][d] = s1;
+          du[2][d] = s2;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            G[c][k] = GEO == 0 ? Ja[k * 4] * du[c][k] : Ja[k] * du[c][0] + Ja[3 + k] * du[c][1] + Ja[6 + k] * du[c][2];
+      }
+      // BR1 lifting on the faces of this node: (1/w_end) (u* - u) S
+      const FaceLink* LK = reinterpret_cast<const FaceLink*>(INe + P::iLK);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (ii[d] != 0 && ii[d] != N) continue;
+        const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+        const float sg = side ? 1.f : -1.f;
+        const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+        const FaceLink L = LK[f];
+        const float Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+        if (L.kind == FK_MORTAR) {
+          const int64_t ms = troff + f * n2 + a + n * b;
+          double Sd[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Sd[k] = sg * M.ec[e].Ja[d * 3 + k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double uc = q[(1 + c) * M.total + off + p];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) G[c][k] += invw * (float)(M.LU[(c * 3 + k) * M.tr_total + ms] - uc * Sd[k]);
+          }
+        } else {
+          float jump[3] = {0.f, 0.f, 0.f};
+          if (L.kind == FK_CONF) {
+            int a1, b1;
+            inv_orient(L.orient, N, a, b, a1, b1);
+            // the neighbour's record (p, u, v, w as hi, lo); 16-byte aligned, no shift
+            const float4* tr = reinterpret_cast<const float4*>(INe + P::iNT + f * P::SNT) + 2 * (a1 + n * b1);
+            const float4 t01 = tr[0], t23 = tr[1];
+            jump[0] = (t01.z - uh[0]) + (t01.w - ul[0]);
+            jump[1] = (t23.x - uh[1]) + (t23.y - ul[1]);
+            jump[2] = (t23.z - uh[2]) + (t23.w - ul[2]);
+          } else if (L.kind == FK_INFLOW) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float ih, il;
+              split_hilo(M.inflow[1 + c], ih, il);
+              jump[c] = (ih - uh[c]) + (il - ul[c]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) G[c][k] += invw * 0.5f * jump[c] * Sv[k];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[c][k] *= invJ;
+      const float mu = M.nu32 + eddy_visc32(G, delta, M.closure, M.cs32, M.cv32);
+      const float tr = G[0][0] + G[1][1] + G[2][2];
+      float tau[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tau[c][k] = mu * (G[c][k] + G[k][c]) - (c == k ? (2.f / 3.f) * mu * tr : 0.f);
+      float Fv[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Fv[d][c] = GEO == 0 ? Ja[d * 4] * tau[c][d]
+                              : Ja[d * 3] * tau[c][0] + Ja[d * 3 + 1] * tau[c][1] + Ja[d * 3 + 2] * tau[c][2];
+          F[(d * 3 + c) * n3 + p] = Fv[d][c];
+        }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (ii[d] != 0 && ii[d] != N) continue;
+        const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+        const float sg = side ? 1.f : -1.f;
+        const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+        const int64_t ms = troff + f * n2 + a + n * b;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Tvf[ms * 3 + c] = sg * Fv[d][c];
+      }
+    }
+    consumer_sync(NC);
+    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);  // the input buffer is no longer read
+    if (active) {
+      float V[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int bs = p - ii[d] * str[d];
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const float dm = sD[ii[d] * n + m];
+          const int pm = bs + m * str[d];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) V[c] += dm * F[(d * 3 + c) * n3 + pm];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rvf[c * M.total + off + p] = V[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------------------
 cudaError_t upload_ops32(const Ops1D& ops) {
@@ -1035,6 +1318,9 @@ static cudaError_t prep32_n() {
                                 (int)visc_smem32<N, 1>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 2>())) != cudaSuccess) return r;
+  const int vs = (int)ViscTmaSmem32<N>::bytes;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
   const int ps = (int)TmaSmem32<N>::bytes;
   if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
@@ -1078,8 +1364,34 @@ cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, 
   return cudaGetLastError();
 }
 
+// grid of the persistent viscous kernel: every resident block slot of the GPU, at most one per tile
+template <int N, int GEO>
+static cudaError_t launch_vpipe(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
+  static int per_sm = -1, sms = 0;
+  const size_t sm = ViscTmaSmem32<N>::bytes;
+  if (per_sm < 0) {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_viscous32t<N, GEO>, Shape<N>::threads + 32, sm);
+    if (r != cudaSuccess) return r;
+    int dev = 0;
+    if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntiles = (b.count + Shape<N>::EPB - 1) / Shape<N>::EPB;
+  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
+  k_viscous32t<N, GEO><<<grid, Shape<N>::threads + 32, sm, s>>>(M, b, q);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
+  if (b.geo != 2) {  // box and affine: the pipelined kernel
+    if (!b.blink || !b.bmeta) return cudaErrorInvalidValue;
+    DG32_DISPATCH_N(b.N, {
+      return b.geo == 0 ? launch_vpipe<NN, 0>(M, b, q, s) : launch_vpipe<NN, 1>(M, b, q, s);
+    });
+    return cudaSuccess;
+  }
   DG32_DISPATCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
