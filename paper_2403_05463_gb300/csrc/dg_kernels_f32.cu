@@ -1034,27 +1034,19 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
           if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
         }
         if (write_tr && on_face) {
-          QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
-          QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
-        }
-      }
-    }
-    if (MODE == MODE_RK && write_tr) {
-      consumer_sync(NC);
-      // traces of the new state for the next stage, one thread per face slot (coalesced)
-      float4* Tn = reinterpret_cast<float4*>(M.Tq_next);
+          // the next stage's trace records of this node's faces (32 bytes each, one sector)
+          float4* Tn = reinterpret_cast<float4*>(M.Tq_next) + 2 * MT->troff;  // record still staged
+          const float4 r01 = make_float4(h[0], l[0], h[1], l[1]), r23 = make_float4(h[2], l[2], h[3], l[3]);
 #pragma unroll
-      for (int r = 0; r < FR; ++r) {
-        const int fd = fdesc[r];
-        if (fd < 0) break;
-        const int le2 = fd & 31, f = (fd >> 5) & 7, pv = fd >> 14;
-        const int ab = ((fd >> 8) & 7) + n * ((fd >> 11) & 7);
-        if (tile * EPB + le2 >= B.count) continue;
-        const float4* Q2 = reinterpret_cast<const float4*>(W + le2 * P::work_elem + P::wQ);
-        const int64_t dst = reinterpret_cast<const EntryMeta*>(IN + le2 * P::in_elem + P::iMT)->troff + f * n2 + ab;
-        const float4 h4 = Q2[pv], l4 = Q2[n3 + pv];
-        Tn[2 * dst] = make_float4(h4.x, l4.x, h4.y, l4.y);
-        Tn[2 * dst + 1] = make_float4(h4.z, l4.z, h4.w, l4.w);
+          for (int d = 0; d < 3; ++d) {
+            if (ii[d] != 0 && ii[d] != N) continue;
+            const int f = 2 * d + (ii[d] == N ? 1 : 0);
+            const int a = d == 0 ? ii[1] : ii[0], bb = d == 2 ? ii[1] : ii[2];
+            const int dst = f * n2 + a + n * bb;
+            Tn[2 * dst] = r01;
+            Tn[2 * dst + 1] = r23;
+          }
+        }
       }
     }
     consumer_sync(NC);  // work buffers are reused by the next tile
