@@ -436,19 +436,21 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 // constants — at most 18 copies instead of ~2000 thread-level copies. A bulk copy needs
 // 16-byte-aligned ends, so each copy covers the 16-byte-aligned superset of its range and the
 // offset of the first wanted byte is kept in a small table. Per element (bytes):
-//   QD [4] slots of a16(8 n3 + 16) | NT [6] slots of a16(32 n2 + 16) |
+//   QD [4] slots of a16(8 n3 + 8) | NT [6] slots of a16(32 n2 + 16) |
 //   NV [6] slots of a16(12 n2 + 16) | OV a16(72 n2 + 16) | LK 96 | EC 48 |
 //   MT 32 (EntryMeta) | SH 32 (byte offsets of the slots' first wanted byte)
 template <int N>
 struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
-  static constexpr int SQD = a16(8 * n3 + 16), SNT = a16(32 * n2 + 16), SNV = a16(12 * n2 + 16),
+  // QD: q is 8-byte aligned, so its copies start at most 8 bytes early
+  static constexpr int SQD = a16(8 * n3 + 8), SNT = a16(32 * n2 + 16), SNV = a16(12 * n2 + 16),
                        SOV = a16(72 * n2 + 16);
   static constexpr int iQD = 0, iNT = 4 * SQD, iNV = iNT + 6 * SNT, iOV = iNV + 6 * SNV, iLK = iOV + SOV,
                        iEC = iLK + 96, iMT = iEC + 48, iSH = iMT + 32, in_elem = a16(iSH + 32);
   static constexpr int ITEMS = 18;  // copies per element: 4 QD, 6 NT, 6 NV, OV, EC
-  static constexpr int wF = 0, wQ = 48 * n3, work_elem = 80 * n3;
+  // work per element: F [3 n3] flux deviations, QH/QL [n3] hi/lo state, T [6 n2] face terms
+  static constexpr int wF = 0, wQ = 48 * n3, wT = 80 * n3, work_elem = 80 * n3 + 96 * n2;
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
 };
@@ -885,7 +887,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 #pragma unroll
       for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
     }
-    consumer_sync(NC);  // F is reused for the face terms below
+    // no barrier: the face phase reads QH/QL and the input buffer and writes T, none of which
+    // the contraction touches
     // ---- faces, one thread per (element, face, face node) -----------------------------
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
@@ -998,7 +1001,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
           }
         }
       }
-      reinterpret_cast<float4*>(W2 + P::wF)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
+      reinterpret_cast<float4*>(W2 + P::wT)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
     }
     consumer_sync(NC);
     // ---- assembly and update ------------------------------------------------------------
@@ -1008,7 +1011,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         if (ii[d] != 0 && ii[d] != N) continue;
         const int f = 2 * d + (ii[d] == N ? 1 : 0);
         const int a = d == 0 ? ii[1] : ii[0], bb = d == 2 ? ii[1] : ii[2];
-        const float4 sc = F4[f * n2 + a + n * bb];
+        const float4 sc = reinterpret_cast<const float4*>(W + le * P::work_elem + P::wT)[f * n2 + a + n * bb];
         JR[0] -= invw * sc.x;
         JR[1] -= invw * sc.y;
         JR[2] -= invw * sc.z;
@@ -1049,8 +1052,11 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         }
       }
     }
-    consumer_sync(NC);  // work buffers are reused by the next tile
-    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);  // this input buffer may be refilled
+    // No barrier here: the next tile writes F and QH/QL only after its node phase, which no
+    // thread starts before every consumer has passed the next tile's vote (bar.red), i.e.
+    // finished this assembly; T is rewritten only after the next tile's first barrier.
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);  // this warp no longer reads the buffer
   }
 }
 
