@@ -595,6 +595,24 @@ dg_status rebuild_flags(dg_ctx* c) {
   dg_status st = dev_upload(c, "link", link, &dl);
   if (st != DG_OK) return st;
   c->M.link = dl;
+  // all-element buckets: NS elements first, each class in element order, so that a tile of the
+  // pipelined passes holds elements of one flag (no NS/Euler imbalance inside a tile)
+  for (size_t i = 0; i < c->all_buckets.size() && i < c->all_lists.size(); ++i) {
+    std::vector<int32_t>& L = c->all_lists[i];
+    std::stable_partition(L.begin(), L.end(), [&](int32_t e) { return c->flag[e] != 0; });
+    std::vector<int64_t> bo(L.size()), bt(L.size());
+    for (size_t j = 0; j < L.size(); ++j) {
+      bo[j] = c->off[L[j]];
+      bt[j] = c->troff[L[j]];
+    }
+    Bucket& b = c->all_buckets[i];
+    int64_t* d;
+    if ((st = dev_upload(c, "allb" + std::to_string(i), L, &b.list)) != DG_OK) return st;
+    if ((st = dev_upload(c, "allbo" + std::to_string(i), bo, &d)) != DG_OK) return st;
+    b.boff = d;
+    if ((st = dev_upload(c, "allbt" + std::to_string(i), bt, &d)) != DG_OK) return st;
+    b.btr = d;
+  }
   // per-entry link and flag tables of the all-element buckets
   if ((st = upload_entry_tables(c, "allb", c->all_lists, link, c->all_buckets)) != DG_OK) return st;
   uint8_t* df;
