@@ -84,7 +84,10 @@ typedef struct {
   int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                                   */
   int precision;    /* 0 FP64 throughout; 1 FP32 element/face arithmetic with FP64 state,
                        traces and Runge-Kutta accumulation                              */
-  int reserved;     /* must be 0                                                       */
+  int mixed_face;   /* viscous flux on a face between an NS and an Euler element (Sec. 2.3
+                       asks only that it be single-valued): 0 the average of the NS side's
+                       flux and zero (BR1 with an inviscid side), 1 the NS side's flux
+                       alone; faces between two NS elements always take the average      */
   double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
 } dg_params;
 

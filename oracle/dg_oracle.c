@@ -460,6 +460,10 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const or_real* gxyz, c
     set_err("geometry degree %d unsupported", g);
     return NULL;
   }
+  if (prm->mixed_face != 0 && prm->mixed_face != 1) {
+    set_err("mixed_face %d invalid", prm->mixed_face);
+    return NULL;
+  }
   or_mesh* m = (or_mesh*)calloc(1, sizeof(or_mesh));
   m->ne = ne;
   m->g = g;
@@ -936,6 +940,13 @@ static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
       for (int i = 0; i < 3 * nM2; ++i) Fvp[i] = -Fvm[i];
     }
   }
+  /* F_v* . S = wm Fvm - wp Fvp: the BR1 average, except on a face between an NS and an Euler
+   * element with the one-sided choice, where the NS side's flux alone is taken */
+  or_real wm = 0.5, wp = 0.5;
+  if (m->p.mixed_face == 1 && mt.nbr >= 0 && m->flag[e] != m->flag[mt.nbr]) {
+    wm = m->flag[e] ? 1.0 : 0.0;
+    wp = m->flag[e] ? 0.0 : 1.0;
+  }
   int rc = 0;
   for (int p = 0; p < nM2; ++p) {
     or_real S[3] = {mt.S[p], mt.S[nM2 + p], mt.S[2 * nM2 + p]};
@@ -949,7 +960,7 @@ static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
     if (or_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
     H[p] = Fs[0] * s;
     for (int c = 0; c < 3; ++c) {
-      or_real fv = 0.5 * (Fvm[c * nM2 + p] - Fvp[c * nM2 + p]);
+      or_real fv = wm * Fvm[c * nM2 + p] - wp * Fvp[c * nM2 + p];
       H[(1 + c) * nM2 + p] = Fs[1 + c] * s - fv;
     }
   }

@@ -45,6 +45,9 @@ typedef struct {
   or_real cv;        /* Vreman constant (paper: 0.07)                             */
   int closure;      /* 0 Smagorinsky, 1 Vreman                                   */
   int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                             */
+  int mixed_face;   /* viscous flux on a face between an NS and an Euler element
+                       (Sec. 2.3 asks only that it be single-valued): 0 the average
+                       of the NS side's flux and zero, 1 the NS side's flux alone    */
   or_real inflow[4]; /* ghost state used at inflow faces (velocity part)          */
 } or_params;
 

@@ -52,7 +52,7 @@ _u8 = _P(ctypes.c_uint8)
 def _params_type(real):
     class P(ctypes.Structure):
         _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
-                    ("riemann", ctypes.c_int), ("inflow", real * 4)]
+                    ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("inflow", real * 4)]
     return P
 
 
@@ -112,10 +112,10 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0)):
+def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0):
     p = Params()
     p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
-    p.closure, p.riemann = closure, riemann
+    p.closure, p.riemann, p.mixed_face = closure, riemann, mixed_face
     for i in range(4):
         p.inflow[i] = inflow[i]
     return p

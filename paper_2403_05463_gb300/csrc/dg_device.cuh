@@ -11,6 +11,17 @@ struct Shape {
   static constexpr int threads = ((EPB * n3 + 31) / 32) * 32;
 };
 
+// Weights of the own and the neighbour's outward viscous traces (tau . S) in the face term
+// F_v,own . S - F_v* . S. BR1 averages: (1/2, 1/2). With the one-sided choice on a face between
+// an NS and an Euler element, F_v* is the NS side's flux: the NS side's term vanishes (0, 0)
+// and the Euler side takes the whole neighbour flux (1, 1; its own trace is zero).
+__host__ __device__ __forceinline__ void visc_face_weights(int mixed_face, bool own_ns, bool nbr_ns, float& wo,
+                                                           float& wn) {
+  const bool one = mixed_face == 1 && own_ns != nbr_ns;
+  wo = one ? (own_ns ? 0.f : 1.f) : 0.5f;
+  wn = one ? (own_ns ? 0.f : 1.f) : 0.5f;
+}
+
 // volume node of face f = 2d+s at face coordinates (a, b)
 __host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
   int d = f >> 1, fix = (f & 1) ? n - 1 : 0;

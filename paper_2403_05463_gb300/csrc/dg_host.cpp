@@ -310,7 +310,7 @@ dg_status check_params(const dg_params* p) {
   if (p->closure < 0 || p->closure > 1) return fail(DG_ERR_ARG, "closure must be 0 or 1");
   if (p->riemann < 0 || p->riemann > 1) return fail(DG_ERR_ARG, "riemann must be 0 or 1");
   if (p->precision < 0 || p->precision > 1) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
-  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
+  if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
   return DG_OK;
 }
 
@@ -321,6 +321,7 @@ void apply_params(dg_ctx* c) {
   c->M.cv = c->prm.cv;
   c->M.closure = c->prm.closure;
   c->M.riemann = c->prm.riemann;
+  c->M.mixed_face = c->prm.mixed_face;
   c->M.precision = c->prm.precision;
   c->M.nu32 = (float)c->prm.nu;
   c->M.c0sq32 = (float)c->prm.c0sq;

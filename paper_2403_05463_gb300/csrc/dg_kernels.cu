@@ -426,13 +426,15 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
     for (int v = 0; v < 4; ++v) JR[v] -= invw * s * fx[v];
     if (L.kind == FK_CONF && (ns || L.nflag)) {
-      // BR1: F_v* . S - Ftil_v,out = -1/2 (tau_own . S_own + tau_nbr . S_nbr)
+      // BR1: Ftil_v,out - F_v* . S = wo tau_own . S_own + wn tau_nbr . S_nbr
+      float wo, wn;
+      visc_face_weights(M.mixed_face, ns, L.nflag != 0, wo, wn);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         double t = 0.0;
-        if (ns) t += M.Tv[c * M.tr_total + ms];
-        if (L.nflag) t += M.Tv[c * M.tr_total + nsl];
-        JR[1 + c] -= invw * 0.5 * t;
+        if (ns) t += (double)wo * M.Tv[c * M.tr_total + ms];
+        if (L.nflag) t += (double)wn * M.Tv[c * M.tr_total + nsl];
+        JR[1 + c] -= invw * t;
       }
     }
   }
@@ -610,8 +612,11 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
       qp[v] = sm.nM[v][t];
     }
     flux_full(qm, qp, nh, M.c0sq, M.riemann, Fs);
+    // F_v* . S = wm (mine) - wp (neighbour's outward): the average, or the NS side alone
+    const bool one = M.mixed_face == 1 && vm != vn;
+    const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;
     sm.H[0][t] = s * Fs[0];
-    for (int c = 0; c < 3; ++c) sm.H[1 + c][t] = s * Fs[1 + c] - 0.5 * (sm.mM[4 + c][t] - sm.nM[4 + c][t]);
+    for (int c = 0; c < 3; ++c) sm.H[1 + c][t] = s * Fs[1 + c] - (wm * sm.mM[4 + c][t] - wp * sm.nM[4 + c][t]);
   }
   __syncthreads();
   if (t < nm * nm) {

@@ -992,12 +992,14 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 #pragma unroll
         for (int v = 0; v < 4; ++v) term[v] = s * fx[v];
         if (L.kind == FK_CONF && (ns2 || L.nflag)) {
+          float wo, wn;
+          visc_face_weights(M.mixed_face, ns2, L.nflag != 0, wo, wn);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             float tv = 0.f;
-            if (ns2) tv += reinterpret_cast<const float*>(I2 + P::iOV + SH2[16])[(f * n2 + ab) * 3 + c];
-            if (L.nflag) tv += reinterpret_cast<const float*>(I2 + P::iNV + f * P::SNV + SH2[10 + f])[nab * 3 + c];
-            term[1 + c] += 0.5f * tv;
+            if (ns2) tv += wo * reinterpret_cast<const float*>(I2 + P::iOV + SH2[16])[(f * n2 + ab) * 3 + c];
+            if (L.nflag) tv += wn * reinterpret_cast<const float*>(I2 + P::iNV + f * P::SNV + SH2[10 + f])[nab * 3 + c];
+            term[1 + c] += tv;
           }
         }
       }

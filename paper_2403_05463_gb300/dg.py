@@ -40,7 +40,7 @@ class MeshDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
                 ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
+                ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
 
 
 _lock = threading.Lock()
@@ -102,7 +102,7 @@ def make_params(p: dict, precision=0) -> Params:
     out.nu, out.c0sq, out.cs, out.cv = p["nu"], p["c0sq"], p["cs"], p["cv"]
     out.closure, out.riemann = int(p.get("closure", 0)), int(p.get("riemann", 0))
     out.precision = PRECISION.get(precision, precision) if isinstance(precision, str) else int(precision)
-    out.reserved = 0
+    out.mixed_face = int(p.get("mixed_face", 0))
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
     return out

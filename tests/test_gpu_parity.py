@@ -109,6 +109,22 @@ def test_curved_mixed_orders_rotated_elements():
     _assert_parity(R, R_ref)
 
 
+def test_one_sided_mixed_face():
+    # the one-sided Euler/NS face flux on a curved, rotated mesh with mortars (orders 2..6)
+    # and on the wake box (inflow/outflow faces); it must differ from the default average
+    w = wl.padapt_32x32x32(n=4)
+    mesh, _ = wl.rotate_elements(w.mesh, 9)
+    w = small_mixed(dataclasses.replace(w, mesh=mesh), seed=13, orders=(2, 6))
+    p1 = dict(w.params, nu=1e-2, mixed_face=1)
+    R, R_ref, M, S, q = _residual_pair(w, params=p1)
+    _assert_parity(R, R_ref)
+    R0 = oracle_mesh(w, dict(p1, mixed_face=0)).residual(q)
+    assert rel_l2(R_ref, R0) > 1e-6
+    ww = wl.wake_16x16x16_n4(n=8)
+    R2, R2_ref, *_ = _residual_pair(ww, params=dict(ww.params, nu=1e-3, mixed_face=1))
+    _assert_parity(R2, R2_ref)
+
+
 def test_padapt_scaled():
     w = wl.padapt_32x32x32(n=6)
     R, R_ref, *_ = _residual_pair(w)
@@ -216,4 +232,7 @@ def test_bad_inputs_are_rejected():
     assert ei.value.status == 2
     with pytest.raises(dg.DGError) as ei:
         dg.Solver(w.mesh.hex, w.mesh.geom, 1, dict(w.params, c0sq=-1.0))
+    assert ei.value.status == 1
+    with pytest.raises(dg.DGError) as ei:
+        dg.Solver(w.mesh.hex, w.mesh.geom, 1, dict(w.params, mixed_face=2))
     assert ei.value.status == 1

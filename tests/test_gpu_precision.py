@@ -22,7 +22,7 @@ BOUNDS = {
     "padapt_6x6x6_curved": 1.5e-5, "tgv_5x5x5_n1_vreman_llf": 1e-6, "tgv_5x5x5_n2_vreman_llf": 5e-6,
     "tgv_5x5x5_n6_vreman_llf": 3e-4, "tgv_5x5x5_n7_vreman_llf": 3e-4,
     "tgv_4x4x4_n3_rk3_10_steps_update": 7e-6, "mixed_64x64x64_n4_sampled": 1e-4,
-    "tgv_5x5x5_rotated_affine_mixed_orders": 1e-4,
+    "tgv_5x5x5_rotated_affine_mixed_orders": 1e-4, "padapt_5x5x5_one_sided_mixed_face": 5e-5,
 }
 
 
@@ -80,6 +80,13 @@ def test_fp32_rotated_affine_mixed_orders():
     err = _fp32_error(w, params=dict(w.params, nu=1e-2))
     _record("tgv_5x5x5_rotated_affine_mixed_orders", err)
     assert err <= BOUNDS["tgv_5x5x5_rotated_affine_mixed_orders"]
+
+
+def test_fp32_one_sided_mixed_face():
+    w = small_mixed(wl.padapt_32x32x32(n=5), seed=14, orders=(2, 5))
+    err = _fp32_error(w, params=dict(w.params, nu=1e-2, mixed_face=1))
+    _record("padapt_5x5x5_one_sided_mixed_face", err)
+    assert err <= BOUNDS["padapt_5x5x5_one_sided_mixed_face"]
 
 
 def test_fp32_rk3_ten_steps():

@@ -447,3 +447,62 @@ def test_vreman_term_converges_to_symbolic_divergence():
     pytest.importorskip("sympy")
     e1, e2 = _les_error(1, 4, 7), _les_error(1, 8, 7)
     assert e1 < 0.4 and e2 < 0.65 * e1, (e1, e2)
+
+
+def test_one_sided_mixed_face_changes_only_the_interface_terms():
+    # Sec. 2.3 only asks for a single-valued viscous flux on an NS/Euler face. The one-sided
+    # choice takes F_v* = F_v(NS side) instead of the average (F_v(NS) + 0)/2, so on such a
+    # face the NS element's residual changes by +(1/(J w_end)) (1/2) tau . S at its face nodes
+    # (tau from its own BR1 gradient), the Euler side by the opposite flux, nothing else moves,
+    # and the sums stay conservative. Checked with tau built here from the oracle's gradient.
+    n, N = 4, 3
+    w = wl.tgv_4x4x4_n3(n_elem_dir=n, order=N)
+    rng = np.random.default_rng(31)
+    flags = (rng.uniform(size=n ** 3) < 0.5).astype(np.uint8)
+    m = w.mesh
+    nu = 1e-2
+    base = dict(w.params, nu=nu, cs=0.0)
+    A = orc.Mesh(m.hex, m.geom, 1, w.orders, flags, orc.params(**base, mixed_face=0))
+    B = orc.Mesh(m.hex, m.geom, 1, w.orders, flags, orc.params(**base, mixed_face=1))
+    q = w.state(A.node_coords())
+    q[1:] += 0.05 * np.sin(3.0 * A.node_coords())  # break the TGV symmetries
+    d = B.residual(q) - A.residual(q)
+    # neighbours on the periodic structured grid, from the element centres
+    h = 2 * np.pi / n
+    ijk = np.rint(m.centers / h - 0.5).astype(int) % n
+    index = {tuple(c): e for e, c in enumerate(ijk)}
+    np1 = N + 1
+    x, wq = orc.lgl(N)
+    w_end = wq[0]
+    pred = np.zeros_like(d)
+    touched = np.zeros(d.shape[1], dtype=bool)
+    for e in range(n ** 3):
+        sl = A.element_nodes(e)
+        J, Ja = A.element_geometry(e)
+        G = A.element_gradient(q, e) if flags[e] else None
+        for f in range(6):
+            dd, s = f >> 1, f & 1
+            nb = list(ijk[e])
+            nb[dd] = (nb[dd] + (1 if s else -1)) % n
+            k = index[tuple(nb)]
+            if flags[k] == flags[e]:
+                continue
+            for p in range(np1 ** 3):
+                ii = (p % np1, (p // np1) % np1, p // np1 ** 2)
+                if ii[dd] != (N if s else 0):
+                    continue
+                touched[sl.start + p] = True
+                if not flags[e]:
+                    continue
+                Gp = G[:, :, p]
+                tau = nu * (Gp + Gp.T - 2.0 / 3.0 * np.trace(Gp) * np.eye(3))
+                S = (1.0 if s else -1.0) * Ja[dd, :, p]
+                pred[1:, sl.start + p] += 0.5 * (tau @ S) / (J[p] * w_end)
+    ns_nodes = np.concatenate([np.arange(*A.element_nodes(e).indices(A.total)[:2]) for e in np.flatnonzero(flags)])
+    scale = np.abs(pred).max()
+    assert scale > 1e-4
+    np.testing.assert_allclose(d[:, ns_nodes], pred[:, ns_nodes], rtol=0, atol=1e-12 * scale)
+    assert np.abs(d[0]).max() <= 1e-13 * scale          # no viscous flux in the pressure row
+    assert np.abs(d[:, ~touched]).max() <= 1e-13 * scale  # only interface face nodes move
+    assert np.abs(d[1:, touched & ~np.isin(np.arange(A.total), ns_nodes)]).max() > 0.1 * scale
+    assert np.abs(A.conservation(d)).max() <= 1e-13 * scale
