@@ -46,6 +46,7 @@ def parse_args():
                          "mixed configuration's precision); fp64: FP64 throughout")
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -246,6 +247,8 @@ def main():
     world, rank, local = dist_setup()
     w = wl.WORKLOADS[args.workload]() if args.n is None else wl.WORKLOADS[args.workload](n=args.n)
     S = dg.Solver.from_workload(w, precision=args.precision, device=local)
+    # launch shapes per (order, geometry) timed on this GPU and mesh before the timed region
+    tuning = "default" if args.no_autotune else S.autotune()
     dof = S.total_nodes
     xyz = S.node_coords()
     q = w.state_fn(xyz, None, None) if args.workload == "mixed_64x64x64_n4" else \
@@ -309,7 +312,10 @@ def main():
                       "ns_fraction": w.ns_fraction, "precision": args.precision, "stages_per_step": 3,
                       "state": "FP64 q, g resident in HBM; FP64 RK accumulation",
                       "l2": f"inputs larger than L2 (q + g = {2 * q.numel() * 8 / 1e9:.2f} GB per rank)",
-                      "parallelism": "replicas" if world > 1 else "single GPU"},
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "launch_shapes": "default" if tuning == "default" else "autotuned: " +
+                      "; ".join(line.split(" ms")[0].split(":")[0] + ":" + line.split(":")[1]
+                                for line in tuning.strip().splitlines() if ":" in line)},
            "roofline": roofline, "phases": phases, "gpu_launches": launches, "clocks": clk}
 
     if not args.no_extras:

@@ -145,6 +145,22 @@ dg_status dg_rk_step_host(dg_ctx* ctx, double* q_host, double* g_host, double t,
  * discretisation conserves every variable, so these sums vanish to rounding. */
 dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double out_host[4], void* stream);
 
+/* Launch-shape autotuner of the reduced-precision passes (precision 1). For every bucket of
+ * the current mesh -- one per (polynomial order, geometry kind) -- it times the candidate
+ * launch shapes on this GPU and keeps the fastest: for the inviscid pass the elements per
+ * tile (the default ~256-node tile or the alternative: half of it for orders 1..4, two
+ * elements for orders 5, 6) and the resident blocks per SM (all that fit, 1 or 2); for the
+ * viscous pass on box/affine elements the pipelined (bulk-copy) kernel at those block counts
+ * or the cp.async-staged kernel. Timing uses a library-owned scratch state, so q, g and R are
+ * untouched; the choices then apply to every later call (they are kept per order and
+ * geometry kind across dg_set_orders / dg_set_element_flags) and the captured step graph
+ * is rebuilt. cache_path (NULL: none) names a text file of choices keyed by the device
+ * name: choices found there are used without timing, and the file is rewritten with this
+ * device's choices. report (NULL allowed) receives a human-readable summary, truncated to
+ * report_len bytes. Precision 0 has nothing to tune and returns DG_OK. Synchronises. Errors:
+ * DG_ERR_ARG (NULL ctx, unwritable cache), DG_ERR_OOM (scratch), DG_ERR_CUDA. */
+dg_status dg_autotune(dg_ctx* ctx, const char* cache_path, char* report, int report_len);
+
 /* Largest mesh (elements) that dg_conservation_noalloc accepts. */
 #define DG_CONSERVATION_NOALLOC_MAX_ELEMS 65536
 

@@ -270,6 +270,9 @@ struct dg_ctx {
   double* stage_r = nullptr;
   double* partial = nullptr;
   std::vector<double> partial_host;
+  // autotuned launch choices of the reduced-precision passes, key (pass, N, geometry kind) with
+  // pass 0 inviscid, 1 viscous; value (tile_alt, bps, visc_alt)
+  std::map<std::array<int, 3>, std::array<int, 3>> tuning;
 };
 
 namespace {
@@ -530,6 +533,23 @@ dg_status upload_buckets(dg_ctx* c, const std::string& prefix, const std::vector
   return DG_OK;
 }
 
+// Copy the autotuned choices onto the buckets they apply to (buckets are rebuilt with the
+// orders and flags; the choices are kept per (pass, order, geometry kind)).
+void apply_tuning(dg_ctx* c) {
+  for (Bucket& b : c->all_buckets) {
+    auto it = c->tuning.find({0, b.N, b.geo});
+    b.tile_alt = it == c->tuning.end() ? 0 : it->second[0];
+    b.bps = it == c->tuning.end() ? 0 : it->second[1];
+    b.visc_alt = 0;
+  }
+  for (Bucket& b : c->ns_buckets) {
+    auto it = c->tuning.find({1, b.N, b.geo});
+    b.tile_alt = 0;
+    b.bps = it == c->tuning.end() ? 0 : it->second[1];
+    b.visc_alt = it == c->tuning.end() ? 0 : it->second[2];
+  }
+}
+
 // Per-entry tables of a set of buckets, in bucket order: the element's 6 face links, its flag
 // and its 32-byte record (read by the pipelined passes instead of chasing the element id).
 dg_status upload_entry_tables(dg_ctx* c, const std::string& prefix, const std::vector<std::vector<int32_t>>& lists,
@@ -636,6 +656,7 @@ dg_status rebuild_flags(dg_ctx* c) {
   if ((st = upload_entry_tables(c, "nsbx", ns_lists, link, c->ns_buckets)) != DG_OK) return st;
   // viscous traces of Euler elements are never written: keep them at zero
   if (c->M.Tv) CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
+  apply_tuning(c);
   c->version++;
   destroy_graph(c);
   return DG_OK;
@@ -1211,6 +1232,176 @@ dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, d
   for (auto& e : ev) cudaEventDestroy(e);
   if (st != DG_OK) return st;
   for (int ph = 0; ph < DG_NPHASES; ++ph) out_ms[ph] = acc[ph] / reps;
+  return DG_OK;
+}
+
+// Launch-shape autotuning of the reduced-precision passes (see include/dg.h).
+dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int report_len) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (report && report_len > 0) report[0] = 0;
+  std::string rep;
+  auto give_report = [&]() {
+    if (report && report_len > 0) std::snprintf(report, (size_t)report_len, "%s", rep.c_str());
+  };
+  CU(cudaSetDevice(c->device));
+  if (c->prm.precision != 1) {
+    rep = "precision 0: the FP64 passes have no launch choices\n";
+    give_report();
+    return DG_OK;
+  }
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, c->device));
+  std::string dev = prop.name;
+  for (char& ch : dev)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  // cached choices for this device: "device<TAB>pass<TAB>N<TAB>geo<TAB>tile_alt<TAB>bps<TAB>visc_alt"
+  std::map<std::array<int, 3>, std::array<int, 3>> cached;
+  if (cache_path && *cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof line, f)) {
+        const char* tab = std::strchr(line, '\t');
+        if (!tab || std::string(line, (size_t)(tab - line)) != dev) continue;
+        int v[6];
+        if (std::sscanf(tab + 1, "%d\t%d\t%d\t%d\t%d\t%d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6)
+          cached[{v[0], v[1], v[2]}] = {v[3], v[4], v[5]};
+      }
+      std::fclose(f);
+    }
+  }
+  // a scratch state and output, and every buffer a pass reads, filled once for that state
+  double *tq = nullptr, *tr = nullptr;
+  dg_status st;
+  if ((st = dev_alloc(c, "tune_q", 4 * c->total, &tq)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "tune_r", 4 * c->total, &tr)) != DG_OK) return st;
+  {
+    std::vector<double> hq(4 * c->total);
+    for (int64_t i = 0; i < c->total; ++i) {
+      hq[i] = 0.01 * std::sin(0.001 * (double)i);
+      hq[c->total + i] = 1.0;
+      hq[2 * c->total + i] = 0.1 * std::cos(0.002 * (double)i);
+      hq[3 * c->total + i] = -0.1;
+    }
+    CU(cudaMemcpy(tq, hq.data(), sizeof(double) * hq.size(), cudaMemcpyHostToDevice));
+  }
+  cudaStream_t s = c->cap_stream;
+  for (int ph = 0; ph < DG_NPHASES; ++ph)
+    if ((st = issue_phase(c, ph, tq, tr, tr, MODE_RESIDUAL, 0, 0.0, s, nullptr)) != DG_OK) return st;
+  CU(cudaMemsetAsync(tr, 0, sizeof(double) * 4 * c->total, s));  // the scratch RK register
+  DevMesh M = c->M;
+  M.Tq = c->trace_buf[0];
+  M.Tq_next = c->trace_buf[1];
+  M.dt32 = 1e-9f;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  auto timed = [&](auto&& launch, float& ms) -> cudaError_t {
+    cudaError_t r = launch();
+    if (r != cudaSuccess) return r;
+    if ((r = cudaEventRecord(e0, s)) != cudaSuccess) return r;
+    for (int k = 0; k < 5 && r == cudaSuccess; ++k) r = launch();
+    if (r != cudaSuccess) return r;
+    if ((r = cudaEventRecord(e1, s)) != cudaSuccess) return r;
+    if ((r = cudaEventSynchronize(e1)) != cudaSuccess) return r;
+    if ((r = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return r;
+    ms /= 5.f;
+    return cudaSuccess;
+  };
+  cudaError_t ce = cudaSuccess;
+  char buf[256];
+  for (Bucket& b : c->all_buckets) {
+    if (ce != cudaSuccess) break;
+    const std::array<int, 3> key = {0, b.N, b.geo};
+    auto hit = cached.find(key);
+    if (hit != cached.end()) {
+      c->tuning[key] = hit->second;
+      std::snprintf(buf, sizeof buf, "inviscid N=%d geo=%d: cached, %d elements/tile, %d blocks/SM (0 = max)\n", b.N,
+                    b.geo, tile_epb32(b.N, hit->second[0]), hit->second[1]);
+      rep += buf;
+      continue;
+    }
+    std::array<int, 3> best = {0, 0, 0};
+    float best_ms = 0.f, default_ms = 0.f;
+    for (int alt = 0; alt < 2 && ce == cudaSuccess; ++alt) {
+      if (alt == 1 && tile_epb32(b.N, 1) == tile_epb32(b.N, 0)) continue;
+      for (int bps = 0; bps < 3 && ce == cudaSuccess; ++bps) {
+        b.tile_alt = alt;
+        b.bps = bps;
+        float ms = 0.f;
+        // the RK form of the pass (stage 1: reads g, writes q, g and the next traces) on the
+        // scratch state, with g in the scratch output buffer
+        ce = timed([&]() { return launch_inviscid(M, b, tq, tq, tr, MODE_RK, 1, 1e-9, 1, 1, s); }, ms);
+        if (alt == 0 && bps == 0) default_ms = best_ms = ms;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = {alt, bps, 0};
+        }
+      }
+    }
+    c->tuning[key] = best;
+    std::snprintf(buf, sizeof buf,
+                  "inviscid N=%d geo=%d: %d elements/tile, %d blocks/SM (0 = max): %.4f ms, default %.4f ms\n", b.N,
+                  b.geo, tile_epb32(b.N, best[0]), best[1], best_ms, default_ms);
+    rep += buf;
+  }
+  for (Bucket& b : c->ns_buckets) {
+    if (b.geo == 2 || ce != cudaSuccess) continue;  // curved: a single kernel
+    const std::array<int, 3> key = {1, b.N, b.geo};
+    auto hit = cached.find(key);
+    if (hit != cached.end()) {
+      c->tuning[key] = hit->second;
+      std::snprintf(buf, sizeof buf, "viscous N=%d geo=%d: cached, %s kernel, %d blocks/SM (0 = max)\n", b.N, b.geo,
+                    hit->second[2] ? "cp.async" : "pipelined", hit->second[1]);
+      rep += buf;
+      continue;
+    }
+    const int cand[4][2] = {{0, 0}, {1, 0}, {2, 0}, {0, 1}};  // (bps, visc_alt)
+    std::array<int, 3> best = {0, 0, 0};
+    float best_ms = 0.f, default_ms = 0.f;
+    for (int k = 0; k < 4 && ce == cudaSuccess; ++k) {
+      b.bps = cand[k][0];
+      b.visc_alt = cand[k][1];
+      float ms = 0.f;
+      ce = timed([&]() { return launch_viscous(M, b, tq, 1, s); }, ms);
+      if (k == 0) default_ms = best_ms = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = {0, cand[k][0], cand[k][1]};
+      }
+    }
+    c->tuning[key] = best;
+    std::snprintf(buf, sizeof buf, "viscous N=%d geo=%d: %s kernel, %d blocks/SM (0 = max): %.4f ms, default %.4f ms\n",
+                  b.N, b.geo, best[2] ? "cp.async" : "pipelined", best[1], best_ms, default_ms);
+    rep += buf;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_buf(c, "tune_q");
+  free_buf(c, "tune_r");
+  apply_tuning(c);
+  destroy_graph(c);
+  c->version++;
+  if (ce != cudaSuccess) return fail(DG_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(ce));
+  if (cache_path && *cache_path) {
+    // keep other devices' lines, replace this device's
+    std::vector<std::string> keep;
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof line, f)) {
+        const char* tab = std::strchr(line, '\t');
+        if (tab && std::string(line, (size_t)(tab - line)) != dev) keep.emplace_back(line);
+      }
+      std::fclose(f);
+    }
+    FILE* f = std::fopen(cache_path, "w");
+    if (!f) return fail(DG_ERR_ARG, "cannot write the tuning cache %s", cache_path);
+    for (const std::string& l : keep) std::fputs(l.c_str(), f);
+    for (const auto& kv : c->tuning)
+      std::fprintf(f, "%s\t%d\t%d\t%d\t%d\t%d\t%d\n", dev.c_str(), kv.first[0], kv.first[1], kv.first[2], kv.second[0],
+                   kv.second[1], kv.second[2]);
+    std::fclose(f);
+  }
+  give_report();
   return DG_OK;
 }
 

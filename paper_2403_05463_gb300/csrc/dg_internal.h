@@ -113,6 +113,10 @@ struct Bucket {
   const FaceLink* blink = nullptr;  // the element's 6 face links
   const uint8_t* bflag = nullptr;   // the element's flag
   const EntryMeta* bmeta = nullptr; // the entry's record
+  // launch choices of the reduced-precision passes (set by the autotuner; 0 = default)
+  int tile_alt = 0;   // inviscid: 1 = the alternative elements-per-tile shape
+  int bps = 0;        // pipelined passes: resident blocks per SM (0 = as many as fit)
+  int visc_alt = 0;   // viscous, box/affine: 1 = the cp.async-staged kernel instead of the pipelined one
 };
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };
@@ -145,6 +149,9 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
 cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
 cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                               int mode, int stage, int write_tr, cudaStream_t s);
+
+// elements per tile of the FP32 inviscid pass at order N: the default shape or the alternative
+int tile_epb32(int N, int alt);
 
 // Allocation-free conservation sums (dg_noalloc.cu)
 cudaError_t noalloc_scratch(int device, double** ptr);

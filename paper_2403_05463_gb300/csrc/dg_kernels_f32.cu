@@ -439,9 +439,22 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
 //   QD [4] slots of a16(8 n3 + 8) | NT [6] slots of a16(32 n2 + 16) |
 //   NV [6] slots of a16(12 n2 + 16) | OV a16(72 n2 + 16) | LK 96 | EC 48 |
 //   MT 32 (EntryMeta) | SH 32 (byte offsets of the slots' first wanted byte)
+// Tile shape of the pipelined passes: E elements per tile, one consumer thread per node
+// (rounded up to whole warps). The default E packs about 256 nodes; the alternative halves it
+// (orders 1..4) or doubles it (orders 5, 6); the autotuner picks per (order, geometry).
+template <int N, int E>
+struct Tile {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
+  static constexpr int threads = ((E * n3 + 31) / 32) * 32;
+};
 template <int N>
+struct AltEPB {
+  static constexpr int value = N <= 4 ? Shape<N>::EPB / 2 : (N <= 6 ? 2 : Shape<N>::EPB);
+};
+
+template <int N, int E = Shape<N>::EPB>
 struct TmaSmem32 {
-  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
   // QD: q is 8-byte aligned, so its copies start at most 8 bytes early
   static constexpr int SQD = a16(8 * n3 + 8), SNT = a16(32 * n2 + 16), SNV = a16(12 * n2 + 16),
@@ -584,18 +597,18 @@ __device__ __forceinline__ bool vtma_item(const DevMesh& M, const double* q, con
 // The records of one tile, held in the producer warp's registers between the time they are
 // loaded and the time the tile's input buffer is free: record r = lane + 32 j of the tile's
 // EPB x 7 records (k = r % 7 = 0: the element's 32-byte EntryMeta, 1..6: its face links).
-template <int N>
+template <int E>
 struct TileRecs {
-  static constexpr int R = (Shape<N>::EPB * 7 + 31) / 32;
+  static constexpr int R = (E * 7 + 31) / 32;
   uint4 a[R], b[R];
 };
 
-template <int N>
-__device__ __forceinline__ void load_recs(const Bucket& B, int tile, TileRecs<N>& T) {
-  constexpr int EPB = Shape<N>::EPB;
+template <int E>
+__device__ __forceinline__ void load_recs(const Bucket& B, int tile, TileRecs<E>& T) {
+  constexpr int EPB = E;
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int j = 0; j < TileRecs<N>::R; ++j) {
+  for (int j = 0; j < TileRecs<E>::R; ++j) {
     const int r = lane + 32 * j, le = r / 7, k = r % 7, i = tile * EPB + le;
     if (r < EPB * 7 && i < B.count) {
       if (k == 0) {
@@ -609,12 +622,12 @@ __device__ __forceinline__ void load_recs(const Bucket& B, int tile, TileRecs<N>
   }
 }
 
-template <int N, class P>
-__device__ __forceinline__ void store_recs(const Bucket& B, int tile, const TileRecs<N>& T, char* IN) {
-  constexpr int EPB = Shape<N>::EPB;
+template <class P>
+__device__ __forceinline__ void store_recs(const Bucket& B, int tile, const TileRecs<P::EPB>& T, char* IN) {
+  constexpr int EPB = P::EPB;
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int j = 0; j < TileRecs<N>::R; ++j) {
+  for (int j = 0; j < TileRecs<EPB>::R; ++j) {
     const int r = lane + 32 * j, le = r / 7, k = r % 7, i = tile * EPB + le;
     if (r < EPB * 7 && i < B.count) {
       char* base = IN + le * P::in_elem;
@@ -707,22 +720,28 @@ template <int N>
 struct TmaMinBlocks {
   static constexpr int value = N == 4 ? 3 : (N == 5 ? 4 : (N == 1 || N == 7 ? 1 : 2));
 };
+// register cap of a tile shape: the default shapes as above; 128-thread tiles 5 blocks, larger
+// ones none
+template <int N, int E>
+struct InvMinBlocks {
+  static constexpr int value = E == Shape<N>::EPB ? TmaMinBlocks<N>::value : (Tile<N, E>::threads <= 128 ? 5 : 1);
+};
 
 // Warp-specialised: threads [0, Shape<N>::threads) compute (one per node, as elsewhere), the
 // last warp only fetches tiles. Input buffer b is handed over through full[b] (the copies'
 // bytes) and returned through empty[b] (one arrival per consumer warp).
-template <int N, int GEO, int MODE>
-__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+template <int N, int GEO, int MODE, int E>
+__global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
-  using S = Shape<N>;
-  using P = TmaSmem32<N>;
+  using S = Tile<N, E>;
+  using P = TmaSmem32<N, E>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(128) char smc[];
   void* bar0 = smc + P::oBAR;        // full[0]
   void* bar1 = smc + P::oBAR + 8;    // full[1]
   void* ebar0 = smc + P::oBAR + 16;  // empty[0]
   void* ebar1 = smc + P::oBAR + 24;  // empty[1]
-  constexpr int NC = Shape<N>::threads;  // consumer threads
+  constexpr int NC = S::threads;  // consumer threads
   float* sD = reinterpret_cast<float*>(smc + P::oD);
   char* const IN0 = smc + P::oIN0;
   char* const IN1 = smc + P::oIN1;
@@ -746,8 +765,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     // ---- producer warp ----------------------------------------------------------------
     // the records of the next tile are loaded one tile ahead, so their latency is hidden
     // behind the wait for a free buffer and the copies of the current tile
-    TileRecs<N> recs;
-    if ((int)blockIdx.x < ntiles) load_recs<N>(B, blockIdx.x, recs);
+    TileRecs<E> recs;
+    if ((int)blockIdx.x < ntiles) load_recs<E>(B, blockIdx.x, recs);
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
@@ -759,8 +778,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         return;
       }
       char* IN = b ? IN1 : IN0;
-      store_recs<N, P>(B, tile, recs, IN);
-      if (tile + (int)gridDim.x < ntiles) load_recs<N>(B, tile + gridDim.x, recs);
+      store_recs<P>(B, tile, recs, IN);
+      if (tile + (int)gridDim.x < ntiles) load_recs<E>(B, tile + gridDim.x, recs);
       __syncwarp();
       tma_stage<N, P, false>(M, B, qin, tile, IN, b ? bar1 : bar0);
     }
@@ -1103,8 +1122,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   __syncthreads();
   if (tid >= NC) {
     // ---- producer warp ----------------------------------------------------------------
-    TileRecs<N> recs;
-    if ((int)blockIdx.x < ntiles) load_recs<N>(B, blockIdx.x, recs);
+    TileRecs<EPB> recs;
+    if ((int)blockIdx.x < ntiles) load_recs<EPB>(B, blockIdx.x, recs);
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
@@ -1116,8 +1135,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
         return;
       }
       char* IN = b ? IN1 : IN0;
-      store_recs<N, P>(B, tile, recs, IN);
-      if (tile + (int)gridDim.x < ntiles) load_recs<N>(B, tile + gridDim.x, recs);
+      store_recs<P>(B, tile, recs, IN);
+      if (tile + (int)gridDim.x < ntiles) load_recs<EPB>(B, tile + gridDim.x, recs);
       __syncwarp();
       tma_stage<N, P, true>(M, B, q, tile, IN, b ? bar1 : bar0);
     }
@@ -1309,6 +1328,18 @@ static size_t visc_smem32() {
   return ViscSmem32<N, GEO>::bytes;
 }
 
+template <int N, int E>
+static cudaError_t prep_inv() {
+  const int ps = (int)TmaSmem32<N, E>::bytes;
+  cudaError_t r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  return cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+}
+
 template <int N>
 static cudaError_t prep32_n() {
   cudaError_t r;
@@ -1321,14 +1352,8 @@ static cudaError_t prep32_n() {
   const int vs = (int)ViscTmaSmem32<N>::bytes;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
-  const int ps = (int)TmaSmem32<N>::bytes;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  return cudaSuccess;
+  if ((r = prep_inv<N, Shape<N>::EPB>()) != cudaSuccess) return r;
+  return prep_inv<N, AltEPB<N>::value>();
 }
 
 cudaError_t prepare_kernels32() {
@@ -1364,7 +1389,8 @@ cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, 
   return cudaGetLastError();
 }
 
-// grid of the persistent viscous kernel: every resident block slot of the GPU, at most one per tile
+// grid of the persistent viscous kernel: every resident block slot of the GPU (or b.bps blocks
+// per SM when the autotuner chose fewer), at most one per tile
 template <int N, int GEO>
 static cudaError_t launch_vpipe(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
@@ -1378,14 +1404,15 @@ static cudaError_t launch_vpipe(const DevMesh& M, const Bucket& b, const double*
     if (per_sm < 1) per_sm = 1;
   }
   const int ntiles = (b.count + Shape<N>::EPB - 1) / Shape<N>::EPB;
-  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
+  const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
+  const int grid = ntiles < bps * sms ? ntiles : bps * sms;
   k_viscous32t<N, GEO><<<grid, Shape<N>::threads + 32, sm, s>>>(M, b, q);
   return cudaGetLastError();
 }
 
 cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  if (b.geo != 2) {  // box and affine: the pipelined kernel
+  if (b.geo != 2 && b.visc_alt == 0) {  // box and affine: the pipelined kernel unless tuned away
     if (!b.blink || !b.bmeta) return cudaErrorInvalidValue;
     DG32_DISPATCH_N(b.N, {
       return b.geo == 0 ? launch_vpipe<NN, 0>(M, b, q, s) : launch_vpipe<NN, 1>(M, b, q, s);
@@ -1405,25 +1432,53 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
   return cudaGetLastError();
 }
 
-// grid of the persistent kernel: every resident block slot of the GPU, at most one per tile
-template <int N, int GEO, int MODE>
+// grid of the persistent kernel: every resident block slot of the GPU (or b.bps blocks per SM
+// when the autotuner chose fewer), at most one per tile
+template <int N, int GEO, int MODE, int E>
 static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                int stage, int write_tr, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
-  const size_t sm = TmaSmem32<N>::bytes;
+  const size_t sm = TmaSmem32<N, E>::bytes;
   if (per_sm < 0) {
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE>,
-                                                                  Shape<N>::threads + 32, sm);
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E>,
+                                                                  Tile<N, E>::threads + 32, sm);
     if (r != cudaSuccess) return r;
     int dev = 0;
     if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
     if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
     if (per_sm < 1) per_sm = 1;
   }
-  const int ntiles = (b.count + Shape<N>::EPB - 1) / Shape<N>::EPB;
-  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
-  k_inviscid32t<N, GEO, MODE><<<grid, Shape<N>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
+  const int ntiles = (b.count + E - 1) / E;
+  const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
+  const int grid = ntiles < bps * sms ? ntiles : bps * sms;
+  k_inviscid32t<N, GEO, MODE, E><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
   return cudaGetLastError();
+}
+
+template <int N, int E>
+static cudaError_t launch_inv_shape(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                                   int mode, int stage, int write_tr, cudaStream_t s) {
+  if (mode == MODE_RESIDUAL) {
+    if (b.geo == 0) return launch_pipe<N, 0, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
+    if (b.geo == 1) return launch_pipe<N, 1, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
+    return launch_pipe<N, 2, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
+  }
+  if (b.geo == 0) return launch_pipe<N, 0, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
+  if (b.geo == 1) return launch_pipe<N, 1, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
+  return launch_pipe<N, 2, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
+}
+
+int tile_epb32(int N, int alt) {
+  switch (N) {
+    case 1: return alt ? AltEPB<1>::value : Shape<1>::EPB;
+    case 2: return alt ? AltEPB<2>::value : Shape<2>::EPB;
+    case 3: return alt ? AltEPB<3>::value : Shape<3>::EPB;
+    case 4: return alt ? AltEPB<4>::value : Shape<4>::EPB;
+    case 5: return alt ? AltEPB<5>::value : Shape<5>::EPB;
+    case 6: return alt ? AltEPB<6>::value : Shape<6>::EPB;
+    case 7: return alt ? AltEPB<7>::value : Shape<7>::EPB;
+    default: return 0;
+  }
 }
 
 cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g, int mode,
@@ -1431,17 +1486,8 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
   if (b.count == 0) return cudaSuccess;
   if (!b.boff || !b.btr || !b.blink || !b.bflag || !b.bmeta) return cudaErrorInvalidValue;
   DG32_DISPATCH_N(b.N, {
-    cudaError_t r;
-    if (mode == MODE_RESIDUAL) {
-      if (b.geo == 0) r = launch_pipe<NN, 0, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
-      else if (b.geo == 1) r = launch_pipe<NN, 1, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
-      else r = launch_pipe<NN, 2, MODE_RESIDUAL>(M, b, q, out, g, stage, write_tr, s);
-    } else {
-      if (b.geo == 0) r = launch_pipe<NN, 0, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
-      else if (b.geo == 1) r = launch_pipe<NN, 1, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
-      else r = launch_pipe<NN, 2, MODE_RK>(M, b, q, out, g, stage, write_tr, s);
-    }
-    return r;
+    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value>(M, b, q, out, g, mode, stage, write_tr, s);
+    return launch_inv_shape<NN, Shape<NN>::EPB>(M, b, q, out, g, mode, stage, write_tr, s);
   });
   return cudaSuccess;
 }

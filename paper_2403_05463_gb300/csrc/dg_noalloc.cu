@@ -10,8 +10,8 @@
 //
 // Every call in one process on one device shares that array, whatever mesh it is for: two
 // calls whose kernels overlap on the GPU (different streams, or different host threads)
-// overwrite each other's partial sums. Nothing in the array has to start at zero: each call writes every partial sum
-// (4 per element) before its final reduction reads them.
+// overwrite each other's partial sums. Nothing in the array has to start at zero: each call
+// writes every partial sum (4 per element) before its final reduction reads them.
 #include <mutex>
 
 #include "dg_device.cuh"

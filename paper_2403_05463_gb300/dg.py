@@ -77,6 +77,7 @@ def load():
         L.dg_rk_step_host.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]
         L.dg_conservation.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_conservation_noalloc.argtypes = [_vp, _vp, _vp, _vp]
+        L.dg_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
         L.dg_check_device.argtypes = [_vp, _vp]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -240,6 +241,14 @@ class Solver:
             raise ValueError("out must hold 4 float64 values")
         _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R"), _dev_ptr(out, "out"),
                                               _stream_handle(stream)))
+
+    def autotune(self, cache_path=None):
+        """Time the candidate launch shapes of the reduced-precision passes on this mesh and
+        keep the fastest (see dg_autotune); returns the library's report."""
+        buf = ctypes.create_string_buffer(8192)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(load().dg_autotune(self.h, path, buf, len(buf)))
+        return buf.value.decode()
 
     PHASES = ("traces", "mortar_lift", "viscous", "mortar_flux", "inviscid_update")
 
