@@ -291,6 +291,19 @@ int or_abs_jacobian(const or_real q[4], const or_real nh[3], or_real c0sq, or_re
 
 /* Convective numerical flux through a face with unit normal nh pointing from the
  * qm side to the qp side (Sec. 2.3: Roe; LLF as the alternative flux). */
+void or_kep_flux(const or_real qi[4], const or_real qm[4], const or_real Ja_i[3], const or_real Ja_m[3],
+                 or_real c0sq, or_real out[4]) {
+  or_real ja[3], u[3];
+  for (int k = 0; k < 3; ++k) {
+    ja[k] = 0.5 * (Ja_i[k] + Ja_m[k]);
+    u[k] = 0.5 * (qi[1 + k] + qm[1 + k]);
+  }
+  const or_real p = 0.5 * (qi[0] + qm[0]);
+  const or_real U = ja[0] * u[0] + ja[1] * u[1] + ja[2] * u[2];
+  out[0] = c0sq * U;
+  for (int c = 0; c < 3; ++c) out[1 + c] = u[c] * U + p * ja[c];
+}
+
 int or_riemann(const or_real qm[4], const or_real qp[4], const or_real nh[3], const or_params* prm,
                or_real out[4]) {
   or_real fm[4], fp[4];
@@ -458,6 +471,10 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const or_real* gxyz, c
   }
   if (g < 1 || g > OR_MAXG) {
     set_err("geometry degree %d unsupported", g);
+    return NULL;
+  }
+  if (prm->split != 0 && prm->split != 1) {
+    set_err("split %d invalid", prm->split);
     return NULL;
   }
   if (prm->mixed_face != 0 && prm->mixed_face != 1) {
@@ -1045,8 +1062,10 @@ static int element_residual(const work_t* W, int64_t e, or_real* R) {
   const or_real* q = W->q;
   int64_t o = m->off[e], T = m->total;
   or_real c0sq = m->p.c0sq;
-  /* contravariant total flux Ftil[d][v][p] = sum_k Ja^d_k (F_e - F_v)_{v,k} */
+  /* contravariant total flux Ftil[d][v][p] = sum_k Ja^d_k (F_e - F_v)_{v,k}, and its convective
+   * part Fc (kept for the split form) */
   or_real* Ft = (or_real*)malloc(sizeof(or_real) * 12 * n3);
+  or_real* Fc = (or_real*)malloc(sizeof(or_real) * 12 * n3);
   for (int p = 0; p < n3; ++p) {
     or_real qq[4];
     for (int v = 0; v < 4; ++v) qq[v] = q[v * T + o + p];
@@ -1055,6 +1074,12 @@ static int element_residual(const work_t* W, int64_t e, or_real* R) {
       F[0][k] = c0sq * qq[1 + k];
       for (int c = 0; c < 3; ++c) F[1 + c][k] = qq[1 + c] * qq[1 + k] + (c == k ? qq[0] : 0.0);
     }
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 4; ++v) {
+        or_real sc = 0.0;
+        for (int k = 0; k < 3; ++k) sc += gt->Ja[(d * 3 + k) * n3 + p] * F[v][k];
+        Fc[(d * 4 + v) * n3 + p] = sc;
+      }
     if (m->flag[e]) {
       or_real tau[3][3];
       stress(m, gt, W->G[e], e, n3, p, tau);
@@ -1086,6 +1111,34 @@ static int element_residual(const work_t* W, int64_t e, or_real* R) {
           }
           JR[v * n3 + ii + n * (jj + n * kk)] = s;
         }
+  if (m->p.split == 1) {
+    /* By summation by parts the weak convective volume term above equals -sum_m D_im Fc_m plus
+     * the end-node terms; the split form replaces -sum_m D_im Fc_m along each direction by
+     * -sum_m 2 D_im F#(q_i, q_m). Both sums are taken directly here. */
+    for (int kk = 0; kk < n; ++kk)
+      for (int jj = 0; jj < n; ++jj)
+        for (int ii = 0; ii < n; ++ii) {
+          int ijk[3] = {ii, jj, kk};
+          const int pi = ii + n * (jj + n * kk);
+          or_real qi[4];
+          for (int v = 0; v < 4; ++v) qi[v] = q[v * T + o + pi];
+          for (int d = 0; d < 3; ++d) {
+            or_real jai[3] = {gt->Ja[(d * 3) * n3 + pi], gt->Ja[(d * 3 + 1) * n3 + pi], gt->Ja[(d * 3 + 2) * n3 + pi]};
+            for (int mm = 0; mm < n; ++mm) {
+              int src[3] = {ii, jj, kk};
+              src[d] = mm;
+              const int pm = src[0] + n * (src[1] + n * src[2]);
+              or_real qm2[4], fs[4];
+              for (int v = 0; v < 4; ++v) qm2[v] = q[v * T + o + pm];
+              or_real jam[3] = {gt->Ja[(d * 3) * n3 + pm], gt->Ja[(d * 3 + 1) * n3 + pm], gt->Ja[(d * 3 + 2) * n3 + pm]};
+              or_kep_flux(qi, qm2, jai, jam, c0sq, fs);
+              const or_real Dim = D[ijk[d] * n + mm];
+              for (int v = 0; v < 4; ++v)
+                JR[v * n3 + pi] += Dim * Fc[(d * 4 + v) * n3 + pm] - 2.0 * Dim * fs[v];
+            }
+          }
+        }
+  }
   or_real* LH = (or_real*)malloc(sizeof(or_real) * 4 * n2);
   int rc = 0;
   for (int f = 0; f < 6; ++f) {
@@ -1101,6 +1154,7 @@ static int element_residual(const work_t* W, int64_t e, or_real* R) {
   free(LH);
   free(JR);
   free(Ft);
+  free(Fc);
   return rc;
 }
 

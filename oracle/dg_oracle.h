@@ -48,6 +48,9 @@ typedef struct {
   int mixed_face;   /* viscous flux on a face between an NS and an Euler element
                        (Sec. 2.3 asks only that it be single-valued): 0 the average
                        of the NS side's flux and zero, 1 the NS side's flux alone    */
+  int split;        /* convective volume term: 0 the standard form (App. B, Eq. NS4),
+                       1 the kinetic-energy-preserving split form: along each direction
+                       sum_m 2 D_im F#(q_i, q_m) with the two-point flux of or_kep_flux */
   or_real inflow[4]; /* ghost state used at inflow faces (velocity part)          */
 } or_params;
 
@@ -63,6 +66,11 @@ int or_project_lgl(int Nh, int Nl, or_real* P);            /* P[(Nl+1)][(Nh+1)] 
 void or_normal_flux(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real out[4]);
 void or_flux_jacobian(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real A[16]);
 int or_abs_jacobian(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real absA[16]);
+/* Kinetic-energy-preserving two-point flux along one direction between nodes i and m, with
+ * their contravariant metric vectors Ja_i, Ja_m (J dxi/dx for that direction): averages
+ * {{.}} = (a_i + a_m)/2, U = {{Ja}}.{{u}}; out = (c0^2 U, {{u}} U + {{p}} {{Ja}}). */
+void or_kep_flux(const or_real qi[4], const or_real qm[4], const or_real Ja_i[3], const or_real Ja_m[3],
+                 or_real c0sq, or_real out[4]);
 int or_riemann(const or_real qm[4], const or_real qp[4], const or_real n_hat[3],
                const or_params* prm, or_real out[4]);
 or_real or_eddy_viscosity(const or_real G[9], or_real delta, const or_params* prm);

@@ -52,7 +52,8 @@ _u8 = _P(ctypes.c_uint8)
 def _params_type(real):
     class P(ctypes.Structure):
         _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
-                    ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("inflow", real * 4)]
+                    ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
+                    ("inflow", real * 4)]
     return P
 
 
@@ -75,6 +76,8 @@ def lib(extended: bool = False):
             L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_normal_flux.argtypes = [_d, _d, real, _d]
             L.or_normal_flux.restype = None
+            L.or_kep_flux.argtypes = [_d, _d, _d, _d, real, _d]
+            L.or_kep_flux.restype = None
             L.or_flux_jacobian.argtypes = [_d, _d, real, _d]
             L.or_flux_jacobian.restype = None
             L.or_abs_jacobian.argtypes = [_d, _d, real, _d]
@@ -112,10 +115,11 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0):
+def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0,
+           split=0):
     p = Params()
     p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
-    p.closure, p.riemann, p.mixed_face = closure, riemann, mixed_face
+    p.closure, p.riemann, p.mixed_face, p.split = closure, riemann, mixed_face, split
     for i in range(4):
         p.inflow[i] = inflow[i]
     return p
@@ -157,6 +161,13 @@ def project(Nh, Nl):
 def normal_flux(q, n, c0sq):
     out = np.zeros(4)
     lib().or_normal_flux(_ptr(_f64(q), _d), _ptr(_f64(n), _d), c0sq, _ptr(out, _d))
+    return out
+
+
+def kep_flux(qi, qm, ja_i, ja_m, c0sq):
+    out = np.zeros(4)
+    lib().or_kep_flux(_ptr(_f64(qi), _d), _ptr(_f64(qm), _d), _ptr(_f64(ja_i), _d), _ptr(_f64(ja_m), _d), c0sq,
+                      _ptr(out, _d))
     return out
 
 

@@ -506,3 +506,78 @@ def test_one_sided_mixed_face_changes_only_the_interface_terms():
     assert np.abs(d[:, ~touched]).max() <= 1e-13 * scale  # only interface face nodes move
     assert np.abs(d[1:, touched & ~np.isin(np.arange(A.total), ns_nodes)]).max() > 0.1 * scale
     assert np.abs(A.conservation(d)).max() <= 1e-13 * scale
+
+
+# ---- kinetic-energy-preserving split form (split = 1) ----------------------------------------
+
+def _kep_mesh(w, **extra):
+    m = w.mesh
+    return orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**dict(w.params, split=1, **extra)),
+                    m.bc_tag)
+
+
+def test_kep_two_point_flux_consistent_and_symmetric():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a, b = rng.normal(size=4), rng.normal(size=4)
+        ja, jb = rng.normal(size=3), rng.normal(size=3)
+        np.testing.assert_allclose(orc.kep_flux(a, a, ja, ja, 25.0), orc.normal_flux(a, ja, 25.0), rtol=1e-14,
+                                   atol=1e-13)
+        np.testing.assert_allclose(orc.kep_flux(a, b, ja, jb, 25.0), orc.kep_flux(b, a, jb, ja, 25.0), rtol=1e-15,
+                                   atol=1e-14)
+
+
+def test_kep_equals_standard_form_for_low_degree_states():
+    # On affine elements sum_m 2 D_im {{a}}{{b}} = (a Db + b Da + D(ab))/2, which is (ab)' when a b
+    # has degree <= N: for velocities of degree N/2 along every line the split form is the
+    # standard one; for other states it is not.
+    w = wl.tgv_4x4x4_n3(n_elem_dir=3, order=4)
+    mesh, _ = wl.rotate_elements(w.mesh, 23)
+    import dataclasses
+    w = dataclasses.replace(w, mesh=mesh, flags=np.zeros(27, np.uint8))
+    std, kep = _mesh(w), _kep_mesh(w)
+    x = std.node_coords()
+    q = np.stack([0.3 + 0.1 * x[0] * x[1], 1.0 + 0.2 * x[1] - 0.05 * x[2] ** 2,
+                  0.1 * x[0] * x[2] - 0.3, 0.07 * x[0] ** 2 + 0.1 * x[1]])
+    Rs, Rk = std.residual(q), kep.residual(q)
+    assert np.abs(Rk - Rs).max() <= 1e-12 * np.abs(Rs).max()
+    q2 = w.state(x)  # trigonometric: the two forms differ
+    assert np.abs(kep.residual(q2) - std.residual(q2)).max() > 1e-4 * np.abs(std.residual(q2)).max()
+
+
+def test_kep_free_stream_curved_mixed_orders():
+    w = _small_padapt(seed=7)
+    M = _kep_mesh(w)
+    q = np.zeros((4, M.total))
+    q[0], q[1], q[2], q[3] = 0.3, 1.0, -0.5, 0.25
+    assert np.abs(M.residual(q)).max() < 1e-11
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_kep_conservation_periodic_mixed(seed):
+    # F#(a, b) = F#(b, a) and summation by parts: the volume sums telescope to the end-node
+    # fluxes, which the face terms replace by the single-valued numerical flux
+    w = _small_padapt(seed=seed)
+    M = _kep_mesh(w, nu=1e-2)
+    xyz = M.node_coords()
+    q = w.state(xyz)
+    q[0] += 0.1 * np.sin(2 * np.pi * xyz[0])
+    R = M.residual(q)
+    _, scale = _weighted_abs(M, R)
+    assert np.abs(M.conservation(R)).max() < 1e-12 * scale
+
+
+def test_kep_spectral_convergence_tgv():
+    pytest.importorskip("sympy")
+    errs = []
+    for N in range(2, 8):
+        w = wl.tgv_4x4x4_n3(order=N)
+        prm = orc.params(**dict(w.params, nu=0.01, cs=0.0, split=1))
+        M = orc.Mesh(w.mesh.hex, w.mesh.geom, 1, w.orders, w.flags, prm)
+        xyz = M.node_coords()
+        R = M.residual(w.state(xyz))
+        Rex = _tgv_exact_residual(xyz, 0.01, 25.0)
+        errs.append(np.sqrt(((R - Rex) ** 2).sum() / (Rex ** 2).sum()))
+    errs = np.array(errs)
+    assert np.all(np.diff(np.log(errs)) < -0.5), errs
+    assert errs[-1] < 5e-4, errs
