@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read, then rewritten)")
     return ap.parse_args()
 
 
@@ -248,7 +249,7 @@ def main():
     w = wl.WORKLOADS[args.workload]() if args.n is None else wl.WORKLOADS[args.workload](n=args.n)
     S = dg.Solver.from_workload(w, precision=args.precision, device=local)
     # launch shapes per (order, geometry) timed on this GPU and mesh before the timed region
-    tuning = "default" if args.no_autotune else S.autotune()
+    tuning = "default" if args.no_autotune else S.autotune(args.tune_cache)
     dof = S.total_nodes
     xyz = S.node_coords()
     q = w.state_fn(xyz, None, None) if args.workload == "mixed_64x64x64_n4" else \
