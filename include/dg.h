@@ -88,6 +88,11 @@ typedef struct {
                        asks only that it be single-valued): 0 the average of the NS side's
                        flux and zero (BR1 with an inviscid side), 1 the NS side's flux
                        alone; faces between two NS elements always take the average      */
+  int split;        /* convective volume term: 0 the standard form (App. B, Eq. NS4), 1 the
+                       kinetic-energy-preserving split form: along each direction
+                       sum_m 2 D_im F#(q_i, q_m) with F# = (c0^2 U, {{u}} U + {{p}} {{Ja}}),
+                       U = {{Ja}}.{{u}}, {{.}} the two-node average                       */
+  int reserved;     /* must be 0                                                       */
   double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
 } dg_params;
 

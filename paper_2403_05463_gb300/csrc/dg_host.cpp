@@ -314,6 +314,8 @@ dg_status check_params(const dg_params* p) {
   if (p->riemann < 0 || p->riemann > 1) return fail(DG_ERR_ARG, "riemann must be 0 or 1");
   if (p->precision < 0 || p->precision > 1) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
   if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
+  if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
+  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
   return DG_OK;
 }
 
@@ -325,6 +327,7 @@ void apply_params(dg_ctx* c) {
   c->M.closure = c->prm.closure;
   c->M.riemann = c->prm.riemann;
   c->M.mixed_face = c->prm.mixed_face;
+  c->M.split = c->prm.split;
   c->M.precision = c->prm.precision;
   c->M.nu32 = (float)c->prm.nu;
   c->M.c0sq32 = (float)c->prm.c0sq;

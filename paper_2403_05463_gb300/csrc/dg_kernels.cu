@@ -317,15 +317,18 @@ __global__ void __launch_bounds__(Shape<N>::threads) k_viscous(DevMesh M, const 
 // ---------------------------------------------------------------------------------------
 // inviscid pass + assembly + (optional) RK update
 // ---------------------------------------------------------------------------------------
-template <int N, bool CURVED, int MODE>
+// KEP: the split form's volume term, sum_m 2 D_im F#(q_i, q_m) along each direction; the
+// element's state [4][n3] (and, curved, its metric [9][n3]) is kept in shared memory instead
+// of the contravariant fluxes.
+template <int N, bool CURVED, int MODE, bool KEP>
 __global__ void __launch_bounds__(Shape<N>::threads)
     k_inviscid(DevMesh M, const int32_t* __restrict__ list, int count, const double* qin, double* out,
                double* g, int stage, double dt, int write_tr) {
   using S = Shape<N>;
-  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB, PER = KEP ? 13 : 12;
   extern __shared__ double sm[];
   double* sD = sm;
-  double* sF = sD + NP * NP;  // EPB * 12 * n3: Ftil_e[d][v]
+  double* sF = sD + NP * NP;  // EPB * PER * n3: Ftil_e[d][v], or (KEP) q[v] and Ja[9]
   const int tid = threadIdx.x;
   for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_ops.D[N][t];
   int le = tid / n3, p = tid % n3;
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   if (le >= EPB) le = EPB - 1;
   const int e = active ? list[slot] : 0;
   const int64_t off = active ? M.elem_off[e] : 0;
-  double* F = sF + le * 12 * n3;
+  double* F = sF + le * PER * n3;
   double qq[4] = {0.0, 0.0, 0.0, 0.0}, Ja[9], invJ = 0.0, fl[4][3];
   if (active) {
 #pragma unroll
@@ -355,11 +358,20 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
       for (int c = 0; c < 3; ++c) fl[1 + c][k] = qq[1 + c] * qq[1 + k] + (c == k ? qq[0] : 0.0);
     }
+    if (!KEP) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        F[(d * 4 + v) * n3 + p] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+        for (int v = 0; v < 4; ++v)
+          F[(d * 4 + v) * n3 + p] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) F[v * n3 + p] = qq[v];
+      if (CURVED) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[(4 + k) * n3 + p] = Ja[k];
+      }
+    }
   }
   __syncthreads();
   if (!active) return;
@@ -373,8 +385,24 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     for (int m = 0; m < n; ++m) {
       double dm = sD[ii[d] * n + m];
       int pm = base + m * str[d];
+      if (!KEP) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) JR[v] -= dm * F[(d * 4 + v) * n3 + pm];
+        for (int v = 0; v < 4; ++v) JR[v] -= dm * F[(d * 4 + v) * n3 + pm];
+      } else {
+        // two-point flux between this node and node m of the line: averages of u, p, Ja^d
+        double ja[3], u[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ja[k] = CURVED ? 0.5 * (Ja[d * 3 + k] + F[(4 + d * 3 + k) * n3 + pm]) : Ja[d * 3 + k];
+          u[k] = 0.5 * (qq[1 + k] + F[(1 + k) * n3 + pm]);
+        }
+        const double pa = 0.5 * (qq[0] + F[pm]);
+        const double U = ja[0] * u[0] + ja[1] * u[1] + ja[2] * u[2];
+        const double d2 = 2.0 * dm;
+        JR[0] -= d2 * M.c0sq * U;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) JR[1 + c] -= d2 * (u[c] * U + pa * ja[c]);
+      }
     }
   }
   const bool ns = M.flag[e] != 0;
@@ -683,8 +711,8 @@ static size_t visc_smem() {
   return sizeof(double) * (NP * NP + Shape<N>::EPB * (3 + (C ? 9 : 0) + 9) * Shape<N>::n3);
 }
 template <int N>
-static size_t inv_smem() {
-  return sizeof(double) * (NP * NP + Shape<N>::EPB * 12 * Shape<N>::n3);
+static size_t inv_smem(bool kep = false) {
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * (kep ? 13 : 12) * Shape<N>::n3);
 }
 
 template <int N>
@@ -694,11 +722,15 @@ static cudaError_t prep_n() {
                                 (int)visc_smem<N, false>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem<N, true>())) != cudaSuccess) return r;
-  const int is = (int)inv_smem<N>();
-  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  const int is = (int)inv_smem<N>(), ks = (int)inv_smem<N>(true);
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RESIDUAL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RESIDUAL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RESIDUAL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RESIDUAL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, false, MODE_RK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid<N, true, MODE_RK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ks)) != cudaSuccess) return r;
   return cudaSuccess;
 }
 
@@ -751,25 +783,33 @@ cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, i
   return cudaGetLastError();
 }
 
+template <int N, bool CURVED, int MODE, bool KEP>
+static cudaError_t launch_inv64(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                                int stage, double dt, int write_tr, cudaStream_t s) {
+  using SH = Shape<N>;
+  const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+  k_inviscid<N, CURVED, MODE, KEP><<<grid, SH::threads, inv_smem<N>(KEP), s>>>(M, b.list, b.count, q, out, g, stage,
+                                                                                dt, write_tr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                             int mode, int stage, double dt, int write_tr, int precision, cudaStream_t s) {
   if (precision == 1) return launch_inviscid32(M, b, q, out, g, mode, stage, write_tr, s);
   if (b.count == 0) return cudaSuccess;
   DG_DISPATCH_N(b.N, {
-    using SH = Shape<NN>;
-    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
-    const size_t sm = inv_smem<NN>();
-    if (mode == MODE_RESIDUAL) {
-      if (b.curved)
-        k_inviscid<NN, true, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
-      else
-        k_inviscid<NN, false, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
-    } else {
-      if (b.curved)
-        k_inviscid<NN, true, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
-      else
-        k_inviscid<NN, false, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, q, out, g, stage, dt, write_tr);
+    if (M.split == 1) {
+      if (mode == MODE_RESIDUAL)
+        return b.curved ? launch_inv64<NN, true, MODE_RESIDUAL, true>(M, b, q, out, g, stage, dt, write_tr, s)
+                        : launch_inv64<NN, false, MODE_RESIDUAL, true>(M, b, q, out, g, stage, dt, write_tr, s);
+      return b.curved ? launch_inv64<NN, true, MODE_RK, true>(M, b, q, out, g, stage, dt, write_tr, s)
+                      : launch_inv64<NN, false, MODE_RK, true>(M, b, q, out, g, stage, dt, write_tr, s);
     }
+    if (mode == MODE_RESIDUAL)
+      return b.curved ? launch_inv64<NN, true, MODE_RESIDUAL, false>(M, b, q, out, g, stage, dt, write_tr, s)
+                      : launch_inv64<NN, false, MODE_RESIDUAL, false>(M, b, q, out, g, stage, dt, write_tr, s);
+    return b.curved ? launch_inv64<NN, true, MODE_RK, false>(M, b, q, out, g, stage, dt, write_tr, s)
+                    : launch_inv64<NN, false, MODE_RK, false>(M, b, q, out, g, stage, dt, write_tr, s);
   });
   return cudaGetLastError();
 }

@@ -452,7 +452,7 @@ struct AltEPB {
   static constexpr int value = N <= 4 ? Shape<N>::EPB / 2 : (N <= 6 ? 2 : Shape<N>::EPB);
 };
 
-template <int N, int E = Shape<N>::EPB>
+template <int N, int E = Shape<N>::EPB, bool KEPC = false>
 struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
@@ -463,7 +463,10 @@ struct TmaSmem32 {
                        iEC = iLK + 96, iMT = iEC + 48, iSH = iMT + 32, in_elem = a16(iSH + 32);
   static constexpr int ITEMS = 18;  // copies per element: 4 QD, 6 NT, 6 NV, OV, EC
   // work per element: F [3 n3] flux deviations, QH/QL [n3] hi/lo state, T [6 n2] face terms
-  static constexpr int wF = 0, wQ = 48 * n3, wT = 80 * n3, work_elem = 80 * n3 + 96 * n2;
+  // (split form on curved elements: F holds the state deviations and the three metric vectors,
+  // 4 n3 float4, so everything after it moves by 16 n3)
+  static constexpr int FB = KEPC ? 64 * n3 : 48 * n3;
+  static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, work_elem = FB + 32 * n3 + 96 * n2;
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
 };
@@ -730,11 +733,16 @@ struct InvMinBlocks {
 // Warp-specialised: threads [0, Shape<N>::threads) compute (one per node, as elsewhere), the
 // last warp only fetches tiles. Input buffer b is handed over through full[b] (the copies'
 // bytes) and returned through empty[b] (one arrival per consumer warp).
-template <int N, int GEO, int MODE, int E>
+// KEP: the split form's volume term sum_m 2 D_im F#(q_i, q_m), in deviation form like the
+// standard one: F#(q_i, q_m) - F#(q_r, q_r) with the averages {{q}} = q_r + {{dq}} has only terms
+// of the size of the deviations, and sum_d sum_m 2 D_im F#(q_r, q_r) = f(q_r) . sum_d (D_d Ja^d)
+// vanishes by the discrete metric identities. Shared memory then holds the deviations dq (and,
+// on curved elements, the metric vectors Ja^d) instead of the contravariant fluxes.
+template <int N, int GEO, int MODE, int E, bool KEP>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
   using S = Tile<N, E>;
-  using P = TmaSmem32<N, E>;
+  using P = TmaSmem32<N, E, KEP && GEO == 2>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(128) char smc[];
   void* bar0 = smc + P::oBAR;        // full[0]
@@ -839,8 +847,9 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
     float invJ = 0.f;
     // ---- node phase: split state, flux deviations --------------------------------------
+    float qr32[4] = {0.f, 0.f, 0.f, 0.f};  // the element's reference state (hi parts of node 0)
     if (active) {
-      float dq[4], qr32[4], h[4], l[4];
+      float dq[4], h[4], l[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const double* QDv = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v]);
@@ -858,12 +867,15 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
         for (int c = 0; c < 3; ++c)
           fl[1 + c][k] = qr32[1 + c] * dq[1 + k] + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
       }
+      if (KEP) F4[p] = make_float4(dq[0], dq[1], dq[2], dq[3]);
       if (GEO == 0) {
         invJ = EC->invJ;
+        if (!KEP) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float j = EC->Ja[d * 4];
-          F4[d * n3 + p] = make_float4(j * fl[0][d], j * fl[1][d], j * fl[2][d], j * fl[3][d]);
+          for (int d = 0; d < 3; ++d) {
+            const float j = EC->Ja[d * 4];
+            F4[d * n3 + p] = make_float4(j * fl[0][d], j * fl[1][d], j * fl[2][d], j * fl[3][d]);
+          }
         }
       } else {
         float Ja[9];
@@ -876,12 +888,17 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
           for (int k = 0; k < 9; ++k) Ja[k] = EC->Ja[k];
           invJ = EC->invJ;
         }
+        if (!KEP) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          float c4[4];
+          for (int d = 0; d < 3; ++d) {
+            float c4[4];
 #pragma unroll
-          for (int v = 0; v < 4; ++v) c4[v] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
-          F4[d * n3 + p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+            for (int v = 0; v < 4; ++v) c4[v] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+            F4[d * n3 + p] = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          }
+        } else if (GEO == 2) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) F4[(1 + d) * n3 + p] = make_float4(Ja[d * 3], Ja[d * 3 + 1], Ja[d * 3 + 2], 0.f);
         }
       }
     }
@@ -890,17 +907,54 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     float JR[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
       const int str[3] = {1, n, n2};
+      if (!KEP) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int bs = p - ii[d] * str[d];
+        for (int d = 0; d < 3; ++d) {
+          const int bs = p - ii[d] * str[d];
 #pragma unroll
-        for (int m = 0; m < n; ++m) {
-          const float dm = sD[ii[d] * n + m];
-          const float4 f4 = F4[d * n3 + bs + m * str[d]];
-          JR[0] -= dm * f4.x;
-          JR[1] -= dm * f4.y;
-          JR[2] -= dm * f4.z;
-          JR[3] -= dm * f4.w;
+          for (int m = 0; m < n; ++m) {
+            const float dm = sD[ii[d] * n + m];
+            const float4 f4 = F4[d * n3 + bs + m * str[d]];
+            JR[0] -= dm * f4.x;
+            JR[1] -= dm * f4.y;
+            JR[2] -= dm * f4.z;
+            JR[3] -= dm * f4.w;
+          }
+        }
+      } else {
+        const float4 di = F4[p];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int bs = p - ii[d] * str[d];
+          float jai[3];
+          if (GEO == 2) {
+            const float4 j4 = F4[(1 + d) * n3 + p];
+            jai[0] = j4.x, jai[1] = j4.y, jai[2] = j4.z;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) jai[k] = GEO == 0 ? (k == d ? EC->Ja[d * 4] : 0.f) : EC->Ja[d * 3 + k];
+          }
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            const int pm = bs + m * str[d];
+            const float d2 = 2.f * sD[ii[d] * n + m];
+            const float4 dmv = F4[pm];
+            // averaged deviations and metric of the pair (i, m)
+            const float bp = 0.5f * (di.x + dmv.x), bu[3] = {0.5f * (di.y + dmv.y), 0.5f * (di.z + dmv.z),
+                                                               0.5f * (di.w + dmv.w)};
+            float ja[3];
+            if (GEO == 2) {
+              const float4 j4 = F4[(1 + d) * n3 + pm];
+              ja[0] = 0.5f * (jai[0] + j4.x), ja[1] = 0.5f * (jai[1] + j4.y), ja[2] = 0.5f * (jai[2] + j4.z);
+            } else {
+              ja[0] = jai[0], ja[1] = jai[1], ja[2] = jai[2];
+            }
+            const float Ur = ja[0] * qr32[1] + ja[1] * qr32[2] + ja[2] * qr32[3];
+            const float Ud = ja[0] * bu[0] + ja[1] * bu[1] + ja[2] * bu[2];
+            JR[0] -= d2 * (c0sq * Ud);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) JR[1 + c] -= d2 * (qr32[1 + c] * Ud + bu[c] * (Ur + Ud) + bp * ja[c]);
+          }
         }
       }
 #pragma unroll
@@ -1328,16 +1382,16 @@ static size_t visc_smem32() {
   return ViscSmem32<N, GEO>::bytes;
 }
 
-template <int N, int E>
+template <int N, int E, bool KEP>
 static cudaError_t prep_inv() {
-  const int ps = (int)TmaSmem32<N, E>::bytes;
+  const int ps = (int)TmaSmem32<N, E>::bytes, pc = (int)TmaSmem32<N, E, KEP>::bytes;
   cudaError_t r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  return cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  return cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc);
 }
 
 template <int N>
@@ -1352,8 +1406,9 @@ static cudaError_t prep32_n() {
   const int vs = (int)ViscTmaSmem32<N>::bytes;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
-  if ((r = prep_inv<N, Shape<N>::EPB>()) != cudaSuccess) return r;
-  return prep_inv<N, AltEPB<N>::value>();
+  if ((r = prep_inv<N, Shape<N>::EPB, false>()) != cudaSuccess) return r;
+  if ((r = prep_inv<N, Shape<N>::EPB, true>()) != cudaSuccess) return r;
+  return prep_inv<N, AltEPB<N>::value, false>();
 }
 
 cudaError_t prepare_kernels32() {
@@ -1434,13 +1489,13 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
 
 // grid of the persistent kernel: every resident block slot of the GPU (or b.bps blocks per SM
 // when the autotuner chose fewer), at most one per tile
-template <int N, int GEO, int MODE, int E>
+template <int N, int GEO, int MODE, int E, bool KEP>
 static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                int stage, int write_tr, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
-  const size_t sm = TmaSmem32<N, E>::bytes;
+  const size_t sm = TmaSmem32<N, E, KEP && GEO == 2>::bytes;
   if (per_sm < 0) {
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E>,
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E, KEP>,
                                                                   Tile<N, E>::threads + 32, sm);
     if (r != cudaSuccess) return r;
     int dev = 0;
@@ -1451,21 +1506,21 @@ static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* 
   const int ntiles = (b.count + E - 1) / E;
   const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
   const int grid = ntiles < bps * sms ? ntiles : bps * sms;
-  k_inviscid32t<N, GEO, MODE, E><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
+  k_inviscid32t<N, GEO, MODE, E, KEP><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
   return cudaGetLastError();
 }
 
-template <int N, int E>
+template <int N, int E, bool KEP>
 static cudaError_t launch_inv_shape(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                    int mode, int stage, int write_tr, cudaStream_t s) {
   if (mode == MODE_RESIDUAL) {
-    if (b.geo == 0) return launch_pipe<N, 0, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
-    if (b.geo == 1) return launch_pipe<N, 1, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
-    return launch_pipe<N, 2, MODE_RESIDUAL, E>(M, b, q, out, g, stage, write_tr, s);
+    if (b.geo == 0) return launch_pipe<N, 0, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+    if (b.geo == 1) return launch_pipe<N, 1, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+    return launch_pipe<N, 2, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
   }
-  if (b.geo == 0) return launch_pipe<N, 0, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
-  if (b.geo == 1) return launch_pipe<N, 1, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
-  return launch_pipe<N, 2, MODE_RK, E>(M, b, q, out, g, stage, write_tr, s);
+  if (b.geo == 0) return launch_pipe<N, 0, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+  if (b.geo == 1) return launch_pipe<N, 1, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+  return launch_pipe<N, 2, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
 }
 
 int tile_epb32(int N, int alt) {
@@ -1486,8 +1541,10 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
   if (b.count == 0) return cudaSuccess;
   if (!b.boff || !b.btr || !b.blink || !b.bflag || !b.bmeta) return cudaErrorInvalidValue;
   DG32_DISPATCH_N(b.N, {
-    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value>(M, b, q, out, g, mode, stage, write_tr, s);
-    return launch_inv_shape<NN, Shape<NN>::EPB>(M, b, q, out, g, mode, stage, write_tr, s);
+    // the split form is built for the default tile shape only
+    if (M.split == 1) return launch_inv_shape<NN, Shape<NN>::EPB, true>(M, b, q, out, g, mode, stage, write_tr, s);
+    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value, false>(M, b, q, out, g, mode, stage, write_tr, s);
+    return launch_inv_shape<NN, Shape<NN>::EPB, false>(M, b, q, out, g, mode, stage, write_tr, s);
   });
   return cudaSuccess;
 }

@@ -40,7 +40,8 @@ class MeshDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
                 ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
+                ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
 
 
 _lock = threading.Lock()
@@ -104,6 +105,8 @@ def make_params(p: dict, precision=0) -> Params:
     out.closure, out.riemann = int(p.get("closure", 0)), int(p.get("riemann", 0))
     out.precision = PRECISION.get(precision, precision) if isinstance(precision, str) else int(precision)
     out.mixed_face = int(p.get("mixed_face", 0))
+    out.split = int(p.get("split", 0))
+    out.reserved = 0
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
     return out

@@ -125,6 +125,38 @@ def test_one_sided_mixed_face():
     _assert_parity(R2, R2_ref)
 
 
+@pytest.mark.parametrize("rotated", [False, True])
+def test_kep_split_form(rotated):
+    # the kinetic-energy-preserving split form: curved mesh with mortars (orders 2..6) and
+    # mixed flags, optionally with every element re-oriented
+    w = wl.padapt_32x32x32(n=4)
+    if rotated:
+        mesh, _ = wl.rotate_elements(w.mesh, 19)
+        w = dataclasses.replace(w, mesh=mesh)
+    w = small_mixed(w, seed=17, orders=(2, 6))
+    p = dict(w.params, nu=1e-2, split=1)
+    R, R_ref, M, S, q = _residual_pair(w, params=p)
+    _assert_parity(R, R_ref)
+    assert rel_l2(R_ref, oracle_mesh(w, dict(p, split=0)).residual(q)) > 1e-6  # differs from the standard form
+
+
+def test_kep_box_and_rk_steps():
+    ww = wl.wake_16x16x16_n4(n=8)
+    R, R_ref, *_ = _residual_pair(ww, params=dict(ww.params, split=1))
+    _assert_parity(R, R_ref)
+    w = wl.tgv_4x4x4_n3()
+    p = dict(w.params, split=1)
+    M = oracle_mesh(w, p)
+    q = oracle_state(w, M)
+    q0 = q.copy()
+    g = np.zeros_like(q)
+    qd, gd = to_dev(q), to_dev(g)
+    S = gpu_solver(w, params=p)
+    S.rk_step(qd, gd, w.dt, w.steps)
+    M.rk_step(q, g, w.dt, w.steps)
+    assert rel_l2(qd.cpu().numpy() - q0, q - q0) <= 1e-10
+
+
 def test_padapt_scaled():
     w = wl.padapt_32x32x32(n=6)
     R, R_ref, *_ = _residual_pair(w)

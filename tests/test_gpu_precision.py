@@ -23,6 +23,7 @@ BOUNDS = {
     "tgv_5x5x5_n6_vreman_llf": 3e-4, "tgv_5x5x5_n7_vreman_llf": 3e-4,
     "tgv_4x4x4_n3_rk3_10_steps_update": 7e-6, "mixed_64x64x64_n4_sampled": 1e-4,
     "tgv_5x5x5_rotated_affine_mixed_orders": 1e-4, "padapt_5x5x5_one_sided_mixed_face": 5e-5,
+    "padapt_5x5x5_kep": 5e-5, "wake_8x8x8_n4_kep": 1e-6,
 }
 
 
@@ -87,6 +88,17 @@ def test_fp32_one_sided_mixed_face():
     err = _fp32_error(w, params=dict(w.params, nu=1e-2, mixed_face=1))
     _record("padapt_5x5x5_one_sided_mixed_face", err)
     assert err <= BOUNDS["padapt_5x5x5_one_sided_mixed_face"]
+
+
+def test_fp32_kep_split_form():
+    w = small_mixed(wl.padapt_32x32x32(n=5), seed=15, orders=(2, 5))
+    err = _fp32_error(w, params=dict(w.params, nu=1e-2, split=1))
+    _record("padapt_5x5x5_kep", err)
+    assert err <= BOUNDS["padapt_5x5x5_kep"]
+    ww = wl.wake_16x16x16_n4(n=8)
+    err = _fp32_error(ww, params=dict(ww.params, split=1))
+    _record("wake_8x8x8_n4_kep", err)
+    assert err <= BOUNDS["wake_8x8x8_n4_kep"]
 
 
 def test_fp32_rk3_ten_steps():
