@@ -41,7 +41,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_64x64x64_n4")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3"],
                     help="fp32: FP32 arithmetic with FP64 state and FP64 accumulation of q (the large "
                          "mixed configuration's precision); fp64: FP64 throughout")
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
@@ -308,7 +308,7 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3"}[args.precision], "data": "synthetic",
            "config": {"workload": w.name, "n_elem": int(w.n_elem), "order": int(w.orders.max()), "dof": int(dof),
                       "ns_fraction": w.ns_fraction, "precision": args.precision, "stages_per_step": 3,
                       "state": "FP64 q, g resident in HBM; FP64 RK accumulation",

@@ -83,7 +83,10 @@ typedef struct {
   int closure;      /* 0 Smagorinsky, 1 Vreman                                         */
   int riemann;      /* 0 Roe, 1 local Lax-Friedrichs                                   */
   int precision;    /* 0 FP64 throughout; 1 FP32 element/face arithmetic with FP64 state,
-                       traces and Runge-Kutta accumulation                              */
+                       traces and Runge-Kutta accumulation; 2 as 1, with the inviscid
+                       volume term's D contractions on the tensor cores in 3xTF32 (each
+                       FP32 operand split into two TF32 parts, big*big + big*small +
+                       small*big accumulated in FP32; the split form keeps FP32 FMAs)   */
   int mixed_face;   /* viscous flux on a face between an NS and an Euler element (Sec. 2.3
                        asks only that it be single-valued): 0 the average of the NS side's
                        flux and zero (BR1 with an inviscid side), 1 the NS side's flux

@@ -312,7 +312,7 @@ dg_status check_params(const dg_params* p) {
     return fail(DG_ERR_ARG, "need c0sq > 0 and nu, cs, cv >= 0");
   if (p->closure < 0 || p->closure > 1) return fail(DG_ERR_ARG, "closure must be 0 or 1");
   if (p->riemann < 0 || p->riemann > 1) return fail(DG_ERR_ARG, "riemann must be 0 or 1");
-  if (p->precision < 0 || p->precision > 1) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
+  if (p->precision < 0 || p->precision > 2) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
   if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
   if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
   if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
@@ -328,7 +328,10 @@ void apply_params(dg_ctx* c) {
   c->M.riemann = c->prm.riemann;
   c->M.mixed_face = c->prm.mixed_face;
   c->M.split = c->prm.split;
-  c->M.precision = c->prm.precision;
+  // precision 2 is the FP32 path (same data layout) with the inviscid volume contraction on
+  // the tensor cores
+  c->M.precision = c->prm.precision >= 1 ? 1 : 0;
+  c->M.tc = c->prm.precision == 2 ? 1 : 0;
   c->M.nu32 = (float)c->prm.nu;
   c->M.c0sq32 = (float)c->prm.c0sq;
   c->M.cs32 = (float)c->prm.cs;
@@ -826,7 +829,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
     case 0:
       if (mode == MODE_RK && stage > 0) break;
       for (const Bucket& b : c->ord_buckets) {
-        CU(launch_traces(M, b, q, c->prm.precision, s));
+        CU(launch_traces(M, b, q, M.precision, s));
         ++nl;
       }
       break;
@@ -838,7 +841,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       break;
     case 2:
       for (const Bucket& b : c->ns_buckets) {
-        CU(launch_viscous(M, b, q, c->prm.precision, s));
+        CU(launch_viscous(M, b, q, M.precision, s));
         ++nl;
       }
       break;
@@ -850,7 +853,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       break;
     default:
       for (const Bucket& b : c->all_buckets) {
-        CU(launch_inviscid(M, b, q, out, g, mode, stage, dt, write_tr, c->prm.precision, s));
+        CU(launch_inviscid(M, b, q, out, g, mode, stage, dt, write_tr, M.precision, s));
         ++nl;
       }
   }
@@ -1247,7 +1250,7 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
     if (report && report_len > 0) std::snprintf(report, (size_t)report_len, "%s", rep.c_str());
   };
   CU(cudaSetDevice(c->device));
-  if (c->prm.precision != 1) {
+  if (c->M.precision != 1) {
     rep = "precision 0: the FP64 passes have no launch choices\n";
     give_report();
     return DG_OK;
@@ -1413,7 +1416,7 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
   // Mean over the three stages of one RK step. State q is FP64 (8 B); traces are 8 B per
   // value (FP64, or an FP32 hi/lo pair); with precision 1 the RK register g, the viscous
   // traces and the viscous divergence are FP32 (4 B).
-  const bool f32 = c->prm.precision == 1;
+  const bool f32 = c->M.precision == 1;
   const double d = 8.0, sg = f32 ? 4.0 : 8.0, sv = f32 ? 4.0 : 8.0, tr = 8.0;
   double b[DG_NPHASES] = {0, 0, 0, 0, 0};
   for (int64_t e = 0; e < c->ne; ++e) {

@@ -452,7 +452,7 @@ struct AltEPB {
   static constexpr int value = N <= 4 ? Shape<N>::EPB / 2 : (N <= 6 ? 2 : Shape<N>::EPB);
 };
 
-template <int N, int E = Shape<N>::EPB, bool KEPC = false>
+template <int N, int E = Shape<N>::EPB, bool KEPC = false, bool TCX = false>
 struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
@@ -465,8 +465,10 @@ struct TmaSmem32 {
   // work per element: F [3 n3] flux deviations, QH/QL [n3] hi/lo state, T [6 n2] face terms
   // (split form on curved elements: F holds the state deviations and the three metric vectors,
   // 4 n3 float4, so everything after it moves by 16 n3)
+  // (tensor-core contraction: C [3][n3] float4, the three directions' D contractions, after T)
   static constexpr int FB = KEPC ? 64 * n3 : 48 * n3;
-  static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, work_elem = FB + 32 * n3 + 96 * n2;
+  static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, wC = FB + 32 * n3 + 96 * n2,
+                       work_elem = wC + (TCX ? 48 * n3 : 0);
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
 };
@@ -595,6 +597,25 @@ __device__ __forceinline__ bool vtma_item(const DevMesh& M, const double* q, con
   slot = P::iEC;
   sh_index = -1;
   return true;
+}
+
+// TF32 (tensor-core input) split of an FP32 value with integer instructions (conversions to
+// TF32 run on a slow pipe): big = x rounded to 10 mantissa bits (half away from zero, by adding
+// half a TF32 unit to the bit pattern and clearing the 13 low bits), small = x - big (exact in
+// FP32) truncated to TF32, so big + small = x to 2^-21 relative.
+__device__ __forceinline__ void tf32_split(float x, unsigned& big, unsigned& small) {
+  big = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  small = __float_as_uint(x - __uint_as_float(big)) & 0xffffe000u;
+}
+
+// D += A B for one 16x8x8 TF32 tile (A row-major 16x8, B column-major 8x8, FP32 accumulators);
+// fragment ownership as the PTX ISA defines it for m16n8k8 with .tf32 operands.
+__device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 // The records of one tile, held in the producer warp's registers between the time they are
@@ -738,11 +759,19 @@ struct InvMinBlocks {
 // of the size of the deviations, and sum_d sum_m 2 D_im F#(q_r, q_r) = f(q_r) . sum_d (D_d Ja^d)
 // vanishes by the discrete metric identities. Shared memory then holds the deviations dq (and,
 // on curved elements, the metric vectors Ja^d) instead of the contravariant fluxes.
-template <int N, int GEO, int MODE, int E, bool KEP>
+//
+// VOL = 2: the standard volume term with the D contractions on the tensor cores in 3xTF32.
+// Along direction d, C[(line, v), i] = sum_m F[(line, v), m] D[i][m] is a 16x8x8 TF32 tile
+// product per 16 (line, variable) rows (m and i padded from n to 8 with zeros); each FP32
+// operand is split into big + small TF32 parts and C accumulates big*big + big*small +
+// small*big in FP32. Consumer warps take the (element, direction, row tile) items in turn and
+// store C per direction; after the face phase each node sums its three directions.
+template <int N, int GEO, int MODE, int E, int VOL>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
+  constexpr bool KEP = VOL == 1, TC = VOL == 2;
   using S = Tile<N, E>;
-  using P = TmaSmem32<N, E, KEP && GEO == 2>;
+  using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   extern __shared__ __align__(128) char smc[];
   void* bar0 = smc + P::oBAR;        // full[0]
@@ -907,7 +936,9 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     float JR[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
       const int str[3] = {1, n, n2};
-      if (!KEP) {
+      if (TC) {
+        // done below by the tensor-core items; the node sums follow the face phase
+      } else if (!KEP) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const int bs = p - ii[d] * str[d];
@@ -959,6 +990,51 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
+    }
+    if (TC) {
+      // tensor-core items: (element, direction, 16-row tile), rows r = 4 line + v
+      constexpr int R = 4 * n2, TR = (R + 15) / 16, ITEMS = EPB * 3 * TR;
+      const int lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+      for (int item = tid >> 5; item < ITEMS; item += NC / 32) {
+        const int le2 = item / (3 * TR), rem = item % (3 * TR), d = rem / TR, rt = rem % TR;
+        if (tile * EPB + le2 >= B.count) continue;
+        const float* Fs = reinterpret_cast<const float*>(W + le2 * P::work_elem + P::wF) + d * n3 * 4;
+        float4* Cd = reinterpret_cast<float4*>(W + le2 * P::work_elem + P::wC) + d * n3;
+        // node of (line, position m) along direction d: base(line) + m * stride, line = a + n b
+        // over the other two indices; this lane's rows are r0 = 16 rt + gq and r0 + 8, i.e.
+        // lines l0 = r0 / 4 and l0 + 2 with variable v = gq % 4
+        const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
+        auto base_of = [&](int line) {
+          const int a = line % n, b = line / n;
+          return d == 0 ? n * (a + n * b) : (d == 1 ? a + n2 * b : a + n * b);
+        };
+        const int r0 = rt * 16 + gq, v = gq & 3;
+        const bool ok0 = r0 < R, ok1 = r0 + 8 < R;
+        const int b0 = ok0 ? base_of(r0 >> 2) : 0, b1 = ok1 ? base_of((r0 + 8) >> 2) : 0;
+        unsigned ab[4], as[4], bb[2], bs[2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int m = tq + ((k & 2) ? 4 : 0);
+          const bool ok = ((k & 1) ? ok1 : ok0) && m < n;
+          const float x = ok ? Fs[((k & 1) ? b1 : b0) * 4 + m * stride * 4 + v] : 0.f;
+          tf32_split(x, ab[k], as[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int m = tq + 4 * k;  // B[k = m][column = i = gq] = D[i][m]
+          tf32_split((m < n && gq < n) ? sD[gq * n + m] : 0.f, bb[k], bs[k]);
+        }
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(c, as, bb);
+        mma_tf32(c, ab, bs);
+        mma_tf32(c, ab, bb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = 2 * tq + (k & 1);
+          const bool ok = ((k & 2) ? ok1 : ok0) && i < n;
+          if (ok) reinterpret_cast<float*>(Cd)[(((k & 2) ? b1 : b0) + i * stride) * 4 + v] = c[k];
+        }
+      }
     }
     // no barrier: the face phase reads QH/QL and the input buffer and writes T, none of which
     // the contraction touches
@@ -1080,6 +1156,17 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     }
     consumer_sync(NC);
     // ---- assembly and update ------------------------------------------------------------
+    if (TC && active) {
+      const float4* Cp = reinterpret_cast<const float4*>(W + le * P::work_elem + P::wC);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float4 c4 = Cp[d * n3 + p];
+        JR[0] -= c4.x;
+        JR[1] -= c4.y;
+        JR[2] -= c4.z;
+        JR[3] -= c4.w;
+      }
+    }
     if (active) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -1382,16 +1469,16 @@ static size_t visc_smem32() {
   return ViscSmem32<N, GEO>::bytes;
 }
 
-template <int N, int E, bool KEP>
+template <int N, int E, int VOL>
 static cudaError_t prep_inv() {
-  const int ps = (int)TmaSmem32<N, E>::bytes, pc = (int)TmaSmem32<N, E, KEP>::bytes;
+  const int ps = (int)TmaSmem32<N, E, false, VOL == 2>::bytes, pc = (int)TmaSmem32<N, E, VOL == 1, VOL == 2>::bytes;
   cudaError_t r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
-  return cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK, E, KEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc);
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RESIDUAL, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RESIDUAL, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 1, MODE_RK, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  return cudaFuncSetAttribute(k_inviscid32t<N, 2, MODE_RK, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc);
 }
 
 template <int N>
@@ -1406,9 +1493,10 @@ static cudaError_t prep32_n() {
   const int vs = (int)ViscTmaSmem32<N>::bytes;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
-  if ((r = prep_inv<N, Shape<N>::EPB, false>()) != cudaSuccess) return r;
-  if ((r = prep_inv<N, Shape<N>::EPB, true>()) != cudaSuccess) return r;
-  return prep_inv<N, AltEPB<N>::value, false>();
+  if ((r = prep_inv<N, Shape<N>::EPB, 0>()) != cudaSuccess) return r;
+  if ((r = prep_inv<N, Shape<N>::EPB, 1>()) != cudaSuccess) return r;
+  if ((r = prep_inv<N, Shape<N>::EPB, 2>()) != cudaSuccess) return r;
+  return prep_inv<N, AltEPB<N>::value, 0>();
 }
 
 cudaError_t prepare_kernels32() {
@@ -1489,13 +1577,13 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
 
 // grid of the persistent kernel: every resident block slot of the GPU (or b.bps blocks per SM
 // when the autotuner chose fewer), at most one per tile
-template <int N, int GEO, int MODE, int E, bool KEP>
+template <int N, int GEO, int MODE, int E, int VOL>
 static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                int stage, int write_tr, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
-  const size_t sm = TmaSmem32<N, E, KEP && GEO == 2>::bytes;
+  const size_t sm = TmaSmem32<N, E, VOL == 1 && GEO == 2, VOL == 2>::bytes;
   if (per_sm < 0) {
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E, KEP>,
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E, VOL>,
                                                                   Tile<N, E>::threads + 32, sm);
     if (r != cudaSuccess) return r;
     int dev = 0;
@@ -1506,21 +1594,21 @@ static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* 
   const int ntiles = (b.count + E - 1) / E;
   const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
   const int grid = ntiles < bps * sms ? ntiles : bps * sms;
-  k_inviscid32t<N, GEO, MODE, E, KEP><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
+  k_inviscid32t<N, GEO, MODE, E, VOL><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
   return cudaGetLastError();
 }
 
-template <int N, int E, bool KEP>
+template <int N, int E, int VOL>
 static cudaError_t launch_inv_shape(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                    int mode, int stage, int write_tr, cudaStream_t s) {
   if (mode == MODE_RESIDUAL) {
-    if (b.geo == 0) return launch_pipe<N, 0, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
-    if (b.geo == 1) return launch_pipe<N, 1, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
-    return launch_pipe<N, 2, MODE_RESIDUAL, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+    if (b.geo == 0) return launch_pipe<N, 0, MODE_RESIDUAL, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+    if (b.geo == 1) return launch_pipe<N, 1, MODE_RESIDUAL, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+    return launch_pipe<N, 2, MODE_RESIDUAL, E, VOL>(M, b, q, out, g, stage, write_tr, s);
   }
-  if (b.geo == 0) return launch_pipe<N, 0, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
-  if (b.geo == 1) return launch_pipe<N, 1, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
-  return launch_pipe<N, 2, MODE_RK, E, KEP>(M, b, q, out, g, stage, write_tr, s);
+  if (b.geo == 0) return launch_pipe<N, 0, MODE_RK, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+  if (b.geo == 1) return launch_pipe<N, 1, MODE_RK, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+  return launch_pipe<N, 2, MODE_RK, E, VOL>(M, b, q, out, g, stage, write_tr, s);
 }
 
 int tile_epb32(int N, int alt) {
@@ -1541,10 +1629,12 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
   if (b.count == 0) return cudaSuccess;
   if (!b.boff || !b.btr || !b.blink || !b.bflag || !b.bmeta) return cudaErrorInvalidValue;
   DG32_DISPATCH_N(b.N, {
-    // the split form is built for the default tile shape only
-    if (M.split == 1) return launch_inv_shape<NN, Shape<NN>::EPB, true>(M, b, q, out, g, mode, stage, write_tr, s);
-    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value, false>(M, b, q, out, g, mode, stage, write_tr, s);
-    return launch_inv_shape<NN, Shape<NN>::EPB, false>(M, b, q, out, g, mode, stage, write_tr, s);
+    // the split form and the tensor-core contraction are built for the default tile shape; the
+    // split form's two-point sums are no plain contraction and stay on the FP32 pipe
+    if (M.split == 1) return launch_inv_shape<NN, Shape<NN>::EPB, 1>(M, b, q, out, g, mode, stage, write_tr, s);
+    if (M.tc) return launch_inv_shape<NN, Shape<NN>::EPB, 2>(M, b, q, out, g, mode, stage, write_tr, s);
+    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value, 0>(M, b, q, out, g, mode, stage, write_tr, s);
+    return launch_inv_shape<NN, Shape<NN>::EPB, 0>(M, b, q, out, g, mode, stage, write_tr, s);
   });
   return cudaSuccess;
 }

@@ -42,11 +42,11 @@ def _record(name, err):
             f.write(json.dumps({"case": name, "rel_l2": err}) + "\n")
 
 
-def _fp32_error(w, params=None):
+def _fp32_error(w, params=None, precision=1):
     M = oracle_mesh(w, params)
     q = oracle_state(w, M)
     R_ref = M.residual(q)
-    S = gpu_solver(w, precision=1, params=params)
+    S = gpu_solver(w, precision=precision, params=params)
     R = S.residual(to_dev(q)).cpu().numpy()
     return rel_l2(R, R_ref)
 
@@ -99,6 +99,48 @@ def test_fp32_kep_split_form():
     err = _fp32_error(ww, params=dict(ww.params, split=1))
     _record("wake_8x8x8_n4_kep", err)
     assert err <= BOUNDS["wake_8x8x8_n4_kep"]
+
+
+@pytest.mark.parametrize("name,make", [
+    ("tgv_8x8x8_n5_slab30", lambda: wl.tgv_32x32x32_n5(n=8)),
+    ("wake_16x16x16_n4", lambda: wl.wake_16x16x16_n4()),
+    ("padapt_6x6x6_curved", lambda: wl.padapt_32x32x32(n=6)),
+])
+def test_tf32x3_tensor_core_contraction(name, make):
+    # precision 2: the inviscid D contractions on the tensor cores in 3xTF32. Its error against
+    # the FP64 oracle is reported like the FP32 path's, and it differs from the FP32-FMA path
+    # by no more than FP32 rounding does (both amplified by the residual's conditioning)
+    w = make()
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    R_ref = M.residual(q)
+    qd = to_dev(q)
+    R_tc = gpu_solver(w, precision=2).residual(qd).cpu().numpy()
+    R_32 = gpu_solver(w, precision=1).residual(qd).cpu().numpy()
+    err = rel_l2(R_tc, R_ref)
+    _record(name + "_tf32x3", err)
+    assert err <= 1.5 * BOUNDS[name], err
+    assert rel_l2(R_tc, R_32) <= 1e-6 + 2.0 * rel_l2(R_32, R_ref), rel_l2(R_tc, R_32)
+
+
+def test_tf32x3_every_order_rk_steps():
+    for N in (1, 2, 3, 6, 7):
+        w = small_mixed(wl.tgv_4x4x4_n3(n_elem_dir=5, order=N), seed=30 + N)
+        p = dict(w.params, nu=1e-2)
+        err = _fp32_error(w, params=p, precision=2)
+        _record(f"tgv_5x5x5_n{N}_tf32x3", err)
+        assert err <= 3e-4, (N, err)
+    w = wl.tgv_4x4x4_n3()
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    q0 = q.copy()
+    g = np.zeros_like(q)
+    qd, gd = to_dev(q), to_dev(g)
+    gpu_solver(w, precision=2).rk_step(qd, gd, w.dt, w.steps)
+    M.rk_step(q, g, w.dt, w.steps)
+    err = rel_l2(qd.cpu().numpy() - q0, q - q0)
+    _record("tgv_4x4x4_n3_rk3_10_steps_update_tf32x3", err)
+    assert err <= 1.5 * BOUNDS["tgv_4x4x4_n3_rk3_10_steps_update"]
 
 
 def test_fp32_rk3_ten_steps():
