@@ -156,6 +156,29 @@ def project(Nh, Nl):
     return P
 
 
+def project_state(orders_old, orders_new, q_old):
+    """The state re-laid out for new per-element orders (Sec. 3.2, re-assigning orders):
+    element by element, Lagrange interpolation onto the new Gauss-Lobatto nodes where the order
+    grows or stays, the L2 projection (in reference coordinates) where it drops, applied along
+    each of the three directions. q_old: [4][sum (N_old + 1)^3]; returns [4][sum (N_new + 1)^3]."""
+    orders_old = np.asarray(orders_old, dtype=np.int64)
+    orders_new = np.asarray(orders_new, dtype=np.int64)
+    off_o = np.concatenate([[0], np.cumsum((orders_old + 1) ** 3)])
+    off_n = np.concatenate([[0], np.cumsum((orders_new + 1) ** 3)])
+    q_new = np.zeros((4, off_n[-1]))
+    ops = {}
+    for e in range(len(orders_old)):
+        No, Nn = int(orders_old[e]), int(orders_new[e])
+        if (No, Nn) not in ops:
+            ops[No, Nn] = interp(No, Nn) if Nn >= No else project(No, Nn)
+        T = ops[No, Nn]
+        no, nn = No + 1, Nn + 1
+        A = q_old[:, off_o[e]:off_o[e + 1]].reshape(4, no, no, no)  # [v][k][j][i], i fastest
+        B = np.einsum('Ia,Jb,Kc,vcba->vKJI', T, T, T, A)
+        q_new[:, off_n[e]:off_n[e + 1]] = B.reshape(4, -1)
+    return q_new
+
+
 # ---- pointwise -----------------------------------------------------------------------
 
 def normal_flux(q, n, c0sq):
