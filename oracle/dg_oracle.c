@@ -522,6 +522,11 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const or_real* gxyz, c
       m->nb_f[e * 6 + f] = -1;
       m->nb_o[e * 6 + f] = 0;
       m->bc[e * 6 + f] = bc_tag ? bc_tag[e * 6 + f] : -1;
+      if (m->bc[e * 6 + f] == 0 || m->bc[e * 6 + f] < -1 || m->bc[e * 6 + f] > 4) {
+        set_err("element %lld face %d: boundary tag %d invalid", (long long)e, f, m->bc[e * 6 + f]);
+        or_destroy(m);
+        return NULL;
+      }
     }
   }
   m->total = m->off[ne];
@@ -815,13 +820,20 @@ static void face_fv(const work_t* W, int64_t e, int f, or_real* Fv /*[3][n2]*/) 
   free(S);
 }
 
-static void ghost_state(const or_mesh* m, int tag, const or_real* qin, or_real* qg) {
+/* ghost state behind a boundary face with area-weighted outward normal S */
+static void ghost_state(const or_mesh* m, int tag, const or_real* qin, const or_real S[3], or_real* qg) {
+  qg[0] = qin[0];
   if (tag == 1) { /* inflow: prescribed velocity, interior pressure */
-    qg[0] = qin[0];
     for (int c = 0; c < 3; ++c) qg[1 + c] = m->p.inflow[1 + c];
-  } else { /* outflow: interior velocity, zero pressure */
+  } else if (tag == 2) { /* outflow: interior velocity, zero pressure */
     qg[0] = 0.0;
     for (int c = 0; c < 3; ++c) qg[1 + c] = qin[1 + c];
+  } else if (tag == 3) { /* no-slip wall: the mirror state with every velocity component reversed */
+    for (int c = 0; c < 3; ++c) qg[1 + c] = -qin[1 + c];
+  } else { /* free-slip wall: the mirror state, normal velocity reversed */
+    const or_real s = SQRT(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    const or_real un = (qin[1] * S[0] + qin[2] * S[1] + qin[3] * S[2]) / s;
+    for (int c = 0; c < 3; ++c) qg[1 + c] = qin[1 + c] - 2.0 * un * S[c] / s;
   }
 }
 
@@ -907,7 +919,8 @@ static void mortar_build(const work_t* W, int64_t e, int f, mortar_t* mt) {
     for (int p = 0; p < nM2; ++p) {
       or_real qi[4], qg[4];
       for (int v = 0; v < 4; ++v) qi[v] = mt->qm[v * nM2 + p];
-      ghost_state(m, mt->tag, qi, qg);
+      const or_real Sp[3] = {mt->S[p], mt->S[nM2 + p], mt->S[2 * nM2 + p]};
+      ghost_state(m, mt->tag, qi, Sp, qg);
       for (int v = 0; v < 4; ++v) mt->qp[v * nM2 + p] = qg[v];
     }
   }
@@ -952,8 +965,18 @@ static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
       face_fv(W, mt.nbr, mt.nf, tn);
       nbr_to_mortar(m->N[mt.nbr], mt.M, mt.no, 3, tn, Fvp);
       free(tn);
+    } else if (mt.tag == 4) {
+      /* free-slip wall: the mirror ghost's outward viscous flux is R Fvm, R = I - 2 n n^T the
+       * reflection, so the BR1 average keeps only the normal part of the traction */
+      for (int p = 0; p < nM2; ++p) {
+        const or_real S[3] = {mt.S[p], mt.S[nM2 + p], mt.S[2 * nM2 + p]};
+        const or_real ss = S[0] * S[0] + S[1] * S[1] + S[2] * S[2];
+        const or_real fn = (Fvm[p] * S[0] + Fvm[nM2 + p] * S[1] + Fvm[2 * nM2 + p] * S[2]) / ss;
+        for (int c = 0; c < 3; ++c) Fvp[c * nM2 + p] = Fvm[c * nM2 + p] - 2.0 * fn * S[c];
+      }
     } else {
-      /* boundary: the ghost carries the interior viscous flux, pointing the other way */
+      /* inflow, outflow and no-slip wall: the interior viscous flux (at a no-slip wall the
+       * interior traction) -- the ghost carries it, pointing the other way */
       for (int i = 0; i < 3 * nM2; ++i) Fvp[i] = -Fvm[i];
     }
   }

@@ -622,3 +622,80 @@ def test_project_state_round_trip_and_element_integrals():
     for e in range(E):
         wh, wl3 = [np.einsum('i,j,k->kji', *(orc.lgl(int(N))[1],) * 3).ravel() for N in (o_hi[e], o_lo[e])]
         np.testing.assert_allclose(ql[:, ol[e]:ol[e + 1]] @ wl3, qh[:, oh[e]:oh[e + 1]] @ wh, rtol=1e-12, atol=1e-12)
+
+
+# ---- walls (bc tags 3 no-slip, 4 free-slip) ---------------------------------------------------
+
+def _channel(ny, y0, H, tags, N=3):
+    n = 3
+    xb = np.linspace(0, 2 * np.pi, n + 1)
+    yb = np.linspace(y0, y0 + H, ny + 1)
+    periodic = tags is None
+    m = wl.box_mesh(n, ny, n, xb, yb, xb, periodic=(True, periodic, True), bc_x=tags or (1, 2))
+    return m, np.full(n * ny * n, N, np.int8)
+
+
+def _mirror_residuals(tag, state, flags_value):
+    H = 2.0
+    mw, ow = _channel(3, 0.0, H, (tag, tag))      # [0, H] between two walls
+    mp, op = _channel(6, -H, 2 * H, None)          # [-H, H], periodic: the mirror extension
+    prm = orc.params(nu=1e-2, c0sq=25.0, cs=0.1)
+    Aw = orc.Mesh(mw.hex, mw.geom, 1, ow, np.full(len(ow), flags_value, np.uint8), prm, mw.bc_tag)
+    Ap = orc.Mesh(mp.hex, mp.geom, 1, op, np.full(len(op), flags_value, np.uint8), prm, mp.bc_tag)
+    Rw = Aw.residual(state(Aw.node_coords(), H))
+    Rp = Ap.residual(state(Ap.node_coords(), H))
+    # element (i, j, k) of the wall mesh is element (i, j + 3, k) of the periodic one
+    out_w, out_p = [], []
+    for e in range(len(ow)):
+        i, j, k = e % 3, (e // 3) % 3, e // 9
+        ep = i + 3 * ((j + 3) + 6 * k)
+        out_w.append(Rw[:, Aw.element_nodes(e)])
+        out_p.append(Rp[:, Ap.element_nodes(ep)])
+    return np.concatenate(out_w, axis=1), np.concatenate(out_p, axis=1)
+
+
+@pytest.mark.parametrize("flags_value", [0, 1])
+def test_free_slip_wall_is_a_mirror(flags_value):
+    # p, u, w even and v odd about y = 0 (and, with period 2H, about y = H): the periodic
+    # residual of the extended field restricted to [0, H] is the residual between free-slip walls
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        return np.stack([c * (0.3 + 0.1 * np.sin(x[0])), 1.0 + 0.2 * c * np.sin(x[2]), 0.3 * s * np.cos(x[0]),
+                         0.2 * c * np.cos(x[0]) + 0.1 * np.cos(2 * np.pi * x[1] / H)])
+    Rw, Rp = _mirror_residuals(4, state, flags_value)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+def test_no_slip_wall_is_an_antimirror_for_euler():
+    # convective terms: p even and every velocity component odd about the walls
+    flags_value = 0
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        return np.stack([c * (0.2 + 0.1 * np.cos(x[0])), s * (1.0 + 0.1 * np.cos(x[2])),
+                         0.2 * np.sin(2 * np.pi * x[1] / H) * np.cos(x[0]), 0.3 * s * np.sin(x[0])])
+    Rw, Rp = _mirror_residuals(3, state, flags_value)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+def test_free_slip_wall_keeps_a_tangential_free_stream():
+    mw, ow = _channel(3, 0.0, 2.0, (4, 4), N=4)
+    A = orc.Mesh(mw.hex, mw.geom, 1, ow, np.ones(len(ow), np.uint8), orc.params(nu=1e-2), mw.bc_tag)
+    q = np.zeros((4, A.total))
+    q[0], q[1], q[3] = 0.4, 1.0, -0.3
+    assert np.abs(A.residual(q)).max() < 1e-12
+
+
+def test_no_slip_wall_poiseuille_residual_is_exact():
+    # plane Poiseuille profile u = U y (H - y) between no-slip walls, no pressure gradient: the
+    # velocity is quadratic, vanishes on the walls and is divergence-free, so at N >= 2 every
+    # BR1 term is exact and the residual is the continuum one, R_u = nu u'' = -2 nu U, the rest 0
+    H, U, nu = 2.0, 0.7, 0.03
+    mw, ow = _channel(3, 0.0, H, (3, 3), N=3)
+    A = orc.Mesh(mw.hex, mw.geom, 1, ow, np.ones(len(ow), np.uint8), orc.params(nu=nu, cs=0.0), mw.bc_tag)
+    x = A.node_coords()
+    q = np.zeros((4, A.total))
+    q[0] = 0.25
+    q[1] = U * x[1] * (H - x[1])
+    R = A.residual(q)
+    np.testing.assert_allclose(R[1], -2.0 * nu * U, rtol=0, atol=1e-12)
+    assert np.abs(R[[0, 2, 3]]).max() < 1e-12
