@@ -273,6 +273,9 @@ struct dg_ctx {
   // autotuned launch choices of the reduced-precision passes, key (pass, N, geometry kind) with
   // pass 0 inviscid, 1 viscous; value (tile_alt, bps, visc_alt)
   std::map<std::array<int, 3>, std::array<int, 3>> tuning;
+  // orders and node offsets before the last successful dg_set_orders (for dg_project_state)
+  std::vector<int8_t> prev_order;
+  std::vector<int64_t> prev_off;
 };
 
 namespace {
@@ -1022,6 +1025,7 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
       return fail(DG_ERR_ARG, "element %lld: order %d outside %d..%d", (long long)e, orders[e], std::max(1, c->gdeg), MAXN);
   CU(cudaSetDevice(c->device));
   std::vector<int8_t> old = c->order;
+  std::vector<int64_t> old_off = c->off;
   c->order.assign(orders, orders + c->ne);
   dg_status st = rebuild_orders(c);
   if (st != DG_OK) {
@@ -1029,8 +1033,25 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
     std::string msg = g_last_error;
     rebuild_orders(c);
     g_last_error = msg;
+  } else {
+    c->prev_order = std::move(old);
+    c->prev_off = std::move(old_off);
   }
   return st;
+}
+
+dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* stream) {
+  if (!c || !q_old || !q_new) return fail(DG_ERR_ARG, "NULL argument");
+  if (c->prev_order.empty()) return fail(DG_ERR_STATE, "dg_project_state needs a preceding dg_set_orders");
+  if (q_old == q_new) return fail(DG_ERR_ARG, "q_old and q_new must not overlap");
+  CU(cudaSetDevice(c->device));
+  int8_t* dord = nullptr;
+  int64_t* doff = nullptr;
+  dg_status st;
+  if ((st = dev_upload(c, "prev_order", c->prev_order, &dord)) != DG_OK) return st;
+  if ((st = dev_upload(c, "prev_off", c->prev_off, &doff)) != DG_OK) return st;
+  CU(launch_project_state(c->M, dord, doff, c->prev_off.back(), q_old, q_new, (cudaStream_t)stream));
+  return DG_OK;
 }
 
 dg_status dg_set_element_flags(dg_ctx* c, const uint8_t* flags) {

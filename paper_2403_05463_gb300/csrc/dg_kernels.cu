@@ -656,6 +656,52 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
 }
 
 // ---------------------------------------------------------------------------------------
+// state re-projection after a change of orders (Sec. 3.2): one block per element
+// ---------------------------------------------------------------------------------------
+// The element's state at its previous order, re-laid out at its current order by a 1D operator
+// applied along each direction in turn: Lagrange interpolation when the order grows or stays,
+// the L2 projection when it drops. Two shared buffers of 4 n^3 doubles ping-pong between the
+// three passes.
+__global__ void __launch_bounds__(256) k_project_state(DevMesh M, const int8_t* __restrict__ old_order,
+                                                       const int64_t* __restrict__ old_off, int64_t total_old,
+                                                       const double* __restrict__ qo, double* __restrict__ qn) {
+  __shared__ double A[4 * NP * NP * NP], X[4 * NP * NP * NP];
+  const int e = blockIdx.x;
+  const int No = old_order[e], Nn = M.order[e], no = No + 1, nn = Nn + 1;
+  const double* T = Nn >= No ? interp_tab(M, No, Nn) : proj_tab(M, No, Nn);  // T[i * NP + j]: new i, old j
+  const int64_t oo = old_off[e], on = M.elem_off[e];
+  const int no3 = no * no * no;
+  for (int t = threadIdx.x; t < 4 * no3; t += blockDim.x) A[t] = qo[(t / no3) * total_old + oo + t % no3];
+  __syncthreads();
+  // along xi_1: X[v][c][b][I] = sum_a T[I][a] A[v][c][b][a]
+  const int s1 = no * no * nn;
+  for (int t = threadIdx.x; t < 4 * s1; t += blockDim.x) {
+    const int v = t / s1, r = t % s1, I = r % nn, cb = r / nn;
+    double s = 0.0;
+    for (int a = 0; a < no; ++a) s += T[I * NP + a] * A[v * no3 + cb * no + a];
+    X[v * s1 + cb * nn + I] = s;
+  }
+  __syncthreads();
+  // along xi_2: A[v][c][J][I] = sum_b T[J][b] X[v][c][b][I]
+  const int s2 = no * nn * nn;
+  for (int t = threadIdx.x; t < 4 * s2; t += blockDim.x) {
+    const int v = t / s2, r = t % s2, I = r % nn, J = (r / nn) % nn, c = r / (nn * nn);
+    double s = 0.0;
+    for (int b = 0; b < no; ++b) s += T[J * NP + b] * X[v * s1 + (c * no + b) * nn + I];
+    A[v * s2 + (c * nn + J) * nn + I] = s;
+  }
+  __syncthreads();
+  // along xi_3: qn[v][K][J][I] = sum_c T[K][c] A[v][c][J][I]
+  const int nn3 = nn * nn * nn;
+  for (int t = threadIdx.x; t < 4 * nn3; t += blockDim.x) {
+    const int v = t / nn3, r = t % nn3, IJ = r % (nn * nn), K = r / (nn * nn);
+    double s = 0.0;
+    for (int c = 0; c < no; ++c) s += T[K * NP + c] * A[v * s2 + c * nn * nn + IJ];
+    qn[v * M.total + on + r] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // node coordinates and conservation sums (not on the hot path)
 // ---------------------------------------------------------------------------------------
 template <int N>
@@ -811,6 +857,13 @@ cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, 
     return b.curved ? launch_inv64<NN, true, MODE_RK, false>(M, b, q, out, g, stage, dt, write_tr, s)
                     : launch_inv64<NN, false, MODE_RK, false>(M, b, q, out, g, stage, dt, write_tr, s);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_state(const DevMesh& M, const int8_t* old_order, const int64_t* old_off, int64_t total_old,
+                                 const double* qo, double* qn, cudaStream_t s) {
+  if (M.n_elem == 0) return cudaSuccess;
+  k_project_state<<<(unsigned)M.n_elem, 256, 0, s>>>(M, old_order, old_off, total_old, qo, qn);
   return cudaGetLastError();
 }
 

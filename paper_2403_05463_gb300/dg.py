@@ -79,6 +79,7 @@ def load():
         L.dg_conservation.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_conservation_noalloc.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
+        L.dg_project_state.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_check_device.argtypes = [_vp, _vp]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -244,6 +245,15 @@ class Solver:
             raise ValueError("out must hold 4 float64 values")
         _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R"), _dev_ptr(out, "out"),
                                               _stream_handle(stream)))
+
+    def project_state(self, q_old, stream=None):
+        """q_old in the layout before the last set_orders -> a new tensor in the current one
+        (see dg_project_state)."""
+        import torch
+        q_new = torch.empty((4, self.total_nodes), dtype=torch.float64, device=q_old.device)
+        _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old"), _dev_ptr(q_new, "q_new"),
+                                       _stream_handle(stream)))
+        return q_new
 
     def autotune(self, cache_path=None):
         """Time the candidate launch shapes of the reduced-precision passes on this mesh and

@@ -157,6 +157,33 @@ def test_kep_box_and_rk_steps():
     assert rel_l2(qd.cpu().numpy() - q0, q - q0) <= 1e-10
 
 
+def test_project_state_after_order_change():
+    # dynamic p-adaptation: orders re-assigned twice on a curved mesh; the state follows
+    from oracle import oracle as orc
+    import torch
+    w = small_mixed(wl.padapt_32x32x32(n=4), seed=21, orders=(2, 7))
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    S = gpu_solver(w)
+    rng = np.random.default_rng(22)
+    o_prev, q_prev = w.orders.copy(), q
+    qd = to_dev(q)
+    for _ in range(2):
+        o_new = rng.integers(2, 8, size=w.n_elem).astype(np.int8)
+        S.set_orders(o_new)
+        qd = S.project_state(qd)
+        torch.cuda.synchronize()
+        ref = orc.project_state(o_prev, o_new, q_prev)
+        got = qd.cpu().numpy()
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        o_prev, q_prev = o_new, ref
+    # and the residual runs on the re-laid-out state
+    R = S.residual(qd).cpu().numpy()
+    Mn = orc.Mesh(w.mesh.hex, w.mesh.geom, w.mesh.geom_degree, o_prev, w.flags, orc.params(**w.params), w.mesh.bc_tag)
+    _assert_parity(R, Mn.residual(q_prev))
+
+
 def test_padapt_scaled():
     w = wl.padapt_32x32x32(n=6)
     R, R_ref, *_ = _residual_pair(w)
