@@ -70,7 +70,10 @@ typedef struct {
   const double* geom_xyz;
   /* [n_elem][6] boundary tag per local face f = 2 d + s (plane xi_{d+1} = s ? +1 : -1):
    * -1 interior or periodic, 1 inflow (velocity from dg_params.inflow, interior pressure),
-   * 2 outflow (interior velocity, zero pressure). NULL means every face is interior. */
+   * 2 outflow (interior velocity, zero pressure), 3 no-slip wall (mirror ghost with the velocity
+   * reversed; the interior viscous traction), 4 free-slip wall (mirror ghost with the normal
+   * velocity reversed; the BR1 average with the mirror ghost keeps the normal traction).
+   * NULL means every face is interior; any other value is DG_ERR_ARG. */
   const int8_t* bc_tag;
 } dg_mesh_desc;
 

@@ -22,6 +22,29 @@ __host__ __device__ __forceinline__ void visc_face_weights(int mixed_face, bool 
   wn = one ? (own_ns ? 0.f : 1.f) : 0.5f;
 }
 
+// Velocity jump u_ghost - u behind a wall face with area-weighted outward normal S: -2u at a
+// no-slip wall, -2 (u.n) n at a free-slip one.
+template <typename T>
+__device__ __forceinline__ void wall_jump(int kind, const T u[3], const T S[3], T jump[3]) {
+  if (kind == FK_WALL) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) jump[c] = T(-2) * u[c];
+  } else {
+    const T us = (u[0] * S[0] + u[1] * S[1] + u[2] * S[2]) / (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) jump[c] = T(-2) * us * S[c];
+  }
+}
+
+// The viscous face term F_v,own . S - F_v* . S behind a free-slip wall (F_v* keeps only the
+// normal part of the traction): the tangential part of the own outward trace t = tau . S.
+template <typename T>
+__device__ __forceinline__ void slip_visc_term(const T t[3], const T S[3], T out[3]) {
+  const T ts = (t[0] * S[0] + t[1] * S[1] + t[2] * S[2]) / (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = t[c] - ts * S[c];
+}
+
 // volume node of face f = 2d+s at face coordinates (a, b)
 __host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
   int d = f >> 1, fix = (f & 1) ? n - 1 : 0;

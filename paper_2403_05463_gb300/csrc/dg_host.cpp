@@ -616,7 +616,8 @@ dg_status rebuild_flags(dg_ctx* c) {
         }
       } else {
         L.nbr = -1;
-        L.kind = c->bc[e * 6 + f] == 1 ? FK_INFLOW : FK_OUTFLOW;
+        const int tag = c->bc[e * 6 + f];
+        L.kind = tag == 1 ? FK_INFLOW : (tag == 2 ? FK_OUTFLOW : (tag == 3 ? FK_WALL : FK_SLIP));
       }
       link[e * 6 + f] = L;
     }
@@ -909,6 +910,13 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
   c->gnodes.assign(mesh->geom_xyz, mesh->geom_xyz + c->ne * ng3 * 3);
   c->bc.assign(c->ne * 6, -1);
   if (mesh->bc_tag) c->bc.assign(mesh->bc_tag, mesh->bc_tag + c->ne * 6);
+  for (int64_t i = 0; i < c->ne * 6; ++i)
+    if (c->bc[i] == 0 || c->bc[i] < -1 || c->bc[i] > 4) {
+      const int tag = c->bc[i];
+      delete c;
+      return fail(DG_ERR_ARG, "element %lld face %d: boundary tag %d is not -1, 1, 2, 3 or 4", (long long)(i / 6),
+                  (int)(i % 6), tag);
+    }
   c->prm = *params;
   // face matching on sorted corner ids
   c->nb.assign(c->ne * 6, -1);
@@ -936,7 +944,7 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
     }
     if (v.size() == 1) {
       int64_t s = v[0];
-      if (c->bc[s] != 1 && c->bc[s] != 2) {
+      if (c->bc[s] < 1) {
         delete c;
         return fail(DG_ERR_MESH, "element %lld face %d is unmatched and has no boundary tag", (long long)(s / 6),
                     (int)(s % 6));

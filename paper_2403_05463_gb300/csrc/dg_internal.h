@@ -16,6 +16,8 @@ enum FaceKind : uint8_t {
   FK_MORTAR = 1,   // different orders: flux on the mortar of the larger order, projected back
   FK_INFLOW = 2,   // ghost state: prescribed velocity, interior pressure
   FK_OUTFLOW = 3,  // ghost state: interior velocity, zero pressure
+  FK_WALL = 4,     // no-slip wall: mirror ghost with every velocity component reversed
+  FK_SLIP = 5,     // free-slip wall: mirror ghost with the normal velocity reversed
 };
 
 // One entry per (element, local face). Local face f = 2 d + s lies on xi_{d+1} = s ? +1 : -1;

@@ -254,6 +254,9 @@ __global__ void __launch_bounds__(Shape<N>::threads) k_viscous(DevMesh M, const 
         } else if (L.kind == FK_INFLOW) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) jump[c] = M.inflow[1 + c] - u[c];
+        } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+          const double Sd[3] = {Sv[0], Sv[1], Sv[2]};
+          wall_jump<double>(L.kind, u, Sd, jump);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -444,6 +447,13 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       qp[0] = qq[0];
 #pragma unroll
       for (int c = 0; c < 3; ++c) qp[1 + c] = M.inflow[1 + c];
+    } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+      const double uo[3] = {qq[1], qq[2], qq[3]};
+      double jw[3];
+      wall_jump<double>(L.kind, uo, Sv, jw);
+      qp[0] = qq[0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qp[1 + c] = qq[1 + c] + jw[c];
     } else {
       qp[0] = 0.0;
 #pragma unroll
@@ -464,6 +474,12 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         if (L.nflag) t += (double)wn * M.Tv[c * M.tr_total + nsl];
         JR[1 + c] -= invw * t;
       }
+    } else if (L.kind == FK_SLIP && ns) {
+      const double tv[3] = {M.Tv[ms], M.Tv[M.tr_total + ms], M.Tv[2 * M.tr_total + ms]};
+      double tt[3];
+      slip_visc_term<double>(tv, Sv, tt);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) JR[1 + c] -= invw * tt[c];
     }
   }
   if (MODE == MODE_RESIDUAL) {

@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(Shape<N>::threads, MinBlocks32<N>::value)
             split_hilo(M.inflow[1 + c], ih, il);
             jump[c] = (ih - uh[c]) + (il - ul[c]);
           }
+        } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+          const float uo[3] = {uh[0] + ul[0], uh[1] + ul[1], uh[2] + ul[2]};
+          wall_jump<float>(L.kind, uo, Sv, jump);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1120,6 +1123,12 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
             split_hilo(M.inflow[1 + c], ih, il);
             dqf[1 + c] = (ih - qh[1 + c]) + (il - ql[1 + c]);
           }
+        } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+          const float uo[3] = {qh[1] + ql[1], qh[2] + ql[2], qh[3] + ql[3]};
+          float jw[3];
+          wall_jump<float>(L.kind, uo, Sv, jw);
+          dqf[0] = 0.f;
+          dqf[1] = jw[0], dqf[2] = jw[1], dqf[3] = jw[2];
         } else {
           dqf[0] = -(qh[0] + ql[0]);
           dqf[1] = dqf[2] = dqf[3] = 0.f;
@@ -1150,6 +1159,13 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
             if (L.nflag) tv += wn * reinterpret_cast<const float*>(I2 + P::iNV + f * P::SNV + SH2[10 + f])[nab * 3 + c];
             term[1 + c] += tv;
           }
+        } else if (L.kind == FK_SLIP && ns2) {
+          const float* ov = reinterpret_cast<const float*>(I2 + P::iOV + SH2[16]) + (f * n2 + ab) * 3;
+          const float tv[3] = {ov[0], ov[1], ov[2]};
+          float tt[3];
+          slip_visc_term<float>(tv, Sv, tt);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) term[1 + c] += tt[c];
         }
       }
       reinterpret_cast<float4*>(W2 + P::wT)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);
@@ -1393,6 +1409,9 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
               split_hilo(M.inflow[1 + c], ih, il);
               jump[c] = (ih - uh[c]) + (il - ul[c]);
             }
+          } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+            const float uo[3] = {uh[0] + ul[0], uh[1] + ul[1], uh[2] + ul[2]};
+            wall_jump<float>(L.kind, uo, Sv, jump);
           }
 #pragma unroll
           for (int c = 0; c < 3; ++c)

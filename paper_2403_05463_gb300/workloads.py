@@ -451,10 +451,41 @@ def mixed_64x64x64_n4(n=64, order=4, y_wall=0.2, r_wake=0.4, all_ns=False, all_e
                     default_params(nu=1e-4), seed, 2e-4, 100, state)
 
 
+def channel_walls(n=8, order=4, wall=3, wavy=0.08):
+    """Channel between walls at y = 0 and y = 2 (boundary tag 3 no-slip, 4 free-slip), periodic
+    in x and z over 2 pi, Re 1e3; degree-2 geometry with wavy walls y += wavy sin x cos z; NS
+    within 0.5 of either wall, Euler in the core; Poiseuille-like profile plus noise."""
+    seed = 1006
+    b = np.linspace(0, 2 * np.pi, n + 1)
+    yb = np.linspace(0, 2, n + 1)
+
+    def warp(x, y, z):
+        return x, y + wavy * np.sin(x) * np.cos(z), z
+
+    mesh = box_mesh(n, n, n, b, yb, b, periodic=(True, False, True), geom_degree=2, warp=warp,
+                    bc_x=(wall, wall))
+    yc = mesh.centers[:, 1]
+    flags = ((yc < 0.5) | (yc > 1.5)).astype(np.uint8)
+
+    def state(xyz, e, l):
+        q = np.zeros((4, xyz.shape[1]))
+        yy = xyz[1] - wavy * np.sin(xyz[0]) * np.cos(xyz[2])
+        q[1] = 1.5 * yy * (2.0 - yy)
+        q[2] = 0.05 * np.sin(np.pi * yy) * np.cos(xyz[0])
+        q[3] = 0.05 * np.sin(np.pi * yy) * np.sin(xyz[2])
+        for v in (1, 2, 3):
+            q[v] += node_noise(seed, e, l, v, 0.01)
+        return q
+
+    return Workload(f"channel_{n}x{n}x{n}_n{order}_{'noslip' if wall == 3 else 'slip'}", mesh,
+                    np.full(n ** 3, order, np.int8), flags, default_params(nu=1e-3), seed, 1e-3, 10, state)
+
+
 WORKLOADS = {
     "tgv_4x4x4_n3": tgv_4x4x4_n3,
     "wake_16x16x16_n4": wake_16x16x16_n4,
     "tgv_32x32x32_n5": tgv_32x32x32_n5,
     "padapt_32x32x32": padapt_32x32x32,
     "mixed_64x64x64_n4": mixed_64x64x64_n4,
+    "channel_walls": channel_walls,
 }

@@ -184,6 +184,18 @@ def test_project_state_after_order_change():
     _assert_parity(R, Mn.residual(q_prev))
 
 
+@pytest.mark.parametrize("wall", [3, 4])
+def test_walls(wall):
+    # no-slip (3) and free-slip (4) walls on a wavy degree-2 channel, mixed flags and orders,
+    # every element re-oriented
+    w = wl.channel_walls(n=4, wall=wall)
+    mesh, _ = wl.rotate_elements(w.mesh, 31 + wall)
+    w = small_mixed(dataclasses.replace(w, mesh=mesh), seed=32 + wall, orders=(2, 5))
+    p = dict(w.params, nu=1e-2)
+    R, R_ref, *_ = _residual_pair(w, params=p)
+    _assert_parity(R, R_ref)
+
+
 def test_padapt_scaled():
     w = wl.padapt_32x32x32(n=6)
     R, R_ref, *_ = _residual_pair(w)

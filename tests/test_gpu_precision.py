@@ -24,6 +24,7 @@ BOUNDS = {
     "tgv_4x4x4_n3_rk3_10_steps_update": 7e-6, "mixed_64x64x64_n4_sampled": 1e-4,
     "tgv_5x5x5_rotated_affine_mixed_orders": 1e-4, "padapt_5x5x5_one_sided_mixed_face": 5e-5,
     "padapt_5x5x5_kep": 5e-5, "wake_8x8x8_n4_kep": 1e-6,
+    "channel_6x6x6_noslip": 1e-5, "channel_6x6x6_slip": 1e-5,
 }
 
 
@@ -141,6 +142,15 @@ def test_tf32x3_every_order_rk_steps():
     err = rel_l2(qd.cpu().numpy() - q0, q - q0)
     _record("tgv_4x4x4_n3_rk3_10_steps_update_tf32x3", err)
     assert err <= 1.5 * BOUNDS["tgv_4x4x4_n3_rk3_10_steps_update"]
+
+
+@pytest.mark.parametrize("wall", [3, 4])
+def test_fp32_walls(wall):
+    w = wl.channel_walls(n=6, wall=wall)
+    name = "channel_6x6x6_" + ("noslip" if wall == 3 else "slip")
+    err = _fp32_error(w, params=dict(w.params, nu=1e-2))
+    _record(name, err)
+    assert err <= BOUNDS[name], err
 
 
 def test_fp32_rk3_ten_steps():
