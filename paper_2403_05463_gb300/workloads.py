@@ -60,13 +60,14 @@ class MeshDesc:
 
 
 def box_mesh(nx, ny, nz, xb, yb, zb, periodic=(True, True, True), geom_degree=1,
-             warp: Optional[Callable] = None, bc_x=(1, 2)) -> MeshDesc:
+             warp: Optional[Callable] = None, bc_lohi=(1, 2)) -> MeshDesc:
     """Structured hexahedral mesh with element boundaries xb, yb, zb (lengths n+1).
 
     Element (i, j, k) has index i + nx (j + ny k). Vertex ids wrap in periodic directions,
     so periodic faces match by their corner ids. Geometry nodes of degree 1 or 2 sit at
     the reference points {-1, 1} or {-1, 0, 1} (the Gauss-Lobatto points of those degrees);
-    ``warp`` maps undeformed (x, y, z) arrays to deformed ones.
+    ``warp`` maps undeformed (x, y, z) arrays to deformed ones; ``bc_lohi`` gives the boundary
+    tags of the low and high faces of every non-periodic direction.
     """
     assert geom_degree in (1, 2)
     xb, yb, zb = (np.asarray(a, dtype=np.float64) for a in (xb, yb, zb))
@@ -106,14 +107,14 @@ def box_mesh(nx, ny, nz, xb, yb, zb, periodic=(True, True, True), geom_degree=1,
     if not all(periodic):
         bc = np.full((E, 6), -1, dtype=np.int8)
         if not periodic[0]:
-            bc[ii == 0, 0] = bc_x[0]
-            bc[ii == nx - 1, 1] = bc_x[1]
+            bc[ii == 0, 0] = bc_lohi[0]
+            bc[ii == nx - 1, 1] = bc_lohi[1]
         if not periodic[1]:
-            bc[jj == 0, 2] = bc_x[0]
-            bc[jj == ny - 1, 3] = bc_x[1]
+            bc[jj == 0, 2] = bc_lohi[0]
+            bc[jj == ny - 1, 3] = bc_lohi[1]
         if not periodic[2]:
-            bc[kk == 0, 4] = bc_x[0]
-            bc[kk == nz - 1, 5] = bc_x[1]
+            bc[kk == 0, 4] = bc_lohi[0]
+            bc[kk == nz - 1, 5] = bc_lohi[1]
     return MeshDesc(hexa, geom, geom_degree, bc, centers, (nx, ny, nz))
 
 
@@ -463,7 +464,7 @@ def channel_walls(n=8, order=4, wall=3, wavy=0.08):
         return x, y + wavy * np.sin(x) * np.cos(z), z
 
     mesh = box_mesh(n, n, n, b, yb, b, periodic=(True, False, True), geom_degree=2, warp=warp,
-                    bc_x=(wall, wall))
+                    bc_lohi=(wall, wall))
     yc = mesh.centers[:, 1]
     flags = ((yc < 0.5) | (yc > 1.5)).astype(np.uint8)
 

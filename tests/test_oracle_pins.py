@@ -631,7 +631,7 @@ def _channel(ny, y0, H, tags, N=3):
     xb = np.linspace(0, 2 * np.pi, n + 1)
     yb = np.linspace(y0, y0 + H, ny + 1)
     periodic = tags is None
-    m = wl.box_mesh(n, ny, n, xb, yb, xb, periodic=(True, periodic, True), bc_x=tags or (1, 2))
+    m = wl.box_mesh(n, ny, n, xb, yb, xb, periodic=(True, periodic, True), bc_lohi=tags or (1, 2))
     return m, np.full(n * ny * n, N, np.int8)
 
 
