@@ -203,6 +203,39 @@ dg_status dg_autotune(dg_ctx* ctx, const char* cache_path, char* report, int rep
  * order on the device, so it may differ from dg_conservation's host sum by rounding. */
 dg_status dg_conservation_noalloc(dg_ctx* ctx, const double* R_dev, double* out_dev, void* stream);
 
+/* Two-component Gaussian mixture on the node features (Q_S, R_S, Q_Omega) of Sec. 2.1. The
+ * mixture is fitted outside the library (on snapshots of developed flow); any per-feature
+ * scaling used in that fit folds into the means and covariances. */
+typedef struct {
+  double weight[2];     /* mixture weights, positive (they need not sum to 1)        */
+  double mean[2][3];    /* component means, in (Q_S, R_S, Q_Omega) order              */
+  double cov[2][3][3];  /* component covariances, symmetric positive definite        */
+  int viscous;          /* 0 or 1: the component of the viscous/rotational region    */
+  int reserved;         /* must be 0                                                  */
+} dg_gmm;
+
+/* Viscous/inviscid region detection (Sec. 2.1), on the device, from the state q_dev
+ * ([4][total_nodes] FP64, the current mesh and orders):
+ *   1. at every node, the gradient of the element's velocity polynomial, J_ck = du_c/dx_k, by
+ *      the chain rule with the element's metric terms (no interface terms);
+ *   2. S = (J + J^T)/2, Omega = (J - J^T)/2, Q_S = (tr(S)^2 - tr(S^2))/2, R_S = -det(S)/3,
+ *      Q_Omega = -tr(Omega^2)/2;
+ *   3. the posterior probabilities p_v, p_i of the viscous and the other component of `gmm`
+ *      at the node's features (the mixture's E-step);
+ *   4. per element, the means of p_v and p_i over its (N+1)^3 nodes, and the region with the
+ *      larger mean (1 viscous/NS, 0 inviscid/Euler; a tie is viscous).
+ * FP64 throughout. Outputs, caller-owned device memory, NULL to skip (at least one given):
+ *   flags_dev    [n_elements] uint8, element order: ready for dg_set_element_flags once copied
+ *                to the host (this call does not change the context's flags);
+ *   pbar_dev     [2][n_elements] FP64: mean p_v, then mean p_i;
+ *   features_dev [4][total_nodes] FP64: Q_S, R_S, Q_Omega, p_v per node (node layout of q).
+ * Asynchronous on `stream`. Errors: DG_ERR_ARG for a NULL ctx, q_dev or gmm, no output, a
+ * non-positive or non-finite weight, a covariance that is not symmetric (to 1e-12 of its
+ * largest entry) or not positive definite, viscous outside {0, 1}, reserved != 0;
+ * DG_ERR_CUDA if a launch fails. */
+dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm, uint8_t* flags_dev,
+                            double* pbar_dev, double* features_dev, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 dg_status dg_check_device(dg_ctx* ctx, void* stream);
 

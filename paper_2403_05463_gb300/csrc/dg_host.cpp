@@ -1062,6 +1062,67 @@ dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* 
   return DG_OK;
 }
 
+// Mixture constants for the detection kernel: inverse covariances by cofactors, log-weights
+// with the log-determinants (Sec. 2.1; the mixture itself is an input).
+static dg_status gmm_prepare(const dg_gmm& g, GmmDev& out) {
+  if (g.viscous != 0 && g.viscous != 1) return fail(DG_ERR_ARG, "gmm.viscous must be 0 or 1");
+  if (g.reserved != 0) return fail(DG_ERR_ARG, "gmm.reserved must be 0");
+  for (int k = 0; k < 2; ++k) {
+    if (!std::isfinite(g.weight[k]) || !(g.weight[k] > 0.0))
+      return fail(DG_ERR_ARG, "gmm.weight[%d] must be positive and finite", k);
+    const double(*C)[3] = g.cov[k];
+    double big = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      if (!std::isfinite(g.mean[k][i])) return fail(DG_ERR_ARG, "gmm.mean[%d] is not finite", k);
+      for (int j = 0; j < 3; ++j) {
+        if (!std::isfinite(C[i][j])) return fail(DG_ERR_ARG, "gmm.cov[%d] is not finite", k);
+        big = std::max(big, std::fabs(C[i][j]));
+      }
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = i + 1; j < 3; ++j)
+        if (std::fabs(C[i][j] - C[j][i]) > 1e-12 * big) return fail(DG_ERR_ARG, "gmm.cov[%d] is not symmetric", k);
+    // Sylvester's criterion on the leading principal minors
+    const double m1 = C[0][0], m2 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+    const double c00 = C[1][1] * C[2][2] - C[1][2] * C[2][1];
+    const double c01 = C[1][2] * C[2][0] - C[1][0] * C[2][2];
+    const double c02 = C[1][0] * C[2][1] - C[1][1] * C[2][0];
+    const double det = C[0][0] * c00 + C[0][1] * c01 + C[0][2] * c02;
+    if (!(m1 > 0.0) || !(m2 > 0.0) || !(det > 0.0))
+      return fail(DG_ERR_ARG, "gmm.cov[%d] is not positive definite", k);
+    const double inv00 = c00 / det;
+    const double inv01 = (C[0][2] * C[2][1] - C[0][1] * C[2][2]) / det;
+    const double inv02 = (C[0][1] * C[1][2] - C[0][2] * C[1][1]) / det;
+    const double inv11 = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) / det;
+    const double inv12 = (C[0][2] * C[1][0] - C[0][0] * C[1][2]) / det;
+    const double inv22 = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) / det;
+    const double P[6] = {inv00, inv01, inv02, inv11, inv12, inv22};
+    for (int i = 0; i < 6; ++i) out.P[k][i] = P[i];
+    for (int i = 0; i < 3; ++i) out.mu[k][i] = g.mean[k][i];
+    out.c[k] = std::log(g.weight[k]) - 0.5 * std::log(det);
+  }
+  out.viscous = g.viscous;
+  return DG_OK;
+}
+
+dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8_t* flags, double* pbar,
+                            double* feat, void* stream) {
+  if (!c || !q || !gmm) return fail(DG_ERR_ARG, "NULL argument");
+  if (!flags && !pbar && !feat) return fail(DG_ERR_ARG, "dg_detect_regions: no output requested");
+  GmmDev g{};
+  dg_status st = gmm_prepare(*gmm, g);
+  if (st != DG_OK) return st;
+  CU(cudaSetDevice(c->device));
+  const OpTables& T = ops();
+  for (const Bucket& b : c->all_buckets) {
+    DMatArg D{};
+    const std::vector<double>& Dn = T.rule[b.N].D;
+    for (size_t i = 0; i < Dn.size(); ++i) D.D[i] = Dn[i];
+    CU(launch_detect_regions(c->M, b, g, D, q, flags, pbar, feat, (cudaStream_t)stream));
+  }
+  return DG_OK;
+}
+
 dg_status dg_set_element_flags(dg_ctx* c, const uint8_t* flags) {
   if (!c || !flags) return fail(DG_ERR_ARG, "NULL argument");
   for (int64_t e = 0; e < c->ne; ++e)

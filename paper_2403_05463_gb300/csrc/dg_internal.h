@@ -159,6 +159,19 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
 // elements per tile of the FP32 inviscid pass at order N: the default shape or the alternative
 int tile_epb32(int N, int alt);
 
+// Region detection (dg_regions.cu): the mixture as the kernel uses it.
+struct GmmDev {
+  double P[2][6];   // inverse covariance of component k, upper triangle: 00 01 02 11 12 22
+  double mu[2][3];  // means
+  double c[2];      // log w_k - log det(C_k) / 2 (the common -3/2 log 2 pi cancels)
+  int viscous;      // index of the viscous component
+};
+struct DMatArg {
+  double D[NP * NP];  // D of one order, row-major [i * n + m], n = N + 1
+};
+cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D,
+                                  const double* q, uint8_t* flags, double* pbar, double* feat, cudaStream_t s);
+
 // Allocation-free conservation sums (dg_noalloc.cu)
 cudaError_t noalloc_scratch(int device, double** ptr);
 cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets,

@@ -44,6 +44,25 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
 
 
+class GMM(ctypes.Structure):
+    """Two-component Gaussian mixture on the node features (Q_S, R_S, Q_Omega) (dg_gmm)."""
+    _fields_ = [("weight", ctypes.c_double * 2), ("mean", (ctypes.c_double * 3) * 2),
+                ("cov", ((ctypes.c_double * 3) * 3) * 2), ("viscous", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+def make_gmm(weights, means, covs, viscous) -> GMM:
+    out = GMM()
+    for k in range(2):
+        out.weight[k] = float(weights[k])
+        for i in range(3):
+            out.mean[k][i] = float(means[k][i])
+            for j in range(3):
+                out.cov[k][i][j] = float(covs[k][i][j])
+    out.viscous = int(viscous)
+    out.reserved = 0
+    return out
+
+
 _lock = threading.Lock()
 _lib = None
 _vp = ctypes.c_void_p
@@ -80,6 +99,7 @@ def load():
         L.dg_conservation_noalloc.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
         L.dg_project_state.argtypes = [_vp, _vp, _vp, _vp]
+        L.dg_detect_regions.argtypes = [_vp, _vp, ctypes.POINTER(GMM), _vp, _vp, _vp, _vp]
         L.dg_check_device.argtypes = [_vp, _vp]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -254,6 +274,24 @@ class Solver:
         _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old"), _dev_ptr(q_new, "q_new"),
                                        _stream_handle(stream)))
         return q_new
+
+    def detect_regions(self, q, gmm, flags=True, pbar=True, features=False, stream=None):
+        """Viscous/inviscid region detection from the state q (see dg_detect_regions). gmm is a
+        GMM or a dict with weights, means, covs, viscous. Returns (flags, pbar, features):
+        uint8 [n_elem], float64 [2][n_elem], float64 [4][total_nodes] CUDA tensors, None where
+        not requested. The context's own flags are left as they are."""
+        import torch
+        if isinstance(gmm, dict):
+            gmm = make_gmm(gmm["weights"], gmm["means"], gmm["covs"], gmm["viscous"])
+        dev = q.device
+        f = torch.empty(self.n_elem, dtype=torch.uint8, device=dev) if flags else None
+        pb = torch.empty((2, self.n_elem), dtype=torch.float64, device=dev) if pbar else None
+        ft = torch.empty((4, self.total_nodes), dtype=torch.float64, device=dev) if features else None
+        _check(load().dg_detect_regions(self.h, _dev_ptr(q, "q"), ctypes.byref(gmm),
+                                        None if f is None else ctypes.c_void_p(f.data_ptr()),
+                                        None if pb is None else _dev_ptr(pb, "pbar"),
+                                        None if ft is None else _dev_ptr(ft, "features"), _stream_handle(stream)))
+        return f, pb, ft
 
     def autotune(self, cache_path=None):
         """Time the candidate launch shapes of the reduced-precision passes on this mesh and
