@@ -1298,3 +1298,555 @@ int or_conservation(const or_mesh* m, const or_real* R, or_real out[4]) {
   free(part);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Compressible Navier-Stokes (App. A): state u = (rho, rho v, rho e), ideal gas with unit
+ * gas constant (p = (gamma - 1)(rho e - rho |v|^2 / 2), T = p / rho, H = (rho e + p) / rho).
+ * The same weak form as above (App. B, Eq. NS4, viscous terms under BR1), five variables.
+ * ---------------------------------------------------------------------------------- */
+
+static void cns_prim(const or_real u[5], or_real gamma, or_real v[3], or_real* p) {
+  for (int c = 0; c < 3; ++c) v[c] = u[1 + c] / u[0];
+  *p = (gamma - 1.0) * (u[4] - 0.5 * u[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+}
+
+/* Euler flux along n_hat: (rho v.n, rho v v.n + p n, (rho e + p) v.n) */
+void or_cns_flux(const or_real u[5], const or_real nh[3], or_real gamma, or_real out[5]) {
+  or_real v[3], p;
+  cns_prim(u, gamma, v, &p);
+  const or_real vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
+  out[0] = u[0] * vn;
+  for (int c = 0; c < 3; ++c) out[1 + c] = u[1 + c] * vn + p * nh[c];
+  out[4] = (u[4] + p) * vn;
+}
+
+/* d(F.n)/du written in (v, H): for an ideal gas the Jacobian depends on the state only
+ * through the velocity and the total enthalpy. Rows/columns (rho, m1, m2, m3, E). */
+static void cns_jacobian_vH(const or_real v[3], or_real H, const or_real nh[3], or_real gamma, or_real A[25]) {
+  const or_real g1 = gamma - 1.0;
+  const or_real vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
+  const or_real k = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int i = 0; i < 25; ++i) A[i] = 0.0;
+  /* mass: d(m.n)/du */
+  for (int c = 0; c < 3; ++c) A[0 * 5 + 1 + c] = nh[c];
+  /* momentum: m_i vn + p n_i, with dp/du = g1 (k, -v, 1) */
+  for (int i = 0; i < 3; ++i) {
+    A[(1 + i) * 5 + 0] = -v[i] * vn + g1 * k * nh[i];
+    for (int c = 0; c < 3; ++c) A[(1 + i) * 5 + 1 + c] = v[i] * nh[c] - g1 * v[c] * nh[i] + (i == c ? vn : 0.0);
+    A[(1 + i) * 5 + 4] = g1 * nh[i];
+  }
+  /* energy: H m.n, with d(rho H)/du = (g1 k, -g1 v, gamma) */
+  A[4 * 5 + 0] = vn * (g1 * k - H);
+  for (int c = 0; c < 3; ++c) A[4 * 5 + 1 + c] = H * nh[c] - g1 * v[c] * vn;
+  A[4 * 5 + 4] = gamma * vn;
+}
+
+void or_cns_jacobian(const or_real u[5], const or_real nh[3], or_real gamma, or_real A[25]) {
+  or_real v[3], p;
+  cns_prim(u, gamma, v, &p);
+  cns_jacobian_vH(v, (u[4] + p) / u[0], nh, gamma, A);
+}
+
+/* |A| at the Roe average (sqrt(rho)-weighted v and H) by its eigen-decomposition
+ * R |Lambda| R^-1, R^-1 by Gauss-Jordan. Eigenvectors: acoustic (1, v -+ a n, H -+ a vn),
+ * entropy (1, v, |v|^2/2), shear (0, t, v.t) for two unit tangents t. */
+int or_cns_roe_abs_jacobian(const or_real uL[5], const or_real uR[5], const or_real nh[3], or_real gamma,
+                            or_real absA[25]) {
+  or_real vL[3], vR[3], pL, pR;
+  cns_prim(uL, gamma, vL, &pL);
+  cns_prim(uR, gamma, vR, &pR);
+  if (!(uL[0] > 0.0) || !(uR[0] > 0.0)) return -1;
+  const or_real sL = SQRT(uL[0]), sR = SQRT(uR[0]);
+  const or_real HL = (uL[4] + pL) / uL[0], HR = (uR[4] + pR) / uR[0];
+  or_real v[3];
+  for (int c = 0; c < 3; ++c) v[c] = (sL * vL[c] + sR * vR[c]) / (sL + sR);
+  const or_real H = (sL * HL + sR * HR) / (sL + sR);
+  const or_real k = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const or_real a2 = (gamma - 1.0) * (H - k);
+  if (!(a2 > 0.0)) return -1;
+  const or_real a = SQRT(a2);
+  const or_real vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
+  /* two unit tangents: t1 from the coordinate axis least aligned with n */
+  int ax = 0;
+  for (int c = 1; c < 3; ++c)
+    if (FABS(nh[c]) < FABS(nh[ax])) ax = c;
+  or_real e[3] = {0.0, 0.0, 0.0};
+  e[ax] = 1.0;
+  or_real t1[3] = {nh[1] * e[2] - nh[2] * e[1], nh[2] * e[0] - nh[0] * e[2], nh[0] * e[1] - nh[1] * e[0]};
+  const or_real l1 = SQRT(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int c = 0; c < 3; ++c) t1[c] /= l1;
+  const or_real t2[3] = {nh[1] * t1[2] - nh[2] * t1[1], nh[2] * t1[0] - nh[0] * t1[2], nh[0] * t1[1] - nh[1] * t1[0]};
+  or_real R[25], lam[5];
+  /* columns: 0 acoustic -, 1 entropy, 2 shear t1, 3 shear t2, 4 acoustic + */
+  R[0 * 5 + 0] = 1.0;
+  R[0 * 5 + 1] = 1.0;
+  R[0 * 5 + 2] = 0.0;
+  R[0 * 5 + 3] = 0.0;
+  R[0 * 5 + 4] = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    R[(1 + c) * 5 + 0] = v[c] - a * nh[c];
+    R[(1 + c) * 5 + 1] = v[c];
+    R[(1 + c) * 5 + 2] = t1[c];
+    R[(1 + c) * 5 + 3] = t2[c];
+    R[(1 + c) * 5 + 4] = v[c] + a * nh[c];
+  }
+  R[4 * 5 + 0] = H - a * vn;
+  R[4 * 5 + 1] = k;
+  R[4 * 5 + 2] = v[0] * t1[0] + v[1] * t1[1] + v[2] * t1[2];
+  R[4 * 5 + 3] = v[0] * t2[0] + v[1] * t2[1] + v[2] * t2[2];
+  R[4 * 5 + 4] = H + a * vn;
+  lam[0] = vn - a;
+  lam[1] = lam[2] = lam[3] = vn;
+  lam[4] = vn + a;
+  or_real Rc[25], Ri[25];
+  for (int i = 0; i < 25; ++i) {
+    Rc[i] = R[i];
+    Ri[i] = (i % 6 == 0) ? 1.0 : 0.0;
+  }
+  if (gauss_jordan(5, Rc, 5, Ri)) return -1;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      or_real s = 0.0;
+      for (int w = 0; w < 5; ++w) s += R[i * 5 + w] * FABS(lam[w]) * Ri[w * 5 + j];
+      absA[i * 5 + j] = s;
+    }
+  return 0;
+}
+
+/* Roe: (F(uL) + F(uR))/2 - |A_roe| (uR - uL)/2; LLF: the largest |vn| + a of the two sides */
+int or_cns_riemann(const or_real uL[5], const or_real uR[5], const or_real nh[3], const or_params* prm,
+                   or_real out[5]) {
+  or_real fL[5], fR[5];
+  or_cns_flux(uL, nh, prm->gamma, fL);
+  or_cns_flux(uR, nh, prm->gamma, fR);
+  if (prm->riemann == 0) {
+    or_real absA[25];
+    if (or_cns_roe_abs_jacobian(uL, uR, nh, prm->gamma, absA)) return -1;
+    for (int i = 0; i < 5; ++i) {
+      or_real d = 0.0;
+      for (int j = 0; j < 5; ++j) d += absA[i * 5 + j] * (uR[j] - uL[j]);
+      out[i] = 0.5 * (fL[i] + fR[i]) - 0.5 * d;
+    }
+  } else {
+    or_real s = 0.0;
+    const or_real* us[2] = {uL, uR};
+    for (int k = 0; k < 2; ++k) {
+      or_real v[3], p;
+      cns_prim(us[k], prm->gamma, v, &p);
+      if (!(us[k][0] > 0.0) || !(p > 0.0)) return -1;
+      const or_real sp = FABS(v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2]) + SQRT(prm->gamma * p / us[k][0]);
+      if (sp > s) s = sp;
+    }
+    for (int i = 0; i < 5; ++i) out[i] = 0.5 * (fL[i] + fR[i]) - 0.5 * s * (uR[i] - uL[i]);
+  }
+  return 0;
+}
+
+/* primitive quantities lifted by BR1: phi = (v1, v2, v3, T) */
+static void cns_phi(const or_real u[5], or_real gamma, or_real phi[4]) {
+  or_real v[3], p;
+  cns_prim(u, gamma, v, &p);
+  for (int c = 0; c < 3; ++c) phi[c] = v[c];
+  phi[3] = p / u[0];
+}
+
+static void face_u5(const or_mesh* m, const or_real* u, int64_t e, int f, or_real* T /*[5][n2]*/) {
+  int N = m->N[e], n = N + 1, n2 = n * n;
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      int64_t p = m->off[e] + face_node(f, N, a, b);
+      for (int v = 0; v < 5; ++v) T[v * n2 + a + n * b] = u[v * m->total + p];
+    }
+}
+
+/* the neighbour's face state in my face coordinates (conforming faces: same order) */
+static void cns_nbr_face(const or_mesh* m, const or_real* u, int64_t e, int f, or_real* T /*[5][n2]*/) {
+  int N = m->N[e], n = N + 1;
+  int64_t nb = m->nb_e[e * 6 + f];
+  or_real* tn = (or_real*)malloc(sizeof(or_real) * 5 * n * n);
+  face_u5(m, u, nb, m->nb_f[e * 6 + f], tn);
+  nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 5, tn, T);
+  free(tn);
+}
+
+typedef struct {
+  const or_mesh* m;
+  const or_real* u;
+  geo_t* geo;
+  or_real** G;  /* per NS element [4][3][n3] */
+} cwork_t;
+
+/* BR1 gradient of phi, weak form: w J G_ck = -sum_d (w/w_{i_d}) sum_m w_m D_{m i_d} (phi_c Ja^d_k)_m
+ * + face terms phi*_c S_k with phi* = (phi^- + phi^+)/2 */
+static void cns_gradient(const cwork_t* W, int64_t e, or_real* G) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  const or_real* w = m->op[N].w;
+  const or_real* D = m->op[N].D;
+  const geo_t* gt = &W->geo[e];
+  or_real* phi = (or_real*)malloc(sizeof(or_real) * 4 * n3);
+  for (int p = 0; p < n3; ++p) {
+    or_real uu[5], ph[4];
+    for (int v = 0; v < 5; ++v) uu[v] = W->u[v * m->total + m->off[e] + p];
+    cns_phi(uu, m->p.gamma, ph);
+    for (int c = 0; c < 4; ++c) phi[c * n3 + p] = ph[c];
+  }
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < 3; ++k)
+      for (int kk = 0; kk < n; ++kk)
+        for (int jj = 0; jj < n; ++jj)
+          for (int ii = 0; ii < n; ++ii) {
+            int ijk[3] = {ii, jj, kk};
+            or_real s = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              or_real sd = 0.0;
+              for (int mm = 0; mm < n; ++mm) {
+                int src[3] = {ii, jj, kk};
+                src[d] = mm;
+                int64_t ps = src[0] + n * (src[1] + n * src[2]);
+                sd += w[mm] * D[mm * n + ijk[d]] * phi[c * n3 + ps] * gt->Ja[(d * 3 + k) * n3 + ps];
+              }
+              s -= sd / w[ijk[d]];
+            }
+            G[(c * 3 + k) * n3 + ii + n * (jj + n * kk)] = s;
+          }
+  or_real* um = (or_real*)malloc(sizeof(or_real) * 5 * n2);
+  or_real* up = (or_real*)malloc(sizeof(or_real) * 5 * n2);
+  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+  for (int f = 0; f < 6; ++f) {
+    face_u5(m, W->u, e, f, um);
+    cns_nbr_face(m, W->u, e, f, up);
+    face_S(m, gt, e, f, S);
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        const int fp = a + n * b;
+        or_real qm[5], qp[5], pm[4], pp[4];
+        for (int v = 0; v < 5; ++v) {
+          qm[v] = um[v * n2 + fp];
+          qp[v] = up[v * n2 + fp];
+        }
+        cns_phi(qm, m->p.gamma, pm);
+        cns_phi(qp, m->p.gamma, pp);
+        const int64_t p = face_node(f, N, a, b);
+        for (int c = 0; c < 4; ++c)
+          for (int k = 0; k < 3; ++k) G[(c * 3 + k) * n3 + p] += 0.5 * (pm[c] + pp[c]) * S[k * n2 + fp] / w[0];
+      }
+  }
+  free(um);
+  free(up);
+  free(S);
+  free(phi);
+  for (int ck = 0; ck < 12; ++ck)
+    for (int p = 0; p < n3; ++p) G[ck * n3 + p] /= gt->J[p];
+}
+
+/* viscous flux rows at one node of an NS element: Fv[v][k], v = momentum 1..3 then energy */
+static void cns_visc_flux(const cwork_t* W, int64_t e, int n3, int64_t p, const or_real u[5], or_real Fv[4][3]) {
+  const or_mesh* m = W->m;
+  const or_real* G = W->G[e];
+  or_real Gv[9], gT[3];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) Gv[c * 3 + k] = G[(c * 3 + k) * n3 + p];
+  for (int k = 0; k < 3; ++k) gT[k] = G[(9 + k) * n3 + p];
+  const or_real mut = u[0] * or_eddy_viscosity(Gv, W->geo[e].delta, &m->p);
+  const or_real mu = m->p.nu * m->vscale[e], mt = mut * m->vscale[e];
+  const or_real mue = mu + mt;
+  const or_real cp = m->p.gamma / (m->p.gamma - 1.0);
+  const or_real kappa = cp * (mu / m->p.prandtl + mt / m->p.prandtl_t);
+  const or_real tr = Gv[0] + Gv[4] + Gv[8];
+  or_real tau[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) tau[c][k] = mue * (Gv[c * 3 + k] + Gv[k * 3 + c]) - (c == k ? 2.0 / 3.0 * mue * tr : 0.0);
+  or_real v[3];
+  for (int c = 0; c < 3; ++c) v[c] = u[1 + c] / u[0];
+  for (int k = 0; k < 3; ++k) {
+    for (int c = 0; c < 3; ++c) Fv[c][k] = tau[c][k];
+    Fv[3][k] = v[0] * tau[0][k] + v[1] * tau[1][k] + v[2] * tau[2][k] + kappa * gT[k];
+  }
+}
+
+/* outward area-weighted viscous flux trace Fv . S of element e on face f, [4][n2] (zero for Euler) */
+static void cns_face_fv(const cwork_t* W, int64_t e, int f, or_real* out) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  if (!m->flag[e]) {
+    memset(out, 0, sizeof(or_real) * 4 * n2);
+    return;
+  }
+  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+  face_S(m, &W->geo[e], e, f, S);
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      const int fp = a + n * b;
+      const int64_t p = face_node(f, N, a, b);
+      or_real uu[5], Fv[4][3];
+      for (int v = 0; v < 5; ++v) uu[v] = W->u[v * m->total + m->off[e] + p];
+      cns_visc_flux(W, e, n3, p, uu, Fv);
+      for (int v = 0; v < 4; ++v) out[v * n2 + fp] = Fv[v][0] * S[fp] + Fv[v][1] * S[n2 + fp] + Fv[v][2] * S[2 * n2 + fp];
+    }
+  free(S);
+}
+
+/* w J R = sum_d (w / w_{i_d}) sum_m w_m D_{m i_d} Ftil^d_m - w_face H*, five variables */
+static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
+  const or_mesh* m = W->m;
+  int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+  const or_real* w = m->op[N].w;
+  const or_real* D = m->op[N].D;
+  const geo_t* gt = &W->geo[e];
+  int64_t o = m->off[e], T = m->total;
+  or_real* Ft = (or_real*)malloc(sizeof(or_real) * 15 * n3);
+  for (int p = 0; p < n3; ++p) {
+    or_real uu[5], F[5][3];
+    for (int v = 0; v < 5; ++v) uu[v] = W->u[v * T + o + p];
+    for (int k = 0; k < 3; ++k) {
+      const or_real ek[3] = {k == 0 ? 1.0 : 0.0, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0};
+      or_real fk[5];
+      or_cns_flux(uu, ek, m->p.gamma, fk);
+      for (int v = 0; v < 5; ++v) F[v][k] = fk[v];
+    }
+    if (m->flag[e]) {
+      or_real Fv[4][3];
+      cns_visc_flux(W, e, n3, p, uu, Fv);
+      for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < 3; ++k) F[1 + v][k] -= Fv[v][k];
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 5; ++v) {
+        or_real s = 0.0;
+        for (int k = 0; k < 3; ++k) s += gt->Ja[(d * 3 + k) * n3 + p] * F[v][k];
+        Ft[(d * 5 + v) * n3 + p] = s;
+      }
+  }
+  or_real* JR = (or_real*)calloc(5 * n3, sizeof(or_real));
+  for (int v = 0; v < 5; ++v)
+    for (int kk = 0; kk < n; ++kk)
+      for (int jj = 0; jj < n; ++jj)
+        for (int ii = 0; ii < n; ++ii) {
+          int ijk[3] = {ii, jj, kk};
+          or_real s = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            or_real sd = 0.0;
+            for (int mm = 0; mm < n; ++mm) {
+              int src[3] = {ii, jj, kk};
+              src[d] = mm;
+              sd += w[mm] * D[mm * n + ijk[d]] * Ft[(d * 5 + v) * n3 + src[0] + n * (src[1] + n * src[2])];
+            }
+            s += sd / w[ijk[d]];
+          }
+          JR[v * n3 + ii + n * (jj + n * kk)] = s;
+        }
+  /* faces: H* = F_e* . n |S| - F_v* . S with F_v* . S = wm Fv^- . S - wp Fv^+ . S^+ */
+  or_real* um = (or_real*)malloc(sizeof(or_real) * 5 * n2);
+  or_real* up = (or_real*)malloc(sizeof(or_real) * 5 * n2);
+  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+  or_real* Fvm = (or_real*)malloc(sizeof(or_real) * 4 * n2);
+  or_real* Fvp = (or_real*)malloc(sizeof(or_real) * 4 * n2);
+  or_real* tn = (or_real*)malloc(sizeof(or_real) * 4 * n2);
+  int rc = 0;
+  for (int f = 0; f < 6; ++f) {
+    const int64_t nb = m->nb_e[e * 6 + f];
+    face_u5(m, W->u, e, f, um);
+    cns_nbr_face(m, W->u, e, f, up);
+    face_S(m, gt, e, f, S);
+    const int any_visc = m->flag[e] || m->flag[nb];
+    memset(Fvm, 0, sizeof(or_real) * 4 * n2);
+    memset(Fvp, 0, sizeof(or_real) * 4 * n2);
+    if (any_visc) {
+      cns_face_fv(W, e, f, Fvm);
+      cns_face_fv(W, nb, m->nb_f[e * 6 + f], tn);
+      nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
+    }
+    or_real wm = 0.5, wp = 0.5;
+    if (m->p.mixed_face == 1 && m->flag[e] != m->flag[nb]) {
+      wm = m->flag[e] ? 1.0 : 0.0;
+      wp = m->flag[e] ? 0.0 : 1.0;
+    }
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        const int fp = a + n * b;
+        const or_real Sv[3] = {S[fp], S[n2 + fp], S[2 * n2 + fp]};
+        const or_real s = SQRT(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+        const or_real nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+        or_real qm[5], qp[5], Fs[5];
+        for (int v = 0; v < 5; ++v) {
+          qm[v] = um[v * n2 + fp];
+          qp[v] = up[v * n2 + fp];
+        }
+        if (or_cns_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
+        const int64_t p = face_node(f, N, a, b);
+        JR[p] -= Fs[0] * s / w[0];
+        for (int v = 0; v < 4; ++v) {
+          const or_real fv = wm * Fvm[v * n2 + fp] - wp * Fvp[v * n2 + fp];
+          JR[(1 + v) * n3 + p] -= (Fs[1 + v] * s - fv) / w[0];
+        }
+      }
+  }
+  for (int v = 0; v < 5; ++v)
+    for (int p = 0; p < n3; ++p) R[v * T + o + p] = JR[v * n3 + p] / gt->J[p];
+  free(um);
+  free(up);
+  free(S);
+  free(Fvm);
+  free(Fvp);
+  free(tn);
+  free(JR);
+  free(Ft);
+  return rc;
+}
+
+static int cns_check(const or_mesh* m) {
+  if (!(m->p.gamma > 1.0) || !(m->p.prandtl > 0.0) || !(m->p.prandtl_t > 0.0)) {
+    set_err("compressible form: need gamma > 1 and positive Prandtl numbers");
+    return -1;
+  }
+  for (int64_t e = 0; e < m->ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int64_t nb = m->nb_e[e * 6 + f];
+      if (nb < 0) {
+        set_err("compressible form: element %lld face %d is a boundary (periodic meshes only)", (long long)e, f);
+        return -1;
+      }
+      if (m->N[nb] != m->N[e]) {
+        set_err("compressible form: element %lld face %d is p-nonconforming", (long long)e, f);
+        return -1;
+      }
+    }
+  return 0;
+}
+
+static void cns_free(cwork_t* W) {
+  for (int64_t e = 0; e < W->m->ne; ++e) {
+    free(W->geo[e].J);
+    free(W->geo[e].Ja);
+    free(W->G[e]);
+  }
+  free(W->geo);
+  free(W->G);
+}
+
+int or_cns_element_gradient(const or_mesh* m, const or_real* u, int64_t e, or_real* G) {
+  if (e < 0 || e >= m->ne || cns_check(m)) return -1;
+  uint8_t* need = (uint8_t*)calloc(m->ne, 1);
+  need[e] = 1;
+  for (int f = 0; f < 6; ++f) need[m->nb_e[e * 6 + f]] = 1;
+  cwork_t W;
+  W.m = m;
+  W.u = u;
+  W.geo = (geo_t*)calloc(m->ne, sizeof(geo_t));
+  W.G = (or_real**)calloc(m->ne, sizeof(or_real*));
+  for (int64_t i = 0; i < m->ne; ++i)
+    if (need[i]) compute_geo(m, i, &W.geo[i]);
+  cns_gradient(&W, e, G);
+  cns_free(&W);
+  free(need);
+  return 0;
+}
+
+int or_cns_residual(const or_mesh* m, const or_real* u, or_real* R, int64_t n_sel, const int64_t* sel) {
+  if (cns_check(m)) return -1;
+  int64_t ne = m->ne;
+  uint8_t* want = (uint8_t*)calloc(ne, 1);
+  if (sel) {
+    for (int64_t i = 0; i < n_sel; ++i) {
+      if (sel[i] < 0 || sel[i] >= ne) {
+        free(want);
+        set_err("selected element out of range");
+        return -1;
+      }
+      want[sel[i]] = 1;
+    }
+  } else {
+    memset(want, 1, ne);
+  }
+  uint8_t* need = (uint8_t*)calloc(ne, 1);
+  for (int64_t e = 0; e < ne; ++e)
+    if (want[e]) {
+      need[e] = 1;
+      for (int f = 0; f < 6; ++f) need[m->nb_e[e * 6 + f]] = 1;
+    }
+  /* a neighbour's gradient needs its own neighbours' geometry */
+  uint8_t* need2 = (uint8_t*)calloc(ne, 1);
+  for (int64_t e = 0; e < ne; ++e)
+    if (need[e]) {
+      need2[e] = 1;
+      for (int f = 0; f < 6; ++f) need2[m->nb_e[e * 6 + f]] = 1;
+    }
+  cwork_t W;
+  W.m = m;
+  W.u = u;
+  W.geo = (geo_t*)calloc(ne, sizeof(geo_t));
+  W.G = (or_real**)calloc(ne, sizeof(or_real*));
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t e = 0; e < ne; ++e)
+    if (need2[e]) compute_geo(m, e, &W.geo[e]);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t e = 0; e < ne; ++e) {
+    if (!need[e] || !m->flag[e]) continue;
+    int n = m->N[e] + 1;
+    W.G[e] = (or_real*)malloc(sizeof(or_real) * 12 * n * n * n);
+    cns_gradient(&W, e, W.G[e]);
+  }
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(| : rc)
+  for (int64_t e = 0; e < ne; ++e)
+    if (want[e]) rc |= cns_element_residual(&W, e, R) ? 1 : 0;
+  cns_free(&W);
+  free(need);
+  free(need2);
+  free(want);
+  if (rc) {
+    set_err("Riemann solver failed (non-positive density or pressure)");
+    return -1;
+  }
+  return 0;
+}
+
+int or_cns_rk_step(const or_mesh* m, or_real* u, or_real* g, or_real dt, int nsteps) {
+  int64_t T5 = 5 * m->total;
+  or_real* R = (or_real*)malloc(sizeof(or_real) * T5);
+  for (int st = 0; st < nsteps; ++st)
+    for (int s = 0; s < 3; ++s) {
+      if (or_cns_residual(m, u, R, 0, NULL)) {
+        free(R);
+        return -1;
+      }
+      for (int64_t i = 0; i < T5; ++i) {
+        g[i] = (s == 0 ? 0.0 : RK_A[s] * g[i]) + dt * R[i];
+        u[i] = u[i] + RK_B[s] * g[i];
+      }
+    }
+  free(R);
+  return 0;
+}
+
+int or_cns_conservation(const or_mesh* m, const or_real* R, or_real out[5]) {
+  int64_t ne = m->ne;
+  or_real* part = (or_real*)calloc(5 * ne, sizeof(or_real));
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t e = 0; e < ne; ++e) {
+    geo_t gt;
+    compute_geo(m, e, &gt);
+    int N = m->N[e], n = N + 1;
+    const or_real* w = m->op[N].w;
+    for (int v = 0; v < 5; ++v) {
+      or_real s = 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            int64_t p = i + n * (j + n * k);
+            s += w[i] * w[j] * w[k] * gt.J[p] * R[v * m->total + m->off[e] + p];
+          }
+      part[v * ne + e] = s;
+    }
+    free(gt.J);
+    free(gt.Ja);
+  }
+  for (int v = 0; v < 5; ++v) {
+    or_real s = 0.0;
+    for (int64_t e = 0; e < ne; ++e) s += part[v * ne + e];
+    out[v] = s;
+  }
+  free(part);
+  return 0;
+}

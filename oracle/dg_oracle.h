@@ -52,6 +52,11 @@ typedef struct {
                        1 the kinetic-energy-preserving split form: along each direction
                        sum_m 2 D_im F#(q_i, q_m) with the two-point flux of or_kep_flux */
   or_real inflow[4]; /* ghost state used at inflow faces (velocity part)          */
+  /* compressible form only (the or_cns_* entry points): ideal gas with unit gas constant,
+     so T = p / rho and c_p = gamma / (gamma - 1); nu is then the dynamic viscosity mu   */
+  or_real gamma;     /* ratio of specific heats                                   */
+  or_real prandtl;   /* laminar Prandtl number                                    */
+  or_real prandtl_t; /* turbulent Prandtl number                                  */
 } or_params;
 
 typedef struct or_mesh or_mesh;
@@ -98,6 +103,27 @@ int or_residual(const or_mesh* m, const or_real* q, or_real* R, int64_t n_sel, c
 int or_rk_step(const or_mesh* m, or_real* q, or_real* g, or_real dt, int nsteps);
 /* out[v] = sum_e sum_nodes w_i w_j w_k J R_v. */
 int or_conservation(const or_mesh* m, const or_real* R, or_real out[4]);
+
+/* ---- Compressible Navier-Stokes (App. A) --------------------------------------------------
+ * Conservative state u = (rho, rho v1, rho v2, rho v3, rho e), SoA [5][total_nodes], on the
+ * same mesh, orders, flags and parameters (nu = mu, gamma, prandtl, prandtl_t, closure,
+ * riemann, mixed_face). Flag 0 elements solve the Euler equations, flag 1 the Navier-Stokes
+ * equations with the eddy viscosity mu_t = rho nu_t of the selected closure; heat flux
+ * kappa grad T with kappa = c_p (mu / Pr + mu_t / Pr_t). BR1 lifts the primitive
+ * (v1, v2, v3, T). Conforming faces and interior/periodic faces only: a boundary tag or a
+ * p-nonconforming face makes these calls fail. */
+void or_cns_flux(const or_real u[5], const or_real n_hat[3], or_real gamma, or_real out[5]);
+void or_cns_jacobian(const or_real u[5], const or_real n_hat[3], or_real gamma, or_real A[25]);
+/* Roe matrix |A(u_roe)| = R |Lambda| R^-1 at the Roe average of uL, uR */
+int or_cns_roe_abs_jacobian(const or_real uL[5], const or_real uR[5], const or_real n_hat[3], or_real gamma,
+                            or_real absA[25]);
+int or_cns_riemann(const or_real uL[5], const or_real uR[5], const or_real n_hat[3], const or_params* prm,
+                   or_real out[5]);
+/* BR1 gradient of (v1, v2, v3, T) of one NS element: G[4][3][n^3], G[c][k] = d phi_c / d x_k. */
+int or_cns_element_gradient(const or_mesh* m, const or_real* u, int64_t e, or_real* G);
+int or_cns_residual(const or_mesh* m, const or_real* u, or_real* R, int64_t n_sel, const int64_t* sel);
+int or_cns_rk_step(const or_mesh* m, or_real* u, or_real* g, or_real dt, int nsteps);
+int or_cns_conservation(const or_mesh* m, const or_real* R, or_real out[5]);
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);
 

@@ -53,7 +53,7 @@ def _params_type(real):
     class P(ctypes.Structure):
         _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
                     ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
-                    ("inflow", real * 4)]
+                    ("inflow", real * 4), ("gamma", real), ("prandtl", real), ("prandtl_t", real)]
     return P
 
 
@@ -103,6 +103,16 @@ def lib(extended: bool = False):
             L.or_rk_step.argtypes = [ctypes.c_void_p, _d, _d, real, ctypes.c_int]
             L.or_conservation.argtypes = [ctypes.c_void_p, _d, _d]
             L.or_num_threads.restype = ctypes.c_int
+            L.or_cns_flux.argtypes = [_d, _d, real, _d]
+            L.or_cns_flux.restype = None
+            L.or_cns_jacobian.argtypes = [_d, _d, real, _d]
+            L.or_cns_jacobian.restype = None
+            L.or_cns_roe_abs_jacobian.argtypes = [_d, _d, _d, real, _d]
+            L.or_cns_riemann.argtypes = [_d, _d, _d, _P(Pt), _d]
+            L.or_cns_element_gradient.argtypes = [ctypes.c_void_p, _d, ctypes.c_int64, _d]
+            L.or_cns_residual.argtypes = [ctypes.c_void_p, _d, _d, ctypes.c_int64, _i64]
+            L.or_cns_rk_step.argtypes = [ctypes.c_void_p, _d, _d, real, ctypes.c_int]
+            L.or_cns_conservation.argtypes = [ctypes.c_void_p, _d, _d]
             _libs[extended] = L
     return _libs[extended]
 
@@ -116,10 +126,11 @@ def _f64(a):
 
 
 def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0,
-           split=0):
+           split=0, gamma=1.4, prandtl=0.72, prandtl_t=0.9):
     p = Params()
     p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
     p.closure, p.riemann, p.mixed_face, p.split = closure, riemann, mixed_face, split
+    p.gamma, p.prandtl, p.prandtl_t = gamma, prandtl, prandtl_t
     for i in range(4):
         p.inflow[i] = inflow[i]
     return p
@@ -205,6 +216,32 @@ def abs_jacobian(q, n, c0sq):
     if lib().or_abs_jacobian(_ptr(_f64(q), _d), _ptr(_f64(n), _d), c0sq, _ptr(A, _d)):
         raise ValueError(lib().or_error().decode())
     return A
+
+
+def cns_flux(u, n, gamma=1.4):
+    out = np.zeros(5)
+    lib().or_cns_flux(_ptr(_f64(u), _d), _ptr(_f64(n), _d), gamma, _ptr(out, _d))
+    return out
+
+
+def cns_jacobian(u, n, gamma=1.4):
+    A = np.zeros((5, 5))
+    lib().or_cns_jacobian(_ptr(_f64(u), _d), _ptr(_f64(n), _d), gamma, _ptr(A, _d))
+    return A
+
+
+def cns_roe_abs_jacobian(uL, uR, n, gamma=1.4):
+    A = np.zeros((5, 5))
+    if lib().or_cns_roe_abs_jacobian(_ptr(_f64(uL), _d), _ptr(_f64(uR), _d), _ptr(_f64(n), _d), gamma, _ptr(A, _d)):
+        raise ValueError("no Roe average (non-positive density or sound speed)")
+    return A
+
+
+def cns_riemann(uL, uR, n, prm):
+    out = np.zeros(5)
+    if lib().or_cns_riemann(_ptr(_f64(uL), _d), _ptr(_f64(uR), _d), _ptr(_f64(n), _d), ctypes.byref(prm), _ptr(out, _d)):
+        raise ValueError("Riemann solver failed")
+    return out
 
 
 def riemann(qm, qp, n, prm):
@@ -336,6 +373,48 @@ class Mesh:
         R = self._r(R)
         self._L.or_conservation(self.h, _ptr(R, self._ptr_t), _ptr(out, self._ptr_t))
         return out.astype(np.float64)
+
+    # ---- compressible form (App. A): state u [5][total_nodes] ------------------------------
+
+    def cns_residual(self, u, sel=None, out=None):
+        u = self._r(u)
+        assert u.shape == (5, self.total)
+        R = np.zeros((5, self.total), dtype=self._real)
+        if sel is None:
+            rc = self._L.or_cns_residual(self.h, _ptr(u, self._ptr_t), _ptr(R, self._ptr_t), 0, None)
+        else:
+            s = np.ascontiguousarray(sel, dtype=np.int64)
+            rc = self._L.or_cns_residual(self.h, _ptr(u, self._ptr_t), _ptr(R, self._ptr_t), s.size, _ptr(s, _i64))
+        if rc:
+            raise RuntimeError(self._L.or_error().decode())
+        if out is None:
+            return R.astype(np.float64)
+        idx = np.concatenate([np.arange(self.offsets[e], self.offsets[e + 1]) for e in np.asarray(sel)])
+        out[:, idx] = R[:, idx]
+        return out
+
+    def cns_rk_step(self, u, g, dt, nsteps=1):
+        """In place on FP64 arrays u, g [5][total_nodes]."""
+        assert u.dtype == np.float64 and g.dtype == np.float64 and u.flags.c_contiguous and g.flags.c_contiguous
+        ur, gr = self._r(u), self._r(g)
+        if self._L.or_cns_rk_step(self.h, _ptr(ur, self._ptr_t), _ptr(gr, self._ptr_t), dt, nsteps):
+            raise RuntimeError(self._L.or_error().decode())
+        if self.extended:
+            u[...] = ur
+            g[...] = gr
+
+    def cns_conservation(self, R):
+        out = np.zeros(5, dtype=self._real)
+        R = self._r(R)
+        self._L.or_cns_conservation(self.h, _ptr(R, self._ptr_t), _ptr(out, self._ptr_t))
+        return out.astype(np.float64)
+
+    def cns_element_gradient(self, u, e):
+        n = int(self.orders[e]) + 1
+        G = np.zeros((4, 3, n ** 3), dtype=self._real)
+        if self._L.or_cns_element_gradient(self.h, _ptr(self._r(u), self._ptr_t), e, _ptr(G, self._ptr_t)):
+            raise RuntimeError(self._L.or_error().decode())
+        return G.astype(np.float64)
 
     def element_nodes(self, e):
         return slice(int(self.offsets[e]), int(self.offsets[e + 1]))

@@ -482,6 +482,23 @@ def channel_walls(n=8, order=4, wall=3, wavy=0.08):
                     np.full(n ** 3, order, np.int8), flags, default_params(nu=1e-3), seed, 1e-3, 10, state)
 
 
+def cns_state(xyz, seed, period=1.0):
+    """Conservative state (rho, rho v1, rho v2, rho v3, rho e) of the compressible form for a
+    mesh periodic with the given period: smooth fields with seeded phases, density 1 +- 0.2,
+    velocity ~0.5 and total energy ~20, so the pressure stays positive (Mach ~0.25 at gamma
+    1.4). Returns [5][T]."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0.0, 2 * np.pi, 8)
+    k = 2 * np.pi / period
+    x, y, z = np.asarray(xyz)
+    rho = 1.0 + 0.2 * np.sin(k * x + ph[0]) * np.cos(k * y + ph[1]) * np.sin(k * z + ph[2])
+    v1 = 0.5 + 0.3 * np.sin(k * x + ph[3]) * np.cos(k * y)
+    v2 = -0.3 * np.cos(k * x) * np.sin(k * y + ph[4]) + 0.2
+    v3 = 0.2 * np.sin(k * z + ph[5]) * np.cos(k * x)
+    E = 20.0 + 0.5 * np.cos(2 * k * x + ph[6]) * np.cos(k * y + ph[7])
+    return np.ascontiguousarray(np.stack([rho, rho * v1, rho * v2, rho * v3, E]))
+
+
 WORKLOADS = {
     "tgv_4x4x4_n3": tgv_4x4x4_n3,
     "wake_16x16x16_n4": wake_16x16x16_n4,

@@ -1,0 +1,250 @@
+"""Pins of the compressible form of the oracle (App. A): state u = (rho, rho v, rho e), Roe
+flux, BR1 on (v, T), heat flux, Vreman/Smagorinsky eddy viscosity mu_t = rho nu_t.
+
+Pinned against what the mathematics fixes: the flux Jacobian against finite differences and
+the Euler flux's homogeneity F(u) = A(u) u; the Roe property A(u_roe)(uR - uL) = F(uR) - F(uL)
+with the textbook Roe averages, and |A_roe| against numpy's eigen-decomposition of that
+matrix; consistency, conservation and supersonic upwinding of the numerical fluxes; free
+stream and conservation of the residual on curved, re-oriented, mixed-flag meshes; Euler = NS
+without viscosity; invariance under element re-numbering; spectral convergence to the
+symbolic (sympy) residual of the compressible Navier-Stokes equations with heat flux."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2403_05463_gb300 import workloads as wl
+
+GAMMA = 1.4
+
+
+def _state(rng, n=1):
+    rho = rng.uniform(0.5, 2.0, n)
+    v = rng.normal(scale=0.8, size=(3, n))
+    p = rng.uniform(0.5, 3.0, n)
+    E = p / (GAMMA - 1) + 0.5 * rho * (v ** 2).sum(0)
+    return np.vstack([rho, rho * v, E]).T.squeeze()
+
+
+def _unit(rng):
+    n = rng.normal(size=3)
+    return n / np.linalg.norm(n)
+
+
+def _roe_state(uL, uR):
+    """A conservative state with the Roe-averaged velocity and enthalpy (textbook definition)."""
+    def vh(u):
+        v = u[1:4] / u[0]
+        p = (GAMMA - 1) * (u[4] - 0.5 * u[0] * v @ v)
+        return v, (u[4] + p) / u[0]
+    vL, HL = vh(uL)
+    vR, HR = vh(uR)
+    sL, sR = np.sqrt(uL[0]), np.sqrt(uR[0])
+    v = (sL * vL + sR * vR) / (sL + sR)
+    H = (sL * HL + sR * HR) / (sL + sR)
+    rho = sL * sR
+    E = (rho * H + (GAMMA - 1) * 0.5 * rho * v @ v) / GAMMA
+    return np.concatenate([[rho], rho * v, [E]])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_jacobian_finite_differences_and_homogeneity(seed):
+    rng = np.random.default_rng(seed)
+    u, n = _state(rng), _unit(rng)
+    A = orc.cns_jacobian(u, n, GAMMA)
+    h = 1e-6
+    Afd = np.zeros((5, 5))
+    for j in range(5):
+        e = np.zeros(5)
+        e[j] = h * max(1.0, abs(u[j]))
+        Afd[:, j] = (orc.cns_flux(u + e, n, GAMMA) - orc.cns_flux(u - e, n, GAMMA)) / (2 * e[j])
+    np.testing.assert_allclose(A, Afd, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(A @ u, orc.cns_flux(u, n, GAMMA), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_roe_property_and_eigen_decomposition(seed):
+    rng = np.random.default_rng(10 + seed)
+    uL, uR, n = _state(rng), _state(rng), _unit(rng)
+    A = orc.cns_jacobian(_roe_state(uL, uR), n, GAMMA)
+    dF = orc.cns_flux(uR, n, GAMMA) - orc.cns_flux(uL, n, GAMMA)
+    np.testing.assert_allclose(A @ (uR - uL), dF, rtol=1e-12, atol=1e-12)
+    lam, V = np.linalg.eig(A)
+    absA = (V * np.abs(lam)) @ np.linalg.inv(V)
+    np.testing.assert_allclose(orc.cns_roe_abs_jacobian(uL, uR, n, GAMMA), absA.real, rtol=1e-10, atol=1e-11)
+    # eigenvalues vn -+ a and vn three times at the Roe state
+    assert np.allclose(np.sort(lam.real)[1:4], np.sort(lam.real)[2], atol=1e-10)
+
+
+@pytest.mark.parametrize("riemann", [0, 1])
+def test_numerical_flux_consistency_conservation_and_upwinding(riemann):
+    rng = np.random.default_rng(20)
+    prm = orc.params(riemann=riemann, gamma=GAMMA)
+    for _ in range(5):
+        u, uR, n = _state(rng), _state(rng), _unit(rng)
+        np.testing.assert_allclose(orc.cns_riemann(u, u, n, prm), orc.cns_flux(u, n, GAMMA), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(orc.cns_riemann(u, uR, n, prm), -orc.cns_riemann(uR, u, -n, prm), rtol=1e-12,
+                                   atol=1e-12)
+    if riemann == 0:
+        # supersonic along n on both sides (and at the Roe state): the Roe flux is the left flux
+        n = np.array([1.0, 0.0, 0.0])
+        def sup(rho, vx, p):
+            return np.array([rho, rho * vx, 0.1 * rho, 0.0, p / (GAMMA - 1) + 0.5 * rho * (vx ** 2 + 0.01)])
+        uL, uR = sup(1.0, 3.0, 1.0), sup(1.2, 3.2, 1.1)
+        np.testing.assert_allclose(orc.cns_riemann(uL, uR, n, prm), orc.cns_flux(uL, n, GAMMA), rtol=1e-13)
+
+
+def _cns_params(**kw):
+    base = dict(nu=0.0, cs=0.1, cv=0.07, closure=1, riemann=0, gamma=GAMMA, prandtl=0.72, prandtl_t=0.9)
+    base.update(kw)
+    return orc.params(**base)
+
+
+def _curved_periodic(n=3, order=3, seed=0, rotate=True, flags_p=0.5):
+    w = wl.padapt_32x32x32(n=n, amp=0.05)
+    rng = np.random.default_rng(seed)
+    flags = (rng.uniform(size=n ** 3) < flags_p).astype(np.uint8)
+    mesh = w.mesh
+    if rotate:
+        mesh, _ = wl.rotate_elements(mesh, seed + 7)
+    return dataclasses.replace(w, mesh=mesh, orders=np.full(n ** 3, order, np.int8), flags=flags)
+
+
+def _mesh(w, prm):
+    m = w.mesh
+    return orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, prm, m.bc_tag)
+
+
+def test_free_stream_is_preserved_on_curved_reoriented_meshes():
+    w = _curved_periodic(order=4, seed=1)
+    M = _mesh(w, _cns_params(nu=1e-2))
+    u = np.zeros((5, M.total))
+    rho, v, p = 1.3, np.array([0.4, -0.2, 0.3]), 2.0
+    u[0], u[1:4] = rho, (rho * v)[:, None]
+    u[4] = p / (GAMMA - 1) + 0.5 * rho * v @ v
+    R = M.cns_residual(u)
+    assert np.abs(R).max() < 1e-12
+
+
+@pytest.mark.parametrize("closure,riemann,mixed_face", [(1, 0, 0), (0, 1, 1)])
+def test_conservation_on_periodic_mixed_meshes(closure, riemann, mixed_face):
+    w = _curved_periodic(order=3, seed=2)
+    M = _mesh(w, _cns_params(nu=5e-3, closure=closure, riemann=riemann, mixed_face=mixed_face))
+    u = wl.cns_state(M.node_coords(), seed=3)
+    R = M.cns_residual(u)
+    s = M.cns_conservation(R)
+    J_scale = np.abs(R).max()
+    assert np.all(np.abs(s) < 1e-12 * J_scale * 8.0), s  # domain volume 1, |R| scale
+    assert np.abs(R).max() > 1e-3  # a non-trivial residual
+
+
+def test_euler_equals_ns_without_viscosity():
+    w = _curved_periodic(order=3, seed=3)
+    M0 = _mesh(dataclasses.replace(w, flags=np.zeros_like(w.flags)), _cns_params())
+    M1 = _mesh(dataclasses.replace(w, flags=np.ones_like(w.flags)), _cns_params(cs=0.0, closure=0))
+    u = wl.cns_state(M0.node_coords(), seed=4)
+    R0, R1 = M0.cns_residual(u), M1.cns_residual(u)
+    assert np.abs(R1 - R0).max() <= 1e-12 * np.abs(R0).max()
+    # and viscosity does matter
+    M2 = _mesh(dataclasses.replace(w, flags=np.ones_like(w.flags)), _cns_params(nu=1e-2))
+    assert np.abs(M2.cns_residual(u) - R0).max() > 1e-6
+
+
+def test_invariance_under_element_renumbering():
+    w = _curved_periodic(order=3, seed=5, rotate=False)
+    prm = _cns_params(nu=1e-2)
+    rmesh, rot_of = wl.rotate_elements(w.mesh, 55)
+    A = _mesh(w, prm)
+    B = _mesh(dataclasses.replace(w, mesh=rmesh), prm)
+    xa = A.node_coords()
+    perm = np.zeros(A.total, dtype=np.int64)
+    for e in range(A.ne):
+        n = int(w.orders[e]) + 1
+        idx = wl.rotation_index_map(wl.CUBE_ROTATIONS[rot_of[e]], n)
+        perm[B.offsets[e]:B.offsets[e + 1]] = A.offsets[e] + idx
+    np.testing.assert_allclose(B.node_coords(), xa[:, perm], atol=1e-13)
+    u = wl.cns_state(xa, seed=6)
+    Ra, Rb = A.cns_residual(u), B.cns_residual(u[:, perm])
+    assert np.abs(Rb - Ra[:, perm]).max() <= 1e-12 * np.abs(Ra).max()
+
+
+def _exact_cns_residual(xyz, mu, prandtl):
+    """-div F_e + div F_v of App. A for a smooth periodic state (laminar, constant mu,
+    kappa = c_p mu / Pr, T = p / rho), evaluated symbolically (sympy)."""
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    X = [x, y, z]
+    rho = 1 + sp.Rational(1, 5) * sp.sin(x) * sp.cos(y) * sp.sin(z)
+    v = [sp.sin(x) * sp.cos(y) * sp.cos(z), -sp.cos(x) * sp.sin(y) * sp.cos(z), sp.Rational(3, 10) * sp.sin(z) * sp.cos(x)]
+    p = 10 + (sp.cos(2 * x) + sp.cos(2 * y)) * (sp.cos(2 * z) + 2) / 16
+    g = sp.Rational(7, 5)
+    E = p / (g - 1) + rho * sum(vi ** 2 for vi in v) / 2
+    T = p / rho
+    cp = g / (g - 1)
+    kappa = cp * mu / prandtl
+    G = [[sp.diff(v[c], X[k]) for k in range(3)] for c in range(3)]
+    div = G[0][0] + G[1][1] + G[2][2]
+    tau = [[mu * (G[c][k] + G[k][c]) - (sp.Rational(2, 3) * mu * div if c == k else 0) for k in range(3)]
+           for c in range(3)]
+    Fe = [[rho * v[k] for k in range(3)]]
+    for c in range(3):
+        Fe.append([rho * v[c] * v[k] + (p if c == k else 0) for k in range(3)])
+    Fe.append([(E + p) * v[k] for k in range(3)])
+    Fv = [[0, 0, 0]] + [[tau[c][k] for k in range(3)] for c in range(3)]
+    Fv.append([sum(v[j] * tau[j][k] for j in range(3)) + kappa * sp.diff(T, X[k]) for k in range(3)])
+    R = [sum(-sp.diff(Fe[i][k], X[k]) + sp.diff(Fv[i][k], X[k]) for k in range(3)) for i in range(5)]
+    U = [rho] + [rho * vi for vi in v] + [E]
+    fR = sp.lambdify((x, y, z), R, "numpy")
+    fU = sp.lambdify((x, y, z), U, "numpy")
+    shape = xyz[0].shape
+    Rex = np.array([np.broadcast_to(np.asarray(o, dtype=float), shape) for o in fR(*xyz)])
+    u = np.array([np.broadcast_to(np.asarray(o, dtype=float), shape) for o in fU(*xyz)])
+    return u, Rex
+
+
+def test_spectral_convergence_to_the_symbolic_residual():
+    pytest.importorskip("sympy")
+    errs = []
+    for N in range(2, 8):
+        w = wl.tgv_4x4x4_n3(order=N)
+        w = dataclasses.replace(w, flags=np.ones(w.n_elem, np.uint8))
+        M = _mesh(w, _cns_params(nu=0.05, cs=0.0, closure=0))
+        u, Rex = _exact_cns_residual(M.node_coords(), 0.05, 0.72)
+        R = M.cns_residual(u)
+        errs.append(np.sqrt(((R - Rex) ** 2).sum() / (Rex ** 2).sum()))
+    errs = np.array(errs)
+    assert np.all(np.diff(np.log(errs)) < -0.5), errs
+    assert errs[-1] < 1e-3, errs
+
+
+def test_rk_step_conserves_and_keeps_a_uniform_state():
+    w = _curved_periodic(order=2, seed=8)
+    M = _mesh(w, _cns_params(nu=1e-2))
+    u = wl.cns_state(M.node_coords(), seed=9)
+    g = np.zeros_like(u)
+    J = np.zeros(M.total)
+    for e in range(M.ne):
+        Je, _ = M.element_geometry(e)
+        J[M.element_nodes(e)] = Je
+    n = int(w.orders[0]) + 1
+    x, wq = orc.lgl(n - 1)
+    W = np.einsum('i,j,k->kji', wq, wq, wq).ravel()
+    Wall = np.tile(W, M.ne)
+    before = (Wall * J * u).sum(axis=1)
+    M.cns_rk_step(u, g, 1e-3, 2)
+    after = (Wall * J * u).sum(axis=1)
+    np.testing.assert_allclose(after, before, rtol=1e-12)
+
+
+def test_boundaries_and_nonconforming_faces_are_rejected():
+    w = wl.wake_16x16x16_n4(n=3, order=2)
+    M = _mesh(w, _cns_params())
+    with pytest.raises(RuntimeError):
+        M.cns_residual(np.ones((5, M.total)))
+    w2 = _curved_periodic(order=3, seed=10)
+    o = w2.orders.copy()
+    o[0] = 4
+    M2 = _mesh(dataclasses.replace(w2, orders=o), _cns_params())
+    with pytest.raises(RuntimeError):
+        M2.cns_residual(np.ones((5, M2.total)))
