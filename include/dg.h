@@ -16,8 +16,11 @@
  *   - Sec. 2.3 (last paragraph): low-storage explicit third-order Runge-Kutta.
  *   - Sec. 3.2: local p-adaptation, one polynomial order per element, p-nonconforming faces.
  *
- * State: q = (p, u, v, w), rho = 1. All state arrays are FP64, structure-of-arrays
- * [4][total_nodes]: variable v of global node i lives at q[v * total_nodes + i]. Element e
+ * State: q = (p, u, v, w), rho = 1 (dg_params.model 0), or the compressible conservative
+ * state u = (rho, rho v, rho e) of App. A (model 1). All state arrays are FP64, structure-of-
+ * arrays [4][total_nodes] (model 0) or [5][total_nodes] (model 1; wherever this header says
+ * [4][...] for q, g or R, read [5][...] under model 1): variable v of global node i lives at
+ * q[v * total_nodes + i]. Element e
  * owns nodes [elem_offset[e], elem_offset[e] + (N_e + 1)^3), lexicographic with xi_1
  * fastest, then xi_2, then xi_3 (see dg_get_layout).
  *
@@ -98,8 +101,22 @@ typedef struct {
                        kinetic-energy-preserving split form: along each direction
                        sum_m 2 D_im F#(q_i, q_m) with F# = (c0^2 U, {{u}} U + {{p}} {{Ja}}),
                        U = {{Ja}}.{{u}}, {{.}} the two-node average                       */
-  int reserved;     /* must be 0                                                       */
+  int model;        /* governing equations: 0 incompressible flow in artificial-
+                       compressibility form, state q = (p, u, v, w), rho = 1; 1 the
+                       compressible Navier-Stokes equations of App. A, conservative state
+                       u = (rho, rho v1, rho v2, rho v3, rho e), ideal gas with unit gas
+                       constant (p = (gamma - 1)(rho e - rho |v|^2 / 2), T = p / rho), nu the
+                       dynamic viscosity mu, eddy viscosity mu_t = rho nu_t of the closure,
+                       heat flux kappa grad T with kappa = c_p (mu / Pr + mu_t / Pr_t),
+                       c_p = gamma / (gamma - 1), BR1 on (v, T). Model 1 runs in FP64
+                       (precision 0) with the standard volume term (split 0) on meshes whose
+                       faces are all interior or periodic and conforming (both sides of one
+                       order); other meshes give DG_ERR_UNSUPPORTED. Its state, RK register
+                       and residual arrays have 5 planes, [5][total_nodes].               */
   double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
+  double gamma;     /* model 1: ratio of specific heats (> 1)                           */
+  double prandtl;   /* model 1: laminar Prandtl number (> 0)                            */
+  double prandtl_t; /* model 1: turbulent Prandtl number (> 0)                          */
 } dg_params;
 
 /* Build the mesh topology (face matching, orientations, periodic pairs), the geometry
@@ -122,7 +139,7 @@ dg_status dg_set_orders(dg_ctx* ctx, const int8_t* orders);
  * onto the new Gauss-Lobatto nodes where the order grew or stayed (exact for the old
  * polynomial), the L2 projection in reference coordinates where it dropped (keeps each
  * element's reference-space integral), applied along each direction. Asynchronous on
- * `stream`. DG_ERR_STATE before any dg_set_orders. */
+ * `stream`. DG_ERR_STATE before any dg_set_orders; DG_ERR_UNSUPPORTED under model 1. */
 dg_status dg_project_state(dg_ctx* ctx, const double* q_old_dev, double* q_new_dev, void* stream);
 
 /* Per-element flag (host array, length n_elem): 0 Euler, 1 Navier-Stokes + LES (Sec. 2.3).
@@ -161,10 +178,11 @@ dg_status dg_residual_host(dg_ctx* ctx, const double* q_host, double* R_host, vo
 dg_status dg_rk_step_host(dg_ctx* ctx, double* q_host, double* g_host, double t, double dt, int nsteps,
                           void* stream);
 
-/* out_host[v] = sum_e sum_nodes w_i w_j w_k J R_v (FP64, deterministic order). Synchronises
- * the stream and also reports a pending device error. On a periodic mesh the exact
+/* out_host[v] = sum_e sum_nodes w_i w_j w_k J R_v (FP64, deterministic order) for every
+ * variable of the model: out_host holds 4 values (model 0) or 5 (model 1). Synchronises the
+ * stream and also reports a pending device error. On a periodic mesh the exact
  * discretisation conserves every variable, so these sums vanish to rounding. */
-dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double out_host[4], void* stream);
+dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double* out_host, void* stream);
 
 /* Launch-shape autotuner of the reduced-precision passes (precision 1). For every bucket of
  * the current mesh -- one per (polynomial order, geometry kind) -- it times the candidate
@@ -198,7 +216,8 @@ dg_status dg_autotune(dg_ctx* ctx, const char* cache_path, char* report, int rep
  * sums: serialise them. The first call on a device looks up the array's device address (which
  * can load the library's device code), so make that first call before any stream capture.
  * Errors: DG_ERR_ARG for a NULL pointer or a mesh of more than
- * DG_CONSERVATION_NOALLOC_MAX_ELEMS elements; DG_ERR_CUDA if the look-up or a launch fails.
+ * DG_CONSERVATION_NOALLOC_MAX_ELEMS elements; DG_ERR_UNSUPPORTED under model 1; DG_ERR_CUDA
+ * if the look-up or a launch fails.
  * The device error word is not read (see dg_check_device). The final sum runs in a fixed
  * order on the device, so it may differ from dg_conservation's host sum by rounding. */
 dg_status dg_conservation_noalloc(dg_ctx* ctx, const double* R_dev, double* out_dev, void* stream);
@@ -232,7 +251,7 @@ typedef struct {
  * Asynchronous on `stream`. Errors: DG_ERR_ARG for a NULL ctx, q_dev or gmm, no output, a
  * non-positive or non-finite weight, a covariance that is not symmetric (to 1e-12 of its
  * largest entry) or not positive definite, viscous outside {0, 1}, reserved != 0;
- * DG_ERR_CUDA if a launch fails. */
+ * DG_ERR_UNSUPPORTED under model 1 (q holds momenta there); DG_ERR_CUDA if a launch fails. */
 dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm, uint8_t* flags_dev,
                             double* pbar_dev, double* features_dev, void* stream);
 

@@ -1,0 +1,527 @@
+// dg_cns.cu -- sm_103a kernels of the compressible form (arXiv 2403.05463, App. A), FP64.
+//
+// State u = (rho, rho v1, rho v2, rho v3, rho e), ideal gas with unit gas constant:
+// p = (gamma - 1)(rho e - rho |v|^2 / 2), T = p / rho, H = (rho e + p) / rho. Flag 0 elements
+// solve the Euler equations, flag 1 the Navier-Stokes equations with the eddy viscosity
+// mu_t = rho nu_t of the selected closure and the heat flux kappa grad T,
+// kappa = c_p (mu / Pr + mu_t / Pr_t), c_p = gamma / (gamma - 1). Conforming faces between
+// elements of one order (interior or periodic); the host rejects other meshes.
+//
+// Per residual evaluation / Runge-Kutta stage (the passes of the incompressible FP64 path with
+// five variables):
+//   traces   : the 5 conservative face values of every element into the trace buffer;
+//   viscous  (NS elements): BR1 gradient of phi = (v1, v2, v3, T) with the average {{phi}} on
+//              faces, eddy viscosity, stress, heat flux, contravariant viscous flux of momentum
+//              and energy, its divergence (J r_v) and the outward traces Fv . S;
+//   inviscid (all elements): contravariant Euler flux and its divergence from shared memory,
+//              Roe (or LLF) fluctuation and the BR1 viscous face average, + J r_v, then
+//              R = (1/J)(...) or the in-place low-storage RK3 update (next-stage traces too).
+// Strong form on Gauss-Lobatto nodes, equal to the weak form of App. B, Eq. NS4 by summation
+// by parts:
+//   J R = -sum_d D_d (Ftil_e^d - Ftil_v^d) - sum_faces (1/w_end) [(F_e* - F_v*) . S - (Ftil_e - Ftil_v)_out]
+#include "dg_device.cuh"
+
+namespace dgk {
+
+__constant__ double c_Dc[NP][NP * NP];  // Gauss-Lobatto derivative matrices D[N][i*n+m]
+__constant__ double c_w0c[NP];          // end weights w[N][0]
+// Williamson 2N-storage RK3 (the paper's low-storage third-order scheme, Sec. 2.3)
+__constant__ double c_rkAc[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+__constant__ double c_rkBc[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+cudaError_t upload_ops_cns(const Ops1D& ops) {
+  cudaError_t r = cudaMemcpyToSymbol(c_Dc, ops.D, sizeof(ops.D));
+  if (r != cudaSuccess) return r;
+  double w0[NP];
+  for (int N = 0; N < NP; ++N) w0[N] = ops.w[N][0];
+  return cudaMemcpyToSymbol(c_w0c, w0, sizeof(w0));
+}
+
+struct Prim {
+  double rho, v[3], p;
+};
+
+__device__ __forceinline__ Prim prim(const double u[5], double gamma) {
+  Prim P;
+  P.rho = u[0];
+  const double ir = 1.0 / u[0];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) P.v[c] = u[1 + c] * ir;
+  P.p = (gamma - 1.0) * (u[4] - 0.5 * (u[1] * P.v[0] + u[2] * P.v[1] + u[3] * P.v[2]));
+  return P;
+}
+
+// Fluctuation F*(uL, uR) . n - F(uL) . n. Roe (riemann == 0) in wave-strength form with the
+// Roe averages (sqrt(rho)-weighted v and H, a^2 = (gamma - 1)(H - |v|^2/2)): the jump uR - uL
+// is split into two acoustic waves (vn -+ a), an entropy wave and the shear part (vn), each
+// weighted by |lambda|. LLF: the largest |vn| + a of the two sides.
+__device__ __forceinline__ void cns_fluct(const double uL[5], const double uR[5], const double nh[3], double gamma,
+                                          int riemann, double fx[5]) {
+  const Prim L = prim(uL, gamma), R = prim(uR, gamma);
+  const double vnL = L.v[0] * nh[0] + L.v[1] * nh[1] + L.v[2] * nh[2];
+  const double vnR = R.v[0] * nh[0] + R.v[1] * nh[1] + R.v[2] * nh[2];
+  double dF[5];  // F(uR).n - F(uL).n
+  dF[0] = uR[0] * vnR - uL[0] * vnL;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dF[1 + c] = (uR[1 + c] * vnR + R.p * nh[c]) - (uL[1 + c] * vnL + L.p * nh[c]);
+  dF[4] = (uR[4] + R.p) * vnR - (uL[4] + L.p) * vnL;
+  if (riemann == 0) {
+    const double sL = sqrt(L.rho), sR = sqrt(R.rho), inv = 1.0 / (sL + sR);
+    const double HL = (uL[4] + L.p) / L.rho, HR = (uR[4] + R.p) / R.rho;
+    double v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = (sL * L.v[c] + sR * R.v[c]) * inv;
+    const double H = (sL * HL + sR * HR) * inv;
+    const double q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double a2 = (gamma - 1.0) * (H - 0.5 * q2), a = sqrt(a2);
+    const double vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
+    const double rho = sL * sR;
+    const double dr = R.rho - L.rho, dp = R.p - L.p;
+    double dv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dv[c] = R.v[c] - L.v[c];
+    const double dvn = dv[0] * nh[0] + dv[1] * nh[1] + dv[2] * nh[2];
+    const double al1 = (dp - rho * a * dvn) / (2.0 * a2);  // acoustic, vn - a
+    const double al5 = (dp + rho * a * dvn) / (2.0 * a2);  // acoustic, vn + a
+    const double al2 = dr - dp / a2;                       // entropy, vn
+    const double l1 = fabs(vn - a), l2 = fabs(vn), l5 = fabs(vn + a);
+    const double w1 = l1 * al1, w5 = l5 * al5;
+    double d[5];
+    d[0] = w1 + l2 * al2 + w5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      d[1 + c] = w1 * (v[c] - a * nh[c]) + l2 * (al2 * v[c] + rho * (dv[c] - dvn * nh[c])) + w5 * (v[c] + a * nh[c]);
+    const double vdv = v[0] * dv[0] + v[1] * dv[1] + v[2] * dv[2];
+    d[4] = w1 * (H - a * vn) + l2 * (al2 * 0.5 * q2 + rho * (vdv - vn * dvn)) + w5 * (H + a * vn);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) fx[k] = 0.5 * (dF[k] - d[k]);
+  } else {
+    const double lam = fmax(fabs(vnL) + sqrt(gamma * L.p / L.rho), fabs(vnR) + sqrt(gamma * R.p / R.rho));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) fx[k] = 0.5 * (dF[k] - lam * (uR[k] - uL[k]));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// traces
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void k_traces_cns(DevMesh M, const int32_t* __restrict__ list, int count, const double* __restrict__ u) {
+  constexpr int n = N + 1, n2 = n * n, per = 6 * n2;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)count * per) return;
+  const int le = (int)(gid / per), r = (int)(gid % per);
+  const int f = r / n2, ab = r % n2;
+  const int e = list[le];
+  const int64_t src = M.elem_off[e] + face_node(f, n, ab % n, ab / n);
+  const int64_t dst = M.tr_off[e] + f * n2 + ab;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) M.Tq[v * M.tr_total + dst] = __ldg(&u[v * M.total + src]);
+}
+
+// ---------------------------------------------------------------------------------------
+// viscous pass (NS elements)
+// ---------------------------------------------------------------------------------------
+template <int N, bool CURVED>
+__global__ void __launch_bounds__(Shape<N>::threads)
+    k_viscous_cns(DevMesh M, const int32_t* __restrict__ list, int count, const double* __restrict__ u) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ double sm[];
+  double* sD = sm;                                 // n*n
+  double* sP = sD + NP * NP;                       // EPB * 4 * n3: phi = (v1, v2, v3, T)
+  double* sJa = sP + EPB * 4 * n3;                 // EPB * 9 * n3 (curved only)
+  double* sF = sJa + (CURVED ? EPB * 9 * n3 : 0);  // EPB * 12 * n3: Ftil_v[d][4]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_Dc[N][t];
+  int le = tid / n3;
+  const int p = tid % n3;
+  const int slot = blockIdx.x * EPB + le;
+  const bool active = (le < EPB) && (slot < count);
+  if (le >= EPB) le = EPB - 1;
+  const int e = active ? list[slot] : 0;
+  const int64_t off = active ? M.elem_off[e] : 0;
+  double* P = sP + le * 4 * n3;
+  double* JA = sJa + le * 9 * n3;
+  double* F = sF + le * 12 * n3;
+  const double gamma = M.gamma;
+  double Ja[9], invJ = 0.0, uu[5] = {1.0, 0.0, 0.0, 0.0, 1.0}, ph[4] = {0.0, 0.0, 0.0, 0.0};
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) uu[v] = __ldg(&u[v * M.total + off + p]);
+    const Prim Q = prim(uu, gamma);
+    ph[0] = Q.v[0], ph[1] = Q.v[1], ph[2] = Q.v[2], ph[3] = Q.p / Q.rho;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) P[c * n3 + p] = ph[c];
+    if (CURVED) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        Ja[k] = __ldg(&M.geo[k * M.total + off + p]);
+        JA[k * n3 + p] = Ja[k];
+      }
+      invJ = 1.0 / __ldg(&M.geo[9 * M.total + off + p]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
+      invJ = M.ec[e].invJ;
+    }
+  }
+  __syncthreads();
+  const int ii[3] = {p % n, (p / n) % n, p / n2};
+  const int str[3] = {1, n, n2};
+  if (active) {
+    double G[4][3];  // G[c][k] = d phi_c / d x_k
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[c][k] = 0.0;
+    // volume part: J G_ck = sum_d D_d (Ja^d_k phi_c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int base = p - ii[d] * str[d];
+      if (!CURVED) {
+        double dp[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const double dm = sD[ii[d] * n + m];
+          const int pm = base + m * str[d];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dp[c] += dm * P[c * n3 + pm];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) G[c][k] += Ja[d * 3 + k] * dp[c];
+      } else {
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const double dm = sD[ii[d] * n + m];
+          const int pm = base + m * str[d];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double dj = dm * JA[(d * 3 + k) * n3 + pm];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) G[c][k] += dj * P[c * n3 + pm];
+          }
+        }
+      }
+    }
+    // BR1 lifting on the faces this node lies on: (1/w_end) ({{phi}} - phi) S
+    const double invw = 1.0 / c_w0c[N];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (ii[d] != 0 && ii[d] != N) continue;
+      const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+      const double sg = side ? 1.0 : -1.0;
+      const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+      const FaceLink L = M.link[e * 6 + f];
+      if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
+        atomicCAS(&M.err[0], 0, 5);
+        atomicCAS(&M.err[1], 0, 10);
+        continue;
+      }
+      int a1, b1;
+      inv_orient(L.orient, N, a, b, a1, b1);
+      const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+      double un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) un[v] = M.Tq[v * M.tr_total + ns];
+      const Prim Q = prim(un, gamma);
+      const double jump[4] = {Q.v[0] - ph[0], Q.v[1] - ph[1], Q.v[2] - ph[2], Q.p / Q.rho - ph[3]};
+      const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[c][k] += invw * 0.5 * jump[c] * Sv[k];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[c][k] *= invJ;
+    // eddy viscosity, stress, heat flux
+    const double Gv[3][3] = {{G[0][0], G[0][1], G[0][2]}, {G[1][0], G[1][1], G[1][2]}, {G[2][0], G[2][1], G[2][2]}};
+    const double mut = uu[0] * eddy_visc(Gv, M.ec[e].delta, M.closure, M.cs, M.cv);
+    const double mu = M.nu + mut;
+    const double kappa = gamma / (gamma - 1.0) * (M.nu / M.prandtl + mut / M.prandtl_t);
+    const double tr = Gv[0][0] + Gv[1][1] + Gv[2][2];
+    double fv[4][3];  // physical viscous flux rows: momentum 1..3, energy
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fv[c][k] = mu * (Gv[c][k] + Gv[k][c]) - (c == k ? (2.0 / 3.0) * mu * tr : 0.0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fv[3][k] = ph[0] * fv[0][k] + ph[1] * fv[1][k] + ph[2] * fv[2][k] + kappa * G[3][k];
+    // contravariant viscous flux Ftil_v^d = sum_k Ja^d_k fv_k
+    double Fc[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Fc[d][v] = Ja[d * 3] * fv[v][0] + Ja[d * 3 + 1] * fv[v][1] + Ja[d * 3 + 2] * fv[v][2];
+        F[(d * 4 + v) * n3 + p] = Fc[d][v];
+      }
+    // outward viscous flux traces Fv . S = sigma Ftil_v^d
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (ii[d] != 0 && ii[d] != N) continue;
+      const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+      const double sg = side ? 1.0 : -1.0;
+      const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+      const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) M.Tv[v * M.tr_total + ms] = sg * Fc[d][v];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // J r_v = sum_d D_d Ftil_v^d
+    double V[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int base = p - ii[d] * str[d];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const double dm = sD[ii[d] * n + m];
+        const int pm = base + m * str[d];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) V[v] += dm * F[(d * 4 + v) * n3 + pm];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) M.rv[v * M.total + off + p] = V[v];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// inviscid pass + assembly + (optional) RK update
+// ---------------------------------------------------------------------------------------
+template <int N, bool CURVED, int MODE>
+__global__ void __launch_bounds__(Shape<N>::threads)
+    k_inviscid_cns(DevMesh M, const int32_t* __restrict__ list, int count, const double* uin, double* out,
+                   double* g, int stage, double dt, int write_tr) {
+  using S = Shape<N>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sF = sD + NP * NP;  // EPB * 15 * n3: Ftil_e[d][v]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_Dc[N][t];
+  int le = tid / n3;
+  const int p = tid % n3;
+  const int slot = blockIdx.x * EPB + le;
+  const bool active = (le < EPB) && (slot < count);
+  if (le >= EPB) le = EPB - 1;
+  const int e = active ? list[slot] : 0;
+  const int64_t off = active ? M.elem_off[e] : 0;
+  double* F = sF + le * 15 * n3;
+  const double gamma = M.gamma;
+  double uu[5] = {1.0, 0.0, 0.0, 0.0, 1.0}, Ja[9], invJ = 0.0;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) uu[v] = uin[v * M.total + off + p];
+    if (CURVED) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = __ldg(&M.geo[k * M.total + off + p]);
+      invJ = 1.0 / __ldg(&M.geo[9 * M.total + off + p]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
+      invJ = M.ec[e].invJ;
+    }
+    // physical Euler flux fl[v][k] and its contravariant form
+    const Prim Q = prim(uu, gamma);
+    double fl[5][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      fl[0][k] = uu[1 + k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fl[1 + c][k] = uu[1 + c] * Q.v[k] + (c == k ? Q.p : 0.0);
+      fl[4][k] = (uu[4] + Q.p) * Q.v[k];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        F[(d * 5 + v) * n3 + p] = Ja[d * 3] * fl[v][0] + Ja[d * 3 + 1] * fl[v][1] + Ja[d * 3 + 2] * fl[v][2];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int ii[3] = {p % n, (p / n) % n, p / n2};
+  const int str[3] = {1, n, n2};
+  double JR[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int base = p - ii[d] * str[d];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const double dm = sD[ii[d] * n + m];
+      const int pm = base + m * str[d];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) JR[v] -= dm * F[(d * 5 + v) * n3 + pm];
+    }
+  }
+  const bool ns = M.flag[e] != 0;
+  if (ns) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) JR[1 + v] += M.rv[v * M.total + off + p];
+  }
+  const double invw = 1.0 / c_w0c[N];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (ii[d] != 0 && ii[d] != N) continue;
+    const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+    const double sg = side ? 1.0 : -1.0;
+    const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+    const FaceLink L = M.link[e * 6 + f];
+    if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
+      atomicCAS(&M.err[0], 0, 5);
+      atomicCAS(&M.err[1], 0, 11);
+      continue;
+    }
+    const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+    const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+    const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+    const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+    int a1, b1;
+    inv_orient(L.orient, N, a, b, a1, b1);
+    const int64_t nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+    double up[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) up[v] = M.Tq[v * M.tr_total + nsl];
+    double fx[5];
+    cns_fluct(uu, up, nh, gamma, M.riemann, fx);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) JR[v] -= invw * s * fx[v];
+    if (ns || L.nflag) {
+      // BR1: Ftil_v,out - F_v* . S = wo Fv_own . S_own + wn Fv_nbr . S_nbr
+      float wo, wn;
+      visc_face_weights(M.mixed_face, ns, L.nflag != 0, wo, wn);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double t = 0.0;
+        if (ns) t += (double)wo * M.Tv[v * M.tr_total + ms];
+        if (L.nflag) t += (double)wn * M.Tv[v * M.tr_total + nsl];
+        JR[1 + v] -= invw * t;
+      }
+    }
+  }
+  if (MODE == MODE_RESIDUAL) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * M.total + off + p] = JR[v] * invJ;
+  } else {
+    const double A = c_rkAc[stage], B = c_rkBc[stage];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t ix = v * M.total + off + p;
+      double gi = dt * (JR[v] * invJ);
+      if (stage > 0) gi += A * g[ix];
+      g[ix] = gi;
+      const double qn = uu[v] + B * gi;
+      out[ix] = qn;
+      if (write_tr) {  // traces of the new state for the next stage
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (ii[d] != 0 && ii[d] != N) continue;
+          const int f = 2 * d + (ii[d] == N ? 1 : 0);
+          const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
+          M.Tq_next[v * M.tr_total + M.tr_off[e] + f * n2 + a + n * b] = qn;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------------------
+template <int N, bool C>
+static size_t visc_smem_cns() {
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * (4 + (C ? 9 : 0) + 12) * Shape<N>::n3);
+}
+template <int N>
+static size_t inv_smem_cns() {
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * 15 * Shape<N>::n3);
+}
+
+template <int N>
+static cudaError_t prep_cns() {
+  cudaError_t r;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((r = cudaFuncSetAttribute(k_viscous_cns<N, false>, attr, (int)visc_smem_cns<N, false>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous_cns<N, true>, attr, (int)visc_smem_cns<N, true>())) != cudaSuccess) return r;
+  const int is = (int)inv_smem_cns<N>();
+  if ((r = cudaFuncSetAttribute(k_inviscid_cns<N, false, MODE_RESIDUAL>, attr, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid_cns<N, true, MODE_RESIDUAL>, attr, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid_cns<N, false, MODE_RK>, attr, is)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_inviscid_cns<N, true, MODE_RK>, attr, is)) != cudaSuccess) return r;
+  return cudaSuccess;
+}
+
+cudaError_t prepare_kernels_cns() {
+  cudaError_t r;
+  if ((r = prep_cns<1>()) != cudaSuccess) return r;
+  if ((r = prep_cns<2>()) != cudaSuccess) return r;
+  if ((r = prep_cns<3>()) != cudaSuccess) return r;
+  if ((r = prep_cns<4>()) != cudaSuccess) return r;
+  if ((r = prep_cns<5>()) != cudaSuccess) return r;
+  if ((r = prep_cns<6>()) != cudaSuccess) return r;
+  return prep_cns<7>();
+}
+
+#define DG_CNS_N(NVAR, ...)                                     \
+  switch (NVAR) {                                               \
+    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;       \
+    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;       \
+    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;       \
+    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;       \
+    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;       \
+    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;       \
+    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;       \
+    default: return cudaErrorInvalidValue;                      \
+  }
+
+cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_CNS_N(b.N, {
+    const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
+    k_traces_cns<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, u);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_CNS_N(b.N, {
+    using SH = Shape<NN>;
+    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+    if (b.curved)
+      k_viscous_cns<NN, true><<<grid, SH::threads, visc_smem_cns<NN, true>(), s>>>(M, b.list, b.count, u);
+    else
+      k_viscous_cns<NN, false><<<grid, SH::threads, visc_smem_cns<NN, false>(), s>>>(M, b.list, b.count, u);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
+                                int mode, int stage, double dt, int write_tr, cudaStream_t s) {
+  if (b.count == 0) return cudaSuccess;
+  DG_CNS_N(b.N, {
+    using SH = Shape<NN>;
+    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+    const size_t sm = inv_smem_cns<NN>();
+    if (mode == MODE_RESIDUAL) {
+      if (b.curved)
+        k_inviscid_cns<NN, true, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, u, out, g, stage, dt, write_tr);
+      else
+        k_inviscid_cns<NN, false, MODE_RESIDUAL><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, u, out, g, stage, dt, write_tr);
+    } else {
+      if (b.curved)
+        k_inviscid_cns<NN, true, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, u, out, g, stage, dt, write_tr);
+      else
+        k_inviscid_cns<NN, false, MODE_RK><<<grid, SH::threads, sm, s>>>(M, b.list, b.count, u, out, g, stage, dt, write_tr);
+    }
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

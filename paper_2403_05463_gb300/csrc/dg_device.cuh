@@ -45,6 +45,39 @@ __device__ __forceinline__ void slip_visc_term(const T t[3], const T S[3], T out
   for (int c = 0; c < 3; ++c) out[c] = t[c] - ts * S[c];
 }
 
+// LES eddy viscosity from G[c][k] = d u_c / d x_k (App. A: Vreman; Smagorinsky alternative).
+__device__ __forceinline__ double eddy_visc(const double G[3][3], double delta, int closure, double cs,
+                                            double cv) {
+  if (closure == 0) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.5 * (G[c][k] + G[k][c]);
+        s2 += s * s;
+      }
+    double l = cs * delta;
+    return l * l * sqrt(2.0 * s2);
+  }
+  // Vreman: alpha_ij = d u_j / d x_i = G[j][i]; beta = delta^2 alpha^T alpha
+  double aa = 0.0, b[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      aa += G[j][i] * G[j][i];
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) s += G[i][m] * G[j][m];  // alpha_mi alpha_mj = G[i][m] G[j][m]
+      b[i][j] = delta * delta * s;
+    }
+  double B = b[0][0] * b[1][1] - b[0][1] * b[0][1] + b[0][0] * b[2][2] - b[0][2] * b[0][2] +
+             b[1][1] * b[2][2] - b[1][2] * b[1][2];
+  if (aa < 1e-300 || B <= 0.0) return 0.0;
+  return cv * sqrt(B / aa);
+}
+
 // volume node of face f = 2d+s at face coordinates (a, b)
 __host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
   int d = f >> 1, fix = (f & 1) ? n - 1 : 0;

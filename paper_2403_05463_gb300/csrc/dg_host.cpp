@@ -318,9 +318,18 @@ dg_status check_params(const dg_params* p) {
   if (p->precision < 0 || p->precision > 2) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
   if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
   if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
-  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
+  if (p->model < 0 || p->model > 1) return fail(DG_ERR_ARG, "model must be 0 or 1");
+  if (p->model == 1) {
+    if (p->precision != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form runs in FP64 (precision 0) only");
+    if (p->split != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form has the standard volume term only");
+    if (!(p->gamma > 1.0) || !(p->prandtl > 0.0) || !(p->prandtl_t > 0.0))
+      return fail(DG_ERR_ARG, "the compressible form needs gamma > 1 and positive Prandtl numbers");
+  }
   return DG_OK;
 }
+
+// variables of the state: 4 (incompressible), 5 (compressible)
+int nvar(const dg_ctx* c) { return c->prm.model == 1 ? 5 : 4; }
 
 void apply_params(dg_ctx* c) {
   c->M.nu = c->prm.nu;
@@ -331,6 +340,10 @@ void apply_params(dg_ctx* c) {
   c->M.riemann = c->prm.riemann;
   c->M.mixed_face = c->prm.mixed_face;
   c->M.split = c->prm.split;
+  c->M.model = c->prm.model;
+  c->M.gamma = c->prm.gamma;
+  c->M.prandtl = c->prm.prandtl;
+  c->M.prandtl_t = c->prm.prandtl_t;
   // precision 2 is the FP32 path (same data layout) with the inviscid volume contraction on
   // the tensor cores
   c->M.precision = c->prm.precision >= 1 ? 1 : 0;
@@ -665,16 +678,32 @@ dg_status rebuild_flags(dg_ctx* c) {
   if ((st = upload_buckets(c, "nsb", ns_elems, true, true, c->ns_buckets, &ns_lists)) != DG_OK) return st;
   if ((st = upload_entry_tables(c, "nsbx", ns_lists, link, c->ns_buckets)) != DG_OK) return st;
   // viscous traces of Euler elements are never written: keep them at zero
-  if (c->M.Tv) CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
+  if (c->M.Tv) CU(cudaMemset(c->M.Tv, 0, sizeof(double) * (nvar(c) - 1) * std::max<int64_t>(c->tr_total, 1)));
   apply_tuning(c);
   c->version++;
   destroy_graph(c);
   return DG_OK;
 }
 
+// The compressible form is built for interior/periodic conforming faces only.
+dg_status check_model_mesh(const dg_ctx* c) {
+  if (c->prm.model != 1) return DG_OK;
+  for (int64_t s = 0; s < c->ne * 6; ++s) {
+    if (c->nb[s] < 0)
+      return fail(DG_ERR_UNSUPPORTED, "compressible form: element %lld face %d is a boundary face (interior and "
+                  "periodic faces only)", (long long)(s / 6), (int)(s % 6));
+    if (c->order[c->nb[s]] != c->order[s / 6])
+      return fail(DG_ERR_UNSUPPORTED, "compressible form: element %lld face %d is p-nonconforming", (long long)(s / 6),
+                  (int)(s % 6));
+  }
+  return DG_OK;
+}
+
 // order-dependent layout, geometry, buffers
 dg_status rebuild_orders(dg_ctx* c) {
   const int64_t E = c->ne;
+  dg_status cm = check_model_mesh(c);
+  if (cm != DG_OK) return cm;
   c->off.assign(E + 1, 0);
   c->troff.assign(E + 1, 0);
   for (int64_t e = 0; e < E; ++e) {
@@ -783,21 +812,22 @@ dg_status rebuild_orders(dg_ctx* c) {
   c->M.n_elem = E;
   c->M.total = c->total;
   c->M.tr_total = c->tr_total;
-  if ((st = dev_alloc(c, "Tq", 4 * c->tr_total, &c->trace_buf[0])) != DG_OK) return st;
-  if ((st = dev_alloc(c, "Tq2", 4 * c->tr_total, &c->trace_buf[1])) != DG_OK) return st;
+  const int nv = nvar(c), nvv = nv - 1;  // state planes; viscous planes (momentum, + energy)
+  if ((st = dev_alloc(c, "Tq", nv * c->tr_total, &c->trace_buf[0])) != DG_OK) return st;
+  if ((st = dev_alloc(c, "Tq2", nv * c->tr_total, &c->trace_buf[1])) != DG_OK) return st;
   c->M.Tq = c->trace_buf[0];
   c->M.Tq_next = c->trace_buf[1];
-  if ((st = dev_alloc(c, "Tv", 3 * c->tr_total, &c->M.Tv)) != DG_OK) return st;
-  if ((st = dev_alloc(c, "rv", 3 * c->total, &c->M.rv)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "Tv", nvv * c->tr_total, &c->M.Tv)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "rv", nvv * c->total, &c->M.rv)) != DG_OK) return st;
   bool has_mortar = false;
   for (int64_t s = 0; s < E * 6 && !has_mortar; ++s)
     has_mortar = c->nb[s] >= 0 && c->order[c->nb[s]] != c->order[s / 6];
   const int64_t mort = has_mortar ? c->tr_total : 0;
   if ((st = dev_alloc(c, "LU", 9 * mort, &c->M.LU)) != DG_OK) return st;
   if ((st = dev_alloc(c, "LH", 4 * mort, &c->M.LH)) != DG_OK) return st;
-  CU(cudaMemset(c->M.Tv, 0, sizeof(double) * 3 * std::max<int64_t>(c->tr_total, 1)));
-  if ((st = dev_alloc(c, "partial", 4 * E, &c->partial)) != DG_OK) return st;
-  c->partial_host.assign(4 * E, 0.0);
+  CU(cudaMemset(c->M.Tv, 0, sizeof(double) * nvv * std::max<int64_t>(c->tr_total, 1)));
+  if ((st = dev_alloc(c, "partial", 5 * E, &c->partial)) != DG_OK) return st;
+  c->partial_host.assign(5 * E, 0.0);
   free_buf(c, "stage_q");
   free_buf(c, "stage_r");
   c->stage_q = c->stage_r = nullptr;
@@ -829,6 +859,26 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
   const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
+  if (M.model == 1) {  // compressible form: no mortar phases (conforming faces only)
+    if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
+      for (const Bucket& b : c->ord_buckets) {
+        CU(launch_traces_cns(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 2) {
+      for (const Bucket& b : c->ns_buckets) {
+        CU(launch_viscous_cns(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 4) {
+      for (const Bucket& b : c->all_buckets) {
+        CU(launch_inviscid_cns(M, b, q, out, g, mode, stage, dt, write_tr, s));
+        ++nl;
+      }
+    }
+    if (nlaunch) *nlaunch += nl;
+    return DG_OK;
+  }
   switch (phase) {
     case 0:
       if (mode == MODE_RK && stage > 0) break;
@@ -1051,6 +1101,7 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
 dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* stream) {
   if (!c || !q_old || !q_new) return fail(DG_ERR_ARG, "NULL argument");
   if (c->prev_order.empty()) return fail(DG_ERR_STATE, "dg_project_state needs a preceding dg_set_orders");
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form only");
   if (q_old == q_new) return fail(DG_ERR_ARG, "q_old and q_new must not overlap");
   CU(cudaSetDevice(c->device));
   int8_t* dord = nullptr;
@@ -1109,6 +1160,7 @@ dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8
                             double* feat, void* stream) {
   if (!c || !q || !gmm) return fail(DG_ERR_ARG, "NULL argument");
   if (!flags && !pbar && !feat) return fail(DG_ERR_ARG, "dg_detect_regions: no output requested");
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_detect_regions: incompressible form only");
   GmmDev g{};
   dg_status st = gmm_prepare(*gmm, g);
   if (st != DG_OK) return st;
@@ -1136,9 +1188,23 @@ dg_status dg_set_params(dg_ctx* c, const dg_params* params) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   dg_status st = check_params(params);
   if (st != DG_OK) return st;
+  CU(cudaSetDevice(c->device));
+  const dg_params old = c->prm;
   c->prm = *params;
   apply_params(c);
   destroy_graph(c);
+  if (params->model != old.model) {
+    // the number of state planes changes the trace and viscous buffers
+    st = rebuild_orders(c);
+    if (st != DG_OK) {
+      std::string msg = g_last_error;
+      c->prm = old;
+      apply_params(c);
+      rebuild_orders(c);
+      g_last_error = msg;
+      return st;
+    }
+  }
   return DG_OK;
 }
 
@@ -1163,7 +1229,7 @@ dg_status dg_node_coords(dg_ctx* c, double* xyz, void* stream) {
 
 dg_status dg_residual(dg_ctx* c, const double* q, double* R, void* stream) {
   if (!c || !q || !R) return fail(DG_ERR_ARG, "NULL argument");
-  const size_t bytes = sizeof(double) * 4 * c->total;
+  const size_t bytes = sizeof(double) * nvar(c) * c->total;
   if (overlaps(q, bytes, R, bytes)) return fail(DG_ERR_ARG, "q and R overlap");
   CU(cudaSetDevice(c->device));
   int nl = 0;
@@ -1177,7 +1243,7 @@ dg_status dg_rk_step(dg_ctx* c, double* q, double* g, double t, double dt, int n
   if (!c || !q || !g) return fail(DG_ERR_ARG, "NULL argument");
   if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps < 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dt is not finite");
-  const size_t bytes = sizeof(double) * 4 * c->total;
+  const size_t bytes = sizeof(double) * nvar(c) * c->total;
   if (overlaps(q, bytes, g, bytes)) return fail(DG_ERR_ARG, "q and g overlap");
   if (nsteps == 0) return DG_OK;
   CU(cudaSetDevice(c->device));
@@ -1214,8 +1280,8 @@ dg_status dg_rk_step(dg_ctx* c, double* q, double* g, double t, double dt, int n
 
 static dg_status ensure_staging(dg_ctx* c) {
   dg_status st = DG_OK;
-  if (!c->stage_q) st = dev_alloc(c, "stage_q", 4 * c->total, &c->stage_q);
-  if (st == DG_OK && !c->stage_r) st = dev_alloc(c, "stage_r", 4 * c->total, &c->stage_r);
+  if (!c->stage_q) st = dev_alloc(c, "stage_q", nvar(c) * c->total, &c->stage_q);
+  if (st == DG_OK && !c->stage_r) st = dev_alloc(c, "stage_r", nvar(c) * c->total, &c->stage_r);
   return st;
 }
 
@@ -1225,7 +1291,7 @@ dg_status dg_residual_host(dg_ctx* c, const double* q_host, double* R_host, void
   dg_status st = ensure_staging(c);
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(double) * 4 * c->total;
+  const size_t bytes = sizeof(double) * nvar(c) * c->total;
   CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
   if ((st = dg_residual(c, c->stage_q, c->stage_r, stream)) != DG_OK) return st;
   CU(cudaMemcpyAsync(R_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s));
@@ -1239,7 +1305,7 @@ dg_status dg_rk_step_host(dg_ctx* c, double* q_host, double* g_host, double t, d
   dg_status st = ensure_staging(c);
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(double) * 4 * c->total;
+  const size_t bytes = sizeof(double) * nvar(c) * c->total;
   CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(c->stage_r, g_host, bytes, cudaMemcpyHostToDevice, s));
   if ((st = dg_rk_step(c, c->stage_q, c->stage_r, t, dt, nsteps, stream)) != DG_OK) return st;
@@ -1263,15 +1329,16 @@ dg_status dg_check_device(dg_ctx* c, void* stream) {
   return DG_OK;
 }
 
-dg_status dg_conservation(dg_ctx* c, const double* R, double out[4], void* stream) {
+dg_status dg_conservation(dg_ctx* c, const double* R, double* out, void* stream) {
   if (!c || !R || !out) return fail(DG_ERR_ARG, "NULL argument");
   CU(cudaSetDevice(c->device));
-  for (const Bucket& b : c->ord_buckets) CU(launch_conservation(c->M, b, R, c->partial, (cudaStream_t)stream));
-  CU(cudaMemcpyAsync(c->partial_host.data(), c->partial, sizeof(double) * 4 * c->ne, cudaMemcpyDeviceToHost,
+  const int nv = nvar(c);
+  for (const Bucket& b : c->ord_buckets) CU(launch_conservation(c->M, b, R, nv, c->partial, (cudaStream_t)stream));
+  CU(cudaMemcpyAsync(c->partial_host.data(), c->partial, sizeof(double) * nv * c->ne, cudaMemcpyDeviceToHost,
                      (cudaStream_t)stream));
   dg_status st = dg_check_device(c, stream);
   if (st != DG_OK) return st;
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < nv; ++v) {
     double s = 0.0;
     for (int64_t e = 0; e < c->ne; ++e) s += c->partial_host[v * c->ne + e];
     out[v] = s;
@@ -1285,6 +1352,7 @@ static_assert(DG_CONSERVATION_NOALLOC_MAX_ELEMS == kNoAllocMaxElems, "scratch li
 // argument built on the stack; the partial sums use the static scratch of dg_noalloc.cu.
 dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, void* stream) {
   if (!c || !R || !out_dev) return fail(DG_ERR_ARG, "NULL argument");
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form only");
   if (c->ne > kNoAllocMaxElems)
     return fail(DG_ERR_ARG, "dg_conservation_noalloc: the mesh has %lld elements, the static scratch holds %lld",
                 (long long)c->ne, (long long)kNoAllocMaxElems);
@@ -1508,6 +1576,9 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
   // traces and the viscous divergence are FP32 (4 B).
   const bool f32 = c->M.precision == 1;
   const double d = 8.0, sg = f32 ? 4.0 : 8.0, sv = f32 ? 4.0 : 8.0, tr = 8.0;
+  // state planes, viscous planes (momentum, + energy), planes the viscous pass reads (the
+  // velocity; the whole conservative state in the compressible form)
+  const double nv = nvar(c), nvv = nv - 1.0, nu_in = c->prm.model == 1 ? 5.0 : 3.0;
   double b[DG_NPHASES] = {0, 0, 0, 0, 0};
   for (int64_t e = 0; e < c->ne; ++e) {
     const double n = c->order[e] + 1, n2 = n * n, n3 = n2 * n;
@@ -1515,13 +1586,13 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
     const bool curved = c->ec[e].curved != 0.0;
     const double geo = curved ? 10.0 * n3 * (f32 ? 4.0 : 8.0) : (f32 ? 48.0 : 112.0);
     // traces: launched in one stage out of three (q at the face nodes in, traces out)
-    b[0] += (4.0 * 6.0 * n2 * d + 4.0 * 6.0 * n2 * tr) / 3.0;
+    b[0] += (nv * 6.0 * n2 * d + nv * 6.0 * n2 * tr) / 3.0;
     // inviscid + update: q in and out, g out (and in for two stages of three), geometry,
     // traces of the new state written in two stages of three
-    double inv = 4.0 * n3 * d * 2.0 + 4.0 * n3 * sg * (1.0 + 2.0 / 3.0) + geo + (2.0 / 3.0) * 4.0 * 6.0 * n2 * tr;
+    double inv = nv * n3 * d * 2.0 + nv * n3 * sg * (1.0 + 2.0 / 3.0) + geo + (2.0 / 3.0) * nv * 6.0 * n2 * tr;
     if (ns) {
-      b[2] += 3.0 * n3 * d + geo + 3.0 * n3 * sv + 18.0 * n2 * sv;  // u in, rv and Tv out
-      inv += 3.0 * n3 * sv;                                         // rv in
+      b[2] += nu_in * n3 * d + geo + nvv * n3 * sv + 6.0 * nvv * n2 * sv;  // state in, rv and Tv out
+      inv += nvv * n3 * sv;                                                // rv in
     }
     for (int f = 0; f < 6; ++f) {
       const int32_t nb = c->nb[e * 6 + f];
@@ -1529,10 +1600,10 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
       const double nn = c->order[nb] + 1;
       const bool nbns = c->flag[nb] != 0;
       if (c->order[nb] == c->order[e]) {
-        if (ns) b[2] += 3.0 * n2 * tr;                 // neighbour velocity trace
-        inv += 4.0 * n2 * tr;                           // neighbour q trace
-        if (ns) inv += 3.0 * n2 * sv;                   // own viscous trace
-        if (nbns) inv += 3.0 * n2 * sv;                 // neighbour viscous trace
+        if (ns) b[2] += nu_in * n2 * tr;                // neighbour trace for the lifting
+        inv += nv * n2 * tr;                            // neighbour q trace
+        if (ns) inv += nvv * n2 * sv;                   // own viscous trace
+        if (nbns) inv += nvv * n2 * sv;                 // neighbour viscous trace
       } else {
         if (ns) {
           b[1] += 3.0 * (n2 + nn * nn) * tr + 9.0 * n2 * d;  // both velocity traces in, lifting out

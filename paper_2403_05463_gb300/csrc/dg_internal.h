@@ -83,6 +83,10 @@ struct DevMesh {
   int tc;                    // 1: the FP32 inviscid volume contraction on tensor cores (3xTF32)
   float nu32, c0sq32, cs32, cv32, dt32;  // FP32 copies for the reduced-precision passes
   double inflow[4];
+  // governing equations: 0 incompressible (artificial compressibility, q = (p, u, v, w)),
+  // 1 compressible (App. A, u = (rho, rho v, rho e); FP64, conforming periodic meshes)
+  int model;
+  double gamma, prandtl, prandtl_t;  // compressible: ideal gas with unit gas constant
 };
 
 // 1D Gauss-Lobatto operators for N = 1..MAXN (uploaded to constant memory).
@@ -145,7 +149,7 @@ cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, 
                             cudaStream_t s);
 cudaError_t launch_node_coords(const DevMesh& M, const double* geom_nodes, int geom_degree,
                                const Bucket& b, double* xyz, cudaStream_t s);
-cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R,
+cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, int nvar,
                                 double* partial, cudaStream_t s);
 cudaError_t prepare_kernels();
 // FP32-arithmetic variants (dg_kernels_f32.cu)
@@ -158,6 +162,15 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
 
 // elements per tile of the FP32 inviscid pass at order N: the default shape or the alternative
 int tile_epb32(int N, int alt);
+
+// Compressible form (dg_cns.cu), FP64: traces [5][tr_total] in Tq, viscous traces Fv . S
+// [4][tr_total] in Tv (momentum, energy), J r_v [4][total] in rv.
+cudaError_t upload_ops_cns(const Ops1D& ops);
+cudaError_t prepare_kernels_cns();
+cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
+cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
+cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
+                                int mode, int stage, double dt, int write_tr, cudaStream_t s);
 
 // Region detection (dg_regions.cu): the mixture as the kernel uses it.
 struct GmmDev {

@@ -83,39 +83,6 @@ __device__ __forceinline__ void flux_full(const double qm[4], const double qp[4]
   for (int c = 0; c < 3; ++c) out[1 + c] = qm[1 + c] * un + qm[0] * nh[c] + fl[1 + c];
 }
 
-// LES eddy viscosity from G[c][k] = d u_c / d x_k (App. A: Vreman; Smagorinsky alternative).
-__device__ __forceinline__ double eddy_visc(const double G[3][3], double delta, int closure, double cs,
-                                            double cv) {
-  if (closure == 0) {
-    double s2 = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        double s = 0.5 * (G[c][k] + G[k][c]);
-        s2 += s * s;
-      }
-    double l = cs * delta;
-    return l * l * sqrt(2.0 * s2);
-  }
-  // Vreman: alpha_ij = d u_j / d x_i = G[j][i]; beta = delta^2 alpha^T alpha
-  double aa = 0.0, b[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      aa += G[j][i] * G[j][i];
-      double s = 0.0;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) s += G[i][m] * G[j][m];  // alpha_mi alpha_mj = G[i][m] G[j][m]
-      b[i][j] = delta * delta * s;
-    }
-  double B = b[0][0] * b[1][1] - b[0][1] * b[0][1] + b[0][0] * b[2][2] - b[0][2] * b[0][2] +
-             b[1][1] * b[2][2] - b[1][2] * b[1][2];
-  if (aa < 1e-300 || B <= 0.0) return 0.0;
-  return cv * sqrt(B / aa);
-}
-
 // ---------------------------------------------------------------------------------------
 // traces
 // ---------------------------------------------------------------------------------------
@@ -741,7 +708,7 @@ __global__ void k_node_coords(DevMesh M, const int32_t* __restrict__ list, int c
 }
 
 template <int N>
-__global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int count, const double* R,
+__global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int count, const double* R, int nvar,
                                double* partial) {
   constexpr int n = N + 1, n3 = n * n * n;
   int le = blockIdx.x * blockDim.x + threadIdx.x;
@@ -749,7 +716,7 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
   const int e = list[le];
   const int64_t off = M.elem_off[e];
   const bool curved = M.ec[e].curved != 0.0;
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < nvar; ++v) {
     double s = 0.0;
     for (int p = 0; p < n3; ++p) {
       const double w = c_ops.w[N][p % n] * c_ops.w[N][(p / n) % n] * c_ops.w[N][p / (n * n)];
@@ -765,6 +732,7 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
 // ---------------------------------------------------------------------------------------
 cudaError_t upload_ops(const Ops1D& ops) {
   cudaError_t r = cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D));
+  if (r == cudaSuccess) r = upload_ops_cns(ops);
   return r == cudaSuccess ? upload_ops32(ops) : r;
 }
 
@@ -805,6 +773,7 @@ cudaError_t prepare_kernels() {
   if ((r = prep_n<5>()) != cudaSuccess) return r;
   if ((r = prep_n<6>()) != cudaSuccess) return r;
   if ((r = prep_n<7>()) != cudaSuccess) return r;
+  if ((r = prepare_kernels_cns()) != cudaSuccess) return r;
   return prepare_kernels32();
 }
 
@@ -905,11 +874,11 @@ cudaError_t launch_node_coords(const DevMesh& M, const double* gn, int gdeg, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, double* partial,
+cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, int nvar, double* partial,
                                 cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
   DG_DISPATCH_N(b.N, {
-    k_conservation<NN><<<(unsigned)((b.count + 127) / 128), 128, 0, s>>>(M, b.list, b.count, R, partial);
+    k_conservation<NN><<<(unsigned)((b.count + 127) / 128), 128, 0, s>>>(M, b.list, b.count, R, nvar, partial);
   });
   return cudaGetLastError();
 }

@@ -1124,11 +1124,21 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
             dqf[1 + c] = (ih - qh[1 + c]) + (il - ql[1 + c]);
           }
         } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+          // mirror ghost: -2u (no-slip) or -2 (u.n)n (free-slip; n the unit normal, the axis on
+          // a box), written with n rather than S so that S need not stay live
           const float uo[3] = {qh[1] + ql[1], qh[2] + ql[2], qh[3] + ql[3]};
-          float jw[3];
-          wall_jump<float>(L.kind, uo, Sv, jw);
           dqf[0] = 0.f;
-          dqf[1] = jw[0], dqf[2] = jw[1], dqf[3] = jw[2];
+          if (L.kind == FK_WALL) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dqf[1 + c] = -2.f * uo[c];
+          } else if (GEO == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dqf[1 + c] = c == d ? -2.f * uo[c] : 0.f;
+          } else {
+            const float un = uo[0] * nh[0] + uo[1] * nh[1] + uo[2] * nh[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dqf[1 + c] = -2.f * un * nh[c];
+          }
         } else {
           dqf[0] = -(qh[0] + ql[0]);
           dqf[1] = dqf[2] = dqf[3] = 0.f;
@@ -1160,12 +1170,17 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
             term[1 + c] += tv;
           }
         } else if (L.kind == FK_SLIP && ns2) {
+          // free-slip wall: the tangential part of the own outward trace t = tau . S
           const float* ov = reinterpret_cast<const float*>(I2 + P::iOV + SH2[16]) + (f * n2 + ab) * 3;
           const float tv[3] = {ov[0], ov[1], ov[2]};
-          float tt[3];
-          slip_visc_term<float>(tv, Sv, tt);
+          if (GEO == 0) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) term[1 + c] += tt[c];
+            for (int c = 0; c < 3; ++c) term[1 + c] += c == d ? 0.f : tv[c];
+          } else {
+            const float tn = tv[0] * nh[0] + tv[1] * nh[1] + tv[2] * nh[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) term[1 + c] += tv[c] - tn * nh[c];
+          }
         }
       }
       reinterpret_cast<float4*>(W2 + P::wT)[f * n2 + ab] = make_float4(term[0], term[1], term[2], term[3]);

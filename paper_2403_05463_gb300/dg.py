@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("c0sq", ctypes.c_double), ("cs", ctypes.c_double),
                 ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("inflow", ctypes.c_double * 4)]
+                ("model", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("gamma", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("prandtl_t", ctypes.c_double)]
 
 
 class GMM(ctypes.Structure):
@@ -127,7 +128,10 @@ def make_params(p: dict, precision=0) -> Params:
     out.precision = PRECISION.get(precision, precision) if isinstance(precision, str) else int(precision)
     out.mixed_face = int(p.get("mixed_face", 0))
     out.split = int(p.get("split", 0))
-    out.reserved = 0
+    out.model = int(p.get("model", 0))
+    out.gamma = float(p.get("gamma", 1.4))
+    out.prandtl = float(p.get("prandtl", 0.72))
+    out.prandtl_t = float(p.get("prandtl_t", 0.9))
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
     return out
@@ -214,6 +218,15 @@ class Solver:
         _check(load().dg_set_params(self.h, ctypes.byref(self._prm)))
 
     @property
+    def nvar(self) -> int:
+        """Planes of the state: 4 (incompressible), 5 (compressible, params["model"] = 1)."""
+        return 5 if int(self.params.get("model", 0)) == 1 else 4
+
+    def _check_state(self, t, name):
+        if t.numel() != self.nvar * self.total_nodes:
+            raise ValueError(f"{name} must hold [{self.nvar}][{self.total_nodes}] values")
+
+    @property
     def total_nodes(self) -> int:
         t = ctypes.c_int64()
         _check(load().dg_get_layout(self.h, ctypes.byref(t), None))
@@ -235,27 +248,36 @@ class Solver:
 
     def residual(self, q, R=None, stream=None):
         import torch
+        self._check_state(q, "q")
         if R is None:
             R = torch.empty_like(q)
+        self._check_state(R, "R")
         _check(load().dg_residual(self.h, _dev_ptr(q, "q"), _dev_ptr(R, "R"), _stream_handle(stream)))
         return R
 
     def rk_step(self, q, g, dt, nsteps=1, t=0.0, stream=None):
+        self._check_state(q, "q")
+        self._check_state(g, "g")
         _check(load().dg_rk_step(self.h, _dev_ptr(q, "q"), _dev_ptr(g, "g"), float(t), float(dt), int(nsteps),
                                  _stream_handle(stream)))
 
     def residual_host(self, q, R, stream=None):
-        """q, R: host arrays (numpy or pinned CPU tensors), float64 [4][total]."""
+        """q, R: host arrays (numpy or pinned CPU tensors), float64 [nvar][total]."""
+        self._check_state(_as_sized(q), "q")
+        self._check_state(_as_sized(R), "R")
         _check(load().dg_residual_host(self.h, _host_ptr(q), _host_ptr(R), _stream_handle(stream)))
 
     def rk_step_host(self, q, g, dt, nsteps=1, t=0.0, stream=None):
+        self._check_state(_as_sized(q), "q")
+        self._check_state(_as_sized(g), "g")
         _check(load().dg_rk_step_host(self.h, _host_ptr(q), _host_ptr(g), float(t), float(dt), int(nsteps),
                                       _stream_handle(stream)))
 
     def conservation(self, R, stream=None):
-        out = (ctypes.c_double * 4)()
+        self._check_state(R, "R")
+        out = (ctypes.c_double * 5)()
         _check(load().dg_conservation(self.h, _dev_ptr(R, "R"), out, _stream_handle(stream)))
-        return np.array(list(out))
+        return np.array(list(out)[:self.nvar])
 
     def conservation_noalloc(self, R, out, stream=None):
         """The same sums into `out` (a caller-owned float64 CUDA tensor of 4 values), without
@@ -325,6 +347,15 @@ class Solver:
     @property
     def launches_per_step(self):
         return load().dg_launches_per_step(self.h)
+
+
+class _as_sized:
+    """numel() of a numpy array or a tensor, for the size checks."""
+    def __init__(self, a):
+        self._n = a.size if isinstance(a, np.ndarray) else a.numel()
+
+    def numel(self):
+        return self._n
 
 
 def _host_ptr(a):

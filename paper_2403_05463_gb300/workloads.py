@@ -499,6 +499,31 @@ def cns_state(xyz, seed, period=1.0):
     return np.ascontiguousarray(np.stack([rho, rho * v1, rho * v2, rho * v3, E]))
 
 
+def cns_tgv(n=32, order=4, ns_fraction=0.3, curved=False):
+    """Compressible form (App. A): periodic [0,2pi]^3, smooth seeded state of cns_state (Mach
+    ~0.25), mu = 1/1600, Vreman (Cv 0.07), Pr 0.72, Pr_t 0.9; NS in a seeded contiguous run of
+    30% of the elements (lexicographic). curved=True warps the mesh with a degree-2 geometry
+    (x_k += 0.1 sin x sin y sin z)."""
+    seed = 1007
+    b = np.linspace(0, 2 * np.pi, n + 1)
+    warp = None
+    if curved:
+        def warp(x, y, z):
+            s = 0.1 * np.sin(x) * np.sin(y) * np.sin(z)
+            return x + s, y + s, z + s
+    mesh = box_mesh(n, n, n, b, b, b, geom_degree=2 if curved else 1, warp=warp)
+    E = n ** 3
+    rng = np.random.default_rng(seed)
+    start = int(rng.integers(0, E))
+    count = int(round(ns_fraction * E))
+    flags = np.zeros(E, np.uint8)
+    flags[(start + np.arange(count)) % E] = 1
+    params = default_params(nu=1.0 / 1600.0, closure=1, model=1, gamma=1.4, prandtl=0.72, prandtl_t=0.9)
+    return Workload(f"cns_tgv_{n}x{n}x{n}_n{order}" + ("_curved" if curved else ""), mesh,
+                    np.full(E, order, np.int8), flags, params, seed, 5e-4, 10,
+                    lambda xyz, e, l: cns_state(xyz, seed, period=2 * np.pi))
+
+
 WORKLOADS = {
     "tgv_4x4x4_n3": tgv_4x4x4_n3,
     "wake_16x16x16_n4": wake_16x16x16_n4,
@@ -506,4 +531,5 @@ WORKLOADS = {
     "padapt_32x32x32": padapt_32x32x32,
     "mixed_64x64x64_n4": mixed_64x64x64_n4,
     "channel_walls": channel_walls,
+    "cns_tgv": cns_tgv,
 }
