@@ -247,26 +247,33 @@ BENCH_GMM = {"weights": [0.7, 0.3], "means": [[-0.15, 0.0, 0.1], [-0.45, 0.0, 0.
 
 
 def time_detection(S, w, q, q0, stream, reps=10):
-    """Mean time of dg_detect_regions (flags and element means, no node features) with CUDA
-    events on the launching stream, and its algorithmic bytes: the three velocity planes, the
-    metric terms (per element on box/affine meshes, per node on curved ones) and the outputs."""
+    """Mean time of dg_detect_regions (flags and element means, no node features), FP64 and
+    FP32 passes, with CUDA events on the launching stream, and the algorithmic bytes: the three
+    velocity planes, the metric terms (per element on box/affine meshes, per node on curved
+    ones) and the outputs; the two passes' flags are compared."""
     import torch
     q.copy_(q0)
-    for _ in range(3):
-        S.detect_regions(q, BENCH_GMM, stream=stream)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        fl, pb, _ = S.detect_regions(q, BENCH_GMM, stream=stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / reps
     total, ne = S.total_nodes, S.n_elem
     curved = w.mesh.geom_degree > 1
-    nbytes = 24 * total + (80 * total if curved else 80 * ne) + 17 * ne
-    return {"ms": ms, "algorithmic_gb": nbytes / 1e9, "gbs": nbytes / (ms * 1e-3) / 1e9,
-            "viscous_fraction": float(fl.double().mean()), "node_rate": total / (ms * 1e-3)}
+    out, flags = {}, {}
+    for prec, name in ((0, "fp64"), (1, "fp32")):
+        for _ in range(3):
+            S.detect_regions(q, BENCH_GMM, precision=prec, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fl, pb, _ = S.detect_regions(q, BENCH_GMM, precision=prec, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        geo_bytes = (40 if prec else 80) * (total if curved else 1) * (1 if curved else ne)
+        nbytes = 24 * total + geo_bytes + 17 * ne
+        flags[name] = fl
+        out[name] = {"ms": ms, "algorithmic_gb": nbytes / 1e9, "gbs": nbytes / (ms * 1e-3) / 1e9,
+                     "viscous_fraction": float(fl.double().mean()), "node_rate": total / (ms * 1e-3)}
+    out["flags_agree"] = float((flags["fp64"] == flags["fp32"]).double().mean())
+    return out
 
 
 def time_compressible(stream, device=0, steps=10):

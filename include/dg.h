@@ -230,7 +230,12 @@ typedef struct {
   double mean[2][3];    /* component means, in (Q_S, R_S, Q_Omega) order              */
   double cov[2][3][3];  /* component covariances, symmetric positive definite        */
   int viscous;          /* 0 or 1: the component of the viscous/rotational region    */
-  int reserved;         /* must be 0                                                  */
+  int precision;        /* 0 FP64 (the state's precision; the decision of the FP64
+                           oracle), 1 FP32: the velocity rounded to FP32, the gradient,
+                           features, memberships and element means in FP32 (the pass is
+                           then bound by HBM, not the FP64 pipe); flags can differ from
+                           the FP64 decision only for elements whose two means lie within
+                           the FP32 error of each other                               */
 } dg_gmm;
 
 /* Viscous/inviscid region detection (Sec. 2.1), on the device, from the state q_dev
@@ -243,14 +248,15 @@ typedef struct {
  *      at the node's features (the mixture's E-step);
  *   4. per element, the means of p_v and p_i over its (N+1)^3 nodes, and the region with the
  *      larger mean (1 viscous/NS, 0 inviscid/Euler; a tie is viscous).
- * FP64 throughout. Outputs, caller-owned device memory, NULL to skip (at least one given):
+ * FP64 throughout (gmm.precision 0) or FP32 (gmm.precision 1). Outputs, caller-owned device
+ * memory, NULL to skip (at least one given):
  *   flags_dev    [n_elements] uint8, element order: ready for dg_set_element_flags once copied
  *                to the host (this call does not change the context's flags);
  *   pbar_dev     [2][n_elements] FP64: mean p_v, then mean p_i;
  *   features_dev [4][total_nodes] FP64: Q_S, R_S, Q_Omega, p_v per node (node layout of q).
  * Asynchronous on `stream`. Errors: DG_ERR_ARG for a NULL ctx, q_dev or gmm, no output, a
  * non-positive or non-finite weight, a covariance that is not symmetric (to 1e-12 of its
- * largest entry) or not positive definite, viscous outside {0, 1}, reserved != 0;
+ * largest entry) or not positive definite, viscous outside {0, 1}, precision outside {0, 1};
  * DG_ERR_UNSUPPORTED under model 1 (q holds momenta there); DG_ERR_CUDA if a launch fails. */
 dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm, uint8_t* flags_dev,
                             double* pbar_dev, double* features_dev, void* stream);

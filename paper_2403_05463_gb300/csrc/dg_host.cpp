@@ -1117,7 +1117,7 @@ dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* 
 // with the log-determinants (Sec. 2.1; the mixture itself is an input).
 static dg_status gmm_prepare(const dg_gmm& g, GmmDev& out) {
   if (g.viscous != 0 && g.viscous != 1) return fail(DG_ERR_ARG, "gmm.viscous must be 0 or 1");
-  if (g.reserved != 0) return fail(DG_ERR_ARG, "gmm.reserved must be 0");
+  if (g.precision != 0 && g.precision != 1) return fail(DG_ERR_ARG, "gmm.precision must be 0 or 1");
   for (int k = 0; k < 2; ++k) {
     if (!std::isfinite(g.weight[k]) || !(g.weight[k] > 0.0))
       return fail(DG_ERR_ARG, "gmm.weight[%d] must be positive and finite", k);
@@ -1151,6 +1151,9 @@ static dg_status gmm_prepare(const dg_gmm& g, GmmDev& out) {
     for (int i = 0; i < 6; ++i) out.P[k][i] = P[i];
     for (int i = 0; i < 3; ++i) out.mu[k][i] = g.mean[k][i];
     out.c[k] = std::log(g.weight[k]) - 0.5 * std::log(det);
+    for (int i = 0; i < 6; ++i) out.P32[k][i] = (float)P[i];
+    for (int i = 0; i < 3; ++i) out.mu32[k][i] = (float)g.mean[k][i];
+    out.c32[k] = (float)out.c[k];
   }
   out.viscous = g.viscous;
   return DG_OK;
@@ -1170,7 +1173,7 @@ dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8
     DMatArg D{};
     const std::vector<double>& Dn = T.rule[b.N].D;
     for (size_t i = 0; i < Dn.size(); ++i) D.D[i] = Dn[i];
-    CU(launch_detect_regions(c->M, b, g, D, q, flags, pbar, feat, (cudaStream_t)stream));
+    CU(launch_detect_regions(c->M, b, g, D, gmm->precision, q, flags, pbar, feat, (cudaStream_t)stream));
   }
   return DG_OK;
 }

@@ -178,11 +178,13 @@ struct GmmDev {
   double mu[2][3];  // means
   double c[2];      // log w_k - log det(C_k) / 2 (the common -3/2 log 2 pi cancels)
   int viscous;      // index of the viscous component
+  // FP32 copies for the FP32 pass
+  float P32[2][6], mu32[2][3], c32[2];
 };
 struct DMatArg {
   double D[NP * NP];  // D of one order, row-major [i * n + m], n = N + 1
 };
-cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D,
+cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D, int fp32,
                                   const double* q, uint8_t* flags, double* pbar, double* feat, cudaStream_t s);
 
 // Allocation-free conservation sums (dg_noalloc.cu)

@@ -15,25 +15,45 @@
 //   4. per element, the plain means of p_v and p_i over its (N+1)^3 nodes, summed by one warp
 //      in a fixed order (lane-strided partial sums, then a shuffle tree), and the flag
 //      (mean p_v >= mean p_i: viscous/NS).
-// FP64 throughout, so the flag is decided in the precision of the solver's state.
+// FP64 by default, so that the flag is decided in the precision of the solver's state; the FP32
+// variant (gmm.precision 1) runs the same steps in FP32 and is bound by HBM instead of the FP64
+// pipe.
 #include "dg_device.cuh"
 
 namespace dgk {
 
-// GEO: 0 axis-aligned box (diagonal metric), 1 affine, 2 curved (per-node metric terms)
-template <int N, int GEO>
+// GEO: 0 axis-aligned box (diagonal metric), 1 affine, 2 curved (per-node metric terms).
+// T: double (FP64 pass) or float (FP32 pass: the velocity rounded to FP32 with integer
+// instructions, FP32 metric copies, FP32 arithmetic, outputs widened to FP64).
+template <typename T>
+__device__ __forceinline__ T to_t(double x);
+template <>
+__device__ __forceinline__ double to_t<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_t<float>(double x) {
+  float h, l;
+  split_hilo(x, h, l);
+  return h + l;
+}
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return widen_f32(x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
+
+template <int N, int GEO, typename T>
 __global__ void __launch_bounds__(Shape<N>::threads)
     k_detect_regions(DevMesh M, const int32_t* __restrict__ list, int count, GmmDev g, DMatArg Dm,
                      const double* __restrict__ q, uint8_t* __restrict__ flags, double* __restrict__ pbar,
                      double* __restrict__ feat) {
   using S = Shape<N>;
+  constexpr bool F32 = sizeof(T) == 4;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
-  __shared__ double sD[n * n];
-  __shared__ double sU[EPB * 3 * n3];
-  __shared__ double sPv[EPB * n3];
-  __shared__ double sPi[EPB * n3];
+  __shared__ T sD[n * n];
+  __shared__ T sU[EPB * 3 * n3];
+  __shared__ T sPv[EPB * n3];
+  __shared__ T sPi[EPB * n3];
   const int tid = threadIdx.x;
-  for (int t = tid; t < n * n; t += blockDim.x) sD[t] = Dm.D[t];
+  for (int t = tid; t < n * n; t += blockDim.x) sD[t] = (T)Dm.D[t];
   int le = tid / n3;
   const int p = tid % n3;
   const int slot = blockIdx.x * EPB + le;
@@ -41,23 +61,23 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   if (le >= EPB) le = EPB - 1;
   const int e = active ? list[slot] : 0;
   const int64_t off = active ? M.elem_off[e] : 0;
-  double* U = sU + le * 3 * n3;
+  T* U = sU + le * 3 * n3;
   if (active) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) U[c * n3 + p] = __ldg(&q[(1 + c) * M.total + off + p]);
+    for (int c = 0; c < 3; ++c) U[c * n3 + p] = to_t<T>(__ldg(&q[(1 + c) * M.total + off + p]));
   }
   __syncthreads();
   if (active) {
     const int ii[3] = {p % n, (p / n) % n, p / n2};
     const int str[3] = {1, n, n2};
-    double du[3][3];  // du[c][d] = d u_c / d xi_d
+    T du[3][3];  // du[c][d] = d u_c / d xi_d
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int base = p - ii[d] * str[d];
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
-        const double dm = sD[ii[d] * n + m];
+        const T dm = sD[ii[d] * n + m];
         const int pm = base + m * str[d];
         s0 += dm * U[pm];
         s1 += dm * U[n3 + pm];
@@ -67,10 +87,12 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       du[1][d] = s1;
       du[2][d] = s2;
     }
-    double G[3][3];
+    T G[3][3];
     if (GEO == 0) {
-      const double invJ = M.ec[e].invJ;
-      const double a0 = M.ec[e].Ja[0], a1 = M.ec[e].Ja[4], a2 = M.ec[e].Ja[8];
+      const T invJ = F32 ? (T)M.ec32[e].invJ : (T)M.ec[e].invJ;
+      const T a0 = F32 ? (T)M.ec32[e].Ja[0] : (T)M.ec[e].Ja[0];
+      const T a1 = F32 ? (T)M.ec32[e].Ja[4] : (T)M.ec[e].Ja[4];
+      const T a2 = F32 ? (T)M.ec32[e].Ja[8] : (T)M.ec[e].Ja[8];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         G[c][0] = invJ * (a0 * du[c][0]);
@@ -78,15 +100,16 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         G[c][2] = invJ * (a2 * du[c][2]);
       }
     } else {
-      double Ja[9], invJ;
+      T Ja[9], invJ;
       if (GEO == 2) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Ja[k] = __ldg(&M.geo[k * M.total + off + p]);
-        invJ = 1.0 / __ldg(&M.geo[9 * M.total + off + p]);
+        for (int k = 0; k < 9; ++k)
+          Ja[k] = F32 ? (T)__ldg(&M.geo32[k * M.total + off + p]) : (T)__ldg(&M.geo[k * M.total + off + p]);
+        invJ = F32 ? (T)__ldg(&M.geo32[9 * M.total + off + p]) : (T)(1.0 / __ldg(&M.geo[9 * M.total + off + p]));
       } else {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
-        invJ = M.ec[e].invJ;
+        for (int k = 0; k < 9; ++k) Ja[k] = F32 ? (T)M.ec32[e].Ja[k] : (T)M.ec[e].Ja[k];
+        invJ = F32 ? (T)M.ec32[e].invJ : (T)M.ec[e].invJ;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -94,34 +117,38 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         for (int k = 0; k < 3; ++k) G[c][k] = invJ * (Ja[k] * du[c][0] + Ja[3 + k] * du[c][1] + Ja[6 + k] * du[c][2]);
     }
     // strain rate (symmetric) and rotation rate (skew) parts
-    const double s00 = G[0][0], s11 = G[1][1], s22 = G[2][2];
-    const double s01 = 0.5 * (G[0][1] + G[1][0]), s02 = 0.5 * (G[0][2] + G[2][0]), s12 = 0.5 * (G[1][2] + G[2][1]);
-    const double o01 = 0.5 * (G[0][1] - G[1][0]), o02 = 0.5 * (G[0][2] - G[2][0]), o12 = 0.5 * (G[1][2] - G[2][1]);
-    const double trS = s00 + s11 + s22;
-    const double trS2 = s00 * s00 + s11 * s11 + s22 * s22 + 2.0 * (s01 * s01 + s02 * s02 + s12 * s12);
-    const double detS = s00 * (s11 * s22 - s12 * s12) - s01 * (s01 * s22 - s12 * s02) + s02 * (s01 * s12 - s11 * s02);
-    const double x[3] = {0.5 * (trS * trS - trS2), -detS / 3.0, o01 * o01 + o02 * o02 + o12 * o12};
-    double a[2];
+    const T h = (T)0.5;
+    const T s00 = G[0][0], s11 = G[1][1], s22 = G[2][2];
+    const T s01 = h * (G[0][1] + G[1][0]), s02 = h * (G[0][2] + G[2][0]), s12 = h * (G[1][2] + G[2][1]);
+    const T o01 = h * (G[0][1] - G[1][0]), o02 = h * (G[0][2] - G[2][0]), o12 = h * (G[1][2] - G[2][1]);
+    const T trS = s00 + s11 + s22;
+    const T trS2 = s00 * s00 + s11 * s11 + s22 * s22 + (T)2 * (s01 * s01 + s02 * s02 + s12 * s12);
+    const T detS = s00 * (s11 * s22 - s12 * s12) - s01 * (s01 * s22 - s12 * s02) + s02 * (s01 * s12 - s11 * s02);
+    const T x[3] = {h * (trS * trS - trS2), -detS / (T)3, o01 * o01 + o02 * o02 + o12 * o12};
+    T a[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const double d0 = x[0] - g.mu[k][0], d1 = x[1] - g.mu[k][1], d2 = x[2] - g.mu[k][2];
-      const double* P = g.P[k];
-      const double m = P[0] * d0 * d0 + P[3] * d1 * d1 + P[5] * d2 * d2 +
-                       2.0 * (P[1] * d0 * d1 + P[2] * d0 * d2 + P[4] * d1 * d2);
-      a[k] = g.c[k] - 0.5 * m;
+      const T d0 = x[0] - (F32 ? (T)g.mu32[k][0] : (T)g.mu[k][0]);
+      const T d1 = x[1] - (F32 ? (T)g.mu32[k][1] : (T)g.mu[k][1]);
+      const T d2 = x[2] - (F32 ? (T)g.mu32[k][2] : (T)g.mu[k][2]);
+      T P[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) P[i] = F32 ? (T)g.P32[k][i] : (T)g.P[k][i];
+      const T m = P[0] * d0 * d0 + P[3] * d1 * d1 + P[5] * d2 * d2 + (T)2 * (P[1] * d0 * d1 + P[2] * d0 * d2 + P[4] * d1 * d2);
+      a[k] = (F32 ? (T)g.c32[k] : (T)g.c[k]) - h * m;
     }
-    const double av = g.viscous ? a[1] : a[0], ai = g.viscous ? a[0] : a[1];
-    const double E = exp(ai - av);
-    const double pv = 1.0 / (1.0 + E);
-    const double pi = 1.0 / (1.0 + 1.0 / E);
+    const T av = g.viscous ? a[1] : a[0], ai = g.viscous ? a[0] : a[1];
+    const T E = t_exp(ai - av);
+    const T pv = (T)1 / ((T)1 + E);
+    const T pi = (T)1 / ((T)1 + (T)1 / E);
     sPv[le * n3 + p] = pv;
     sPi[le * n3 + p] = pi;
     if (feat) {
       const int64_t i = off + p;
-      feat[i] = x[0];
-      feat[M.total + i] = x[1];
-      feat[2 * M.total + i] = x[2];
-      feat[3 * M.total + i] = pv;
+      feat[i] = to_f64(x[0]);
+      feat[M.total + i] = to_f64(x[1]);
+      feat[2 * M.total + i] = to_f64(x[2]);
+      feat[3 * M.total + i] = to_f64(pv);
     }
   }
   __syncthreads();
@@ -130,7 +157,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   for (int el = warp; el < EPB; el += nwarps) {
     const int sl = blockIdx.x * EPB + el;
     if (sl >= count) break;
-    double sv = 0.0, si = 0.0;
+    T sv = 0, si = 0;
     for (int j = lane; j < n3; j += 32) {
       sv += sPv[el * n3 + j];
       si += sPi[el * n3 + j];
@@ -142,10 +169,10 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     }
     if (lane == 0) {
       const int ee = list[sl];
-      const double mv = sv / n3, mi = si / n3;
+      const T mv = sv / (T)n3, mi = si / (T)n3;
       if (pbar) {
-        pbar[ee] = mv;
-        pbar[M.n_elem + ee] = mi;
+        pbar[ee] = to_f64(mv);
+        pbar[M.n_elem + ee] = to_f64(mi);
       }
       if (flags) flags[ee] = mv >= mi ? 1 : 0;
     }
@@ -164,18 +191,27 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     default: return cudaErrorInvalidValue;                       \
   }
 
-cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D,
+template <int N, typename T>
+static void launch_detect_t(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D, const double* q,
+                            uint8_t* flags, double* pbar, double* feat, cudaStream_t s) {
+  using SH = Shape<N>;
+  const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
+  if (b.geo == 2)
+    k_detect_regions<N, 2, T><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
+  else if (b.geo == 1)
+    k_detect_regions<N, 1, T><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
+  else
+    k_detect_regions<N, 0, T><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
+}
+
+cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D, int fp32,
                                   const double* q, uint8_t* flags, double* pbar, double* feat, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
   DG_DETECT_N(b.N, {
-    using SH = Shape<NN>;
-    const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
-    if (b.geo == 2)
-      k_detect_regions<NN, 2><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
-    else if (b.geo == 1)
-      k_detect_regions<NN, 1><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
+    if (fp32)
+      launch_detect_t<NN, float>(M, b, g, D, q, flags, pbar, feat, s);
     else
-      k_detect_regions<NN, 0><<<grid, SH::threads, 0, s>>>(M, b.list, b.count, g, D, q, flags, pbar, feat);
+      launch_detect_t<NN, double>(M, b, g, D, q, flags, pbar, feat, s);
   });
   return cudaGetLastError();
 }

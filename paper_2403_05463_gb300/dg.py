@@ -48,10 +48,10 @@ class Params(ctypes.Structure):
 class GMM(ctypes.Structure):
     """Two-component Gaussian mixture on the node features (Q_S, R_S, Q_Omega) (dg_gmm)."""
     _fields_ = [("weight", ctypes.c_double * 2), ("mean", (ctypes.c_double * 3) * 2),
-                ("cov", ((ctypes.c_double * 3) * 3) * 2), ("viscous", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("cov", ((ctypes.c_double * 3) * 3) * 2), ("viscous", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
-def make_gmm(weights, means, covs, viscous) -> GMM:
+def make_gmm(weights, means, covs, viscous, precision=0) -> GMM:
     out = GMM()
     for k in range(2):
         out.weight[k] = float(weights[k])
@@ -60,7 +60,7 @@ def make_gmm(weights, means, covs, viscous) -> GMM:
             for j in range(3):
                 out.cov[k][i][j] = float(covs[k][i][j])
     out.viscous = int(viscous)
-    out.reserved = 0
+    out.precision = int(precision)
     return out
 
 
@@ -297,14 +297,18 @@ class Solver:
                                        _stream_handle(stream)))
         return q_new
 
-    def detect_regions(self, q, gmm, flags=True, pbar=True, features=False, stream=None):
+    def detect_regions(self, q, gmm, flags=True, pbar=True, features=False, precision=None, stream=None):
         """Viscous/inviscid region detection from the state q (see dg_detect_regions). gmm is a
-        GMM or a dict with weights, means, covs, viscous. Returns (flags, pbar, features):
-        uint8 [n_elem], float64 [2][n_elem], float64 [4][total_nodes] CUDA tensors, None where
-        not requested. The context's own flags are left as they are."""
+        GMM or a dict with weights, means, covs, viscous; precision (0 FP64, 1 FP32) overrides
+        the mixture's. Returns (flags, pbar, features): uint8 [n_elem], float64 [2][n_elem],
+        float64 [4][total_nodes] CUDA tensors, None where not requested. The context's own
+        flags are left as they are."""
         import torch
         if isinstance(gmm, dict):
-            gmm = make_gmm(gmm["weights"], gmm["means"], gmm["covs"], gmm["viscous"])
+            gmm = make_gmm(gmm["weights"], gmm["means"], gmm["covs"], gmm["viscous"], gmm.get("precision", 0))
+        if precision is not None:
+            gmm = make_gmm(list(gmm.weight), [list(m) for m in gmm.mean], [[list(r) for r in c] for c in gmm.cov],
+                           gmm.viscous, precision)
         dev = q.device
         f = torch.empty(self.n_elem, dtype=torch.uint8, device=dev) if flags else None
         pb = torch.empty((2, self.n_elem), dtype=torch.float64, device=dev) if pbar else None

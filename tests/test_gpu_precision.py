@@ -1,6 +1,6 @@
 """Reduced-precision path (FP32 arithmetic, FP64 state/traces/RK accumulation) against the
-FP64 oracle: every result reports its relative L2 error (printed, and appended to
-gpurun_out/precision_errors.jsonl when that folder exists) and must stay within its
+FP64 oracle: every result reports its relative L2 error (printed, and appended as a JSON line
+to the file the DG_PRECISION_LOG environment variable names, if set) and must stay within its
 regression bound below.
 """
 import json
@@ -36,10 +36,11 @@ def _cuda():
 
 
 def _record(name, err):
+    """Print the error; also append it as a JSON line to the file DG_PRECISION_LOG names, if set."""
     print(f"{name}: FP32 relative L2 error vs FP64 oracle = {err:.3e}")
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(d):
-        with open(os.path.join(d, "precision_errors.jsonl"), "a") as f:
+    path = os.environ.get("DG_PRECISION_LOG")
+    if path:
+        with open(path, "a") as f:
             f.write(json.dumps({"case": name, "rel_l2": err}) + "\n")
 
 

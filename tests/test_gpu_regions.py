@@ -168,7 +168,7 @@ def test_only_the_requested_outputs_are_written():
     np.testing.assert_array_equal(f.cpu().numpy(), (pb2[0] >= pb2[1]).to(torch.uint8).cpu().numpy())
 
 
-@pytest.mark.parametrize("bad", ["not_spd", "not_symmetric", "weight", "viscous", "reserved", "no_output"])
+@pytest.mark.parametrize("bad", ["not_spd", "not_symmetric", "weight", "viscous", "precision", "no_output"])
 def test_bad_arguments_are_rejected(bad):
     import torch
     from paper_2403_05463_gb300 import dg
@@ -186,8 +186,8 @@ def test_bad_arguments_are_rejected(bad):
     if bad == "viscous":
         viscous = 2
     g = dg.make_gmm(weights, np.zeros((2, 3)), covs, viscous)
-    if bad == "reserved":
-        g.reserved = 1
+    if bad == "precision":
+        g.precision = 2
     with pytest.raises(dg.DGError) as ei:
         if bad == "no_output":
             S.detect_regions(q, g, flags=False, pbar=False, features=False)
@@ -217,3 +217,43 @@ def test_full_size_sampled():
     S = gpu_solver(w)
     f, pb, ref = _compare(S, M, qh, gmm, elements=sel, q_dev=q)
     assert 0 < f.sum() < w.n_elem
+
+
+# FP32 pass (gmm precision 1): the gradient from the velocity rounded to FP32 carries ~1e-7 of
+# |u| times ||D|| ~ 40, the features ~1e-6 of their scale, and the memberships that times the
+# mixture's |d a / d x| (~1/sigma, up to ~100 here); the bounds below leave a factor ~10.
+FP32_PROB_TOL = 2e-3
+FP32_MARGIN = 1e-2
+
+
+@pytest.mark.parametrize("make", [_case_wake, _case_curved_mixed_orders, _case_rotated_all_orders])
+def test_fp32_detection_within_its_error(make):
+    import json
+    import os
+    import torch
+    w = make()
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    F = rg.detect_regions(M, q, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": np.stack([np.eye(3)] * 2),
+                                 "viscous": 1})["features"]
+    gmm = _gmm_from(F)
+    ref = rg.detect_regions(M, q, gmm)
+    S = gpu_solver(w, precision=1)
+    f, pb, ft = S.detect_regions(to_dev(q), gmm, features=True, precision=1)
+    torch.cuda.synchronize()
+    f, pb, ft = f.cpu().numpy(), pb.cpu().numpy(), ft.cpu().numpy()
+    g = _gradient_scale(M, q, range(M.ne))
+    feat_err = max(np.abs(ft[i] - ref["features"][i]).max() / s for i, s in ((0, g * g), (1, g ** 3), (2, g * g)))
+    p_err = np.abs(ft[3] - ref["p_v"]).max()
+    pbar_err = np.abs(pb - ref["pbar"]).max()
+    clear = np.abs(ref["pbar"][0] - ref["pbar"][1]) > FP32_MARGIN
+    np.testing.assert_array_equal(f[clear], ref["flags"][clear])
+    agree = float((f == ref["flags"]).mean())
+    rec = {"case": "detect_fp32_" + w.name, "feature_rel": feat_err, "p_v_abs": float(p_err),
+           "pbar_abs": float(pbar_err), "flags_agree": agree}
+    print(rec)
+    if os.environ.get("DG_PRECISION_LOG"):
+        with open(os.environ["DG_PRECISION_LOG"], "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
+    assert feat_err <= 1e-4, feat_err
+    assert p_err <= FP32_PROB_TOL and pbar_err <= FP32_PROB_TOL, (p_err, pbar_err)
