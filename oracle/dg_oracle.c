@@ -116,6 +116,40 @@ int or_lgl(int N, or_real* x, or_real* w) {
   return 0;
 }
 
+/* Gauss-Legendre nodes (the N+1 roots of L_{N+1}) and weights 2 / ((1 - x^2) L'_{N+1}(x)^2),
+ * Newton from the guesses -cos(pi (j + 3/4) / (N + 3/2)); L'_{N+1} = (N+1)(x L_{N+1} - L_N)/(x^2 - 1). */
+int or_gl(int N, or_real* x, or_real* w) {
+  if (N < 1 || N > OR_MAXN) {
+    set_err("order %d outside 1..%d", N, OR_MAXN);
+    return -1;
+  }
+  for (int j = 0; j <= N; ++j) {
+    or_real xj = -COS(PI_R * (j + 0.75) / (N + 1.5));
+    for (int it = 0; it < 200; ++it) {
+      or_real lm1, l0, lp1;
+      legendre3(N, xj, &lm1, &l0, &lp1);
+      const or_real dl = (N + 1.0) * (xj * lp1 - l0) / (xj * xj - 1.0);
+      const or_real dx = lp1 / dl;
+      xj -= dx;
+      if (FABS(dx) <= 1e-17) break;
+    }
+    x[j] = xj;
+  }
+  for (int j = 0; j < (N + 1) / 2; ++j) {
+    or_real s = 0.5 * (x[N - j] - x[j]);
+    x[j] = -s;
+    x[N - j] = s;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  for (int j = 0; j <= N; ++j) {
+    or_real lm1, l0, lp1;
+    legendre3(N, x[j], &lm1, &l0, &lp1);
+    const or_real dl = (N + 1.0) * (x[j] * lp1 - l0) / (x[j] * x[j] - 1.0);
+    w[j] = 2.0 / ((1.0 - x[j] * x[j]) * dl * dl);
+  }
+  return 0;
+}
+
 /* Lagrange basis l_j(y) on nodes xs[0..n-1] by the product formula. */
 static or_real lagrange(int n, const or_real* xs, int j, or_real y) {
   or_real v = 1.0;
@@ -124,10 +158,9 @@ static or_real lagrange(int n, const or_real* xs, int j, or_real y) {
   return v;
 }
 
-int or_dmat(int N, or_real* D) {
-  or_real x[OR_MAXN + 1], w[OR_MAXN + 1], lam[OR_MAXN + 1];
-  if (or_lgl(N, x, w)) return -1;
-  int n = N + 1;
+/* D_ij = l_j'(x_i) on the nodes x[0..n-1], barycentric form */
+static void dmat_nodes(int n, const or_real* x, or_real* D) {
+  or_real lam[OR_MAXN + 1];
   /* barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k) */
   for (int j = 0; j < n; ++j) {
     or_real p = 1.0;
@@ -144,6 +177,12 @@ int or_dmat(int N, or_real* D) {
     }
     D[i * n + i] = -s;
   }
+}
+
+int or_dmat(int N, or_real* D) {
+  or_real x[OR_MAXN + 1], w[OR_MAXN + 1];
+  if (or_lgl(N, x, w)) return -1;
+  dmat_nodes(N + 1, x, D);
   return 0;
 }
 
@@ -381,6 +420,7 @@ or_real or_rk3_linear(or_real z) {
 
 typedef struct {
   or_real x[OR_MAXN + 1], w[OR_MAXN + 1], D[(OR_MAXN + 1) * (OR_MAXN + 1)];
+  or_real lb[2][OR_MAXN + 1]; /* l_i(-1), l_i(+1): face interpolation (unit vectors on Lobatto nodes) */
 } op1d;
 
 struct or_mesh {
@@ -485,9 +525,28 @@ or_mesh* or_create(int64_t ne, const int64_t* hex, int g, const or_real* gxyz, c
   m->ne = ne;
   m->g = g;
   m->p = *prm;
+  if (prm->nodes != 0 && prm->nodes != 1) {
+    set_err("nodes %d invalid", prm->nodes);
+    free(m);
+    return NULL;
+  }
+  if (prm->nodes == 1 && prm->split == 1) {
+    set_err("the split form needs Gauss-Lobatto nodes");
+    free(m);
+    return NULL;
+  }
   for (int N = 1; N <= OR_MAXN; ++N) {
-    or_lgl(N, m->op[N].x, m->op[N].w);
-    or_dmat(N, m->op[N].D);
+    if (prm->nodes == 1) {
+      or_gl(N, m->op[N].x, m->op[N].w);
+      dmat_nodes(N + 1, m->op[N].x, m->op[N].D);
+    } else {
+      or_lgl(N, m->op[N].x, m->op[N].w);
+      or_dmat(N, m->op[N].D);
+    }
+    for (int i = 0; i <= N; ++i) {
+      m->op[N].lb[0][i] = lagrange(N + 1, m->op[N].x, i, -1.0);
+      m->op[N].lb[1][i] = lagrange(N + 1, m->op[N].x, i, 1.0);
+    }
   }
   int ng = g + 1, ng3 = ng * ng * ng;
   m->N = (int8_t*)malloc(ne);
@@ -653,12 +712,23 @@ static void interp3(int ns, int nd, const or_real* I, const or_real* u, or_real*
       }
 }
 
+/* Interpolation from the geometry nodes (Gauss-Lobatto points of degree g) to the element's
+ * nodes of order N (Gauss-Lobatto or Gauss-Legendre): I[(N+1)][(g+1)] */
+static void geom_interp(const or_mesh* m, int N, or_real* I) {
+  or_real xg[OR_MAXG + 1], wg[OR_MAXG + 1];
+  or_lgl(m->g, xg, wg);
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= m->g; ++j) I[i * (m->g + 1) + j] = lagrange(m->g + 1, xg, j, m->op[N].x[i]);
+}
+
 int or_element_geometry(const or_mesh* m, int64_t e, or_real* J, or_real* Ja) {
   int g = m->g, ng = g + 1, ng3 = ng * ng * ng;
   int N = m->N[e], n = N + 1, n3 = n * n * n;
-  const or_real* Dg = m->op[g].D;
+  /* the geometry nodes are Gauss-Lobatto points of degree g whatever the element's node set */
+  or_real Dg[(OR_MAXG + 1) * (OR_MAXG + 1)];
+  or_dmat(g, Dg);
   or_real I[(OR_MAXN + 1) * (OR_MAXG + 1)];
-  or_interp_lgl(g, N, I);
+  geom_interp(m, N, I);
   or_real X[3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
   or_real dX[3][3][(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
   for (int p = 0; p < ng3; ++p)
@@ -706,7 +776,7 @@ int or_node_coords(const or_mesh* m, or_real* xyz) {
   for (int64_t e = 0; e < m->ne; ++e) {
     int N = m->N[e], n = N + 1, n3 = n * n * n;
     or_real I[(OR_MAXN + 1) * (OR_MAXG + 1)];
-    or_interp_lgl(g, N, I);
+    geom_interp(m, N, I);
     or_real X[(OR_MAXG + 1) * (OR_MAXG + 1) * (OR_MAXG + 1)];
     or_real* out = (or_real*)malloc(sizeof(or_real) * n3);
     for (int c = 0; c < 3; ++c) {
@@ -762,24 +832,55 @@ static void interp2(int ns, int nd, const or_real* I, const or_real* u, or_real*
 }
 
 /* outward area-weighted normal S = sigma Ja^d at the face nodes of element e, face f */
+/* volume node i along the normal line of face f through the face coordinates (a, b) */
+static int64_t line_node(int f, int N, int a, int b, int i) {
+  int d = f >> 1, t0, t1, ijk[3];
+  face_dirs(d, &t0, &t1);
+  ijk[d] = i;
+  ijk[t0] = a;
+  ijk[t1] = b;
+  int n = N + 1;
+  return ijk[0] + (int64_t)n * (ijk[1] + (int64_t)n * ijk[2]);
+}
+
+/* the value at face f of a nodal field u[n3] at face coordinates (a, b): the face node's value
+ * on Gauss-Lobatto nodes, the interpolation sum_i l_i(+-1) u_i along the normal line on
+ * Gauss-Legendre nodes */
+static or_real face_value(const or_mesh* m, int N, int f, int a, int b, const or_real* u) {
+  if (m->p.nodes == 0) return u[face_node(f, N, a, b)];
+  const or_real* l = m->op[N].lb[f & 1];
+  or_real s = 0.0;
+  for (int i = 0; i <= N; ++i) s += l[i] * u[line_node(f, N, a, b, i)];
+  return s;
+}
+
+/* adds v * (lifting of face f at (a, b)) to the nodal field u[n3]: v / w_end at the face node
+ * on Gauss-Lobatto nodes, v l_i(+-1) / w_i along the normal line on Gauss-Legendre nodes
+ * (the surface integral of the weak form divided by the node's quadrature weight) */
+static void face_lift(const or_mesh* m, int N, int f, int a, int b, or_real v, or_real* u) {
+  const or_real* w = m->op[N].w;
+  if (m->p.nodes == 0) {
+    u[face_node(f, N, a, b)] += v / w[0];
+    return;
+  }
+  const or_real* l = m->op[N].lb[f & 1];
+  for (int i = 0; i <= N; ++i) u[line_node(f, N, a, b, i)] += v * l[i] / w[i];
+}
+
 static void face_S(const or_mesh* m, const geo_t* gt, int64_t e, int f, or_real* S /*[3][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
   int d = f >> 1;
   or_real sg = (f & 1) ? 1.0 : -1.0;
   for (int b = 0; b < n; ++b)
-    for (int a = 0; a < n; ++a) {
-      int64_t p = face_node(f, N, a, b);
-      for (int c = 0; c < 3; ++c) S[c * n2 + a + n * b] = sg * gt->Ja[(d * 3 + c) * n3 + p];
-    }
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < 3; ++c) S[c * n2 + a + n * b] = sg * face_value(m, N, f, a, b, gt->Ja + (d * 3 + c) * n3);
 }
 
 static void face_q(const or_mesh* m, const or_real* q, int64_t e, int f, or_real* T /*[4][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n;
   for (int b = 0; b < n; ++b)
-    for (int a = 0; a < n; ++a) {
-      int64_t p = m->off[e] + face_node(f, N, a, b);
-      for (int v = 0; v < 4; ++v) T[v * n2 + a + n * b] = q[v * m->total + p];
-    }
+    for (int a = 0; a < n; ++a)
+      for (int v = 0; v < 4; ++v) T[v * n2 + a + n * b] = face_value(m, N, f, a, b, q + v * m->total + m->off[e]);
 }
 
 /* viscous stress at one node of an NS element */
@@ -804,6 +905,27 @@ static void face_fv(const work_t* W, int64_t e, int f, or_real* Fv /*[3][n2]*/) 
     return;
   }
   const geo_t* gt = &W->geo[e];
+  if (m->p.nodes == 1) {
+    /* Gauss-Legendre: the outward contravariant viscous flux sigma Ja^d . tau at every node,
+     * interpolated to the face */
+    const int d = f >> 1;
+    const or_real sg = (f & 1) ? 1.0 : -1.0;
+    or_real* Ft = (or_real*)malloc(sizeof(or_real) * 3 * n3);
+    for (int p = 0; p < n3; ++p) {
+      or_real tau[3][3];
+      stress(m, gt, W->G[e], e, n3, p, tau);
+      for (int c = 0; c < 3; ++c) {
+        or_real s = 0.0;
+        for (int k = 0; k < 3; ++k) s += tau[c][k] * gt->Ja[(d * 3 + k) * n3 + p];
+        Ft[c * n3 + p] = sg * s;
+      }
+    }
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < 3; ++c) Fv[c * n2 + a + n * b] = face_value(m, N, f, a, b, Ft + c * n3);
+    free(Ft);
+    return;
+  }
   or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
   face_S(m, gt, e, f, S);
   for (int b = 0; b < n; ++b)
@@ -1048,10 +1170,8 @@ static void element_gradient(const work_t* W, int64_t e, or_real* G) {
   for (int f = 0; f < 6; ++f) {
     face_ustar(W, e, f, LU);
     for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        int64_t p = face_node(f, N, a, b);
-        for (int ck = 0; ck < 9; ++ck) G[ck * n3 + p] += LU[ck * n2 + a + n * b] / w[0];
-      }
+      for (int a = 0; a < n; ++a)
+        for (int ck = 0; ck < 9; ++ck) face_lift(m, N, f, a, b, LU[ck * n2 + a + n * b], G + ck * n3);
   }
   free(LU);
   for (int ck = 0; ck < 9; ++ck)
@@ -1167,10 +1287,8 @@ static int element_residual(const work_t* W, int64_t e, or_real* R) {
   for (int f = 0; f < 6; ++f) {
     if (face_hstar(W, e, f, LH)) rc = -1;
     for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        int64_t p = face_node(f, N, a, b);
-        for (int v = 0; v < 4; ++v) JR[v * n3 + p] -= LH[v * n2 + a + n * b] / w[0];
-      }
+      for (int a = 0; a < n; ++a)
+        for (int v = 0; v < 4; ++v) face_lift(m, N, f, a, b, -LH[v * n2 + a + n * b], JR + v * n3);
   }
   for (int v = 0; v < 4; ++v)
     for (int p = 0; p < n3; ++p) R[v * T + o + p] = JR[v * n3 + p] / gt->J[p];
@@ -1193,6 +1311,12 @@ static void free_work(work_t* W) {
 
 int or_residual(const or_mesh* m, const or_real* q, or_real* R, int64_t n_sel, const int64_t* sel) {
   int64_t ne = m->ne;
+  if (m->p.nodes == 1)
+    for (int64_t s = 0; s < ne * 6; ++s)
+      if (m->nb_e[s] >= 0 && m->N[m->nb_e[s]] != m->N[s / 6]) {
+        set_err("Gauss-Legendre nodes: element %lld face %d is p-nonconforming", (long long)(s / 6), (int)(s % 6));
+        return -1;
+      }
   /* elements whose residual is wanted */
   uint8_t* want = (uint8_t*)calloc(ne, 1);
   if (sel) {
@@ -1696,6 +1820,10 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
 }
 
 static int cns_check(const or_mesh* m) {
+  if (m->p.nodes != 0) {
+    set_err("compressible form: Gauss-Lobatto nodes only");
+    return -1;
+  }
   if (!(m->p.gamma > 1.0) || !(m->p.prandtl > 0.0) || !(m->p.prandtl_t > 0.0)) {
     set_err("compressible form: need gamma > 1 and positive Prandtl numbers");
     return -1;

@@ -57,12 +57,18 @@ typedef struct {
   or_real gamma;     /* ratio of specific heats                                   */
   or_real prandtl;   /* laminar Prandtl number                                    */
   or_real prandtl_t; /* turbulent Prandtl number                                  */
+  int nodes;        /* element nodes and quadrature: 0 Gauss-Lobatto, 1 Gauss-Legendre
+                       (the paper's choice, App. B): face values, face metric terms and
+                       face fluxes are interpolated from the element's nodes and face terms
+                       are lifted with l_i(+-1) / w_i; p-nonconforming faces and the split
+                       form need Gauss-Lobatto                                     */
 } or_params;
 
 typedef struct or_mesh or_mesh;
 
 /* 1D building blocks (Gauss-Lobatto-Legendre nodes on [-1,1]). */
 int or_lgl(int N, or_real* x, or_real* w);                  /* x[N+1], w[N+1]          */
+int or_gl(int N, or_real* x, or_real* w);                   /* Gauss-Legendre, N+1 nodes */
 int or_dmat(int N, or_real* D);                            /* D[(N+1)*(N+1)] row-major */
 int or_interp_lgl(int Ns, int Nd, or_real* I);             /* I[(Nd+1)][(Ns+1)]        */
 int or_project_lgl(int Nh, int Nl, or_real* P);            /* P[(Nl+1)][(Nh+1)]        */

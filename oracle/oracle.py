@@ -53,7 +53,8 @@ def _params_type(real):
     class P(ctypes.Structure):
         _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
                     ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
-                    ("inflow", real * 4), ("gamma", real), ("prandtl", real), ("prandtl_t", real)]
+                    ("inflow", real * 4), ("gamma", real), ("prandtl", real), ("prandtl_t", real),
+                    ("nodes", ctypes.c_int)]
     return P
 
 
@@ -71,6 +72,7 @@ def lib(extended: bool = False):
             _d = _P(real)
             L = ctypes.CDLL(LIB_PATH_EXT if extended else LIB_PATH)
             L.or_lgl.argtypes = [ctypes.c_int, _d, _d]
+            L.or_gl.argtypes = [ctypes.c_int, _d, _d]
             L.or_dmat.argtypes = [ctypes.c_int, _d]
             L.or_interp_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
@@ -126,11 +128,12 @@ def _f64(a):
 
 
 def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0,
-           split=0, gamma=1.4, prandtl=0.72, prandtl_t=0.9):
+           split=0, gamma=1.4, prandtl=0.72, prandtl_t=0.9, nodes=0):
     p = Params()
     p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
     p.closure, p.riemann, p.mixed_face, p.split = closure, riemann, mixed_face, split
     p.gamma, p.prandtl, p.prandtl_t = gamma, prandtl, prandtl_t
+    p.nodes = nodes
     for i in range(4):
         p.inflow[i] = inflow[i]
     return p
@@ -142,6 +145,15 @@ def lgl(N):
     x = np.zeros(N + 1)
     w = np.zeros(N + 1)
     if lib().or_lgl(N, _ptr(x, _d), _ptr(w, _d)):
+        raise ValueError(lib().or_error().decode())
+    return x, w
+
+
+def gl(N):
+    """Gauss-Legendre nodes and weights (N + 1 points)."""
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if lib().or_gl(N, _ptr(x, _d), _ptr(w, _d)):
         raise ValueError(lib().or_error().decode())
     return x, w
 
