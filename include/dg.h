@@ -117,6 +117,17 @@ typedef struct {
   double gamma;     /* model 1: ratio of specific heats (> 1)                           */
   double prandtl;   /* model 1: laminar Prandtl number (> 0)                            */
   double prandtl_t; /* model 1: turbulent Prandtl number (> 0)                          */
+  int nodes;        /* element nodes and quadrature (App. B): 0 Gauss-Lobatto, 1 Gauss-
+                       Legendre (the paper's choice): the element's (N+1)^3 nodes are the
+                       tensor Gauss points, face values, face metric terms and viscous
+                       traces are interpolated along the normal lines and face terms lifted
+                       with l_i(+-1) / w_i. Nodes 1 runs the incompressible form (model 0)
+                       in FP64 (precision 0) with the standard volume term (split 0) on
+                       meshes whose faces are all interior or periodic and conforming; other
+                       settings give DG_ERR_UNSUPPORTED, as do dg_project_state,
+                       dg_conservation_noalloc and dg_detect_regions. dg_node_coords returns
+                       the Gauss points.                                                 */
+  int reserved;     /* must be 0                                                       */
 } dg_params;
 
 /* Build the mesh topology (face matching, orientations, periodic pairs), the geometry

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdgflag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_kernels_f32.cu", "dg_noalloc.cu", "dg_regions.cu", "dg_cns.cu"]
+SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_kernels_f32.cu", "dg_noalloc.cu", "dg_regions.cu", "dg_cns.cu", "dg_gl.cu"]
 HEADERS = ["dg_internal.h", "dg_device.cuh", os.path.join("..", "..", "include", "dg.h")]
 
 

@@ -45,6 +45,50 @@ __device__ __forceinline__ void slip_visc_term(const T t[3], const T S[3], T out
   for (int c = 0; c < 3; ++c) out[c] = t[c] - ts * S[c];
 }
 
+// y = A(ub) x for the artificial-compressibility flux Jacobian in direction nh
+__device__ __forceinline__ void ac_jac_apply(const double ub[3], double un, const double nh[3],
+                                             double c0sq, const double x[4], double y[4]) {
+  double nx = nh[0] * x[1] + nh[1] * x[2] + nh[2] * x[3];
+  y[0] = c0sq * nx;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) y[1 + c] = nh[c] * x[0] + ub[c] * nx + un * x[1 + c];
+}
+
+// Fluctuation A^-(qbar) dq = (F* - F_n(q-)) for Roe (riemann == 0): the flux is quadratic,
+// so F(q+) - F(q-) = A(qbar) dq exactly with qbar the arithmetic mean, and |A| is the
+// quadratic polynomial in A that matches |lambda| on the three distinct eigenvalues
+// u_n - a, u_n, u_n + a (a = sqrt(u_n^2 + c0^2)). For LLF: 1/2 (A dq - lambda_max dq).
+__device__ __forceinline__ void flux_fluct(const double qm[4], const double qp[4], const double nh[3],
+                                           double c0sq, int riemann, double out[4]) {
+  double dq[4], ub[3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) dq[v] = qp[v] - qm[v];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (qm[1 + c] + qp[1 + c]);
+  double un = ub[0] * nh[0] + ub[1] * nh[1] + ub[2] * nh[2];
+  double y1[4];
+  ac_jac_apply(ub, un, nh, c0sq, dq, y1);
+  if (riemann == 0) {
+    double y2[4];
+    ac_jac_apply(ub, un, nh, c0sq, y1, y2);
+    double a = sqrt(un * un + c0sq);
+    double aun = fabs(un);
+    double lm = un - a, l0 = un;
+    double d1 = (aun + un - a) / a;        // divided difference of |.| on (lm, l0)
+    double d2 = (a - aun) / (a * a);       // second divided difference on (lm, l0, lp)
+    double k0 = -lm - d1 * lm + d2 * lm * l0;
+    double k1 = d1 - d2 * (lm + l0);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - (k0 * dq[v] + k1 * y1[v] + d2 * y2[v]));
+  } else {
+    double unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+    double unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
+    double lam = fmax(fabs(unm) + sqrt(unm * unm + c0sq), fabs(unp) + sqrt(unp * unp + c0sq));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - lam * dq[v]);
+  }
+}
+
 // LES eddy viscosity from G[c][k] = d u_c / d x_k (App. A: Vreman; Smagorinsky alternative).
 __device__ __forceinline__ double eddy_visc(const double G[3][3], double delta, int closure, double cs,
                                             double cv) {

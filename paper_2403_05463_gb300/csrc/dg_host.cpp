@@ -107,6 +107,54 @@ Rule make_rule(int N) {
   return r;
 }
 
+// Gauss-Legendre rule of N+1 points (App. B's quadrature): the roots of P_{N+1}, by Newton from
+// the Chebyshev-Gauss guesses cos(pi (2j+1) / (2N+2)), weights 2 / ((1 - x^2) P'_{N+1}^2);
+// D_ij = l_j'(x_i) from the barycentric weights.
+Rule make_gl_rule(int N) {
+  Rule r;
+  r.N = N;
+  const int n = N + 1;
+  r.x.assign(n, 0.0);
+  r.w.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double x = -std::cos(M_PI * (2.0 * j + 1.0) / (2.0 * n));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_and_derivative(n, x, P, dP);
+      const double dx = P / dP;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    r.x[j] = x;
+  }
+  for (int j = 0; j < n / 2; ++j) {  // symmetrise
+    const double m = 0.5 * (r.x[N - j] - r.x[j]);
+    r.x[j] = -m;
+    r.x[N - j] = m;
+  }
+  if (n % 2 == 1) r.x[N / 2] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double P, dP;
+    legendre_and_derivative(n, r.x[j], P, dP);
+    r.w[j] = 2.0 / ((1.0 - r.x[j] * r.x[j]) * dP * dP);
+  }
+  std::vector<double> lam(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (r.x[j] - r.x[k]);
+  r.D.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) {
+        r.D[i * n + j] = lam[j] / (lam[i] * (r.x[i] - r.x[j]));
+        diag -= r.D[i * n + j];
+      }
+    r.D[i * n + i] = diag;
+  }
+  return r;
+}
+
 // barycentric Lagrange interpolation matrix from nodes xs to points xd: I[i][j]
 std::vector<double> interp_matrix(const std::vector<double>& xs, const std::vector<double>& xd) {
   const int ns = (int)xs.size(), nd = (int)xd.size();
@@ -155,9 +203,26 @@ std::vector<double> projection_matrix(const Rule& hi, const Rule& lo) {
 
 struct OpTables {
   Rule rule[NP];
+  Rule gl[NP];                          // Gauss-Legendre rules (element nodes with nodes = 1)
+  double glb[NP][2][NP] = {};           // Gauss-Legendre l_i(-1), l_i(+1)
   std::vector<double> interp, proj;  // [(a*NP+b)*NP*NP + i*NP + j]
+  std::vector<double> interp_gl;     // Gauss-Lobatto of degree a -> Gauss-Legendre of order b
   OpTables() {
     for (int N = 1; N <= MAXN; ++N) rule[N] = make_rule(N);
+    for (int N = 1; N <= MAXN; ++N) {
+      gl[N] = make_gl_rule(N);
+      const std::vector<double> ends = {-1.0, 1.0};
+      const std::vector<double> E = interp_matrix(gl[N].x, ends);
+      for (int s = 0; s < 2; ++s)
+        for (int i = 0; i <= N; ++i) glb[N][s][i] = E[s * (N + 1) + i];
+    }
+    interp_gl.assign(NP * NP * NP * NP, 0.0);
+    for (int a = 1; a <= MAXN; ++a)
+      for (int b = 1; b <= MAXN; ++b) {
+        auto I = interp_matrix(rule[a].x, gl[b].x);
+        for (int i = 0; i <= b; ++i)
+          for (int j = 0; j <= a; ++j) interp_gl[(a * NP + b) * NP * NP + i * NP + j] = I[i * (a + 1) + j];
+      }
     interp.assign(NP * NP * NP * NP, 0.0);
     proj.assign(NP * NP * NP * NP, 0.0);
     for (int a = 1; a <= MAXN; ++a)
@@ -319,6 +384,11 @@ dg_status check_params(const dg_params* p) {
   if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
   if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
   if (p->model < 0 || p->model > 1) return fail(DG_ERR_ARG, "model must be 0 or 1");
+  if (p->nodes < 0 || p->nodes > 1) return fail(DG_ERR_ARG, "nodes must be 0 or 1");
+  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
+  if (p->nodes == 1 && (p->model != 0 || p->precision != 0 || p->split != 0))
+    return fail(DG_ERR_UNSUPPORTED, "Gauss-Legendre nodes run the incompressible form in FP64 with the standard "
+                "volume term only");
   if (p->model == 1) {
     if (p->precision != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form runs in FP64 (precision 0) only");
     if (p->split != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form has the standard volume term only");
@@ -331,6 +401,9 @@ dg_status check_params(const dg_params* p) {
 // variables of the state: 4 (incompressible), 5 (compressible)
 int nvar(const dg_ctx* c) { return c->prm.model == 1 ? 5 : 4; }
 
+// the element's node rule: Gauss-Lobatto, or Gauss-Legendre with nodes = 1
+const Rule& node_rule(const dg_ctx* c, int N) { return c->prm.nodes == 1 ? ops().gl[N] : ops().rule[N]; }
+
 void apply_params(dg_ctx* c) {
   c->M.nu = c->prm.nu;
   c->M.c0sq = c->prm.c0sq;
@@ -341,6 +414,7 @@ void apply_params(dg_ctx* c) {
   c->M.mixed_face = c->prm.mixed_face;
   c->M.split = c->prm.split;
   c->M.model = c->prm.model;
+  c->M.nodes = c->prm.nodes;
   c->M.gamma = c->prm.gamma;
   c->M.prandtl = c->prm.prandtl;
   c->M.prandtl_t = c->prm.prandtl_t;
@@ -417,7 +491,7 @@ void elem_geometry(const dg_ctx* c, int64_t e, int N, ElemGeo& G) {
   }
   G.affine = false;
   const Rule& rg = ops().rule[g];
-  const Rule& rn = ops().rule[N];
+  const Rule& rn = node_rule(c, N);
   const int n = N + 1, n3 = n * n * n;
   const double* X = &c->gnodes[(size_t)e * ng3 * 3];
   // derivative along direction d on the ng^3 grid
@@ -687,13 +761,14 @@ dg_status rebuild_flags(dg_ctx* c) {
 
 // The compressible form is built for interior/periodic conforming faces only.
 dg_status check_model_mesh(const dg_ctx* c) {
-  if (c->prm.model != 1) return DG_OK;
+  if (c->prm.model != 1 && c->prm.nodes != 1) return DG_OK;
+  const char* what = c->prm.model == 1 ? "compressible form" : "Gauss-Legendre nodes";
   for (int64_t s = 0; s < c->ne * 6; ++s) {
     if (c->nb[s] < 0)
-      return fail(DG_ERR_UNSUPPORTED, "compressible form: element %lld face %d is a boundary face (interior and "
-                  "periodic faces only)", (long long)(s / 6), (int)(s % 6));
+      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is a boundary face (interior and periodic faces "
+                  "only)", what, (long long)(s / 6), (int)(s % 6));
     if (c->order[c->nb[s]] != c->order[s / 6])
-      return fail(DG_ERR_UNSUPPORTED, "compressible form: element %lld face %d is p-nonconforming", (long long)(s / 6),
+      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is p-nonconforming", what, (long long)(s / 6),
                   (int)(s % 6));
   }
   return DG_OK;
@@ -726,7 +801,7 @@ dg_status rebuild_orders(dg_ctx* c) {
     const int N = c->order[e], n = N + 1, n3 = n * n * n;
     elem_geometry(c, e, N, G);
     ElemConst& k = c->ec[e];
-    const Rule& r = ops().rule[N];
+    const Rule& r = node_rule(c, N);
     double vol = 0.0;
     if (G.affine) {
       if (!(G.J > 0.0)) return fail(DG_ERR_MESH, "element %lld has a non-positive Jacobian", (long long)e);
@@ -859,6 +934,26 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
   const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
+  if (M.nodes == 1) {  // Gauss-Legendre nodes: no mortar phases (conforming faces only)
+    if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
+      for (const Bucket& b : c->ord_buckets) {
+        CU(launch_traces_gl(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 2) {
+      for (const Bucket& b : c->ns_buckets) {
+        CU(launch_viscous_gl(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 4) {
+      for (const Bucket& b : c->all_buckets) {
+        CU(launch_inviscid_gl(M, b, q, out, g, mode, stage, dt, write_tr, s));
+        ++nl;
+      }
+    }
+    if (nlaunch) *nlaunch += nl;
+    return DG_OK;
+  }
   if (M.model == 1) {  // compressible form: no mortar phases (conforming faces only)
     if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
       for (const Bucket& b : c->ord_buckets) {
@@ -1039,6 +1134,12 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
       o1.w[N][i] = T.rule[N].w[i];
       o1.x[N][i] = T.rule[N].x[i];
     }
+    for (int i = 0; i < n * n; ++i) o1.Dg[N][i] = T.gl[N].D[i];
+    for (int i = 0; i < n; ++i) {
+      o1.wg[N][i] = T.gl[N].w[i];
+      o1.lbg[N][0][i] = T.glb[N][0][i];
+      o1.lbg[N][1][i] = T.glb[N][1][i];
+    }
   }
   cudaError_t ce = upload_ops(o1);
   if (ce == cudaSuccess) ce = prepare_kernels();
@@ -1058,6 +1159,11 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
     return st;
   }
   c->M.proj = dtab;
+  if ((st = dev_upload(c, "interp_gl", T.interp_gl, &dtab)) != DG_OK) {
+    dg_destroy(c);
+    return st;
+  }
+  c->M.interp_gl = dtab;
   int* derr;
   if ((st = dev_alloc(c, "err", 4, &derr)) != DG_OK) {
     dg_destroy(c);
@@ -1101,7 +1207,8 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
 dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* stream) {
   if (!c || !q_old || !q_new) return fail(DG_ERR_ARG, "NULL argument");
   if (c->prev_order.empty()) return fail(DG_ERR_STATE, "dg_project_state needs a preceding dg_set_orders");
-  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form only");
+  if (c->prm.model != 0 || c->prm.nodes != 0)
+    return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form on Gauss-Lobatto nodes only");
   if (q_old == q_new) return fail(DG_ERR_ARG, "q_old and q_new must not overlap");
   CU(cudaSetDevice(c->device));
   int8_t* dord = nullptr;
@@ -1163,7 +1270,8 @@ dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8
                             double* feat, void* stream) {
   if (!c || !q || !gmm) return fail(DG_ERR_ARG, "NULL argument");
   if (!flags && !pbar && !feat) return fail(DG_ERR_ARG, "dg_detect_regions: no output requested");
-  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_detect_regions: incompressible form only");
+  if (c->prm.model != 0 || c->prm.nodes != 0)
+    return fail(DG_ERR_UNSUPPORTED, "dg_detect_regions: incompressible form on Gauss-Lobatto nodes only");
   GmmDev g{};
   dg_status st = gmm_prepare(*gmm, g);
   if (st != DG_OK) return st;
@@ -1355,7 +1463,8 @@ static_assert(DG_CONSERVATION_NOALLOC_MAX_ELEMS == kNoAllocMaxElems, "scratch li
 // argument built on the stack; the partial sums use the static scratch of dg_noalloc.cu.
 dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, void* stream) {
   if (!c || !R || !out_dev) return fail(DG_ERR_ARG, "NULL argument");
-  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form only");
+  if (c->prm.model != 0 || c->prm.nodes != 0)
+    return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form on Gauss-Lobatto nodes only");
   if (c->ne > kNoAllocMaxElems)
     return fail(DG_ERR_ARG, "dg_conservation_noalloc: the mesh has %lld elements, the static scratch holds %lld",
                 (long long)c->ne, (long long)kNoAllocMaxElems);
@@ -1588,8 +1697,9 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
     const bool ns = c->flag[e] != 0;
     const bool curved = c->ec[e].curved != 0.0;
     const double geo = curved ? 10.0 * n3 * (f32 ? 4.0 : 8.0) : (f32 ? 48.0 : 112.0);
-    // traces: launched in one stage out of three (q at the face nodes in, traces out)
-    b[0] += (nv * 6.0 * n2 * d + nv * 6.0 * n2 * tr) / 3.0;
+    // traces: launched in one stage out of three (q at the face nodes in, or the whole
+    // element on Gauss-Legendre nodes, traces out)
+    b[0] += ((c->prm.nodes == 1 ? nv * n3 * d : nv * 6.0 * n2 * d) + nv * 6.0 * n2 * tr) / 3.0;
     // inviscid + update: q in and out, g out (and in for two stages of three), geometry,
     // traces of the new state written in two stages of three
     double inv = nv * n3 * d * 2.0 + nv * n3 * sg * (1.0 + 2.0 / 3.0) + geo + (2.0 / 3.0) * nv * 6.0 * n2 * tr;

@@ -87,6 +87,10 @@ struct DevMesh {
   // 1 compressible (App. A, u = (rho, rho v, rho e); FP64, conforming periodic meshes)
   int model;
   double gamma, prandtl, prandtl_t;  // compressible: ideal gas with unit gas constant
+  // element nodes: 0 Gauss-Lobatto, 1 Gauss-Legendre (face values interpolated; FP64,
+  // incompressible, conforming interior/periodic faces)
+  int nodes;
+  const double* interp_gl;   // [(g*NP+N)*NP*NP + i*NP + j]: Gauss-Lobatto degree g -> Gauss-Legendre order N
 };
 
 // 1D Gauss-Lobatto operators for N = 1..MAXN (uploaded to constant memory).
@@ -94,6 +98,10 @@ struct Ops1D {
   double D[NP][NP * NP];  // D[N][i*n+m]
   double w[NP][NP];       // w[N][i]
   double x[NP][NP];       // x[N][i]
+  // Gauss-Legendre element nodes (nodes = 1)
+  double Dg[NP][NP * NP];    // D[N][i*n+m] on the Gauss points
+  double wg[NP][NP];         // Gauss weights
+  double lbg[NP][2][NP];     // l_i(-1), l_i(+1)
 };
 
 // Per-entry record of a bucket (32 bytes, copied whole into shared memory by the
@@ -171,6 +179,15 @@ cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u
 cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
 cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
                                 int mode, int stage, double dt, int write_tr, cudaStream_t s);
+
+// Gauss-Legendre element nodes (dg_gl.cu), FP64, incompressible form: traces are the face values
+// interpolated along the normal lines; face terms are lifted with l_i(+-1) / w_i.
+cudaError_t upload_ops_gl(const Ops1D& ops);
+cudaError_t prepare_kernels_gl();
+cudaError_t launch_traces_gl(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_viscous_gl(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
+cudaError_t launch_inviscid_gl(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                               int mode, int stage, double dt, int write_tr, cudaStream_t s);
 
 // Region detection (dg_regions.cu): the mixture as the kernel uses it.
 struct GmmDev {

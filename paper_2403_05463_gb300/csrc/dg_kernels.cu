@@ -28,50 +28,6 @@ __constant__ Ops1D c_ops;
 __constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 __constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 
-// y = A(ub) x for the artificial-compressibility flux Jacobian in direction nh
-__device__ __forceinline__ void ac_jac_apply(const double ub[3], double un, const double nh[3],
-                                             double c0sq, const double x[4], double y[4]) {
-  double nx = nh[0] * x[1] + nh[1] * x[2] + nh[2] * x[3];
-  y[0] = c0sq * nx;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) y[1 + c] = nh[c] * x[0] + ub[c] * nx + un * x[1 + c];
-}
-
-// Fluctuation A^-(qbar) dq = (F* - F_n(q-)) for Roe (riemann == 0): the flux is quadratic,
-// so F(q+) - F(q-) = A(qbar) dq exactly with qbar the arithmetic mean, and |A| is the
-// quadratic polynomial in A that matches |lambda| on the three distinct eigenvalues
-// u_n - a, u_n, u_n + a (a = sqrt(u_n^2 + c0^2)). For LLF: 1/2 (A dq - lambda_max dq).
-__device__ __forceinline__ void flux_fluct(const double qm[4], const double qp[4], const double nh[3],
-                                           double c0sq, int riemann, double out[4]) {
-  double dq[4], ub[3];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) dq[v] = qp[v] - qm[v];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (qm[1 + c] + qp[1 + c]);
-  double un = ub[0] * nh[0] + ub[1] * nh[1] + ub[2] * nh[2];
-  double y1[4];
-  ac_jac_apply(ub, un, nh, c0sq, dq, y1);
-  if (riemann == 0) {
-    double y2[4];
-    ac_jac_apply(ub, un, nh, c0sq, y1, y2);
-    double a = sqrt(un * un + c0sq);
-    double aun = fabs(un);
-    double lm = un - a, l0 = un;
-    double d1 = (aun + un - a) / a;        // divided difference of |.| on (lm, l0)
-    double d2 = (a - aun) / (a * a);       // second divided difference on (lm, l0, lp)
-    double k0 = -lm - d1 * lm + d2 * lm * l0;
-    double k1 = d1 - d2 * (lm + l0);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - (k0 * dq[v] + k1 * y1[v] + d2 * y2[v]));
-  } else {
-    double unm = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
-    double unp = qp[1] * nh[0] + qp[2] * nh[1] + qp[3] * nh[2];
-    double lam = fmax(fabs(unm) + sqrt(unm * unm + c0sq), fabs(unp) + sqrt(unp * unp + c0sq));
-#pragma unroll
-    for (int v = 0; v < 4; ++v) out[v] = 0.5 * (y1[v] - lam * dq[v]);
-  }
-}
-
 // Full numerical flux F*(q-, q+) (mortar faces): F_n(q-) + fluctuation.
 __device__ __forceinline__ void flux_full(const double qm[4], const double qp[4], const double nh[3],
                                           double c0sq, int riemann, double out[4]) {
@@ -696,7 +652,7 @@ __global__ void k_node_coords(DevMesh M, const int32_t* __restrict__ list, int c
   const int e = list[gid / n3], p = (int)(gid % n3);
   const int i = p % n, j = (p / n) % n, k = p / (n * n);
   const int ng = gdeg + 1, ng3 = ng * ng * ng;
-  const double* I = M.interp + (gdeg * NP + N) * NP * NP;
+  const double* I = (M.nodes == 1 ? M.interp_gl : M.interp) + (gdeg * NP + N) * NP * NP;
   for (int c = 0; c < 3; ++c) {
     double s = 0.0;
     for (int cc = 0; cc < ng; ++cc)
@@ -719,7 +675,8 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
   for (int v = 0; v < nvar; ++v) {
     double s = 0.0;
     for (int p = 0; p < n3; ++p) {
-      const double w = c_ops.w[N][p % n] * c_ops.w[N][(p / n) % n] * c_ops.w[N][p / (n * n)];
+      const double(*wt)[NP] = M.nodes == 1 ? c_ops.wg : c_ops.w;
+      const double w = wt[N][p % n] * wt[N][(p / n) % n] * wt[N][p / (n * n)];
       const double J = curved ? M.geo[9 * M.total + off + p] : M.ec[e].J;
       s += w * J * R[v * M.total + off + p];
     }
@@ -733,6 +690,7 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
 cudaError_t upload_ops(const Ops1D& ops) {
   cudaError_t r = cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D));
   if (r == cudaSuccess) r = upload_ops_cns(ops);
+  if (r == cudaSuccess) r = upload_ops_gl(ops);
   return r == cudaSuccess ? upload_ops32(ops) : r;
 }
 
@@ -774,6 +732,7 @@ cudaError_t prepare_kernels() {
   if ((r = prep_n<6>()) != cudaSuccess) return r;
   if ((r = prep_n<7>()) != cudaSuccess) return r;
   if ((r = prepare_kernels_cns()) != cudaSuccess) return r;
+  if ((r = prepare_kernels_gl()) != cudaSuccess) return r;
   return prepare_kernels32();
 }
 

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("cv", ctypes.c_double), ("closure", ctypes.c_int), ("riemann", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
                 ("model", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("gamma", ctypes.c_double),
-                ("prandtl", ctypes.c_double), ("prandtl_t", ctypes.c_double)]
+                ("prandtl", ctypes.c_double), ("prandtl_t", ctypes.c_double), ("nodes", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class GMM(ctypes.Structure):
@@ -132,6 +133,8 @@ def make_params(p: dict, precision=0) -> Params:
     out.gamma = float(p.get("gamma", 1.4))
     out.prandtl = float(p.get("prandtl", 0.72))
     out.prandtl_t = float(p.get("prandtl_t", 0.9))
+    out.nodes = int(p.get("nodes", 0))
+    out.reserved = 0
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
     return out

@@ -1,0 +1,146 @@
+"""Gauss-Legendre element nodes (dg_params.nodes = 1, App. B's quadrature) on the GPU, through the
+C ABI, against the oracle on the same node set: node coordinates, residuals, RK steps and
+conservation sums at the FP64 tolerance 1e-12 (relative L2) on box, re-oriented curved and every
+order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman and both mixed-face choices; plus what the
+node set refuses."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from helpers import rel_l2, to_dev
+from oracle import oracle as orc
+from paper_2403_05463_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _oracle(w, params):
+    m = w.mesh
+    return orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**params), m.bc_tag)
+
+
+def _solver(w, params):
+    from paper_2403_05463_gb300 import dg
+    return dg.Solver.from_workload(w, precision=0, params=dict(params))
+
+
+def _box(order, n=4, seed=0):
+    w = wl.tgv_4x4x4_n3(n_elem_dir=n, order=order)
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8))
+
+
+def _curved(order, seed):
+    w = wl.padapt_32x32x32(n=4, amp=0.05)
+    mesh, _ = wl.rotate_elements(w.mesh, seed)
+    rng = np.random.default_rng(seed)
+    flags = (rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8)
+    return dataclasses.replace(w, mesh=mesh, orders=np.full(w.n_elem, order, np.int8), flags=flags)
+
+
+def _gl(w, **kw):
+    return dict(w.params, nodes=1, **kw)
+
+
+CASES = [
+    ("box_n4", lambda: _box(4), dict(nu=1e-2)),
+    ("box_n3_vreman_llf_onesided", lambda: _box(3, seed=1), dict(nu=1e-2, closure=1, riemann=1, mixed_face=1)),
+    ("curved_n3", lambda: _curved(3, 61), dict(nu=1e-2)),
+    ("curved_n5", lambda: _curved(5, 62), dict(nu=1e-2, closure=1)),
+]
+
+
+@pytest.mark.parametrize("name,make,extra", CASES, ids=[c[0] for c in CASES])
+def test_residual_matches_the_oracle(name, make, extra):
+    w = make()
+    p = _gl(w, **extra)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    R_ref = M.residual(q)
+    S = _solver(w, p)
+    np.testing.assert_allclose(S.node_coords().cpu().numpy(), M.node_coords(), atol=1e-13)
+    R = S.residual(to_dev(q)).cpu().numpy()
+    err = rel_l2(R, R_ref)
+    assert err <= TOL, err
+    assert np.abs(R - R_ref).max() <= 10 * TOL * np.abs(R_ref).max()
+
+
+@pytest.mark.parametrize("order", [1, 2, 6, 7])
+def test_every_order(order):
+    w = _box(1, n=5) if order == 1 else _curved(order, 70 + order)
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    R = _solver(w, p).residual(to_dev(q)).cpu().numpy()
+    assert rel_l2(R, M.residual(q)) <= TOL
+
+
+def test_rk_steps_and_conservation():
+    w = _curved(3, 80)
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    g = np.zeros_like(q)
+    S = _solver(w, p)
+    qd, gd = to_dev(q), to_dev(g)
+    S.rk_step(qd, gd, 1e-3, 5)
+    M.rk_step(q, g, 1e-3, 5)
+    assert rel_l2(qd.cpu().numpy(), q) <= TOL
+    R = S.residual(qd)
+    sums = S.conservation(R)
+    scale = np.abs(R.cpu().numpy()).max()
+    assert np.all(np.abs(sums) <= 1e-11 * scale), sums
+    np.testing.assert_allclose(sums, M.conservation(R.cpu().numpy()), atol=1e-11 * scale)
+
+
+def test_what_gauss_legendre_refuses():
+    import torch
+    from paper_2403_05463_gb300 import dg
+    wake = wl.wake_16x16x16_n4(n=3, order=2)
+    with pytest.raises(dg.DGError) as ei:
+        _solver(wake, _gl(wake))
+    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
+    w = _box(3)
+    p = _gl(w)
+    S = _solver(w, p)
+    o = w.orders.copy()
+    o[0] = 4
+    with pytest.raises(dg.DGError) as ei:
+        S.set_orders(o)
+    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
+    for bad, prec in ((dict(split=1), 0), (dict(model=1), 0), ({}, 1)):
+        with pytest.raises(dg.DGError):
+            S.set_params(dict(p, **bad), precision=prec)
+    S.set_params(p, precision=0)
+    q = torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DGError):
+        S.conservation_noalloc(q, torch.zeros(4, dtype=torch.float64, device="cuda"))
+    with pytest.raises(dg.DGError):
+        S.detect_regions(q, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": [np.eye(3)] * 2, "viscous": 1})
+
+
+def test_a_32cube_case_sampled():
+    """tgv 32^3 at N = 5 on Gauss-Legendre nodes (4.4 M nodes), 30% NS: the whole mesh on the
+    GPU, a sample of elements on the oracle."""
+    w = wl.tgv_32x32x32_n5()
+    p = _gl(w, nu=1e-3)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    R = _solver(w, p).residual(to_dev(q)).cpu().numpy()
+    rng = np.random.default_rng(3)
+    ns, eu = np.flatnonzero(w.flags), np.flatnonzero(w.flags == 0)
+    sel = np.concatenate([rng.choice(ns, 20, replace=False), rng.choice(eu, 20, replace=False), [0, w.n_elem - 1]])
+    idx = np.concatenate([np.arange(M.offsets[e], M.offsets[e + 1]) for e in sel])
+    R_ref = np.zeros_like(q)
+    M.residual(q, sel=sel, out=R_ref)
+    assert rel_l2(R[:, idx], R_ref[:, idx]) <= TOL
