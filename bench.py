@@ -41,7 +41,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_64x64x64_n4")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3"],
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "tf32"],
                     help="fp32: FP32 arithmetic with FP64 state and FP64 accumulation of q (the large "
                          "mixed configuration's precision); fp64: FP64 throughout")
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
@@ -306,6 +306,32 @@ def time_compressible(stream, device=0, steps=10):
             "phases": {k: {"ms": ph_ms[k], "algorithmic_gb": ph_b[k] / 1e9} for k in ph_ms if ph_ms[k] > 0}}
 
 
+def time_gauss_legendre(stream, device=0, steps=5):
+    """FP64 RK3 steps of the incompressible form on tgv 32^3 N = 5 (4.4 M nodes, 30% NS) on
+    Gauss-Lobatto and on Gauss-Legendre element nodes, CUDA events on the launching stream."""
+    import torch
+    from paper_2403_05463_gb300 import dg, workloads as wl
+    w = wl.tgv_32x32x32_n5()
+    out = {"workload": w.name, "dtype": "f64", "unit": UNIT}
+    for nodes, name in ((0, "gauss_lobatto"), (1, "gauss_legendre")):
+        S = dg.Solver.from_workload(w, precision=0, device=device, params=dict(w.params, nodes=nodes))
+        xyz = S.node_coords()
+        q = torch.from_numpy(w.state(xyz.cpu().numpy())).to(xyz.device)
+        g = torch.zeros_like(q)
+        S.rk_step(q, g, w.dt, 2, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.rk_step(q, g, w.dt, steps, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        S.check_device()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "value": S.total_nodes * 3 / (ms * 1e-3)}
+        del S, q, g, xyz
+    return out
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -377,7 +403,7 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3"}[args.precision], "data": "synthetic",
+           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3", "tf32": "tf32"}[args.precision], "data": "synthetic",
            "config": {"workload": w.name, "n_elem": int(w.n_elem), "order": int(w.orders.max()), "dof": int(dof),
                       "ns_fraction": w.ns_fraction, "precision": args.precision, "stages_per_step": 3,
                       "state": "FP64 q, g resident in HBM; FP64 RK accumulation",
@@ -417,6 +443,8 @@ def main():
         out["detect"] = time_detection(S, w, q, q0, stream)
         # the compressible form (App. A), FP64, on its own periodic workload
         out["compressible"] = time_compressible(stream, device=local)
+        # Gauss-Legendre element nodes (App. B's quadrature) against Gauss-Lobatto, FP64
+        out["gauss_legendre"] = time_gauss_legendre(stream, device=local)
         # end to end through the C ABI with host buffers (pinned), copies inside the timing
         qh = q0.cpu().pin_memory()
         gh = torch.zeros_like(qh).pin_memory()

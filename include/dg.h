@@ -92,7 +92,9 @@ typedef struct {
                        traces and Runge-Kutta accumulation; 2 as 1, with the inviscid
                        volume term's D contractions on the tensor cores in 3xTF32 (each
                        FP32 operand split into two TF32 parts, big*big + big*small +
-                       small*big accumulated in FP32; the split form keeps FP32 FMAs)   */
+                       small*big accumulated in FP32; the split form keeps FP32 FMAs);
+                       3 as 2 with plain TF32 (only big*big: operands rounded to 10
+                       mantissa bits; an accuracy contrast, not a production setting)    */
   int mixed_face;   /* viscous flux on a face between an NS and an Euler element (Sec. 2.3
                        asks only that it be single-valued): 0 the average of the NS side's
                        flux and zero (BR1 with an inviscid side), 1 the NS side's flux

@@ -380,7 +380,7 @@ dg_status check_params(const dg_params* p) {
     return fail(DG_ERR_ARG, "need c0sq > 0 and nu, cs, cv >= 0");
   if (p->closure < 0 || p->closure > 1) return fail(DG_ERR_ARG, "closure must be 0 or 1");
   if (p->riemann < 0 || p->riemann > 1) return fail(DG_ERR_ARG, "riemann must be 0 or 1");
-  if (p->precision < 0 || p->precision > 2) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
+  if (p->precision < 0 || p->precision > 3) return fail(DG_ERR_UNSUPPORTED, "precision %d not built", p->precision);
   if (p->mixed_face < 0 || p->mixed_face > 1) return fail(DG_ERR_ARG, "mixed_face must be 0 or 1");
   if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
   if (p->model < 0 || p->model > 1) return fail(DG_ERR_ARG, "model must be 0 or 1");
@@ -418,10 +418,10 @@ void apply_params(dg_ctx* c) {
   c->M.gamma = c->prm.gamma;
   c->M.prandtl = c->prm.prandtl;
   c->M.prandtl_t = c->prm.prandtl_t;
-  // precision 2 is the FP32 path (same data layout) with the inviscid volume contraction on
-  // the tensor cores
+  // precisions 2 and 3 are the FP32 path (same data layout) with the inviscid volume
+  // contraction on the tensor cores (3xTF32, plain TF32)
   c->M.precision = c->prm.precision >= 1 ? 1 : 0;
-  c->M.tc = c->prm.precision == 2 ? 1 : 0;
+  c->M.tc = c->prm.precision == 2 ? 1 : (c->prm.precision == 3 ? 2 : 0);
   c->M.nu32 = (float)c->prm.nu;
   c->M.c0sq32 = (float)c->prm.c0sq;
   c->M.cs32 = (float)c->prm.cs;

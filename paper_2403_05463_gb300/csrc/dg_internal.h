@@ -80,7 +80,8 @@ struct DevMesh {
   int mixed_face;            // 0 average, 1 one-sided viscous flux on NS/Euler faces
   int split;                 // 0 standard convective volume term, 1 kinetic-energy-preserving split form
   int precision;             // 0: Tv/rv hold FP64; 1: they hold FP32 (same buffers)
-  int tc;                    // 1: the FP32 inviscid volume contraction on tensor cores (3xTF32)
+  int tc;                    // the FP32 inviscid volume contraction on tensor cores: 1 in 3xTF32,
+                             // 2 in plain TF32 (one product of the rounded operands); 0 FP32 FMAs
   float nu32, c0sq32, cs32, cv32, dt32;  // FP32 copies for the reduced-precision passes
   double inflow[4];
   // governing equations: 0 incompressible (artificial compressibility, q = (p, u, v, w)),

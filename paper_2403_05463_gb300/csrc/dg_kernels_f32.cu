@@ -1028,8 +1028,10 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
           tf32_split((m < n && gq < n) ? sD[gq * n + m] : 0.f, bb[k], bs[k]);
         }
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_tf32(c, as, bb);
-        mma_tf32(c, ab, bs);
+        if (M.tc == 1) {  // 3xTF32: the two correction products first; plain TF32 (tc 2) skips them
+          mma_tf32(c, as, bb);
+          mma_tf32(c, ab, bs);
+        }
         mma_tf32(c, ab, bb);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {

@@ -22,7 +22,7 @@ DG_OK = 0
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH", 3: "DG_ERR_CUDA", 4: "DG_ERR_OOM",
           5: "DG_ERR_UNSUPPORTED", 6: "DG_ERR_STATE", 7: "DG_ERR_TIMEOUT", 8: "DG_ERR_DEVICE"}
 
-PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3}
 
 
 class DGError(RuntimeError):

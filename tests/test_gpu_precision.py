@@ -145,6 +145,16 @@ def test_tf32x3_every_order_rk_steps():
     assert err <= 1.5 * BOUNDS["tgv_4x4x4_n3_rk3_10_steps_update"]
 
 
+def test_plain_tf32_contrast():
+    # precision 3: one TF32 product of operands rounded to 10 mantissa bits, reported against
+    # the FP64 oracle beside FP32 and 3xTF32 on the precision-variant configuration (reduced)
+    w = wl.tgv_32x32x32_n5(n=8)
+    errs = {p: _fp32_error(w, precision=p) for p in (1, 2, 3)}
+    _record("tgv_8x8x8_n5_slab30_tf32", errs[3])
+    assert errs[3] > 10 * errs[2], errs  # the correction products matter
+    assert errs[3] < 5e-2, errs
+
+
 @pytest.mark.parametrize("wall", [3, 4])
 def test_fp32_walls(wall):
     w = wl.channel_walls(n=6, wall=wall)
