@@ -468,21 +468,10 @@ cudaError_t prepare_kernels_cns() {
   return prep_cns<7>();
 }
 
-#define DG_CNS_N(NVAR, ...)                                     \
-  switch (NVAR) {                                               \
-    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;       \
-    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;       \
-    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;       \
-    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;       \
-    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;       \
-    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;       \
-    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;       \
-    default: return cudaErrorInvalidValue;                      \
-  }
 
 cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_CNS_N(b.N, {
+  DG_SWITCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
     k_traces_cns<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, u);
   });
@@ -491,7 +480,7 @@ cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u
 
 cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_CNS_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     if (b.curved)
@@ -505,7 +494,7 @@ cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* 
 cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
                                 int mode, int stage, double dt, int write_tr, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_CNS_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     const size_t sm = inv_smem_cns<NN>();

@@ -4,6 +4,20 @@
 
 namespace dgk {
 
+// Runs the statements with the compile-time order NN = NVAR (1..MAXN); other values return
+// cudaErrorInvalidValue from the enclosing launcher.
+#define DG_SWITCH_N(NVAR, ...)                                  \
+  switch (NVAR) {                                               \
+    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;       \
+    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;       \
+    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;       \
+    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;       \
+    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;       \
+    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;       \
+    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;       \
+    default: return cudaErrorInvalidValue;                      \
+  }
+
 template <int N>
 struct Shape {
   static constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;

@@ -478,21 +478,10 @@ cudaError_t prepare_kernels_gl() {
   return prep_gl<7>();
 }
 
-#define DG_GL_N(NVAR, ...)                                      \
-  switch (NVAR) {                                               \
-    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;       \
-    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;       \
-    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;       \
-    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;       \
-    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;       \
-    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;       \
-    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;       \
-    default: return cudaErrorInvalidValue;                      \
-  }
 
 cudaError_t launch_traces_gl(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_GL_N(b.N, {
+  DG_SWITCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
     k_traces_gl<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, q);
   });
@@ -501,7 +490,7 @@ cudaError_t launch_traces_gl(const DevMesh& M, const Bucket& b, const double* q,
 
 cudaError_t launch_viscous_gl(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_GL_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     if (b.curved)
@@ -515,7 +504,7 @@ cudaError_t launch_viscous_gl(const DevMesh& M, const Bucket& b, const double* q
 cudaError_t launch_inviscid_gl(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                int mode, int stage, double dt, int write_tr, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_GL_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     if (mode == MODE_RESIDUAL) {

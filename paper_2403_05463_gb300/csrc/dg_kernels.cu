@@ -736,22 +736,11 @@ cudaError_t prepare_kernels() {
   return prepare_kernels32();
 }
 
-#define DG_DISPATCH_N(NVAR, ...)                                  \
-  switch (NVAR) {                                                 \
-    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;         \
-    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;         \
-    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;         \
-    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;         \
-    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;         \
-    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;         \
-    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;         \
-    default: return cudaErrorInvalidValue;                        \
-  }
 
 cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s) {
   if (precision == 1) return launch_traces32(M, b, q, s);
   if (b.count == 0) return cudaSuccess;
-  DG_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
     const int thr = 256;
     k_traces<NN><<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(M, b.list, b.count, q);
@@ -762,7 +751,7 @@ cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, in
 cudaError_t launch_viscous(const DevMesh& M, const Bucket& b, const double* q, int precision, cudaStream_t s) {
   if (precision == 1) return launch_viscous32(M, b, q, s);
   if (b.count == 0) return cudaSuccess;
-  DG_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     if (b.curved)
@@ -787,7 +776,7 @@ cudaError_t launch_inviscid(const DevMesh& M, const Bucket& b, const double* q, 
                             int mode, int stage, double dt, int write_tr, int precision, cudaStream_t s) {
   if (precision == 1) return launch_inviscid32(M, b, q, out, g, mode, stage, write_tr, s);
   if (b.count == 0) return cudaSuccess;
-  DG_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     if (M.split == 1) {
       if (mode == MODE_RESIDUAL)
         return b.curved ? launch_inv64<NN, true, MODE_RESIDUAL, true>(M, b, q, out, g, stage, dt, write_tr, s)
@@ -826,7 +815,7 @@ cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, int count
 cudaError_t launch_node_coords(const DevMesh& M, const double* gn, int gdeg, const Bucket& b, double* xyz,
                                cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * (NN + 1) * (NN + 1) * (NN + 1);
     k_node_coords<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, gn, gdeg, xyz);
   });
@@ -836,7 +825,7 @@ cudaError_t launch_node_coords(const DevMesh& M, const double* gn, int gdeg, con
 cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, int nvar, double* partial,
                                 cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     k_conservation<NN><<<(unsigned)((b.count + 127) / 128), 128, 0, s>>>(M, b.list, b.count, R, nvar, partial);
   });
   return cudaGetLastError();

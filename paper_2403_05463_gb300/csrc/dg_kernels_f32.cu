@@ -1547,21 +1547,9 @@ cudaError_t prepare_kernels32() {
   return cudaSuccess;
 }
 
-#define DG32_DISPATCH_N(NVAR, ...)                         \
-  switch (NVAR) {                                          \
-    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;  \
-    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;  \
-    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;  \
-    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;  \
-    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;  \
-    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;  \
-    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;  \
-    default: return cudaErrorInvalidValue;                 \
-  }
-
 cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG32_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     const int64_t tot = (int64_t)b.count * 6 * (NN + 1) * (NN + 1);
     k_traces32<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, q);
   });
@@ -1593,12 +1581,12 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
   if (b.count == 0) return cudaSuccess;
   if (b.geo != 2 && b.visc_alt == 0) {  // box and affine: the pipelined kernel unless tuned away
     if (!b.blink || !b.bmeta) return cudaErrorInvalidValue;
-    DG32_DISPATCH_N(b.N, {
+    DG_SWITCH_N(b.N, {
       return b.geo == 0 ? launch_vpipe<NN, 0>(M, b, q, s) : launch_vpipe<NN, 1>(M, b, q, s);
     });
     return cudaSuccess;
   }
-  DG32_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     using SH = Shape<NN>;
     const unsigned grid = (unsigned)((b.count + SH::EPB - 1) / SH::EPB);
     if (b.geo == 0)
@@ -1664,7 +1652,7 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
                               int stage, int write_tr, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
   if (!b.boff || !b.btr || !b.blink || !b.bflag || !b.bmeta) return cudaErrorInvalidValue;
-  DG32_DISPATCH_N(b.N, {
+  DG_SWITCH_N(b.N, {
     // the split form and the tensor-core contraction are built for the default tile shape; the
     // split form's two-point sums are no plain contraction and stay on the FP32 pipe
     if (M.split == 1) return launch_inv_shape<NN, Shape<NN>::EPB, 1>(M, b, q, out, g, mode, stage, write_tr, s);

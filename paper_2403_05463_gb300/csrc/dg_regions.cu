@@ -179,17 +179,6 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   }
 }
 
-#define DG_DETECT_N(NVAR, ...)                                   \
-  switch (NVAR) {                                                \
-    case 1: { constexpr int NN = 1; __VA_ARGS__; } break;        \
-    case 2: { constexpr int NN = 2; __VA_ARGS__; } break;        \
-    case 3: { constexpr int NN = 3; __VA_ARGS__; } break;        \
-    case 4: { constexpr int NN = 4; __VA_ARGS__; } break;        \
-    case 5: { constexpr int NN = 5; __VA_ARGS__; } break;        \
-    case 6: { constexpr int NN = 6; __VA_ARGS__; } break;        \
-    case 7: { constexpr int NN = 7; __VA_ARGS__; } break;        \
-    default: return cudaErrorInvalidValue;                       \
-  }
 
 template <int N, typename T>
 static void launch_detect_t(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D, const double* q,
@@ -207,7 +196,7 @@ static void launch_detect_t(const DevMesh& M, const Bucket& b, const GmmDev& g, 
 cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDev& g, const DMatArg& D, int fp32,
                                   const double* q, uint8_t* flags, double* pbar, double* feat, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;
-  DG_DETECT_N(b.N, {
+  DG_SWITCH_N(b.N, {
     if (fp32)
       launch_detect_t<NN, float>(M, b, g, D, q, flags, pbar, feat, s);
     else
