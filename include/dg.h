@@ -125,8 +125,9 @@ typedef struct {
                        traces are interpolated along the normal lines and face terms lifted
                        with l_i(+-1) / w_i. Nodes 1 runs the incompressible form (model 0)
                        in FP64 (precision 0) with the standard volume term (split 0) on
-                       meshes whose faces are all interior or periodic and conforming; other
-                       settings give DG_ERR_UNSUPPORTED, as do dg_project_state,
+                       meshes whose faces are conforming (boundary faces take the same ghost
+                       states as on Gauss-Lobatto nodes); other settings give
+                       DG_ERR_UNSUPPORTED, as do dg_project_state,
                        dg_conservation_noalloc and dg_detect_regions. dg_node_coords returns
                        the Gauss points.                                                 */
   int reserved;     /* must be 0                                                       */
@@ -186,7 +187,11 @@ dg_status dg_rk_step(dg_ctx* ctx, double* q_dev, double* g_dev, double t, double
                      void* stream);
 
 /* Host-buffer variants: copy the host arrays to library-owned device buffers, compute on
- * `stream`, copy the result back and synchronise the stream before returning. */
+ * `stream`, copy the result back and synchronise the stream before returning. Each transfer is
+ * split over several library-owned streams so that copy engines can work in parallel; the
+ * host arrays should be pinned (page-locked) for full speed. g_host may be NULL: the first
+ * stage of every step overwrites the RK register without reading it, so it then stays in a
+ * library-owned device buffer and only q is copied in and out. */
 dg_status dg_residual_host(dg_ctx* ctx, const double* q_host, double* R_host, void* stream);
 dg_status dg_rk_step_host(dg_ctx* ctx, double* q_host, double* g_host, double t, double dt, int nsteps,
                           void* stream);

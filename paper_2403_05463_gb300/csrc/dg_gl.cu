@@ -15,7 +15,8 @@
 // With Gauss quadrature exact to degree 2N+1, this strong form equals the weak form of Eq. NS4
 // (the integration by parts is exact for the degree-2N-1 products), face terms included:
 // (.)_face is the interpolant of the nodal product, as the weak form's boundary term requires.
-// Conforming interior or periodic faces only (the host refuses other meshes).
+// Conforming faces only (the host refuses p-nonconforming meshes); boundary faces take the
+// ghost states of the Gauss-Lobatto path (inflow, outflow, no-slip and free-slip walls).
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         const int f = 2 * d + s;
         const double sg = s ? 1.0 : -1.0;
         const FaceLink L = M.link[e * 6 + f];
-        if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
+        if (L.kind == FK_MORTAR) {  // the host admits conforming faces only
           atomicCAS(&M.err[0], 0, 5);
           atomicCAS(&M.err[1], 0, 20);
           continue;
@@ -185,12 +186,28 @@ __global__ void __launch_bounds__(Shape<N>::threads)
             for (int c = 0; c < 3; ++c) JU[c][k] = Ja[d * 3 + k] * uf[c];
           }
         }
-        int a1, b1;
-        inv_orient(L.orient, N, a, b, a1, b1);
-        const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+        double up[3];  // the neighbour's face velocity, or the ghost's behind a boundary face
+        if (L.kind == FK_CONF) {
+          int a1, b1;
+          inv_orient(L.orient, N, a, b, a1, b1);
+          const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) up[c] = M.Tq[(1 + c) * M.tr_total + ns];
+        } else if (L.kind == FK_INFLOW) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) up[c] = M.inflow[1 + c];
+        } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+          double jw[3];
+          wall_jump<double>(L.kind, uf, Sv, jw);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) up[c] = uf[c] + jw[c];
+        } else {  // outflow: the interior velocity
+#pragma unroll
+          for (int c = 0; c < 3; ++c) up[c] = uf[c];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double us = 0.5 * (uf[c] + M.Tq[(1 + c) * M.tr_total + ns]);
+          const double us = 0.5 * (uf[c] + up[c]);
 #pragma unroll
           for (int k = 0; k < 3; ++k) G[c][k] += cf * sg * (us * Sv[k] - JU[c][k]);
         }
@@ -336,7 +353,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       const double* l = c_lb[N][f & 1];
       const double sg = (f & 1) ? 1.0 : -1.0;
       const FaceLink L = M.link[e * 6 + f];
-      if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
+      if (L.kind == FK_MORTAR) {  // the host admits conforming faces only
         atomicCAS(&M.err[0], 0, 5);
         atomicCAS(&M.err[1], 0, 21);
 #pragma unroll
@@ -365,12 +382,30 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       for (int k = 0; k < 3; ++k) Sv[k] *= sg;
       const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
       const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
-      int a1, b1;
-      inv_orient(L.orient, N, a, b, a1, b1);
-      const int64_t nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
-      double qp[4];
+      double qp[4];  // the neighbour's face state, or the ghost's behind a boundary face
+      int64_t nsl = 0;
+      if (L.kind == FK_CONF) {
+        int a1, b1;
+        inv_orient(L.orient, N, a, b, a1, b1);
+        nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) qp[v] = M.Tq[v * M.tr_total + nsl];
+        for (int v = 0; v < 4; ++v) qp[v] = M.Tq[v * M.tr_total + nsl];
+      } else if (L.kind == FK_INFLOW) {  // prescribed velocity, interior pressure
+        qp[0] = qf[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qp[1 + c] = M.inflow[1 + c];
+      } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {  // mirror states
+        const double uo[3] = {qf[1], qf[2], qf[3]};
+        double jw[3];
+        wall_jump<double>(L.kind, uo, Sv, jw);
+        qp[0] = qf[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qp[1 + c] = qf[1 + c] + jw[c];
+      } else {  // outflow: interior velocity, zero pressure
+        qp[0] = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qp[1 + c] = qf[1 + c];
+      }
       double fx[4];
       flux_fluct(qf, qp, nh, M.c0sq, M.riemann, fx);
       const double un = qf[1] * nh[0] + qf[2] * nh[1] + qf[3] * nh[2];
@@ -378,7 +413,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       tv[0] = s * (M.c0sq * un + fx[0]) - sg * Ff[0];
 #pragma unroll
       for (int c = 0; c < 3; ++c) tv[1 + c] = s * (qf[1 + c] * un + qf[0] * nh[c] + fx[1 + c]) - sg * Ff[1 + c];
-      if (ns || L.nflag) {
+      if (L.kind == FK_CONF && (ns || L.nflag)) {
         float wo, wn;
         visc_face_weights(M.mixed_face, ns, L.nflag != 0, wo, wn);
         const int64_t ms = M.tr_off[e] + t;
@@ -387,6 +422,15 @@ __global__ void __launch_bounds__(Shape<N>::threads)
           if (ns) tv[1 + c] += (double)wo * M.Tv[c * M.tr_total + ms];
           if (L.nflag) tv[1 + c] += (double)wn * M.Tv[c * M.tr_total + nsl];
         }
+      } else if (L.kind == FK_SLIP && ns) {
+        // free-slip wall: F_v* keeps the normal traction, leaving the tangential part of the
+        // own trace; at the other boundaries F_v* is the own (interior) flux and nothing remains
+        const int64_t ms = M.tr_off[e] + t;
+        const double tw[3] = {M.Tv[ms], M.Tv[M.tr_total + ms], M.Tv[2 * M.tr_total + ms]};
+        double tt[3];
+        slip_visc_term<double>(tw, Sv, tt);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tv[1 + c] += tt[c];
       }
 #pragma unroll
       for (int v = 0; v < 4; ++v) T[t * 4 + v] = tv[v];

@@ -326,6 +326,11 @@ struct dg_ctx {
   std::vector<uint8_t> geo_kind;  // 0 axis-aligned box, 1 affine, 2 curved
   bool any_curved = false;
   cudaStream_t cap_stream = nullptr;
+  // host-buffer variants: the transfers are split over kCopyStreams streams (created on first
+  // use), each piece ordered after the caller's stream and joined back into it
+  static constexpr int kCopyStreams = 4;
+  cudaStream_t copy_stream[kCopyStreams] = {};
+  cudaEvent_t copy_fork = nullptr, copy_done[kCopyStreams] = {};
   GraphCache graph;
   uint64_t version = 1;
   int launches_residual = 0, launches_step = 0;
@@ -764,9 +769,10 @@ dg_status check_model_mesh(const dg_ctx* c) {
   if (c->prm.model != 1 && c->prm.nodes != 1) return DG_OK;
   const char* what = c->prm.model == 1 ? "compressible form" : "Gauss-Legendre nodes";
   for (int64_t s = 0; s < c->ne * 6; ++s) {
-    if (c->nb[s] < 0)
+    if (c->nb[s] < 0 && c->prm.model == 1)
       return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is a boundary face (interior and periodic faces "
                   "only)", what, (long long)(s / 6), (int)(s % 6));
+    if (c->nb[s] < 0) continue;
     if (c->order[c->nb[s]] != c->order[s / 6])
       return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is p-nonconforming", what, (long long)(s / 6),
                   (int)(s % 6));
@@ -1396,6 +1402,31 @@ static dg_status ensure_staging(dg_ctx* c) {
   return st;
 }
 
+// One host<->device transfer of `bytes`, split into kCopyStreams pieces issued on the copy
+// streams (several copy engines can then run at once), ordered after the work already on `s`
+// and before the work enqueued on `s` afterwards.
+static dg_status split_copy(dg_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+  constexpr int K = dg_ctx::kCopyStreams;
+  if (!c->copy_fork) {
+    CU(cudaEventCreateWithFlags(&c->copy_fork, cudaEventDisableTiming));
+    for (int i = 0; i < K; ++i) {
+      CU(cudaStreamCreateWithFlags(&c->copy_stream[i], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&c->copy_done[i], cudaEventDisableTiming));
+    }
+  }
+  CU(cudaEventRecord(c->copy_fork, s));
+  const size_t piece = ((bytes + K - 1) / K + 4095) & ~(size_t)4095;  // whole 4 KiB pages
+  for (int i = 0; i < K; ++i) {
+    const size_t off = std::min(bytes, (size_t)i * piece), len = std::min(bytes - off, piece);
+    if (len == 0) continue;
+    CU(cudaStreamWaitEvent(c->copy_stream[i], c->copy_fork, 0));
+    CU(cudaMemcpyAsync((char*)dst + off, (const char*)src + off, len, kind, c->copy_stream[i]));
+    CU(cudaEventRecord(c->copy_done[i], c->copy_stream[i]));
+    CU(cudaStreamWaitEvent(s, c->copy_done[i], 0));
+  }
+  return DG_OK;
+}
+
 dg_status dg_residual_host(dg_ctx* c, const double* q_host, double* R_host, void* stream) {
   if (!c || !q_host || !R_host) return fail(DG_ERR_ARG, "NULL argument");
   CU(cudaSetDevice(c->device));
@@ -1403,25 +1434,27 @@ dg_status dg_residual_host(dg_ctx* c, const double* q_host, double* R_host, void
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * nvar(c) * c->total;
-  CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
+  if ((st = split_copy(c, c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s)) != DG_OK) return st;
   if ((st = dg_residual(c, c->stage_q, c->stage_r, stream)) != DG_OK) return st;
-  CU(cudaMemcpyAsync(R_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s));
+  if ((st = split_copy(c, R_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s)) != DG_OK) return st;
   CU(cudaStreamSynchronize(s));
   return DG_OK;
 }
 
 dg_status dg_rk_step_host(dg_ctx* c, double* q_host, double* g_host, double t, double dt, int nsteps, void* stream) {
-  if (!c || !q_host || !g_host) return fail(DG_ERR_ARG, "NULL argument");
+  if (!c || !q_host) return fail(DG_ERR_ARG, "NULL argument");
   CU(cudaSetDevice(c->device));
   dg_status st = ensure_staging(c);
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * nvar(c) * c->total;
-  CU(cudaMemcpyAsync(c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(c->stage_r, g_host, bytes, cudaMemcpyHostToDevice, s));
+  if ((st = split_copy(c, c->stage_q, q_host, bytes, cudaMemcpyHostToDevice, s)) != DG_OK) return st;
+  // the first stage of every step overwrites the RK register without reading it (A_0 = 0), so
+  // without g_host it simply lives in the library's device buffer
+  if (g_host && (st = split_copy(c, c->stage_r, g_host, bytes, cudaMemcpyHostToDevice, s)) != DG_OK) return st;
   if ((st = dg_rk_step(c, c->stage_q, c->stage_r, t, dt, nsteps, stream)) != DG_OK) return st;
-  CU(cudaMemcpyAsync(q_host, c->stage_q, bytes, cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(g_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s));
+  if ((st = split_copy(c, q_host, c->stage_q, bytes, cudaMemcpyDeviceToHost, s)) != DG_OK) return st;
+  if (g_host && (st = split_copy(c, g_host, c->stage_r, bytes, cudaMemcpyDeviceToHost, s)) != DG_OK) return st;
   CU(cudaStreamSynchronize(s));
   return DG_OK;
 }
@@ -1743,6 +1776,11 @@ void dg_destroy(dg_ctx* c) {
   for (auto& kv : c->buf) cudaFree(kv.second.p);
   c->buf.clear();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (int i = 0; i < dg_ctx::kCopyStreams; ++i) {
+    if (c->copy_stream[i]) cudaStreamDestroy(c->copy_stream[i]);
+    if (c->copy_done[i]) cudaEventDestroy(c->copy_done[i]);
+  }
+  if (c->copy_fork) cudaEventDestroy(c->copy_fork);
   delete c;
 }
 

@@ -270,11 +270,13 @@ class Solver:
         self._check_state(_as_sized(R), "R")
         _check(load().dg_residual_host(self.h, _host_ptr(q), _host_ptr(R), _stream_handle(stream)))
 
-    def rk_step_host(self, q, g, dt, nsteps=1, t=0.0, stream=None):
+    def rk_step_host(self, q, g=None, dt=0.0, nsteps=1, t=0.0, stream=None):
+        """q (and g unless None, see dg_rk_step_host): host arrays, float64 [nvar][total]."""
         self._check_state(_as_sized(q), "q")
-        self._check_state(_as_sized(g), "g")
-        _check(load().dg_rk_step_host(self.h, _host_ptr(q), _host_ptr(g), float(t), float(dt), int(nsteps),
-                                      _stream_handle(stream)))
+        if g is not None:
+            self._check_state(_as_sized(g), "g")
+        _check(load().dg_rk_step_host(self.h, _host_ptr(q), None if g is None else _host_ptr(g), float(t), float(dt),
+                                      int(nsteps), _stream_handle(stream)))
 
     def conservation(self, R, stream=None):
         self._check_state(R, "R")

@@ -1,8 +1,8 @@
 """Gauss-Legendre element nodes (dg_params.nodes = 1, App. B's quadrature) on the GPU, through the
 C ABI, against the oracle on the same node set: node coordinates, residuals, RK steps and
 conservation sums at the FP64 tolerance 1e-12 (relative L2) on box, re-oriented curved and every
-order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman and both mixed-face choices; plus what the
-node set refuses."""
+order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman, both mixed-face choices, inflow/outflow and
+wall boundaries; plus what the node set refuses."""
 import dataclasses
 
 import numpy as np
@@ -103,13 +103,24 @@ def test_rk_steps_and_conservation():
     np.testing.assert_allclose(sums, M.conservation(R.cpu().numpy()), atol=1e-11 * scale)
 
 
+@pytest.mark.parametrize("make", [lambda: wl.wake_16x16x16_n4(n=6, order=4),
+                                  lambda: wl.channel_walls(n=4, wall=3), lambda: wl.channel_walls(n=4, wall=4)],
+                         ids=["wake_inflow_outflow", "channel_noslip", "channel_slip"])
+def test_boundary_faces(make):
+    # inflow/outflow ghosts and no-slip/free-slip mirror walls on Gauss points, mixed flags
+    w = make()
+    rng = np.random.default_rng(5)
+    w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8))
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    R = _solver(w, p).residual(to_dev(q)).cpu().numpy()
+    assert rel_l2(R, M.residual(q)) <= TOL
+
+
 def test_what_gauss_legendre_refuses():
     import torch
     from paper_2403_05463_gb300 import dg
-    wake = wl.wake_16x16x16_n4(n=3, order=2)
-    with pytest.raises(dg.DGError) as ei:
-        _solver(wake, _gl(wake))
-    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
     w = _box(3)
     p = _gl(w)
     S = _solver(w, p)

@@ -307,3 +307,27 @@ def test_bad_inputs_are_rejected():
     with pytest.raises(dg.DGError) as ei:
         dg.Solver(w.mesh.hex, w.mesh.geom, 1, dict(w.params, mixed_face=2))
     assert ei.value.status == 1
+
+
+def test_host_buffer_variants():
+    """dg_residual_host / dg_rk_step_host (split transfers; without g the RK register stays on
+    the device) give the device results."""
+    import torch
+    w = small_mixed(wl.padapt_32x32x32(n=4), seed=90, orders=(2, 4))
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    S = gpu_solver(w)
+    R = S.residual(to_dev(q)).cpu().numpy()
+    Rh = np.zeros_like(q)
+    S.residual_host(q, Rh)
+    np.testing.assert_array_equal(Rh, R)
+    qd, gd = to_dev(q), torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda")
+    S.rk_step(qd, gd, 1e-4, 2)
+    q1 = q.copy()
+    g1 = np.zeros_like(q)
+    S.rk_step_host(q1, g1, 1e-4, 2)
+    np.testing.assert_array_equal(q1, qd.cpu().numpy())
+    np.testing.assert_array_equal(g1, gd.cpu().numpy())
+    q2 = torch.from_numpy(q.copy()).pin_memory()
+    S.rk_step_host(q2, None, 1e-4, 2)
+    np.testing.assert_array_equal(q2.numpy(), qd.cpu().numpy())

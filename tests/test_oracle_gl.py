@@ -2,7 +2,8 @@
 forms and exactness, the derivative matrix on polynomials, and the residual with interpolated
 face values (free stream on curved re-oriented meshes, conservation with the Gauss weights,
 Euler = NS without viscosity, invariance under element re-numbering, spectral convergence to
-the symbolic Taylor-Green residual) and what the node set refuses."""
+the symbolic Taylor-Green residual), the wall mirror identities, the inflow/outflow free stream,
+and what the node set refuses."""
 import dataclasses
 import math
 
@@ -148,3 +149,33 @@ def test_what_gauss_legendre_refuses():
         M.residual(np.zeros((4, M.total)))
     with pytest.raises(ValueError):
         _mesh(w, _params(split=1))
+
+
+@pytest.mark.parametrize("flags_value", [0, 1])
+def test_free_slip_wall_is_a_mirror(flags_value):
+    # the Lobatto pin on Gauss points: interpolation to the wall commutes with the reflection
+    from test_oracle_pins import _mirror_residuals
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        return np.stack([c * (0.3 + 0.1 * np.sin(x[0])), 1.0 + 0.2 * c * np.sin(x[2]), 0.3 * s * np.cos(x[0]),
+                         0.2 * c * np.cos(x[0]) + 0.1 * np.cos(2 * np.pi * x[1] / H)])
+    Rw, Rp = _mirror_residuals(4, state, flags_value, nodes=1)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+def test_no_slip_wall_is_an_antimirror_for_euler():
+    from test_oracle_pins import _mirror_residuals
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        return np.stack([c * (0.2 + 0.1 * np.cos(x[0])), s * (1.0 + 0.1 * np.cos(x[2])),
+                         0.2 * np.sin(2 * np.pi * x[1] / H) * np.cos(x[0]), 0.3 * s * np.sin(x[0])])
+    Rw, Rp = _mirror_residuals(3, state, 0, nodes=1)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+def test_inflow_outflow_free_stream():
+    w = wl.wake_16x16x16_n4(n=3, order=3)
+    M = _mesh(w, _params())
+    q = np.zeros((4, M.total))
+    q[1] = 1.0
+    assert np.abs(M.residual(q)).max() < 1e-12

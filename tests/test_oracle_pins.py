@@ -635,11 +635,11 @@ def _channel(ny, y0, H, tags, N=3):
     return m, np.full(n * ny * n, N, np.int8)
 
 
-def _mirror_residuals(tag, state, flags_value):
+def _mirror_residuals(tag, state, flags_value, nodes=0):
     H = 2.0
     mw, ow = _channel(3, 0.0, H, (tag, tag))      # [0, H] between two walls
     mp, op = _channel(6, -H, 2 * H, None)          # [-H, H], periodic: the mirror extension
-    prm = orc.params(nu=1e-2, c0sq=25.0, cs=0.1)
+    prm = orc.params(nu=1e-2, c0sq=25.0, cs=0.1, nodes=nodes)
     Aw = orc.Mesh(mw.hex, mw.geom, 1, ow, np.full(len(ow), flags_value, np.uint8), prm, mw.bc_tag)
     Ap = orc.Mesh(mp.hex, mp.geom, 1, op, np.full(len(op), flags_value, np.uint8), prm, mp.bc_tag)
     Rw = Aw.residual(state(Aw.node_coords(), H))
