@@ -161,6 +161,9 @@ cudaError_t launch_node_coords(const DevMesh& M, const double* geom_nodes, int g
 cudaError_t launch_conservation(const DevMesh& M, const Bucket& b, const double* R, int nvar,
                                 double* partial, cudaStream_t s);
 cudaError_t prepare_kernels();
+// Copy between page-locked host memory and device memory with the SMs (16-byte aligned
+// pointers, a whole number of doubles); cudaErrorInvalidValue otherwise.
+cudaError_t launch_copy_sm(void* dst, const void* src, size_t bytes, int sms, cudaStream_t s);
 // FP32-arithmetic variants (dg_kernels_f32.cu)
 cudaError_t upload_ops32(const Ops1D& ops);
 cudaError_t prepare_kernels32();

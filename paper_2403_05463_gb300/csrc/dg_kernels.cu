@@ -18,6 +18,7 @@
 //   J R = -sum_d D_d (Ftil_e^d - Ftil_v^d) - sum_faces (1/w_end) [(F_e* - F_v*) . S - (Ftil_e - Ftil_v)_out]
 #include "dg_device.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace dgk {
@@ -682,6 +683,37 @@ __global__ void k_conservation(DevMesh M, const int32_t* __restrict__ list, int 
     }
     partial[v * M.n_elem + e] = s;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// host <-> device copy by the SMs (page-locked host memory is directly addressable)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16,
+                                                const double* __restrict__ src_tail, double* __restrict__ dst_tail,
+                                                int64_t n_tail) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {  // four independent 16-byte loads in flight
+    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x < n_tail) dst_tail[threadIdx.x] = src_tail[threadIdx.x];
+}
+
+cudaError_t launch_copy_sm(void* dst, const void* src, size_t bytes, int sms, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  const bool aligned = ((uintptr_t)dst % 16 == 0) && ((uintptr_t)src % 16 == 0) && bytes % 8 == 0;
+  if (!aligned) return cudaErrorInvalidValue;
+  const int64_t n16 = (int64_t)(bytes / 16), tail = (int64_t)((bytes % 16) / 8);
+  const unsigned grid = (unsigned)std::max(1, sms * 4);
+  k_copy16<<<grid, 256, 0, s>>>(reinterpret_cast<const uint4*>(src), reinterpret_cast<uint4*>(dst), n16,
+                                reinterpret_cast<const double*>(src) + 2 * n16, reinterpret_cast<double*>(dst) + 2 * n16,
+                                tail);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
