@@ -1583,10 +1583,27 @@ static void face_u5(const or_mesh* m, const or_real* u, int64_t e, int f, or_rea
     }
 }
 
-/* the neighbour's face state in my face coordinates (conforming faces: same order) */
-static void cns_nbr_face(const or_mesh* m, const or_real* u, int64_t e, int f, or_real* T /*[5][n2]*/) {
-  int N = m->N[e], n = N + 1;
+/* the neighbour's face state in my face coordinates (conforming faces: same order), or behind a
+ * wall the mirror state: (rho, -rho v, rho e) at a no-slip wall (tag 3), the normal momentum
+ * reversed at a free-slip wall (tag 4); density and energy, hence p and T, are kept */
+static void cns_nbr_face(const or_mesh* m, const or_real* u, const geo_t* gt, int64_t e, int f, or_real* T /*[5][n2]*/) {
+  int N = m->N[e], n = N + 1, n2 = n * n;
   int64_t nb = m->nb_e[e * 6 + f];
+  if (nb < 0) {
+    const int tag = m->bc[e * 6 + f];
+    or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+    face_u5(m, u, e, f, T);
+    face_S(m, gt, e, f, S);
+    for (int p = 0; p < n2; ++p) {
+      const or_real Sv[3] = {S[p], S[n2 + p], S[2 * n2 + p]};
+      const or_real ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
+      const or_real mn = (T[n2 + p] * Sv[0] + T[2 * n2 + p] * Sv[1] + T[3 * n2 + p] * Sv[2]) / ss;
+      for (int c = 0; c < 3; ++c)
+        T[(1 + c) * n2 + p] = tag == 3 ? -T[(1 + c) * n2 + p] : T[(1 + c) * n2 + p] - 2.0 * mn * Sv[c];
+    }
+    free(S);
+    return;
+  }
   or_real* tn = (or_real*)malloc(sizeof(or_real) * 5 * n * n);
   face_u5(m, u, nb, m->nb_f[e * 6 + f], tn);
   nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 5, tn, T);
@@ -1639,7 +1656,7 @@ static void cns_gradient(const cwork_t* W, int64_t e, or_real* G) {
   or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
   for (int f = 0; f < 6; ++f) {
     face_u5(m, W->u, e, f, um);
-    cns_nbr_face(m, W->u, e, f, up);
+    cns_nbr_face(m, W->u, gt, e, f, up);
     face_S(m, gt, e, f, S);
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
@@ -1771,18 +1788,34 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
   for (int f = 0; f < 6; ++f) {
     const int64_t nb = m->nb_e[e * 6 + f];
     face_u5(m, W->u, e, f, um);
-    cns_nbr_face(m, W->u, e, f, up);
+    cns_nbr_face(m, W->u, gt, e, f, up);
     face_S(m, gt, e, f, S);
-    const int any_visc = m->flag[e] || m->flag[nb];
+    const int any_visc = m->flag[e] || (nb >= 0 && m->flag[nb]);
     memset(Fvm, 0, sizeof(or_real) * 4 * n2);
     memset(Fvp, 0, sizeof(or_real) * 4 * n2);
     if (any_visc) {
       cns_face_fv(W, e, f, Fvm);
-      cns_face_fv(W, nb, m->nb_f[e * 6 + f], tn);
-      nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
+      if (nb >= 0) {
+        cns_face_fv(W, nb, m->nb_f[e * 6 + f], tn);
+        nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
+      } else {
+        /* adiabatic walls: the ghost's outward flux makes the BR1 average the interior traction
+         * (no-slip) or its normal part (free-slip, the reflection R = I - 2 n n^T of the traction),
+         * and a zero energy flux (no heat flux, no work by a traction on a resting or tangentially
+         * moving wall) */
+        const int tag = m->bc[e * 6 + f];
+        for (int p = 0; p < n2; ++p) {
+          const or_real Sv[3] = {S[p], S[n2 + p], S[2 * n2 + p]};
+          const or_real ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
+          const or_real fn = (Fvm[p] * Sv[0] + Fvm[n2 + p] * Sv[1] + Fvm[2 * n2 + p] * Sv[2]) / ss;
+          for (int c = 0; c < 3; ++c)
+            Fvp[c * n2 + p] = tag == 3 ? -Fvm[c * n2 + p] : Fvm[c * n2 + p] - 2.0 * fn * Sv[c];
+          Fvp[3 * n2 + p] = Fvm[3 * n2 + p];
+        }
+      }
     }
     or_real wm = 0.5, wp = 0.5;
-    if (m->p.mixed_face == 1 && m->flag[e] != m->flag[nb]) {
+    if (m->p.mixed_face == 1 && nb >= 0 && m->flag[e] != m->flag[nb]) {
       wm = m->flag[e] ? 1.0 : 0.0;
       wp = m->flag[e] ? 0.0 : 1.0;
     }
@@ -1832,7 +1865,9 @@ static int cns_check(const or_mesh* m) {
     for (int f = 0; f < 6; ++f) {
       const int64_t nb = m->nb_e[e * 6 + f];
       if (nb < 0) {
-        set_err("compressible form: element %lld face %d is a boundary (periodic meshes only)", (long long)e, f);
+        if (m->bc[e * 6 + f] == 3 || m->bc[e * 6 + f] == 4) continue;
+        set_err("compressible form: element %lld face %d: boundary tag %d (walls 3 and 4 only)", (long long)e, f,
+                m->bc[e * 6 + f]);
         return -1;
       }
       if (m->N[nb] != m->N[e]) {
@@ -1857,7 +1892,8 @@ int or_cns_element_gradient(const or_mesh* m, const or_real* u, int64_t e, or_re
   if (e < 0 || e >= m->ne || cns_check(m)) return -1;
   uint8_t* need = (uint8_t*)calloc(m->ne, 1);
   need[e] = 1;
-  for (int f = 0; f < 6; ++f) need[m->nb_e[e * 6 + f]] = 1;
+  for (int f = 0; f < 6; ++f)
+        if (m->nb_e[e * 6 + f] >= 0) need[m->nb_e[e * 6 + f]] = 1;
   cwork_t W;
   W.m = m;
   W.u = u;
@@ -1891,14 +1927,16 @@ int or_cns_residual(const or_mesh* m, const or_real* u, or_real* R, int64_t n_se
   for (int64_t e = 0; e < ne; ++e)
     if (want[e]) {
       need[e] = 1;
-      for (int f = 0; f < 6; ++f) need[m->nb_e[e * 6 + f]] = 1;
+      for (int f = 0; f < 6; ++f)
+        if (m->nb_e[e * 6 + f] >= 0) need[m->nb_e[e * 6 + f]] = 1;
     }
   /* a neighbour's gradient needs its own neighbours' geometry */
   uint8_t* need2 = (uint8_t*)calloc(ne, 1);
   for (int64_t e = 0; e < ne; ++e)
     if (need[e]) {
       need2[e] = 1;
-      for (int f = 0; f < 6; ++f) need2[m->nb_e[e * 6 + f]] = 1;
+      for (int f = 0; f < 6; ++f)
+        if (m->nb_e[e * 6 + f] >= 0) need2[m->nb_e[e * 6 + f]] = 1;
     }
   cwork_t W;
   W.m = m;

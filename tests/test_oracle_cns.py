@@ -7,7 +7,9 @@ with the textbook Roe averages, and |A_roe| against numpy's eigen-decomposition 
 matrix; consistency, conservation and supersonic upwinding of the numerical fluxes; free
 stream and conservation of the residual on curved, re-oriented, mixed-flag meshes; Euler = NS
 without viscosity; invariance under element re-numbering; spectral convergence to the
-symbolic (sympy) residual of the compressible Navier-Stokes equations with heat flux."""
+symbolic (sympy) residual of the compressible Navier-Stokes equations with heat flux; at
+adiabatic walls the mirror identities with the doubled periodic channel, mass and energy
+conservation and a tangential free stream."""
 import dataclasses
 
 import numpy as np
@@ -237,14 +239,97 @@ def test_rk_step_conserves_and_keeps_a_uniform_state():
     np.testing.assert_allclose(after, before, rtol=1e-12)
 
 
-def test_boundaries_and_nonconforming_faces_are_rejected():
-    w = wl.wake_16x16x16_n4(n=3, order=2)
-    M = _mesh(w, _cns_params())
-    with pytest.raises(RuntimeError):
-        M.cns_residual(np.ones((5, M.total)))
+def test_nonconforming_faces_are_rejected():
     w2 = _curved_periodic(order=3, seed=10)
     o = w2.orders.copy()
     o[0] = 4
     M2 = _mesh(dataclasses.replace(w2, orders=o), _cns_params())
     with pytest.raises(RuntimeError):
         M2.cns_residual(np.ones((5, M2.total)))
+
+
+# ---- adiabatic walls (boundary tags 3 no-slip, 4 free-slip) ----------------------------------
+
+def _cns_mirror_residuals(tag, state, flags_value):
+    from test_oracle_pins import _channel
+    H = 2.0
+    mw, ow = _channel(3, 0.0, H, (tag, tag))      # [0, H] between two walls
+    mp, op = _channel(6, -H, 2 * H, None)          # [-H, H], periodic: the mirror extension
+    prm = _cns_params(nu=1e-2)
+    Aw = orc.Mesh(mw.hex, mw.geom, 1, ow, np.full(len(ow), flags_value, np.uint8), prm, mw.bc_tag)
+    Ap = orc.Mesh(mp.hex, mp.geom, 1, op, np.full(len(op), flags_value, np.uint8), prm, mp.bc_tag)
+    Rw = Aw.cns_residual(state(Aw.node_coords(), H))
+    Rp = Ap.cns_residual(state(Ap.node_coords(), H))
+    out_w, out_p = [], []
+    for e in range(len(ow)):
+        i, j, k = e % 3, (e // 3) % 3, e // 9
+        ep = i + 3 * ((j + 3) + 6 * k)
+        out_w.append(Rw[:, Aw.element_nodes(e)])
+        out_p.append(Rp[:, Ap.element_nodes(ep)])
+    return np.concatenate(out_w, axis=1), np.concatenate(out_p, axis=1)
+
+
+def _cns_from_primitive(rho, v, p):
+    return np.stack([rho, rho * v[0], rho * v[1], rho * v[2], p / (GAMMA - 1) + 0.5 * rho * (v ** 2).sum(0)])
+
+
+@pytest.mark.parametrize("flags_value", [0, 1])
+def test_free_slip_wall_is_a_mirror(flags_value):
+    # rho, p, v_x, v_z even and v_y odd about y = 0 and y = H: the periodic residual of the
+    # extended field restricted to [0, H] is the residual between free-slip walls (Euler and NS:
+    # the mirror average keeps the normal traction and cancels the normal energy flux)
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        rho = 1.0 + 0.1 * c * np.sin(x[0])
+        v = np.stack([0.5 + 0.1 * c * np.sin(x[2]), 0.2 * s * np.cos(x[0]), 0.1 * c * np.cos(x[0])])
+        p = 2.0 + 0.2 * c * np.cos(x[2]) + 0.1 * np.cos(2 * np.pi * x[1] / H)
+        return _cns_from_primitive(rho, v, p)
+    Rw, Rp = _cns_mirror_residuals(4, state, flags_value)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+def test_no_slip_wall_is_an_antimirror_for_euler():
+    # rho, p even and every velocity component odd about the walls
+    def state(x, H):
+        c, s = np.cos(np.pi * x[1] / H), np.sin(np.pi * x[1] / H)
+        rho = 1.0 + 0.1 * c * np.cos(x[0])
+        v = np.stack([s * (0.5 + 0.1 * np.cos(x[2])), 0.2 * np.sin(2 * np.pi * x[1] / H) * np.cos(x[0]),
+                      0.3 * s * np.sin(x[0])])
+        p = 2.0 + 0.2 * c * np.sin(x[2])
+        return _cns_from_primitive(rho, v, p)
+    Rw, Rp = _cns_mirror_residuals(3, state, 0)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+
+
+@pytest.mark.parametrize("tag", [3, 4])
+def test_walls_conserve_mass_and_energy(tag):
+    # the mirror ghost makes the Roe mass and energy fluxes through a wall vanish, and the
+    # adiabatic wall carries no viscous energy flux: the mass and energy sums stay zero
+    from test_oracle_pins import _channel
+    mw, ow = _channel(3, 0.0, 2.0, (tag, tag))
+    rng = np.random.default_rng(30 + tag)
+    flags = rng.integers(0, 2, size=len(ow)).astype(np.uint8)
+    M = orc.Mesh(mw.hex, mw.geom, 1, ow, flags, _cns_params(nu=1e-2), mw.bc_tag)
+    u = wl.cns_state(M.node_coords(), seed=tag, period=2 * np.pi)
+    R = M.cns_residual(u)
+    s = M.cns_conservation(R)
+    scale = np.abs(R).max()
+    assert abs(s[0]) < 1e-12 * scale and abs(s[4]) < 1e-12 * scale, s
+    assert np.abs(s[1:4]).max() > 1e-6 * scale  # momentum does cross the walls (pressure, traction)
+
+
+def test_free_slip_walls_keep_a_tangential_free_stream():
+    from test_oracle_pins import _channel
+    mw, ow = _channel(3, 0.0, 2.0, (4, 4), N=4)
+    M = orc.Mesh(mw.hex, mw.geom, 1, ow, np.ones(len(ow), np.uint8), _cns_params(nu=1e-2), mw.bc_tag)
+    xyz = M.node_coords()
+    u = _cns_from_primitive(np.full(M.total, 1.2), np.stack([np.full(M.total, 0.6), np.zeros(M.total),
+                                                              np.full(M.total, -0.2)]), np.full(M.total, 1.5))
+    assert np.abs(M.cns_residual(u)).max() < 1e-12
+
+
+def test_inflow_outflow_are_refused():
+    w = wl.wake_16x16x16_n4(n=3, order=2)
+    M = _mesh(w, _cns_params())
+    with pytest.raises(RuntimeError):
+        M.cns_residual(np.ones((5, M.total)))
