@@ -112,8 +112,11 @@ typedef struct {
                        heat flux kappa grad T with kappa = c_p (mu / Pr + mu_t / Pr_t),
                        c_p = gamma / (gamma - 1), BR1 on (v, T). Model 1 runs in FP64
                        (precision 0) with the standard volume term (split 0) on meshes whose
-                       faces are all interior or periodic and conforming (both sides of one
-                       order); other meshes give DG_ERR_UNSUPPORTED. Its state, RK register
+                       faces are conforming (both sides of one order) and whose boundary faces
+                       are adiabatic walls: no-slip (tag 3, the mirror ghost (rho, -rho v,
+                       rho e), the interior traction) or free-slip (tag 4, the normal momentum
+                       reversed, the normal traction), with no viscous energy flux; other
+                       meshes give DG_ERR_UNSUPPORTED. Its state, RK register
                        and residual arrays have 5 planes, [5][total_nodes].               */
   double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
   double gamma;     /* model 1: ratio of specific heats (> 1)                           */

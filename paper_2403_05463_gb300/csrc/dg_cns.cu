@@ -5,7 +5,8 @@
 // solve the Euler equations, flag 1 the Navier-Stokes equations with the eddy viscosity
 // mu_t = rho nu_t of the selected closure and the heat flux kappa grad T,
 // kappa = c_p (mu / Pr + mu_t / Pr_t), c_p = gamma / (gamma - 1). Conforming faces between
-// elements of one order (interior or periodic); the host rejects other meshes.
+// elements of one order (interior or periodic) and adiabatic walls (no-slip, free-slip: mirror
+// ghost states, no viscous energy flux); the host rejects other meshes.
 //
 // Per residual evaluation / Runge-Kutta stage (the passes of the incompressible FP64 path with
 // five variables):
@@ -215,20 +216,27 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       const double sg = side ? 1.0 : -1.0;
       const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
       const FaceLink L = M.link[e * 6 + f];
-      if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
+      const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+      double jump[4];
+      if (L.kind == FK_CONF) {
+        int a1, b1;
+        inv_orient(L.orient, N, a, b, a1, b1);
+        const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+        double un[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) un[v] = M.Tq[v * M.tr_total + ns];
+        const Prim Q = prim(un, gamma);
+        jump[0] = Q.v[0] - ph[0], jump[1] = Q.v[1] - ph[1], jump[2] = Q.v[2] - ph[2], jump[3] = Q.p / Q.rho - ph[3];
+      } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {  // mirror ghost: T kept, velocity reflected
+        const double vo[3] = {ph[0], ph[1], ph[2]};
+        double jw[3];
+        wall_jump<double>(L.kind, vo, Sv, jw);
+        jump[0] = jw[0], jump[1] = jw[1], jump[2] = jw[2], jump[3] = 0.0;
+      } else {  // the host admits conforming faces and walls only
         atomicCAS(&M.err[0], 0, 5);
         atomicCAS(&M.err[1], 0, 10);
         continue;
       }
-      int a1, b1;
-      inv_orient(L.orient, N, a, b, a1, b1);
-      const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
-      double un[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) un[v] = M.Tq[v * M.tr_total + ns];
-      const Prim Q = prim(un, gamma);
-      const double jump[4] = {Q.v[0] - ph[0], Q.v[1] - ph[1], Q.v[2] - ph[2], Q.p / Q.rho - ph[3]};
-      const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -373,25 +381,51 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     const double sg = side ? 1.0 : -1.0;
     const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
     const FaceLink L = M.link[e * 6 + f];
-    if (L.kind != FK_CONF) {  // the host admits conforming interior faces only
-      atomicCAS(&M.err[0], 0, 5);
-      atomicCAS(&M.err[1], 0, 11);
-      continue;
-    }
     const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
     const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
     const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
     const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
-    int a1, b1;
-    inv_orient(L.orient, N, a, b, a1, b1);
-    const int64_t nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
-    double up[5];
+    double up[5];  // the neighbour's face state, or the mirror ghost behind a wall
+    int64_t nsl = 0;
+    if (L.kind == FK_CONF) {
+      int a1, b1;
+      inv_orient(L.orient, N, a, b, a1, b1);
+      nsl = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) up[v] = M.Tq[v * M.tr_total + nsl];
+      for (int v = 0; v < 5; ++v) up[v] = M.Tq[v * M.tr_total + nsl];
+    } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {  // density and energy kept, momentum reflected
+      const double mo[3] = {uu[1], uu[2], uu[3]};
+      double jw[3];
+      wall_jump<double>(L.kind, mo, Sv, jw);
+      up[0] = uu[0];
+      up[4] = uu[4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) up[1 + c] = uu[1 + c] + jw[c];
+    } else {  // the host admits conforming faces and walls only
+      atomicCAS(&M.err[0], 0, 5);
+      atomicCAS(&M.err[1], 0, 11);
+      continue;
+    }
     double fx[5];
     cns_fluct(uu, up, nh, gamma, M.riemann, fx);
 #pragma unroll
     for (int v = 0; v < 5; ++v) JR[v] -= invw * s * fx[v];
+    if (L.kind != FK_CONF) {
+      // adiabatic wall, NS element: F_v* . S is the own traction (no-slip) or its normal part
+      // (free-slip) and carries no energy, so the own outward flux minus F_v* . S leaves nothing
+      // (no-slip) or the tangential traction (free-slip) in momentum, and the own energy flux
+      if (ns) {
+        const double tw[3] = {M.Tv[ms], M.Tv[M.tr_total + ms], M.Tv[2 * M.tr_total + ms]};
+        if (L.kind == FK_SLIP) {
+          double tt[3];
+          slip_visc_term<double>(tw, Sv, tt);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) JR[1 + c] -= invw * tt[c];
+        }
+        JR[4] -= invw * M.Tv[3 * M.tr_total + ms];
+      }
+      continue;
+    }
     if (ns || L.nflag) {
       // BR1: Ftil_v,out - F_v* . S = wo Fv_own . S_own + wn Fv_nbr . S_nbr
       float wo, wn;

@@ -769,9 +769,9 @@ dg_status check_model_mesh(const dg_ctx* c) {
   if (c->prm.model != 1 && c->prm.nodes != 1) return DG_OK;
   const char* what = c->prm.model == 1 ? "compressible form" : "Gauss-Legendre nodes";
   for (int64_t s = 0; s < c->ne * 6; ++s) {
-    if (c->nb[s] < 0 && c->prm.model == 1)
-      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is a boundary face (interior and periodic faces "
-                  "only)", what, (long long)(s / 6), (int)(s % 6));
+    if (c->nb[s] < 0 && c->prm.model == 1 && c->bc[s] != 3 && c->bc[s] != 4)
+      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d has boundary tag %d (walls 3 and 4 only)", what,
+                  (long long)(s / 6), (int)(s % 6), (int)c->bc[s]);
     if (c->nb[s] < 0) continue;
     if (c->order[c->nb[s]] != c->order[s / 6])
       return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is p-nonconforming", what, (long long)(s / 6),

@@ -1,7 +1,8 @@
 """Compressible form (App. A, dg_params.model = 1) on the GPU, through the C ABI, against the FP64
 oracle's compressible entry points: residuals, RK steps and conservation sums at the FP64
 tolerance 1e-12 (relative L2), on box, re-oriented curved and every order 1..7, mixed flags,
-Roe/LLF, Vreman/Smagorinsky and both mixed-face choices; plus what the build rejects."""
+Roe/LLF, Vreman/Smagorinsky, both mixed-face choices and adiabatic no-slip/free-slip walls; plus
+what the build rejects."""
 import dataclasses
 
 import numpy as np
@@ -120,6 +121,26 @@ def test_model_switch_on_an_existing_context():
     assert rel_l2(R, M.cns_residual(u)) <= TOL
     with pytest.raises(ValueError):
         S.residual(torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("wall", [3, 4])
+def test_adiabatic_walls(wall):
+    # the wavy degree-2 channel between walls, re-oriented elements, mixed flags, one order
+    # (the compressible form needs conforming faces)
+    w = wl.channel_walls(n=4, wall=wall)
+    mesh, _ = wl.rotate_elements(w.mesh, 90 + wall)
+    rng = np.random.default_rng(wall)
+    w = dataclasses.replace(w, mesh=mesh, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8),
+                            params=dict(wl.cns_tgv().params, nu=1e-2))
+    M = _oracle(w)
+    u = wl.cns_state(M.node_coords(), w.seed, period=2 * np.pi)
+    R_ref = M.cns_residual(u)
+    S = _solver(w)
+    R = S.residual(to_dev(u)).cpu().numpy()
+    assert rel_l2(R, R_ref) <= TOL, rel_l2(R, R_ref)
+    sums = S.conservation(to_dev(R))
+    scale = np.abs(R).max()
+    assert abs(sums[0]) <= 1e-11 * scale and abs(sums[4]) <= 1e-11 * scale, sums  # walls pass no mass, energy
 
 
 def test_what_the_compressible_build_rejects():
