@@ -60,6 +60,14 @@ int or_num_threads(void) {
 #endif
 }
 
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------
  * 1D: Gauss-Lobatto-Legendre nodes and weights, differentiation, interpolation,
  * L2 projection. (Quadrature of App. B, last paragraph; Gauss-Lobatto variant.)

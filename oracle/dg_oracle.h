@@ -132,6 +132,7 @@ int or_cns_rk_step(const or_mesh* m, or_real* u, or_real* g, or_real dt, int nst
 int or_cns_conservation(const or_mesh* m, const or_real* R, or_real out[5]);
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);
+void or_set_num_threads(int n);  /* OpenMP threads of the element loops (n > 0) */
 
 #ifdef __cplusplus
 }

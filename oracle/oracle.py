@@ -105,6 +105,8 @@ def lib(extended: bool = False):
             L.or_rk_step.argtypes = [ctypes.c_void_p, _d, _d, real, ctypes.c_int]
             L.or_conservation.argtypes = [ctypes.c_void_p, _d, _d]
             L.or_num_threads.restype = ctypes.c_int
+            L.or_set_num_threads.argtypes = [ctypes.c_int]
+            L.or_set_num_threads.restype = None
             L.or_cns_flux.argtypes = [_d, _d, real, _d]
             L.or_cns_flux.restype = None
             L.or_cns_jacobian.argtypes = [_d, _d, real, _d]
@@ -274,6 +276,10 @@ def rk3_linear(z):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    lib().or_set_num_threads(int(n))
 
 
 # ---- mesh ----------------------------------------------------------------------------

@@ -257,3 +257,44 @@ def test_fp32_detection_within_its_error(make):
             fh.write(json.dumps(rec) + "\n")
     assert feat_err <= 1e-4, feat_err
     assert p_err <= FP32_PROB_TOL and pbar_err <= FP32_PROB_TOL, (p_err, pbar_err)
+
+
+def test_detect_then_adapt_then_step():
+    """The hybrid p-adapted workflow (Sec. 2.1 then Sec. 3.2), all through the C ABI: detect the
+    regions on the current state, flag them, give the viscous region order P_v and the rest
+    P_i, re-project the state onto the new orders, take RK steps; the oracle runs the same
+    sequence from the same inputs (its own detection, projection and steps)."""
+    import torch
+    from oracle import oracle as orc
+    w = wl.padapt_32x32x32(n=5)  # curved, degree-2 geometry, NS shear layer
+    w = dataclasses.replace(w, orders=np.full(w.n_elem, 3, np.int8), flags=np.zeros(w.n_elem, np.uint8))
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    F = rg.detect_regions(M, q, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": np.stack([np.eye(3)] * 2),
+                                 "viscous": 1})["features"]
+    gmm = _gmm_from(F, quantile=0.7)
+    # GPU: detect, flag, adapt, project, step
+    S = gpu_solver(w)
+    qd = to_dev(q)
+    f, _, _ = S.detect_regions(qd, gmm, pbar=False)
+    flags = f.cpu().numpy()
+    orders = np.where(flags == 1, 5, 2).astype(np.int8)
+    S.set_flags(flags)
+    S.set_orders(orders)
+    qd = S.project_state(qd)
+    gd = torch.zeros_like(qd)
+    S.rk_step(qd, gd, 1e-4, 3)
+    # oracle: the same sequence (flags must agree outside near-ties; here every decision is clear)
+    ref = rg.detect_regions(M, q, gmm)
+    assert np.all(np.abs(ref["pbar"][0] - ref["pbar"][1]) > MARGIN)
+    np.testing.assert_array_equal(flags, ref["flags"])
+    assert 0 < flags.sum() < w.n_elem
+    q2 = orc.project_state(w.orders, orders, q)
+    w2 = dataclasses.replace(w, orders=orders, flags=flags)
+    M2 = oracle_mesh(w2)
+    g2 = np.zeros_like(q2)
+    M2.rk_step(q2, g2, 1e-4, 3)
+    got = qd.cpu().numpy()
+    assert got.shape == q2.shape
+    err = np.sqrt(((got - q2) ** 2).sum() / (q2 ** 2).sum())
+    assert err <= 1e-12, err
