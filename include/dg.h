@@ -113,12 +113,16 @@ typedef struct {
                        c_p = gamma / (gamma - 1), BR1 on (v, T). Model 1 runs in FP64
                        (precision 0) with the standard volume term (split 0) on meshes whose
                        faces are conforming (both sides of one order) and whose boundary faces
-                       are adiabatic walls: no-slip (tag 3, the mirror ghost (rho, -rho v,
-                       rho e), the interior traction) or free-slip (tag 4, the normal momentum
-                       reversed, the normal traction), with no viscous energy flux; other
-                       meshes give DG_ERR_UNSUPPORTED. Its state, RK register
+                       are far-field inflow (tag 1, the ghost is the state of inflow[] and
+                       p_inf), pressure outflow (tag 2, interior density and velocity with
+                       p_inf), both with the interior viscous flux, or adiabatic walls:
+                       no-slip (tag 3, the mirror ghost (rho, -rho v, rho e), the interior
+                       traction) or free-slip (tag 4, the normal momentum reversed, the normal
+                       traction), with no viscous energy flux at walls; other meshes give
+                       DG_ERR_UNSUPPORTED. Its state, RK register
                        and residual arrays have 5 planes, [5][total_nodes].               */
-  double inflow[4]; /* ghost state at inflow faces (only the velocity part is used)    */
+  double inflow[4]; /* ghost state at inflow faces: model 0 uses the velocity part;
+                       model 1 reads (rho, u, v, w) of the far field                    */
   double gamma;     /* model 1: ratio of specific heats (> 1)                           */
   double prandtl;   /* model 1: laminar Prandtl number (> 0)                            */
   double prandtl_t; /* model 1: turbulent Prandtl number (> 0)                          */
@@ -134,6 +138,9 @@ typedef struct {
                        dg_conservation_noalloc and dg_detect_regions. dg_node_coords returns
                        the Gauss points.                                                 */
   int reserved;     /* must be 0                                                       */
+  double p_inf;     /* model 1: far-field pressure of the inflow ghost (with inflow[]) and
+                       the static pressure of the outflow ghost (interior density and
+                       velocity); both need rho_inf = inflow[0] > 0 and p_inf > 0          */
 } dg_params;
 
 /* Build the mesh topology (face matching, orientations, periodic pairs), the geometry

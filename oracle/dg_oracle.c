@@ -1591,16 +1591,35 @@ static void face_u5(const or_mesh* m, const or_real* u, int64_t e, int f, or_rea
     }
 }
 
-/* the neighbour's face state in my face coordinates (conforming faces: same order), or behind a
- * wall the mirror state: (rho, -rho v, rho e) at a no-slip wall (tag 3), the normal momentum
- * reversed at a free-slip wall (tag 4); density and energy, hence p and T, are kept */
+/* the neighbour's face state in my face coordinates (conforming faces: same order), or the ghost
+ * behind a boundary face: the far-field state at an inflow (tag 1); interior density and
+ * momentum with the far-field pressure at an outflow (tag 2); the mirror state (rho, -rho v,
+ * rho e) at a no-slip wall (tag 3), the normal momentum reversed at a free-slip wall (tag 4),
+ * density and energy, hence p and T, kept */
 static void cns_nbr_face(const or_mesh* m, const or_real* u, const geo_t* gt, int64_t e, int f, or_real* T /*[5][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n;
   int64_t nb = m->nb_e[e * 6 + f];
   if (nb < 0) {
     const int tag = m->bc[e * 6 + f];
-    or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+    const or_real g1 = m->p.gamma - 1.0;
     face_u5(m, u, e, f, T);
+    if (tag == 1) { /* far-field inflow: (rho_inf, rho_inf v_inf, p_inf/(gamma-1) + rho_inf |v_inf|^2/2) */
+      const or_real r = m->p.inflow[0], v[3] = {m->p.inflow[1], m->p.inflow[2], m->p.inflow[3]};
+      for (int p = 0; p < n2; ++p) {
+        T[p] = r;
+        for (int c = 0; c < 3; ++c) T[(1 + c) * n2 + p] = r * v[c];
+        T[4 * n2 + p] = m->p.p_inf / g1 + 0.5 * r * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      }
+      return;
+    }
+    if (tag == 2) { /* pressure outflow: interior density and momentum, the far-field pressure */
+      for (int p = 0; p < n2; ++p) {
+        const or_real mm = T[n2 + p] * T[n2 + p] + T[2 * n2 + p] * T[2 * n2 + p] + T[3 * n2 + p] * T[3 * n2 + p];
+        T[4 * n2 + p] = m->p.p_inf / g1 + 0.5 * mm / T[p];
+      }
+      return;
+    }
+    or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
     face_S(m, gt, e, f, S);
     for (int p = 0; p < n2; ++p) {
       const or_real Sv[3] = {S[p], S[n2 + p], S[2 * n2 + p]};
@@ -1813,6 +1832,10 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
          * moving wall) */
         const int tag = m->bc[e * 6 + f];
         for (int p = 0; p < n2; ++p) {
+          if (tag == 1 || tag == 2) { /* inflow, outflow: the interior viscous flux */
+            for (int v = 0; v < 4; ++v) Fvp[v * n2 + p] = -Fvm[v * n2 + p];
+            continue;
+          }
           const or_real Sv[3] = {S[p], S[n2 + p], S[2 * n2 + p]};
           const or_real ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
           const or_real fn = (Fvm[p] * Sv[0] + Fvm[n2 + p] * Sv[1] + Fvm[2 * n2 + p] * Sv[2]) / ss;
@@ -1873,10 +1896,12 @@ static int cns_check(const or_mesh* m) {
     for (int f = 0; f < 6; ++f) {
       const int64_t nb = m->nb_e[e * 6 + f];
       if (nb < 0) {
-        if (m->bc[e * 6 + f] == 3 || m->bc[e * 6 + f] == 4) continue;
-        set_err("compressible form: element %lld face %d: boundary tag %d (walls 3 and 4 only)", (long long)e, f,
-                m->bc[e * 6 + f]);
-        return -1;
+        const int tag = m->bc[e * 6 + f];
+        if ((tag == 1 || tag == 2) && !(m->p.inflow[0] > 0.0 && m->p.p_inf > 0.0)) {
+          set_err("compressible form: inflow/outflow faces need a positive far-field density and pressure");
+          return -1;
+        }
+        continue;
       }
       if (m->N[nb] != m->N[e]) {
         set_err("compressible form: element %lld face %d is p-nonconforming", (long long)e, f);

@@ -62,6 +62,8 @@ typedef struct {
                        face fluxes are interpolated from the element's nodes and face terms
                        are lifted with l_i(+-1) / w_i; p-nonconforming faces and the split
                        form need Gauss-Lobatto                                     */
+  or_real p_inf;     /* compressible form: far-field pressure at inflow (with the far-field
+                       (rho, u, v, w) in inflow[]) and static pressure at outflow     */
 } or_params;
 
 typedef struct or_mesh or_mesh;

@@ -54,7 +54,7 @@ def _params_type(real):
         _fields_ = [("nu", real), ("c0sq", real), ("cs", real), ("cv", real), ("closure", ctypes.c_int),
                     ("riemann", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
                     ("inflow", real * 4), ("gamma", real), ("prandtl", real), ("prandtl_t", real),
-                    ("nodes", ctypes.c_int)]
+                    ("nodes", ctypes.c_int), ("p_inf", real)]
     return P
 
 
@@ -130,12 +130,13 @@ def _f64(a):
 
 
 def params(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, inflow=(0.0, 1.0, 0.0, 0.0), mixed_face=0,
-           split=0, gamma=1.4, prandtl=0.72, prandtl_t=0.9, nodes=0):
+           split=0, gamma=1.4, prandtl=0.72, prandtl_t=0.9, nodes=0, p_inf=0.0):
     p = Params()
     p.nu, p.c0sq, p.cs, p.cv = nu, c0sq, cs, cv
     p.closure, p.riemann, p.mixed_face, p.split = closure, riemann, mixed_face, split
     p.gamma, p.prandtl, p.prandtl_t = gamma, prandtl, prandtl_t
     p.nodes = nodes
+    p.p_inf = p_inf
     for i in range(4):
         p.inflow[i] = inflow[i]
     return p

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
                 ("model", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("prandtl_t", ctypes.c_double), ("nodes", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int), ("p_inf", ctypes.c_double)]
 
 
 class GMM(ctypes.Structure):
@@ -135,6 +135,7 @@ def make_params(p: dict, precision=0) -> Params:
     out.prandtl_t = float(p.get("prandtl_t", 0.9))
     out.nodes = int(p.get("nodes", 0))
     out.reserved = 0
+    out.p_inf = float(p.get("p_inf", 0.0))
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
     return out

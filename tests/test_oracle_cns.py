@@ -9,7 +9,9 @@ stream and conservation of the residual on curved, re-oriented, mixed-flag meshe
 without viscosity; invariance under element re-numbering; spectral convergence to the
 symbolic (sympy) residual of the compressible Navier-Stokes equations with heat flux; at
 adiabatic walls the mirror identities with the doubled periodic channel, mass and energy
-conservation and a tangential free stream."""
+conservation and a tangential free stream; at far-field inflow and pressure outflow faces the
+free stream and the identity with the periodic box for a state that is the far field near
+them."""
 import dataclasses
 
 import numpy as np
@@ -328,8 +330,86 @@ def test_free_slip_walls_keep_a_tangential_free_stream():
     assert np.abs(M.cns_residual(u)).max() < 1e-12
 
 
-def test_inflow_outflow_are_refused():
+# ---- far-field inflow (tag 1) and pressure outflow (tag 2) ------------------------------------
+
+FAR = dict(rho=1.1, v=(0.6, 0.1, -0.2), p=1.8)
+
+
+def _far_params(**kw):
+    return _cns_params(inflow=(FAR["rho"], *FAR["v"]), p_inf=FAR["p"], **kw)
+
+
+def _box_x(periodic_x, n=(5, 3, 3), order=3):
+    nx, ny, nz = n
+    m = wl.box_mesh(nx, ny, nz, np.linspace(0, 5.0, nx + 1), np.linspace(0, 2 * np.pi, ny + 1),
+                    np.linspace(0, 2 * np.pi, nz + 1), periodic=(periodic_x, True, True), bc_lohi=(1, 2))
+    return m, np.full(nx * ny * nz, order, np.int8)
+
+
+@pytest.mark.parametrize("flags_value", [0, 1])
+def test_far_field_free_stream_through_inflow_and_outflow(flags_value):
+    m, o = _box_x(False)
+    M = orc.Mesh(m.hex, m.geom, 1, o, np.full(len(o), flags_value, np.uint8), _far_params(nu=1e-2), m.bc_tag)
+    n = M.total
+    v = np.stack([np.full(n, c) for c in FAR["v"]])
+    u = _cns_from_primitive(np.full(n, FAR["rho"]), v, np.full(n, FAR["p"]))
+    assert np.abs(M.cns_residual(u)).max() < 1e-12
+
+
+def test_inflow_outflow_equal_the_periodic_box_for_euler():
+    # the state is the far field in the first and last element layers along x and varies in
+    # between: the inflow ghost (far field) and the outflow ghost (interior rho, v and p_inf)
+    # then see what the periodic neighbour shows, so every element's residual is the same
+    mw, o = _box_x(False)
+    mp, _ = _box_x(True)
+    prm = _far_params()
+    Aw = orc.Mesh(mw.hex, mw.geom, 1, o, np.zeros(len(o), np.uint8), prm, mw.bc_tag)
+    Ap = orc.Mesh(mp.hex, mp.geom, 1, o, np.zeros(len(o), np.uint8), prm, mp.bc_tag)
+    x = Aw.node_coords()
+    np.testing.assert_array_equal(x, Ap.node_coords())
+    b = np.where((x[0] > 1.0) & (x[0] < 4.0), np.sin(np.pi * (x[0] - 1.0) / 3.0) ** 2, 0.0)
+    rho = FAR["rho"] * (1 + 0.1 * b * np.cos(x[1]))
+    v = np.stack([FAR["v"][0] + 0.2 * b * np.sin(x[2]), FAR["v"][1] + 0.1 * b, FAR["v"][2] * (1 + b * np.cos(x[1]))])
+    p = FAR["p"] * (1 + 0.05 * b * np.sin(x[1] + x[2]))
+    u = _cns_from_primitive(rho, v, p)
+    Rw, Rp = Aw.cns_residual(u), Ap.cns_residual(u)
+    assert np.abs(Rw - Rp).max() <= 1e-12 * np.abs(Rp).max()
+    assert np.abs(Rp).max() > 1e-2
+
+
+def test_inflow_and_outflow_ghost_states():
+    # a uniform interior (rho1, v1, p1) and a different far field: only the face nodes on the
+    # inflow and outflow faces feel the ghosts, with R = s/(w_end J) (F(u) - F*(u, u_ghost)) . n;
+    # the ghost is the far field at the inflow and (rho1, rho1 v1, p_inf) at the outflow (F* from
+    # the pinned Roe flux)
+    nx, N = 5, 3
+    m, o = _box_x(False, order=N)
+    rho1, v1, p1 = 1.1, np.array([0.6, 0.1, -0.2]), 1.8
+    rinf, vinf, pinf = 0.9, np.array([0.7, -0.1, 0.05]), 2.1
+    prm = _cns_params(inflow=(rinf, *vinf), p_inf=pinf)
+    M = orc.Mesh(m.hex, m.geom, 1, o, np.zeros(len(o), np.uint8), prm, m.bc_tag)
+    n = M.total
+    u1 = _cns_from_primitive(np.array([rho1]), v1[:, None], np.array([p1]))[:, 0]
+    R = M.cns_residual(np.repeat(u1[:, None], n, axis=1))
+    g_in = _cns_from_primitive(np.array([rinf]), vinf[:, None], np.array([pinf]))[:, 0]
+    g_out = _cns_from_primitive(np.array([rho1]), v1[:, None], np.array([pinf]))[:, 0]
+    h = 1.0
+    w0 = 2.0 / (N * (N + 1))
+    for nx_sign, elem_i, node_i, ghost in ((-1.0, 0, 0, g_in), (1.0, nx - 1, N, g_out)):
+        nh = np.array([nx_sign, 0.0, 0.0])
+        expect = (2.0 / h) / w0 * (orc.cns_flux(u1, nh, GAMMA) - orc.cns_riemann(u1, ghost, nh, prm))
+        e = elem_i  # element (elem_i, 0, 0)
+        Re = R[:, M.element_nodes(e)].reshape(5, N + 1, N + 1, N + 1)
+        np.testing.assert_allclose(Re[:, :, :, node_i], expect[:, None, None] * np.ones((N + 1, N + 1)), rtol=1e-12,
+                                   atol=1e-12)
+        other = np.delete(Re, node_i, axis=3)
+        assert np.abs(other).max() < 1e-12
+    # the interior elements see only uniform neighbours
+    assert np.abs(R[:, M.element_nodes(2)]).max() < 1e-12
+
+
+def test_inflow_outflow_need_a_far_field():
     w = wl.wake_16x16x16_n4(n=3, order=2)
-    M = _mesh(w, _cns_params())
+    M = _mesh(w, _cns_params())  # no far-field density or pressure given
     with pytest.raises(RuntimeError):
         M.cns_residual(np.ones((5, M.total)))
