@@ -5,8 +5,9 @@
 // solve the Euler equations, flag 1 the Navier-Stokes equations with the eddy viscosity
 // mu_t = rho nu_t of the selected closure and the heat flux kappa grad T,
 // kappa = c_p (mu / Pr + mu_t / Pr_t), c_p = gamma / (gamma - 1). Conforming faces between
-// elements of one order (interior or periodic) and adiabatic walls (no-slip, free-slip: mirror
-// ghost states, no viscous energy flux); the host rejects other meshes.
+// elements of one order (interior or periodic); boundary faces: far-field inflow and pressure
+// outflow (ghost states, interior viscous flux), adiabatic walls (no-slip, free-slip: mirror
+// ghost states, no viscous energy flux). The host rejects p-nonconforming meshes.
 //
 // Per residual evaluation / Runge-Kutta stage (the passes of the incompressible FP64 path with
 // five variables):
@@ -232,7 +233,14 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         double jw[3];
         wall_jump<double>(L.kind, vo, Sv, jw);
         jump[0] = jw[0], jump[1] = jw[1], jump[2] = jw[2], jump[3] = 0.0;
-      } else {  // the host admits conforming faces and walls only
+      } else if (L.kind == FK_INFLOW) {  // the far field: v_inf, T = p_inf / rho_inf
+#pragma unroll
+        for (int c = 0; c < 3; ++c) jump[c] = M.inflow[1 + c] - ph[c];
+        jump[3] = M.p_inf / M.inflow[0] - ph[3];
+      } else if (L.kind == FK_OUTFLOW) {  // interior velocity, T = p_inf / rho
+        jump[0] = jump[1] = jump[2] = 0.0;
+        jump[3] = M.p_inf / uu[0] - ph[3];
+      } else {  // the host admits conforming faces and boundary faces only
         atomicCAS(&M.err[0], 0, 5);
         atomicCAS(&M.err[1], 0, 10);
         continue;
@@ -401,7 +409,19 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       up[4] = uu[4];
 #pragma unroll
       for (int c = 0; c < 3; ++c) up[1 + c] = uu[1 + c] + jw[c];
-    } else {  // the host admits conforming faces and walls only
+    } else if (L.kind == FK_INFLOW) {  // the far-field state
+      const double r = M.inflow[0];
+      up[0] = r;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) up[1 + c] = r * M.inflow[1 + c];
+      up[4] = M.p_inf / (gamma - 1.0) +
+              0.5 * r * (M.inflow[1] * M.inflow[1] + M.inflow[2] * M.inflow[2] + M.inflow[3] * M.inflow[3]);
+    } else if (L.kind == FK_OUTFLOW) {  // interior density and momentum, the far-field pressure
+      up[0] = uu[0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) up[1 + c] = uu[1 + c];
+      up[4] = M.p_inf / (gamma - 1.0) + 0.5 * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0];
+    } else {  // the host admits conforming faces and boundary faces only
       atomicCAS(&M.err[0], 0, 5);
       atomicCAS(&M.err[1], 0, 11);
       continue;
@@ -411,10 +431,11 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
     for (int v = 0; v < 5; ++v) JR[v] -= invw * s * fx[v];
     if (L.kind != FK_CONF) {
-      // adiabatic wall, NS element: F_v* . S is the own traction (no-slip) or its normal part
-      // (free-slip) and carries no energy, so the own outward flux minus F_v* . S leaves nothing
-      // (no-slip) or the tangential traction (free-slip) in momentum, and the own energy flux
-      if (ns) {
+      // inflow, outflow: F_v* . S is the own flux, nothing is left. Adiabatic wall, NS element:
+      // F_v* . S is the own traction (no-slip) or its normal part (free-slip) and carries no
+      // energy, so the own outward flux minus F_v* . S leaves nothing (no-slip) or the
+      // tangential traction (free-slip) in momentum, and the own energy flux
+      if (ns && (L.kind == FK_WALL || L.kind == FK_SLIP)) {
         const double tw[3] = {M.Tv[ms], M.Tv[M.tr_total + ms], M.Tv[2 * M.tr_total + ms]};
         if (L.kind == FK_SLIP) {
           double tt[3];

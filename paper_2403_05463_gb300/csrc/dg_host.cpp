@@ -423,6 +423,7 @@ void apply_params(dg_ctx* c) {
   c->M.gamma = c->prm.gamma;
   c->M.prandtl = c->prm.prandtl;
   c->M.prandtl_t = c->prm.prandtl_t;
+  c->M.p_inf = c->prm.p_inf;
   // precisions 2 and 3 are the FP32 path (same data layout) with the inviscid volume
   // contraction on the tensor cores (3xTF32, plain TF32)
   c->M.precision = c->prm.precision >= 1 ? 1 : 0;
@@ -769,9 +770,9 @@ dg_status check_model_mesh(const dg_ctx* c) {
   if (c->prm.model != 1 && c->prm.nodes != 1) return DG_OK;
   const char* what = c->prm.model == 1 ? "compressible form" : "Gauss-Legendre nodes";
   for (int64_t s = 0; s < c->ne * 6; ++s) {
-    if (c->nb[s] < 0 && c->prm.model == 1 && c->bc[s] != 3 && c->bc[s] != 4)
-      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d has boundary tag %d (walls 3 and 4 only)", what,
-                  (long long)(s / 6), (int)(s % 6), (int)c->bc[s]);
+    if (c->nb[s] < 0 && c->prm.model == 1 && (c->bc[s] == 1 || c->bc[s] == 2) &&
+        !(c->prm.inflow[0] > 0.0 && c->prm.p_inf > 0.0))
+      return fail(DG_ERR_ARG, "%s: inflow/outflow faces need a far-field density inflow[0] > 0 and p_inf > 0", what);
     if (c->nb[s] < 0) continue;
     if (c->order[c->nb[s]] != c->order[s / 6])
       return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is p-nonconforming", what, (long long)(s / 6),

@@ -88,6 +88,7 @@ struct DevMesh {
   // 1 compressible (App. A, u = (rho, rho v, rho e); FP64, conforming periodic meshes)
   int model;
   double gamma, prandtl, prandtl_t;  // compressible: ideal gas with unit gas constant
+  double p_inf;                      // compressible: far-field pressure (inflow, outflow ghosts)
   // element nodes: 0 Gauss-Lobatto, 1 Gauss-Legendre (face values interpolated; FP64,
   // incompressible, conforming interior/periodic faces)
   int nodes;

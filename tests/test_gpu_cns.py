@@ -1,8 +1,8 @@
 """Compressible form (App. A, dg_params.model = 1) on the GPU, through the C ABI, against the FP64
 oracle's compressible entry points: residuals, RK steps and conservation sums at the FP64
 tolerance 1e-12 (relative L2), on box, re-oriented curved and every order 1..7, mixed flags,
-Roe/LLF, Vreman/Smagorinsky, both mixed-face choices and adiabatic no-slip/free-slip walls; plus
-what the build rejects."""
+Roe/LLF, Vreman/Smagorinsky, both mixed-face choices, far-field inflow / pressure outflow and
+adiabatic no-slip/free-slip walls; plus what the build rejects."""
 import dataclasses
 
 import numpy as np
@@ -143,15 +143,29 @@ def test_adiabatic_walls(wall):
     assert abs(sums[0]) <= 1e-11 * scale and abs(sums[4]) <= 1e-11 * scale, sums  # walls pass no mass, energy
 
 
+def test_inflow_outflow():
+    # the wake box: far-field inflow at x = 0, pressure outflow at x = 8, periodic in y and z,
+    # mixed flags
+    w = wl.wake_16x16x16_n4(n=5, order=3)
+    rng = np.random.default_rng(7)
+    w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8),
+                            params=dict(wl.cns_tgv().params, nu=1e-2, inflow=(1.05, 0.6, 0.0, 0.05), p_inf=16.0))
+    M = _oracle(w)
+    u = wl.cns_state(M.node_coords(), w.seed, period=4.0)
+    R_ref = M.cns_residual(u)
+    R = _solver(w).residual(to_dev(u)).cpu().numpy()
+    assert rel_l2(R, R_ref) <= TOL, rel_l2(R, R_ref)
+
+
 def test_what_the_compressible_build_rejects():
     import torch
     from paper_2403_05463_gb300 import dg
     p = dict(wl.cns_tgv().params)
-    # boundary faces
+    # inflow/outflow faces without a far field
     wake = wl.wake_16x16x16_n4(n=3, order=2)
     with pytest.raises(dg.DGError) as ei:
         dg.Solver.from_workload(wake, params=p)
-    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
+    assert dg.STATUS[ei.value.status] == "DG_ERR_ARG"
     w = _box(3)
     S = _solver(w)
     # p-nonconforming faces
