@@ -194,6 +194,13 @@ int or_dmat(int N, or_real* D) {
   return 0;
 }
 
+int or_dmat_gl(int N, or_real* D) {
+  or_real x[OR_MAXN + 1], w[OR_MAXN + 1];
+  if (or_gl(N, x, w)) return -1;
+  dmat_nodes(N + 1, x, D);
+  return 0;
+}
+
 int or_interp_lgl(int Ns, int Nd, or_real* I) {
   or_real xs[OR_MAXN + 1], ws[OR_MAXN + 1], xd[OR_MAXN + 1], wd[OR_MAXN + 1];
   if (or_lgl(Ns, xs, ws) || or_lgl(Nd, xd, wd)) return -1;

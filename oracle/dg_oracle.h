@@ -72,6 +72,7 @@ typedef struct or_mesh or_mesh;
 int or_lgl(int N, or_real* x, or_real* w);                  /* x[N+1], w[N+1]          */
 int or_gl(int N, or_real* x, or_real* w);                   /* Gauss-Legendre, N+1 nodes */
 int or_dmat(int N, or_real* D);                            /* D[(N+1)*(N+1)] row-major */
+int or_dmat_gl(int N, or_real* D);                         /* the same on Gauss-Legendre nodes */
 int or_interp_lgl(int Ns, int Nd, or_real* I);             /* I[(Nd+1)][(Ns+1)]        */
 int or_project_lgl(int Nh, int Nl, or_real* P);            /* P[(Nl+1)][(Nh+1)]        */
 

@@ -74,6 +74,7 @@ def lib(extended: bool = False):
             L.or_lgl.argtypes = [ctypes.c_int, _d, _d]
             L.or_gl.argtypes = [ctypes.c_int, _d, _d]
             L.or_dmat.argtypes = [ctypes.c_int, _d]
+            L.or_dmat_gl.argtypes = [ctypes.c_int, _d]
             L.or_interp_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_normal_flux.argtypes = [_d, _d, real, _d]
@@ -164,6 +165,14 @@ def gl(N):
 def dmat(N):
     D = np.zeros((N + 1, N + 1))
     if lib().or_dmat(N, _ptr(D, _d)):
+        raise ValueError(lib().or_error().decode())
+    return D
+
+
+def dmat_gl(N):
+    """Derivative matrix on the N + 1 Gauss-Legendre nodes."""
+    D = np.zeros((N + 1, N + 1))
+    if lib().or_dmat_gl(N, _ptr(D, _d)):
         raise ValueError(lib().or_error().decode())
     return D
 

@@ -16,7 +16,9 @@ Steps, in the order of Sec. 2.1, each written as its plain definition:
 
 Readings where the paper is silent:
   * J is the gradient of the element's own velocity polynomial (no interface lifting), by the
-    chain rule with the discrete metric terms: J_ck = (1/J) sum_d (J dxi_d/dx_k) du_c/dxi_d.
+    chain rule with the discrete metric terms: J_ck = (1/J) sum_d (J dxi_d/dx_k) du_c/dxi_d,
+    at the mesh's nodes: Gauss-Lobatto, or the Gauss-Legendre points the paper's detection
+    uses (the derivative matrix of the mesh's own node set).
   * The mixture is an input (its fitting needs developed-flow snapshots and stays outside):
     weights, means and covariances of the two components in the raw feature units, and which
     component is the viscous/rotational one. Any per-feature scaling used while fitting folds
@@ -35,7 +37,7 @@ def element_velocity_gradient(M: orc.Mesh, q, e):
     """J[c][k][node] = d u_c / d x_k of element e's velocity polynomial at its nodes (step 1)."""
     N = int(M.orders[e])
     n = N + 1
-    D = orc.dmat(N)
+    D = orc.dmat_gl(N) if M.prm.nodes == 1 else orc.dmat(N)  # the mesh's own node set
     sl = M.element_nodes(e)
     U = np.asarray(q[1:4, sl], dtype=np.float64).reshape(3, n, n, n)  # [c][k3][k2][k1], xi_1 fastest
     dU = np.zeros((3, 3, n, n, n))  # [c][d] du_c / dxi_{d+1}

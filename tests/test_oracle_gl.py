@@ -34,6 +34,19 @@ def test_gauss_legendre_exact_to_degree_2n_plus_1(N):
     np.testing.assert_allclose(x, np.polynomial.legendre.leggauss(N + 1)[0], atol=1e-14)
 
 
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_gauss_legendre_derivative_matrix(N):
+    # exact on x^k for k <= N at the Gauss points, rows sum to zero, and it is not the
+    # Lobatto matrix (which would differentiate the wrong interpolant)
+    x, _ = orc.gl(N)
+    D = orc.dmat_gl(N)
+    for k in range(N + 1):
+        exact = k * x ** (k - 1) if k else np.zeros_like(x)
+        np.testing.assert_allclose(D @ x ** k, exact, atol=1e-12 * max(1, k * k))
+    assert np.abs(D.sum(axis=1)).max() < 1e-13
+    assert np.abs(D - orc.dmat(N)).max() > 0.1
+
+
 def _params(**kw):
     base = dict(nu=0.0, c0sq=25.0, cs=0.1, cv=0.07, closure=0, riemann=0, nodes=1)
     base.update(kw)

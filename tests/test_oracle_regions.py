@@ -20,11 +20,11 @@ def _gmm(w=(0.5, 0.5), means=((0, 0, 0), (-0.1, 0, 0.1)), covs=None, viscous=1):
             "viscous": viscous}
 
 
-def _mesh(desc, orders, flags=None):
+def _mesh(desc, orders, flags=None, nodes=0):
     E = desc.hex.shape[0]
     orders = np.broadcast_to(np.asarray(orders, np.int8), (E,)).copy()
     flags = np.zeros(E, np.uint8) if flags is None else flags
-    return orc.Mesh(desc.hex, desc.geom, desc.geom_degree, orders, flags, orc.params(), desc.bc_tag)
+    return orc.Mesh(desc.hex, desc.geom, desc.geom_degree, orders, flags, orc.params(nodes=nodes), desc.bc_tag)
 
 
 def _open_box(n=3, warp=None, geom_degree=1):
@@ -50,16 +50,18 @@ def _trilinear_warp():
     return lambda x, y, z: (x + 0.3 * y * z, y + 0.2 * x * z, z + 0.25 * x * y)
 
 
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
 @pytest.mark.parametrize("kind,orders", [("box", 1), ("box", 3), ("affine", 2), ("rotated", 3),
                                          ("trilinear", 2), ("trilinear", 4)])
-def test_gradient_of_a_linear_field_is_exact(kind, orders):
+def test_gradient_of_a_linear_field_is_exact(kind, orders, nodes):
     # u = A x + b is multilinear in xi on these maps and the metric terms are exact, so the
-    # chain rule returns A at every node (per-node metrics on the trilinear map)
+    # chain rule returns A at every node (per-node metrics on the trilinear map), on either
+    # node set (the paper's detection runs on Gauss-Legendre points)
     warp = {"box": None, "affine": _affine_warp(), "rotated": _affine_warp(), "trilinear": _trilinear_warp()}[kind]
     desc = _open_box(3, warp, geom_degree=2 if kind == "trilinear" else 1)
     if kind == "rotated":
         desc, _ = wl.rotate_elements(desc, 5)
-    M = _mesh(desc, orders)
+    M = _mesh(desc, orders, nodes=nodes)
     rng = np.random.default_rng(11)
     A = rng.normal(size=(3, 3))  # not symmetric: a transposed gradient fails
     q = _linear_state(M, A, rng.normal(size=3))
@@ -68,10 +70,11 @@ def test_gradient_of_a_linear_field_is_exact(kind, orders):
         assert np.abs(G - A[:, :, None]).max() <= 1e-12 * np.abs(A).max(), (kind, e)
 
 
-def test_gradient_of_a_quadratic_field_on_an_affine_element():
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_gradient_of_a_quadratic_field_on_an_affine_element(nodes):
     # u_c = x . H_c x has d u_c / d x_k = ((H_c + H_c^T) x)_k; degree 2 is exact at N = 2
     desc = _open_box(2, _affine_warp())
-    M = _mesh(desc, 2)
+    M = _mesh(desc, 2, nodes=nodes)
     rng = np.random.default_rng(12)
     H = rng.normal(size=(3, 3, 3))
     xyz = M.node_coords()
