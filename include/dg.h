@@ -134,9 +134,9 @@ typedef struct {
                        in FP64 (precision 0) with the standard volume term (split 0) on
                        meshes whose faces are conforming (boundary faces take the same ghost
                        states as on Gauss-Lobatto nodes); other settings give
-                       DG_ERR_UNSUPPORTED, as do dg_project_state,
-                       dg_conservation_noalloc and dg_detect_regions. dg_node_coords returns
-                       the Gauss points.                                                 */
+                       DG_ERR_UNSUPPORTED, as do dg_project_state and
+                       dg_conservation_noalloc. dg_node_coords returns the Gauss points;
+                       dg_detect_regions works on them.                                  */
   int reserved;     /* must be 0                                                       */
   double p_inf;     /* model 1: far-field pressure of the inflow ghost (with inflow[]) and
                        the static pressure of the outflow ghost (interior density and
@@ -269,7 +269,8 @@ typedef struct {
 /* Viscous/inviscid region detection (Sec. 2.1), on the device, from the state q_dev
  * ([4][total_nodes] FP64, the current mesh and orders):
  *   1. at every node, the gradient of the element's velocity polynomial, J_ck = du_c/dx_k, by
- *      the chain rule with the element's metric terms (no interface terms);
+ *      the chain rule with the element's metric terms (no interface terms); the nodes are the
+ *      context's (dg_params.nodes: Gauss-Lobatto, or the Gauss points the paper uses);
  *   2. S = (J + J^T)/2, Omega = (J - J^T)/2, Q_S = (tr(S)^2 - tr(S^2))/2, R_S = -det(S)/3,
  *      Q_Omega = -tr(Omega^2)/2;
  *   3. the posterior probabilities p_v, p_i of the viscous and the other component of `gmm`

@@ -1277,8 +1277,7 @@ dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8
                             double* feat, void* stream) {
   if (!c || !q || !gmm) return fail(DG_ERR_ARG, "NULL argument");
   if (!flags && !pbar && !feat) return fail(DG_ERR_ARG, "dg_detect_regions: no output requested");
-  if (c->prm.model != 0 || c->prm.nodes != 0)
-    return fail(DG_ERR_UNSUPPORTED, "dg_detect_regions: incompressible form on Gauss-Lobatto nodes only");
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_detect_regions: incompressible form only");
   GmmDev g{};
   dg_status st = gmm_prepare(*gmm, g);
   if (st != DG_OK) return st;
@@ -1286,7 +1285,7 @@ dg_status dg_detect_regions(dg_ctx* c, const double* q, const dg_gmm* gmm, uint8
   const OpTables& T = ops();
   for (const Bucket& b : c->all_buckets) {
     DMatArg D{};
-    const std::vector<double>& Dn = T.rule[b.N].D;
+    const std::vector<double>& Dn = node_rule(c, b.N).D;  // Lobatto or Gauss points
     for (size_t i = 0; i < Dn.size(); ++i) D.D[i] = Dn[i];
     CU(launch_detect_regions(c->M, b, g, D, gmm->precision, q, flags, pbar, feat, (cudaStream_t)stream));
   }

@@ -2,7 +2,7 @@
 C ABI, against the oracle on the same node set: node coordinates, residuals, RK steps and
 conservation sums at the FP64 tolerance 1e-12 (relative L2) on box, re-oriented curved and every
 order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman, both mixed-face choices, inflow/outflow and
-wall boundaries; plus what the node set refuses."""
+wall boundaries; the region detection on the Gauss points; plus what the node set refuses."""
 import dataclasses
 
 import numpy as np
@@ -136,8 +136,43 @@ def test_what_gauss_legendre_refuses():
     q = torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda")
     with pytest.raises(dg.DGError):
         S.conservation_noalloc(q, torch.zeros(4, dtype=torch.float64, device="cuda"))
-    with pytest.raises(dg.DGError):
-        S.detect_regions(q, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": [np.eye(3)] * 2, "viscous": 1})
+
+
+@pytest.mark.parametrize("make,precision", [(lambda: _box(3, n=5, seed=2), 0), (lambda: _curved(5, 63), 0),
+                                            (lambda: _curved(4, 64), 1)], ids=["box_n3", "curved_n5", "curved_n4_fp32"])
+def test_region_detection_on_gauss_points(make, precision):
+    """Sec. 2.1's detection on the Gauss-Legendre points the paper clusters: features, node
+    memberships, element means and flags against the oracle on the same node set (FP64 at the
+    region tests' bars; FP32 within its own error), and the flags fed back into the residual."""
+    import torch
+    from oracle import regions as rg
+    from test_gpu_regions import FP32_MARGIN, FP32_PROB_TOL, _gmm_from, _gradient_scale
+    w = make()
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    F = rg.detect_regions(M, q, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": np.stack([np.eye(3)] * 2),
+                                 "viscous": 1})["features"]
+    gmm = _gmm_from(F)
+    ref = rg.detect_regions(M, q, gmm)
+    assert 0 < ref["flags"].sum() < w.n_elem
+    S = _solver(w, p)
+    f, pb, ft = S.detect_regions(to_dev(q), gmm, features=True, precision=precision)
+    torch.cuda.synchronize()
+    f, pb, ft = f.cpu().numpy(), pb.cpu().numpy(), ft.cpu().numpy()
+    g = _gradient_scale(M, q, range(M.ne))
+    # the FP32 bounds are those of the Lobatto FP32 detection test
+    feat_tol, prob_tol, margin = (1e-12, 1e-11, 1e-9) if precision == 0 else (1e-4, FP32_PROB_TOL, FP32_MARGIN)
+    for i, scale in ((0, g * g), (1, g ** 3), (2, g * g)):
+        assert np.abs(ft[i] - ref["features"][i]).max() <= feat_tol * scale, i
+    assert np.abs(ft[3] - ref["p_v"]).max() <= prob_tol
+    assert np.abs(pb - ref["pbar"]).max() <= prob_tol
+    clear = np.abs(ref["pbar"][0] - ref["pbar"][1]) > margin
+    np.testing.assert_array_equal(f[clear], ref["flags"][clear])
+    S.set_flags(f)
+    R = S.residual(to_dev(q)).cpu().numpy()
+    R_ref = _oracle(dataclasses.replace(w, flags=f), p).residual(q)
+    assert rel_l2(R, R_ref) <= TOL
 
 
 def test_a_32cube_case_sampled():
