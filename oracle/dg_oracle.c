@@ -201,13 +201,21 @@ int or_dmat_gl(int N, or_real* D) {
   return 0;
 }
 
-int or_interp_lgl(int Ns, int Nd, or_real* I) {
+/* the rule of a node set: 0 Gauss-Lobatto, 1 Gauss-Legendre */
+static int node_set(int gl, int N, or_real* x, or_real* w) { return gl ? or_gl(N, x, w) : or_lgl(N, x, w); }
+
+/* I[i][j] = l_j(x_i): the degree-Ns interpolant through the source nodes, evaluated at the
+ * destination nodes (both of the same node set) */
+static int interp_nodes(int gl, int Ns, int Nd, or_real* I) {
   or_real xs[OR_MAXN + 1], ws[OR_MAXN + 1], xd[OR_MAXN + 1], wd[OR_MAXN + 1];
-  if (or_lgl(Ns, xs, ws) || or_lgl(Nd, xd, wd)) return -1;
+  if (node_set(gl, Ns, xs, ws) || node_set(gl, Nd, xd, wd)) return -1;
   for (int i = 0; i <= Nd; ++i)
     for (int j = 0; j <= Ns; ++j) I[i * (Ns + 1) + j] = lagrange(Ns + 1, xs, j, xd[i]);
   return 0;
 }
+
+int or_interp_lgl(int Ns, int Nd, or_real* I) { return interp_nodes(0, Ns, Nd, I); }
+int or_interp_gl(int Ns, int Nd, or_real* I) { return interp_nodes(1, Ns, Nd, I); }
 
 /* Solve A X = B in place (A n x n, B n x m, row-major) by Gauss-Jordan with partial
  * pivoting. Returns -1 if A is singular. */
@@ -247,7 +255,11 @@ static int gauss_jordan(int n, or_real* A, int m, or_real* B) {
  * degree Nl <= Nh: P = M_l^{-1} I^T W_h, where I interpolates Nl -> Nh nodes and
  * M_l = I^T W_h I is the exact mass matrix (Nh-point Lobatto quadrature is exact for
  * degree 2 Nl <= 2 Nh - 1 when Nh > Nl). For Nh == Nl, P is the identity. */
-int or_project_lgl(int Nh, int Nl, or_real* P) {
+/* L2 projection of a degree-Nh nodal polynomial onto degree Nl, both on the same node set:
+ * P = M^-1 B with the mass matrix M_ab = (l_a, l_b) and B_aj = (l_a, L_j) of the low (l) and
+ * high (L) Lagrange bases, both integrated exactly by the high rule (degree <= 2 Nh - 1 for
+ * Lobatto, 2 Nh + 1 for Legendre, and the integrands have degree <= Nl + Nh) */
+static int project_nodes(int gl, int Nh, int Nl, or_real* P) {
   int nh = Nh + 1, nl = Nl + 1;
   if (Nl > Nh) {
     set_err("projection needs Nl <= Nh");
@@ -261,7 +273,7 @@ int or_project_lgl(int Nh, int Nl, or_real* P) {
   or_real xh[OR_MAXN + 1], wh[OR_MAXN + 1];
   or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
   or_real M[(OR_MAXN + 1) * (OR_MAXN + 1)];
-  if (or_lgl(Nh, xh, wh) || or_interp_lgl(Nl, Nh, I)) return -1;
+  if (node_set(gl, Nh, xh, wh) || interp_nodes(gl, Nl, Nh, I)) return -1;
   for (int a = 0; a < nl; ++a)
     for (int b = 0; b < nl; ++b) {
       or_real s = 0.0;
@@ -276,6 +288,9 @@ int or_project_lgl(int Nh, int Nl, or_real* P) {
   }
   return 0;
 }
+
+int or_project_lgl(int Nh, int Nl, or_real* P) { return project_nodes(0, Nh, Nl, P); }
+int or_project_gl(int Nh, int Nl, or_real* P) { return project_nodes(1, Nh, Nl, P); }
 
 /* ------------------------------------------------------------------------------------
  * Pointwise physics (App. A in artificial-compressibility form, rho = 1).
@@ -993,10 +1008,10 @@ static void mortar_free(mortar_t* mt) {
 
 /* interpolate a neighbour face field (order Nn) to the mortar order M and rotate it into
  * my face coordinates */
-static void nbr_to_mortar(int Nn, int M, int o, int nvar, const or_real* src, or_real* dst) {
+static void nbr_to_mortar(int gl, int Nn, int M, int o, int nvar, const or_real* src, or_real* dst) {
   int nn = Nn + 1, nM = M + 1, nM2 = nM * nM;
   or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
-  or_interp_lgl(Nn, M, I);
+  interp_nodes(gl, Nn, M, I);
   or_real* tmp = (or_real*)malloc(sizeof(or_real) * nM2);
   for (int v = 0; v < nvar; ++v) {
     interp2(nn, nM, I, src + v * nn * nn, tmp);
@@ -1010,18 +1025,18 @@ static void nbr_to_mortar(int Nn, int M, int o, int nvar, const or_real* src, or
   free(tmp);
 }
 
-static void mine_to_mortar(int Nm, int M, int nvar, const or_real* src, or_real* dst) {
+static void mine_to_mortar(int gl, int Nm, int M, int nvar, const or_real* src, or_real* dst) {
   int nm = Nm + 1, nM = M + 1;
   or_real I[(OR_MAXN + 1) * (OR_MAXN + 1)];
-  or_interp_lgl(Nm, M, I);
+  interp_nodes(gl, Nm, M, I);
   for (int v = 0; v < nvar; ++v) interp2(nm, nM, I, src + v * nm * nm, dst + v * nM * nM);
 }
 
 /* project a mortar field (order M, my coordinates) to my order */
-static void mortar_to_mine(int M, int Nm, int nvar, const or_real* src, or_real* dst) {
+static void mortar_to_mine(int gl, int M, int Nm, int nvar, const or_real* src, or_real* dst) {
   int nm = Nm + 1, nM = M + 1;
   or_real P[(OR_MAXN + 1) * (OR_MAXN + 1)];
-  or_project_lgl(M, Nm, P);
+  project_nodes(gl, M, Nm, P);
   for (int v = 0; v < nvar; ++v) interp2(nM, nm, P, src + v * nM * nM, dst + v * nm * nm);
 }
 
@@ -1044,13 +1059,13 @@ static void mortar_build(const work_t* W, int64_t e, int f, mortar_t* mt) {
   or_real* tS = (or_real*)malloc(sizeof(or_real) * 3 * nm * nm);
   face_q(m, W->q, e, f, tq);
   face_S(m, &W->geo[e], e, f, tS);
-  mine_to_mortar(Nm, M, 4, tq, mt->qm);
-  mine_to_mortar(Nm, M, 3, tS, mt->S);
+  mine_to_mortar(m->p.nodes, Nm, M, 4, tq, mt->qm);
+  mine_to_mortar(m->p.nodes, Nm, M, 3, tS, mt->S);
   if (nb >= 0) {
     int nn = Nn + 1;
     or_real* tn = (or_real*)malloc(sizeof(or_real) * 4 * nn * nn);
     face_q(m, W->q, nb, mt->nf, tn);
-    nbr_to_mortar(Nn, M, mt->no, 4, tn, mt->qp);
+    nbr_to_mortar(m->p.nodes, Nn, M, mt->no, 4, tn, mt->qp);
     free(tn);
   } else {
     for (int p = 0; p < nM2; ++p) {
@@ -1076,7 +1091,7 @@ static void face_ustar(const work_t* W, int64_t e, int f, or_real* LU) {
       or_real us = 0.5 * (mt.qm[(1 + c) * nM2 + p] + mt.qp[(1 + c) * nM2 + p]);
       for (int k = 0; k < 3; ++k) U[(c * 3 + k) * nM2 + p] = us * mt.S[k * nM2 + p];
     }
-  mortar_to_mine(mt.M, mt.nm, 9, U, LU);
+  mortar_to_mine(W->m->p.nodes, mt.M, mt.nm, 9, U, LU);
   free(U);
   mortar_free(&mt);
 }
@@ -1094,13 +1109,13 @@ static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
   if (any_visc) {
     or_real* t = (or_real*)malloc(sizeof(or_real) * 3 * nm2);
     face_fv(W, e, f, t);
-    mine_to_mortar(mt.nm, mt.M, 3, t, Fvm);
+    mine_to_mortar(m->p.nodes, mt.nm, mt.M, 3, t, Fvm);
     free(t);
     if (mt.nbr >= 0) {
       int nn = m->N[mt.nbr] + 1;
       or_real* tn = (or_real*)malloc(sizeof(or_real) * 3 * nn * nn);
       face_fv(W, mt.nbr, mt.nf, tn);
-      nbr_to_mortar(m->N[mt.nbr], mt.M, mt.no, 3, tn, Fvp);
+      nbr_to_mortar(m->p.nodes, m->N[mt.nbr], mt.M, mt.no, 3, tn, Fvp);
       free(tn);
     } else if (mt.tag == 4) {
       /* free-slip wall: the mirror ghost's outward viscous flux is R Fvm, R = I - 2 n n^T the
@@ -1141,7 +1156,7 @@ static int face_hstar(const work_t* W, int64_t e, int f, or_real* LH) {
       H[(1 + c) * nM2 + p] = Fs[1 + c] * s - fv;
     }
   }
-  mortar_to_mine(mt.M, mt.nm, 4, H, LH);
+  mortar_to_mine(m->p.nodes, mt.M, mt.nm, 4, H, LH);
   free(H);
   free(Fvm);
   free(Fvp);
@@ -1326,12 +1341,6 @@ static void free_work(work_t* W) {
 
 int or_residual(const or_mesh* m, const or_real* q, or_real* R, int64_t n_sel, const int64_t* sel) {
   int64_t ne = m->ne;
-  if (m->p.nodes == 1)
-    for (int64_t s = 0; s < ne * 6; ++s)
-      if (m->nb_e[s] >= 0 && m->N[m->nb_e[s]] != m->N[s / 6]) {
-        set_err("Gauss-Legendre nodes: element %lld face %d is p-nonconforming", (long long)(s / 6), (int)(s % 6));
-        return -1;
-      }
   /* elements whose residual is wanted */
   uint8_t* want = (uint8_t*)calloc(ne, 1);
   if (sel) {
@@ -1640,7 +1649,7 @@ static void cns_nbr_face(const or_mesh* m, const or_real* u, const geo_t* gt, in
   }
   or_real* tn = (or_real*)malloc(sizeof(or_real) * 5 * n * n);
   face_u5(m, u, nb, m->nb_f[e * 6 + f], tn);
-  nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 5, tn, T);
+  nbr_to_mortar(m->p.nodes, N, N, m->nb_o[e * 6 + f], 5, tn, T);
   free(tn);
 }
 
@@ -1831,7 +1840,7 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
       cns_face_fv(W, e, f, Fvm);
       if (nb >= 0) {
         cns_face_fv(W, nb, m->nb_f[e * 6 + f], tn);
-        nbr_to_mortar(N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
+        nbr_to_mortar(m->p.nodes, N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
       } else {
         /* adiabatic walls: the ghost's outward flux makes the BR1 average the interior traction
          * (no-slip) or its normal part (free-slip, the reflection R = I - 2 n n^T of the traction),

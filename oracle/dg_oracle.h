@@ -75,6 +75,8 @@ int or_dmat(int N, or_real* D);                            /* D[(N+1)*(N+1)] row
 int or_dmat_gl(int N, or_real* D);                         /* the same on Gauss-Legendre nodes */
 int or_interp_lgl(int Ns, int Nd, or_real* I);             /* I[(Nd+1)][(Ns+1)]        */
 int or_project_lgl(int Nh, int Nl, or_real* P);            /* P[(Nl+1)][(Nh+1)]        */
+int or_interp_gl(int Ns, int Nd, or_real* I);              /* the same two on Gauss-Legendre */
+int or_project_gl(int Nh, int Nl, or_real* P);             /* nodes                     */
 
 /* Pointwise building blocks. n_hat must be a unit vector. */
 void or_normal_flux(const or_real q[4], const or_real n_hat[3], or_real c0sq, or_real out[4]);

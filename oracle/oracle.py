@@ -77,6 +77,8 @@ def lib(extended: bool = False):
             L.or_dmat_gl.argtypes = [ctypes.c_int, _d]
             L.or_interp_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_project_lgl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
+            L.or_interp_gl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
+            L.or_project_gl.argtypes = [ctypes.c_int, ctypes.c_int, _d]
             L.or_normal_flux.argtypes = [_d, _d, real, _d]
             L.or_normal_flux.restype = None
             L.or_kep_flux.argtypes = [_d, _d, _d, _d, real, _d]
@@ -187,6 +189,22 @@ def interp(Ns, Nd):
 def project(Nh, Nl):
     P = np.zeros((Nl + 1, Nh + 1))
     if lib().or_project_lgl(Nh, Nl, _ptr(P, _d)):
+        raise ValueError(lib().or_error().decode())
+    return P
+
+
+def interp_gl(Ns, Nd):
+    """Interpolation from the Ns + 1 to the Nd + 1 Gauss-Legendre nodes."""
+    I = np.zeros((Nd + 1, Ns + 1))
+    if lib().or_interp_gl(Ns, Nd, _ptr(I, _d)):
+        raise ValueError(lib().or_error().decode())
+    return I
+
+
+def project_gl(Nh, Nl):
+    """L2 projection from degree Nh to degree Nl, both on Gauss-Legendre nodes."""
+    P = np.zeros((Nl + 1, Nh + 1))
+    if lib().or_project_gl(Nh, Nl, _ptr(P, _d)):
         raise ValueError(lib().or_error().decode())
     return P
 

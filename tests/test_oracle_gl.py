@@ -3,7 +3,8 @@ forms and exactness, the derivative matrix on polynomials, and the residual with
 face values (free stream on curved re-oriented meshes, conservation with the Gauss weights,
 Euler = NS without viscosity, invariance under element re-numbering, spectral convergence to
 the symbolic Taylor-Green residual), the wall mirror identities, the inflow/outflow free stream,
-and what the node set refuses."""
+p-nonconforming faces (Gauss-point interpolation and projection, free stream, conservation and
+exactness of linear states across mortars) and what the node set refuses."""
 import dataclasses
 import math
 
@@ -155,13 +156,92 @@ def test_spectral_convergence_to_the_symbolic_residual():
 
 def test_what_gauss_legendre_refuses():
     w = _curved(3, seed=10)
-    o = w.orders.copy()
-    o[0] = 4
-    M = _mesh(dataclasses.replace(w, orders=o), _params())
-    with pytest.raises(RuntimeError):
-        M.residual(np.zeros((4, M.total)))
     with pytest.raises(ValueError):
         _mesh(w, _params(split=1))
+
+
+# ---- p-nonconforming faces (mortars, Sec. 3.2) between Gauss point sets ----------------------
+
+@pytest.mark.parametrize("Nl,Nh", [(1, 2), (2, 5), (3, 7)])
+def test_gauss_interpolation_and_projection(Nl, Nh):
+    # interpolation is exact on degree <= Nl; projecting an interpolant gives it back; the
+    # projection is the truncated Legendre series of the high-degree polynomial (numpy)
+    xl, _ = orc.gl(Nl)
+    xh, _ = orc.gl(Nh)
+    I, P = orc.interp_gl(Nl, Nh), orc.project_gl(Nh, Nl)
+    for k in range(Nl + 1):
+        np.testing.assert_allclose(I @ xl ** k, xh ** k, atol=1e-13)
+    np.testing.assert_allclose(P @ I, np.eye(Nl + 1), atol=1e-13)
+    rng = np.random.default_rng(Nh)
+    f = rng.normal(size=Nh + 1)
+    c = np.polynomial.legendre.legfit(xh, f, Nh)
+    np.testing.assert_allclose(P @ f, np.polynomial.legendre.legval(xl, c[:Nl + 1]), atol=1e-12)
+
+
+def _mixed_orders(w, seed, lo=2, hi=5):
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(w, orders=rng.integers(lo, hi + 1, size=w.n_elem).astype(np.int8))
+
+
+def test_free_stream_on_a_curved_mixed_order_mesh():
+    w = _mixed_orders(_curved(3, seed=21), 21)
+    M = _mesh(w, _params(nu=1e-2, closure=1))
+    q = np.zeros((4, M.total))
+    q[0], q[1], q[2], q[3] = 0.3, 1.0, -0.5, 0.25
+    assert np.abs(M.residual(q)).max() < 1e-11
+
+
+@pytest.mark.parametrize("riemann,mixed_face", [(0, 0), (1, 1)])
+def test_conservation_on_mixed_orders(riemann, mixed_face):
+    w = _mixed_orders(_curved(3, seed=22), 22)
+    M = _mesh(w, _params(nu=1e-2, riemann=riemann, mixed_face=mixed_face))
+    q = w.state(M.node_coords())
+    R = M.residual(q)
+    assert np.abs(R).max() > 1e-2
+    assert np.all(np.abs(M.conservation(R)) < 1e-12 * np.abs(R).max())
+
+
+def test_euler_equals_ns_without_viscosity_on_mixed_orders():
+    w = _mixed_orders(_curved(3, seed=23), 23)
+    M0 = _mesh(dataclasses.replace(w, flags=np.zeros_like(w.flags)), _params())
+    M1 = _mesh(dataclasses.replace(w, flags=np.ones_like(w.flags)), _params(cs=0.0))
+    q = w.state(M0.node_coords())
+    assert np.abs(M1.residual(q) - M0.residual(q)).max() <= 1e-12 * np.abs(M0.residual(q)).max()
+
+
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_a_linear_state_gives_the_exact_residual_across_mortars(nodes):
+    # q = (p0 + g.x, u0 + A x) is continuous, so every Riemann flux is the physical flux, the
+    # flux u u^T + p I is quadratic (exact at N >= 2) and tau is constant (all elements NS, no
+    # eddy viscosity), so BR1 averages it exactly: on elements two layers
+    # from the boundary R = -div F exactly, R_p = -c0^2 tr A, R_u = -(A u + u tr A) - g, through
+    # faces between orders 2..5 of re-oriented affine elements. A wrong interpolation,
+    # projection or orientation on a mortar breaks it.
+    T = np.array([[1.0, 0.3, -0.1], [0.2, 0.8, 0.25], [-0.15, 0.1, 1.2]])
+    b = np.linspace(0.0, 1.0, 7)
+    desc = wl.box_mesh(6, 6, 6, b, b, b, periodic=(False, False, False),
+                       warp=lambda x, y, z: tuple(T @ np.stack([x, y, z])))
+    desc, _ = wl.rotate_elements(desc, 31)
+    rng = np.random.default_rng(32)
+    orders = rng.integers(2, 6, size=216).astype(np.int8)
+    flags = np.ones(216, np.uint8)  # all NS: an Euler-NS face halves the viscous flux by design
+    c0sq = 25.0
+    M = orc.Mesh(desc.hex, desc.geom, desc.geom_degree, orders, flags,
+                 _params(nu=1e-2, cs=0.0, nodes=nodes, c0sq=c0sq), desc.bc_tag)
+    A = rng.normal(size=(3, 3))
+    g = rng.normal(size=3)
+    x = M.node_coords()
+    u = np.array([1.0, -0.5, 0.3])[:, None] + A @ x
+    q = np.concatenate([(0.2 + g @ x)[None], u])
+    R = M.residual(q)
+    inner = [i + 6 * (j + 6 * k) for i in (2, 3) for j in (2, 3) for k in (2, 3)]
+    assert len({int(orders[e]) for e in inner}) > 1
+    idx = np.concatenate([np.arange(M.offsets[e], M.offsets[e + 1]) for e in inner])
+    ex_p = -c0sq * np.trace(A) * np.ones(idx.size)
+    ex_u = -(A @ u[:, idx] + u[:, idx] * np.trace(A)) - g[:, None]
+    scale = np.abs(ex_u).max()
+    assert np.abs(R[0, idx] - ex_p).max() <= 1e-11 * abs(ex_p[0])
+    assert np.abs(R[1:, idx] - ex_u).max() <= 1e-11 * scale
 
 
 @pytest.mark.parametrize("flags_value", [0, 1])
