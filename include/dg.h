@@ -131,9 +131,10 @@ typedef struct {
                        tensor Gauss points, face values, face metric terms and viscous
                        traces are interpolated along the normal lines and face terms lifted
                        with l_i(+-1) / w_i. Nodes 1 runs the incompressible form (model 0)
-                       in FP64 (precision 0) with the standard volume term (split 0) on
-                       meshes whose faces are conforming (boundary faces take the same ghost
-                       states as on Gauss-Lobatto nodes); other settings give
+                       in FP64 (precision 0) with the standard volume term (split 0), with
+                       p-nonconforming faces (mortars interpolating and projecting between
+                       the Gauss point sets) and the boundary faces' ghost states of the
+                       Gauss-Lobatto path; other settings give
                        DG_ERR_UNSUPPORTED, as do dg_project_state and
                        dg_conservation_noalloc. dg_node_coords returns the Gauss points;
                        dg_detect_regions works on them.                                  */

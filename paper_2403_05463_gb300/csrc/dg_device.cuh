@@ -144,6 +144,15 @@ __host__ __device__ __forceinline__ int face_node(int f, int n, int a, int b) {
   return a + n * (b + n * fix);
 }
 
+// volume node at position i along the normal line of face f through face coordinates (a, b)
+// (face_node is the node of that line on the face)
+__host__ __device__ __forceinline__ int line_node(int f, int n, int a, int b, int i) {
+  const int d = f >> 1;
+  if (d == 0) return i + n * (a + n * b);
+  if (d == 1) return a + n * (i + n * b);
+  return a + n * (b + n * i);
+}
+
 // my face coordinates (a, b) at order N -> neighbour's (a1, b1)
 __device__ __forceinline__ void inv_orient(int o, int N, int a, int b, int& a1, int& b1) {
   int x = (o & 2) ? N - a : a;

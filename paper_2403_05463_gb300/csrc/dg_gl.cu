@@ -15,8 +15,9 @@
 // With Gauss quadrature exact to degree 2N+1, this strong form equals the weak form of Eq. NS4
 // (the integration by parts is exact for the degree-2N-1 products), face terms included:
 // (.)_face is the interpolant of the nodal product, as the weak form's boundary term requires.
-// Conforming faces only (the host refuses p-nonconforming meshes); boundary faces take the
-// ghost states of the Gauss-Lobatto path (inflow, outflow, no-slip and free-slip walls).
+// p-nonconforming faces (Sec. 3.2) take the mortar results of the shared mortar kernels (the
+// projected u* S and (F_e* - F_v*) . S on the Gauss points); boundary faces take the ghost
+// states of the Gauss-Lobatto path (inflow, outflow, no-slip and free-slip walls).
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -33,14 +34,6 @@ cudaError_t upload_ops_gl(const Ops1D& ops) {
   if (r == cudaSuccess) r = cudaMemcpyToSymbol(c_wg, ops.wg, sizeof(ops.wg));
   if (r == cudaSuccess) r = cudaMemcpyToSymbol(c_lb, ops.lbg, sizeof(ops.lbg));
   return r;
-}
-
-// volume node at position i along the normal line of face f through face coordinates (a, b)
-__device__ __forceinline__ int line_node(int f, int n, int a, int b, int i) {
-  const int d = f >> 1;
-  if (d == 0) return i + n * (a + n * b);
-  if (d == 1) return a + n * (i + n * b);
-  return a + n * (b + n * i);
 }
 
 // the element's face coordinates (a, b) of a volume node on faces normal to direction d
@@ -144,11 +137,6 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         const int f = 2 * d + s;
         const double sg = s ? 1.0 : -1.0;
         const FaceLink L = M.link[e * 6 + f];
-        if (L.kind == FK_MORTAR) {  // the host admits conforming faces only
-          atomicCAS(&M.err[0], 0, 5);
-          atomicCAS(&M.err[1], 0, 20);
-          continue;
-        }
         const double* l = c_lb[N][s];
         const double cf = l[ii[d]] / c_wg[N][ii[d]];
         double uf[3] = {0.0, 0.0, 0.0}, Sv[3], JU[3][3];  // JU[c][k] = (Ja^d_k u_c)_face
@@ -185,6 +173,14 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
             for (int c = 0; c < 3; ++c) JU[c][k] = Ja[d * 3 + k] * uf[c];
           }
+        }
+        if (L.kind == FK_MORTAR) {  // u*_c S_k projected from the mortar, S outward
+          const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) G[c][k] += cf * (M.LU[(c * 3 + k) * M.tr_total + ms] - sg * JU[c][k]);
+          continue;
         }
         double up[3];  // the neighbour's face velocity, or the ghost's behind a boundary face
         if (L.kind == FK_CONF) {
@@ -353,13 +349,6 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       const double* l = c_lb[N][f & 1];
       const double sg = (f & 1) ? 1.0 : -1.0;
       const FaceLink L = M.link[e * 6 + f];
-      if (L.kind == FK_MORTAR) {  // the host admits conforming faces only
-        atomicCAS(&M.err[0], 0, 5);
-        atomicCAS(&M.err[1], 0, 21);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) T[t * 4 + v] = 0.0;
-        continue;
-      }
       double qf[4] = {0.0, 0.0, 0.0, 0.0}, Ff[4] = {0.0, 0.0, 0.0, 0.0}, Sv[3] = {0.0, 0.0, 0.0};
 #pragma unroll
       for (int m = 0; m < n; ++m) {
@@ -373,6 +362,15 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
           for (int k = 0; k < 3; ++k) Sv[k] += l[m] * JA[(d * 3 + k) * n3 + pm];
         }
+      }
+      if (L.kind == FK_MORTAR) {
+        // the projected (F_e* - F_v*) . S from the mortar minus the own outward flux
+        // (inviscid, and viscous for NS elements)
+        const int64_t ms = M.tr_off[e] + t;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          T[t * 4 + v] = M.LH[v * M.tr_total + ms] - sg * Ff[v] + (v > 0 && ns ? M.Tv[(v - 1) * M.tr_total + ms] : 0.0);
+        continue;
       }
       if (!CURVED) {
 #pragma unroll

@@ -177,9 +177,10 @@ std::vector<double> interp_matrix(const std::vector<double>& xs, const std::vect
   return I;
 }
 
-// L2 projection of a degree-Nh polynomial (values at its Lobatto nodes) onto degree Nl:
-// Legendre coefficients by the Nh-point Lobatto quadrature (exact for the modes kept,
-// degree k + Nh <= 2 Nh - 1 for k < Nh), truncation, evaluation at the Nl nodes.
+// L2 projection of a degree-Nh polynomial (values at the nodes of `hi`) onto degree Nl:
+// Legendre coefficients by the rule of `hi` (exact for the modes kept: degree k + Nh <=
+// 2 Nh - 1 for k < Nh on Lobatto nodes, <= 2 Nh + 1 on Gauss points), truncation,
+// evaluation at the nodes of `lo`.
 std::vector<double> projection_matrix(const Rule& hi, const Rule& lo) {
   const int nh = hi.N + 1, nl = lo.N + 1;
   std::vector<double> P(nl * nh, 0.0);
@@ -207,6 +208,8 @@ struct OpTables {
   double glb[NP][2][NP] = {};           // Gauss-Legendre l_i(-1), l_i(+1)
   std::vector<double> interp, proj;  // [(a*NP+b)*NP*NP + i*NP + j]
   std::vector<double> interp_gl;     // Gauss-Lobatto of degree a -> Gauss-Legendre of order b
+  std::vector<double> interp_g, proj_g;  // the same as interp, proj between Gauss point sets
+  std::vector<double> lb_g;              // [(N*2+s)*NP + i] = glb[N][s][i]
   OpTables() {
     for (int N = 1; N <= MAXN; ++N) rule[N] = make_rule(N);
     for (int N = 1; N <= MAXN; ++N) {
@@ -223,15 +226,24 @@ struct OpTables {
         for (int i = 0; i <= b; ++i)
           for (int j = 0; j <= a; ++j) interp_gl[(a * NP + b) * NP * NP + i * NP + j] = I[i * (a + 1) + j];
       }
+    lb_g.assign(NP * 2 * NP, 0.0);
+    for (int N = 1; N <= MAXN; ++N)
+      for (int s = 0; s < 2; ++s)
+        for (int i = 0; i <= N; ++i) lb_g[(N * 2 + s) * NP + i] = glb[N][s][i];
+    fill_mortar_tables(rule, interp, proj);
+    fill_mortar_tables(gl, interp_g, proj_g);
+  }
+  // interpolation a -> b and projection a -> b <= a between the node sets of one rule family
+  static void fill_mortar_tables(const Rule* r, std::vector<double>& interp, std::vector<double>& proj) {
     interp.assign(NP * NP * NP * NP, 0.0);
     proj.assign(NP * NP * NP * NP, 0.0);
     for (int a = 1; a <= MAXN; ++a)
       for (int b = 1; b <= MAXN; ++b) {
-        auto I = interp_matrix(rule[a].x, rule[b].x);
+        auto I = interp_matrix(r[a].x, r[b].x);
         for (int i = 0; i <= b; ++i)
           for (int j = 0; j <= a; ++j) interp[(a * NP + b) * NP * NP + i * NP + j] = I[i * (a + 1) + j];
         if (b <= a) {
-          auto P = projection_matrix(rule[a], rule[b]);
+          auto P = projection_matrix(r[a], r[b]);
           for (int i = 0; i <= b; ++i)
             for (int j = 0; j <= a; ++j) proj[(a * NP + b) * NP * NP + i * NP + j] = P[i * (a + 1) + j];
         }
@@ -765,10 +777,11 @@ dg_status rebuild_flags(dg_ctx* c) {
   return DG_OK;
 }
 
-// The compressible form is built for interior/periodic conforming faces only.
+// The compressible form is built for conforming faces only, and needs a far field at its
+// inflow and outflow faces.
 dg_status check_model_mesh(const dg_ctx* c) {
-  if (c->prm.model != 1 && c->prm.nodes != 1) return DG_OK;
-  const char* what = c->prm.model == 1 ? "compressible form" : "Gauss-Legendre nodes";
+  if (c->prm.model != 1) return DG_OK;
+  const char* what = "compressible form";
   for (int64_t s = 0; s < c->ne * 6; ++s) {
     if (c->nb[s] < 0 && c->prm.model == 1 && (c->bc[s] == 1 || c->bc[s] == 2) &&
         !(c->prm.inflow[0] > 0.0 && c->prm.p_inf > 0.0))
@@ -941,12 +954,18 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
   const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
-  if (M.nodes == 1) {  // Gauss-Legendre nodes: no mortar phases (conforming faces only)
+  if (M.nodes == 1) {  // Gauss-Legendre nodes: the mortar kernels take the Gauss-point tables
     if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
       for (const Bucket& b : c->ord_buckets) {
         CU(launch_traces_gl(M, b, q, s));
         ++nl;
       }
+    } else if (phase == 1 && c->n_mortar_ns) {
+      CU(launch_mortar_lift(M, c->mortar_ns, c->n_mortar_ns, s));
+      ++nl;
+    } else if (phase == 3 && c->n_mortar_all) {
+      CU(launch_mortar_flux(M, c->mortar_all, c->n_mortar_all, s));
+      ++nl;
     } else if (phase == 2) {
       for (const Bucket& b : c->ns_buckets) {
         CU(launch_viscous_gl(M, b, q, s));
@@ -1171,6 +1190,16 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
     return st;
   }
   c->M.interp_gl = dtab;
+  const char* gnames[3] = {"interp_g", "proj_g", "lb_g"};
+  const std::vector<double>* gtabs[3] = {&T.interp_g, &T.proj_g, &T.lb_g};
+  const double** gdst[3] = {&c->M.interp_g, &c->M.proj_g, &c->M.lb_g};
+  for (int i = 0; i < 3; ++i) {
+    if ((st = dev_upload(c, gnames[i], *gtabs[i], &dtab)) != DG_OK) {
+      dg_destroy(c);
+      return st;
+    }
+    *gdst[i] = dtab;
+  }
   int* derr;
   if ((st = dev_alloc(c, "err", 4, &derr)) != DG_OK) {
     dg_destroy(c);
@@ -1310,8 +1339,9 @@ dg_status dg_set_params(dg_ctx* c, const dg_params* params) {
   c->prm = *params;
   apply_params(c);
   destroy_graph(c);
-  if (params->model != old.model) {
-    // the number of state planes changes the trace and viscous buffers
+  if (params->model != old.model || params->nodes != old.nodes) {
+    // the number of state planes changes the trace and viscous buffers; the node set moves
+    // the nodes, their metric terms and the face tables
     st = rebuild_orders(c);
     if (st != DG_OK) {
       std::string msg = g_last_error;

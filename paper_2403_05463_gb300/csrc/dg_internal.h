@@ -90,9 +90,12 @@ struct DevMesh {
   double gamma, prandtl, prandtl_t;  // compressible: ideal gas with unit gas constant
   double p_inf;                      // compressible: far-field pressure (inflow, outflow ghosts)
   // element nodes: 0 Gauss-Lobatto, 1 Gauss-Legendre (face values interpolated; FP64,
-  // incompressible, conforming interior/periodic faces)
+  // incompressible)
   int nodes;
   const double* interp_gl;   // [(g*NP+N)*NP*NP + i*NP + j]: Gauss-Lobatto degree g -> Gauss-Legendre order N
+  const double* interp_g;    // the layout of interp and proj, between Gauss-Legendre point sets
+  const double* proj_g;      // (mortars on Gauss-Legendre nodes)
+  const double* lb_g;        // [(N*2+s)*NP + i]: Gauss-Legendre l_i(-1) (s = 0), l_i(+1) (s = 1)
 };
 
 // 1D Gauss-Lobatto operators for N = 1..MAXN (uploaded to constant memory).

@@ -433,13 +433,16 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 }
 
 // ---------------------------------------------------------------------------------------
-// mortars (p-nonconforming faces): one block per (element, face) slot
+// mortars (p-nonconforming faces): one block per (element, face) slot. They serve both node
+// sets: on Gauss-Legendre nodes the traces are already the interpolated face values, S is the
+// interpolated face metric and the tables interpolate and project between Gauss point sets.
 // ---------------------------------------------------------------------------------------
+// the tables of the context's node set: Gauss-Lobatto, or Gauss-Legendre points (nodes = 1)
 __device__ __forceinline__ const double* interp_tab(const DevMesh& M, int Ns, int Nd) {
-  return M.interp + (Ns * NP + Nd) * NP * NP;
+  return (M.nodes == 1 ? M.interp_g : M.interp) + (Ns * NP + Nd) * NP * NP;
 }
 __device__ __forceinline__ const double* proj_tab(const DevMesh& M, int Nh, int Nl) {
-  return M.proj + (Nh * NP + Nl) * NP * NP;
+  return (M.nodes == 1 ? M.proj_g : M.proj) + (Nh * NP + Nl) * NP * NP;
 }
 
 // 2D tensor application on a face: dst[a + nd b] = sum T[a][aa] T[b][bb] src[aa + ns bb]
@@ -459,6 +462,28 @@ __device__ __forceinline__ void node_metric(const DevMesh& M, int e, int64_t nod
   } else {
     for (int k = 0; k < 9; ++k) Ja[k] = M.ec[e].Ja[k];
   }
+}
+
+// outward face metric S = sigma Ja^d at face point (a, b) of face f of element e (order n - 1):
+// the face node's metric on Gauss-Lobatto nodes; on Gauss-Legendre nodes the interpolant of
+// Ja^d along the normal line, sum_i l_i(+-1) Ja^d_i (exact: constant on affine elements)
+__device__ __forceinline__ void face_metric(const DevMesh& M, int e, int f, int n, int a, int b, double S[3]) {
+  const int d = f >> 1;
+  const double sg = (f & 1) ? 1.0 : -1.0;
+  const int64_t off = M.elem_off[e];
+  double Ja[9];
+  if (M.nodes == 1 && M.ec[e].curved != 0.0) {
+    const double* l = M.lb_g + ((n - 1) * 2 + (f & 1)) * NP;
+    S[0] = S[1] = S[2] = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t node = off + line_node(f, n, a, b, i);
+      for (int k = 0; k < 3; ++k) S[k] += l[i] * M.geo[(d * 3 + k) * M.total + node];
+    }
+    for (int k = 0; k < 3; ++k) S[k] *= sg;
+    return;
+  }
+  node_metric(M, e, off + face_node(f, n, a, b), Ja);
+  for (int k = 0; k < 3; ++k) S[k] = sg * Ja[d * 3 + k];
 }
 
 // trace value of variable v at trace slot `slot`: FP64 planes [4][tr_total], or with precision 1
@@ -494,14 +519,11 @@ __global__ void k_mortar_lift(DevMesh M, const int32_t* __restrict__ slots, int 
   const FaceLink L = M.link[es];
   const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
   const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
-  const int d = f >> 1;
-  const double sg = (f & 1) ? 1.0 : -1.0;
   const int t = threadIdx.x;
   if (t < nm * nm) {
-    int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
-    double Ja[9];
-    node_metric(M, e, node, Ja);
-    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
+    double Sv[3];
+    face_metric(M, e, f, nm, t % nm, t / nm, Sv);
+    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = Sv[k];
     for (int c = 0; c < 3; ++c) sm.mine[c][t] = tq_load(M, 1 + c, M.tr_off[e] + f * nm * nm + t);
   }
   if (t < nn * nn)
@@ -539,16 +561,13 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
   const FaceLink L = M.link[es];
   const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
   const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
-  const int d = f >> 1;
-  const double sg = (f & 1) ? 1.0 : -1.0;
   const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
   const int t = threadIdx.x;
   // planes 0..3: q, 4..6: outward viscous traces
   if (t < nm * nm) {
-    int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
-    double Ja[9];
-    node_metric(M, e, node, Ja);
-    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Ja[d * 3 + k];
+    double Sv[3];
+    face_metric(M, e, f, nm, t % nm, t / nm, Sv);
+    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = Sv[k];
     const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
     for (int v = 0; v < 4; ++v) sm.mine[v][t] = tq_load(M, v, s0);
     for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? tv_load(M, c, s0) : 0.0;

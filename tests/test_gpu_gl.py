@@ -2,7 +2,9 @@
 C ABI, against the oracle on the same node set: node coordinates, residuals, RK steps and
 conservation sums at the FP64 tolerance 1e-12 (relative L2) on box, re-oriented curved and every
 order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman, both mixed-face choices, inflow/outflow and
-wall boundaries; the region detection on the Gauss points; plus what the node set refuses."""
+wall boundaries, p-nonconforming faces (mortars between Gauss point sets, orders 1..7), order and
+node-set changes on a live context; the region detection on the Gauss points; plus what the node
+set refuses."""
 import dataclasses
 
 import numpy as np
@@ -124,11 +126,6 @@ def test_what_gauss_legendre_refuses():
     w = _box(3)
     p = _gl(w)
     S = _solver(w, p)
-    o = w.orders.copy()
-    o[0] = 4
-    with pytest.raises(dg.DGError) as ei:
-        S.set_orders(o)
-    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
     for bad, prec in ((dict(split=1), 0), (dict(model=1), 0), ({}, 1)):
         with pytest.raises(dg.DGError):
             S.set_params(dict(p, **bad), precision=prec)
@@ -136,6 +133,69 @@ def test_what_gauss_legendre_refuses():
     q = torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda")
     with pytest.raises(dg.DGError):
         S.conservation_noalloc(q, torch.zeros(4, dtype=torch.float64, device="cuda"))
+
+
+def _mixed(w, seed, lo, hi):
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(w, orders=rng.integers(lo, hi + 1, size=w.n_elem).astype(np.int8))
+
+
+MORTAR_CASES = [
+    ("box_orders_1_7", lambda: _mixed(_box(3, n=5, seed=3), 90, 1, 7), dict(nu=1e-2)),
+    ("curved_orders_2_6_vreman_llf", lambda: _mixed(_curved(3, 91), 91, 2, 6), dict(nu=1e-2, closure=1, riemann=1)),
+    ("curved_orders_2_5_onesided", lambda: _mixed(_curved(3, 92), 92, 2, 5), dict(nu=1e-2, mixed_face=1)),
+    ("channel_noslip_orders_2_5", lambda: _mixed(wl.channel_walls(n=4, wall=3), 93, 2, 5), dict(nu=1e-2)),
+    ("wake_orders_2_5", lambda: _mixed(wl.wake_16x16x16_n4(n=6, order=4), 94, 2, 5), dict(nu=1e-2)),
+]
+
+
+@pytest.mark.parametrize("name,make,extra", MORTAR_CASES, ids=[c[0] for c in MORTAR_CASES])
+def test_p_nonconforming_faces(name, make, extra):
+    """Mortars between Gauss point sets (Sec. 3.2 on App. B's nodes): the residual on meshes
+    whose neighbouring elements differ in order, mixed flags, against the oracle at 1e-12."""
+    w = make()
+    rng = np.random.default_rng(7)
+    w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8))
+    p = _gl(w, **extra)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    R = _solver(w, p).residual(to_dev(q)).cpu().numpy()
+    assert rel_l2(R, M.residual(q)) <= TOL
+
+
+def test_mortar_rk_steps_conservation_and_order_changes():
+    # RK steps on a mixed-order curved mesh, the conservation sums, then a change of orders
+    # through dg_set_orders and a change of node set through dg_set_params on the same context
+    w = _mixed(_curved(3, 95), 95, 2, 6)
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    g = np.zeros_like(q)
+    S = _solver(w, p)
+    qd, gd = to_dev(q), to_dev(g)
+    S.rk_step(qd, gd, 1e-3, 4)
+    M.rk_step(q, g, 1e-3, 4)
+    assert rel_l2(qd.cpu().numpy(), q) <= TOL
+    R = S.residual(qd)
+    sums = S.conservation(R)
+    scale = np.abs(R.cpu().numpy()).max()
+    assert np.all(np.abs(sums) <= 1e-11 * scale), sums
+    w2 = _mixed(w, 96, 2, 7)  # the degree-2 geometry needs N >= 2
+    S.set_orders(w2.orders)
+    M2 = _oracle(w2, p)
+    q2 = w2.state(M2.node_coords())
+    np.testing.assert_allclose(S.node_coords().cpu().numpy(), M2.node_coords(), atol=1e-13)
+    assert rel_l2(S.residual(to_dev(q2)).cpu().numpy(), M2.residual(q2)) <= TOL
+    # back to Gauss-Lobatto nodes, then Gauss points again: the nodes, metric terms and tables
+    # follow the node set
+    p0 = dict(p, nodes=0)
+    S.set_params(p0, precision=0)
+    M0 = _oracle(w2, p0)
+    q0 = w2.state(M0.node_coords())
+    np.testing.assert_allclose(S.node_coords().cpu().numpy(), M0.node_coords(), atol=1e-13)
+    assert rel_l2(S.residual(to_dev(q0)).cpu().numpy(), M0.residual(q0)) <= TOL
+    S.set_params(p, precision=0)
+    assert rel_l2(S.residual(to_dev(q2)).cpu().numpy(), M2.residual(q2)) <= TOL
 
 
 @pytest.mark.parametrize("make,precision", [(lambda: _box(3, n=5, seed=2), 0), (lambda: _curved(5, 63), 0),
