@@ -135,9 +135,9 @@ typedef struct {
                        p-nonconforming faces (mortars interpolating and projecting between
                        the Gauss point sets) and the boundary faces' ghost states of the
                        Gauss-Lobatto path; other settings give
-                       DG_ERR_UNSUPPORTED, as do dg_project_state and
-                       dg_conservation_noalloc. dg_node_coords returns the Gauss points;
-                       dg_detect_regions works on them.                                  */
+                       DG_ERR_UNSUPPORTED. dg_node_coords returns the Gauss points;
+                       dg_detect_regions, dg_project_state and the conservation sums work
+                       on them.                                                          */
   int reserved;     /* must be 0                                                       */
   double p_inf;     /* model 1: far-field pressure of the inflow ghost (with inflow[]) and
                        the static pressure of the outflow ghost (interior density and
@@ -161,7 +161,8 @@ dg_status dg_set_orders(dg_ctx* ctx, const int8_t* orders);
  * restarting after the orders are re-assigned). q_old ([4][total before that call], device)
  * is read in the previous layout, q_new ([4][current total_nodes], device, caller-allocated,
  * not overlapping q_old) is written in the current one: per element, Lagrange interpolation
- * onto the new Gauss-Lobatto nodes where the order grew or stayed (exact for the old
+ * onto the new nodes (Gauss-Lobatto, or Gauss points with nodes 1) where the order grew or
+ * stayed (exact for the old
  * polynomial), the L2 projection in reference coordinates where it dropped (keeps each
  * element's reference-space integral), applied along each direction. Asynchronous on
  * `stream`. DG_ERR_STATE before any dg_set_orders; DG_ERR_UNSUPPORTED under model 1. */

@@ -209,11 +209,13 @@ def project_gl(Nh, Nl):
     return P
 
 
-def project_state(orders_old, orders_new, q_old):
+def project_state(orders_old, orders_new, q_old, nodes=0):
     """The state re-laid out for new per-element orders (Sec. 3.2, re-assigning orders):
-    element by element, Lagrange interpolation onto the new Gauss-Lobatto nodes where the order
-    grows or stays, the L2 projection (in reference coordinates) where it drops, applied along
-    each of the three directions. q_old: [4][sum (N_old + 1)^3]; returns [4][sum (N_new + 1)^3]."""
+    element by element, Lagrange interpolation onto the new nodes (Gauss-Lobatto, or
+    Gauss-Legendre with nodes=1) where the order grows or stays, the L2 projection (in
+    reference coordinates) where it drops, applied along each of the three directions.
+    q_old: [4][sum (N_old + 1)^3]; returns [4][sum (N_new + 1)^3]."""
+    up, down = (interp_gl, project_gl) if nodes == 1 else (interp, project)
     orders_old = np.asarray(orders_old, dtype=np.int64)
     orders_new = np.asarray(orders_new, dtype=np.int64)
     off_o = np.concatenate([[0], np.cumsum((orders_old + 1) ** 3)])
@@ -223,7 +225,7 @@ def project_state(orders_old, orders_new, q_old):
     for e in range(len(orders_old)):
         No, Nn = int(orders_old[e]), int(orders_new[e])
         if (No, Nn) not in ops:
-            ops[No, Nn] = interp(No, Nn) if Nn >= No else project(No, Nn)
+            ops[No, Nn] = up(No, Nn) if Nn >= No else down(No, Nn)
         T = ops[No, Nn]
         no, nn = No + 1, Nn + 1
         A = q_old[:, off_o[e]:off_o[e + 1]].reshape(4, no, no, no)  # [v][k][j][i], i fastest

@@ -1243,8 +1243,8 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
 dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* stream) {
   if (!c || !q_old || !q_new) return fail(DG_ERR_ARG, "NULL argument");
   if (c->prev_order.empty()) return fail(DG_ERR_STATE, "dg_project_state needs a preceding dg_set_orders");
-  if (c->prm.model != 0 || c->prm.nodes != 0)
-    return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form on Gauss-Lobatto nodes only");
+  // the interpolation and projection tables follow the node set (Gauss-Lobatto or Gauss points)
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form only");
   if (q_old == q_new) return fail(DG_ERR_ARG, "q_old and q_new must not overlap");
   CU(cudaSetDevice(c->device));
   int8_t* dord = nullptr;
@@ -1541,8 +1541,7 @@ static_assert(DG_CONSERVATION_NOALLOC_MAX_ELEMS == kNoAllocMaxElems, "scratch li
 // argument built on the stack; the partial sums use the static scratch of dg_noalloc.cu.
 dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, void* stream) {
   if (!c || !R || !out_dev) return fail(DG_ERR_ARG, "NULL argument");
-  if (c->prm.model != 0 || c->prm.nodes != 0)
-    return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form on Gauss-Lobatto nodes only");
+  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form only");
   if (c->ne > kNoAllocMaxElems)
     return fail(DG_ERR_ARG, "dg_conservation_noalloc: the mesh has %lld elements, the static scratch holds %lld",
                 (long long)c->ne, (long long)kNoAllocMaxElems);
@@ -1550,9 +1549,8 @@ dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, v
   double* scratch = nullptr;
   CU(noalloc_scratch(c->device, &scratch));
   NoAllocWeights W{};
-  const OpTables& T = ops();
   for (int N = 1; N <= MAXN; ++N)
-    for (int i = 0; i <= N; ++i) W.w[N][i] = T.rule[N].w[i];
+    for (int i = 0; i <= N; ++i) W.w[N][i] = node_rule(c, N).w[i];
   CU(launch_conservation_noalloc(c->M, c->ord_buckets.data(), (int)c->ord_buckets.size(), W, R, scratch, out_dev,
                                  (cudaStream_t)stream));
   return DG_OK;

@@ -3,8 +3,8 @@ C ABI, against the oracle on the same node set: node coordinates, residuals, RK 
 conservation sums at the FP64 tolerance 1e-12 (relative L2) on box, re-oriented curved and every
 order 1..7, mixed flags, Roe/LLF, Smagorinsky/Vreman, both mixed-face choices, inflow/outflow and
 wall boundaries, p-nonconforming faces (mortars between Gauss point sets, orders 1..7), order and
-node-set changes on a live context; the region detection on the Gauss points; plus what the node
-set refuses."""
+node-set changes on a live context; the state re-projection and the allocation-free sums; the
+region detection on the Gauss points; plus what the node set refuses."""
 import dataclasses
 
 import numpy as np
@@ -130,9 +130,37 @@ def test_what_gauss_legendre_refuses():
         with pytest.raises(dg.DGError):
             S.set_params(dict(p, **bad), precision=prec)
     S.set_params(p, precision=0)
-    q = torch.zeros((4, S.total_nodes), dtype=torch.float64, device="cuda")
-    with pytest.raises(dg.DGError):
-        S.conservation_noalloc(q, torch.zeros(4, dtype=torch.float64, device="cuda"))
+
+
+def test_state_reprojection_and_allocation_free_sums_on_gauss_points():
+    """dg_project_state after two re-assignments of orders on a curved mesh (interpolation
+    onto the new Gauss points, L2 projection where the order drops) against the oracle's, then
+    the residual on the re-laid-out state, and dg_conservation_noalloc with the Gauss weights."""
+    import torch
+    w = _mixed(_curved(3, 97), 97, 2, 7)
+    p = _gl(w, nu=1e-2)
+    M = _oracle(w, p)
+    q = w.state(M.node_coords())
+    S = _solver(w, p)
+    rng = np.random.default_rng(98)
+    o_prev, q_prev, qd = w.orders.copy(), q, to_dev(q)
+    for _ in range(2):
+        o_new = rng.integers(2, 8, size=w.n_elem).astype(np.int8)
+        S.set_orders(o_new)
+        qd = S.project_state(qd)
+        torch.cuda.synchronize()
+        ref = orc.project_state(o_prev, o_new, q_prev, nodes=1)
+        assert np.abs(qd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+        o_prev, q_prev = o_new, ref
+    w2 = dataclasses.replace(w, orders=o_prev)
+    M2 = _oracle(w2, p)
+    R = S.residual(qd)
+    assert rel_l2(R.cpu().numpy(), M2.residual(q_prev)) <= TOL
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    S.conservation_noalloc(R, out)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), S.conservation(R), rtol=0,
+                               atol=1e-13 * np.abs(R.cpu().numpy()).max())
 
 
 def _mixed(w, seed, lo, hi):

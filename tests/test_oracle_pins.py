@@ -590,7 +590,8 @@ def _poly_state(x, deg):
     return np.stack([sum(0.1 * (k + 1) * x[(k + v) % 3] ** k for k in range(deg + 1)) for v in range(4)])
 
 
-def test_project_state_is_exact_for_representable_polynomials():
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_project_state_is_exact_for_representable_polynomials(nodes):
     # affine elements: a polynomial of degree <= min(N_old, N_new) in x is one in xi, so both
     # interpolation (order up) and L2 projection (order down) reproduce it at the new nodes
     w = wl.tgv_4x4x4_n3(n_elem_dir=3, order=3)
@@ -598,29 +599,32 @@ def test_project_state_is_exact_for_representable_polynomials():
     o_old = rng.integers(2, 8, size=27).astype(np.int8)
     o_new = rng.integers(2, 8, size=27).astype(np.int8)
     m = w.mesh
-    A = orc.Mesh(m.hex, m.geom, 1, o_old, w.flags, orc.params(**w.params))
-    B = orc.Mesh(m.hex, m.geom, 1, o_new, w.flags, orc.params(**w.params))
+    prm = orc.params(**dict(w.params, nodes=nodes))
+    A = orc.Mesh(m.hex, m.geom, 1, o_old, w.flags, prm)
+    B = orc.Mesh(m.hex, m.geom, 1, o_new, w.flags, prm)
     deg = 2
     q_old = _poly_state(A.node_coords(), deg)
-    q_new = orc.project_state(o_old, o_new, q_old)
+    q_new = orc.project_state(o_old, o_new, q_old, nodes=nodes)
     np.testing.assert_allclose(q_new, _poly_state(B.node_coords(), deg), rtol=0, atol=1e-12)
 
 
-def test_project_state_round_trip_and_element_integrals():
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_project_state_round_trip_and_element_integrals(nodes):
     rng = np.random.default_rng(9)
     E = 20
     o_lo = rng.integers(1, 6, size=E)
     o_hi = np.minimum(o_lo + rng.integers(0, 3, size=E), 7)
     q = rng.normal(size=(4, int(((o_lo + 1) ** 3).sum())))
-    up = orc.project_state(o_lo, o_hi, q)
-    np.testing.assert_allclose(orc.project_state(o_hi, o_lo, up), q, rtol=0, atol=1e-12)  # refine, coarsen back
+    up = orc.project_state(o_lo, o_hi, q, nodes=nodes)
+    np.testing.assert_allclose(orc.project_state(o_hi, o_lo, up, nodes=nodes), q, rtol=0, atol=1e-12)  # refine, coarsen back
     # coarsening is the L2 projection: the reference-space integral of each element is kept
     qh = rng.normal(size=(4, int(((o_hi + 1) ** 3).sum())))
-    ql = orc.project_state(o_hi, o_lo, qh)
+    ql = orc.project_state(o_hi, o_lo, qh, nodes=nodes)
     oh = np.concatenate([[0], np.cumsum((o_hi + 1) ** 3)])
     ol = np.concatenate([[0], np.cumsum((o_lo + 1) ** 3)])
+    rule = orc.gl if nodes == 1 else orc.lgl
     for e in range(E):
-        wh, wl3 = [np.einsum('i,j,k->kji', *(orc.lgl(int(N))[1],) * 3).ravel() for N in (o_hi[e], o_lo[e])]
+        wh, wl3 = [np.einsum('i,j,k->kji', *(rule(int(N))[1],) * 3).ravel() for N in (o_hi[e], o_lo[e])]
         np.testing.assert_allclose(ql[:, ol[e]:ol[e + 1]] @ wl3, qh[:, oh[e]:oh[e + 1]] @ wh, rtol=1e-12, atol=1e-12)
 
 
