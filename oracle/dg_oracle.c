@@ -1660,6 +1660,8 @@ typedef struct {
   or_real** G;  /* per NS element [4][3][n3] */
 } cwork_t;
 
+static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_real* LH);
+
 /* BR1 gradient of phi, weak form: w J G_ck = -sum_d (w/w_{i_d}) sum_m w_m D_{m i_d} (phi_c Ja^d_k)_m
  * + face terms phi*_c S_k with phi* = (phi^- + phi^+)/2 */
 static void cns_gradient(const cwork_t* W, int64_t e, or_real* G) {
@@ -1694,31 +1696,17 @@ static void cns_gradient(const cwork_t* W, int64_t e, or_real* G) {
             }
             G[(c * 3 + k) * n3 + ii + n * (jj + n * kk)] = s;
           }
-  or_real* um = (or_real*)malloc(sizeof(or_real) * 5 * n2);
-  or_real* up = (or_real*)malloc(sizeof(or_real) * 5 * n2);
-  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
+  or_real* LU = (or_real*)malloc(sizeof(or_real) * 12 * n2);
   for (int f = 0; f < 6; ++f) {
-    face_u5(m, W->u, e, f, um);
-    cns_nbr_face(m, W->u, gt, e, f, up);
-    face_S(m, gt, e, f, S);
+    cns_face_mortar(W, e, f, LU, NULL); /* projected phi* S on my face nodes */
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
         const int fp = a + n * b;
-        or_real qm[5], qp[5], pm[4], pp[4];
-        for (int v = 0; v < 5; ++v) {
-          qm[v] = um[v * n2 + fp];
-          qp[v] = up[v * n2 + fp];
-        }
-        cns_phi(qm, m->p.gamma, pm);
-        cns_phi(qp, m->p.gamma, pp);
         const int64_t p = face_node(f, N, a, b);
-        for (int c = 0; c < 4; ++c)
-          for (int k = 0; k < 3; ++k) G[(c * 3 + k) * n3 + p] += 0.5 * (pm[c] + pp[c]) * S[k * n2 + fp] / w[0];
+        for (int ck = 0; ck < 12; ++ck) G[ck * n3 + p] += LU[ck * n2 + fp] / w[0];
       }
   }
-  free(um);
-  free(up);
-  free(S);
+  free(LU);
   free(phi);
   for (int ck = 0; ck < 12; ++ck)
     for (int p = 0; p < n3; ++p) G[ck * n3 + p] /= gt->J[p];
@@ -1771,6 +1759,106 @@ static void cns_face_fv(const cwork_t* W, int64_t e, int f, or_real* out) {
   free(S);
 }
 
+/* Face (e, f) of the compressible form on the mortar of the larger order (reading 10 with
+ * five variables): both sides' conservative face states (and, for LH, their outward viscous
+ * traces) interpolated to the mortar, combined point by point, L2-projected back to my order.
+ * A conforming face is its own mortar (identity operators); a boundary face takes the ghost
+ * state and the boundary's viscous rule on my own face.
+ *   LU [12][n2] (NULL to skip): projected phi*_c S_k, phi* = ({{phi(u)}}) for phi = (v, T);
+ *   LH [5][n2]  (NULL to skip): projected F_e*(u-, u+) . S - F_v* . S, my outward S.
+ * Returns -1 if a Riemann flux failed. */
+static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_real* LH) {
+  const or_mesh* m = W->m;
+  const geo_t* gt = &W->geo[e];
+  const int N = m->N[e], n = N + 1, n2 = n * n;
+  const int64_t nb = m->nb_e[e * 6 + f];
+  const int Nn = nb >= 0 ? m->N[nb] : N, nn = Nn + 1, nn2 = nn * nn;
+  const int Mo = N > Nn ? N : Nn, nM = Mo + 1, nM2 = nM * nM;
+  const int nf = m->nb_f[e * 6 + f], o = m->nb_o[e * 6 + f];
+  or_real* buf = (or_real*)calloc((size_t)(5 * n2 + 3 * n2 + 4 * n2 + 5 * nn2 + 4 * nn2) + (size_t)nM2 * (5 + 5 + 3 + 4 + 4 + 12),
+                                  sizeof(or_real));
+  or_real *um = buf, *S = um + 5 * n2, *fvm = S + 3 * n2, *tn = fvm + 4 * n2, *fvn = tn + 5 * nn2;
+  or_real *uM = fvn + 4 * nn2, *uP = uM + 5 * nM2, *SM = uP + 5 * nM2, *FvM = SM + 3 * nM2, *FvP = FvM + 4 * nM2;
+  or_real* H = FvP + 4 * nM2; /* [12][nM2] */
+  face_u5(m, W->u, e, f, um);
+  face_S(m, gt, e, f, S);
+  mine_to_mortar(0, N, Mo, 5, um, uM);
+  mine_to_mortar(0, N, Mo, 3, S, SM);
+  if (nb >= 0) {
+    face_u5(m, W->u, nb, nf, tn);
+    nbr_to_mortar(0, Nn, Mo, o, 5, tn, uP);
+  } else {
+    cns_nbr_face(m, W->u, gt, e, f, uP); /* the ghost on my own face (Mo = N) */
+  }
+  if (LU) {
+    for (int p = 0; p < nM2; ++p) {
+      or_real qm[5], qp[5], pm[4], pp[4];
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = uM[v * nM2 + p];
+        qp[v] = uP[v * nM2 + p];
+      }
+      cns_phi(qm, m->p.gamma, pm);
+      cns_phi(qp, m->p.gamma, pp);
+      for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < 3; ++k) H[(c * 3 + k) * nM2 + p] = 0.5 * (pm[c] + pp[c]) * SM[k * nM2 + p];
+    }
+    mortar_to_mine(0, Mo, N, 12, H, LU);
+  }
+  int rc = 0;
+  if (LH) {
+    const int any_visc = m->flag[e] || (nb >= 0 && m->flag[nb]);
+    if (any_visc) {
+      cns_face_fv(W, e, f, fvm);
+      mine_to_mortar(0, N, Mo, 4, fvm, FvM);
+      if (nb >= 0) {
+        cns_face_fv(W, nb, nf, fvn);
+        nbr_to_mortar(0, Nn, Mo, o, 4, fvn, FvP);
+      } else {
+        /* inflow, outflow: the interior viscous flux. Adiabatic walls: the ghost's outward flux
+         * makes the BR1 average the interior traction (no-slip) or its normal part (free-slip,
+         * the reflection R = I - 2 n n^T of the traction), and a zero energy flux (no heat flux,
+         * no work by a traction on a resting or tangentially moving wall) */
+        const int tag = m->bc[e * 6 + f];
+        for (int p = 0; p < nM2; ++p) {
+          if (tag == 1 || tag == 2) {
+            for (int v = 0; v < 4; ++v) FvP[v * nM2 + p] = -FvM[v * nM2 + p];
+            continue;
+          }
+          const or_real Sv[3] = {SM[p], SM[nM2 + p], SM[2 * nM2 + p]};
+          const or_real ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
+          const or_real fn = (FvM[p] * Sv[0] + FvM[nM2 + p] * Sv[1] + FvM[2 * nM2 + p] * Sv[2]) / ss;
+          for (int c = 0; c < 3; ++c)
+            FvP[c * nM2 + p] = tag == 3 ? -FvM[c * nM2 + p] : FvM[c * nM2 + p] - 2.0 * fn * Sv[c];
+          FvP[3 * nM2 + p] = FvM[3 * nM2 + p];
+        }
+      }
+    }
+    /* F_v* . S = wm Fv^- . S - wp Fv^+ . S^+: the BR1 average, or the NS side alone on an
+     * Euler-NS face with the one-sided choice */
+    or_real wm = 0.5, wp = 0.5;
+    if (m->p.mixed_face == 1 && nb >= 0 && m->flag[e] != m->flag[nb]) {
+      wm = m->flag[e] ? 1.0 : 0.0;
+      wp = m->flag[e] ? 0.0 : 1.0;
+    }
+    for (int p = 0; p < nM2; ++p) {
+      const or_real Sv[3] = {SM[p], SM[nM2 + p], SM[2 * nM2 + p]};
+      const or_real s = SQRT(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+      const or_real nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+      or_real qm[5], qp[5], Fs[5];
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = uM[v * nM2 + p];
+        qp[v] = uP[v * nM2 + p];
+      }
+      if (or_cns_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
+      H[p] = Fs[0] * s;
+      for (int v = 0; v < 4; ++v) H[(1 + v) * nM2 + p] = Fs[1 + v] * s - (wm * FvM[v * nM2 + p] - wp * FvP[v * nM2 + p]);
+    }
+    mortar_to_mine(0, Mo, N, 5, H, LH);
+  }
+  free(buf);
+  return rc;
+}
+
 /* w J R = sum_d (w / w_{i_d}) sum_m w_m D_{m i_d} Ftil^d_m - w_face H*, five variables */
 static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
   const or_mesh* m = W->m;
@@ -1820,80 +1908,20 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
           }
           JR[v * n3 + ii + n * (jj + n * kk)] = s;
         }
-  /* faces: H* = F_e* . n |S| - F_v* . S with F_v* . S = wm Fv^- . S - wp Fv^+ . S^+ */
-  or_real* um = (or_real*)malloc(sizeof(or_real) * 5 * n2);
-  or_real* up = (or_real*)malloc(sizeof(or_real) * 5 * n2);
-  or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
-  or_real* Fvm = (or_real*)malloc(sizeof(or_real) * 4 * n2);
-  or_real* Fvp = (or_real*)malloc(sizeof(or_real) * 4 * n2);
-  or_real* tn = (or_real*)malloc(sizeof(or_real) * 4 * n2);
+  /* faces: the projected H* = F_e* . S - F_v* . S from each face's mortar */
+  or_real* LH = (or_real*)malloc(sizeof(or_real) * 5 * n2);
   int rc = 0;
   for (int f = 0; f < 6; ++f) {
-    const int64_t nb = m->nb_e[e * 6 + f];
-    face_u5(m, W->u, e, f, um);
-    cns_nbr_face(m, W->u, gt, e, f, up);
-    face_S(m, gt, e, f, S);
-    const int any_visc = m->flag[e] || (nb >= 0 && m->flag[nb]);
-    memset(Fvm, 0, sizeof(or_real) * 4 * n2);
-    memset(Fvp, 0, sizeof(or_real) * 4 * n2);
-    if (any_visc) {
-      cns_face_fv(W, e, f, Fvm);
-      if (nb >= 0) {
-        cns_face_fv(W, nb, m->nb_f[e * 6 + f], tn);
-        nbr_to_mortar(m->p.nodes, N, N, m->nb_o[e * 6 + f], 4, tn, Fvp);
-      } else {
-        /* adiabatic walls: the ghost's outward flux makes the BR1 average the interior traction
-         * (no-slip) or its normal part (free-slip, the reflection R = I - 2 n n^T of the traction),
-         * and a zero energy flux (no heat flux, no work by a traction on a resting or tangentially
-         * moving wall) */
-        const int tag = m->bc[e * 6 + f];
-        for (int p = 0; p < n2; ++p) {
-          if (tag == 1 || tag == 2) { /* inflow, outflow: the interior viscous flux */
-            for (int v = 0; v < 4; ++v) Fvp[v * n2 + p] = -Fvm[v * n2 + p];
-            continue;
-          }
-          const or_real Sv[3] = {S[p], S[n2 + p], S[2 * n2 + p]};
-          const or_real ss = Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2];
-          const or_real fn = (Fvm[p] * Sv[0] + Fvm[n2 + p] * Sv[1] + Fvm[2 * n2 + p] * Sv[2]) / ss;
-          for (int c = 0; c < 3; ++c)
-            Fvp[c * n2 + p] = tag == 3 ? -Fvm[c * n2 + p] : Fvm[c * n2 + p] - 2.0 * fn * Sv[c];
-          Fvp[3 * n2 + p] = Fvm[3 * n2 + p];
-        }
-      }
-    }
-    or_real wm = 0.5, wp = 0.5;
-    if (m->p.mixed_face == 1 && nb >= 0 && m->flag[e] != m->flag[nb]) {
-      wm = m->flag[e] ? 1.0 : 0.0;
-      wp = m->flag[e] ? 0.0 : 1.0;
-    }
+    if (cns_face_mortar(W, e, f, NULL, LH)) rc = -1;
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
-        const int fp = a + n * b;
-        const or_real Sv[3] = {S[fp], S[n2 + fp], S[2 * n2 + fp]};
-        const or_real s = SQRT(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
-        const or_real nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
-        or_real qm[5], qp[5], Fs[5];
-        for (int v = 0; v < 5; ++v) {
-          qm[v] = um[v * n2 + fp];
-          qp[v] = up[v * n2 + fp];
-        }
-        if (or_cns_riemann(qm, qp, nh, &m->p, Fs)) rc = -1;
         const int64_t p = face_node(f, N, a, b);
-        JR[p] -= Fs[0] * s / w[0];
-        for (int v = 0; v < 4; ++v) {
-          const or_real fv = wm * Fvm[v * n2 + fp] - wp * Fvp[v * n2 + fp];
-          JR[(1 + v) * n3 + p] -= (Fs[1 + v] * s - fv) / w[0];
-        }
+        for (int v = 0; v < 5; ++v) JR[v * n3 + p] -= LH[v * n2 + a + n * b] / w[0];
       }
   }
   for (int v = 0; v < 5; ++v)
     for (int p = 0; p < n3; ++p) R[v * T + o + p] = JR[v * n3 + p] / gt->J[p];
-  free(um);
-  free(up);
-  free(S);
-  free(Fvm);
-  free(Fvp);
-  free(tn);
+  free(LH);
   free(JR);
   free(Ft);
   return rc;
@@ -1918,10 +1946,6 @@ static int cns_check(const or_mesh* m) {
           return -1;
         }
         continue;
-      }
-      if (m->N[nb] != m->N[e]) {
-        set_err("compressible form: element %lld face %d is p-nonconforming", (long long)e, f);
-        return -1;
       }
     }
   return 0;
