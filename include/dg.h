@@ -111,14 +111,14 @@ typedef struct {
                        dynamic viscosity mu, eddy viscosity mu_t = rho nu_t of the closure,
                        heat flux kappa grad T with kappa = c_p (mu / Pr + mu_t / Pr_t),
                        c_p = gamma / (gamma - 1), BR1 on (v, T). Model 1 runs in FP64
-                       (precision 0) with the standard volume term (split 0) on meshes whose
-                       faces are conforming (both sides of one order) and whose boundary faces
+                       (precision 0) with the standard volume term (split 0), p-nonconforming
+                       faces through five-variable mortars, and boundary faces that
                        are far-field inflow (tag 1, the ghost is the state of inflow[] and
                        p_inf), pressure outflow (tag 2, interior density and velocity with
                        p_inf), both with the interior viscous flux, or adiabatic walls:
                        no-slip (tag 3, the mirror ghost (rho, -rho v, rho e), the interior
                        traction) or free-slip (tag 4, the normal momentum reversed, the normal
-                       traction), with no viscous energy flux at walls; other meshes give
+                       traction), with no viscous energy flux at walls; other settings give
                        DG_ERR_UNSUPPORTED. Its state, RK register
                        and residual arrays have 5 planes, [5][total_nodes].               */
   double inflow[4]; /* ghost state at inflow faces: model 0 uses the velocity part;

@@ -5,9 +5,11 @@
 // solve the Euler equations, flag 1 the Navier-Stokes equations with the eddy viscosity
 // mu_t = rho nu_t of the selected closure and the heat flux kappa grad T,
 // kappa = c_p (mu / Pr + mu_t / Pr_t), c_p = gamma / (gamma - 1). Conforming faces between
-// elements of one order (interior or periodic); boundary faces: far-field inflow and pressure
+// elements of one order (interior or periodic) node by node; p-nonconforming faces (Sec. 3.2)
+// on the mortar of the larger order (five-variable mortar kernels below: interpolated states
+// and viscous traces, L2 projection back); boundary faces: far-field inflow and pressure
 // outflow (ghost states, interior viscous flux), adiabatic walls (no-slip, free-slip: mirror
-// ghost states, no viscous energy flux). The host rejects p-nonconforming meshes.
+// ghost states, no viscous energy flux).
 //
 // Per residual evaluation / Runge-Kutta stage (the passes of the incompressible FP64 path with
 // five variables):
@@ -101,6 +103,150 @@ __device__ __forceinline__ void cns_fluct(const double uL[5], const double uR[5]
     const double lam = fmax(fabs(vnL) + sqrt(gamma * L.p / L.rho), fabs(vnR) + sqrt(gamma * R.p / R.rho));
 #pragma unroll
     for (int k = 0; k < 5; ++k) fx[k] = 0.5 * (dF[k] - lam * (uR[k] - uL[k]));
+  }
+}
+
+// F(u) . n of the Euler flux
+__device__ __forceinline__ void cns_normal_flux(const double u[5], const double nh[3], double gamma, double F[5]) {
+  const Prim P = prim(u, gamma);
+  const double vn = P.v[0] * nh[0] + P.v[1] * nh[1] + P.v[2] * nh[2];
+  F[0] = u[0] * vn;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) F[1 + c] = u[1 + c] * vn + P.p * nh[c];
+  F[4] = (u[4] + P.p) * vn;
+}
+
+// ---------------------------------------------------------------------------------------
+// mortars (p-nonconforming faces): one block of 64 threads per (element, face) slot
+// ---------------------------------------------------------------------------------------
+// sum_{aa, bb} T[a][aa] T[b][bb] src[aa + ns bb]: a 1D operator T (rows of NP) on both face
+// directions
+__device__ __forceinline__ double face_op(const double* T, int ns, int a, int b, const double* src) {
+  double s = 0.0;
+  for (int bb = 0; bb < ns; ++bb) {
+    double t = 0.0;
+    for (int aa = 0; aa < ns; ++aa) t += T[a * NP + aa] * src[aa + ns * bb];
+    s += T[b * NP + bb] * t;
+  }
+  return s;
+}
+
+struct CnsMortarSmem {
+  double mine[9][NP * NP];  // my face states (5) and outward viscous traces (4), my order
+  double nbr[9][NP * NP];   // the neighbour's, its order
+  double mM[9][NP * NP];    // mine on the mortar
+  double nM[9][NP * NP];    // the neighbour's on the mortar, in my face coordinates
+  double Sm[3][NP * NP];    // my outward face metric S, my order
+  double SM[3][NP * NP];    // S on the mortar
+  double H[12][NP * NP];    // mortar result
+};
+
+// my outward S at face node t and my (and the neighbour's) face planes [0, nv) (+5 viscous)
+__device__ __forceinline__ void cns_mortar_load(const DevMesh& M, int e, int f, const FaceLink& L, int nm, int nn,
+                                                bool visc_m, bool visc_n, int nplanes, CnsMortarSmem& sm) {
+  const int t = threadIdx.x, d = f >> 1;
+  const double sg = (f & 1) ? 1.0 : -1.0;
+  if (t < nm * nm) {
+    const int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
+    const bool cur = M.ec[e].curved != 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * (cur ? M.geo[(d * 3 + k) * M.total + node] : M.ec[e].Ja[d * 3 + k]);
+    const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
+    for (int v = 0; v < 5; ++v) sm.mine[v][t] = M.Tq[v * M.tr_total + s0];
+    for (int v = 5; v < nplanes; ++v) sm.mine[v][t] = visc_m ? M.Tv[(v - 5) * M.tr_total + s0] : 0.0;
+  }
+  if (t < nn * nn) {
+    const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
+    for (int v = 0; v < 5; ++v) sm.nbr[v][t] = M.Tq[v * M.tr_total + s1];
+    for (int v = 5; v < nplanes; ++v) sm.nbr[v][t] = visc_n ? M.Tv[(v - 5) * M.tr_total + s1] : 0.0;
+  }
+}
+
+// both sides' planes and my S interpolated to the mortar of order Mo
+__device__ __forceinline__ void cns_to_mortar(const DevMesh& M, const FaceLink& L, int Nm, int Nn, int Mo, int nplanes,
+                                              CnsMortarSmem& sm) {
+  const int t = threadIdx.x, nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
+  if (t < nM * nM) {
+    const int a = t % nM, b = t / nM;
+    const double* Im = M.interp + (Nm * NP + Mo) * NP * NP;
+    const double* In = M.interp + (Nn * NP + Mo) * NP * NP;
+    for (int v = 0; v < nplanes; ++v) sm.mM[v][t] = face_op(Im, nm, a, b, sm.mine[v]);
+    for (int k = 0; k < 3; ++k) sm.SM[k][t] = face_op(Im, nm, a, b, sm.Sm[k]);
+    int a0, b0;
+    fwd_orient(L.orient, Mo, a, b, a0, b0);  // (a, b) are the neighbour's mortar coordinates here
+    for (int v = 0; v < nplanes; ++v) sm.nM[v][a0 + nM * b0] = face_op(In, nn, a, b, sm.nbr[v]);
+  }
+}
+
+// BR1 lifting data of the NS elements' mortar faces: LU[c*3+k] = P(phi*_c S_k), phi = (v, T)
+__global__ void __launch_bounds__(64) k_mortar_lift_cns(DevMesh M, const int32_t* __restrict__ slots, int count) {
+  __shared__ CnsMortarSmem sm;
+  if (blockIdx.x >= count) return;
+  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
+  const FaceLink L = M.link[es];
+  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
+  const int nm = Nm + 1, nM = Mo + 1, t = threadIdx.x;
+  cns_mortar_load(M, e, f, L, nm, Nn + 1, false, false, 5, sm);
+  __syncthreads();
+  cns_to_mortar(M, L, Nm, Nn, Mo, 5, sm);
+  __syncthreads();
+  if (t < nM * nM) {
+    double um[5], up[5];
+    for (int v = 0; v < 5; ++v) {
+      um[v] = sm.mM[v][t];
+      up[v] = sm.nM[v][t];
+    }
+    const Prim A = prim(um, M.gamma), B = prim(up, M.gamma);
+    const double ps[4] = {0.5 * (A.v[0] + B.v[0]), 0.5 * (A.v[1] + B.v[1]), 0.5 * (A.v[2] + B.v[2]),
+                          0.5 * (A.p / A.rho + B.p / B.rho)};
+    for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < 3; ++k) sm.H[c * 3 + k][t] = ps[c] * sm.SM[k][t];
+  }
+  __syncthreads();
+  if (t < nm * nm) {
+    const double* P = M.proj + (Mo * NP + Nm) * NP * NP;
+    const int a = t % nm, b = t / nm;
+    for (int ck = 0; ck < 12; ++ck)
+      M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = face_op(P, nM, a, b, sm.H[ck]);
+  }
+}
+
+// total flux of every mortar face: LH[v] = P((F_e*(u-, u+) - F_v*) . S), my outward S
+__global__ void __launch_bounds__(64) k_mortar_flux_cns(DevMesh M, const int32_t* __restrict__ slots, int count) {
+  __shared__ CnsMortarSmem sm;
+  if (blockIdx.x >= count) return;
+  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
+  const FaceLink L = M.link[es];
+  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
+  const int nm = Nm + 1, nM = Mo + 1, t = threadIdx.x;
+  const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
+  cns_mortar_load(M, e, f, L, nm, Nn + 1, vm, vn, 9, sm);
+  __syncthreads();
+  cns_to_mortar(M, L, Nm, Nn, Mo, 9, sm);
+  __syncthreads();
+  if (t < nM * nM) {
+    const double Sv[3] = {sm.SM[0][t], sm.SM[1][t], sm.SM[2][t]};
+    const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+    const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+    double um[5], up[5], Fn[5], fx[5];
+    for (int v = 0; v < 5; ++v) {
+      um[v] = sm.mM[v][t];
+      up[v] = sm.nM[v][t];
+    }
+    cns_normal_flux(um, nh, M.gamma, Fn);
+    cns_fluct(um, up, nh, M.gamma, M.riemann, fx);
+    // F_v* . S = wm (mine) - wp (the neighbour's outward): the average, or the NS side alone
+    const bool one = M.mixed_face == 1 && vm != vn;
+    const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;
+    sm.H[0][t] = s * (Fn[0] + fx[0]);
+    for (int v = 0; v < 4; ++v) sm.H[1 + v][t] = s * (Fn[1 + v] + fx[1 + v]) - (wm * sm.mM[5 + v][t] - wp * sm.nM[5 + v][t]);
+  }
+  __syncthreads();
+  if (t < nm * nm) {
+    const double* P = M.proj + (Mo * NP + Nm) * NP * NP;
+    const int a = t % nm, b = t / nm;
+    for (int v = 0; v < 5; ++v)
+      M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = face_op(P, nM, a, b, sm.H[v]);
   }
 }
 
@@ -218,6 +364,14 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
       const FaceLink L = M.link[e * 6 + f];
       const double Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
+      if (L.kind == FK_MORTAR) {  // the projected phi* S from the mortar
+        const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) G[c][k] += invw * (M.LU[(c * 3 + k) * M.tr_total + ms] - ph[c] * Sv[k]);
+        continue;
+      }
       double jump[4];
       if (L.kind == FK_CONF) {
         int a1, b1;
@@ -240,7 +394,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       } else if (L.kind == FK_OUTFLOW) {  // interior velocity, T = p_inf / rho
         jump[0] = jump[1] = jump[2] = 0.0;
         jump[3] = M.p_inf / uu[0] - ph[3];
-      } else {  // the host admits conforming faces and boundary faces only
+      } else {  // no other face kind exists
         atomicCAS(&M.err[0], 0, 5);
         atomicCAS(&M.err[1], 0, 10);
         continue;
@@ -393,6 +547,19 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
     const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
     const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
+    if (L.kind == FK_MORTAR) {
+      // the projected (F_e* - F_v*) . S from the mortar minus the own outward flux (Euler, and
+      // viscous for NS elements)
+      double Fo[5];
+      cns_normal_flux(uu, nh, gamma, Fo);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double own = s * Fo[v];
+        if (v > 0 && ns) own -= M.Tv[(v - 1) * M.tr_total + ms];
+        JR[v] -= invw * (M.LH[v * M.tr_total + ms] - own);
+      }
+      continue;
+    }
     double up[5];  // the neighbour's face state, or the mirror ghost behind a wall
     int64_t nsl = 0;
     if (L.kind == FK_CONF) {
@@ -421,7 +588,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 #pragma unroll
       for (int c = 0; c < 3; ++c) up[1 + c] = uu[1 + c];
       up[4] = M.p_inf / (gamma - 1.0) + 0.5 * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0];
-    } else {  // the host admits conforming faces and boundary faces only
+    } else {  // no other face kind exists
       atomicCAS(&M.err[0], 0, 5);
       atomicCAS(&M.err[1], 0, 11);
       continue;
@@ -523,6 +690,18 @@ cudaError_t prepare_kernels_cns() {
   return prep_cns<7>();
 }
 
+
+cudaError_t launch_mortar_lift_cns(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_mortar_lift_cns<<<count, 64, 0, s>>>(M, slots, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mortar_flux_cns(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_mortar_flux_cns<<<count, 64, 0, s>>>(M, slots, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s) {
   if (b.count == 0) return cudaSuccess;

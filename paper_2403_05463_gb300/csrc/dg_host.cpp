@@ -777,20 +777,12 @@ dg_status rebuild_flags(dg_ctx* c) {
   return DG_OK;
 }
 
-// The compressible form is built for conforming faces only, and needs a far field at its
-// inflow and outflow faces.
+// The compressible form needs a far field at its inflow and outflow faces.
 dg_status check_model_mesh(const dg_ctx* c) {
   if (c->prm.model != 1) return DG_OK;
-  const char* what = "compressible form";
-  for (int64_t s = 0; s < c->ne * 6; ++s) {
-    if (c->nb[s] < 0 && c->prm.model == 1 && (c->bc[s] == 1 || c->bc[s] == 2) &&
-        !(c->prm.inflow[0] > 0.0 && c->prm.p_inf > 0.0))
-      return fail(DG_ERR_ARG, "%s: inflow/outflow faces need a far-field density inflow[0] > 0 and p_inf > 0", what);
-    if (c->nb[s] < 0) continue;
-    if (c->order[c->nb[s]] != c->order[s / 6])
-      return fail(DG_ERR_UNSUPPORTED, "%s: element %lld face %d is p-nonconforming", what, (long long)(s / 6),
-                  (int)(s % 6));
-  }
+  for (int64_t s = 0; s < c->ne * 6; ++s)
+    if (c->nb[s] < 0 && (c->bc[s] == 1 || c->bc[s] == 2) && !(c->prm.inflow[0] > 0.0 && c->prm.p_inf > 0.0))
+      return fail(DG_ERR_ARG, "compressible form: inflow/outflow faces need a far-field density inflow[0] > 0 and p_inf > 0");
   return DG_OK;
 }
 
@@ -918,8 +910,9 @@ dg_status rebuild_orders(dg_ctx* c) {
   for (int64_t s = 0; s < E * 6 && !has_mortar; ++s)
     has_mortar = c->nb[s] >= 0 && c->order[c->nb[s]] != c->order[s / 6];
   const int64_t mort = has_mortar ? c->tr_total : 0;
-  if ((st = dev_alloc(c, "LU", 9 * mort, &c->M.LU)) != DG_OK) return st;
-  if ((st = dev_alloc(c, "LH", 4 * mort, &c->M.LH)) != DG_OK) return st;
+  const int64_t lu_planes = c->prm.model == 1 ? 12 : 9;  // phi*_c S_k: phi = (v, T) or u
+  if ((st = dev_alloc(c, "LU", lu_planes * mort, &c->M.LU)) != DG_OK) return st;
+  if ((st = dev_alloc(c, "LH", (int64_t)nvar(c) * mort, &c->M.LH)) != DG_OK) return st;
   CU(cudaMemset(c->M.Tv, 0, sizeof(double) * nvv * std::max<int64_t>(c->tr_total, 1)));
   if ((st = dev_alloc(c, "partial", 5 * E, &c->partial)) != DG_OK) return st;
   c->partial_host.assign(5 * E, 0.0);
@@ -980,12 +973,18 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
     if (nlaunch) *nlaunch += nl;
     return DG_OK;
   }
-  if (M.model == 1) {  // compressible form: no mortar phases (conforming faces only)
+  if (M.model == 1) {  // compressible form: five-variable kernels and mortars
     if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
       for (const Bucket& b : c->ord_buckets) {
         CU(launch_traces_cns(M, b, q, s));
         ++nl;
       }
+    } else if (phase == 1 && c->n_mortar_ns) {
+      CU(launch_mortar_lift_cns(M, c->mortar_ns, c->n_mortar_ns, s));
+      ++nl;
+    } else if (phase == 3 && c->n_mortar_all) {
+      CU(launch_mortar_flux_cns(M, c->mortar_all, c->n_mortar_all, s));
+      ++nl;
     } else if (phase == 2) {
       for (const Bucket& b : c->ns_buckets) {
         CU(launch_viscous_cns(M, b, q, s));

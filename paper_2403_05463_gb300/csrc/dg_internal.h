@@ -71,7 +71,8 @@ struct DevMesh {
                              // [3][tr_total], or with precision 1 FP32 [tr_total][3]
   double* rv;                // [3][total]    J * viscous volume divergence (NS elements)
   double* LU;                // [9][tr_total] projected BR1 lifting u*_c S_k on mortar faces
-  double* LH;                // [4][tr_total] projected total flux (F_e* - F_v*) . S on mortars
+                             // (compressible: [12][tr_total], phi*_c S_k with phi = (v, T))
+  double* LH;                // [nvar][tr_total] projected total flux (F_e* - F_v*) . S on mortars
   const double* interp;      // [(Ns*NP+Nd)*NP*NP + i*NP + j]: Lagrange interpolation Ns -> Nd
   const double* proj;        // [(Nh*NP+Nl)*NP*NP + i*NP + j]: L2 projection Nh -> Nl
   int* err;                  // device error word
@@ -183,6 +184,8 @@ int tile_epb32(int N, int alt);
 // [4][tr_total] in Tv (momentum, energy), J r_v [4][total] in rv.
 cudaError_t upload_ops_cns(const Ops1D& ops);
 cudaError_t prepare_kernels_cns();
+cudaError_t launch_mortar_lift_cns(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
+cudaError_t launch_mortar_flux_cns(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s);
 cudaError_t launch_traces_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
 cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
 cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,

@@ -2,7 +2,8 @@
 oracle's compressible entry points: residuals, RK steps and conservation sums at the FP64
 tolerance 1e-12 (relative L2), on box, re-oriented curved and every order 1..7, mixed flags,
 Roe/LLF, Vreman/Smagorinsky, both mixed-face choices, far-field inflow / pressure outflow and
-adiabatic no-slip/free-slip walls; plus what the build rejects."""
+adiabatic no-slip/free-slip walls, p-nonconforming faces (orders 1..7); plus what the build
+rejects."""
 import dataclasses
 
 import numpy as np
@@ -126,7 +127,6 @@ def test_model_switch_on_an_existing_context():
 @pytest.mark.parametrize("wall", [3, 4])
 def test_adiabatic_walls(wall):
     # the wavy degree-2 channel between walls, re-oriented elements, mixed flags, one order
-    # (the compressible form needs conforming faces)
     w = wl.channel_walls(n=4, wall=wall)
     mesh, _ = wl.rotate_elements(w.mesh, 90 + wall)
     rng = np.random.default_rng(wall)
@@ -168,13 +168,6 @@ def test_what_the_compressible_build_rejects():
     assert dg.STATUS[ei.value.status] == "DG_ERR_ARG"
     w = _box(3)
     S = _solver(w)
-    # p-nonconforming faces
-    o = w.orders.copy()
-    o[0] = 4
-    with pytest.raises(dg.DGError) as ei:
-        S.set_orders(o)
-    assert dg.STATUS[ei.value.status] == "DG_ERR_UNSUPPORTED"
-    assert S.total_nodes == w.total_nodes  # the previous layout is kept
     # reduced precision, split form, bad gas constants
     for bad in (dict(precision=1), dict(split=1), dict(gamma=1.0)):
         with pytest.raises(dg.DGError):
@@ -186,6 +179,59 @@ def test_what_the_compressible_build_rejects():
         S.detect_regions(u, {"weights": [1, 1], "means": np.zeros((2, 3)), "covs": [np.eye(3)] * 2, "viscous": 1})
     with pytest.raises(dg.DGError):
         S.conservation_noalloc(u, torch.zeros(5, dtype=torch.float64, device="cuda"))
+
+
+def _mixed(w, seed, lo, hi):
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(w, orders=rng.integers(lo, hi + 1, size=w.n_elem).astype(np.int8))
+
+
+MORTAR_CASES = [
+    ("box_orders_1_7_vreman_roe", lambda: _mixed(_box(3, n=5), 60, 1, 7), {}),
+    ("curved_orders_2_6_smagorinsky_llf_onesided", lambda: _mixed(_curved_small(3, 61), 61, 2, 6),
+     dict(closure=0, riemann=1, mixed_face=1)),
+    ("curved_orders_2_5_all_ns", lambda: dataclasses.replace(_mixed(_curved_small(3, 62), 62, 2, 5),
+                                                              flags=np.ones(64, np.uint8)), dict(nu=1e-2)),
+]
+
+
+@pytest.mark.parametrize("name,make,extra", MORTAR_CASES, ids=[c[0] for c in MORTAR_CASES])
+def test_p_nonconforming_faces(name, make, extra):
+    """Five-variable mortars (Sec. 3.2): interpolated states and viscous traces, Roe/LLF and the
+    BR1 average of (v, T) on the mortar, L2 projection back, against the oracle at 1e-12."""
+    w = make()
+    p = dict(w.params, **extra)
+    M = _oracle(w, p)
+    u = _state(w, M)
+    R = _solver(w, p).residual(to_dev(u)).cpu().numpy()
+    assert rel_l2(R, M.cns_residual(u)) <= TOL
+
+
+def test_mortars_with_walls_rk_steps_and_order_changes():
+    # the wall channel with orders 2..5, RK steps against the oracle's, conservation of mass and
+    # energy through the walls, then new orders on the same context
+    w = wl.channel_walls(n=4, wall=3)
+    rng = np.random.default_rng(63)
+    w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8),
+                            orders=rng.integers(2, 6, size=w.n_elem).astype(np.int8),
+                            params=dict(wl.cns_tgv().params, nu=1e-2))
+    M = _oracle(w)
+    u = wl.cns_state(M.node_coords(), w.seed, period=2 * np.pi)
+    g = np.zeros_like(u)
+    S = _solver(w)
+    ud, gd = to_dev(u), to_dev(g)
+    S.rk_step(ud, gd, 1e-3, 3)
+    M.cns_rk_step(u, g, 1e-3, 3)
+    assert rel_l2(ud.cpu().numpy(), u) <= TOL
+    R = S.residual(ud)
+    sums = S.conservation(R)
+    scale = np.abs(R.cpu().numpy()).max()
+    assert abs(sums[0]) <= 1e-11 * scale and abs(sums[4]) <= 1e-11 * scale, sums
+    w2 = dataclasses.replace(w, orders=rng.integers(2, 8, size=w.n_elem).astype(np.int8))
+    S.set_orders(w2.orders)
+    M2 = _oracle(w2)
+    u2 = wl.cns_state(M2.node_coords(), w.seed, period=2 * np.pi)
+    assert rel_l2(S.residual(to_dev(u2)).cpu().numpy(), M2.cns_residual(u2)) <= TOL
 
 
 def test_a_32cube_case_sampled():
