@@ -1598,13 +1598,13 @@ static void cns_phi(const or_real u[5], or_real gamma, or_real phi[4]) {
   phi[3] = p / u[0];
 }
 
+/* the conservative state at the face points: the face nodes (Gauss-Lobatto) or the
+ * interpolation along the normal lines (Gauss-Legendre) */
 static void face_u5(const or_mesh* m, const or_real* u, int64_t e, int f, or_real* T /*[5][n2]*/) {
   int N = m->N[e], n = N + 1, n2 = n * n;
   for (int b = 0; b < n; ++b)
-    for (int a = 0; a < n; ++a) {
-      int64_t p = m->off[e] + face_node(f, N, a, b);
-      for (int v = 0; v < 5; ++v) T[v * n2 + a + n * b] = u[v * m->total + p];
-    }
+    for (int a = 0; a < n; ++a)
+      for (int v = 0; v < 5; ++v) T[v * n2 + a + n * b] = face_value(m, N, f, a, b, u + v * m->total + m->off[e]);
 }
 
 /* the neighbour's face state in my face coordinates (conforming faces: same order), or the ghost
@@ -1698,13 +1698,10 @@ static void cns_gradient(const cwork_t* W, int64_t e, or_real* G) {
           }
   or_real* LU = (or_real*)malloc(sizeof(or_real) * 12 * n2);
   for (int f = 0; f < 6; ++f) {
-    cns_face_mortar(W, e, f, LU, NULL); /* projected phi* S on my face nodes */
+    cns_face_mortar(W, e, f, LU, NULL); /* projected phi* S at my face points */
     for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        const int fp = a + n * b;
-        const int64_t p = face_node(f, N, a, b);
-        for (int ck = 0; ck < 12; ++ck) G[ck * n3 + p] += LU[ck * n2 + fp] / w[0];
-      }
+      for (int a = 0; a < n; ++a)
+        for (int ck = 0; ck < 12; ++ck) face_lift(m, N, f, a, b, LU[ck * n2 + a + n * b], G + ck * n3);
   }
   free(LU);
   free(phi);
@@ -1745,6 +1742,29 @@ static void cns_face_fv(const cwork_t* W, int64_t e, int f, or_real* out) {
     memset(out, 0, sizeof(or_real) * 4 * n2);
     return;
   }
+  if (m->p.nodes == 1) {
+    /* Gauss-Legendre: the outward contravariant viscous flux sigma Ja^d . Fv at every node,
+     * interpolated to the face */
+    const geo_t* gt = &W->geo[e];
+    const int d = f >> 1;
+    const or_real sg = (f & 1) ? 1.0 : -1.0;
+    or_real* Ft = (or_real*)malloc(sizeof(or_real) * 4 * n3);
+    for (int p = 0; p < n3; ++p) {
+      or_real uu[5], Fv[4][3];
+      for (int v = 0; v < 5; ++v) uu[v] = W->u[v * m->total + m->off[e] + p];
+      cns_visc_flux(W, e, n3, p, uu, Fv);
+      for (int v = 0; v < 4; ++v) {
+        or_real s = 0.0;
+        for (int k = 0; k < 3; ++k) s += Fv[v][k] * gt->Ja[(d * 3 + k) * n3 + p];
+        Ft[v * n3 + p] = sg * s;
+      }
+    }
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a)
+        for (int v = 0; v < 4; ++v) out[v * n2 + a + n * b] = face_value(m, N, f, a, b, Ft + v * n3);
+    free(Ft);
+    return;
+  }
   or_real* S = (or_real*)malloc(sizeof(or_real) * 3 * n2);
   face_S(m, &W->geo[e], e, f, S);
   for (int b = 0; b < n; ++b)
@@ -1774,7 +1794,7 @@ static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_r
   const int64_t nb = m->nb_e[e * 6 + f];
   const int Nn = nb >= 0 ? m->N[nb] : N, nn = Nn + 1, nn2 = nn * nn;
   const int Mo = N > Nn ? N : Nn, nM = Mo + 1, nM2 = nM * nM;
-  const int nf = m->nb_f[e * 6 + f], o = m->nb_o[e * 6 + f];
+  const int nf = m->nb_f[e * 6 + f], o = m->nb_o[e * 6 + f], gl = m->p.nodes;
   or_real* buf = (or_real*)calloc((size_t)(5 * n2 + 3 * n2 + 4 * n2 + 5 * nn2 + 4 * nn2) + (size_t)nM2 * (5 + 5 + 3 + 4 + 4 + 12),
                                   sizeof(or_real));
   or_real *um = buf, *S = um + 5 * n2, *fvm = S + 3 * n2, *tn = fvm + 4 * n2, *fvn = tn + 5 * nn2;
@@ -1782,11 +1802,11 @@ static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_r
   or_real* H = FvP + 4 * nM2; /* [12][nM2] */
   face_u5(m, W->u, e, f, um);
   face_S(m, gt, e, f, S);
-  mine_to_mortar(0, N, Mo, 5, um, uM);
-  mine_to_mortar(0, N, Mo, 3, S, SM);
+  mine_to_mortar(gl, N, Mo, 5, um, uM);
+  mine_to_mortar(gl, N, Mo, 3, S, SM);
   if (nb >= 0) {
     face_u5(m, W->u, nb, nf, tn);
-    nbr_to_mortar(0, Nn, Mo, o, 5, tn, uP);
+    nbr_to_mortar(gl, Nn, Mo, o, 5, tn, uP);
   } else {
     cns_nbr_face(m, W->u, gt, e, f, uP); /* the ghost on my own face (Mo = N) */
   }
@@ -1802,17 +1822,17 @@ static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_r
       for (int c = 0; c < 4; ++c)
         for (int k = 0; k < 3; ++k) H[(c * 3 + k) * nM2 + p] = 0.5 * (pm[c] + pp[c]) * SM[k * nM2 + p];
     }
-    mortar_to_mine(0, Mo, N, 12, H, LU);
+    mortar_to_mine(gl, Mo, N, 12, H, LU);
   }
   int rc = 0;
   if (LH) {
     const int any_visc = m->flag[e] || (nb >= 0 && m->flag[nb]);
     if (any_visc) {
       cns_face_fv(W, e, f, fvm);
-      mine_to_mortar(0, N, Mo, 4, fvm, FvM);
+      mine_to_mortar(gl, N, Mo, 4, fvm, FvM);
       if (nb >= 0) {
         cns_face_fv(W, nb, nf, fvn);
-        nbr_to_mortar(0, Nn, Mo, o, 4, fvn, FvP);
+        nbr_to_mortar(gl, Nn, Mo, o, 4, fvn, FvP);
       } else {
         /* inflow, outflow: the interior viscous flux. Adiabatic walls: the ghost's outward flux
          * makes the BR1 average the interior traction (no-slip) or its normal part (free-slip,
@@ -1853,7 +1873,7 @@ static int cns_face_mortar(const cwork_t* W, int64_t e, int f, or_real* LU, or_r
       H[p] = Fs[0] * s;
       for (int v = 0; v < 4; ++v) H[(1 + v) * nM2 + p] = Fs[1 + v] * s - (wm * FvM[v * nM2 + p] - wp * FvP[v * nM2 + p]);
     }
-    mortar_to_mine(0, Mo, N, 5, H, LH);
+    mortar_to_mine(gl, Mo, N, 5, H, LH);
   }
   free(buf);
   return rc;
@@ -1914,10 +1934,8 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
   for (int f = 0; f < 6; ++f) {
     if (cns_face_mortar(W, e, f, NULL, LH)) rc = -1;
     for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        const int64_t p = face_node(f, N, a, b);
-        for (int v = 0; v < 5; ++v) JR[v * n3 + p] -= LH[v * n2 + a + n * b] / w[0];
-      }
+      for (int a = 0; a < n; ++a)
+        for (int v = 0; v < 5; ++v) face_lift(m, N, f, a, b, -LH[v * n2 + a + n * b], JR + v * n3);
   }
   for (int v = 0; v < 5; ++v)
     for (int p = 0; p < n3; ++p) R[v * T + o + p] = JR[v * n3 + p] / gt->J[p];
@@ -1928,10 +1946,6 @@ static int cns_element_residual(const cwork_t* W, int64_t e, or_real* R) {
 }
 
 static int cns_check(const or_mesh* m) {
-  if (m->p.nodes != 0) {
-    set_err("compressible form: Gauss-Lobatto nodes only");
-    return -1;
-  }
   if (!(m->p.gamma > 1.0) || !(m->p.prandtl > 0.0) || !(m->p.prandtl_t > 0.0)) {
     set_err("compressible form: need gamma > 1 and positive Prandtl numbers");
     return -1;
