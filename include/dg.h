@@ -130,8 +130,8 @@ typedef struct {
                        Legendre (the paper's choice): the element's (N+1)^3 nodes are the
                        tensor Gauss points, face values, face metric terms and viscous
                        traces are interpolated along the normal lines and face terms lifted
-                       with l_i(+-1) / w_i. Nodes 1 runs the incompressible form (model 0)
-                       in FP64 (precision 0) with the standard volume term (split 0), with
+                       with l_i(+-1) / w_i. Nodes 1 runs either form (model 0 or 1) in FP64
+                       (precision 0) with the standard volume term (split 0), with
                        p-nonconforming faces (mortars interpolating and projecting between
                        the Gauss point sets) and the boundary faces' ghost states of the
                        Gauss-Lobatto path; other settings give

@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdgflag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_kernels_f32.cu", "dg_noalloc.cu", "dg_regions.cu", "dg_cns.cu", "dg_gl.cu"]
-HEADERS = ["dg_internal.h", "dg_device.cuh", os.path.join("..", "..", "include", "dg.h")]
+SOURCES = ["dg_host.cpp", "dg_kernels.cu", "dg_kernels_f32.cu", "dg_noalloc.cu", "dg_regions.cu", "dg_cns.cu", "dg_gl.cu", "dg_cns_gl.cu"]
+HEADERS = ["dg_internal.h", "dg_device.cuh", "dg_cns_phys.cuh", os.path.join("..", "..", "include", "dg.h")]
 
 
 def _nvcc():

@@ -24,6 +24,7 @@
 // by parts:
 //   J R = -sum_d D_d (Ftil_e^d - Ftil_v^d) - sum_faces (1/w_end) [(F_e* - F_v*) . S - (Ftil_e - Ftil_v)_out]
 #include "dg_device.cuh"
+#include "dg_cns_phys.cuh"
 
 namespace dgk {
 
@@ -39,81 +40,6 @@ cudaError_t upload_ops_cns(const Ops1D& ops) {
   double w0[NP];
   for (int N = 0; N < NP; ++N) w0[N] = ops.w[N][0];
   return cudaMemcpyToSymbol(c_w0c, w0, sizeof(w0));
-}
-
-struct Prim {
-  double rho, v[3], p;
-};
-
-__device__ __forceinline__ Prim prim(const double u[5], double gamma) {
-  Prim P;
-  P.rho = u[0];
-  const double ir = 1.0 / u[0];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) P.v[c] = u[1 + c] * ir;
-  P.p = (gamma - 1.0) * (u[4] - 0.5 * (u[1] * P.v[0] + u[2] * P.v[1] + u[3] * P.v[2]));
-  return P;
-}
-
-// Fluctuation F*(uL, uR) . n - F(uL) . n. Roe (riemann == 0) in wave-strength form with the
-// Roe averages (sqrt(rho)-weighted v and H, a^2 = (gamma - 1)(H - |v|^2/2)): the jump uR - uL
-// is split into two acoustic waves (vn -+ a), an entropy wave and the shear part (vn), each
-// weighted by |lambda|. LLF: the largest |vn| + a of the two sides.
-__device__ __forceinline__ void cns_fluct(const double uL[5], const double uR[5], const double nh[3], double gamma,
-                                          int riemann, double fx[5]) {
-  const Prim L = prim(uL, gamma), R = prim(uR, gamma);
-  const double vnL = L.v[0] * nh[0] + L.v[1] * nh[1] + L.v[2] * nh[2];
-  const double vnR = R.v[0] * nh[0] + R.v[1] * nh[1] + R.v[2] * nh[2];
-  double dF[5];  // F(uR).n - F(uL).n
-  dF[0] = uR[0] * vnR - uL[0] * vnL;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dF[1 + c] = (uR[1 + c] * vnR + R.p * nh[c]) - (uL[1 + c] * vnL + L.p * nh[c]);
-  dF[4] = (uR[4] + R.p) * vnR - (uL[4] + L.p) * vnL;
-  if (riemann == 0) {
-    const double sL = sqrt(L.rho), sR = sqrt(R.rho), inv = 1.0 / (sL + sR);
-    const double HL = (uL[4] + L.p) / L.rho, HR = (uR[4] + R.p) / R.rho;
-    double v[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = (sL * L.v[c] + sR * R.v[c]) * inv;
-    const double H = (sL * HL + sR * HR) * inv;
-    const double q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const double a2 = (gamma - 1.0) * (H - 0.5 * q2), a = sqrt(a2);
-    const double vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
-    const double rho = sL * sR;
-    const double dr = R.rho - L.rho, dp = R.p - L.p;
-    double dv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dv[c] = R.v[c] - L.v[c];
-    const double dvn = dv[0] * nh[0] + dv[1] * nh[1] + dv[2] * nh[2];
-    const double al1 = (dp - rho * a * dvn) / (2.0 * a2);  // acoustic, vn - a
-    const double al5 = (dp + rho * a * dvn) / (2.0 * a2);  // acoustic, vn + a
-    const double al2 = dr - dp / a2;                       // entropy, vn
-    const double l1 = fabs(vn - a), l2 = fabs(vn), l5 = fabs(vn + a);
-    const double w1 = l1 * al1, w5 = l5 * al5;
-    double d[5];
-    d[0] = w1 + l2 * al2 + w5;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      d[1 + c] = w1 * (v[c] - a * nh[c]) + l2 * (al2 * v[c] + rho * (dv[c] - dvn * nh[c])) + w5 * (v[c] + a * nh[c]);
-    const double vdv = v[0] * dv[0] + v[1] * dv[1] + v[2] * dv[2];
-    d[4] = w1 * (H - a * vn) + l2 * (al2 * 0.5 * q2 + rho * (vdv - vn * dvn)) + w5 * (H + a * vn);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) fx[k] = 0.5 * (dF[k] - d[k]);
-  } else {
-    const double lam = fmax(fabs(vnL) + sqrt(gamma * L.p / L.rho), fabs(vnR) + sqrt(gamma * R.p / R.rho));
-#pragma unroll
-    for (int k = 0; k < 5; ++k) fx[k] = 0.5 * (dF[k] - lam * (uR[k] - uL[k]));
-  }
-}
-
-// F(u) . n of the Euler flux
-__device__ __forceinline__ void cns_normal_flux(const double u[5], const double nh[3], double gamma, double F[5]) {
-  const Prim P = prim(u, gamma);
-  const double vn = P.v[0] * nh[0] + P.v[1] * nh[1] + P.v[2] * nh[2];
-  F[0] = u[0] * vn;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) F[1 + c] = u[1 + c] * vn + P.p * nh[c];
-  F[4] = (u[4] + P.p) * vn;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -147,10 +73,20 @@ __device__ __forceinline__ void cns_mortar_load(const DevMesh& M, int e, int f, 
   const int t = threadIdx.x, d = f >> 1;
   const double sg = (f & 1) ? 1.0 : -1.0;
   if (t < nm * nm) {
-    const int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
     const bool cur = M.ec[e].curved != 0.0;
+    if (M.nodes == 1 && cur) {  // Gauss-Legendre: the interpolant of Ja^d along the normal line
+      const double* l = M.lb_g + ((nm - 1) * 2 + (f & 1)) * NP;
+      double Sk[3] = {0.0, 0.0, 0.0};
+      for (int i = 0; i < nm; ++i) {
+        const int64_t node = M.elem_off[e] + line_node(f, nm, t % nm, t / nm, i);
+        for (int k = 0; k < 3; ++k) Sk[k] += l[i] * M.geo[(d * 3 + k) * M.total + node];
+      }
+      for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * Sk[k];
+    } else {
+      const int64_t node = M.elem_off[e] + face_node(f, nm, t % nm, t / nm);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * (cur ? M.geo[(d * 3 + k) * M.total + node] : M.ec[e].Ja[d * 3 + k]);
+      for (int k = 0; k < 3; ++k) sm.Sm[k][t] = sg * (cur ? M.geo[(d * 3 + k) * M.total + node] : M.ec[e].Ja[d * 3 + k]);
+    }
     const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
     for (int v = 0; v < 5; ++v) sm.mine[v][t] = M.Tq[v * M.tr_total + s0];
     for (int v = 5; v < nplanes; ++v) sm.mine[v][t] = visc_m ? M.Tv[(v - 5) * M.tr_total + s0] : 0.0;
@@ -168,8 +104,9 @@ __device__ __forceinline__ void cns_to_mortar(const DevMesh& M, const FaceLink& 
   const int t = threadIdx.x, nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
   if (t < nM * nM) {
     const int a = t % nM, b = t / nM;
-    const double* Im = M.interp + (Nm * NP + Mo) * NP * NP;
-    const double* In = M.interp + (Nn * NP + Mo) * NP * NP;
+    const double* I = M.nodes == 1 ? M.interp_g : M.interp;  // the node set's tables
+    const double* Im = I + (Nm * NP + Mo) * NP * NP;
+    const double* In = I + (Nn * NP + Mo) * NP * NP;
     for (int v = 0; v < nplanes; ++v) sm.mM[v][t] = face_op(Im, nm, a, b, sm.mine[v]);
     for (int k = 0; k < 3; ++k) sm.SM[k][t] = face_op(Im, nm, a, b, sm.Sm[k]);
     int a0, b0;
@@ -204,7 +141,7 @@ __global__ void __launch_bounds__(64) k_mortar_lift_cns(DevMesh M, const int32_t
   }
   __syncthreads();
   if (t < nm * nm) {
-    const double* P = M.proj + (Mo * NP + Nm) * NP * NP;
+    const double* P = (M.nodes == 1 ? M.proj_g : M.proj) + (Mo * NP + Nm) * NP * NP;
     const int a = t % nm, b = t / nm;
     for (int ck = 0; ck < 12; ++ck)
       M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = face_op(P, nM, a, b, sm.H[ck]);
@@ -243,7 +180,7 @@ __global__ void __launch_bounds__(64) k_mortar_flux_cns(DevMesh M, const int32_t
   }
   __syncthreads();
   if (t < nm * nm) {
-    const double* P = M.proj + (Mo * NP + Nm) * NP * NP;
+    const double* P = (M.nodes == 1 ? M.proj_g : M.proj) + (Mo * NP + Nm) * NP * NP;
     const int a = t % nm, b = t / nm;
     for (int v = 0; v < 5; ++v)
       M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = face_op(P, nM, a, b, sm.H[v]);

@@ -403,9 +403,8 @@ dg_status check_params(const dg_params* p) {
   if (p->model < 0 || p->model > 1) return fail(DG_ERR_ARG, "model must be 0 or 1");
   if (p->nodes < 0 || p->nodes > 1) return fail(DG_ERR_ARG, "nodes must be 0 or 1");
   if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
-  if (p->nodes == 1 && (p->model != 0 || p->precision != 0 || p->split != 0))
-    return fail(DG_ERR_UNSUPPORTED, "Gauss-Legendre nodes run the incompressible form in FP64 with the standard "
-                "volume term only");
+  if (p->nodes == 1 && (p->precision != 0 || p->split != 0))
+    return fail(DG_ERR_UNSUPPORTED, "Gauss-Legendre nodes run in FP64 with the standard volume term only");
   if (p->model == 1) {
     if (p->precision != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form runs in FP64 (precision 0) only");
     if (p->split != 0) return fail(DG_ERR_UNSUPPORTED, "the compressible form has the standard volume term only");
@@ -947,6 +946,32 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
   const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
+  if (M.nodes == 1 && M.model == 1) {  // compressible form on Gauss-Legendre nodes
+    if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
+      for (const Bucket& b : c->ord_buckets) {
+        CU(launch_traces_cns_gl(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 1 && c->n_mortar_ns) {
+      CU(launch_mortar_lift_cns(M, c->mortar_ns, c->n_mortar_ns, s));
+      ++nl;
+    } else if (phase == 3 && c->n_mortar_all) {
+      CU(launch_mortar_flux_cns(M, c->mortar_all, c->n_mortar_all, s));
+      ++nl;
+    } else if (phase == 2) {
+      for (const Bucket& b : c->ns_buckets) {
+        CU(launch_viscous_cns_gl(M, b, q, s));
+        ++nl;
+      }
+    } else if (phase == 4) {
+      for (const Bucket& b : c->all_buckets) {
+        CU(launch_inviscid_cns_gl(M, b, q, out, g, mode, stage, dt, write_tr, s));
+        ++nl;
+      }
+    }
+    if (nlaunch) *nlaunch += nl;
+    return DG_OK;
+  }
   if (M.nodes == 1) {  // Gauss-Legendre nodes: the mortar kernels take the Gauss-point tables
     if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
       for (const Bucket& b : c->ord_buckets) {

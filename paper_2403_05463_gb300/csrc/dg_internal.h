@@ -191,6 +191,15 @@ cudaError_t launch_viscous_cns(const DevMesh& M, const Bucket& b, const double* 
 cudaError_t launch_inviscid_cns(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
                                 int mode, int stage, double dt, int write_tr, cudaStream_t s);
 
+// Compressible form on Gauss-Legendre element nodes (dg_cns_gl.cu), FP64: the buffers of the
+// compressible form, with the face values and viscous traces interpolated to the face points.
+cudaError_t upload_ops_cns_gl(const Ops1D& ops);
+cudaError_t prepare_kernels_cns_gl();
+cudaError_t launch_traces_cns_gl(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
+cudaError_t launch_viscous_cns_gl(const DevMesh& M, const Bucket& b, const double* u, cudaStream_t s);
+cudaError_t launch_inviscid_cns_gl(const DevMesh& M, const Bucket& b, const double* u, double* out, double* g,
+                                   int mode, int stage, double dt, int write_tr, cudaStream_t s);
+
 // Gauss-Legendre element nodes (dg_gl.cu), FP64, incompressible form: traces are the face values
 // interpolated along the normal lines; face terms are lifted with l_i(+-1) / w_i.
 cudaError_t upload_ops_gl(const Ops1D& ops);

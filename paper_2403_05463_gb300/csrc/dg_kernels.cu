@@ -742,6 +742,7 @@ cudaError_t upload_ops(const Ops1D& ops) {
   cudaError_t r = cudaMemcpyToSymbol(c_ops, &ops, sizeof(Ops1D));
   if (r == cudaSuccess) r = upload_ops_cns(ops);
   if (r == cudaSuccess) r = upload_ops_gl(ops);
+  if (r == cudaSuccess) r = upload_ops_cns_gl(ops);
   return r == cudaSuccess ? upload_ops32(ops) : r;
 }
 
@@ -784,6 +785,7 @@ cudaError_t prepare_kernels() {
   if ((r = prep_n<7>()) != cudaSuccess) return r;
   if ((r = prepare_kernels_cns()) != cudaSuccess) return r;
   if ((r = prepare_kernels_gl()) != cudaSuccess) return r;
+  if ((r = prepare_kernels_cns_gl()) != cudaSuccess) return r;
   return prepare_kernels32();
 }
 

@@ -2,8 +2,8 @@
 oracle's compressible entry points: residuals, RK steps and conservation sums at the FP64
 tolerance 1e-12 (relative L2), on box, re-oriented curved and every order 1..7, mixed flags,
 Roe/LLF, Vreman/Smagorinsky, both mixed-face choices, far-field inflow / pressure outflow and
-adiabatic no-slip/free-slip walls, p-nonconforming faces (orders 1..7); plus what the build
-rejects."""
+adiabatic no-slip/free-slip walls, p-nonconforming faces (orders 1..7), and all of these on the
+Gauss-Legendre nodes too; plus what the build rejects."""
 import dataclasses
 
 import numpy as np
@@ -232,6 +232,63 @@ def test_mortars_with_walls_rk_steps_and_order_changes():
     M2 = _oracle(w2)
     u2 = wl.cns_state(M2.node_coords(), w.seed, period=2 * np.pi)
     assert rel_l2(S.residual(to_dev(u2)).cpu().numpy(), M2.cns_residual(u2)) <= TOL
+
+
+GL_CASES = [
+    ("box_n3", lambda: _box(3), {}),
+    ("box_n1_llf_onesided", lambda: _box(1, n=5), dict(riemann=1, mixed_face=1, closure=0)),
+    ("curved_n5", lambda: _curved_small(5, 70), {}),
+    ("curved_n7_all_ns", lambda: dataclasses.replace(_curved_small(7, 71), flags=np.ones(64, np.uint8)), dict(nu=1e-2)),
+    ("curved_orders_2_6_mortars", lambda: _mixed(_curved_small(3, 72), 72, 2, 6), {}),
+    ("box_orders_1_7_mortars_smagorinsky", lambda: _mixed(_box(3, n=5), 73, 1, 7), dict(closure=0)),
+]
+
+
+@pytest.mark.parametrize("name,make,extra", GL_CASES, ids=[c[0] for c in GL_CASES])
+def test_gauss_legendre_nodes(name, make, extra):
+    """The compressible form on the Gauss-Legendre points (App. A on App. B's nodes): interpolated
+    face states and viscous traces, l_i(+-1)/w_i lifting, Gauss-point mortars; against the oracle
+    on the same node set at 1e-12."""
+    w = make()
+    p = dict(w.params, nodes=1, **extra)
+    M = _oracle(w, p)
+    u = _state(w, M)
+    S = _solver(w, p)
+    np.testing.assert_allclose(S.node_coords().cpu().numpy(), M.node_coords(), atol=1e-13)
+    R = S.residual(to_dev(u)).cpu().numpy()
+    assert rel_l2(R, M.cns_residual(u)) <= TOL
+
+
+def test_gauss_legendre_boundaries_rk_steps_and_conservation():
+    # walls (no-slip, free-slip) with mixed orders, the far-field wake box, then RK steps and the
+    # conservation sums with the Gauss weights
+    for wall in (3, 4):
+        w = wl.channel_walls(n=4, wall=wall)
+        rng = np.random.default_rng(80 + wall)
+        w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8),
+                                orders=rng.integers(2, 6, size=w.n_elem).astype(np.int8),
+                                params=dict(wl.cns_tgv().params, nu=1e-2, nodes=1))
+        M = _oracle(w)
+        u = wl.cns_state(M.node_coords(), w.seed, period=2 * np.pi)
+        S = _solver(w)
+        R = S.residual(to_dev(u)).cpu().numpy()
+        assert rel_l2(R, M.cns_residual(u)) <= TOL, wall
+        sums = S.conservation(to_dev(R))
+        assert abs(sums[0]) <= 1e-11 * np.abs(R).max() and abs(sums[4]) <= 1e-11 * np.abs(R).max(), sums
+    w = wl.wake_16x16x16_n4(n=5, order=3)
+    rng = np.random.default_rng(82)
+    w = dataclasses.replace(w, flags=(rng.uniform(size=w.n_elem) < 0.5).astype(np.uint8),
+                            params=dict(wl.cns_tgv().params, nu=1e-2, inflow=(1.05, 0.6, 0.0, 0.05), p_inf=16.0,
+                                        nodes=1))
+    M = _oracle(w)
+    u = wl.cns_state(M.node_coords(), w.seed, period=4.0)
+    S = _solver(w)
+    assert rel_l2(S.residual(to_dev(u)).cpu().numpy(), M.cns_residual(u)) <= TOL
+    g = np.zeros_like(u)
+    ud, gd = to_dev(u), to_dev(g)
+    S.rk_step(ud, gd, 1e-3, 3)
+    M.cns_rk_step(u, g, 1e-3, 3)
+    assert rel_l2(ud.cpu().numpy(), u) <= TOL
 
 
 def test_a_32cube_case_sampled():

@@ -126,7 +126,7 @@ def test_what_gauss_legendre_refuses():
     w = _box(3)
     p = _gl(w)
     S = _solver(w, p)
-    for bad, prec in ((dict(split=1), 0), (dict(model=1), 0), ({}, 1)):
+    for bad, prec in ((dict(split=1), 0), ({}, 1)):
         with pytest.raises(dg.DGError):
             S.set_params(dict(p, **bad), precision=prec)
     S.set_params(p, precision=0)
