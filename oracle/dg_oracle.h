@@ -15,7 +15,7 @@
  *     Read here in artificial-compressibility form with rho = 1, state q = (p, u, v, w).
  *   - App. B, Eqs. NS2-NS5: DGSEM on curvilinear hexahedra, weak form with the
  *     convective numerical flux on element faces, tensor-product Gauss quadrature
- *     (Gauss-Lobatto nodes here).
+ *     (Gauss-Lobatto nodes, or the paper's Gauss-Legendre nodes with params.nodes = 1).
  *   - Sec. 2.3 (last paragraph): low-storage explicit third-order Runge-Kutta.
  *
  * Layout: q and R are SoA [4][total_nodes]; element e occupies nodes
@@ -60,8 +60,8 @@ typedef struct {
   int nodes;        /* element nodes and quadrature: 0 Gauss-Lobatto, 1 Gauss-Legendre
                        (the paper's choice, App. B): face values, face metric terms and
                        face fluxes are interpolated from the element's nodes and face terms
-                       are lifted with l_i(+-1) / w_i; p-nonconforming faces and the split
-                       form need Gauss-Lobatto                                     */
+                       are lifted with l_i(+-1) / w_i; the split form needs
+                       Gauss-Lobatto                                               */
   or_real p_inf;     /* compressible form: far-field pressure at inflow (with the far-field
                        (rho, u, v, w) in inflow[]) and static pressure at outflow     */
 } or_params;
@@ -121,8 +121,9 @@ int or_conservation(const or_mesh* m, const or_real* R, or_real out[4]);
  * riemann, mixed_face). Flag 0 elements solve the Euler equations, flag 1 the Navier-Stokes
  * equations with the eddy viscosity mu_t = rho nu_t of the selected closure; heat flux
  * kappa grad T with kappa = c_p (mu / Pr + mu_t / Pr_t). BR1 lifts the primitive
- * (v1, v2, v3, T). Conforming faces and interior/periodic faces only: a boundary tag or a
- * p-nonconforming face makes these calls fail. */
+ * (v1, v2, v3, T). p-nonconforming faces through five-variable mortars; boundary faces:
+ * far-field inflow (tag 1) and pressure outflow (tag 2), which need inflow[0] > 0 and
+ * p_inf > 0, and adiabatic no-slip (3) and free-slip (4) walls. Either node set. */
 void or_cns_flux(const or_real u[5], const or_real n_hat[3], or_real gamma, or_real out[5]);
 void or_cns_jacobian(const or_real u[5], const or_real n_hat[3], or_real gamma, or_real A[25]);
 /* Roe matrix |A(u_roe)| = R |Lambda| R^-1 at the Roe average of uL, uR */
