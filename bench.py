@@ -16,6 +16,7 @@ sample of the same workload, in the same metric.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -47,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip comparison, e2e and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (smaller profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--nodes", type=int, default=None, choices=[0, 1],
+                    help="element nodes: 0 Gauss-Lobatto, 1 Gauss-Legendre (default: the workload's)")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read, then rewritten)")
     return ap.parse_args()
 
@@ -368,6 +371,8 @@ def main():
 
     world, rank, local = dist_setup()
     w = wl.WORKLOADS[args.workload]() if args.n is None else wl.WORKLOADS[args.workload](n=args.n)
+    if args.nodes is not None:
+        w = dataclasses.replace(w, params=dict(w.params, nodes=args.nodes))
     S = dg.Solver.from_workload(w, precision=args.precision, device=local)
     # launch shapes per (order, geometry) timed on this GPU and mesh before the timed region
     tuning = "default" if args.no_autotune else S.autotune(args.tune_cache)
