@@ -9,8 +9,10 @@
 //   viscous  (NS elements): BR1 gradient of phi = (v, T), J G = sum_d D_d (Ja^d phi)
 //              + sum_faces l_i/w_i (phi* S - sigma (Ja^d phi)_face), phi* = {{phi}} of the face
 //              states (interpolated own state, the neighbour's trace or the boundary ghost) or
-//              the projected mortar value; eddy viscosity, stress, heat flux, contravariant
-//              viscous flux, its divergence J r_v and the outward traces sigma (Ja^d . Fv)_face;
+//              the projected mortar value (the face terms evaluated once per face point in
+//              shared memory, then lifted onto every node); eddy viscosity, stress, heat flux,
+//              contravariant viscous flux, its divergence J r_v and the outward traces
+//              sigma (Ja^d . Fv)_face;
 //   inviscid (all elements): J R = -sum_d D_d Ftil^d - sum_faces l_i/w_i [(F_e* - F_v*) . S
 //              - sigma (Ftil_e - Ftil_v)_face] + J r_v, Roe/LLF on the interpolated states, the
 //              RK update and the interpolated next-stage traces.
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   double* sP = sU + EPB * 5 * n3;                  // EPB * 4 * n3: phi = (v, T)
   double* sJa = sP + EPB * 4 * n3;                 // EPB * 9 * n3 (curved only)
   double* sF = sJa + (CURVED ? EPB * 9 * n3 : 0);  // EPB * 12 * n3: Ftil_v[d][4]
+  double* sT = sF + EPB * 12 * n3;                 // EPB * 72 * n2: face terms [f*n2+ab][c*3+k]
   const int tid = threadIdx.x;
   for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_Dgc[N][t];
   int le = tid / n3;
@@ -125,6 +128,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   double* P = sP + le * 4 * n3;
   double* JA = sJa + le * 9 * n3;
   double* F = sF + le * 12 * n3;
+  double* TG = sT + le * 72 * n2;
   const double gamma = M.gamma;
   double Ja[9], invJ = 0.0, uu[5] = {1.0, 0.0, 0.0, 0.0, 1.0}, ph[4] = {0.0, 0.0, 0.0, 0.0};
   if (active) {
@@ -152,12 +156,12 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   __syncthreads();
   const int ii[3] = {p % n, (p / n) % n, p / n2};
   const int str[3] = {1, n, n2};
+  double G[4][3];  // G[c][k] = d phi_c / d x_k
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[c][k] = 0.0;
   if (active) {
-    double G[4][3];  // G[c][k] = d phi_c / d x_k
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) G[c][k] = 0.0;
     // volume part: J G_ck = sum_d D_d (Ja^d_k phi_c)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -174,81 +178,89 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         }
       }
     }
-    // lifting from both faces of every direction: l_i / w_i (phi* S - sigma (Ja^d phi)_face)
+    // face phase, one item per face point of the element's 6 n^2:
+    // TG = phi* S - sigma (Ja^d phi)_face, S outward (the mortar's projected phi* S there)
+    for (int t = p; t < 6 * n2; t += n3) {
+      const int f = t / n2, ab = t % n2, a = ab % n, b = ab / n, d = f >> 1;
+      const double* l = c_lbc[N][f & 1];
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      const FaceLink L = M.link[e * 6 + f];
+      double uf[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, Sv[3] = {0.0, 0.0, 0.0}, JP[4][3];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) JP[c][k] = 0.0;
+      double pf[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const int pm = line_node(f, n, a, b, m);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) uf[v] += l[m] * U[v * n3 + pm];
+        if (CURVED) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double jk = JA[(d * 3 + k) * n3 + pm];
+            Sv[k] += l[m] * jk;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) JP[c][k] += l[m] * jk * P[c * n3 + pm];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pf[c] += l[m] * P[c * n3 + pm];
+        }
+      }
+      if (!CURVED) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          Sv[k] = M.ec[e].Ja[d * 3 + k];  // d varies at run time here
+#pragma unroll
+          for (int c = 0; c < 4; ++c) JP[c][k] = Sv[k] * pf[c];
+        }
+      }
+      double* tg = TG + t * 12;
+      if (L.kind == FK_MORTAR) {
+        const int64_t ms = M.tr_off[e] + t;
+#pragma unroll
+        for (int ck = 0; ck < 12; ++ck) tg[ck] = M.LU[ck * M.tr_total + ms] - sg * JP[ck / 3][ck % 3];
+        continue;
+      }
+      const double So[3] = {sg * Sv[0], sg * Sv[1], sg * Sv[2]};
+      double up[5];  // the neighbour's face state, or the ghost's behind a boundary face
+      if (L.kind == FK_CONF) {
+        int a1, b1;
+        inv_orient(L.orient, N, a, b, a1, b1);
+        const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) up[v] = M.Tq[v * M.tr_total + ns];
+      } else {
+        cns_ghost(M, L.kind, uf, So, up);
+      }
+      double pm_[4], pp_[4];
+      phi_of(uf, gamma, pm_);
+      phi_of(up, gamma, pp_);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double ps = 0.5 * (pm_[c] + pp_[c]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tg[c * 3 + k] = sg * (ps * Sv[k] - JP[c][k]);
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // lifting from both faces of every direction: l_i(+-1) / w_i times the face term
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int a, b;
       face_ab(d, ii, a, b);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const int f = 2 * d + s;
-        const double sg = s ? 1.0 : -1.0;
-        const FaceLink L = M.link[e * 6 + f];
-        const double* l = c_lbc[N][s];
-        const double cf = l[ii[d]] / c_wgc[N][ii[d]];
-        double uf[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, Sv[3] = {0.0, 0.0, 0.0}, JP[4][3];
+        const double cf = c_lbc[N][s][ii[d]] / c_wgc[N][ii[d]];
+        const double* tg = TG + ((2 * d + s) * n2 + a + n * b) * 12;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) JP[c][k] = 0.0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          const int pm = line_node(f, n, a, b, m);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) uf[v] += l[m] * U[v * n3 + pm];
-          if (CURVED) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const double jk = JA[(d * 3 + k) * n3 + pm];
-              Sv[k] += l[m] * jk;
-#pragma unroll
-              for (int c = 0; c < 4; ++c) JP[c][k] += l[m] * jk * P[c * n3 + pm];
-            }
-          }
-        }
-        if (!CURVED) {
-          double pf[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const int pm = line_node(f, n, a, b, m);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) pf[c] += l[m] * P[c * n3 + pm];
-          }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            Sv[k] = Ja[d * 3 + k];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) JP[c][k] = Ja[d * 3 + k] * pf[c];
-          }
-        }
-        if (L.kind == FK_MORTAR) {  // phi*_c S_k projected from the mortar, S outward
-          const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) G[c][k] += cf * (M.LU[(c * 3 + k) * M.tr_total + ms] - sg * JP[c][k]);
-          continue;
-        }
-        const double So[3] = {sg * Sv[0], sg * Sv[1], sg * Sv[2]};
-        double up[5];  // the neighbour's face state, or the ghost's behind a boundary face
-        if (L.kind == FK_CONF) {
-          int a1, b1;
-          inv_orient(L.orient, N, a, b, a1, b1);
-          const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) up[v] = M.Tq[v * M.tr_total + ns];
-        } else {
-          cns_ghost(M, L.kind, uf, So, up);
-        }
-        double pm_[4], pp_[4];
-        phi_of(uf, gamma, pm_);
-        phi_of(up, gamma, pp_);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const double ps = 0.5 * (pm_[c] + pp_[c]);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) G[c][k] += cf * sg * (ps * Sv[k] - JP[c][k]);
-        }
+          for (int k = 0; k < 3; ++k) G[c][k] += cf * tg[c * 3 + k];
       }
     }
 #pragma unroll
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 // ---------------------------------------------------------------------------------------
 template <int N, bool C>
 static size_t visc_smem_cns_gl() {
-  return sizeof(double) * (NP * NP + Shape<N>::EPB * (5 + 4 + (C ? 9 : 0) + 12) * Shape<N>::n3);
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * ((5 + 4 + (C ? 9 : 0) + 12) * Shape<N>::n3 + 72 * Shape<N>::n2));
 }
 
 template <int N>

@@ -7,7 +7,8 @@
 //   traces   : q at the face points, sum_i l_i(+-1) q_i, for the neighbours;
 //   viscous  (NS elements): BR1 gradient J G = sum_d D_d (Ja^d u) + sum_faces l_i/w_i
 //              (u* S - sigma (Ja^d u)_face), u* = ({u}_face + u_nbr)/2, S the interpolated face
-//              metric; eddy viscosity, stress, contravariant viscous flux, its divergence J r_v
+//              metric (the face terms evaluated once per face point in shared memory, then
+//              lifted onto every node); eddy viscosity, stress, contravariant viscous flux, its divergence J r_v
 //              and the outward viscous traces sigma (Ja^d . tau)_face;
 //   inviscid (all elements): J R = -sum_d D_d Ftil^d - sum_faces l_i/w_i [F* . S - sigma
 //              Ftil^d_face + BR1 viscous face terms] + J r_v, Roe/LLF on the interpolated states;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   double* sU = sD + NP * NP;                      // EPB * 3 * n3
   double* sJa = sU + EPB * 3 * n3;                // EPB * 9 * n3 (curved only)
   double* sF = sJa + (CURVED ? EPB * 9 * n3 : 0); // EPB * 9 * n3: Ftil_v[d][c]
+  double* sT = sF + EPB * 9 * n3;                 // EPB * 54 * n2: face terms [f*n2+ab][c*3+k]
   const int tid = threadIdx.x;
   for (int t = tid; t < n2; t += blockDim.x) sD[t] = c_Dg[N][t];
   int le = tid / n3;
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   double* U = sU + le * 3 * n3;
   double* JA = sJa + le * 9 * n3;
   double* F = sF + le * 9 * n3;
+  double* TG = sT + le * 54 * n2;
   double Ja[9], invJ = 0.0;
   if (active) {
 #pragma unroll
@@ -109,8 +112,8 @@ __global__ void __launch_bounds__(Shape<N>::threads)
   __syncthreads();
   const int ii[3] = {p % n, (p / n) % n, p / n2};
   const int str[3] = {1, n, n2};
+  double G[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   if (active) {
-    double G[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
     // volume part: J G_ck = sum_d D_d (Ja^d_k u_c)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -127,86 +130,90 @@ __global__ void __launch_bounds__(Shape<N>::threads)
         }
       }
     }
-    // lifting from both faces of every direction: l_i / w_i (u* S - sigma (Ja^d u)_face)
+    // face phase, one item per face point of the element's 6 n^2:
+    // TG = u* S - sigma (Ja^d u)_face, S outward (the mortar's projected u* S there)
+    for (int t = p; t < 6 * n2; t += n3) {
+      const int f = t / n2, ab = t % n2, a = ab % n, b = ab / n, d = f >> 1;
+      const double* l = c_lb[N][f & 1];
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      const FaceLink L = M.link[e * 6 + f];
+      double uf[3] = {0.0, 0.0, 0.0}, Sv[3] = {0.0, 0.0, 0.0}, JU[3][3];  // JU[c][k] = (Ja^d_k u_c)_face
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) JU[c][k] = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const int pm = line_node(f, n, a, b, m);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uf[c] += l[m] * U[c * n3 + pm];
+        if (CURVED) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double jk = JA[(d * 3 + k) * n3 + pm];
+            Sv[k] += l[m] * jk;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) JU[c][k] += l[m] * jk * U[c * n3 + pm];
+          }
+        }
+      }
+      if (!CURVED) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          Sv[k] = M.ec[e].Ja[d * 3 + k];  // d varies at run time here
+#pragma unroll
+          for (int c = 0; c < 3; ++c) JU[c][k] = Sv[k] * uf[c];
+        }
+      }
+      double* tg = TG + t * 9;
+      if (L.kind == FK_MORTAR) {  // u*_c S_k projected from the mortar, S outward
+        const int64_t ms = M.tr_off[e] + t;
+#pragma unroll
+        for (int ck = 0; ck < 9; ++ck) tg[ck] = M.LU[ck * M.tr_total + ms] - sg * JU[ck / 3][ck % 3];
+        continue;
+      }
+      double up[3];  // the neighbour's face velocity, or the ghost's behind a boundary face
+      if (L.kind == FK_CONF) {
+        int a1, b1;
+        inv_orient(L.orient, N, a, b, a1, b1);
+        const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) up[c] = M.Tq[(1 + c) * M.tr_total + ns];
+      } else if (L.kind == FK_INFLOW) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) up[c] = M.inflow[1 + c];
+      } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+        double jw[3];
+        wall_jump<double>(L.kind, uf, Sv, jw);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) up[c] = uf[c] + jw[c];
+      } else {  // outflow: the interior velocity
+#pragma unroll
+        for (int c = 0; c < 3; ++c) up[c] = uf[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double us = 0.5 * (uf[c] + up[c]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tg[c * 3 + k] = sg * (us * Sv[k] - JU[c][k]);
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // lifting from both faces of every direction: l_i(+-1) / w_i times the face term
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int a, b;
       face_coords(d, ii, a, b);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int f = 2 * d + s;
-        const double sg = s ? 1.0 : -1.0;
-        const FaceLink L = M.link[e * 6 + f];
-        const double* l = c_lb[N][s];
-        const double cf = l[ii[d]] / c_wg[N][ii[d]];
-        double uf[3] = {0.0, 0.0, 0.0}, Sv[3], JU[3][3];  // JU[c][k] = (Ja^d_k u_c)_face
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const double cf = c_lb[N][s2][ii[d]] / c_wg[N][ii[d]];
+        const double* tg = TG + ((2 * d + s2) * n2 + a + n * b) * 9;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) JU[c][k] = 0.0;
-        if (CURVED) {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) Sv[k] = 0.0;
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const int pm = line_node(f, n, a, b, m);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const double jk = JA[(d * 3 + k) * n3 + pm];
-              Sv[k] += l[m] * jk;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) JU[c][k] += l[m] * jk * U[c * n3 + pm];
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) uf[c] += l[m] * U[c * n3 + pm];
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const int pm = line_node(f, n, a, b, m);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) uf[c] += l[m] * U[c * n3 + pm];
-          }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            Sv[k] = Ja[d * 3 + k];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) JU[c][k] = Ja[d * 3 + k] * uf[c];
-          }
-        }
-        if (L.kind == FK_MORTAR) {  // u*_c S_k projected from the mortar, S outward
-          const int64_t ms = M.tr_off[e] + f * n2 + a + n * b;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) G[c][k] += cf * (M.LU[(c * 3 + k) * M.tr_total + ms] - sg * JU[c][k]);
-          continue;
-        }
-        double up[3];  // the neighbour's face velocity, or the ghost's behind a boundary face
-        if (L.kind == FK_CONF) {
-          int a1, b1;
-          inv_orient(L.orient, N, a, b, a1, b1);
-          const int64_t ns = M.tr_off[L.nbr] + L.nface * n2 + a1 + n * b1;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) up[c] = M.Tq[(1 + c) * M.tr_total + ns];
-        } else if (L.kind == FK_INFLOW) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) up[c] = M.inflow[1 + c];
-        } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
-          double jw[3];
-          wall_jump<double>(L.kind, uf, Sv, jw);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) up[c] = uf[c] + jw[c];
-        } else {  // outflow: the interior velocity
-#pragma unroll
-          for (int c = 0; c < 3; ++c) up[c] = uf[c];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double us = 0.5 * (uf[c] + up[c]);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) G[c][k] += cf * sg * (us * Sv[k] - JU[c][k]);
-        }
+          for (int k = 0; k < 3; ++k) G[c][k] += cf * tg[c * 3 + k];
       }
     }
 #pragma unroll
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(Shape<N>::threads)
 // ---------------------------------------------------------------------------------------
 template <int N, bool C>
 static size_t visc_smem_gl() {
-  return sizeof(double) * (NP * NP + Shape<N>::EPB * (3 + (C ? 9 : 0) + 9) * Shape<N>::n3);
+  return sizeof(double) * (NP * NP + Shape<N>::EPB * ((3 + (C ? 9 : 0) + 9) * Shape<N>::n3 + 54 * Shape<N>::n2));
 }
 
 template <int N>
