@@ -291,11 +291,13 @@ def test_gauss_legendre_boundaries_rk_steps_and_conservation():
     assert rel_l2(ud.cpu().numpy(), u) <= TOL
 
 
-def test_a_32cube_case_sampled():
-    """cns_tgv 32^3 at N = 4 (4.1 M nodes), 30% NS: the whole mesh on the GPU, a sample of
-    elements on the oracle."""
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_a_32cube_case_sampled(nodes):
+    """cns_tgv 32^3 at N = 4 (4.1 M nodes), 30% NS, the configuration the benchmark times on
+    either node set: the whole mesh on the GPU, a sample of elements on the oracle."""
     import torch
     w = wl.cns_tgv(n=32, order=4)
+    w = dataclasses.replace(w, params=dict(w.params, nodes=nodes))
     M = _oracle(w)
     u = _state(w, M)
     S = _solver(w)
