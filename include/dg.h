@@ -158,14 +158,15 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
 dg_status dg_set_orders(dg_ctx* ctx, const int8_t* orders);
 
 /* Re-lay out a state for the orders set by the last successful dg_set_orders (Sec. 3.2:
- * restarting after the orders are re-assigned). q_old ([4][total before that call], device)
- * is read in the previous layout, q_new ([4][current total_nodes], device, caller-allocated,
+ * restarting after the orders are re-assigned). q_old ([nvar][total before that call], device;
+ * nvar = 4, or 5 under model 1) is read in the previous layout, q_new ([nvar][current
+ * total_nodes], device, caller-allocated,
  * not overlapping q_old) is written in the current one: per element, Lagrange interpolation
  * onto the new nodes (Gauss-Lobatto, or Gauss points with nodes 1) where the order grew or
  * stayed (exact for the old
  * polynomial), the L2 projection in reference coordinates where it dropped (keeps each
  * element's reference-space integral), applied along each direction. Asynchronous on
- * `stream`. DG_ERR_STATE before any dg_set_orders; DG_ERR_UNSUPPORTED under model 1. */
+ * `stream`. DG_ERR_STATE before any dg_set_orders. */
 dg_status dg_project_state(dg_ctx* ctx, const double* q_old_dev, double* q_new_dev, void* stream);
 
 /* Per-element flag (host array, length n_elem): 0 Euler, 1 Navier-Stokes + LES (Sec. 2.3).

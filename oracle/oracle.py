@@ -214,13 +214,15 @@ def project_state(orders_old, orders_new, q_old, nodes=0):
     element by element, Lagrange interpolation onto the new nodes (Gauss-Lobatto, or
     Gauss-Legendre with nodes=1) where the order grows or stays, the L2 projection (in
     reference coordinates) where it drops, applied along each of the three directions.
-    q_old: [4][sum (N_old + 1)^3]; returns [4][sum (N_new + 1)^3]."""
+    q_old: [nvar][sum (N_old + 1)^3] (nvar 4, or 5 for the compressible state); returns
+    [nvar][sum (N_new + 1)^3]."""
     up, down = (interp_gl, project_gl) if nodes == 1 else (interp, project)
     orders_old = np.asarray(orders_old, dtype=np.int64)
     orders_new = np.asarray(orders_new, dtype=np.int64)
     off_o = np.concatenate([[0], np.cumsum((orders_old + 1) ** 3)])
     off_n = np.concatenate([[0], np.cumsum((orders_new + 1) ** 3)])
-    q_new = np.zeros((4, off_n[-1]))
+    nv = q_old.shape[0]
+    q_new = np.zeros((nv, off_n[-1]))
     ops = {}
     for e in range(len(orders_old)):
         No, Nn = int(orders_old[e]), int(orders_new[e])
@@ -228,9 +230,9 @@ def project_state(orders_old, orders_new, q_old, nodes=0):
             ops[No, Nn] = up(No, Nn) if Nn >= No else down(No, Nn)
         T = ops[No, Nn]
         no, nn = No + 1, Nn + 1
-        A = q_old[:, off_o[e]:off_o[e + 1]].reshape(4, no, no, no)  # [v][k][j][i], i fastest
+        A = q_old[:, off_o[e]:off_o[e + 1]].reshape(nv, no, no, no)  # [v][k][j][i], i fastest
         B = np.einsum('Ia,Jb,Kc,vcba->vKJI', T, T, T, A)
-        q_new[:, off_n[e]:off_n[e + 1]] = B.reshape(4, -1)
+        q_new[:, off_n[e]:off_n[e + 1]] = B.reshape(nv, -1)
     return q_new
 
 

@@ -1267,8 +1267,8 @@ dg_status dg_set_orders(dg_ctx* c, const int8_t* orders) {
 dg_status dg_project_state(dg_ctx* c, const double* q_old, double* q_new, void* stream) {
   if (!c || !q_old || !q_new) return fail(DG_ERR_ARG, "NULL argument");
   if (c->prev_order.empty()) return fail(DG_ERR_STATE, "dg_project_state needs a preceding dg_set_orders");
-  // the interpolation and projection tables follow the node set (Gauss-Lobatto or Gauss points)
-  if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_project_state: incompressible form only");
+  // the interpolation and projection tables follow the node set (Gauss-Lobatto or Gauss points);
+  // every state plane (4, or 5 for the compressible form) is re-laid out the same way
   if (q_old == q_new) return fail(DG_ERR_ARG, "q_old and q_new must not overlap");
   CU(cudaSetDevice(c->device));
   int8_t* dord = nullptr;

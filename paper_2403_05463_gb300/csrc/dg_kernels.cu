@@ -619,22 +619,23 @@ __global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int 
 // ---------------------------------------------------------------------------------------
 // The element's state at its previous order, re-laid out at its current order by a 1D operator
 // applied along each direction in turn: Lagrange interpolation when the order grows or stays,
-// the L2 projection when it drops. Two shared buffers of 4 n^3 doubles ping-pong between the
-// three passes.
+// the L2 projection when it drops. Two shared buffers of nvar n^3 doubles ping-pong between
+// the three passes (nvar = 4, or 5 for the compressible form).
 __global__ void __launch_bounds__(256) k_project_state(DevMesh M, const int8_t* __restrict__ old_order,
                                                        const int64_t* __restrict__ old_off, int64_t total_old,
                                                        const double* __restrict__ qo, double* __restrict__ qn) {
-  __shared__ double A[4 * NP * NP * NP], X[4 * NP * NP * NP];
+  __shared__ double A[5 * NP * NP * NP], X[5 * NP * NP * NP];
+  const int nv = M.model == 1 ? 5 : 4;
   const int e = blockIdx.x;
   const int No = old_order[e], Nn = M.order[e], no = No + 1, nn = Nn + 1;
   const double* T = Nn >= No ? interp_tab(M, No, Nn) : proj_tab(M, No, Nn);  // T[i * NP + j]: new i, old j
   const int64_t oo = old_off[e], on = M.elem_off[e];
   const int no3 = no * no * no;
-  for (int t = threadIdx.x; t < 4 * no3; t += blockDim.x) A[t] = qo[(t / no3) * total_old + oo + t % no3];
+  for (int t = threadIdx.x; t < nv * no3; t += blockDim.x) A[t] = qo[(t / no3) * total_old + oo + t % no3];
   __syncthreads();
   // along xi_1: X[v][c][b][I] = sum_a T[I][a] A[v][c][b][a]
   const int s1 = no * no * nn;
-  for (int t = threadIdx.x; t < 4 * s1; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nv * s1; t += blockDim.x) {
     const int v = t / s1, r = t % s1, I = r % nn, cb = r / nn;
     double s = 0.0;
     for (int a = 0; a < no; ++a) s += T[I * NP + a] * A[v * no3 + cb * no + a];
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(256) k_project_state(DevMesh M, const int8_t* 
   __syncthreads();
   // along xi_2: A[v][c][J][I] = sum_b T[J][b] X[v][c][b][I]
   const int s2 = no * nn * nn;
-  for (int t = threadIdx.x; t < 4 * s2; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nv * s2; t += blockDim.x) {
     const int v = t / s2, r = t % s2, I = r % nn, J = (r / nn) % nn, c = r / (nn * nn);
     double s = 0.0;
     for (int b = 0; b < no; ++b) s += T[J * NP + b] * X[v * s1 + (c * no + b) * nn + I];
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(256) k_project_state(DevMesh M, const int8_t* 
   __syncthreads();
   // along xi_3: qn[v][K][J][I] = sum_c T[K][c] A[v][c][J][I]
   const int nn3 = nn * nn * nn;
-  for (int t = threadIdx.x; t < 4 * nn3; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nv * nn3; t += blockDim.x) {
     const int v = t / nn3, r = t % nn3, IJ = r % (nn * nn), K = r / (nn * nn);
     double s = 0.0;
     for (int c = 0; c < no; ++c) s += T[K * NP + c] * A[v * s2 + c * nn * nn + IJ];

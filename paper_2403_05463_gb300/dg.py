@@ -298,7 +298,7 @@ class Solver:
         """q_old in the layout before the last set_orders -> a new tensor in the current one
         (see dg_project_state)."""
         import torch
-        q_new = torch.empty((4, self.total_nodes), dtype=torch.float64, device=q_old.device)
+        q_new = torch.empty((self.nvar, self.total_nodes), dtype=torch.float64, device=q_old.device)
         _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old"), _dev_ptr(q_new, "q_new"),
                                        _stream_handle(stream)))
         return q_new

@@ -234,6 +234,32 @@ def test_mortars_with_walls_rk_steps_and_order_changes():
     assert rel_l2(S.residual(to_dev(u2)).cpu().numpy(), M2.cns_residual(u2)) <= TOL
 
 
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_state_reprojection_after_order_changes(nodes):
+    """dg_project_state on the five-plane compressible state (Sec. 3.2: restarting with
+    re-assigned orders) after two re-assignments on a curved mesh, against the oracle's, then
+    the residual on the re-laid-out state."""
+    import torch
+    w = _mixed(_curved_small(3, 75), 75, 2, 7)
+    p = dict(w.params, nodes=nodes)
+    M = _oracle(w, p)
+    u = _state(w, M)
+    S = _solver(w, p)
+    rng = np.random.default_rng(76)
+    o_prev, u_prev, ud = w.orders.copy(), u, to_dev(u)
+    for _ in range(2):
+        o_new = rng.integers(2, 8, size=w.n_elem).astype(np.int8)
+        S.set_orders(o_new)
+        ud = S.project_state(ud)
+        torch.cuda.synchronize()
+        ref = orc.project_state(o_prev, o_new, u_prev, nodes=nodes)
+        assert ud.shape == ref.shape
+        assert np.abs(ud.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+        o_prev, u_prev = o_new, ref
+    M2 = _oracle(dataclasses.replace(w, orders=o_prev), p)
+    assert rel_l2(S.residual(ud).cpu().numpy(), M2.cns_residual(u_prev)) <= TOL
+
+
 GL_CASES = [
     ("box_n3", lambda: _box(3), {}),
     ("box_n1_llf_onesided", lambda: _box(1, n=5), dict(riemann=1, mixed_face=1, closure=0)),

@@ -608,6 +608,17 @@ def test_project_state_is_exact_for_representable_polynomials(nodes):
     np.testing.assert_allclose(q_new, _poly_state(B.node_coords(), deg), rtol=0, atol=1e-12)
 
 
+def test_project_state_of_five_planes_is_plane_by_plane():
+    # the compressible state: every plane is re-laid out as a four-plane state would be
+    rng = np.random.default_rng(10)
+    o_old, o_new = rng.integers(1, 8, size=12), rng.integers(1, 8, size=12)
+    q = rng.normal(size=(5, int(((o_old + 1) ** 3).sum())))
+    for nodes in (0, 1):
+        q5 = orc.project_state(o_old, o_new, q, nodes=nodes)
+        np.testing.assert_array_equal(q5[:4], orc.project_state(o_old, o_new, q[:4], nodes=nodes))
+        np.testing.assert_array_equal(q5[4:], orc.project_state(o_old, o_new, q[1:5], nodes=nodes)[3:])
+
+
 @pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
 def test_project_state_round_trip_and_element_integrals(nodes):
     rng = np.random.default_rng(9)
