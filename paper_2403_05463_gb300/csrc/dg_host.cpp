@@ -1561,8 +1561,8 @@ dg_status dg_conservation(dg_ctx* c, const double* R, double* out, void* stream)
 
 static_assert(DG_CONSERVATION_NOALLOC_MAX_ELEMS == kNoAllocMaxElems, "scratch limit");
 
-// Allocates nothing: no cudaMalloc/cudaFree, no host copy. The weights travel as a kernel
-// argument built on the stack; the partial sums use the static scratch of dg_noalloc.cu.
+// Allocates nothing: no cudaMalloc/cudaFree, no host copy. The per-element sums are those of
+// dg_conservation, written to the static scratch of dg_noalloc.cu.
 dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, void* stream) {
   if (!c || !R || !out_dev) return fail(DG_ERR_ARG, "NULL argument");
   if (c->prm.model != 0) return fail(DG_ERR_UNSUPPORTED, "dg_conservation_noalloc: incompressible form only");
@@ -1572,10 +1572,7 @@ dg_status dg_conservation_noalloc(dg_ctx* c, const double* R, double* out_dev, v
   CU(cudaSetDevice(c->device));
   double* scratch = nullptr;
   CU(noalloc_scratch(c->device, &scratch));
-  NoAllocWeights W{};
-  for (int N = 1; N <= MAXN; ++N)
-    for (int i = 0; i <= N; ++i) W.w[N][i] = node_rule(c, N).w[i];
-  CU(launch_conservation_noalloc(c->M, c->ord_buckets.data(), (int)c->ord_buckets.size(), W, R, scratch, out_dev,
+  CU(launch_conservation_noalloc(c->M, c->ord_buckets.data(), (int)c->ord_buckets.size(), R, scratch, out_dev,
                                  (cudaStream_t)stream));
   return DG_OK;
 }

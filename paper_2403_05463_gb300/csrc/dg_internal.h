@@ -145,9 +145,6 @@ enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
 // Allocation-free conservation sums (dg_noalloc.cu): largest mesh its static scratch holds.
 constexpr int64_t kNoAllocMaxElems = 65536;
-struct NoAllocWeights {
-  double w[NP][NP];  // Gauss-Lobatto weights w[N][i]
-};
 
 // Launchers (dg_kernels.cu). All return cudaGetLastError() of their launches.
 cudaError_t upload_ops(const Ops1D& ops);
@@ -226,8 +223,7 @@ cudaError_t launch_detect_regions(const DevMesh& M, const Bucket& b, const GmmDe
 
 // Allocation-free conservation sums (dg_noalloc.cu)
 cudaError_t noalloc_scratch(int device, double** ptr);
-cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets,
-                                        const NoAllocWeights& W, const double* R, double* scratch,
-                                        double* out, cudaStream_t s);
+cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets, const double* R,
+                                        double* scratch, double* out, cudaStream_t s);
 
 }  // namespace dgk

@@ -29,27 +29,6 @@ constexpr int kSumThreads = 256;
 std::mutex g_setup_mutex;
 double* g_scratch[kMaxDevices] = {};  // device address of g_noalloc_partial, per device
 
-template <int N>
-__global__ void k_conservation_partial(DevMesh M, const int32_t* __restrict__ list, int count,
-                                       NoAllocWeights W, const double* __restrict__ R,
-                                       double* __restrict__ partial) {
-  constexpr int n = N + 1, n3 = n * n * n;
-  const int le = blockIdx.x * blockDim.x + threadIdx.x;
-  if (le >= count) return;
-  const int e = list[le];
-  const int64_t off = M.elem_off[e];
-  const bool curved = M.ec[e].curved != 0.0;
-  for (int v = 0; v < 4; ++v) {
-    double s = 0.0;
-    for (int p = 0; p < n3; ++p) {
-      const double w = W.w[N][p % n] * W.w[N][(p / n) % n] * W.w[N][p / (n * n)];
-      const double J = curved ? M.geo[9 * M.total + off + p] : M.ec[e].J;
-      s += w * J * R[v * M.total + off + p];
-    }
-    partial[v * M.n_elem + e] = s;
-  }
-}
-
 // Block v sums partial[v][0..ne): each thread a strided run in element order, then a pairwise
 // tree in shared memory. The order is fixed, so repeated calls give identical sums.
 __global__ void k_conservation_final(const double* __restrict__ partial, int64_t ne, double* out) {
@@ -84,24 +63,14 @@ cudaError_t noalloc_scratch(int device, double** ptr) {
   return cudaSuccess;
 }
 
-cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets,
-                                        const NoAllocWeights& W, const double* R, double* scratch,
-                                        double* out, cudaStream_t s) {
+cudaError_t launch_conservation_noalloc(const DevMesh& M, const Bucket* buckets, int n_buckets, const double* R,
+                                        double* scratch, double* out, cudaStream_t s) {
   if (M.n_elem > kNoAllocMaxElems) return cudaErrorInvalidValue;
+  // the per-element weighted sums are those of dg_conservation (one kernel, k_conservation),
+  // written to the static scratch instead of the context's buffer
   for (int i = 0; i < n_buckets; ++i) {
-    const Bucket& b = buckets[i];
-    if (b.count == 0) continue;
-    const unsigned grid = (unsigned)((b.count + 127) / 128);
-    switch (b.N) {
-      case 1: k_conservation_partial<1><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 2: k_conservation_partial<2><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 3: k_conservation_partial<3><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 4: k_conservation_partial<4><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 5: k_conservation_partial<5><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 6: k_conservation_partial<6><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      case 7: k_conservation_partial<7><<<grid, 128, 0, s>>>(M, b.list, b.count, W, R, scratch); break;
-      default: return cudaErrorInvalidValue;
-    }
+    const cudaError_t e = launch_conservation(M, buckets[i], R, 4, scratch, s);
+    if (e != cudaSuccess) return e;
   }
   k_conservation_final<<<4, kSumThreads, 0, s>>>(scratch, M.n_elem, out);
   return cudaGetLastError();

@@ -206,7 +206,9 @@ class Solver:
     def set_orders(self, orders):
         o = np.ascontiguousarray(orders, dtype=np.int8)
         assert o.size == self.n_elem
+        before = self.total_nodes
         _check(load().dg_set_orders(self.h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))))
+        self._total_before_orders = before  # the layout project_state reads q_old in
 
     def set_flags(self, flags):
         f = np.ascontiguousarray(flags, dtype=np.uint8)
@@ -289,6 +291,7 @@ class Solver:
         """The same sums into `out` (a caller-owned float64 CUDA tensor of 4 values), without
         any allocation, host copy or synchronisation; calls whose kernels overlap on one device
         race on the library's shared scratch."""
+        self._check_state(R, "R")
         if out.numel() < 4:
             raise ValueError("out must hold 4 float64 values")
         _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R"), _dev_ptr(out, "out"),
@@ -298,6 +301,11 @@ class Solver:
         """q_old in the layout before the last set_orders -> a new tensor in the current one
         (see dg_project_state)."""
         import torch
+        before = getattr(self, "_total_before_orders", None)
+        if before is None:
+            raise DGError(6, "project_state: no set_orders before it")
+        if q_old.numel() != self.nvar * before:
+            raise ValueError(f"q_old must hold [{self.nvar}][{before}] values (the layout before the last set_orders)")
         q_new = torch.empty((self.nvar, self.total_nodes), dtype=torch.float64, device=q_old.device)
         _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old"), _dev_ptr(q_new, "q_new"),
                                        _stream_handle(stream)))

@@ -76,3 +76,45 @@ def test_bench_and_entry_compile():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for f in ("bench.py", "__graft_entry__.py"):
         py_compile.compile(os.path.join(root, f), doraise=True)
+
+
+class _FakeTensor:
+    """Stands in for a CUDA tensor of the wrong size: the size checks must refuse it before any
+    pointer is taken or any library call is made."""
+    def __init__(self, n):
+        self._n = n
+
+    def numel(self):
+        return self._n
+
+
+def _sized_solver(monkeypatch, total=100, before=None):
+    class Sized(dg.Solver):
+        total_nodes = total  # no library call
+
+    S = Sized.__new__(Sized)
+    S.params, S.h, S.n_elem = {}, None, 1
+    if before is not None:
+        S._total_before_orders = before
+
+    def no_library():
+        raise AssertionError("the library was called")
+    monkeypatch.setattr(dg, "load", no_library)
+    return S
+
+
+def test_noalloc_sums_refuse_a_wrongly_sized_R_without_a_launch(monkeypatch):
+    S = _sized_solver(monkeypatch)
+    with pytest.raises(ValueError, match=r"R must hold \[4\]\[100\]"):
+        S.conservation_noalloc(_FakeTensor(4 * 99), _FakeTensor(4))
+
+
+def test_project_state_refuses_a_q_old_of_another_layout(monkeypatch):
+    pytest.importorskip("torch")
+    S = _sized_solver(monkeypatch, total=100, before=64)
+    with pytest.raises(ValueError, match=r"q_old must hold \[4\]\[64\]"):
+        S.project_state(_FakeTensor(4 * 100))
+    S5 = _sized_solver(monkeypatch, total=100, before=64)
+    S5.params = {"model": 1}
+    with pytest.raises(ValueError, match=r"q_old must hold \[5\]\[64\]"):
+        S5.project_state(_FakeTensor(4 * 64))  # a four-plane state for the five-plane form
