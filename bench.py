@@ -170,13 +170,103 @@ def recorded_traffic(workload, precision, n, kernel):
     return float(m_t.group(1))
 
 
-def oracle_rate(w, q_host, budget_s=12.0, seed=0):
+def oracle_mesh(w, params=None):
+    from oracle import oracle as orc
+    m = w.mesh
+    return orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**(params or w.params)), m.bc_tag)
+
+
+def sampled_error(M, w, q_host, R_host, k=96, seed=7):
+    """Relative L2 error of a residual computed by the library (host copy) against the FP64
+    oracle, over the nodes of k randomly chosen elements (the oracle evaluates only those, with
+    their neighbours' gradients): ||R - R_oracle|| / ||R_oracle|| and per variable (each
+    variable's error over the same total norm)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(w.n_elem, min(k, w.n_elem), replace=False))
+    R_ref = np.zeros_like(q_host)
+    M.residual(q_host, sel=sel, out=R_ref)
+    off = M.offsets
+    idx = np.concatenate([np.arange(off[e], off[e + 1]) for e in sel])
+    a, b = R_host[:, idx], R_ref[:, idx]
+    nrm = float(np.sqrt((b ** 2).sum()))
+    return {"rel_l2": float(np.sqrt(((a - b) ** 2).sum())) / nrm,
+            "per_var": [float(np.sqrt(((a[v] - b[v]) ** 2).sum())) / nrm for v in range(a.shape[0])],
+            "sample": f"{sel.size} random elements ({idx.size} nodes), FP64 oracle"}
+
+
+def timed_steps(S, q, g, dt, stream, steps, warmup=2):
+    """Mean milliseconds per RK3 step (CUDA events on the launching stream)."""
+    import torch
+    S.rk_step(q, g, dt, warmup, stream=stream)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    S.rk_step(q, g, dt, steps, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    S.check_device()
+    return a.elapsed_time(b) / steps
+
+
+def time_configs(S, w, q0, M, stream, hbm, device=0):
+    """The metric's other points, outside the timed region: the same 64^3 mesh in FP64 and with
+    the 3xTF32 tensor-core contraction; the precision-variant configuration (tgv 32^3, N = 5,
+    30% NS slab) in FP32 and 3xTF32; the p-adaptive configuration (curved 32^3, orders 2..7,
+    18.75% NS, one graph-captured step over every order bucket, autotuned). Each with its
+    DOF-updates/s per stage and its residual error against the FP64 oracle on a sample."""
+    import torch
+    from paper_2403_05463_gb300 import dg, workloads as wl
+    out = {}
+    qh = q0.cpu().numpy()
+    dof = S.total_nodes
+    q = q0.clone()
+    g = torch.zeros_like(q)
+    for prec, steps in (("fp64", 3), ("tf32x3", 10)):
+        S.set_params(precision=prec)
+        R = S.residual(q0).cpu().numpy()
+        q.copy_(q0)
+        ms = timed_steps(S, q, g, w.dt, stream, steps)
+        out[f"{w.name}_{prec}"] = {"ms_per_step": ms, "value": dof * 3 / (ms * 1e-3), "dtype": prec,
+                                   "error_vs_oracle": sampled_error(M, w, qh, R)}
+    S.set_params(precision="fp32")
+    del q, g
+    for name, make, precs in (("tgv_32x32x32_n5", wl.tgv_32x32x32_n5, ("fp32", "tf32x3")),
+                              ("padapt_32x32x32", wl.padapt_32x32x32, ("fp32",))):
+        wc = make()
+        Mc = oracle_mesh(wc)
+        qc_h = wc.state(Mc.node_coords())
+        for prec in precs:
+            Sc = dg.Solver.from_workload(wc, precision=prec, device=device)
+            tuning = Sc.autotune() if prec == "fp32" else "default"
+            qc = torch.from_numpy(qc_h).to(f"cuda:{device}")
+            R = Sc.residual(qc).cpu().numpy()
+            g = torch.zeros_like(qc)
+            ms = timed_steps(Sc, qc, g, wc.dt, stream, 20)
+            qc.copy_(torch.from_numpy(qc_h))
+            ph_ms = Sc.phase_times(qc, g, wc.dt, reps=6, stream=stream)
+            ph_b = Sc.phase_bytes()
+            step_gb = 3 * sum(ph_b.values()) / 1e9
+            out[f"{name}_{prec}"] = {
+                "ms_per_step": ms, "value": Sc.total_nodes * 3 / (ms * 1e-3), "dtype": prec,
+                "dof": Sc.total_nodes, "ns_fraction": wc.ns_fraction,
+                "orders": sorted(int(o) for o in set(wc.orders.tolist())),
+                "hbm_frac_step": step_gb / (ms * 1e-3) / hbm,
+                "inviscid_update_gbs": ph_b["inviscid_update"] / (ph_ms["inviscid_update"] * 1e-3) / 1e9,
+                "launches_per_step": Sc.launches_per_step, "launch_shapes": "autotuned" if tuning != "default" else tuning,
+                "error_vs_oracle": sampled_error(Mc, wc, qc_h, R, k=128)}
+            Sc.close()
+            del qc, g
+    return out
+
+
+def oracle_rate(w, q_host, budget_s=12.0, seed=0, M=None):
     """The FP64 oracle as it stands, on the host cores: residual of a random sample of
     elements (each needs its neighbours' BR1 gradients too), DOF of the sample / wall time."""
     import numpy as np
     from oracle import oracle as orc
-    m = w.mesh
-    M = orc.Mesh(m.hex, m.geom, m.geom_degree, w.orders, w.flags, orc.params(**w.params), m.bc_tag)
+    if M is None:
+        M = oracle_mesh(w)
     rng = np.random.default_rng(seed)
     n3 = (w.orders.astype(np.int64) + 1) ** 3
     R = np.zeros_like(q_host)
@@ -506,8 +596,13 @@ def main():
         out["e2e"] = {"value": world * dof * 3 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e * 1e3}
         if rank == 0 and world == 1:
+            M = oracle_mesh(w)
+            qh0 = q0.cpu().numpy()
+            # the headline's accuracy: the benchmarked residual against the FP64 oracle
+            out["error_vs_oracle"] = sampled_error(M, w, qh0, S.residual(q0).cpu().numpy())
+            out["configs"] = time_configs(S, w, q0, M, stream, hbm, device=local)
             try:
-                out["cpu_baseline"] = oracle_rate(w, q0.cpu().numpy())
+                out["cpu_baseline"] = oracle_rate(w, qh0, M=M)
             except Exception as exc:  # the baseline is context, never the product path
                 out["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle", "cores": None,
                                        "sample": f"not measured: {exc}"}

@@ -22,6 +22,9 @@ struct Ops1D32 {
   float w0inv[NP];  // 1 / w_end
 };
 __constant__ Ops1D32 c_ops32;
+// FP64 D[N][i*n+m] for the FP64 divergence of the box-element inviscid pass (read through L1:
+// the lanes of a warp read up to n different rows, which constant memory would serialise)
+__device__ double g_D64[NP][NP * NP];
 __constant__ double c32_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 __constant__ double c32_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 __constant__ float c32_rkA32[3] = {0.0f, -5.0f / 9.0f, -153.0f / 128.0f};
@@ -773,6 +776,10 @@ template <int N, int GEO, int MODE, int E, int VOL>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
   constexpr bool KEP = VOL == 1, TC = VOL == 2;
+  // Box elements, standard form: the divergence S = sum_d Ja_dd D_d u_d is taken in FP64 from the
+  // staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the momentum
+  // fluxes (U_c S); the FP32 contractions carry only the rest of the momentum fluxes.
+  constexpr bool DIV64 = GEO == 0 && VOL == 0;
   using S = Tile<N, E>;
   using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
@@ -897,7 +904,8 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
         fl[0][k] = c0sq * dq[1 + k];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          fl[1 + c][k] = qr32[1 + c] * dq[1 + k] + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
+          fl[1 + c][k] = (DIV64 ? 0.f : qr32[1 + c] * dq[1 + k]) + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) +
+                         (c == k ? dq[0] : 0.f);
       }
       if (KEP) F4[p] = make_float4(dq[0], dq[1], dq[2], dq[3]);
       if (GEO == 0) {
@@ -949,11 +957,31 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
           for (int m = 0; m < n; ++m) {
             const float dm = sD[ii[d] * n + m];
             const float4 f4 = F4[d * n3 + bs + m * str[d]];
-            JR[0] -= dm * f4.x;
+            if (!DIV64) JR[0] -= dm * f4.x;
             JR[1] -= dm * f4.y;
             JR[2] -= dm * f4.z;
             JR[3] -= dm * f4.w;
           }
+        }
+        if (DIV64) {
+          // S = sum_d Ja_dd (D u_d)_i in FP64 (the pressure row is a small difference of the three
+          // directional derivatives, so FP32 rounding of each would be amplified by c0^2 / |R_p|)
+          const ElemConst* ec64 = M.ec + MT->elem;
+          double S64 = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int bs = p - ii[d] * str[d];
+            const double* ud = reinterpret_cast<const double*>(INe + P::iQD + (1 + d) * P::SQD + SH[1 + d]);
+            const double* Dr = &g_D64[N][ii[d] * n];
+            double sd = 0.0;
+#pragma unroll
+            for (int m = 0; m < n; ++m) sd = fma(__ldg(Dr + m), ud[bs + m * str[d]], sd);
+            S64 = fma(__ldg(&ec64->Ja[d * 4]), sd, S64);
+          }
+          const float s32 = (float)S64;
+          JR[0] = -c0sq * s32;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) JR[1 + c] -= qr32[1 + c] * s32;
         }
       } else {
         const float4 di = F4[p];
@@ -1497,7 +1525,9 @@ cudaError_t upload_ops32(const Ops1D& ops) {
     for (int i = 0; i < NP * NP; ++i) o.D[N][i] = (float)ops.D[N][i];
     o.w0inv[N] = (float)(1.0 / ops.w[N][0]);
   }
-  return cudaMemcpyToSymbol(c_ops32, &o, sizeof o);
+  cudaError_t r = cudaMemcpyToSymbol(c_ops32, &o, sizeof o);
+  if (r != cudaSuccess) return r;
+  return cudaMemcpyToSymbol(g_D64, ops.D, sizeof ops.D);
 }
 
 template <int N, int GEO>
