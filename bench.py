@@ -222,22 +222,25 @@ def time_configs(S, w, q0, M, stream, hbm, device=0):
     dof = S.total_nodes
     q = q0.clone()
     g = torch.zeros_like(q)
-    for prec, steps in (("fp64", 3), ("tf32x3", 10)):
-        S.set_params(precision=prec)
+    div64 = {"fp64_divergence": 1}
+    for prec, extra, steps in (("fp64", {}, 3), ("fp32", div64, 10), ("tf32x3", {}, 10), ("tf32x3", div64, 10)):
+        S.set_params(dict(w.params, **extra), precision=prec)
         R = S.residual(q0).cpu().numpy()
         q.copy_(q0)
         ms = timed_steps(S, q, g, w.dt, stream, steps)
-        out[f"{w.name}_{prec}"] = {"ms_per_step": ms, "value": dof * 3 / (ms * 1e-3), "dtype": prec,
-                                   "error_vs_oracle": sampled_error(M, w, qh, R)}
-    S.set_params(precision="fp32")
+        out[f"{w.name}_{prec}" + ("_div64" if extra else "")] = {
+            "ms_per_step": ms, "value": dof * 3 / (ms * 1e-3), "dtype": prec,
+            "fp64_divergence": bool(extra), "error_vs_oracle": sampled_error(M, w, qh, R)}
+    S.set_params(dict(w.params), precision="fp32")
     del q, g
-    for name, make, precs in (("tgv_32x32x32_n5", wl.tgv_32x32x32_n5, ("fp32", "tf32x3")),
-                              ("padapt_32x32x32", wl.padapt_32x32x32, ("fp32",))):
+    for name, make, variants in (("tgv_32x32x32_n5", wl.tgv_32x32x32_n5,
+                                  (("fp32", {}), ("fp32", div64), ("tf32x3", {}), ("tf32x3", div64))),
+                                 ("padapt_32x32x32", wl.padapt_32x32x32, (("fp32", {}),))):
         wc = make()
         Mc = oracle_mesh(wc)
         qc_h = wc.state(Mc.node_coords())
-        for prec in precs:
-            Sc = dg.Solver.from_workload(wc, precision=prec, device=device)
+        for prec, extra in variants:
+            Sc = dg.Solver.from_workload(wc, precision=prec, device=device, params=dict(wc.params, **extra))
             tuning = Sc.autotune() if prec == "fp32" else "default"
             qc = torch.from_numpy(qc_h).to(f"cuda:{device}")
             R = Sc.residual(qc).cpu().numpy()
@@ -247,11 +250,12 @@ def time_configs(S, w, q0, M, stream, hbm, device=0):
             ph_ms = Sc.phase_times(qc, g, wc.dt, reps=6, stream=stream)
             ph_b = Sc.phase_bytes()
             step_gb = 3 * sum(ph_b.values()) / 1e9
-            out[f"{name}_{prec}"] = {
+            out[f"{name}_{prec}" + ("_div64" if extra else "")] = {
                 "ms_per_step": ms, "value": Sc.total_nodes * 3 / (ms * 1e-3), "dtype": prec,
-                "dof": Sc.total_nodes, "ns_fraction": wc.ns_fraction,
+                "fp64_divergence": bool(extra), "dof": Sc.total_nodes, "ns_fraction": wc.ns_fraction,
                 "orders": sorted(int(o) for o in set(wc.orders.tolist())),
                 "hbm_frac_step": step_gb / (ms * 1e-3) / hbm,
+                "phases_ms": {k: v for k, v in ph_ms.items() if v > 0},
                 "inviscid_update_gbs": ph_b["inviscid_update"] / (ph_ms["inviscid_update"] * 1e-3) / 1e9,
                 "launches_per_step": Sc.launches_per_step, "launch_shapes": "autotuned" if tuning != "default" else tuning,
                 "error_vs_oracle": sampled_error(Mc, wc, qc_h, R, k=128)}

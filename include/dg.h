@@ -138,7 +138,16 @@ typedef struct {
                        DG_ERR_UNSUPPORTED. dg_node_coords returns the Gauss points;
                        dg_detect_regions, dg_project_state and the conservation sums work
                        on them.                                                          */
-  int reserved;     /* must be 0                                                       */
+  int fp64_divergence; /* precision 1..3, standard volume term (split 0), axis-aligned box
+                       elements: 0 every volume contraction in FP32 (fast; the pressure row
+                       R_p = -c0^2 div u of a nearly divergence-free field is a small difference
+                       of three directional derivatives, so their FP32 rounding is amplified
+                       by about c0^2 |grad u| / |R_p|); 1 the divergence
+                       S = sum_d Ja_dd (D_d u_d) in FP64 from the FP64 state, used for the
+                       pressure row and for the U_c du_d part of the momentum fluxes (the
+                       deviation form's linear term), the rest of the momentum fluxes in FP32
+                       (more accurate, but runs on the FP64 pipe: slower). Affine and curved
+                       elements and the split form ignore it. Other values: DG_ERR_ARG      */
   double p_inf;     /* model 1: far-field pressure of the inflow ghost (with inflow[]) and
                        the static pressure of the outflow ghost (interior density and
                        velocity); both need rho_inf = inflow[0] > 0 and p_inf > 0          */
@@ -292,6 +301,21 @@ typedef struct {
  * DG_ERR_UNSUPPORTED under model 1 (q holds momenta there); DG_ERR_CUDA if a launch fails. */
 dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm, uint8_t* flags_dev,
                             double* pbar_dev, double* features_dev, void* stream);
+
+/* Failure detection of the pipelined reduced-precision passes (precision 1..3; the paper has
+ * no counterpart). Each of their warps waits on an mbarrier for a staged tile (consumers) or
+ * for a free buffer (the producer) with a bounded number of polls; when the budget runs out
+ * the warp records DG_ERR_TIMEOUT in the device error word (read by dg_check_device, which
+ * names the site: 1 inviscid consumers, 2 inviscid producer, 3 viscous consumers, 4 viscous
+ * producer) and returns, leaving the CUDA context usable.
+ *   polls      poll budget of every such wait, 1 .. 2^31 - 1; 0 restores the default 2^22.
+ *   stop_tile  test hook: -1 off; k >= 0 makes the producer warp of block 0 of every pipelined
+ *              launch return before staging its k-th tile, so that block's consumers wait for
+ *              data that never comes until their budget runs out. Everything staged before
+ *              was waited for by those consumers, so no copy is left in flight when they return.
+ * Applies to every later launch (the captured step graph is rebuilt). Results computed while
+ * stop_tile >= 0 are wrong by design. Errors: DG_ERR_ARG for a NULL ctx or out-of-range value. */
+dg_status dg_set_wait_limit(dg_ctx* ctx, int64_t polls, int stop_tile);
 
 /* Synchronise `stream`, then read and clear the device error word. */
 dg_status dg_check_device(dg_ctx* ctx, void* stream);

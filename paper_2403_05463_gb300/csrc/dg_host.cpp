@@ -402,7 +402,7 @@ dg_status check_params(const dg_params* p) {
   if (p->split < 0 || p->split > 1) return fail(DG_ERR_ARG, "split must be 0 or 1");
   if (p->model < 0 || p->model > 1) return fail(DG_ERR_ARG, "model must be 0 or 1");
   if (p->nodes < 0 || p->nodes > 1) return fail(DG_ERR_ARG, "nodes must be 0 or 1");
-  if (p->reserved != 0) return fail(DG_ERR_ARG, "reserved must be 0");
+  if (p->fp64_divergence < 0 || p->fp64_divergence > 1) return fail(DG_ERR_ARG, "fp64_divergence must be 0 or 1");
   if (p->nodes == 1 && (p->precision != 0 || p->split != 0))
     return fail(DG_ERR_UNSUPPORTED, "Gauss-Legendre nodes run in FP64 with the standard volume term only");
   if (p->model == 1) {
@@ -439,6 +439,7 @@ void apply_params(dg_ctx* c) {
   // contraction on the tensor cores (3xTF32, plain TF32)
   c->M.precision = c->prm.precision >= 1 ? 1 : 0;
   c->M.tc = c->prm.precision == 2 ? 1 : (c->prm.precision == 3 ? 2 : 0);
+  c->M.div64 = c->prm.fp64_divergence;
   c->M.nu32 = (float)c->prm.nu;
   c->M.c0sq32 = (float)c->prm.c0sq;
   c->M.cs32 = (float)c->prm.cs;
@@ -1231,6 +1232,8 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
   }
   cudaMemset(derr, 0, 16);
   c->M.err = derr;
+  c->M.wait_polls = kWaitPolls;
+  c->M.stop_tile = -1;
   apply_params(c);
   c->order.assign(c->ne, (int8_t)std::max(3, c->gdeg));
   c->flag.assign(c->ne, 1);
@@ -1539,6 +1542,16 @@ dg_status dg_check_device(dg_ctx* c, void* stream) {
     if (h[0] == DG_ERR_TIMEOUT) return fail(DG_ERR_TIMEOUT, "a device-side wait timed out (site %d)", h[1]);
     return fail(DG_ERR_DEVICE, "device error %d at site %d", h[0], h[1]);
   }
+  return DG_OK;
+}
+
+dg_status dg_set_wait_limit(dg_ctx* c, int64_t polls, int stop_tile) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (polls < 0 || polls > INT32_MAX) return fail(DG_ERR_ARG, "polls must be in [0, 2^31)");
+  if (stop_tile < -1) return fail(DG_ERR_ARG, "stop_tile must be -1 (off) or a tile index");
+  c->M.wait_polls = polls == 0 ? kWaitPolls : (int)polls;
+  c->M.stop_tile = stop_tile;
+  destroy_graph(c);  // captured launches hold the previous values
   return DG_OK;
 }
 

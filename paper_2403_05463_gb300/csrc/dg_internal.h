@@ -9,6 +9,7 @@ namespace dgk {
 constexpr int MAXN = 7;        // largest polynomial order with a kernel instantiation
 constexpr int NP = MAXN + 1;   // table stride
 constexpr int kErrTimeout = 7;  // DG_ERR_TIMEOUT in the device error word
+constexpr int kWaitPolls = 1 << 22;  // default poll budget of a bounded mbarrier wait
 
 // Kind of coupling behind one local face of an element.
 enum FaceKind : uint8_t {
@@ -76,11 +77,16 @@ struct DevMesh {
   const double* interp;      // [(Ns*NP+Nd)*NP*NP + i*NP + j]: Lagrange interpolation Ns -> Nd
   const double* proj;        // [(Nh*NP+Nl)*NP*NP + i*NP + j]: L2 projection Nh -> Nl
   int* err;                  // device error word
+  int wait_polls;            // polls of a bounded mbarrier wait before it gives up (timeout)
+  int stop_tile;             // test hook, -1 off: the producer warp of block 0 of each pipelined
+                             // launch returns before staging its stop_tile-th tile
   double nu, c0sq, cs, cv;
   int closure, riemann;
   int mixed_face;            // 0 average, 1 one-sided viscous flux on NS/Euler faces
   int split;                 // 0 standard convective volume term, 1 kinetic-energy-preserving split form
   int precision;             // 0: Tv/rv hold FP64; 1: they hold FP32 (same buffers)
+  int div64;                 // reduced-precision inviscid pass, box elements: the velocity
+                             // divergence (pressure row, U_c du_d fluxes) in FP64
   int tc;                    // the FP32 inviscid volume contraction on tensor cores: 1 in 3xTF32,
                              // 2 in plain TF32 (one product of the rounded operands); 0 FP32 FMAs
   float nu32, c0sq32, cs32, cv32, dt32;  // FP32 copies for the reduced-precision passes

@@ -723,9 +723,9 @@ __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, con
 }
 
 // bounded wait on an mbarrier phase: false if it did not complete within the limit
-__device__ __forceinline__ bool mbar_wait_bounded(void* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(void* bar, unsigned parity, int polls) {
   bool ok = false;
-  for (int spin = 0; spin < (1 << 22) && !ok; ++spin) ok = mbar_try_wait(bar, parity);
+  for (int spin = 0; spin < polls && !ok; ++spin) ok = mbar_try_wait(bar, parity);
   return ok;
 }
 __device__ __forceinline__ void mbar_arrive(void* bar) {
@@ -776,10 +776,12 @@ template <int N, int GEO, int MODE, int E, int VOL>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
   constexpr bool KEP = VOL == 1, TC = VOL == 2;
-  // Box elements, standard form: the divergence S = sum_d Ja_dd D_d u_d is taken in FP64 from the
-  // staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the momentum
-  // fluxes (U_c S); the FP32 contractions carry only the rest of the momentum fluxes.
-  constexpr bool DIV64 = GEO == 0 && VOL == 0;
+  // With M.div64 on box elements (standard form, FP32 or tensor-core contraction): the divergence
+  // S = sum_d Ja_dd D_d u_d is taken in FP64 from the staged FP64 state. It gives the pressure row
+  // (-c0^2 S) and the U_c du_d part of the momentum fluxes (U_c S); the FP32 contractions carry
+  // only the rest of the momentum fluxes.
+  constexpr bool DIV64_OK = GEO == 0 && VOL != 1;
+  const bool div64 = DIV64_OK && M.div64 != 0;
   using S = Tile<N, E>;
   using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
@@ -817,13 +819,16 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
-      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1))) {
+      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1), M.wait_polls)) {
         if (tid == NC) {
           atomicCAS(&M.err[0], 0, kErrTimeout);
           atomicCAS(&M.err[1], 0, 2);
         }
         return;
       }
+      // test hook: stage nothing more, so the consumers' bounded wait for this tile runs out
+      // (every copy staged before was waited for by the consumers; none is left in flight)
+      if (blockIdx.x == 0 && it == M.stop_tile) return;
       char* IN = b ? IN1 : IN0;
       store_recs<P>(B, tile, recs, IN);
       if (tile + (int)gridDim.x < ntiles) load_recs<E>(B, tile + gridDim.x, recs);
@@ -857,7 +862,7 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     const int cur = it & 1;
     const int i = tile * EPB + le;
     const bool active = lane_ok && i < B.count;
-    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1));
+    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1), M.wait_polls);
     if (consumer_any(!ok, NC)) {
       if (tid == 0) {
         atomicCAS(&M.err[0], 0, kErrTimeout);
@@ -904,7 +909,7 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
         fl[0][k] = c0sq * dq[1 + k];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          fl[1 + c][k] = (DIV64 ? 0.f : qr32[1 + c] * dq[1 + k]) + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) +
+          fl[1 + c][k] = (div64 ? 0.f : qr32[1 + c] * dq[1 + k]) + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) +
                          (c == k ? dq[0] : 0.f);
       }
       if (KEP) F4[p] = make_float4(dq[0], dq[1], dq[2], dq[3]);
@@ -957,31 +962,11 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
           for (int m = 0; m < n; ++m) {
             const float dm = sD[ii[d] * n + m];
             const float4 f4 = F4[d * n3 + bs + m * str[d]];
-            if (!DIV64) JR[0] -= dm * f4.x;
+            JR[0] -= dm * f4.x;
             JR[1] -= dm * f4.y;
             JR[2] -= dm * f4.z;
             JR[3] -= dm * f4.w;
           }
-        }
-        if (DIV64) {
-          // S = sum_d Ja_dd (D u_d)_i in FP64 (the pressure row is a small difference of the three
-          // directional derivatives, so FP32 rounding of each would be amplified by c0^2 / |R_p|)
-          const ElemConst* ec64 = M.ec + MT->elem;
-          double S64 = 0.0;
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const int bs = p - ii[d] * str[d];
-            const double* ud = reinterpret_cast<const double*>(INe + P::iQD + (1 + d) * P::SQD + SH[1 + d]);
-            const double* Dr = &g_D64[N][ii[d] * n];
-            double sd = 0.0;
-#pragma unroll
-            for (int m = 0; m < n; ++m) sd = fma(__ldg(Dr + m), ud[bs + m * str[d]], sd);
-            S64 = fma(__ldg(&ec64->Ja[d * 4]), sd, S64);
-          }
-          const float s32 = (float)S64;
-          JR[0] = -c0sq * s32;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) JR[1 + c] -= qr32[1 + c] * s32;
         }
       } else {
         const float4 di = F4[p];
@@ -1021,6 +1006,27 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
+      if (DIV64_OK && div64) {
+        // S = sum_d Ja_dd (D u_d)_i in FP64 (the pressure row is a small difference of the three
+        // directional derivatives, so FP32 rounding of each would be amplified by c0^2 / |R_p|)
+        const int str[3] = {1, n, n2};
+        const ElemConst* ec64 = M.ec + MT->elem;
+        double S64 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int bs = p - ii[d] * str[d];
+          const double* ud = reinterpret_cast<const double*>(INe + P::iQD + (1 + d) * P::SQD + SH[1 + d]);
+          const double* Dr = &g_D64[N][ii[d] * n];
+          double sd = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) sd = fma(__ldg(Dr + m), ud[bs + m * str[d]], sd);
+          S64 = fma(__ldg(&ec64->Ja[d * 4]), sd, S64);
+        }
+        const float s32 = (float)S64;
+        JR[0] = -c0sq * s32;  // replaces the FP32 contraction of the pressure row
+#pragma unroll
+        for (int c = 0; c < 3; ++c) JR[1 + c] -= qr32[1 + c] * s32;
+      }
     }
     if (TC) {
       // tensor-core items: (element, direction, 16-row tile), rows r = 4 line + v
@@ -1222,7 +1228,7 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const float4 c4 = Cp[d * n3 + p];
-        JR[0] -= c4.x;
+        if (!div64) JR[0] -= c4.x;  // with div64 the pressure row is -c0^2 S, set above
         JR[1] -= c4.y;
         JR[2] -= c4.z;
         JR[3] -= c4.w;
@@ -1329,13 +1335,14 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int b = it & 1;
-      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1))) {
+      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1), M.wait_polls)) {
         if (tid == NC) {
           atomicCAS(&M.err[0], 0, kErrTimeout);
           atomicCAS(&M.err[1], 0, 4);
         }
         return;
       }
+      if (blockIdx.x == 0 && it == M.stop_tile) return;  // test hook, as in the inviscid pass
       char* IN = b ? IN1 : IN0;
       store_recs<P>(B, tile, recs, IN);
       if (tile + (int)gridDim.x < ntiles) load_recs<EPB>(B, tile + gridDim.x, recs);
@@ -1357,7 +1364,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int cur = it & 1;
     const bool active = lane_ok && tile * EPB + le < B.count;
-    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1));
+    const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1), M.wait_polls);
     if (consumer_any(!ok, NC)) {
       if (tid == 0) {
         atomicCAS(&M.err[0], 0, kErrTimeout);

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("mixed_face", ctypes.c_int), ("split", ctypes.c_int),
                 ("model", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("prandtl_t", ctypes.c_double), ("nodes", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("p_inf", ctypes.c_double)]
+                ("fp64_divergence", ctypes.c_int), ("p_inf", ctypes.c_double)]
 
 
 class GMM(ctypes.Structure):
@@ -103,6 +103,7 @@ def load():
         L.dg_project_state.argtypes = [_vp, _vp, _vp, _vp]
         L.dg_detect_regions.argtypes = [_vp, _vp, ctypes.POINTER(GMM), _vp, _vp, _vp, _vp]
         L.dg_check_device.argtypes = [_vp, _vp]
+        L.dg_set_wait_limit.argtypes = [_vp, ctypes.c_int64, ctypes.c_int]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_launches_per_residual.argtypes = [_vp]
@@ -134,7 +135,7 @@ def make_params(p: dict, precision=0) -> Params:
     out.prandtl = float(p.get("prandtl", 0.72))
     out.prandtl_t = float(p.get("prandtl_t", 0.9))
     out.nodes = int(p.get("nodes", 0))
-    out.reserved = 0
+    out.fp64_divergence = int(p.get("fp64_divergence", 0))
     out.p_inf = float(p.get("p_inf", 0.0))
     for i, v in enumerate(p.get("inflow", (0.0, 1.0, 0.0, 0.0))):
         out.inflow[i] = v
@@ -354,6 +355,11 @@ class Solver:
         out = (ctypes.c_double * 5)()
         _check(load().dg_phase_bytes(self.h, out))
         return dict(zip(self.PHASES, list(out)))
+
+    def set_wait_limit(self, polls=0, stop_tile=-1):
+        """Poll budget of the bounded device-side waits (0: the default) and the stop-tile test
+        hook (-1: off); see dg_set_wait_limit."""
+        _check(load().dg_set_wait_limit(self.h, int(polls), int(stop_tile)))
 
     def check_device(self, stream=None):
         _check(load().dg_check_device(self.h, _stream_handle(stream)))

@@ -14,9 +14,12 @@ from paper_2403_05463_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-# Regression bounds per case, about 3x the measured FP32 error. The error is set by the
-# conditioning of the residual (largest for R_p = -c0^2 div u of divergence-free fields,
-# where c0^2 |u| |D| / |R_p| is 1e2..1e4); the 1e-6 target holds only where that is small.
+# Regression bounds per case of the plain FP32 path (every contraction in FP32), about 3x the
+# measured error. Its error is set by the conditioning of the residual: R_p = -c0^2 div u of a
+# nearly divergence-free field is a small difference of three directional derivatives, each
+# with FP32 rounding (measured on the 64^3 workload: the pressure row carries 2.6e-5 of the
+# 2.65e-5, and the error scales with c0^2). With the divergence in FP64 (fp64_divergence = 1,
+# box elements) the 1e-6 target is met and asserted below (TARGET).
 BOUNDS = {
     "tgv_4x4x4_n3": 3e-5, "wake_16x16x16_n4": 1e-6, "tgv_8x8x8_n5_slab30": 6e-6,
     "padapt_6x6x6_curved": 1.5e-5, "tgv_5x5x5_n1_vreman_llf": 1e-6, "tgv_5x5x5_n2_vreman_llf": 5e-6,
@@ -26,6 +29,10 @@ BOUNDS = {
     "padapt_5x5x5_kep": 5e-5, "wake_8x8x8_n4_kep": 1e-6,
     "channel_6x6x6_noslip": 1e-5, "channel_6x6x6_slip": 1e-5,
 }
+
+
+TARGET = 1e-6  # relative L2 residual error of the reduced-precision path (FP64 divergence)
+DIV64 = {"fp64_divergence": 1}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -204,3 +211,49 @@ def test_fp32_mixed_full_size_sampled():
     err = rel_l2(R[:, idx], Rx[:, idx])
     _record("mixed_64x64x64_n4_sampled", err)
     assert err <= BOUNDS["mixed_64x64x64_n4_sampled"]
+    S.set_params(dict(w.params, **DIV64))
+    R = S.residual(q).cpu().numpy()
+    err = rel_l2(R[:, idx], Rx[:, idx])
+    _record("mixed_64x64x64_n4_sampled_div64", err)
+    assert err <= TARGET, err
+
+
+@pytest.mark.parametrize("name,make", [
+    ("tgv_4x4x4_n3", lambda: wl.tgv_4x4x4_n3()),
+    ("wake_16x16x16_n4", lambda: wl.wake_16x16x16_n4()),
+    ("tgv_8x8x8_n5_slab30", lambda: wl.tgv_32x32x32_n5(n=8)),
+    ("tgv_6x6x6_n4", lambda: wl.tgv_4x4x4_n3(n_elem_dir=6, order=4)),
+])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp64_divergence_meets_the_target(name, make, precision):
+    # box elements: the divergence in FP64, the rest of the momentum fluxes in FP32 FMAs
+    # (precision 1) or 3xTF32 tensor-core contractions (precision 2)
+    w = make()
+    err = _fp32_error(w, params=dict(w.params, **DIV64), precision=precision)
+    _record(f"{name}_div64" + ("_tf32x3" if precision == 2 else ""), err)
+    assert err <= TARGET, err
+    assert err < _fp32_error(w, precision=precision)  # and it is the more accurate mode
+
+
+def test_fp64_divergence_every_order_mixed_flags():
+    for N in (1, 2, 3, 4, 5, 6, 7):
+        w = small_mixed(wl.tgv_4x4x4_n3(n_elem_dir=4, order=N), seed=40 + N)
+        p = dict(w.params, nu=1e-2, **DIV64)
+        err = _fp32_error(w, params=p)
+        _record(f"tgv_4x4x4_n{N}_mixed_flags_div64", err)
+        assert err <= TARGET, (N, err)
+
+
+def test_fp64_divergence_rk_steps():
+    w = wl.tgv_4x4x4_n3()
+    p = dict(w.params, **DIV64)
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    q0 = q.copy()
+    g = np.zeros_like(q)
+    qd, gd = to_dev(q), to_dev(g)
+    gpu_solver(w, precision=1, params=p).rk_step(qd, gd, w.dt, w.steps)
+    M.rk_step(q, g, w.dt, w.steps)
+    err = rel_l2(qd.cpu().numpy() - q0, q - q0)
+    _record("tgv_4x4x4_n3_rk3_10_steps_update_div64", err)
+    assert err <= TARGET, err
