@@ -334,6 +334,9 @@ struct dg_ctx {
   int n_mortar_all = 0;
   int32_t* mortar_ns = nullptr;     // mortar slots of NS elements (lifting)
   int n_mortar_ns = 0;
+  // both lists are sorted by mortar order: [mo_start[MO], mo_start[MO + 1]) holds order MO
+  int mortar_all_mo[MAXN + 2] = {};
+  int mortar_ns_mo[MAXN + 2] = {};
   std::vector<ElemConst> ec;
   std::vector<uint8_t> geo_kind;  // 0 axis-aligned box, 1 affine, 2 curved
   bool any_curved = false;
@@ -754,6 +757,19 @@ dg_status rebuild_flags(dg_ctx* c) {
   uint8_t* df;
   if ((st = dev_upload(c, "flag", c->flag, &df)) != DG_OK) return st;
   c->M.flag = df;
+  // group the mortar slots by mortar order (one launch per order, sized for its points)
+  auto by_order = [&](std::vector<int32_t>& v, int* start) {
+    auto mo = [&](int32_t es) {
+      const int64_t e = es / 6, nb = c->nb[es];
+      return (int)std::max(c->order[e], c->order[nb]);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](int32_t x, int32_t y) { return mo(x) < mo(y); });
+    for (int k = 0; k <= MAXN + 1; ++k) start[k] = 0;
+    for (int32_t es : v) ++start[mo(es) + 1];
+    for (int k = 1; k <= MAXN + 1; ++k) start[k] += start[k - 1];
+  };
+  by_order(mall, c->mortar_all_mo);
+  by_order(mns, c->mortar_ns_mo);
   if ((st = dev_upload(c, "mortar_all", mall, &c->mortar_all)) != DG_OK) return st;
   c->n_mortar_all = (int)mall.size();
   if ((st = dev_upload(c, "mortar_ns", mns, &c->mortar_ns)) != DG_OK) return st;
@@ -980,11 +996,9 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
         ++nl;
       }
     } else if (phase == 1 && c->n_mortar_ns) {
-      CU(launch_mortar_lift(M, c->mortar_ns, c->n_mortar_ns, s));
-      ++nl;
+      CU(launch_mortar_lift(M, c->mortar_ns, c->mortar_ns_mo, &nl, s));
     } else if (phase == 3 && c->n_mortar_all) {
-      CU(launch_mortar_flux(M, c->mortar_all, c->n_mortar_all, s));
-      ++nl;
+      CU(launch_mortar_flux(M, c->mortar_all, c->mortar_all_mo, &nl, s));
     } else if (phase == 2) {
       for (const Bucket& b : c->ns_buckets) {
         CU(launch_viscous_gl(M, b, q, s));
@@ -1034,10 +1048,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       }
       break;
     case 1:
-      if (c->n_mortar_ns) {
-        CU(launch_mortar_lift(M, c->mortar_ns, c->n_mortar_ns, s));
-        ++nl;
-      }
+      if (c->n_mortar_ns) CU(launch_mortar_lift(M, c->mortar_ns, c->mortar_ns_mo, &nl, s));
       break;
     case 2:
       for (const Bucket& b : c->ns_buckets) {
@@ -1046,10 +1057,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       }
       break;
     case 3:
-      if (c->n_mortar_all) {
-        CU(launch_mortar_flux(M, c->mortar_all, c->n_mortar_all, s));
-        ++nl;
-      }
+      if (c->n_mortar_all) CU(launch_mortar_flux(M, c->mortar_all, c->mortar_all_mo, &nl, s));
       break;
     default:
       for (const Bucket& b : c->all_buckets) {

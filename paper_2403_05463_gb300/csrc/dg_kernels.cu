@@ -445,16 +445,6 @@ __device__ __forceinline__ const double* proj_tab(const DevMesh& M, int Nh, int 
   return (M.nodes == 1 ? M.proj_g : M.proj) + (Nh * NP + Nl) * NP * NP;
 }
 
-// 2D tensor application on a face: dst[a + nd b] = sum T[a][aa] T[b][bb] src[aa + ns bb]
-__device__ __forceinline__ double tensor2(const double* T, int ns, int a, int b, const double* src) {
-  double s = 0.0;
-  for (int bb = 0; bb < ns; ++bb) {
-    double t = 0.0;
-    for (int aa = 0; aa < ns; ++aa) t += T[a * NP + aa] * src[aa + ns * bb];
-    s += T[b * NP + bb] * t;
-  }
-  return s;
-}
 
 __device__ __forceinline__ void node_metric(const DevMesh& M, int e, int64_t node, double Ja[9]) {
   if (M.ec[e].curved != 0.0) {
@@ -501,117 +491,180 @@ __device__ __forceinline__ double tv_load(const DevMesh& M, int c, int64_t slot)
   return M.precision == 1 ? (double)reinterpret_cast<const float*>(M.Tv)[slot * 3 + c] : M.Tv[c * M.tr_total + slot];
 }
 
-// loads my face field (nvar from `src` planes, stride tr_total) and S at my face nodes
-struct MortarSmem {
-  double mine[7][NP * NP];   // my trace at my order
-  double nbr[7][NP * NP];    // neighbour trace at its order
-  double mM[7][NP * NP];     // mine on the mortar
-  double nM[7][NP * NP];     // neighbour on the mortar (my coordinates)
-  double Sm[3][NP * NP];     // my S at my nodes
-  double SM[3][NP * NP];     // S on the mortar
-  double H[9][NP * NP];      // mortar result
+// ---------------------------------------------------------------------------------------
+// p-nonconforming faces: one warp per mortar side (element e, local face f)
+// ---------------------------------------------------------------------------------------
+// Launches are grouped by mortar order MO = max(N_e, N_nbr), so a warp's shared-memory planes
+// hold PS = (MO + 1)^2 values. Face fields go to the mortar and back with sum-factorised
+// tensor products (one direction at a time through a scratch plane), lanes over the points.
+constexpr int kMortarWarps = 4;  // warps (mortar sides) per block
+
+template <int MO>
+struct MortarW {
+  static constexpr int nM = MO + 1, PS = nM * nM;
+  static constexpr int LIFT_PLANES = 21;  // A[9] B[3] T[9]
+  static constexpr int FLUX_PLANES = 27;  // A[10] B[7] T[10]
 };
 
-__global__ void k_mortar_lift(DevMesh M, const int32_t* __restrict__ slots, int count) {
-  __shared__ MortarSmem sm;
-  if (blockIdx.x >= count) return;
-  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
-  const FaceLink L = M.link[es];
-  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
-  const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
-  const int t = threadIdx.x;
-  if (t < nm * nm) {
-    double Sv[3];
-    face_metric(M, e, f, nm, t % nm, t / nm, Sv);
-    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = Sv[k];
-    for (int c = 0; c < 3; ++c) sm.mine[c][t] = tq_load(M, 1 + c, M.tr_off[e] + f * nm * nm + t);
-  }
-  if (t < nn * nn)
-    for (int c = 0; c < 3; ++c) sm.nbr[c][t] = tq_load(M, 1 + c, M.tr_off[L.nbr] + L.nface * nn * nn + t);
-  __syncthreads();
-  if (t < nM * nM) {
-    const int a = t % nM, b = t / nM;
-    const double* Im = interp_tab(M, Nm, Mo);
-    const double* In = interp_tab(M, Nn, Mo);
-    for (int c = 0; c < 3; ++c) sm.mM[c][t] = tensor2(Im, nm, a, b, sm.mine[c]);
-    for (int k = 0; k < 3; ++k) sm.SM[k][t] = tensor2(Im, nm, a, b, sm.Sm[k]);
-    int a0, b0;
-    fwd_orient(L.orient, Mo, a, b, a0, b0);  // (a, b) are neighbour mortar coordinates here
-    for (int c = 0; c < 3; ++c) sm.nM[c][a0 + nM * b0] = tensor2(In, nn, a, b, sm.nbr[c]);
-  }
-  __syncthreads();
-  if (t < nM * nM)
-    for (int c = 0; c < 3; ++c) {
-      double us = 0.5 * (sm.mM[c][t] + sm.nM[c][t]);
-      for (int k = 0; k < 3; ++k) sm.H[c * 3 + k][t] = us * sm.SM[k][t];
+// dst = (T x T) src for nv planes of stride PS: src is ns x ns, dst nd x nd, T the 1D table
+// (row a: T[a * NP + aa]). tmp holds nv planes of nd x ns. When `o` >= 0 the result at
+// (a, b), coordinates of the neighbour's mortar, is stored at my coordinates fwd_orient(o).
+// src and dst may be the same planes (src is read only in the first step). ns == nd with T the
+// identity is a (permuted) copy.
+__device__ __forceinline__ void tensor2_warp(const double* __restrict__ T, bool identity, int ns, int nd, int nv,
+                                             const double* src, double* tmp, double* dst, int PS, int o, int Mo,
+                                             int lane) {
+  if (identity) {
+    for (int idx = lane; idx < nv * nd * nd; idx += 32) {
+      const int v = idx / (nd * nd), r = idx % (nd * nd);
+      tmp[v * PS + r] = src[v * PS + r];
     }
-  __syncthreads();
-  if (t < nm * nm) {
-    const double* P = proj_tab(M, Mo, Nm);
-    const int a = t % nm, b = t / nm;
-    for (int ck = 0; ck < 9; ++ck)
-      M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = tensor2(P, nM, a, b, sm.H[ck]);
+  } else {
+    for (int idx = lane; idx < nv * nd * ns; idx += 32) {
+      const int v = idx / (nd * ns), r = idx % (nd * ns), a = r % nd, bb = r / nd;
+      const double* Ta = T + a * NP;
+      const double* sv = src + v * PS + ns * bb;
+      double acc = 0.0;
+      for (int aa = 0; aa < ns; ++aa) acc = fma(__ldg(Ta + aa), sv[aa], acc);
+      tmp[v * PS + r] = acc;
+    }
   }
+  __syncwarp();
+  for (int idx = lane; idx < nv * nd * nd; idx += 32) {
+    const int v = idx / (nd * nd), r = idx % (nd * nd), a = r % nd, b = r / nd;
+    double acc;
+    if (identity) {
+      acc = tmp[v * PS + r];
+    } else {
+      const double* Tb = T + b * NP;
+      const double* tv = tmp + v * PS + a;
+      acc = 0.0;
+      for (int bb = 0; bb < ns; ++bb) acc = fma(__ldg(Tb + bb), tv[nd * bb], acc);
+    }
+    int dr = r;
+    if (o >= 0) {
+      int a0, b0;
+      fwd_orient(o, Mo, a, b, a0, b0);
+      dr = a0 + nd * b0;
+    }
+    dst[v * PS + dr] = acc;
+  }
+  __syncwarp();
 }
 
-__global__ void k_mortar_flux(DevMesh M, const int32_t* __restrict__ slots, int count) {
-  __shared__ MortarSmem sm;
-  if (blockIdx.x >= count) return;
-  const int es = slots[blockIdx.x], e = es / 6, f = es % 6;
+template <int MO>
+static size_t mortar_smem(bool flux) {
+  return sizeof(double) * kMortarWarps * MortarW<MO>::PS * (flux ? MortarW<MO>::FLUX_PLANES : MortarW<MO>::LIFT_PLANES);
+}
+
+// Projected BR1 lifting data of an NS element's mortar face: u*_c S_k on the mortar
+// (u* = the average of both sides' interpolated velocity traces, S my interpolated face
+// metric), L2-projected to my order, [9][tr_total] at my trace slots.
+template <int MO>
+__global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_lift_w(DevMesh M, const int32_t* __restrict__ slots,
+                                                                      int count) {
+  using W = MortarW<MO>;
+  constexpr int nM = W::nM, PS = W::PS;
+  extern __shared__ double smd[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * kMortarWarps + warp;
+  if (item >= count) return;  // the whole warp leaves together
+  double* A = smd + warp * W::LIFT_PLANES * PS;
+  double* B = A + 9 * PS;
+  double* T = B + 3 * PS;
+  const int es = slots[item], e = es / 6, f = es % 6;
   const FaceLink L = M.link[es];
-  const int Nm = M.order[e], Nn = M.order[L.nbr], Mo = Nm > Nn ? Nm : Nn;
-  const int nm = Nm + 1, nn = Nn + 1, nM = Mo + 1;
-  const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
-  const int t = threadIdx.x;
-  // planes 0..3: q, 4..6: outward viscous traces
-  if (t < nm * nm) {
+  const int Nm = M.order[e], Nn = M.order[L.nbr];
+  const int nm = Nm + 1, nn = Nn + 1;
+  // my velocity trace (planes 0..2) and face metric (3..5), the neighbour's velocity trace
+  for (int t = lane; t < nm * nm; t += 32) {
     double Sv[3];
     face_metric(M, e, f, nm, t % nm, t / nm, Sv);
-    for (int k = 0; k < 3; ++k) sm.Sm[k][t] = Sv[k];
     const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
-    for (int v = 0; v < 4; ++v) sm.mine[v][t] = tq_load(M, v, s0);
-    for (int c = 0; c < 3; ++c) sm.mine[4 + c][t] = vm ? tv_load(M, c, s0) : 0.0;
+    for (int c = 0; c < 3; ++c) {
+      A[c * PS + t] = tq_load(M, 1 + c, s0);
+      A[(3 + c) * PS + t] = Sv[c];
+    }
   }
-  if (t < nn * nn) {
+  for (int t = lane; t < nn * nn; t += 32) {
     const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
-    for (int v = 0; v < 4; ++v) sm.nbr[v][t] = tq_load(M, v, s1);
-    for (int c = 0; c < 3; ++c) sm.nbr[4 + c][t] = vn ? tv_load(M, c, s1) : 0.0;
+    for (int c = 0; c < 3; ++c) B[c * PS + t] = tq_load(M, 1 + c, s1);
   }
-  __syncthreads();
-  if (t < nM * nM) {
-    const int a = t % nM, b = t / nM;
-    const double* Im = interp_tab(M, Nm, Mo);
-    const double* In = interp_tab(M, Nn, Mo);
-    for (int v = 0; v < 7; ++v) sm.mM[v][t] = tensor2(Im, nm, a, b, sm.mine[v]);
-    for (int k = 0; k < 3; ++k) sm.SM[k][t] = tensor2(Im, nm, a, b, sm.Sm[k]);
-    int a0, b0;
-    fwd_orient(L.orient, Mo, a, b, a0, b0);
-    for (int v = 0; v < 7; ++v) sm.nM[v][a0 + nM * b0] = tensor2(In, nn, a, b, sm.nbr[v]);
+  __syncwarp();
+  tensor2_warp(interp_tab(M, Nm, MO), nm == nM, nm, nM, 6, A, T, A, PS, -1, MO, lane);
+  tensor2_warp(interp_tab(M, Nn, MO), nn == nM, nn, nM, 3, B, T, B, PS, L.orient, MO, lane);
+  for (int t = lane; t < PS; t += 32)
+    for (int c = 0; c < 3; ++c) {
+      const double us = 0.5 * (A[c * PS + t] + B[c * PS + t]);
+      for (int k = 0; k < 3; ++k) T[(c * 3 + k) * PS + t] = us * A[(3 + k) * PS + t];
+    }
+  __syncwarp();
+  // project to my order (A is free: it takes the first step), then store
+  tensor2_warp(proj_tab(M, MO, Nm), nm == nM, nM, nm, 9, T, A, T, PS, -1, MO, lane);
+  for (int t = lane; t < nm * nm; t += 32)
+    for (int ck = 0; ck < 9; ++ck) M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = T[ck * PS + t];
+}
+
+// Projected total numerical flux of a mortar face: (F_e* - F_v*) . S on the mortar (Roe/LLF of
+// both sides' interpolated states; the BR1 average of both sides' interpolated outward viscous
+// traces, or the NS side alone on an NS/Euler face with the one-sided choice), L2-projected to
+// my order, [4][tr_total] at my trace slots.
+template <int MO>
+__global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_flux_w(DevMesh M, const int32_t* __restrict__ slots,
+                                                                      int count) {
+  using W = MortarW<MO>;
+  constexpr int nM = W::nM, PS = W::PS;
+  extern __shared__ double smd[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * kMortarWarps + warp;
+  if (item >= count) return;
+  double* A = smd + warp * W::FLUX_PLANES * PS;
+  double* B = A + 10 * PS;
+  double* T = B + 7 * PS;
+  const int es = slots[item], e = es / 6, f = es % 6;
+  const FaceLink L = M.link[es];
+  const int Nm = M.order[e], Nn = M.order[L.nbr];
+  const int nm = Nm + 1, nn = Nn + 1;
+  const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
+  // planes 0..3 q, 4..6 outward viscous traces, 7..9 (mine only) the face metric
+  for (int t = lane; t < nm * nm; t += 32) {
+    double Sv[3];
+    face_metric(M, e, f, nm, t % nm, t / nm, Sv);
+    const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
+    for (int v = 0; v < 4; ++v) A[v * PS + t] = tq_load(M, v, s0);
+    for (int c = 0; c < 3; ++c) {
+      A[(4 + c) * PS + t] = vm ? tv_load(M, c, s0) : 0.0;
+      A[(7 + c) * PS + t] = Sv[c];
+    }
   }
-  __syncthreads();
-  if (t < nM * nM) {
-    const double Sv[3] = {sm.SM[0][t], sm.SM[1][t], sm.SM[2][t]};
+  for (int t = lane; t < nn * nn; t += 32) {
+    const int64_t s1 = M.tr_off[L.nbr] + L.nface * nn * nn + t;
+    for (int v = 0; v < 4; ++v) B[v * PS + t] = tq_load(M, v, s1);
+    for (int c = 0; c < 3; ++c) B[(4 + c) * PS + t] = vn ? tv_load(M, c, s1) : 0.0;
+  }
+  __syncwarp();
+  tensor2_warp(interp_tab(M, Nm, MO), nm == nM, nm, nM, 10, A, T, A, PS, -1, MO, lane);
+  tensor2_warp(interp_tab(M, Nn, MO), nn == nM, nn, nM, 7, B, T, B, PS, L.orient, MO, lane);
+  // F_v* . S = wm (mine) - wp (neighbour's outward): the average, or the NS side alone
+  const bool one = M.mixed_face == 1 && vm != vn;
+  const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;
+  for (int t = lane; t < PS; t += 32) {
+    const double Sv[3] = {A[7 * PS + t], A[8 * PS + t], A[9 * PS + t]};
     const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
     const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
     double qm[4], qp[4], Fs[4];
     for (int v = 0; v < 4; ++v) {
-      qm[v] = sm.mM[v][t];
-      qp[v] = sm.nM[v][t];
+      qm[v] = A[v * PS + t];
+      qp[v] = B[v * PS + t];
     }
     flux_full(qm, qp, nh, M.c0sq, M.riemann, Fs);
-    // F_v* . S = wm (mine) - wp (neighbour's outward): the average, or the NS side alone
-    const bool one = M.mixed_face == 1 && vm != vn;
-    const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;
-    sm.H[0][t] = s * Fs[0];
-    for (int c = 0; c < 3; ++c) sm.H[1 + c][t] = s * Fs[1 + c] - (wm * sm.mM[4 + c][t] - wp * sm.nM[4 + c][t]);
+    T[t] = s * Fs[0];
+    for (int c = 0; c < 3; ++c) T[(1 + c) * PS + t] = s * Fs[1 + c] - (wm * A[(4 + c) * PS + t] - wp * B[(4 + c) * PS + t]);
   }
-  __syncthreads();
-  if (t < nm * nm) {
-    const double* P = proj_tab(M, Mo, Nm);
-    const int a = t % nm, b = t / nm;
-    for (int v = 0; v < 4; ++v)
-      M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = tensor2(P, nM, a, b, sm.H[v]);
-  }
+  __syncwarp();
+  tensor2_warp(proj_tab(M, MO, Nm), nm == nM, nM, nm, 4, T, A, T, PS, -1, MO, lane);
+  for (int t = lane; t < nm * nm; t += 32)
+    for (int v = 0; v < 4; ++v) M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = T[v * PS + t];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -775,8 +828,24 @@ static cudaError_t prep_n() {
   return cudaSuccess;
 }
 
+template <int MO>
+static cudaError_t prep_mortar() {
+  cudaError_t r = cudaFuncSetAttribute(k_mortar_lift_w<MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)mortar_smem<MO>(false));
+  if (r != cudaSuccess) return r;
+  return cudaFuncSetAttribute(k_mortar_flux_w<MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mortar_smem<MO>(true));
+}
+
 cudaError_t prepare_kernels() {
   cudaError_t r;
+  if ((r = prep_mortar<1>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<2>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<3>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<4>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<5>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<6>()) != cudaSuccess) return r;
+  if ((r = prep_mortar<7>()) != cudaSuccess) return r;
   if ((r = prep_n<1>()) != cudaSuccess) return r;
   if ((r = prep_n<2>()) != cudaSuccess) return r;
   if ((r = prep_n<3>()) != cudaSuccess) return r;
@@ -854,16 +923,34 @@ cudaError_t launch_project_state(const DevMesh& M, const int8_t* old_order, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  k_mortar_lift<<<count, 64, 0, s>>>(M, slots, count);
+// slots sorted by mortar order, mo_start[MO] .. mo_start[MO + 1] the slots of order MO
+static cudaError_t launch_mortar(bool flux, const DevMesh& M, const int32_t* slots, const int* mo_start, int* nlaunch,
+                                 cudaStream_t s) {
+  for (int mo = 1; mo <= MAXN; ++mo) {
+    const int count = mo_start[mo + 1] - mo_start[mo];
+    if (count <= 0) continue;
+    const int32_t* sl = slots + mo_start[mo];
+    const unsigned grid = (unsigned)((count + kMortarWarps - 1) / kMortarWarps);
+    DG_SWITCH_N(mo, {
+      const size_t sm = mortar_smem<NN>(flux);
+      if (flux)
+        k_mortar_flux_w<NN><<<grid, 32 * kMortarWarps, sm, s>>>(M, sl, count);
+      else
+        k_mortar_lift_w<NN><<<grid, 32 * kMortarWarps, sm, s>>>(M, sl, count);
+    });
+    if (nlaunch) ++*nlaunch;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, int count, cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  k_mortar_flux<<<count, 64, 0, s>>>(M, slots, count);
-  return cudaGetLastError();
+cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, const int* mo_start, int* nlaunch,
+                               cudaStream_t s) {
+  return launch_mortar(false, M, slots, mo_start, nlaunch, s);
+}
+
+cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, const int* mo_start, int* nlaunch,
+                               cudaStream_t s) {
+  return launch_mortar(true, M, slots, mo_start, nlaunch, s);
 }
 
 cudaError_t launch_node_coords(const DevMesh& M, const double* gn, int gdeg, const Bucket& b, double* xyz,

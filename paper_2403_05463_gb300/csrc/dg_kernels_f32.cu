@@ -471,10 +471,10 @@ struct TmaSmem32 {
   // work per element: F [3 n3] flux deviations, QH/QL [n3] hi/lo state, T [6 n2] face terms
   // (split form on curved elements: F holds the state deviations and the three metric vectors,
   // 4 n3 float4, so everything after it moves by 16 n3)
-  // (tensor-core contraction: C [3][n3] float4, the three directions' D contractions, after T)
+  // (tensor-core contraction: each item writes its D contraction over the flux rows it read, so
+  // F holds the three directions' results afterwards and no extra tile is needed)
   static constexpr int FB = KEPC ? 64 * n3 : 48 * n3;
-  static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, wC = FB + 32 * n3 + 96 * n2,
-                       work_elem = wC + (TCX ? 48 * n3 : 0);
+  static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, work_elem = FB + 32 * n3 + 96 * n2;
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
 };
@@ -904,13 +904,21 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
       QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
       QL4[p] = make_float4(l[0], l[1], l[2], l[3]);
       float fl[4][3];
+      if (div64) {  // the U_c du_k part goes through the FP64 divergence
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        fl[0][k] = c0sq * dq[1 + k];
+        for (int k = 0; k < 3; ++k) {
+          fl[0][k] = c0sq * dq[1 + k];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          fl[1 + c][k] = (div64 ? 0.f : qr32[1 + c] * dq[1 + k]) + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) +
-                         (c == k ? dq[0] : 0.f);
+          for (int c = 0; c < 3; ++c) fl[1 + c][k] = dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          fl[0][k] = c0sq * dq[1 + k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            fl[1 + c][k] = qr32[1 + c] * dq[1 + k] + dq[1 + c] * (qr32[1 + k] + dq[1 + k]) + (c == k ? dq[0] : 0.f);
+        }
       }
       if (KEP) F4[p] = make_float4(dq[0], dq[1], dq[2], dq[3]);
       if (GEO == 0) {
@@ -1035,8 +1043,10 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
       for (int item = tid >> 5; item < ITEMS; item += NC / 32) {
         const int le2 = item / (3 * TR), rem = item % (3 * TR), d = rem / TR, rt = rem % TR;
         if (tile * EPB + le2 >= B.count) continue;
-        const float* Fs = reinterpret_cast<const float*>(W + le2 * P::work_elem + P::wF) + d * n3 * 4;
-        float4* Cd = reinterpret_cast<float4*>(W + le2 * P::work_elem + P::wC) + d * n3;
+        // C overwrites the F rows of this item in place: the item's A operands (all of its rows
+        // and positions m) are in registers before its mma, and no other item reads these rows
+        float* Fs = reinterpret_cast<float*>(W + le2 * P::work_elem + P::wF) + d * n3 * 4;
+        float4* Cd = reinterpret_cast<float4*>(Fs);
         // node of (line, position m) along direction d: base(line) + m * stride, line = a + n b
         // over the other two indices; this lane's rows are r0 = 16 rt + gq and r0 + 8, i.e.
         // lines l0 = r0 / 4 and l0 + 2 with variable v = gq % 4
@@ -1224,7 +1234,7 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
     consumer_sync(NC);
     // ---- assembly and update ------------------------------------------------------------
     if (TC && active) {
-      const float4* Cp = reinterpret_cast<const float4*>(W + le * P::work_elem + P::wC);
+      const float4* Cp = reinterpret_cast<const float4*>(W + le * P::work_elem + P::wF);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const float4 c4 = Cp[d * n3 + p];
