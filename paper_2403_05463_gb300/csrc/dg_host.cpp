@@ -337,6 +337,8 @@ struct dg_ctx {
   // both lists are sorted by mortar order: [mo_start[MO], mo_start[MO + 1]) holds order MO
   int mortar_all_mo[MAXN + 2] = {};
   int mortar_ns_mo[MAXN + 2] = {};
+  int32_t* mortar_face = nullptr;   // one slot per mortar face: the side of the larger order
+  int mortar_face_mo[MAXN + 2] = {};
   std::vector<ElemConst> ec;
   std::vector<uint8_t> geo_kind;  // 0 axis-aligned box, 1 affine, 2 curved
   bool any_curved = false;
@@ -770,6 +772,11 @@ dg_status rebuild_flags(dg_ctx* c) {
   };
   by_order(mall, c->mortar_all_mo);
   by_order(mns, c->mortar_ns_mo);
+  std::vector<int32_t> mface;
+  for (int32_t es : mall)
+    if (c->order[es / 6] > c->order[c->nb[es]]) mface.push_back(es);
+  by_order(mface, c->mortar_face_mo);
+  if ((st = dev_upload(c, "mortar_face", mface, &c->mortar_face)) != DG_OK) return st;
   if ((st = dev_upload(c, "mortar_all", mall, &c->mortar_all)) != DG_OK) return st;
   c->n_mortar_all = (int)mall.size();
   if ((st = dev_upload(c, "mortar_ns", mns, &c->mortar_ns)) != DG_OK) return st;
@@ -998,7 +1005,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
     } else if (phase == 1 && c->n_mortar_ns) {
       CU(launch_mortar_lift(M, c->mortar_ns, c->mortar_ns_mo, &nl, s));
     } else if (phase == 3 && c->n_mortar_all) {
-      CU(launch_mortar_flux(M, c->mortar_all, c->mortar_all_mo, &nl, s));
+      CU(launch_mortar_flux(M, c->mortar_face, c->mortar_face_mo, &nl, s));
     } else if (phase == 2) {
       for (const Bucket& b : c->ns_buckets) {
         CU(launch_viscous_gl(M, b, q, s));
@@ -1057,7 +1064,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       }
       break;
     case 3:
-      if (c->n_mortar_all) CU(launch_mortar_flux(M, c->mortar_all, c->mortar_all_mo, &nl, s));
+      if (c->n_mortar_all) CU(launch_mortar_flux(M, c->mortar_face, c->mortar_face_mo, &nl, s));
       break;
     default:
       for (const Bucket& b : c->all_buckets) {

@@ -158,7 +158,9 @@ cudaError_t launch_traces(const DevMesh& M, const Bucket& b, const double* q, in
 cudaError_t launch_project_state(const DevMesh& M, const int8_t* old_order, const int64_t* old_off, int64_t total_old,
                                  const double* qo, double* qn, cudaStream_t s);
 // mortar kernels of the incompressible form: slots sorted by mortar order, mo_start[MO] ..
-// mo_start[MO + 1] (host array of MAXN + 2) those of order MO; *nlaunch counts the launches
+// mo_start[MO + 1] (host array of MAXN + 2) those of order MO; *nlaunch counts the launches.
+// Lifting: one slot per mortar side of an NS element. Flux: one slot per mortar face, the side
+// of the larger order (the kernel writes both sides).
 cudaError_t launch_mortar_lift(const DevMesh& M, const int32_t* slots, const int* mo_start, int* nlaunch,
                                cudaStream_t s);
 cudaError_t launch_mortar_flux(const DevMesh& M, const int32_t* slots, const int* mo_start, int* nlaunch,

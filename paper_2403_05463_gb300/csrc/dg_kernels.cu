@@ -605,10 +605,15 @@ __global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_lift_w(DevMesh M, 
     for (int ck = 0; ck < 9; ++ck) M.LU[ck * M.tr_total + M.tr_off[e] + f * nm * nm + t] = T[ck * PS + t];
 }
 
-// Projected total numerical flux of a mortar face: (F_e* - F_v*) . S on the mortar (Roe/LLF of
-// both sides' interpolated states; the BR1 average of both sides' interpolated outward viscous
-// traces, or the NS side alone on an NS/Euler face with the one-sided choice), L2-projected to
-// my order, [4][tr_total] at my trace slots.
+// Projected total numerical flux of a mortar face, once per face: the warp takes the side of
+// the larger order (element e, its order is the mortar order MO), evaluates (F_e* - F_v*) . S on
+// the mortar in e's face coordinates (Roe/LLF of both sides' states, the neighbour's interpolated
+// to the mortar; the BR1 average of both sides' outward viscous traces, or the NS side alone on
+// an NS/Euler face with the one-sided choice), stores it for e (its own order: no projection)
+// and, with the sign reversed, L2-projected to the neighbour's order in the neighbour's face
+// coordinates: seen from the neighbour the states swap and S turns, F*(q+, q-, -n) = -F*(q-, q+, n)
+// for Roe and LLF and the viscous average changes sign, so its value is -H. [4][tr_total] at
+// both sides' trace slots.
 template <int MO>
 __global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_flux_w(DevMesh M, const int32_t* __restrict__ slots,
                                                                       int count) {
@@ -623,14 +628,14 @@ __global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_flux_w(DevMesh M, 
   double* T = B + 7 * PS;
   const int es = slots[item], e = es / 6, f = es % 6;
   const FaceLink L = M.link[es];
-  const int Nm = M.order[e], Nn = M.order[L.nbr];
-  const int nm = Nm + 1, nn = Nn + 1;
+  const int Nn = M.order[L.nbr], nn = Nn + 1;  // M.order[e] == MO
   const bool vm = M.flag[e] != 0, vn = L.nflag != 0;
-  // planes 0..3 q, 4..6 outward viscous traces, 7..9 (mine only) the face metric
-  for (int t = lane; t < nm * nm; t += 32) {
+  // planes 0..3 q, 4..6 outward viscous traces, 7..9 (mine only) the face metric; mine is at the
+  // mortar order already
+  for (int t = lane; t < PS; t += 32) {
     double Sv[3];
-    face_metric(M, e, f, nm, t % nm, t / nm, Sv);
-    const int64_t s0 = M.tr_off[e] + f * nm * nm + t;
+    face_metric(M, e, f, nM, t % nM, t / nM, Sv);
+    const int64_t s0 = M.tr_off[e] + f * PS + t;
     for (int v = 0; v < 4; ++v) A[v * PS + t] = tq_load(M, v, s0);
     for (int c = 0; c < 3; ++c) {
       A[(4 + c) * PS + t] = vm ? tv_load(M, c, s0) : 0.0;
@@ -643,28 +648,41 @@ __global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_flux_w(DevMesh M, 
     for (int c = 0; c < 3; ++c) B[(4 + c) * PS + t] = vn ? tv_load(M, c, s1) : 0.0;
   }
   __syncwarp();
-  tensor2_warp(interp_tab(M, Nm, MO), nm == nM, nm, nM, 10, A, T, A, PS, -1, MO, lane);
   tensor2_warp(interp_tab(M, Nn, MO), nn == nM, nn, nM, 7, B, T, B, PS, L.orient, MO, lane);
   // F_v* . S = wm (mine) - wp (neighbour's outward): the average, or the NS side alone
   const bool one = M.mixed_face == 1 && vm != vn;
   const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;
+  const int64_t my0 = M.tr_off[e] + f * PS;
   for (int t = lane; t < PS; t += 32) {
     const double Sv[3] = {A[7 * PS + t], A[8 * PS + t], A[9 * PS + t]};
     const double s = sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
     const double nh[3] = {Sv[0] / s, Sv[1] / s, Sv[2] / s};
-    double qm[4], qp[4], Fs[4];
+    double qm[4], qp[4], Fs[4], H[4];
     for (int v = 0; v < 4; ++v) {
       qm[v] = A[v * PS + t];
       qp[v] = B[v * PS + t];
     }
     flux_full(qm, qp, nh, M.c0sq, M.riemann, Fs);
-    T[t] = s * Fs[0];
-    for (int c = 0; c < 3; ++c) T[(1 + c) * PS + t] = s * Fs[1 + c] - (wm * A[(4 + c) * PS + t] - wp * B[(4 + c) * PS + t]);
+    H[0] = s * Fs[0];
+    for (int c = 0; c < 3; ++c) H[1 + c] = s * Fs[1 + c] - (wm * A[(4 + c) * PS + t] - wp * B[(4 + c) * PS + t]);
+    for (int v = 0; v < 4; ++v) {
+      M.LH[v * M.tr_total + my0 + t] = H[v];
+      T[v * PS + t] = H[v];
+    }
   }
   __syncwarp();
-  tensor2_warp(proj_tab(M, MO, Nm), nm == nM, nM, nm, 4, T, A, T, PS, -1, MO, lane);
-  for (int t = lane; t < nm * nm; t += 32)
-    for (int v = 0; v < 4; ++v) M.LH[v * M.tr_total + M.tr_off[e] + f * nm * nm + t] = T[v * PS + t];
+  // the neighbour's side: -H at its mortar coordinates (a1, b1), i.e. at my fwd_orient(a1, b1)
+  for (int idx = lane; idx < 4 * PS; idx += 32) {
+    const int v = idx / PS, r = idx % PS;
+    int a0, b0;
+    fwd_orient(L.orient, MO, r % nM, r / nM, a0, b0);
+    A[v * PS + r] = -T[v * PS + a0 + nM * b0];
+  }
+  __syncwarp();
+  tensor2_warp(proj_tab(M, MO, Nn), nn == nM, nM, nn, 4, A, B, A, PS, -1, MO, lane);
+  const int64_t nb0 = M.tr_off[L.nbr] + L.nface * nn * nn;
+  for (int t = lane; t < nn * nn; t += 32)
+    for (int v = 0; v < 4; ++v) M.LH[v * M.tr_total + nb0 + t] = A[v * PS + t];
 }
 
 // ---------------------------------------------------------------------------------------

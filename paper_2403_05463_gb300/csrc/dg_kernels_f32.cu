@@ -775,13 +775,12 @@ struct InvMinBlocks {
 template <int N, int GEO, int MODE, int E, int VOL>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
-  constexpr bool KEP = VOL == 1, TC = VOL == 2;
-  // With M.div64 on box elements (standard form, FP32 or tensor-core contraction): the divergence
-  // S = sum_d Ja_dd D_d u_d is taken in FP64 from the staged FP64 state. It gives the pressure row
-  // (-c0^2 S) and the U_c du_d part of the momentum fluxes (U_c S); the FP32 contractions carry
-  // only the rest of the momentum fluxes.
-  constexpr bool DIV64_OK = GEO == 0 && VOL != 1;
-  const bool div64 = DIV64_OK && M.div64 != 0;
+  // VOL 3 / 4: VOL 0 / 2 on box elements with the divergence S = sum_d Ja_dd D_d u_d taken in FP64
+  // from the staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the
+  // momentum fluxes (U_c S); the FP32 (or tensor-core) contractions carry only the rest of the
+  // momentum fluxes.
+  constexpr bool KEP = VOL == 1, TC = VOL == 2 || VOL == 4;
+  constexpr bool div64 = GEO == 0 && (VOL == 3 || VOL == 4);
   using S = Tile<N, E>;
   using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
@@ -1014,7 +1013,7 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) JR[1 + c] += rvp[c];
-      if (DIV64_OK && div64) {
+      if (div64) {
         // S = sum_d Ja_dd (D u_d)_i in FP64 (the pressure row is a small difference of the three
         // directional derivatives, so FP32 rounding of each would be amplified by c0^2 / |R_p|)
         const int str[3] = {1, n, n2};
@@ -1552,6 +1551,15 @@ static size_t visc_smem32() {
   return ViscSmem32<N, GEO>::bytes;
 }
 
+// the FP64-divergence variants (VOL 3, 4) exist for box elements only
+template <int N, int E, int VOL>
+static cudaError_t prep_inv_div() {
+  const int ps = (int)TmaSmem32<N, E, false, VOL == 4>::bytes;
+  cudaError_t r;
+  if ((r = cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RESIDUAL, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)) != cudaSuccess) return r;
+  return cudaFuncSetAttribute(k_inviscid32t<N, 0, MODE_RK, E, VOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+}
+
 template <int N, int E, int VOL>
 static cudaError_t prep_inv() {
   const int ps = (int)TmaSmem32<N, E, false, VOL == 2>::bytes, pc = (int)TmaSmem32<N, E, VOL == 1, VOL == 2>::bytes;
@@ -1579,6 +1587,9 @@ static cudaError_t prep32_n() {
   if ((r = prep_inv<N, Shape<N>::EPB, 0>()) != cudaSuccess) return r;
   if ((r = prep_inv<N, Shape<N>::EPB, 1>()) != cudaSuccess) return r;
   if ((r = prep_inv<N, Shape<N>::EPB, 2>()) != cudaSuccess) return r;
+  if ((r = prep_inv_div<N, Shape<N>::EPB, 3>()) != cudaSuccess) return r;
+  if ((r = prep_inv_div<N, Shape<N>::EPB, 4>()) != cudaSuccess) return r;
+  if ((r = prep_inv_div<N, AltEPB<N>::value, 3>()) != cudaSuccess) return r;
   return prep_inv<N, AltEPB<N>::value, 0>();
 }
 
@@ -1652,7 +1663,7 @@ template <int N, int GEO, int MODE, int E, int VOL>
 static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                                int stage, int write_tr, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
-  const size_t sm = TmaSmem32<N, E, VOL == 1 && GEO == 2, VOL == 2>::bytes;
+  const size_t sm = TmaSmem32<N, E, VOL == 1 && GEO == 2, VOL == 2 || VOL == 4>::bytes;
   if (per_sm < 0) {
     cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inviscid32t<N, GEO, MODE, E, VOL>,
                                                                   Tile<N, E>::threads + 32, sm);
@@ -1682,6 +1693,15 @@ static cudaError_t launch_inv_shape(const DevMesh& M, const Bucket& b, const dou
   return launch_pipe<N, 2, MODE_RK, E, VOL>(M, b, q, out, g, stage, write_tr, s);
 }
 
+// box buckets with the FP64 divergence (VOL 3 from 0, 4 from 2); other buckets run VOL 0 or 2
+template <int N, int E, int VOL>
+static cudaError_t launch_inv_div(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
+                                  int mode, int stage, int write_tr, cudaStream_t s) {
+  if (b.geo != 0) return launch_inv_shape<N, E, VOL == 3 ? 0 : 2>(M, b, q, out, g, mode, stage, write_tr, s);
+  if (mode == MODE_RESIDUAL) return launch_pipe<N, 0, MODE_RESIDUAL, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+  return launch_pipe<N, 0, MODE_RK, E, VOL>(M, b, q, out, g, stage, write_tr, s);
+}
+
 int tile_epb32(int N, int alt) {
   switch (N) {
     case 1: return alt ? AltEPB<1>::value : Shape<1>::EPB;
@@ -1703,8 +1723,15 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
     // the split form and the tensor-core contraction are built for the default tile shape; the
     // split form's two-point sums are no plain contraction and stay on the FP32 pipe
     if (M.split == 1) return launch_inv_shape<NN, Shape<NN>::EPB, 1>(M, b, q, out, g, mode, stage, write_tr, s);
-    if (M.tc) return launch_inv_shape<NN, Shape<NN>::EPB, 2>(M, b, q, out, g, mode, stage, write_tr, s);
-    if (b.tile_alt) return launch_inv_shape<NN, AltEPB<NN>::value, 0>(M, b, q, out, g, mode, stage, write_tr, s);
+    if (M.tc) {
+      if (M.div64) return launch_inv_div<NN, Shape<NN>::EPB, 4>(M, b, q, out, g, mode, stage, write_tr, s);
+      return launch_inv_shape<NN, Shape<NN>::EPB, 2>(M, b, q, out, g, mode, stage, write_tr, s);
+    }
+    if (b.tile_alt) {
+      if (M.div64) return launch_inv_div<NN, AltEPB<NN>::value, 3>(M, b, q, out, g, mode, stage, write_tr, s);
+      return launch_inv_shape<NN, AltEPB<NN>::value, 0>(M, b, q, out, g, mode, stage, write_tr, s);
+    }
+    if (M.div64) return launch_inv_div<NN, Shape<NN>::EPB, 3>(M, b, q, out, g, mode, stage, write_tr, s);
     return launch_inv_shape<NN, Shape<NN>::EPB, 0>(M, b, q, out, g, mode, stage, write_tr, s);
   });
   return cudaSuccess;
