@@ -230,7 +230,11 @@ dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double* out_host, vo
  * tile (the default ~256-node tile or the alternative: half of it for orders 1..4, two
  * elements for orders 5, 6) and the resident blocks per SM (all that fit, 1 or 2); for the
  * viscous pass on box/affine elements the pipelined (bulk-copy) kernel at those block counts
- * or the cp.async-staged kernel. Timing uses a library-owned scratch state, so q, g and R are
+ * or the cp.async-staged kernel; and, when the mesh is one (order, box or affine) bucket without
+ * p-nonconforming faces run with FP32 contractions, whether each Runge-Kutta stage after its
+ * traces runs as one persistent cooperative kernel (the viscous pass, a bounded grid barrier,
+ * the inviscid pass and update) instead of separate viscous and inviscid launches.
+ * Timing uses a library-owned scratch state, so q, g and R are
  * untouched; the choices then apply to every later call (they are kept per order and
  * geometry kind across dg_set_orders / dg_set_element_flags) and the captured step graph
  * is rebuilt. cache_path (NULL: none) names a text file of choices keyed by the device
@@ -307,14 +311,17 @@ dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm,
  * for a free buffer (the producer) with a bounded number of polls; when the budget runs out
  * the warp records DG_ERR_TIMEOUT in the device error word (read by dg_check_device, which
  * names the site: 1 inviscid consumers, 2 inviscid producer, 3 viscous consumers, 4 viscous
- * producer) and returns, leaving the CUDA context usable.
+ * producer, 5 the grid barrier of the persistent stage kernel) and returns, leaving the CUDA
+ * context usable; dg_check_device also resets that grid barrier.
  *   polls      poll budget of every such wait, 1 .. 2^31 - 1; 0 restores the default 2^22.
  *   stop_tile  test hook: -1 off; k >= 0 makes the producer warp of block 0 of every pipelined
  *              launch return before staging its k-th tile, so that block's consumers wait for
  *              data that never comes until their budget runs out. Everything staged before
  *              was waited for by those consumers, so no copy is left in flight when they return.
+ *              -2: block 0 of the persistent stage kernel (see dg_autotune) does not arrive at
+ *              its grid barrier, so every block's bounded wait there runs out (site 5).
  * Applies to every later launch (the captured step graph is rebuilt). Results computed while
- * stop_tile >= 0 are wrong by design. Errors: DG_ERR_ARG for a NULL ctx or out-of-range value. */
+ * stop_tile != -1 are wrong by design. Errors: DG_ERR_ARG for a NULL ctx or out-of-range value. */
 dg_status dg_set_wait_limit(dg_ctx* ctx, int64_t polls, int stop_tile);
 
 /* Synchronise `stream`, then read and clear the device error word. */

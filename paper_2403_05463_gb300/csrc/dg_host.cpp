@@ -962,6 +962,38 @@ dg_status rebuild_orders(dg_ctx* c) {
 // Traces are double-buffered: stage s reads buffer s % 2; in RK mode the update of stages 0
 // and 1 writes the traces of the new state into the other buffer, so only stage 0 (and a
 // residual evaluation) launches the trace kernel.
+// The persistent stage kernel (viscous pass, grid barrier, inviscid pass and update in one
+// cooperative launch) applies to a reduced-precision context with FP32 contractions whose mesh
+// is one (order, box or affine) bucket without mortar faces, on the default tile shapes and the
+// pipelined viscous kernel.
+bool stage_fusable(const dg_ctx* c) {
+  const DevMesh& M = c->M;
+  if (M.precision != 1 || M.tc || M.split || M.div64 || M.model || M.nodes) return false;
+  if (c->all_buckets.size() != 1 || c->n_mortar_all) return false;
+  const Bucket& bi = c->all_buckets[0];
+  if (bi.geo > 1 || bi.tile_alt) return false;
+  if (c->ns_buckets.size() > 1) return false;
+  if (c->ns_buckets.size() == 1) {
+    const Bucket& bv = c->ns_buckets[0];
+    if (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo || bv.visc_alt)) return false;
+  }
+  return true;
+}
+
+// ... and is used where the autotuner chose it
+bool stage_fused(const dg_ctx* c) {
+  if (!stage_fusable(c)) return false;
+  auto it = c->tuning.find({2, c->all_buckets[0].N, c->all_buckets[0].geo});
+  return it != c->tuning.end() && it->second[0] == 1;
+}
+
+cudaError_t launch_stage(const dg_ctx* c, const DevMesh& M, const double* q, double* out, double* g, int stage,
+                         int write_tr, cudaStream_t s) {
+  Bucket bv{};
+  if (!c->ns_buckets.empty()) bv = c->ns_buckets[0];
+  return launch_stage32(M, bv, c->all_buckets[0], q, out, g, stage, write_tr, s);
+}
+
 dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage, double dt,
                       cudaStream_t s, int* nlaunch) {
   int nl = 0;
@@ -1058,6 +1090,7 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       if (c->n_mortar_ns) CU(launch_mortar_lift(M, c->mortar_ns, c->mortar_ns_mo, &nl, s));
       break;
     case 2:
+      if (mode == MODE_RK && stage_fused(c)) break;  // the stage kernel runs it in phase 4
       for (const Bucket& b : c->ns_buckets) {
         CU(launch_viscous(M, b, q, M.precision, s));
         ++nl;
@@ -1067,6 +1100,11 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
       if (c->n_mortar_all) CU(launch_mortar_flux(M, c->mortar_face, c->mortar_face_mo, &nl, s));
       break;
     default:
+      if (mode == MODE_RK && stage_fused(c)) {
+        CU(launch_stage(c, M, q, out, g, stage, write_tr, s));
+        ++nl;
+        break;
+      }
       for (const Bucket& b : c->all_buckets) {
         CU(launch_inviscid(M, b, q, out, g, mode, stage, dt, write_tr, M.precision, s));
         ++nl;
@@ -1240,12 +1278,12 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
     }
     *gdst[i] = dtab;
   }
-  int* derr;
-  if ((st = dev_alloc(c, "err", 4, &derr)) != DG_OK) {
+  int* derr;  // [0..3] the device error word, [4..5] the persistent stage kernel's grid barrier
+  if ((st = dev_alloc(c, "err", 8, &derr)) != DG_OK) {
     dg_destroy(c);
     return st;
   }
-  cudaMemset(derr, 0, 16);
+  cudaMemset(derr, 0, 32);
   c->M.err = derr;
   c->M.wait_polls = kWaitPolls;
   c->M.stop_tile = -1;
@@ -1553,7 +1591,8 @@ dg_status dg_check_device(dg_ctx* c, void* stream) {
   int h[4] = {0, 0, 0, 0};
   CU(cudaMemcpy(h, c->M.err, sizeof h, cudaMemcpyDeviceToHost));
   if (h[0] != 0) {
-    CU(cudaMemset(c->M.err, 0, sizeof h));
+    // also the grid barrier's words: a launch that timed out can leave arrivals counted
+    CU(cudaMemset(c->M.err, 0, 8 * sizeof(int)));
     if (h[0] == DG_ERR_TIMEOUT) return fail(DG_ERR_TIMEOUT, "a device-side wait timed out (site %d)", h[1]);
     return fail(DG_ERR_DEVICE, "device error %d at site %d", h[0], h[1]);
   }
@@ -1563,7 +1602,7 @@ dg_status dg_check_device(dg_ctx* c, void* stream) {
 dg_status dg_set_wait_limit(dg_ctx* c, int64_t polls, int stop_tile) {
   if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
   if (polls < 0 || polls > INT32_MAX) return fail(DG_ERR_ARG, "polls must be in [0, 2^31)");
-  if (stop_tile < -1) return fail(DG_ERR_ARG, "stop_tile must be -1 (off) or a tile index");
+  if (stop_tile < -2) return fail(DG_ERR_ARG, "stop_tile must be -1 (off), -2 or a tile index");
   c->M.wait_polls = polls == 0 ? kWaitPolls : (int)polls;
   c->M.stop_tile = stop_tile;
   destroy_graph(c);  // captured launches hold the previous values
@@ -1775,6 +1814,38 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
                   b.N, b.geo, best[2] ? "cp.async" : "pipelined", best[1], best_ms, default_ms);
     rep += buf;
   }
+  // one persistent kernel per stage against the separate viscous and inviscid launches, on the
+  // shapes just chosen (the RK form of stage 1 on the scratch state)
+  apply_tuning(c);
+  if (ce == cudaSuccess && stage_fusable(c)) {
+    const Bucket& bi = c->all_buckets[0];
+    const std::array<int, 3> key = {2, bi.N, bi.geo};
+    auto hit = cached.find(key);
+    if (hit != cached.end()) {
+      c->tuning[key] = hit->second;
+      std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: cached, %s\n", bi.N, bi.geo,
+                    hit->second[0] ? "one persistent kernel" : "separate launches");
+      rep += buf;
+    } else {
+      float ms_sep = 0.f, ms_fused = 0.f;
+      ce = timed(
+          [&]() {
+            cudaError_t r = cudaSuccess;
+            for (const Bucket& b : c->ns_buckets)
+              if (r == cudaSuccess) r = launch_viscous(M, b, tq, 1, s);
+            if (r == cudaSuccess) r = launch_inviscid(M, bi, tq, tq, tr, MODE_RK, 1, 1e-9, 1, 1, s);
+            return r;
+          },
+          ms_sep);
+      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, s); }, ms_fused);
+      const int fused = ce == cudaSuccess && ms_fused < ms_sep ? 1 : 0;
+      c->tuning[key] = {fused, 0, 0};
+      std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: %s: %.4f ms (one persistent kernel %.4f ms, separate %.4f ms)\n",
+                    bi.N, bi.geo, fused ? "one persistent kernel" : "separate launches", fused ? ms_fused : ms_sep,
+                    ms_fused, ms_sep);
+      rep += buf;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   free_buf(c, "tune_q");
@@ -1853,6 +1924,10 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
       }
     }
     b[4] += inv;
+  }
+  if (stage_fused(c)) {  // one persistent kernel runs the viscous pass inside phase 4
+    b[4] += b[2];
+    b[2] = 0.0;
   }
   for (int ph = 0; ph < DG_NPHASES; ++ph) out[ph] = b[ph];
   return DG_OK;

@@ -76,10 +76,12 @@ struct DevMesh {
   double* LH;                // [nvar][tr_total] projected total flux (F_e* - F_v*) . S on mortars
   const double* interp;      // [(Ns*NP+Nd)*NP*NP + i*NP + j]: Lagrange interpolation Ns -> Nd
   const double* proj;        // [(Nh*NP+Nl)*NP*NP + i*NP + j]: L2 projection Nh -> Nl
-  int* err;                  // device error word
+  int* err;                  // device error word [0..3]; [4], [5] the grid barrier of the
+                             // persistent stage kernel (arrivals, generation)
   int wait_polls;            // polls of a bounded mbarrier wait before it gives up (timeout)
   int stop_tile;             // test hook, -1 off: the producer warp of block 0 of each pipelined
-                             // launch returns before staging its stop_tile-th tile
+                             // launch returns before staging its stop_tile-th tile; -2: block 0
+                             // of the persistent stage kernel skips its grid-barrier arrival
   double nu, c0sq, cs, cv;
   int closure, riemann;
   int mixed_face;            // 0 average, 1 one-sided viscous flux on NS/Euler faces
@@ -185,6 +187,12 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
 cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s);
 cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q, double* out, double* g,
                               int mode, int stage, int write_tr, cudaStream_t s);
+
+// One persistent launch per RK stage of a single (order, box/affine) bucket: the viscous pass over
+// bv's NS elements, a bounded grid barrier, the inviscid pass and update over bi (cooperative
+// launch; the default tile shape, FP32 contractions). The grid barrier uses err[4], err[5].
+cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
+                           double* g, int stage, int write_tr, cudaStream_t s);
 
 // elements per tile of the FP32 inviscid pass at order N: the default shape or the alternative
 int tile_epb32(int N, int alt);

@@ -773,8 +773,8 @@ struct InvMinBlocks {
 // small*big in FP32. Consumer warps take the (element, direction, row tile) items in turn and
 // store C per direction; after the face phase each node sums its three directions.
 template <int N, int GEO, int MODE, int E, int VOL>
-__global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
-    k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
+__device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B, const double* qin, double* out,
+                                               double* g, int stage, int write_tr, char* smc, int bar_base) {
   // VOL 3 / 4: VOL 0 / 2 on box elements with the divergence S = sum_d Ja_dd D_d u_d taken in FP64
   // from the staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the
   // momentum fluxes (U_c S); the FP32 (or tensor-core) contractions carry only the rest of the
@@ -784,11 +784,10 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
   using S = Tile<N, E>;
   using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
-  extern __shared__ __align__(128) char smc[];
-  void* bar0 = smc + P::oBAR;        // full[0]
-  void* bar1 = smc + P::oBAR + 8;    // full[1]
-  void* ebar0 = smc + P::oBAR + 16;  // empty[0]
-  void* ebar1 = smc + P::oBAR + 24;  // empty[1]
+  void* bar0 = smc + P::oBAR + bar_base;        // full[0]
+  void* bar1 = smc + P::oBAR + bar_base + 8;    // full[1]
+  void* ebar0 = smc + P::oBAR + bar_base + 16;  // empty[0]
+  void* ebar1 = smc + P::oBAR + bar_base + 24;  // empty[1]
   constexpr int NC = S::threads;  // consumer threads
   float* sD = reinterpret_cast<float*>(smc + P::oD);
   char* const IN0 = smc + P::oIN0;
@@ -1298,6 +1297,13 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
   }
 }
 
+template <int N, int GEO, int MODE, int E, int VOL>
+__global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
+    k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
+  extern __shared__ __align__(128) char smc[];
+  inviscid_tiles<N, GEO, MODE, E, VOL>(M, B, qin, out, g, stage, write_tr, smc, 0);
+}
+
 // ---------------------------------------------------------------------------------------
 // viscous pass, persistent, TMA-staged (box and affine elements)
 // ---------------------------------------------------------------------------------------
@@ -1309,17 +1315,16 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
 // the second; F is written between them and read after the second, and the next tile writes F
 // only after its first barrier.
 template <int N, int GEO>
-__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
-    k_viscous32t(DevMesh M, Bucket B, const double* q) {
+__device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B, const double* q, char* smc,
+                                              int bar_base) {
   using S = Shape<N>;
   using P = ViscTmaSmem32<N>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   constexpr int NC = Shape<N>::threads;  // consumer threads
-  extern __shared__ __align__(128) char smc[];
-  void* bar0 = smc + P::oBAR;
-  void* bar1 = smc + P::oBAR + 8;
-  void* ebar0 = smc + P::oBAR + 16;
-  void* ebar1 = smc + P::oBAR + 24;
+  void* bar0 = smc + P::oBAR + bar_base;
+  void* bar1 = smc + P::oBAR + bar_base + 8;
+  void* ebar0 = smc + P::oBAR + bar_base + 16;
+  void* ebar1 = smc + P::oBAR + bar_base + 24;
   float* sD = reinterpret_cast<float*>(smc + P::oD);
   char* const IN0 = smc + P::oIN0;
   char* const IN1 = smc + P::oIN1;
@@ -1532,6 +1537,117 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   }
 }
 
+template <int N, int GEO>
+__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+    k_viscous32t(DevMesh M, Bucket B, const double* q) {
+  extern __shared__ __align__(128) char smc[];
+  viscous_tiles<N, GEO>(M, B, q, smc, 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// one persistent kernel per Runge-Kutta stage (viscous tiles, grid barrier, inviscid tiles)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a launch whose blocks are all resident (a cooperative launch). Bounded:
+// gbar[0] counts the arrivals, the last one resets it and advances the generation gbar[1];
+// a block that sees no new generation within M.wait_polls polls records DG_ERR_TIMEOUT (site 5).
+// Test hook: with M.stop_tile == -2 block 0 does not arrive, so every block's wait runs out.
+__device__ __forceinline__ bool grid_barrier(const DevMesh& M) {
+  __shared__ int s_ok;
+  unsigned* gbar = reinterpret_cast<unsigned*>(M.err + 4);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire_u32(gbar + 1);  // cannot advance before this block arrives
+    if (!(M.stop_tile == -2 && blockIdx.x == 0)) {
+      __threadfence();  // this block's results (ordered before by the __syncthreads) first
+      if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+        atomicExch(gbar, 0u);
+        __threadfence();
+        atomicAdd(gbar + 1, 1u);
+      }
+    }
+    bool ok = ld_acquire_u32(gbar + 1) != gen;
+    for (int spin = 0; !ok && spin < M.wait_polls; ++spin) {
+      __nanosleep(128);
+      ok = ld_acquire_u32(gbar + 1) != gen;
+    }
+    if (!ok) {
+      atomicCAS(&M.err[0], 0, kErrTimeout);
+      atomicCAS(&M.err[1], 0, 5);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  // the second phase's bulk copies (async proxy) read what other blocks stored before the
+  // barrier and overwrite shared memory that this block's first phase read and wrote
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  return s_ok != 0;
+}
+
+// A whole RK stage of one (order, geometry) bucket after its traces: the viscous pass over the
+// bucket's NS elements (Bv), a grid barrier (the inviscid pass reads the neighbours' viscous
+// traces), the inviscid pass with the RK update over all its elements (Bi). The same device code
+// as k_viscous32t and k_inviscid32t (default tile shape, FP32 contractions); the second phase's
+// mbarriers sit 32 bytes after the first's.
+template <int N, int GEO>
+__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+    k_stage32t(DevMesh M, Bucket Bv, Bucket Bi, const double* q, double* out, double* g, int stage, int write_tr) {
+  extern __shared__ __align__(128) char smc[];
+  viscous_tiles<N, GEO>(M, Bv, q, smc, 0);
+  if (!grid_barrier(M)) return;
+  inviscid_tiles<N, GEO, MODE_RK, Shape<N>::EPB, 0>(M, Bi, q, out, g, stage, write_tr, smc, 32);
+}
+
+template <int N>
+constexpr size_t stage_smem32() {
+  return ViscTmaSmem32<N>::bytes > TmaSmem32<N>::bytes ? ViscTmaSmem32<N>::bytes : TmaSmem32<N>::bytes;
+}
+
+template <int N, int GEO>
+static cudaError_t launch_stage_n(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
+                                  double* g, int stage, int write_tr, cudaStream_t s) {
+  static int per_sm = -1, sms = 0;
+  const size_t sm = stage_smem32<N>();
+  if (per_sm < 0) {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32t<N, GEO>, Shape<N>::threads + 32, sm);
+    if (r != cudaSuccess) return r;
+    int dev = 0;
+    if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  // every block resident: the grid barrier needs it, the cooperative launch guarantees it
+  const int bps = bi.bps > 0 && bi.bps < per_sm ? bi.bps : per_sm;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(bps * sms));
+  cfg.blockDim = dim3(Shape<N>::threads + 32);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_stage32t<N, GEO>, M, bv, bi, q, out, g, stage, write_tr);
+}
+
+cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
+                           double* g, int stage, int write_tr, cudaStream_t s) {
+  if (bi.geo > 1 || (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo))) return cudaErrorInvalidValue;
+  if (!bi.blink || !bi.bmeta || (bv.count > 0 && (!bv.blink || !bv.bmeta))) return cudaErrorInvalidValue;
+  DG_SWITCH_N(bi.N, {
+    return bi.geo == 0 ? launch_stage_n<NN, 0>(M, bv, bi, q, out, g, stage, write_tr, s)
+                       : launch_stage_n<NN, 1>(M, bv, bi, q, out, g, stage, write_tr, s);
+  });
+  return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------------------
@@ -1575,6 +1691,10 @@ static cudaError_t prep_inv() {
 template <int N>
 static cudaError_t prep32_n() {
   cudaError_t r;
+  if ((r = cudaFuncSetAttribute(k_stage32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem32<N>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_stage32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem32<N>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 0>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -101,3 +101,54 @@ def test_tuning_round_trip_and_accuracy(tmp_path):
 def test_fp64_has_nothing_to_tune():
     S = gpu_solver(wl.tgv_4x4x4_n3(), precision=0)
     assert "no launch choices" in S.autotune()
+
+
+def _stage_case(flags_p=0.3, n=10, order=4):
+    # one (order, box) bucket, no mortars: the persistent stage kernel applies
+    w = wl.tgv_4x4x4_n3(n_elem_dir=n, order=order)
+    return small_mixed(w, seed=44, flags_p=flags_p)
+
+
+@pytest.mark.parametrize("flags_p", [0.0, 0.3, 1.0])
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_persistent_stage_kernel_matches_separate_launches(flags_p, order, tmp_path):
+    # one persistent kernel per RK stage (viscous pass, grid barrier, inviscid pass) against the
+    # separate launches: the same device code per element, so the same bits
+    import torch
+    w = _stage_case(flags_p, order=order)
+    p = dict(w.params, nu=1e-2)
+    M = oracle_mesh(w, p)
+    q = oracle_state(w, M)
+    out = {}
+    for fused in (0, 1):
+        cache = tmp_path / f"stage{fused}.txt"
+        # default shapes for both passes (the stage kernel's), the stage choice forced
+        _forced_cache(cache, {(0, order, 0): (0, 0, 0), (1, order, 0): (0, 0, 0), (2, order, 0): (fused, 0, 0)})
+        S = gpu_solver(w, precision=1, params=p)
+        rep = S.autotune(str(cache))
+        assert ("one persistent kernel" if fused else "separate launches") in rep, rep
+        qd, gd = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
+        S.rk_step(qd, gd, 1e-4, 3)
+        S.check_device()
+        out[fused] = (qd.cpu().numpy(), S.launches_per_step)
+    assert np.array_equal(out[0][0], out[1][0])
+    # three stages: traces once, then one launch per stage instead of viscous + inviscid
+    if flags_p > 0:
+        assert out[1][1] == out[0][1] - 3, (out[0][1], out[1][1])
+    # and against the oracle, at the FP32 accuracy of the state change
+    q0 = q.copy()
+    g = np.zeros_like(q)
+    M.rk_step(q, g, 1e-4, 3)
+    assert rel_l2(out[1][0] - q0, q - q0) <= 1e-4
+
+
+def test_autotuner_times_the_persistent_stage_kernel(tmp_path):
+    w = _stage_case(0.3)
+    S = gpu_solver(w, precision=1, params=dict(w.params, nu=1e-2))
+    cache = tmp_path / "t.txt"
+    _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (0, 0, 0)})  # the stage choice is timed
+    rep = S.autotune(str(cache))
+    assert "stage N=4 geo=0" in rep and "one persistent kernel" in rep and "separate" in rep, rep
+    # not offered where it does not apply: mixed orders (several buckets, mortars)
+    T = gpu_solver(_box_mixed_orders(), precision=1)
+    assert "stage N=" not in T.autotune()

@@ -95,3 +95,35 @@ def test_step_graph_is_rebuilt_after_the_limit_changes():
     S.rk_step(qc, gc, w.dt, 1)
     S.check_device()
     assert torch.equal(qc, qa)
+
+
+def test_grid_barrier_of_the_persistent_stage_kernel_times_out(tmp_path):
+    # block 0 of the one-kernel stage skips its grid-barrier arrival: every block's bounded wait
+    # runs out (site 5), the step returns, the barrier is reset, and the next step is exact
+    import torch
+    from paper_2403_05463_gb300 import dg
+    w = _case(1, n=10)
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    S = gpu_solver(w, precision=1)
+    cache = tmp_path / "stage.txt"
+    with open(cache, "w") as f:
+        for ps, choice in ((0, "0\t0\t0"), (1, "0\t0\t0"), (2, "1\t0\t0")):
+            f.write(f"{torch.cuda.get_device_name(0)}\t{ps}\t4\t0\t{choice}\n")
+    assert "one persistent kernel" in S.autotune(str(cache))
+    qa, ga = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
+    S.rk_step(qa, ga, w.dt, 1)
+    S.check_device()
+    S.set_wait_limit(polls=1 << 12, stop_tile=-2)
+    qb, gb = to_dev(q), torch.zeros_like(ga)
+    t0 = time.perf_counter()
+    S.rk_step(qb, gb, w.dt, 1)
+    with pytest.raises(dg.DGError) as ei:
+        S.check_device()
+    assert time.perf_counter() - t0 < 30.0
+    assert dg.STATUS[ei.value.status] == "DG_ERR_TIMEOUT" and "site 5" in str(ei.value), str(ei.value)
+    S.set_wait_limit(0, -1)
+    qc, gc = to_dev(q), torch.zeros_like(ga)
+    S.rk_step(qc, gc, w.dt, 1)
+    S.check_device()
+    assert torch.equal(qc, qa)
