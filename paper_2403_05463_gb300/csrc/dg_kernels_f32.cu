@@ -1599,8 +1599,10 @@ template <int N, int GEO>
 __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
     k_stage32t(DevMesh M, Bucket Bv, Bucket Bi, const double* q, double* out, double* g, int stage, int write_tr) {
   extern __shared__ __align__(128) char smc[];
-  viscous_tiles<N, GEO>(M, Bv, q, smc, 0);
-  if (!grid_barrier(M)) return;
+  if (Bv.count > 0) {  // no NS element: nothing to wait for
+    viscous_tiles<N, GEO>(M, Bv, q, smc, 0);
+    if (!grid_barrier(M)) return;
+  }
   inviscid_tiles<N, GEO, MODE_RK, Shape<N>::EPB, 0>(M, Bi, q, out, g, stage, write_tr, smc, 32);
 }
 

@@ -66,7 +66,7 @@ def test_bounded_wait_times_out_and_the_context_recovers(flags_value, site, stop
 def test_wait_limit_arguments_are_checked():
     from paper_2403_05463_gb300 import dg
     S = gpu_solver(_case(1, n=4), precision=1)
-    for polls, stop in ((-1, -1), (1 << 31, -1), (0, -2)):
+    for polls, stop in ((-1, -1), (1 << 31, -1), (0, -3)):
         with pytest.raises(dg.DGError) as ei:
             S.set_wait_limit(polls, stop)
         assert dg.STATUS[ei.value.status] == "DG_ERR_ARG"
