@@ -889,27 +889,14 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
     const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
     float invJ = 0.f;
     // ---- node phase: split state, flux deviations --------------------------------------
-    // the element's reference state (hi parts of node 0; any per-element constant serves):
-    // computed once per element and passed through the element's T area, which the face
-    // phase only writes after the node phase's barrier
-    float4* QR = reinterpret_cast<float4*>(W + le * P::work_elem + P::wT);
-    if (active && p == 0) {
-      float r[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        r[v] = hi_part(reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v])[0]);
-      *QR = make_float4(r[0], r[1], r[2], r[3]);
-    }
-    consumer_sync(NC);
-    float qr32[4] = {0.f, 0.f, 0.f, 0.f};
+    float qr32[4] = {0.f, 0.f, 0.f, 0.f};  // the element's reference state (hi parts of node 0)
     if (active) {
-      const float4 r4 = *QR;
-      qr32[0] = r4.x, qr32[1] = r4.y, qr32[2] = r4.z, qr32[3] = r4.w;
       float dq[4], h[4], l[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const double* QDv = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v]);
         split_hilo(QDv[p], h[v], l[v]);
+        qr32[v] = hi_part(QDv[0]);  // any per-element constant serves as reference
         dq[v] = (h[v] - qr32[v]) + l[v];
       }
       QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
@@ -1282,7 +1269,7 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
           const float gi = fmaf(A, gold[v], JR[v] * invJ * dtf);
           g32[ix] = gi;
           const double qo = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v])[p];
-          const double qn = fma(Bc, (double)gi, qo);  // exact widening (one conversion)
+          const double qn = fma(Bc, widen_f32(gi), qo);
           out[ix] = qn;
           if (write_tr && on_face) split_hilo(qn, h[v], l[v]);
         }
