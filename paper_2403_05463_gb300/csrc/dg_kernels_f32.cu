@@ -1558,8 +1558,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // a block that sees no new generation within M.wait_polls polls records DG_ERR_TIMEOUT (site 5).
 // Test hook: with M.stop_tile == -2 block 0 does not arrive, so every block's wait runs out.
 __device__ __forceinline__ bool grid_barrier(const DevMesh& M) {
-  __shared__ int s_ok;
   unsigned* gbar = reinterpret_cast<unsigned*>(M.err + 4);
+  bool ok = true;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned gen = ld_acquire_u32(gbar + 1);  // cannot advance before this block arrives
@@ -1571,7 +1571,7 @@ __device__ __forceinline__ bool grid_barrier(const DevMesh& M) {
         atomicAdd(gbar + 1, 1u);
       }
     }
-    bool ok = ld_acquire_u32(gbar + 1) != gen;
+    ok = ld_acquire_u32(gbar + 1) != gen;
     for (int spin = 0; !ok && spin < M.wait_polls; ++spin) {
       __nanosleep(128);
       ok = ld_acquire_u32(gbar + 1) != gen;
@@ -1580,14 +1580,14 @@ __device__ __forceinline__ bool grid_barrier(const DevMesh& M) {
       atomicCAS(&M.err[0], 0, kErrTimeout);
       atomicCAS(&M.err[1], 0, 5);
     }
-    s_ok = ok;
   }
-  __syncthreads();
+  // thread 0's verdict to the block (no static shared memory: the dynamic layouts use it all)
+  ok = __syncthreads_and(ok) != 0;
   // the second phase's bulk copies (async proxy) read what other blocks stored before the
   // barrier and overwrite shared memory that this block's first phase read and wrote
   asm volatile("fence.proxy.async.global;\n" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  return s_ok != 0;
+  return ok;
 }
 
 // A whole RK stage of one (order, geometry) bucket after its traces: the viscous pass over the
