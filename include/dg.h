@@ -233,7 +233,8 @@ dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double* out_host, vo
  * or the cp.async-staged kernel; and, when the mesh is one (order, box or affine) bucket without
  * p-nonconforming faces run with FP32 contractions, whether each Runge-Kutta stage after its
  * traces runs as one persistent cooperative kernel (the viscous pass, a bounded grid barrier,
- * the inviscid pass and update) instead of separate viscous and inviscid launches.
+ * the inviscid pass and update) instead of separate viscous and inviscid launches (chosen only
+ * when at least 1% faster).
  * Timing uses a library-owned scratch state, so q, g and R are
  * untouched; the choices then apply to every later call (they are kept per order and
  * geometry kind across dg_set_orders / dg_set_element_flags) and the captured step graph

@@ -1838,7 +1838,9 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
           },
           ms_sep);
       if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, s); }, ms_fused);
-      const int fused = ce == cudaSuccess && ms_fused < ms_sep ? 1 : 0;
+      // a tie keeps the separate launches (per-pass timing and rooflines stay per kernel): the
+      // persistent form must be at least 1% faster
+      const int fused = ce == cudaSuccess && ms_fused < 0.99f * ms_sep ? 1 : 0;
       c->tuning[key] = {fused, 0, 0};
       std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: %s: %.4f ms (one persistent kernel %.4f ms, separate %.4f ms)\n",
                     bi.N, bi.geo, fused ? "one persistent kernel" : "separate launches", fused ? ms_fused : ms_sep,
