@@ -480,15 +480,17 @@ __device__ __forceinline__ void face_metric(const DevMesh& M, int e, int f, int 
 // FP32 (hi, lo) pairs interleaved per slot, [tr_total][4]
 __device__ __forceinline__ double tq_load(const DevMesh& M, int v, int64_t slot) {
   if (M.precision == 1) {
+    // exact widening with integer instructions, one FP64 add (the mortar kernels are
+    // FP64-pipe bound)
     const float2 t = reinterpret_cast<const float2*>(M.Tq)[slot * 4 + v];
-    return (double)t.x + (double)t.y;
+    return widen_f32(t.x) + widen_f32(t.y);
   }
   return M.Tq[v * M.tr_total + slot];
 }
 
 // viscous trace component c at `slot`: FP64 planes [3][tr_total], or FP32 [tr_total][3]
 __device__ __forceinline__ double tv_load(const DevMesh& M, int c, int64_t slot) {
-  return M.precision == 1 ? (double)reinterpret_cast<const float*>(M.Tv)[slot * 3 + c] : M.Tv[c * M.tr_total + slot];
+  return M.precision == 1 ? widen_f32(reinterpret_cast<const float*>(M.Tv)[slot * 3 + c]) : M.Tv[c * M.tr_total + slot];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -648,7 +650,11 @@ __global__ void __launch_bounds__(32 * kMortarWarps) k_mortar_flux_w(DevMesh M, 
     for (int c = 0; c < 3; ++c) B[(4 + c) * PS + t] = vn ? tv_load(M, c, s1) : 0.0;
   }
   __syncwarp();
-  tensor2_warp(interp_tab(M, Nn, MO), nn == nM, nn, nM, 7, B, T, B, PS, L.orient, MO, lane);
+  // the viscous traces (planes 4..6) only where a side is NS; between Euler elements they are 0
+  tensor2_warp(interp_tab(M, Nn, MO), nn == nM, nn, nM, (vm || vn) ? 7 : 4, B, T, B, PS, L.orient, MO, lane);
+  if (!(vm || vn))
+    for (int t = lane; t < 3 * PS; t += 32) B[4 * PS + t] = 0.0;
+  __syncwarp();
   // F_v* . S = wm (mine) - wp (neighbour's outward): the average, or the NS side alone
   const bool one = M.mixed_face == 1 && vm != vn;
   const double wm = one ? (vm ? 1.0 : 0.0) : 0.5, wp = one ? (vm ? 0.0 : 1.0) : 0.5;

@@ -889,14 +889,27 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
     const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
     float invJ = 0.f;
     // ---- node phase: split state, flux deviations --------------------------------------
-    float qr32[4] = {0.f, 0.f, 0.f, 0.f};  // the element's reference state (hi parts of node 0)
+    // the element's reference state (hi parts of node 0; any per-element constant serves):
+    // computed once per element and passed through the element's T area, which the face
+    // phase writes only after the node phase's barrier
+    float4* QR = reinterpret_cast<float4*>(W + le * P::work_elem + P::wT);
+    if (active && p == 0) {
+      float r[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        r[v] = hi_part(reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v])[0]);
+      *QR = make_float4(r[0], r[1], r[2], r[3]);
+    }
+    consumer_sync(NC);
+    float qr32[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
+      const float4 r4 = *QR;
+      qr32[0] = r4.x, qr32[1] = r4.y, qr32[2] = r4.z, qr32[3] = r4.w;
       float dq[4], h[4], l[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const double* QDv = reinterpret_cast<const double*>(INe + P::iQD + v * P::SQD + SH[v]);
         split_hilo(QDv[p], h[v], l[v]);
-        qr32[v] = hi_part(QDv[0]);  // any per-element constant serves as reference
         dq[v] = (h[v] - qr32[v]) + l[v];
       }
       QH4[p] = make_float4(h[0], h[1], h[2], h[3]);
@@ -1394,6 +1407,14 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
     int e = 0;
     float Ja[9], invJ = 0.f, delta = 0.f;
     float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+    // the element's reference velocity (hi parts of node 0), once per element, through the
+    // element's F area (the previous tile's divergence read it before this tile's vote; this
+    // tile writes F only after its first barrier)
+    if (active && p == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c] = hi_part(reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c])[0]);
+    }
+    consumer_sync(NC);
     if (active) {
       off = MT->off;
       troff = MT->troff;
@@ -1406,7 +1427,7 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
       for (int c = 0; c < 3; ++c) {
         const double* QV = reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c]);
         split_hilo(QV[p], uh[c], ul[c]);
-        U[c * n3 + p] = (uh[c] - hi_part(QV[0])) + ul[c];  // deviation from the element's first node
+        U[c * n3 + p] = (uh[c] - F[c]) + ul[c];  // deviation from the element's first node
       }
     }
     consumer_sync(NC);
