@@ -481,11 +481,10 @@ def main():
     dt = w.dt
     stream = torch.cuda.current_stream()
 
-    def step():
-        S.rk_step(q, g, dt, 1, stream=stream)
-
-    for _ in range(max(args.warmup, 0)):
-        step()
+    # K steps are one dg_rk_step call: the steps are chained (every stage's update writes the
+    # next stage's traces, so only the first step runs the trace kernel)
+    if args.warmup > 0:
+        S.rk_step(q, g, dt, args.warmup, stream=stream)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -494,8 +493,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    S.rk_step(q, g, dt, args.steps, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -504,7 +502,8 @@ def main():
     ms_max = allmax(world, ms)
     value = world * dof * 3 / (ms_max * 1e-3)
     S.check_device()
-    launches = S.launches_per_step * args.steps
+    launches = S.launches_per_step + S.launches_per_chained_step * (args.steps - 1) if args.steps > 1 else \
+        S.launches_per_step * args.steps
 
     # roofline of the dominant phase (CUDA events between the phases, same stream)
     q.copy_(q0)
@@ -518,7 +517,10 @@ def main():
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     ach = ph_bytes[dom] / (ph_ms[dom] * 1e-3) / 1e9
-    step_bytes = 3 * sum(ph_bytes.values())
+    # the timed call's bytes per step: every step's three stages, the trace kernel in the first
+    # step only, and in every step a third update writing traces (ph_bytes are per-stage means:
+    # the trace kernel's launch moves 3 x traces, half of it the written traces)
+    step_bytes = 3 * sum(ph_bytes.values()) - (1.5 * ph_bytes["traces"] * (args.steps - 1) / max(args.steps, 1))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": ach / NOMINAL_HBM_GBS,
@@ -559,14 +561,12 @@ def main():
             if name == "all_ns":
                 bytes_ns = 3 * sum(S.phase_bytes().values())
             q.copy_(q0)
-            for _ in range(3):
-                step()
+            S.rk_step(q, g, dt, 3, stream=stream)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            for _ in range(20):
-                step()
+            S.rk_step(q, g, dt, 20, stream=stream)
             b.record(stream)
             torch.cuda.synchronize()
             cmp[name] = {"ms_per_step": a.elapsed_time(b) / 20, "value": dof * 3 / (a.elapsed_time(b) / 20 * 1e-3)}

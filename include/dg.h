@@ -203,8 +203,11 @@ dg_status dg_residual(dg_ctx* ctx, const double* q_dev, double* R_dev, void* str
  * overwrites it). q is always accumulated in FP64. g is the scheme's register: FP64 with
  * precision 0; with precision 1 it holds FP32 values (the first half of its bytes, laid out
  * [4][total_nodes]), like the residual it accumulates. One step is captured once as a CUDA
- * graph per (q, g, dt) and replayed. t is the time at the start (the residual has no
- * explicit time dependence). */
+ * graph per (q, g, dt) and replayed. With nsteps > 1 the steps are chained: every stage's
+ * update also writes the face traces of the next stage (the last stage those of the next step),
+ * so only the first step runs the separate trace kernel; the results are bitwise those of
+ * nsteps calls with nsteps = 1. t is the time at the start (the residual has no explicit time
+ * dependence). */
 dg_status dg_rk_step(dg_ctx* ctx, double* q_dev, double* g_dev, double t, double dt, int nsteps,
                      void* stream);
 
@@ -344,9 +347,11 @@ dg_status dg_phase_times(dg_ctx* ctx, double* q_dev, double* g_dev, double dt, i
  * roofline of a phase is these bytes over its mean time from dg_phase_times. */
 dg_status dg_phase_bytes(const dg_ctx* ctx, double out_bytes[DG_NPHASES]);
 
-/* Number of kernel launches the last dg_residual / one dg_rk_step step issued. */
+/* Number of kernel launches the last dg_residual / one dg_rk_step step issued, and one step
+ * that follows another in the same dg_rk_step call (0 before any such call). */
 int dg_launches_per_residual(const dg_ctx* ctx);
 int dg_launches_per_step(const dg_ctx* ctx);
+int dg_launches_per_chained_step(const dg_ctx* ctx);
 
 /* Thread-local message describing the last failure on this thread. */
 const char* dg_last_error(void);

@@ -301,7 +301,11 @@ struct DevBuf {
 };
 
 struct GraphCache {
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;  // one step on its own: trace kernel, stages 0..2
+  // chained steps (nsteps > 1): [0] the first step, whose three stages all write the next
+  // stage's traces; [1], [2] a later step of trace-buffer parity 0 or 1, without the trace kernel
+  cudaGraphExec_t chain[3] = {nullptr, nullptr, nullptr};
+  int chain_launches = 0;          // launches of a later chained step
   const double* q = nullptr;
   const double* g = nullptr;
   double dt = 0.0;
@@ -351,6 +355,9 @@ struct dg_ctx {
   GraphCache graph;
   uint64_t version = 1;
   int launches_residual = 0, launches_step = 0;
+  // while a chained RK step is captured: the trace-buffer parity of its stage 0, whether stage 2
+  // writes the next stage's traces too, and whether the trace kernel is left out
+  int cap_parity = 0, cap_write_all = 0, cap_no_traces = 0;
   // host-variant staging
   double* trace_buf[2] = {nullptr, nullptr};
   double* stage_q = nullptr;
@@ -603,6 +610,8 @@ void elem_geometry(const dg_ctx* c, int64_t e, int N, ElemGeo& G) {
 
 void destroy_graph(dg_ctx* c) {
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  for (cudaGraphExec_t& e : c->graph.chain)
+    if (e) cudaGraphExecDestroy(e);
   c->graph = GraphCache{};
 }
 
@@ -998,10 +1007,15 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
                       cudaStream_t s, int* nlaunch) {
   int nl = 0;
   DevMesh M = c->M;
-  const int cur = (mode == MODE_RK) ? stage % 2 : 0;
+  const int cur = (mode == MODE_RK) ? (stage + c->cap_parity) % 2 : 0;
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
-  const int write_tr = (mode == MODE_RK && stage < 2) ? 1 : 0;
+  const int write_tr = (mode == MODE_RK && (stage < 2 || c->cap_write_all)) ? 1 : 0;
+  // a chained step's traces come from the previous step's last update
+  if (phase == 0 && mode == MODE_RK && c->cap_no_traces) {
+    if (nlaunch) *nlaunch += nl;
+    return DG_OK;
+  }
   if (M.nodes == 1 && M.model == 1) {  // compressible form on Gauss-Legendre nodes
     if (phase == 0 && !(mode == MODE_RK && stage > 0)) {
       for (const Bucket& b : c->ord_buckets) {
@@ -1501,7 +1515,41 @@ dg_status dg_rk_step(dg_ctx* c, double* q, double* g, double t, double dt, int n
     G.version = c->version;
     c->launches_step = nl;
   }
-  for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(G.exec, (cudaStream_t)stream));
+  if (nsteps == 1) {
+    CU(cudaGraphLaunch(G.exec, (cudaStream_t)stream));
+    return DG_OK;
+  }
+  // Several steps: the stage index runs on across steps, so the trace-buffer parity of a step's
+  // stage 0 alternates; each stage's update writes the next stage's traces (stage 2 those of
+  // the next step's stage 0), and only the first step runs the trace kernel.
+  if (!G.chain[0]) {
+    for (int k = 0; k < 3; ++k) {
+      c->cap_parity = k == 0 ? 0 : k - 1;
+      c->cap_write_all = 1;
+      c->cap_no_traces = k == 0 ? 0 : 1;
+      CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int nl = 0;
+      dg_status st = DG_OK;
+      for (int s = 0; s < 3 && st == DG_OK; ++s) st = issue_stage(c, q, q, g, MODE_RK, s, dt, c->cap_stream, &nl);
+      c->cap_parity = c->cap_write_all = c->cap_no_traces = 0;
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (st != DG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ce != cudaSuccess) return fail(DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&G.chain[k], graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        G.chain[k] = nullptr;
+        return fail(DG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+      }
+      if (k == 1) G.chain_launches = nl;
+    }
+  }
+  CU(cudaGraphLaunch(G.chain[0], (cudaStream_t)stream));
+  for (int i = 1; i < nsteps; ++i) CU(cudaGraphLaunch(G.chain[1 + (i % 2)], (cudaStream_t)stream));
   return DG_OK;
 }
 
@@ -1937,6 +1985,7 @@ dg_status dg_phase_bytes(const dg_ctx* c, double out[DG_NPHASES]) {
 
 int dg_launches_per_residual(const dg_ctx* c) { return c ? c->launches_residual : 0; }
 int dg_launches_per_step(const dg_ctx* c) { return c ? c->launches_step : 0; }
+int dg_launches_per_chained_step(const dg_ctx* c) { return c ? c->graph.chain_launches : 0; }
 
 void dg_destroy(dg_ctx* c) {
   if (!c) return;

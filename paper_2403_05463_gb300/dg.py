@@ -108,6 +108,7 @@ def load():
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_launches_per_residual.argtypes = [_vp]
         L.dg_launches_per_step.argtypes = [_vp]
+        L.dg_launches_per_chained_step.argtypes = [_vp]
         L.dg_last_error.restype = ctypes.c_char_p
         L.dg_destroy.argtypes = [_vp]
         L.dg_destroy.restype = None
@@ -371,6 +372,11 @@ class Solver:
     @property
     def launches_per_step(self):
         return load().dg_launches_per_step(self.h)
+
+    @property
+    def launches_per_chained_step(self):
+        """Launches of a step that follows another in the same rk_step call."""
+        return load().dg_launches_per_chained_step(self.h)
 
 
 class _as_sized:
