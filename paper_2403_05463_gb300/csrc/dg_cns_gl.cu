@@ -511,9 +511,9 @@ __global__ void __launch_bounds__(Shape<N>::threads)
       for (int v = 0; v < 5; ++v) {
         const int64_t ix = v * M.total + off + p;
         double gi = dt * (JR[v] * invJ);
-        if (stage > 0) gi += A * g[ix];
+        if (stage > 0) gi = fma(A, g[ix], gi);  // explicit FMAs: one rounding order in every code path
         g[ix] = gi;
-        const double qn = uu[v] + B * gi;
+        const double qn = fma(B, gi, uu[v]);
         out[ix] = qn;
         Q[v * n3 + p] = qn;  // every read of the old state ended at the barrier above
       }

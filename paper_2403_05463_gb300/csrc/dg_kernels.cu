@@ -415,9 +415,9 @@ __global__ void __launch_bounds__(Shape<N>::threads)
     for (int v = 0; v < 4; ++v) {
       const int64_t ix = v * M.total + off + p;
       double gi = dt * (JR[v] * invJ);
-      if (stage > 0) gi += A * g[ix];
+      if (stage > 0) gi = fma(A, g[ix], gi);  // explicit FMAs: one rounding order in every code path
       g[ix] = gi;
-      const double qn = qq[v] + B * gi;
+      const double qn = fma(B, gi, qq[v]);
       out[ix] = qn;
       if (write_tr) {  // traces of the new state for the next stage
 #pragma unroll
