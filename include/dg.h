@@ -232,8 +232,8 @@ dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double* out_host, vo
  * launch shapes on this GPU and keeps the fastest: for the inviscid pass the elements per
  * tile (the default ~256-node tile or the alternative: half of it for orders 1..4, two
  * elements for orders 5, 6) and the resident blocks per SM (all that fit, 1 or 2); for the
- * viscous pass on box/affine elements the pipelined (bulk-copy) kernel at those block counts
- * or the cp.async-staged kernel; and, when the mesh is one (order, box or affine) bucket without
+ * viscous pass on box/affine elements the pipelined (bulk-copy) kernel with either tile shape at
+ * those block counts or the cp.async-staged kernel; and, when the mesh is one (order, box or affine) bucket without
  * p-nonconforming faces run with FP32 contractions, whether each Runge-Kutta stage after its
  * traces runs as one persistent cooperative kernel (the viscous pass, a bounded grid barrier,
  * the inviscid pass and update) instead of separate viscous and inviscid launches (chosen only

@@ -672,7 +672,7 @@ void apply_tuning(dg_ctx* c) {
   }
   for (Bucket& b : c->ns_buckets) {
     auto it = c->tuning.find({1, b.N, b.geo});
-    b.tile_alt = 0;
+    b.tile_alt = it == c->tuning.end() ? 0 : it->second[0];
     b.bps = it == c->tuning.end() ? 0 : it->second[1];
     b.visc_alt = it == c->tuning.end() ? 0 : it->second[2];
   }
@@ -984,7 +984,7 @@ bool stage_fusable(const dg_ctx* c) {
   if (c->ns_buckets.size() > 1) return false;
   if (c->ns_buckets.size() == 1) {
     const Bucket& bv = c->ns_buckets[0];
-    if (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo || bv.visc_alt)) return false;
+    if (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo || bv.visc_alt || bv.tile_alt)) return false;
   }
   return true;
 }
@@ -1838,28 +1838,37 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
     auto hit = cached.find(key);
     if (hit != cached.end()) {
       c->tuning[key] = hit->second;
-      std::snprintf(buf, sizeof buf, "viscous N=%d geo=%d: cached, %s kernel, %d blocks/SM (0 = max)\n", b.N, b.geo,
-                    hit->second[2] ? "cp.async" : "pipelined", hit->second[1]);
+      std::snprintf(buf, sizeof buf, "viscous N=%d geo=%d: cached, %s kernel, %d elements/tile, %d blocks/SM (0 = max)\n",
+                    b.N, b.geo, hit->second[2] ? "cp.async" : "pipelined", tile_epb32(b.N, hit->second[0]),
+                    hit->second[1]);
       rep += buf;
       continue;
     }
-    const int cand[4][2] = {{0, 0}, {1, 0}, {2, 0}, {0, 1}};  // (bps, visc_alt)
+    // (tile_alt, bps, visc_alt): the pipelined kernel with the default or the alternative tile
+    // shape (fewer elements per tile: a shorter last round), or the cp.async-staged kernel
+    const int cand[6][3] = {{0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 0, 1}, {1, 0, 0}, {1, 2, 0}};
+    const bool has_alt = tile_epb32(b.N, 1) != tile_epb32(b.N, 0);
     std::array<int, 3> best = {0, 0, 0};
     float best_ms = 0.f, default_ms = 0.f;
-    for (int k = 0; k < 4 && ce == cudaSuccess; ++k) {
-      b.bps = cand[k][0];
-      b.visc_alt = cand[k][1];
+    for (int k = 0; k < 6 && ce == cudaSuccess; ++k) {
+      if (cand[k][0] && !has_alt) continue;
+      b.tile_alt = cand[k][0];
+      b.bps = cand[k][1];
+      b.visc_alt = cand[k][2];
       float ms = 0.f;
       ce = timed([&]() { return launch_viscous(M, b, tq, 1, s); }, ms);
       if (k == 0) default_ms = best_ms = ms;
       if (ms < best_ms) {
         best_ms = ms;
-        best = {0, cand[k][0], cand[k][1]};
+        best = {cand[k][0], cand[k][1], cand[k][2]};
       }
     }
+    b.tile_alt = 0;
     c->tuning[key] = best;
-    std::snprintf(buf, sizeof buf, "viscous N=%d geo=%d: %s kernel, %d blocks/SM (0 = max): %.4f ms, default %.4f ms\n",
-                  b.N, b.geo, best[2] ? "cp.async" : "pipelined", best[1], best_ms, default_ms);
+    std::snprintf(buf, sizeof buf,
+                  "viscous N=%d geo=%d: %s kernel, %d elements/tile, %d blocks/SM (0 = max): %.4f ms, default %.4f ms\n",
+                  b.N, b.geo, best[2] ? "cp.async" : "pipelined", tile_epb32(b.N, best[0]), best[1], best_ms,
+                  default_ms);
     rep += buf;
   }
   // one persistent kernel per stage against the separate viscous and inviscid launches, on the

@@ -565,9 +565,9 @@ __device__ __forceinline__ bool tma_item(const DevMesh& M, const double* qin, co
 // (bytes): QV [3] slots of a16(8 n3 + 16) (velocity planes) | NT [6] slots of a16(32 n2 + 16)
 // (neighbours' trace records) | LK 96 | EC 48 | MT 32 | SH 32; work: U [3 n3] velocity
 // deviations and F [9 n3] contravariant viscous fluxes (floats).
-template <int N>
+template <int N, int E = Shape<N>::EPB>
 struct ViscTmaSmem32 {
-  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = Shape<N>::EPB;
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
   static constexpr int SQV = a16(8 * n3 + 16), SNT = a16(32 * n2 + 16);
   static constexpr int iQV = 0, iNT = 3 * SQV, iLK = iNT + 6 * SNT, iEC = iLK + 96, iMT = iEC + 48,
@@ -1327,13 +1327,13 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
 // divergence. Two consumer barriers per tile: U is written before the first and read before
 // the second; F is written between them and read after the second, and the next tile writes F
 // only after its first barrier.
-template <int N, int GEO>
+template <int N, int GEO, int E = Shape<N>::EPB>
 __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B, const double* q, char* smc,
                                               int bar_base) {
-  using S = Shape<N>;
-  using P = ViscTmaSmem32<N>;
+  using S = Tile<N, E>;
+  using P = ViscTmaSmem32<N, E>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
-  constexpr int NC = Shape<N>::threads;  // consumer threads
+  constexpr int NC = S::threads;  // consumer threads
   void* bar0 = smc + P::oBAR + bar_base;
   void* bar1 = smc + P::oBAR + bar_base + 8;
   void* ebar0 = smc + P::oBAR + bar_base + 16;
@@ -1558,11 +1558,12 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
   }
 }
 
-template <int N, int GEO>
-__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+// E: elements per tile, the default shape (Shape<N>::EPB) or the alternative (AltEPB<N>)
+template <int N, int GEO, int E>
+__global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_viscous32t(DevMesh M, Bucket B, const double* q) {
   extern __shared__ __align__(128) char smc[];
-  viscous_tiles<N, GEO>(M, B, q, smc, 0);
+  viscous_tiles<N, GEO, E>(M, B, q, smc, 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1724,9 +1725,12 @@ static cudaError_t prep32_n() {
                                 (int)visc_smem32<N, 1>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 2>())) != cudaSuccess) return r;
-  const int vs = (int)ViscTmaSmem32<N>::bytes;
-  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
+  constexpr int EA = AltEPB<N>::value;
+  const int vs = (int)ViscTmaSmem32<N>::bytes, va = (int)ViscTmaSmem32<N, EA>::bytes;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0, Shape<N>::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1, Shape<N>::EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, vs)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 0, EA>, cudaFuncAttributeMaxDynamicSharedMemorySize, va)) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_viscous32t<N, 1, EA>, cudaFuncAttributeMaxDynamicSharedMemorySize, va)) != cudaSuccess) return r;
   if ((r = prep_inv<N, Shape<N>::EPB, 0>()) != cudaSuccess) return r;
   if ((r = prep_inv<N, Shape<N>::EPB, 1>()) != cudaSuccess) return r;
   if ((r = prep_inv<N, Shape<N>::EPB, 2>()) != cudaSuccess) return r;
@@ -1759,22 +1763,23 @@ cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, 
 
 // grid of the persistent viscous kernel: every resident block slot of the GPU (or b.bps blocks
 // per SM when the autotuner chose fewer), at most one per tile
-template <int N, int GEO>
+template <int N, int GEO, int E>
 static cudaError_t launch_vpipe(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
-  const size_t sm = ViscTmaSmem32<N>::bytes;
+  const size_t sm = ViscTmaSmem32<N, E>::bytes;
   if (per_sm < 0) {
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_viscous32t<N, GEO>, Shape<N>::threads + 32, sm);
+    cudaError_t r =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_viscous32t<N, GEO, E>, Tile<N, E>::threads + 32, sm);
     if (r != cudaSuccess) return r;
     int dev = 0;
     if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
     if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
     if (per_sm < 1) per_sm = 1;
   }
-  const int ntiles = (b.count + Shape<N>::EPB - 1) / Shape<N>::EPB;
+  const int ntiles = (b.count + E - 1) / E;
   const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
   const int grid = ntiles < bps * sms ? ntiles : bps * sms;
-  k_viscous32t<N, GEO><<<grid, Shape<N>::threads + 32, sm, s>>>(M, b, q);
+  k_viscous32t<N, GEO, E><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q);
   return cudaGetLastError();
 }
 
@@ -1783,7 +1788,10 @@ cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q,
   if (b.geo != 2 && b.visc_alt == 0) {  // box and affine: the pipelined kernel unless tuned away
     if (!b.blink || !b.bmeta) return cudaErrorInvalidValue;
     DG_SWITCH_N(b.N, {
-      return b.geo == 0 ? launch_vpipe<NN, 0>(M, b, q, s) : launch_vpipe<NN, 1>(M, b, q, s);
+      constexpr int EA = AltEPB<NN>::value, ED = Shape<NN>::EPB;
+      if (b.tile_alt && EA != ED)
+        return b.geo == 0 ? launch_vpipe<NN, 0, EA>(M, b, q, s) : launch_vpipe<NN, 1, EA>(M, b, q, s);
+      return b.geo == 0 ? launch_vpipe<NN, 0, ED>(M, b, q, s) : launch_vpipe<NN, 1, ED>(M, b, q, s);
     });
     return cudaSuccess;
   }

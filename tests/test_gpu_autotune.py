@@ -59,7 +59,7 @@ def test_every_choice_gives_the_same_residual(make, tmp_path):
         choices = {}
         for n, g in keys:
             choices[(0, n, g)] = (alt, bps, 0)
-            choices[(1, n, g)] = (0, bps, valt)
+            choices[(1, n, g)] = (alt, bps, valt)  # the viscous pass's tile shape too
         _forced_cache(cache, choices)
         T = gpu_solver(w, precision=1, params=p)
         rep = T.autotune(str(cache))
