@@ -595,6 +595,17 @@ def main():
         cmp["byte_model_speedup"] = bytes_ns / bytes_mixed
         cmp["meets_byte_model_bar"] = cmp["speedup_vs_all_ns"] >= cmp["byte_model_speedup"]
         out["comparison"] = cmp
+        # overlapped launches (the default) against plain ones, same mesh and flags: 20 chained
+        # steps each, alternated twice
+        ov = {"on": [], "off": []}
+        for _ in range(2):
+            for name, on in (("off", False), ("on", True)):
+                S.set_launch_overlap(on)
+                q.copy_(q0)
+                ov[name].append(timed_steps(S, q, g, dt, stream, 20, warmup=3))
+        S.set_launch_overlap(True)
+        out["launch_overlap"] = {"on_ms_per_step": sum(ov["on"]) / 2, "off_ms_per_step": sum(ov["off"]) / 2,
+                                 "steps": 20}
         # region detection (Sec. 2.1) on the benchmark state: one pass over the whole mesh
         out["detect"] = time_detection(S, w, q, q0, stream)
         # the compressible form (App. A), FP64, on its own periodic workload

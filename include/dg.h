@@ -328,6 +328,18 @@ dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm,
  * stop_tile != -1 are wrong by design. Errors: DG_ERR_ARG for a NULL ctx or out-of-range value. */
 dg_status dg_set_wait_limit(dg_ctx* ctx, int64_t polls, int stop_tile);
 
+/* Overlapped launches of the pipelined reduced-precision passes (precision 1..3, box and affine
+ * elements; the paper has no counterpart). With enable = 1 (the default) each of their launches
+ * carries programmatic stream serialisation: its blocks may be scheduled while the kernel before
+ * it in the stream drains, and every thread waits in the kernel (griddepcontrol.wait) for that
+ * kernel to complete before it touches memory the kernel may write or read. An inviscid launch
+ * that directly follows the viscous pass of its stage runs the Euler elements that have no NS
+ * neighbour and no mortar face first, without that wait. Results are identical either way;
+ * enable = 0 gives plain launches (for comparison). dg_phase_times always uses plain launches.
+ * Applies to every later launch (the captured step graph is rebuilt). Errors: DG_ERR_ARG for a
+ * NULL ctx or enable outside {0, 1}. */
+dg_status dg_set_launch_overlap(dg_ctx* ctx, int enable);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 dg_status dg_check_device(dg_ctx* ctx, void* stream);
 

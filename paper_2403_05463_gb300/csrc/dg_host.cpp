@@ -358,6 +358,9 @@ struct dg_ctx {
   // while a chained RK step is captured: the trace-buffer parity of its stage 0, whether stage 2
   // writes the next stage's traces too, and whether the trace kernel is left out
   int cap_parity = 0, cap_write_all = 0, cap_no_traces = 0;
+  // the last phase that launched anything was the viscous pass (phase 2): the inviscid launch
+  // that follows it may start its independent entries before that pass has completed
+  bool visc_last = false;
   // host-variant staging
   double* trace_buf[2] = {nullptr, nullptr};
   double* stage_q = nullptr;
@@ -745,11 +748,25 @@ dg_status rebuild_flags(dg_ctx* c) {
   dg_status st = dev_upload(c, "link", link, &dl);
   if (st != DG_OK) return st;
   c->M.link = dl;
-  // all-element buckets: NS elements first, each class in element order, so that a tile of the
-  // pipelined passes holds elements of one flag (no NS/Euler imbalance inside a tile)
+  // all-element buckets in three classes, each in element order: Euler elements with no NS
+  // neighbour and no mortar face (independent of the viscous and mortar passes: an overlapped
+  // inviscid launch runs them while those passes drain), the other Euler elements, the NS
+  // elements. A tile of the pipelined passes then holds elements of one flag but at the one
+  // boundary between the classes.
+  auto dep_class = [&](int32_t e) {
+    if (c->flag[e]) return 2;
+    for (int f = 0; f < 6; ++f) {
+      const int32_t nb = c->nb[(int64_t)e * 6 + f];
+      if (nb >= 0 && (c->flag[nb] || c->order[nb] != c->order[e])) return 1;
+    }
+    return 0;
+  };
+  std::vector<uint8_t> cls(c->ne, 0);
+  for (int64_t e = 0; e < c->ne; ++e) cls[e] = (uint8_t)dep_class((int32_t)e);
   for (size_t i = 0; i < c->all_buckets.size() && i < c->all_lists.size(); ++i) {
     std::vector<int32_t>& L = c->all_lists[i];
-    std::stable_partition(L.begin(), L.end(), [&](int32_t e) { return c->flag[e] != 0; });
+    std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) { return cls[x] < cls[y]; });
+    c->all_buckets[i].n_indep = (int)std::count_if(L.begin(), L.end(), [&](int32_t e) { return cls[e] == 0; });
     std::vector<int64_t> bo(L.size()), bt(L.size());
     for (size_t j = 0; j < L.size(); ++j) {
       bo[j] = c->off[L[j]];
@@ -1003,10 +1020,12 @@ cudaError_t launch_stage(const dg_ctx* c, const DevMesh& M, const double* q, dou
   return launch_stage32(M, bv, c->all_buckets[0], q, out, g, stage, write_tr, s);
 }
 
-dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage, double dt,
-                      cudaStream_t s, int* nlaunch) {
+dg_status issue_phase_impl(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage,
+                           double dt, cudaStream_t s, int* nlaunch) {
   int nl = 0;
   DevMesh M = c->M;
+  // the inviscid launch directly after this stage's viscous pass (no mortar pass between)
+  M.after_visc = phase == 4 && c->visc_last && c->n_mortar_all == 0 && M.overlap ? 1 : 0;
   const int cur = (mode == MODE_RK) ? (stage + c->cap_parity) % 2 : 0;
   M.Tq = c->trace_buf[cur];
   M.Tq_next = c->trace_buf[1 - cur];
@@ -1126,6 +1145,17 @@ dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double
   }
   if (nlaunch) *nlaunch += nl;
   return DG_OK;
+}
+
+// Every phase is issued through here: it records whether the last launching phase was the
+// viscous pass, which the next phase-4 launch may overlap.
+dg_status issue_phase(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage, double dt,
+                      cudaStream_t s, int* nlaunch) {
+  int nl = 0;
+  const dg_status st = issue_phase_impl(c, phase, q, out, g, mode, stage, dt, s, &nl);
+  if (nl > 0) c->visc_last = phase == 2;
+  if (nlaunch) *nlaunch += nl;
+  return st;
 }
 
 dg_status issue_stage(dg_ctx* c, const double* q, double* out, double* g, int mode, int stage, double dt,
@@ -1301,6 +1331,8 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
   c->M.err = derr;
   c->M.wait_polls = kWaitPolls;
   c->M.stop_tile = -1;
+  c->M.overlap = 1;
+  c->M.after_visc = 0;
   apply_params(c);
   c->order.assign(c->ne, (int8_t)std::max(3, c->gdeg));
   c->flag.assign(c->ne, 1);
@@ -1657,6 +1689,14 @@ dg_status dg_set_wait_limit(dg_ctx* c, int64_t polls, int stop_tile) {
   return DG_OK;
 }
 
+dg_status dg_set_launch_overlap(dg_ctx* c, int enable) {
+  if (!c) return fail(DG_ERR_ARG, "ctx is NULL");
+  if (enable != 0 && enable != 1) return fail(DG_ERR_ARG, "enable must be 0 or 1");
+  c->M.overlap = enable;
+  destroy_graph(c);  // captured launches hold the previous attribute
+  return DG_OK;
+}
+
 dg_status dg_conservation(dg_ctx* c, const double* R, double* out, void* stream) {
   if (!c || !R || !out) return fail(DG_ERR_ARG, "NULL argument");
   CU(cudaSetDevice(c->device));
@@ -1700,6 +1740,13 @@ dg_status dg_phase_times(dg_ctx* c, double* q, double* g, double dt, int reps, d
   cudaStream_t s = (cudaStream_t)stream;
   c->M.dt32 = (float)dt;
   destroy_graph(c);  // the captured step holds its own dt
+  // plain launches: each phase's events bracket its own kernels only (restored on every return)
+  struct KeepOverlap {
+    DevMesh& M;
+    int v;
+    ~KeepOverlap() { M.overlap = v; }
+  } keep{c->M, c->M.overlap};
+  c->M.overlap = 0;
   cudaEvent_t ev[DG_NPHASES + 1];
   for (auto& e : ev) CU(cudaEventCreate(&e));
   double acc[DG_NPHASES] = {0, 0, 0, 0, 0};
@@ -1885,12 +1932,14 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
       rep += buf;
     } else {
       float ms_sep = 0.f, ms_fused = 0.f;
+      DevMesh Mi = M;  // as in a step: the inviscid launch overlaps the viscous pass before it
+      Mi.after_visc = M.overlap;
       ce = timed(
           [&]() {
             cudaError_t r = cudaSuccess;
             for (const Bucket& b : c->ns_buckets)
               if (r == cudaSuccess) r = launch_viscous(M, b, tq, 1, s);
-            if (r == cudaSuccess) r = launch_inviscid(M, bi, tq, tq, tr, MODE_RK, 1, 1e-9, 1, 1, s);
+            if (r == cudaSuccess) r = launch_inviscid(c->ns_buckets.empty() ? M : Mi, bi, tq, tq, tr, MODE_RK, 1, 1e-9, 1, 1, s);
             return r;
           },
           ms_sep);

@@ -82,6 +82,10 @@ struct DevMesh {
   int stop_tile;             // test hook, -1 off: the producer warp of block 0 of each pipelined
                              // launch returns before staging its stop_tile-th tile; -2: block 0
                              // of the persistent stage kernel skips its grid-barrier arrival
+  int overlap;               // 1: the pipelined FP32 passes are overlapped launches (programmatic
+                             // stream serialisation; they wait in the kernel for the launch before)
+  int after_visc;            // set per launch: this inviscid launch directly follows the viscous
+                             // pass of its stage, so its bucket's independent entries need not wait
   double nu, c0sq, cs, cv;
   int closure, riemann;
   int mixed_face;            // 0 average, 1 one-sided viscous flux on NS/Euler faces
@@ -147,6 +151,9 @@ struct Bucket {
   int tile_alt = 0;   // inviscid: 1 = the alternative elements-per-tile shape
   int bps = 0;        // pipelined passes: resident blocks per SM (0 = as many as fit)
   int visc_alt = 0;   // viscous, box/affine: 1 = the cp.async-staged kernel instead of the pipelined one
+  // all-element buckets: the first n_indep entries are Euler elements with no NS neighbour and
+  // no mortar face (their inviscid pass touches nothing the viscous or mortar passes write)
+  int n_indep = 0;
 };
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };

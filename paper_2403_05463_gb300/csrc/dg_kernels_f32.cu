@@ -13,6 +13,8 @@
 //   * mortar faces (rare): the projected flux minus the own flux in FP64.
 // The derivative matrix D is held in FP32 in shared memory; contractions accumulate in FP32.
 // The only FP64 arithmetic per node is the RK update g <- A g + dt R, q <- q + B g.
+#include <climits>
+
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -722,6 +724,17 @@ __device__ __forceinline__ void tma_stage(const DevMesh& M, const Bucket& B, con
   }
 }
 
+// Overlapped launches (PTX griddepcontrol, programmatic dependent launch): a kernel launched
+// with programmatic stream serialisation may be scheduled before the previous kernel in the
+// stream has completed. pdl_wait() blocks the calling thread until that kernel has completed
+// and its memory operations are visible; pdl_launch_dependents() allows the next such launch to
+// be scheduled once every block of this grid has issued it or exited. In a kernel launched
+// without the attribute both return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // bounded wait on an mbarrier phase: false if it did not complete within the limit
 __device__ __forceinline__ bool mbar_wait_bounded(void* bar, unsigned parity, int polls) {
   bool ok = false;
@@ -772,9 +785,13 @@ struct InvMinBlocks {
 // operand is split into big + small TF32 parts and C accumulates big*big + big*small +
 // small*big in FP32. Consumer warps take the (element, direction, row tile) items in turn and
 // store C per direction; after the face phase each node sums its three directions.
+// dep_tile: tiles from this index on touch memory that the previous launch in the stream may
+// still write or read (an overlapped launch), so each thread waits for that launch first; the
+// tiles before it are independent of that launch.
 template <int N, int GEO, int MODE, int E, int VOL>
 __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B, const double* qin, double* out,
-                                               double* g, int stage, int write_tr, char* smc, int bar_base) {
+                                               double* g, int stage, int write_tr, char* smc, int bar_base,
+                                               int dep_tile) {
   // VOL 3 / 4: VOL 0 / 2 on box elements with the divergence S = sum_d Ja_dd D_d u_d taken in FP64
   // from the staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the
   // momentum fluxes (U_c S); the FP32 (or tensor-core) contractions carry only the rest of the
@@ -830,6 +847,7 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
       char* IN = b ? IN1 : IN0;
       store_recs<P>(B, tile, recs, IN);
       if (tile + (int)gridDim.x < ntiles) load_recs<E>(B, tile + gridDim.x, recs);
+      if (tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();  // this block's first such tile
       __syncwarp();
       tma_stage<N, P, false>(M, B, qin, tile, IN, b ? bar1 : bar0);
     }
@@ -857,6 +875,9 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
   // ---- consumer threads ----------------------------------------------------------------
   int it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    // at this block's first dependent tile, before the bounded wait for the tile's data (the
+    // wait for the previous launch is not part of the poll budget)
+    if (tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();
     const int cur = it & 1;
     const int i = tile * EPB + le;
     const bool active = lane_ok && i < B.count;
@@ -1314,7 +1335,16 @@ template <int N, int GEO, int MODE, int E, int VOL>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_inviscid32t(DevMesh M, Bucket B, const double* qin, double* out, double* g, int stage, int write_tr) {
   extern __shared__ __align__(128) char smc[];
-  inviscid_tiles<N, GEO, MODE, E, VOL>(M, B, qin, out, g, stage, write_tr, smc, 0);
+  // An overlapped launch: the next launch (which waits for this one before it touches memory)
+  // may be scheduled as soon as every block runs. After the viscous pass of the same stage
+  // (M.after_visc) the bucket's first B.n_indep entries (Euler elements without an NS or
+  // mortar neighbour) read and write nothing that pass touches, and run without waiting for it.
+  pdl_launch_dependents();
+  const int dep_tile = M.after_visc ? B.n_indep / Tile<N, E>::EPB : 0;
+  inviscid_tiles<N, GEO, MODE, E, VOL>(M, B, qin, out, g, stage, write_tr, smc, 0, dep_tile);
+  // every thread waits for the previous launch before it exits, so this launch completes after
+  // it: a later launch that waits for this one has waited for that one too
+  pdl_wait();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1563,6 +1593,11 @@ template <int N, int GEO, int E>
 __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>::value))
     k_viscous32t(DevMesh M, Bucket B, const double* q) {
   extern __shared__ __align__(128) char smc[];
+  // an overlapped launch: every input comes from the previous launches, and the inviscid pass
+  // before it reads the viscous buffers this pass writes. The next launch is allowed only
+  // after the wait, so it may rely on everything before this launch having completed.
+  pdl_wait();
+  pdl_launch_dependents();
   viscous_tiles<N, GEO, E>(M, B, q, smc, 0);
 }
 
@@ -1625,7 +1660,7 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     viscous_tiles<N, GEO>(M, Bv, q, smc, 0);
     if (!grid_barrier(M)) return;
   }
-  inviscid_tiles<N, GEO, MODE_RK, Shape<N>::EPB, 0>(M, Bi, q, out, g, stage, write_tr, smc, 32);
+  inviscid_tiles<N, GEO, MODE_RK, Shape<N>::EPB, 0>(M, Bi, q, out, g, stage, write_tr, smc, 32, INT_MAX);
 }
 
 template <int N>
@@ -1761,6 +1796,25 @@ cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, 
   return cudaGetLastError();
 }
 
+// Launch of a pipelined pass; with M.overlap it carries programmatic stream serialisation, so
+// its blocks may be scheduled while the previous kernel in the stream drains (the kernel waits
+// for that kernel with griddepcontrol.wait before it touches memory the kernel may write).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_overlapped(const DevMesh& M, void (*kern)(KArgs...), int grid, int block, size_t smem,
+                                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = M.overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // grid of the persistent viscous kernel: every resident block slot of the GPU (or b.bps blocks
 // per SM when the autotuner chose fewer), at most one per tile
 template <int N, int GEO, int E>
@@ -1779,8 +1833,7 @@ static cudaError_t launch_vpipe(const DevMesh& M, const Bucket& b, const double*
   const int ntiles = (b.count + E - 1) / E;
   const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
   const int grid = ntiles < bps * sms ? ntiles : bps * sms;
-  k_viscous32t<N, GEO, E><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q);
-  return cudaGetLastError();
+  return launch_overlapped(M, k_viscous32t<N, GEO, E>, grid, Tile<N, E>::threads + 32, sm, s, M, b, q);
 }
 
 cudaError_t launch_viscous32(const DevMesh& M, const Bucket& b, const double* q, cudaStream_t s) {
@@ -1827,8 +1880,8 @@ static cudaError_t launch_pipe(const DevMesh& M, const Bucket& b, const double* 
   const int ntiles = (b.count + E - 1) / E;
   const int bps = b.bps > 0 && b.bps < per_sm ? b.bps : per_sm;
   const int grid = ntiles < bps * sms ? ntiles : bps * sms;
-  k_inviscid32t<N, GEO, MODE, E, VOL><<<grid, Tile<N, E>::threads + 32, sm, s>>>(M, b, q, out, g, stage, write_tr);
-  return cudaGetLastError();
+  return launch_overlapped(M, k_inviscid32t<N, GEO, MODE, E, VOL>, grid, Tile<N, E>::threads + 32, sm, s, M, b, q,
+                           out, g, stage, write_tr);
 }
 
 template <int N, int E, int VOL>

@@ -104,6 +104,7 @@ def load():
         L.dg_detect_regions.argtypes = [_vp, _vp, ctypes.POINTER(GMM), _vp, _vp, _vp, _vp]
         L.dg_check_device.argtypes = [_vp, _vp]
         L.dg_set_wait_limit.argtypes = [_vp, ctypes.c_int64, ctypes.c_int]
+        L.dg_set_launch_overlap.argtypes = [_vp, ctypes.c_int]
         L.dg_phase_times.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
         L.dg_phase_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_launches_per_residual.argtypes = [_vp]
@@ -361,6 +362,11 @@ class Solver:
         """Poll budget of the bounded device-side waits (0: the default) and the stop-tile test
         hook (-1: off); see dg_set_wait_limit."""
         _check(load().dg_set_wait_limit(self.h, int(polls), int(stop_tile)))
+
+    def set_launch_overlap(self, enable=True):
+        """Overlapped (programmatic-serialisation) launches of the pipelined passes, on by
+        default; off gives plain launches with identical results. See dg_set_launch_overlap."""
+        _check(load().dg_set_launch_overlap(self.h, 1 if enable else 0))
 
     def check_device(self, stream=None):
         _check(load().dg_check_device(self.h, _stream_handle(stream)))
