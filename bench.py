@@ -546,31 +546,35 @@ def main():
     for line in tuning.splitlines():
         if line.startswith("stage ") and "persistent kernel" in line and "separate" in line:
             import re
-            m = re.search(r"one persistent kernel ([0-9.]+) ms, separate ([0-9.]+) ms", line)
+            m = re.search(r"one persistent kernel ([0-9.]+) ms, one launch with tile queues ([0-9.]+) ms, "
+                          r"separate ([0-9.]+) ms", line)
             if m:
-                out["stage_kernel"] = {"chosen": "persistent" if ": one persistent kernel:" in line else "separate",
-                                       "persistent_ms_per_stage": float(m.group(1)),
-                                       "separate_ms_per_stage": float(m.group(2))}
+                chosen = "persistent" if ": one persistent kernel:" in line else \
+                    ("tile_queues" if ": one launch with tile queues:" in line else "separate")
+                out["stage_kernel"] = {"chosen": chosen, "persistent_ms_per_stage": float(m.group(1)),
+                                       "tile_queues_ms_per_stage": float(m.group(2)),
+                                       "separate_ms_per_stage": float(m.group(3))}
 
     if not args.no_extras:
         # mixed vs all-NS and all-Euler on the same mesh and GPU
+        # each flag set timed three times, interleaved (20 chained steps after 3 warm-up steps):
+        # the median of the three
         cmp = {}
         bytes_mixed = 3 * sum(S.phase_bytes().values())
-        for name, fl in (("all_ns", np.ones(w.n_elem, np.uint8)), ("all_euler", np.zeros(w.n_elem, np.uint8))):
-            S.set_flags(fl)
-            if name == "all_ns":
-                bytes_ns = 3 * sum(S.phase_bytes().values())
-            q.copy_(q0)
-            S.rk_step(q, g, dt, 3, stream=stream)
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            S.rk_step(q, g, dt, 20, stream=stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            cmp[name] = {"ms_per_step": a.elapsed_time(b) / 20, "value": dof * 3 / (a.elapsed_time(b) / 20 * 1e-3)}
+        runs = {"mixed": [], "all_ns": [], "all_euler": []}
+        sets = (("mixed", w.flags), ("all_ns", np.ones(w.n_elem, np.uint8)), ("all_euler", np.zeros(w.n_elem, np.uint8)))
+        for _ in range(3):
+            for name, fl in sets:
+                S.set_flags(fl)
+                if name == "all_ns":
+                    bytes_ns = 3 * sum(S.phase_bytes().values())
+                q.copy_(q0)
+                runs[name].append(timed_steps(S, q, g, dt, stream, 20, warmup=3))
         S.set_flags(w.flags)
+        for name in ("all_ns", "all_euler"):
+            t = statistics.median(runs[name])
+            cmp[name] = {"ms_per_step": t, "value": dof * 3 / (t * 1e-3), "runs_ms": runs[name]}
+        ms_mixed = statistics.median(runs["mixed"])
         # "at equal accuracy": what dropping the viscous terms in the Euler elements changes,
         # the residual of the flagged run against the all-NS one on the Euler elements
         q.copy_(q0)
@@ -586,10 +590,11 @@ def main():
         del R_mixed, R_ns, dR, euler_nodes
         f = w.ns_fraction
         bar = f * cmp["all_ns"]["ms_per_step"] + (1 - f) * cmp["all_euler"]["ms_per_step"]
-        cmp["mixed_ms_per_step"] = ms
+        cmp["mixed_ms_per_step"] = ms_mixed
+        cmp["mixed_runs_ms"] = runs["mixed"]
         cmp["bar_ms_per_step"] = bar
-        cmp["speedup_vs_all_ns"] = cmp["all_ns"]["ms_per_step"] / ms
-        cmp["meets_bar"] = ms <= bar
+        cmp["speedup_vs_all_ns"] = cmp["all_ns"]["ms_per_step"] / ms_mixed
+        cmp["meets_bar"] = ms_mixed <= bar
         # the same bar in the byte model's form: the speedup over all-NS that the algorithmic
         # bytes predict, W_allNS / W_mixed
         cmp["byte_model_speedup"] = bytes_ns / bytes_mixed

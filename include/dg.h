@@ -235,9 +235,12 @@ dg_status dg_conservation(dg_ctx* ctx, const double* R_dev, double* out_host, vo
  * viscous pass on box/affine elements the pipelined (bulk-copy) kernel with either tile shape at
  * those block counts or the cp.async-staged kernel; and, when the mesh is one (order, box or affine) bucket without
  * p-nonconforming faces run with FP32 contractions, whether each Runge-Kutta stage after its
- * traces runs as one persistent cooperative kernel (the viscous pass, a bounded grid barrier,
- * the inviscid pass and update) instead of separate viscous and inviscid launches (chosen only
- * when at least 1% faster).
+ * traces runs as one launch (the default tile shapes) instead of separate viscous and inviscid
+ * launches (chosen only when at least 1% faster): either one persistent cooperative kernel
+ * (the viscous pass, a bounded grid barrier, the inviscid pass and update), or one kernel whose
+ * blocks take tiles from queues (viscous tiles first, then the inviscid tiles of the Euler
+ * elements with no NS neighbour, which run while the viscous pass drains, then the rest, which
+ * wait on a bounded counter of finished viscous tiles).
  * Timing uses a library-owned scratch state, so q, g and R are
  * untouched; the choices then apply to every later call (they are kept per order and
  * geometry kind across dg_set_orders / dg_set_element_flags) and the captured step graph
@@ -315,8 +318,9 @@ dg_status dg_detect_regions(dg_ctx* ctx, const double* q_dev, const dg_gmm* gmm,
  * for a free buffer (the producer) with a bounded number of polls; when the budget runs out
  * the warp records DG_ERR_TIMEOUT in the device error word (read by dg_check_device, which
  * names the site: 1 inviscid consumers, 2 inviscid producer, 3 viscous consumers, 4 viscous
- * producer, 5 the grid barrier of the persistent stage kernel) and returns, leaving the CUDA
- * context usable; dg_check_device also resets that grid barrier.
+ * producer, 5 the grid barrier of the persistent stage kernel, 6 the producer's wait for the
+ * finished viscous tiles in the one-launch stage kernel with tile queues) and returns, leaving
+ * the CUDA context usable; dg_check_device also resets that grid barrier and those queues.
  *   polls      poll budget of every such wait, 1 .. 2^31 - 1; 0 restores the default 2^22.
  *   stop_tile  test hook: -1 off; k >= 0 makes the producer warp of block 0 of every pipelined
  *              launch return before staging its k-th tile, so that block's consumers wait for

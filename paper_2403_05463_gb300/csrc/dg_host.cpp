@@ -698,6 +698,8 @@ dg_status upload_entry_tables(dg_ctx* c, const std::string& prefix, const std::v
       bm[j].troff = c->troff[L[j]];
       bm[j].elem = L[j];
       bm[j].flag = c->flag[L[j]];
+      bm[j].has_mortar = 0;
+      for (int f = 0; f < 6; ++f) bm[j].has_mortar |= link[(size_t)L[j] * 6 + f].kind == FK_MORTAR ? 1 : 0;
       bm[j].pad = 0;
     }
     FaceLink* dbl;
@@ -748,25 +750,33 @@ dg_status rebuild_flags(dg_ctx* c) {
   dg_status st = dev_upload(c, "link", link, &dl);
   if (st != DG_OK) return st;
   c->M.link = dl;
-  // all-element buckets in three classes, each in element order: Euler elements with no NS
-  // neighbour and no mortar face (independent of the viscous and mortar passes: an overlapped
-  // inviscid launch runs them while those passes drain), the other Euler elements, the NS
-  // elements. A tile of the pipelined passes then holds elements of one flag but at the one
-  // boundary between the classes.
+  // all-element buckets in four groups, each in element order: Euler elements with no NS
+  // neighbour and no mortar face (independent of the viscous and mortar passes: the inviscid
+  // pass runs them while those passes drain), the NS elements, the other Euler elements, and
+  // last about two rounds of tiles' worth of independent elements held back from the first
+  // group (the lightest tiles end the stage, so its last round is short). n_indep counts the
+  // first group only. A tile of the pipelined passes then holds elements of one flag but at the
+  // boundaries between the groups.
   auto dep_class = [&](int32_t e) {
-    if (c->flag[e]) return 2;
+    if (c->flag[e]) return 1;
     for (int f = 0; f < 6; ++f) {
       const int32_t nb = c->nb[(int64_t)e * 6 + f];
-      if (nb >= 0 && (c->flag[nb] || c->order[nb] != c->order[e])) return 1;
+      if (nb >= 0 && (c->flag[nb] || c->order[nb] != c->order[e])) return 2;
     }
     return 0;
   };
   std::vector<uint8_t> cls(c->ne, 0);
   for (int64_t e = 0; e < c->ne; ++e) cls[e] = (uint8_t)dep_class((int32_t)e);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
   for (size_t i = 0; i < c->all_buckets.size() && i < c->all_lists.size(); ++i) {
     std::vector<int32_t>& L = c->all_lists[i];
     std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) { return cls[x] < cls[y]; });
-    c->all_buckets[i].n_indep = (int)std::count_if(L.begin(), L.end(), [&](int32_t e) { return cls[e] == 0; });
+    const int n0 = (int)std::count_if(L.begin(), L.end(), [&](int32_t e) { return cls[e] == 0; });
+    // two rounds of the persistent grid (about three blocks per SM) at this order's tile size
+    const int tail = n0 < (int)L.size() ? std::min(n0 / 4, 2 * 3 * sms * tile_epb32(c->all_buckets[i].N, 0)) : 0;
+    std::rotate(L.begin() + (n0 - tail), L.begin() + n0, L.end());
+    c->all_buckets[i].n_indep = n0 - tail;
     std::vector<int64_t> bo(L.size()), bt(L.size());
     for (size_t j = 0; j < L.size(); ++j) {
       bo[j] = c->off[L[j]];
@@ -996,28 +1006,30 @@ bool stage_fusable(const dg_ctx* c) {
   const DevMesh& M = c->M;
   if (M.precision != 1 || M.tc || M.split || M.div64 || M.model || M.nodes) return false;
   if (c->all_buckets.size() != 1 || c->n_mortar_all) return false;
+  // (the one-launch kernels use the default tile shapes whatever the separate launches use)
   const Bucket& bi = c->all_buckets[0];
-  if (bi.geo > 1 || bi.tile_alt) return false;
+  if (bi.geo > 1) return false;
   if (c->ns_buckets.size() > 1) return false;
   if (c->ns_buckets.size() == 1) {
     const Bucket& bv = c->ns_buckets[0];
-    if (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo || bv.visc_alt || bv.tile_alt)) return false;
+    if (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo)) return false;
   }
   return true;
 }
 
-// ... and is used where the autotuner chose it
-bool stage_fused(const dg_ctx* c) {
-  if (!stage_fusable(c)) return false;
+// ... and is used where the autotuner chose it: 0 separate launches, 1 the persistent kernel
+// with a grid barrier, 2 the one-launch kernel with tile queues
+int stage_fused(const dg_ctx* c) {
+  if (!stage_fusable(c)) return 0;
   auto it = c->tuning.find({2, c->all_buckets[0].N, c->all_buckets[0].geo});
-  return it != c->tuning.end() && it->second[0] == 1;
+  return it != c->tuning.end() && (it->second[0] == 1 || it->second[0] == 2) ? it->second[0] : 0;
 }
 
 cudaError_t launch_stage(const dg_ctx* c, const DevMesh& M, const double* q, double* out, double* g, int stage,
-                         int write_tr, cudaStream_t s) {
+                         int write_tr, int kind, cudaStream_t s) {
   Bucket bv{};
   if (!c->ns_buckets.empty()) bv = c->ns_buckets[0];
-  return launch_stage32(M, bv, c->all_buckets[0], q, out, g, stage, write_tr, s);
+  return launch_stage32(M, bv, c->all_buckets[0], q, out, g, stage, write_tr, kind == 2 ? 1 : 0, s);
 }
 
 dg_status issue_phase_impl(dg_ctx* c, int phase, const double* q, double* out, double* g, int mode, int stage,
@@ -1134,7 +1146,7 @@ dg_status issue_phase_impl(dg_ctx* c, int phase, const double* q, double* out, d
       break;
     default:
       if (mode == MODE_RK && stage_fused(c)) {
-        CU(launch_stage(c, M, q, out, g, stage, write_tr, s));
+        CU(launch_stage(c, M, q, out, g, stage, write_tr, stage_fused(c), s));
         ++nl;
         break;
       }
@@ -1322,12 +1334,14 @@ dg_status dg_create_mesh(const dg_mesh_desc* mesh, const dg_params* params, int 
     }
     *gdst[i] = dtab;
   }
-  int* derr;  // [0..3] the device error word, [4..5] the persistent stage kernel's grid barrier
-  if ((st = dev_alloc(c, "err", 8, &derr)) != DG_OK) {
+  // [0..3] the device error word, [4..5] the persistent stage kernel's grid barrier, [8..11] the
+  // one-launch stage kernel's tile queues
+  int* derr;
+  if ((st = dev_alloc(c, "err", 16, &derr)) != DG_OK) {
     dg_destroy(c);
     return st;
   }
-  cudaMemset(derr, 0, 32);
+  cudaMemset(derr, 0, 16 * sizeof(int));
   c->M.err = derr;
   c->M.wait_polls = kWaitPolls;
   c->M.stop_tile = -1;
@@ -1671,8 +1685,9 @@ dg_status dg_check_device(dg_ctx* c, void* stream) {
   int h[4] = {0, 0, 0, 0};
   CU(cudaMemcpy(h, c->M.err, sizeof h, cudaMemcpyDeviceToHost));
   if (h[0] != 0) {
-    // also the grid barrier's words: a launch that timed out can leave arrivals counted
-    CU(cudaMemset(c->M.err, 0, 8 * sizeof(int)));
+    // also the grid barrier's and the tile queues' words: a launch that timed out can leave
+    // arrivals or claims counted
+    CU(cudaMemset(c->M.err, 0, 16 * sizeof(int)));
     if (h[0] == DG_ERR_TIMEOUT) return fail(DG_ERR_TIMEOUT, "a device-side wait timed out (site %d)", h[1]);
     return fail(DG_ERR_DEVICE, "device error %d at site %d", h[0], h[1]);
   }
@@ -1928,7 +1943,8 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
     if (hit != cached.end()) {
       c->tuning[key] = hit->second;
       std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: cached, %s\n", bi.N, bi.geo,
-                    hit->second[0] ? "one persistent kernel" : "separate launches");
+                    hit->second[0] == 2 ? "one launch with tile queues"
+                                        : (hit->second[0] ? "one persistent kernel" : "separate launches"));
       rep += buf;
     } else {
       float ms_sep = 0.f, ms_fused = 0.f;
@@ -1943,14 +1959,22 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
             return r;
           },
           ms_sep);
-      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, s); }, ms_fused);
-      // a tie keeps the separate launches (per-pass timing and rooflines stay per kernel): the
-      // persistent form must be at least 1% faster
-      const int fused = ce == cudaSuccess && ms_fused < 0.99f * ms_sep ? 1 : 0;
+      float ms_queue = 0.f;
+      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 1, s); }, ms_fused);
+      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 2, s); }, ms_queue);
+      // a tie keeps the separate launches (per-pass timing and rooflines stay per kernel): a
+      // one-launch form must be at least 1% faster
+      int fused = 0;
+      float best = ms_sep;
+      if (ce == cudaSuccess && ms_fused < 0.99f * best) fused = 1, best = ms_fused;
+      if (ce == cudaSuccess && ms_queue < (fused ? best : 0.99f * best)) fused = 2, best = ms_queue;
       c->tuning[key] = {fused, 0, 0};
-      std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: %s: %.4f ms (one persistent kernel %.4f ms, separate %.4f ms)\n",
-                    bi.N, bi.geo, fused ? "one persistent kernel" : "separate launches", fused ? ms_fused : ms_sep,
-                    ms_fused, ms_sep);
+      std::snprintf(buf, sizeof buf,
+                    "stage N=%d geo=%d: %s: %.4f ms (one persistent kernel %.4f ms, one launch with tile queues %.4f "
+                    "ms, separate %.4f ms)\n",
+                    bi.N, bi.geo,
+                    fused == 2 ? "one launch with tile queues" : (fused ? "one persistent kernel" : "separate launches"),
+                    best, ms_fused, ms_queue, ms_sep);
       rep += buf;
     }
   }

@@ -77,7 +77,8 @@ struct DevMesh {
   const double* interp;      // [(Ns*NP+Nd)*NP*NP + i*NP + j]: Lagrange interpolation Ns -> Nd
   const double* proj;        // [(Nh*NP+Nl)*NP*NP + i*NP + j]: L2 projection Nh -> Nl
   int* err;                  // device error word [0..3]; [4], [5] the grid barrier of the
-                             // persistent stage kernel (arrivals, generation)
+                             // persistent stage kernel (arrivals, generation); [8..11] the tile
+                             // queues of the one-launch stage kernel (16 ints)
   int wait_polls;            // polls of a bounded mbarrier wait before it gives up (timeout)
   int stop_tile;             // test hook, -1 off: the producer warp of block 0 of each pipelined
                              // launch returns before staging its stop_tile-th tile; -2: block 0
@@ -129,7 +130,8 @@ struct EntryMeta {
   int64_t troff;  // first face-trace slot of the element
   int32_t elem;   // element id
   int32_t flag;   // 0 Euler, 1 NS
-  int64_t pad;
+  int32_t has_mortar;  // 1: one of its faces is a mortar face
+  int32_t pad;
 };
 static_assert(sizeof(EntryMeta) == 32, "EntryMeta is copied in 16-byte blocks");
 
@@ -196,10 +198,12 @@ cudaError_t launch_inviscid32(const DevMesh& M, const Bucket& b, const double* q
                               int mode, int stage, int write_tr, cudaStream_t s);
 
 // One persistent launch per RK stage of a single (order, box/affine) bucket: the viscous pass over
-// bv's NS elements, a bounded grid barrier, the inviscid pass and update over bi (cooperative
-// launch; the default tile shape, FP32 contractions). The grid barrier uses err[4], err[5].
+// bv's NS elements, then the inviscid pass and update over bi (the default tile shape, FP32
+// contractions). queue 0: static tile order with a bounded grid barrier between the passes
+// (cooperative launch; err[4], err[5]); queue 1: tiles from queues, the inviscid tiles that read
+// viscous results waiting on a counter of finished viscous tiles (overlapped launch; err[8..11]).
 cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
-                           double* g, int stage, int write_tr, cudaStream_t s);
+                           double* g, int stage, int write_tr, int queue, cudaStream_t s);
 
 // elements per tile of the FP32 inviscid pass at order N: the default shape or the alternative
 int tile_epb32(int N, int alt);

@@ -460,7 +460,9 @@ struct AltEPB {
   static constexpr int value = N <= 4 ? Shape<N>::EPB / 2 : (N <= 6 ? 2 : Shape<N>::EPB);
 };
 
-template <int N, int E = Shape<N>::EPB, bool KEPC = false, bool TCX = false>
+// LAST0: buffer 0 after the work area (the one-launch stage kernel with tile queues stages its
+// first inviscid tile there while the viscous phase still uses the space before it)
+template <int N, int E = Shape<N>::EPB, bool KEPC = false, bool TCX = false, bool LAST0 = false>
 struct TmaSmem32 {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n, EPB = E;
   static constexpr int a16(int x) { return (x + 15) / 16 * 16; }
@@ -477,8 +479,11 @@ struct TmaSmem32 {
   // F holds the three directions' results afterwards and no extra tile is needed)
   static constexpr int FB = KEPC ? 64 * n3 : 48 * n3;
   static constexpr int wF = 0, wQ = FB, wT = FB + 32 * n3, work_elem = FB + 32 * n3 + 96 * n2;
-  static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
-  static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
+  static constexpr int oBAR = 0, oD = 128;
+  static constexpr int oIN0 = LAST0 ? 384 + EPB * (in_elem + work_elem) : 384;
+  static constexpr int oIN1 = LAST0 ? 384 : oIN0 + EPB * in_elem;
+  static constexpr int oW = oIN1 + EPB * in_elem;
+  static constexpr size_t bytes = (size_t)384 + (size_t)EPB * (2 * in_elem + work_elem);
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -575,6 +580,8 @@ struct ViscTmaSmem32 {
   static constexpr int iQV = 0, iNT = 3 * SQV, iLK = iNT + 6 * SNT, iEC = iLK + 96, iMT = iEC + 48,
                        iSH = iMT + 32, in_elem = a16(iSH + 32);
   static constexpr int ITEMS = 10;  // copies per element: 3 QV, 6 NT, EC
+  // work area per element: U (3 x n3 FP32), F (9 x n3 FP32); the velocity's (hi, lo) pairs
+  // overwrite its staged FP64 values in the input buffer (each node's own slot)
   static constexpr int wU = 0, wF = 12 * n3, work_elem = a16(48 * n3);
   static constexpr int oBAR = 0, oD = 128, oIN0 = 384, oIN1 = oIN0 + EPB * in_elem, oW = oIN1 + EPB * in_elem;
   static constexpr size_t bytes = (size_t)oW + (size_t)EPB * work_elem;
@@ -735,11 +742,54 @@ __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// Launch of a pipelined pass; with M.overlap it carries programmatic stream serialisation, so
+// its blocks may be scheduled while the previous kernel in the stream drains (the kernel waits
+// for that kernel with griddepcontrol.wait before it touches memory the kernel may write).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_overlapped(const DevMesh& M, void (*kern)(KArgs...), int grid, int block, size_t smem,
+                                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = M.overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Tile queue of a persistent pass (one launch per RK stage): the producer warp claims the next
+// tile index from a global counter (lane 0's atomic, broadcast to the warp) and passes it to the
+// consumers in shared memory, its last tile flagged with kLastTile (-1: the block got no tile).
+constexpr int kLastTile = 1 << 30;
+__device__ __forceinline__ int claim_tile(unsigned* counter) {
+  unsigned v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(counter, 1u);
+  return (int)__shfl_sync(0xffffffffu, v, 0);
+}
+
 // bounded wait on an mbarrier phase: false if it did not complete within the limit
 __device__ __forceinline__ bool mbar_wait_bounded(void* bar, unsigned parity, int polls) {
   bool ok = false;
   for (int spin = 0; spin < polls && !ok; ++spin) ok = mbar_try_wait(bar, parity);
   return ok;
+}
+// The producer's wait for a free input buffer (it-th tile, buffer it & 1, empty barrier ebar):
+// tiles 0 and 1 find their buffers free. With shift1 (the stage kernel with tile queues) buffer
+// 1 overlaps the viscous phase's shared memory, and its empty barrier's first phase is the
+// consumers' release of that space, so tile 1 waits for phase 0 and tile it for phase it / 2.
+__device__ __forceinline__ bool buffer_free(void* ebar, int it, bool shift1, int polls) {
+  if (shift1 && (it & 1)) return mbar_wait_bounded(ebar, (unsigned)((it >> 1) & 1), polls);
+  return it < 2 || mbar_wait_bounded(ebar, (unsigned)(((it >> 1) - 1) & 1), polls);
 }
 __device__ __forceinline__ void mbar_arrive(void* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
@@ -785,13 +835,20 @@ struct InvMinBlocks {
 // operand is split into big + small TF32 parts and C accumulates big*big + big*small +
 // small*big in FP32. Consumer warps take the (element, direction, row tile) items in turn and
 // store C per direction; after the face phase each node sums its three directions.
-// dep_tile: tiles from this index on touch memory that the previous launch in the stream may
-// still write or read (an overlapped launch), so each thread waits for that launch first; the
-// tiles before it are independent of that launch.
-template <int N, int GEO, int MODE, int E, int VOL>
+// dep_tile: tiles from this index on touch memory that the viscous pass (or, in a plain
+// overlapped launch, the previous launch in the stream) may still write or read; the tiles
+// before it are independent of it. Static order (QU false): block b takes tiles b, b + grid,
+// ...; each thread waits for the previous launch (griddepcontrol) before its first dependent
+// tile. Queue order (QU true, one launch per stage after the viscous tiles): the producer warp
+// claims tiles from *qc and passes each index to the consumers in shared memory (the last one
+// flagged, see claim_tile); before staging a dependent tile it waits until *vdone (viscous tiles
+// finished, each block's count added after its results) reaches vneed. Its buffer 0 lies after
+// the work area and buffer 1's first release is the end of the stage kernel's viscous phase.
+template <int N, int GEO, int MODE, int E, int VOL, bool QU = false>
 __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B, const double* qin, double* out,
                                                double* g, int stage, int write_tr, char* smc, int bar_base,
-                                               int dep_tile) {
+                                               int dep_tile, unsigned* qc = nullptr, const unsigned* vdone = nullptr,
+                                               unsigned vneed = 0) {
   // VOL 3 / 4: VOL 0 / 2 on box elements with the divergence S = sum_d Ja_dd D_d u_d taken in FP64
   // from the staged FP64 state. It gives the pressure row (-c0^2 S) and the U_c du_d part of the
   // momentum fluxes (U_c S); the FP32 (or tensor-core) contractions carry only the rest of the
@@ -799,12 +856,13 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
   constexpr bool KEP = VOL == 1, TC = VOL == 2 || VOL == 4;
   constexpr bool div64 = GEO == 0 && (VOL == 3 || VOL == 4);
   using S = Tile<N, E>;
-  using P = TmaSmem32<N, E, KEP && GEO == 2, TC>;
+  using P = TmaSmem32<N, E, KEP && GEO == 2, TC, QU>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
   void* bar0 = smc + P::oBAR + bar_base;        // full[0]
   void* bar1 = smc + P::oBAR + bar_base + 8;    // full[1]
   void* ebar0 = smc + P::oBAR + bar_base + 16;  // empty[0]
   void* ebar1 = smc + P::oBAR + bar_base + 24;  // empty[1]
+  int* tslot = reinterpret_cast<int*>(smc + P::oBAR + bar_base + 64);  // queue order: tile per buffer
   constexpr int NC = S::threads;  // consumer threads
   float* sD = reinterpret_cast<float*>(smc + P::oD);
   char* const IN0 = smc + P::oIN0;
@@ -816,25 +874,30 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
   float* g32 = reinterpret_cast<float*>(g);
   const float c0sq = M.c0sq32;
   const float invw = c_ops32.w0inv[N];
-  for (int t = tid; t < n2; t += nthr) sD[t] = c_ops32.D[N][t];
-  if (tid == 0) {
-    mbar_init(bar0, 32);
-    mbar_init(bar1, 32);
-    mbar_init(ebar0, NC / 32);
-    mbar_init(ebar1, NC / 32);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (!QU) {  // queue order: the stage kernel set these up before its viscous phase
+    for (int t = tid; t < n2; t += nthr) sD[t] = c_ops32.D[N][t];
+    if (tid == 0) {
+      mbar_init(bar0, 32);
+      mbar_init(bar1, 32);
+      mbar_init(ebar0, NC / 32);
+      mbar_init(ebar1, NC / 32);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid >= NC) {
     // ---- producer warp ----------------------------------------------------------------
     // the records of the next tile are loaded one tile ahead, so their latency is hidden
     // behind the wait for a free buffer and the copies of the current tile
     TileRecs<E> recs;
-    if ((int)blockIdx.x < ntiles) load_recs<E>(B, blockIdx.x, recs);
+    int tile = QU ? claim_tile(qc) : (int)blockIdx.x;
+    int next = QU ? claim_tile(qc) : tile + (int)gridDim.x;  // one tile ahead
+    if (tile < ntiles) load_recs<E>(B, tile, recs);
+    bool dep_ok = false;
     int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (; tile < ntiles; tile = next, next = QU ? claim_tile(qc) : next + (int)gridDim.x, ++it) {
       const int b = it & 1;
-      if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1), M.wait_polls)) {
+      if (!buffer_free(b ? ebar1 : ebar0, it, QU, M.wait_polls)) {
         if (tid == NC) {
           atomicCAS(&M.err[0], 0, kErrTimeout);
           atomicCAS(&M.err[1], 0, 2);
@@ -845,11 +908,34 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
       // (every copy staged before was waited for by the consumers; none is left in flight)
       if (blockIdx.x == 0 && it == M.stop_tile) return;
       char* IN = b ? IN1 : IN0;
+      if (QU && tid == NC) tslot[b] = tile | (next < ntiles ? 0 : kLastTile);
       store_recs<P>(B, tile, recs, IN);
-      if (tile + (int)gridDim.x < ntiles) load_recs<E>(B, tile + gridDim.x, recs);
-      if (tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();  // this block's first such tile
+      if (next < ntiles) load_recs<E>(B, next, recs);
+      if (!QU && tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();  // this block's first such tile
+      if (QU && tile >= dep_tile && !dep_ok) {
+        // every viscous tile finished (bounded, site 6); then the bulk copies may read its results
+        bool ok = ld_acquire_u32(vdone) >= vneed;
+        for (int spin = 0; !ok && spin < M.wait_polls; ++spin) {
+          __nanosleep(128);
+          ok = ld_acquire_u32(vdone) >= vneed;
+        }
+        if (!ok) {
+          if (tid == NC) {
+            atomicCAS(&M.err[0], 0, kErrTimeout);
+            atomicCAS(&M.err[1], 0, 6);
+          }
+          return;
+        }
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        dep_ok = true;
+      }
       __syncwarp();
       tma_stage<N, P, false>(M, B, qin, tile, IN, b ? bar1 : bar0);
+    }
+    if (QU && it == 0) {  // no tile for this block: an empty one with index -1 (buffer 0 is free)
+      if (tid == NC) tslot[0] = -1;
+      __syncwarp();
+      mbar_arrive(bar0);
     }
     return;
   }
@@ -873,14 +959,13 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
     fdesc[r] = t < NFI ? (le2 | f << 5 | (ab % n) << 8 | (ab / n) << 11 | face_node(f, n, ab % n, ab / n) << 14) : -1;
   }
   // ---- consumer threads ----------------------------------------------------------------
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+  bool more = true;
+  int tile = QU ? 0 : (int)blockIdx.x;
+  for (int it = 0; QU ? more : tile < ntiles; ++it, tile += QU ? 0 : (int)gridDim.x) {
     // at this block's first dependent tile, before the bounded wait for the tile's data (the
     // wait for the previous launch is not part of the poll budget)
-    if (tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();
+    if (!QU && tile >= dep_tile && tile - (int)gridDim.x < dep_tile) pdl_wait();
     const int cur = it & 1;
-    const int i = tile * EPB + le;
-    const bool active = lane_ok && i < B.count;
     const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1), M.wait_polls);
     if (consumer_any(!ok, NC)) {
       if (tid == 0) {
@@ -889,6 +974,17 @@ __device__ __forceinline__ void inviscid_tiles(const DevMesh& M, const Bucket& B
       }
       return;
     }
+    if (QU) {
+      tile = tslot[cur];
+      if (tile < 0) break;
+      // (a dependent tile's data, and the viscous results its threads load themselves, are
+      // ordered before this point: the producer's acquire of the finished-tile counter, then
+      // its arrival on the tile's mbarrier, which this wait acquires)
+      more = !(tile & kLastTile);
+      tile &= ~kLastTile;
+    }
+    const int i = tile * EPB + le;
+    const bool active = lane_ok && i < B.count;
     char* IN = cur ? IN1 : IN0;
     const char* INe = IN + le * P::in_elem;
     const EntryMeta* MT = reinterpret_cast<const EntryMeta*>(INe + P::iMT);
@@ -1350,16 +1446,95 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
 // ---------------------------------------------------------------------------------------
 // viscous pass, persistent, TMA-staged (box and affine elements)
 // ---------------------------------------------------------------------------------------
-// The same producer/consumer scheme as the inviscid pass: the last warp stages each tile's
-// velocity planes, neighbour trace records and constants; the consumer threads (one per node)
-// compute the BR1 gradient with its lifting, the eddy viscosity, tau and the contravariant
-// viscous fluxes, write the viscous face traces, and release the input buffer before the
-// divergence. Two consumer barriers per tile: U is written before the first and read before
-// the second; F is written between them and read after the second, and the next tile writes F
-// only after its first barrier.
-template <int N, int GEO, int E = Shape<N>::EPB>
-__device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B, const double* q, char* smc,
-                                              int bar_base) {
+// Line contractions in shared memory, one thread per (element, direction, line): along the
+// line of direction d with index l (the other two node indices a = l % n, b = l / n), the
+// thread loads the n values of each of three node arrays once and forms all n outputs
+// out[i] = sum_m D[i][m] in[m], summed in order m = 0 .. N, with D read from the constant bank
+// (compile-time indices: no load, no register). in(c) = src + c * src_stride, out(c) = dst +
+// c * dst_stride; dst may equal src (each line's values are read before they are written, and
+// no other line touches them). With `ends`, ends[0][c] is added to out(c) at i = 0 and
+// ends[1][c] at i = N.
+template <int N>
+__device__ __forceinline__ void line_contract3(const float* src, int src_stride, float* dst, int dst_stride, int d,
+                                               int l, const float (*ends)[3] = nullptr) {
+  constexpr int n = N + 1, n2 = n * n;
+  const int a = l % n, b = l / n;
+  const int base = d == 0 ? a * n + b * n2 : (d == 1 ? a + b * n2 : a + b * n);
+  const int st = d == 0 ? 1 : (d == 1 ? n : n2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float u[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) u[m] = src[c * src_stride + base + m * st];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc = fmaf(c_ops32.D[N][i * n + m], u[m], acc);
+      if (ends && i == 0) acc += ends[0][c];
+      if (ends && i == N) acc += ends[1][c];
+      dst[c * dst_stride + base + i * st] = acc;
+    }
+  }
+}
+
+// BR1 lifting (1/w_end) (u* - u) S at the two end nodes of the line (d, l) of one element
+// (the face nodes (a, b) = (l % n, l / n) of faces 2d and 2d + 1), for box and affine
+// elements: it equals adding sg (u* - u)_c / (2 w_end) to du_c/dxi_d there (the metric terms
+// multiply both alike). Conforming, inflow and wall faces; mortar faces give 0 here. INe: the
+// element's staged input, its velocity planes already overwritten by (hi, lo) pairs per node.
+template <int N, typename P>
+__device__ __forceinline__ void face_lift(const char* INe, const DevMesh& M, float invw, int d, int l,
+                                          float lift[2][3]) {
+  constexpr int n = N + 1, n2 = n * n;
+  const int a = l % n, b = l / n;
+  const FaceLink* LK = reinterpret_cast<const FaceLink*>(INe + P::iLK);
+  const unsigned char* SH = reinterpret_cast<const unsigned char*>(INe + P::iSH);
+  const float2* H0 = reinterpret_cast<const float2*>(INe + P::iQV + SH[0]);
+  const float2* H1 = reinterpret_cast<const float2*>(INe + P::iQV + P::SQV + SH[1]);
+  const float2* H2 = reinterpret_cast<const float2*>(INe + P::iQV + 2 * P::SQV + SH[2]);
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int f = 2 * d + side, e0 = side ? N : 0;
+    const int node = d == 0 ? e0 + a * n + b * n2 : (d == 1 ? a + e0 * n + b * n2 : a + b * n + e0 * n2);
+    const FaceLink L = LK[f];
+    const float2 h0 = H0[node], h1 = H1[node], h2 = H2[node];
+    float jump[3] = {0.f, 0.f, 0.f};
+    if (L.kind == FK_CONF) {
+      int a1, b1;
+      inv_orient(L.orient, N, a, b, a1, b1);
+      // the neighbour's record (p, u, v, w as hi, lo); 16-byte aligned, no shift
+      const float4* tr = reinterpret_cast<const float4*>(INe + P::iNT + f * P::SNT) + 2 * (a1 + n * b1);
+      const float4 t01 = tr[0], t23 = tr[1];
+      jump[0] = (t01.z - h0.x) + (t01.w - h0.y);
+      jump[1] = (t23.x - h1.x) + (t23.y - h1.y);
+      jump[2] = (t23.z - h2.x) + (t23.w - h2.y);
+    } else if (L.kind == FK_INFLOW) {
+      const float2 hh[3] = {h0, h1, h2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float ih, il;
+        split_hilo(M.inflow[1 + c], ih, il);
+        jump[c] = (ih - hh[c].x) + (il - hh[c].y);
+      }
+    } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
+      const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
+      const float sg = side ? 1.f : -1.f;
+      const float Sv[3] = {sg * EC->Ja[d * 3], sg * EC->Ja[d * 3 + 1], sg * EC->Ja[d * 3 + 2]};
+      const float uo[3] = {h0.x + h0.y, h1.x + h1.y, h2.x + h2.y};
+      wall_jump<float>(L.kind, uo, Sv, jump);
+    }
+    const float sl = (side ? 0.5f : -0.5f) * invw;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lift[side][c] = sl * jump[c];
+  }
+}
+
+// Static or queue order of the tiles as in inviscid_tiles (qc: the claim counter). Returns the
+// number of tiles this block's consumers finished (thread 0's count).
+template <int N, int GEO, int E = Shape<N>::EPB, bool QU = false>
+__device__ __forceinline__ int viscous_tiles(const DevMesh& M, const Bucket& B, const double* q, char* smc,
+                                             int bar_base, unsigned* qc = nullptr) {
   using S = Tile<N, E>;
   using P = ViscTmaSmem32<N, E>;
   constexpr int n = S::n, n2 = S::n2, n3 = S::n3, EPB = S::EPB;
@@ -1368,7 +1543,7 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
   void* bar1 = smc + P::oBAR + bar_base + 8;
   void* ebar0 = smc + P::oBAR + bar_base + 16;
   void* ebar1 = smc + P::oBAR + bar_base + 24;
-  float* sD = reinterpret_cast<float*>(smc + P::oD);
+  int* tslot = reinterpret_cast<int*>(smc + P::oBAR + bar_base + 64);  // queue order: tile per buffer
   char* const IN0 = smc + P::oIN0;
   char* const IN1 = smc + P::oIN1;
   char* W = smc + P::oW;
@@ -1376,7 +1551,6 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
   const int ntiles = (B.count + EPB - 1) / EPB;
   float* Tvf = reinterpret_cast<float*>(M.Tv);
   float* rvf = reinterpret_cast<float*>(M.rv);
-  for (int t = tid; t < n2; t += NC) sD[t] = c_ops32.D[N][t];
   if (tid == 0) {
     mbar_init(bar0, 32);
     mbar_init(bar1, 32);
@@ -1388,47 +1562,62 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
   if (tid >= NC) {
     // ---- producer warp ----------------------------------------------------------------
     TileRecs<EPB> recs;
-    if ((int)blockIdx.x < ntiles) load_recs<EPB>(B, blockIdx.x, recs);
+    int tile = QU ? claim_tile(qc) : (int)blockIdx.x;
+    int next = QU ? claim_tile(qc) : tile + (int)gridDim.x;  // one tile ahead
+    if (tile < ntiles) load_recs<EPB>(B, tile, recs);
     int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (; tile < ntiles; tile = next, next = QU ? claim_tile(qc) : next + (int)gridDim.x, ++it) {
       const int b = it & 1;
       if (it >= 2 && !mbar_wait_bounded(b ? ebar1 : ebar0, (unsigned)(((it >> 1) - 1) & 1), M.wait_polls)) {
         if (tid == NC) {
           atomicCAS(&M.err[0], 0, kErrTimeout);
           atomicCAS(&M.err[1], 0, 4);
         }
-        return;
+        return 0;
       }
-      if (blockIdx.x == 0 && it == M.stop_tile) return;  // test hook, as in the inviscid pass
+      if (blockIdx.x == 0 && it == M.stop_tile) return 0;  // test hook, as in the inviscid pass
       char* IN = b ? IN1 : IN0;
+      if (QU && tid == NC) tslot[b] = tile | (next < ntiles ? 0 : kLastTile);
       store_recs<P>(B, tile, recs, IN);
-      if (tile + (int)gridDim.x < ntiles) load_recs<EPB>(B, tile + gridDim.x, recs);
+      if (next < ntiles) load_recs<EPB>(B, next, recs);
       __syncwarp();
       tma_stage<N, P, true>(M, B, q, tile, IN, b ? bar1 : bar0);
     }
-    return;
+    if (QU && it == 0) {  // no tile for this block: an empty one with index -1 (buffer 0 is free)
+      if (tid == NC) tslot[0] = -1;
+      __syncwarp();
+      mbar_arrive(bar0);
+    }
+    return 0;
   }
   int le = tid / n3;
   const int p = tid % n3;
   const bool lane_ok = le < EPB;
   if (!lane_ok) le = EPB - 1;
   const int ii[3] = {p % n, (p / n) % n, p / n2};
-  const int str[3] = {1, n, n2};
   float* U = reinterpret_cast<float*>(W + le * P::work_elem + P::wU);
   float* F = reinterpret_cast<float*>(W + le * P::work_elem + P::wF);
   const float invw = c_ops32.w0inv[N];
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+  int done = 0;
+  bool more = true;
+  int tile = QU ? 0 : (int)blockIdx.x;
+  for (int it = 0; QU ? more : tile < ntiles; ++it, tile += QU ? 0 : (int)gridDim.x) {
     const int cur = it & 1;
-    const bool active = lane_ok && tile * EPB + le < B.count;
     const bool ok = mbar_wait_bounded(cur ? bar1 : bar0, (unsigned)((it >> 1) & 1), M.wait_polls);
     if (consumer_any(!ok, NC)) {
       if (tid == 0) {
         atomicCAS(&M.err[0], 0, kErrTimeout);
         atomicCAS(&M.err[1], 0, 3);
       }
-      return;
+      return done;
     }
+    if (QU) {
+      tile = tslot[cur];
+      if (tile < 0) break;
+      more = !(tile & kLastTile);
+      tile &= ~kLastTile;
+    }
+    const bool active = lane_ok && tile * EPB + le < B.count;
     const char* INe = (cur ? IN1 : IN0) + le * P::in_elem;
     const EntryMeta* MT = reinterpret_cast<const EntryMeta*>(INe + P::iMT);
     const ElemConst32* EC = reinterpret_cast<const ElemConst32*>(INe + P::iEC);
@@ -1436,13 +1625,37 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
     int64_t off = 0, troff = 0;
     int e = 0;
     float Ja[9], invJ = 0.f, delta = 0.f;
-    float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
     // the element's reference velocity (hi parts of node 0), once per element, through the
     // element's F area (the previous tile's divergence read it before this tile's vote; this
     // tile writes F only after its first barrier)
     if (active && p == 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) F[c] = hi_part(reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c])[0]);
+    }
+    consumer_sync(NC);
+    if (active) {
+      float uh[3], ul[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double* QV = reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c]);
+        split_hilo(QV[p], uh[c], ul[c]);
+        U[c * n3 + p] = (uh[c] - F[c]) + ul[c];  // deviation from the element's first node
+        reinterpret_cast<float2*>(const_cast<double*>(QV))[p] = make_float2(uh[c], ul[c]);
+      }
+    }
+    consumer_sync(NC);
+    // gradient: du_c / dxi_d along every line of direction d, into the F area as
+    // [(c * 3 + d) * n3 + node] (the reference velocity there was read before the last
+    // barrier), with the BR1 lifting of the line's two end faces (the faces of direction d;
+    // mortar faces are lifted per node below)
+    for (int t = tid; t < EPB * 3 * n2; t += NC) {
+      const int lt = t / (3 * n2), r = t - lt * (3 * n2), d = r / n2, l = r - d * n2;
+      if (tile * EPB + lt >= B.count) continue;
+      char* We = W + lt * P::work_elem;
+      float lift[2][3];
+      face_lift<N, P>((cur ? IN1 : IN0) + lt * P::in_elem, M, invw, d, l, lift);
+      line_contract3<N>(reinterpret_cast<const float*>(We + P::wU), n3, reinterpret_cast<float*>(We + P::wF) + d * n3,
+                        3 * n3, d, l, lift);
     }
     consumer_sync(NC);
     if (active) {
@@ -1453,51 +1666,30 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
       invJ = EC->invJ;
 #pragma unroll
       for (int k = 0; k < 9; ++k) Ja[k] = EC->Ja[k];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double* QV = reinterpret_cast<const double*>(INe + P::iQV + c * P::SQV + SH[c]);
-        split_hilo(QV[p], uh[c], ul[c]);
-        U[c * n3 + p] = (uh[c] - F[c]) + ul[c];  // deviation from the element's first node
-      }
-    }
-    consumer_sync(NC);
-    if (active) {
       float G[3][3];
       {
+        // this node's nine derivatives (its own thread overwrites them with F below)
         float du[3][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const int bs = p - ii[d] * str[d];
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const float dm = sD[ii[d] * n + m];
-            const int pm = bs + m * str[d];
-            s0 += dm * U[pm];
-            s1 += dm * U[n3 + pm];
-            s2 += dm * U[2 * n3 + pm];
-          }
-          du[0][d] = s0;
-          du[1][d] = s1;
-          du[2][d] = s2;
-        }
+          for (int d = 0; d < 3; ++d) du[c][d] = F[(c * 3 + d) * n3 + p];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < 3; ++k)
             G[c][k] = GEO == 0 ? Ja[k * 4] * du[c][k] : Ja[k] * du[c][0] + Ja[3 + k] * du[c][1] + Ja[6 + k] * du[c][2];
       }
-      // BR1 lifting on the faces of this node: (1/w_end) (u* - u) S
-      const FaceLink* LK = reinterpret_cast<const FaceLink*>(INe + P::iLK);
+      // BR1 lifting on this node's mortar faces (projected u*_c S_k from the mortar pass)
+      if (MT->has_mortar) {
+        const FaceLink* LK = reinterpret_cast<const FaceLink*>(INe + P::iLK);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (ii[d] != 0 && ii[d] != N) continue;
-        const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
-        const float sg = side ? 1.f : -1.f;
-        const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
-        const FaceLink L = LK[f];
-        const float Sv[3] = {sg * Ja[d * 3], sg * Ja[d * 3 + 1], sg * Ja[d * 3 + 2]};
-        if (L.kind == FK_MORTAR) {
+        for (int d = 0; d < 3; ++d) {
+          if (ii[d] != 0 && ii[d] != N) continue;
+          const int side = ii[d] == N ? 1 : 0, f = 2 * d + side;
+          if (LK[f].kind != FK_MORTAR) continue;
+          const double sg = side ? 1.0 : -1.0;
+          const int a = d == 0 ? ii[1] : ii[0], b = d == 2 ? ii[1] : ii[2];
           const int64_t ms = troff + f * n2 + a + n * b;
           double Sd[3];
 #pragma unroll
@@ -1508,32 +1700,6 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
 #pragma unroll
             for (int k = 0; k < 3; ++k) G[c][k] += invw * (float)(M.LU[(c * 3 + k) * M.tr_total + ms] - uc * Sd[k]);
           }
-        } else {
-          float jump[3] = {0.f, 0.f, 0.f};
-          if (L.kind == FK_CONF) {
-            int a1, b1;
-            inv_orient(L.orient, N, a, b, a1, b1);
-            // the neighbour's record (p, u, v, w as hi, lo); 16-byte aligned, no shift
-            const float4* tr = reinterpret_cast<const float4*>(INe + P::iNT + f * P::SNT) + 2 * (a1 + n * b1);
-            const float4 t01 = tr[0], t23 = tr[1];
-            jump[0] = (t01.z - uh[0]) + (t01.w - ul[0]);
-            jump[1] = (t23.x - uh[1]) + (t23.y - ul[1]);
-            jump[2] = (t23.z - uh[2]) + (t23.w - ul[2]);
-          } else if (L.kind == FK_INFLOW) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float ih, il;
-              split_hilo(M.inflow[1 + c], ih, il);
-              jump[c] = (ih - uh[c]) + (il - ul[c]);
-            }
-          } else if (L.kind == FK_WALL || L.kind == FK_SLIP) {
-            const float uo[3] = {uh[0] + ul[0], uh[1] + ul[1], uh[2] + ul[2]};
-            wall_jump<float>(L.kind, uo, Sv, jump);
-          }
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) G[c][k] += invw * 0.5f * jump[c] * Sv[k];
         }
       }
 #pragma unroll
@@ -1567,25 +1733,28 @@ __device__ __forceinline__ void viscous_tiles(const DevMesh& M, const Bucket& B,
         for (int c = 0; c < 3; ++c) Tvf[ms * 3 + c] = sg * Fv[d][c];
       }
     }
+    // the input buffer is no longer read; its velocity slots were written here, and the next
+    // bulk copies into it are async-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     consumer_sync(NC);
-    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);  // the input buffer is no longer read
-    if (active) {
-      float V[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int bs = p - ii[d] * str[d];
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          const float dm = sD[ii[d] * n + m];
-          const int pm = bs + m * str[d];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) V[c] += dm * F[(d * 3 + c) * n3 + pm];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) rvf[c * M.total + off + p] = V[c];
+    if ((tid & 31) == 0) mbar_arrive(cur ? ebar1 : ebar0);
+    // divergence: D_d applied along every line of direction d to the three fluxes F[d][c],
+    // in place
+    for (int t = tid; t < EPB * 3 * n2; t += NC) {
+      const int lt = t / (3 * n2), r = t - lt * (3 * n2);
+      if (tile * EPB + lt >= B.count) continue;
+      float* Fe = reinterpret_cast<float*>(W + lt * P::work_elem + P::wF) + r / n2 * 3 * n3;
+      line_contract3<N>(Fe, n3, Fe, n3, r / n2, r % n2);
     }
+    consumer_sync(NC);
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        rvf[c * M.total + off + p] = (F[c * n3 + p] + F[(3 + c) * n3 + p]) + F[(6 + c) * n3 + p];
+    }
+    ++done;
   }
+  return done;
 }
 
 // E: elements per tile, the default shape (Shape<N>::EPB) or the alternative (AltEPB<N>)
@@ -1604,12 +1773,6 @@ __global__ void __launch_bounds__(Tile<N, E>::threads + 32, (InvMinBlocks<N, E>:
 // ---------------------------------------------------------------------------------------
 // one persistent kernel per Runge-Kutta stage (viscous tiles, grid barrier, inviscid tiles)
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Grid-wide barrier of a launch whose blocks are all resident (a cooperative launch). Bounded:
 // gbar[0] counts the arrivals, the last one resets it and advances the generation gbar[1];
 // a block that sees no new generation within M.wait_polls polls records DG_ERR_TIMEOUT (site 5).
@@ -1664,6 +1827,80 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
 }
 
 template <int N>
+constexpr size_t stage_smem_bound() {
+  return ViscTmaSmem32<N>::bytes > TmaSmem32<N>::bytes ? ViscTmaSmem32<N>::bytes : TmaSmem32<N>::bytes;
+}
+
+// A whole RK stage in one ordinary launch, the tiles taken from queues: every block claims
+// viscous tiles (Bv's NS elements) until that queue is empty and adds the number it finished to
+// a counter; then it claims inviscid tiles (Bi, independent entries first). A block stages a
+// tile that reads the viscous results only once that counter covers every viscous tile, and
+// such tiles are claimed only after every viscous tile was claimed by a running block, so the
+// wait needs no co-resident grid. Until then the blocks run the independent tiles, so the
+// viscous pass drains into inviscid work. Overlapped launch: everything waits for the previous
+// launch first. Queue counters: err[8] viscous claims, err[9] inviscid claims, err[10] viscous
+// tiles finished, err[11] blocks finished; the last block resets them for the next launch.
+template <int N, int GEO>
+__global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
+    k_stage32q(DevMesh M, Bucket Bv, Bucket Bi, const double* q, double* out, double* g, int stage, int write_tr) {
+  extern __shared__ __align__(128) char smc[];
+  constexpr int EPB = Shape<N>::EPB, NC = Shape<N>::threads, n = N + 1;
+  // the inviscid phase's layout keeps its buffer 0 clear of the viscous phase's shared memory, so
+  // its producer stages the first inviscid tile while the consumers finish the viscous tiles
+  using PI = TmaSmem32<N, EPB, false, false, true>;
+  static_assert(PI::oIN0 >= (int)ViscTmaSmem32<N>::bytes, "inviscid buffer 0 overlaps the viscous phase");
+  static_assert(PI::bytes <= stage_smem_bound<N>(), "stage kernel shared memory");
+  unsigned* qc = reinterpret_cast<unsigned*>(M.err + 8);
+  const int tid = threadIdx.x;
+  pdl_wait();
+  pdl_launch_dependents();
+  // the inviscid phase's operator table and barriers (its mbarriers sit 32 bytes after the
+  // viscous phase's; the viscous phase uses no operator table)
+  float* sD = reinterpret_cast<float*>(smc + PI::oD);
+  for (int t = tid; t < n * n; t += blockDim.x) sD[t] = c_ops32.D[N][t];
+  if (tid == 0) {
+    mbar_init(smc + PI::oBAR + 32, 32);
+    mbar_init(smc + PI::oBAR + 40, 32);
+    mbar_init(smc + PI::oBAR + 48, NC / 32);
+    mbar_init(smc + PI::oBAR + 56, NC / 32);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const unsigned nv = (unsigned)((Bv.count + EPB - 1) / EPB);
+  if (Bv.count > 0) {
+    // the producer warp returns from here when the viscous queue is empty and goes on to stage
+    // inviscid tiles; the consumers return when they have finished their viscous tiles
+    const int done = viscous_tiles<N, GEO, EPB, true>(M, Bv, q, smc, 0, qc);
+    if (tid < NC) {
+      consumer_sync(NC);  // the block's viscous results are written
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(qc + 2, (unsigned)done);
+      }
+    }
+  }
+  if (tid < NC) {
+    // release the viscous phase's shared memory to the inviscid buffer 1 (first phase of its
+    // empty barrier); the bulk copies that follow are async-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(smc + PI::oBAR + 56);
+  }
+  inviscid_tiles<N, GEO, MODE_RK, EPB, 0, true>(M, Bi, q, out, g, stage, write_tr, smc, 32, Bi.n_indep / EPB, qc + 1,
+                                                qc + 2, nv);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(qc + 3, 1u) == gridDim.x - 1) {
+      atomicExch(qc, 0u);
+      atomicExch(qc + 1, 0u);
+      atomicExch(qc + 2, 0u);
+      atomicExch(qc + 3, 0u);
+    }
+  }
+}
+
+template <int N>
 constexpr size_t stage_smem32() {
   return ViscTmaSmem32<N>::bytes > TmaSmem32<N>::bytes ? ViscTmaSmem32<N>::bytes : TmaSmem32<N>::bytes;
 }
@@ -1696,11 +1933,32 @@ static cudaError_t launch_stage_n(const DevMesh& M, const Bucket& bv, const Buck
   return cudaLaunchKernelEx(&cfg, k_stage32t<N, GEO>, M, bv, bi, q, out, g, stage, write_tr);
 }
 
+template <int N, int GEO>
+static cudaError_t launch_stage_q(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
+                                  double* g, int stage, int write_tr, cudaStream_t s) {
+  static int per_sm = -1, sms = 0;
+  const size_t sm = stage_smem32<N>();
+  if (per_sm < 0) {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32q<N, GEO>, Shape<N>::threads + 32, sm);
+    if (r != cudaSuccess) return r;
+    int dev = 0;
+    if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int bps = bi.bps > 0 && bi.bps < per_sm ? bi.bps : per_sm;
+  return launch_overlapped(M, k_stage32q<N, GEO>, bps * sms, Shape<N>::threads + 32, sm, s, M, bv, bi, q, out, g,
+                           stage, write_tr);
+}
+
 cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
-                           double* g, int stage, int write_tr, cudaStream_t s) {
+                           double* g, int stage, int write_tr, int queue, cudaStream_t s) {
   if (bi.geo > 1 || (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo))) return cudaErrorInvalidValue;
   if (!bi.blink || !bi.bmeta || (bv.count > 0 && (!bv.blink || !bv.bmeta))) return cudaErrorInvalidValue;
   DG_SWITCH_N(bi.N, {
+    if (queue)
+      return bi.geo == 0 ? launch_stage_q<NN, 0>(M, bv, bi, q, out, g, stage, write_tr, s)
+                         : launch_stage_q<NN, 1>(M, bv, bi, q, out, g, stage, write_tr, s);
     return bi.geo == 0 ? launch_stage_n<NN, 0>(M, bv, bi, q, out, g, stage, write_tr, s)
                        : launch_stage_n<NN, 1>(M, bv, bi, q, out, g, stage, write_tr, s);
   });
@@ -1754,6 +2012,10 @@ static cudaError_t prep32_n() {
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_stage32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_stage32q<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem32<N>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_stage32q<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem32<N>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 0>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1794,25 +2056,6 @@ cudaError_t launch_traces32(const DevMesh& M, const Bucket& b, const double* q, 
     k_traces32<NN><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, b.list, b.count, q);
   });
   return cudaGetLastError();
-}
-
-// Launch of a pipelined pass; with M.overlap it carries programmatic stream serialisation, so
-// its blocks may be scheduled while the previous kernel in the stream drains (the kernel waits
-// for that kernel with griddepcontrol.wait before it touches memory the kernel may write).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_overlapped(const DevMesh& M, void (*kern)(KArgs...), int grid, int block, size_t smem,
-                                     cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = M.overlap ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // grid of the persistent viscous kernel: every resident block slot of the GPU (or b.bps blocks

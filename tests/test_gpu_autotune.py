@@ -109,37 +109,71 @@ def _stage_case(flags_p=0.3, n=10, order=4):
     return small_mixed(w, seed=44, flags_p=flags_p)
 
 
+STAGE_CHOICES = {0: "separate launches", 1: "one persistent kernel", 2: "one launch with tile queues"}
+
+
 @pytest.mark.parametrize("flags_p", [0.0, 0.3, 1.0])
 @pytest.mark.parametrize("order", [3, 4, 5])
 def test_persistent_stage_kernel_matches_separate_launches(flags_p, order, tmp_path):
-    # one persistent kernel per RK stage (viscous pass, grid barrier, inviscid pass) against the
-    # separate launches: the same device code per element, so the same bits
+    # one launch per RK stage (the persistent kernel with a grid barrier, and the kernel with
+    # tile queues) against the separate launches: the same device code per element, so the same
+    # bits, whatever order the tiles run in
     import torch
     w = _stage_case(flags_p, order=order)
     p = dict(w.params, nu=1e-2)
     M = oracle_mesh(w, p)
     q = oracle_state(w, M)
     out = {}
-    for fused in (0, 1):
+    for fused in (0, 1, 2):
         cache = tmp_path / f"stage{fused}.txt"
-        # default shapes for both passes (the stage kernel's), the stage choice forced
+        # default shapes for both passes (the stage kernels'), the stage choice forced
         _forced_cache(cache, {(0, order, 0): (0, 0, 0), (1, order, 0): (0, 0, 0), (2, order, 0): (fused, 0, 0)})
         S = gpu_solver(w, precision=1, params=p)
         rep = S.autotune(str(cache))
-        assert ("one persistent kernel" if fused else "separate launches") in rep, rep
+        assert STAGE_CHOICES[fused] in rep, rep
         qd, gd = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
         S.rk_step(qd, gd, 1e-4, 3)
         S.check_device()
         out[fused] = (qd.cpu().numpy(), S.launches_per_step)
     assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][0], out[2][0])
     # three stages: traces once, then one launch per stage instead of viscous + inviscid
     if flags_p > 0:
         assert out[1][1] == out[0][1] - 3, (out[0][1], out[1][1])
+        assert out[2][1] == out[0][1] - 3, (out[0][1], out[2][1])
     # and against the oracle, at the FP32 accuracy of the state change
     q0 = q.copy()
     g = np.zeros_like(q)
     M.rk_step(q, g, 1e-4, 3)
     assert rel_l2(out[1][0] - q0, q - q0) <= 1e-4
+
+
+@pytest.mark.parametrize("viscous_shape", [0, 1])
+def test_tile_queue_stage_kernel_chained_steps(viscous_shape, tmp_path):
+    # regional flags (wall layer and wake NS, most Euler elements independent of the viscous
+    # pass), chained steps (the queues are reset by each launch's last block, across graph
+    # replays), with overlapped and plain launches; the separate launches may use the other
+    # viscous tile shape, the one-launch kernel always uses the default one
+    import torch
+    w = wl.mixed_64x64x64_n4(n=12)
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    out = {}
+    for fused in (0, 2):
+        cache = tmp_path / f"q{fused}.txt"
+        _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (viscous_shape, 0, 0), (2, 4, 0): (fused, 0, 0)})
+        S = gpu_solver(w, precision=1)
+        assert STAGE_CHOICES[fused] in S.autotune(str(cache))
+        for overlap in (True, False):
+            S.set_launch_overlap(overlap)
+            qd, gd = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
+            S.rk_step(qd, gd, 1e-4, 2)
+            S.rk_step(qd, gd, 1e-4, 5)
+            S.check_device()
+            out[(fused, overlap)] = qd
+    ref = out[(0, True)]
+    for k, v in out.items():
+        assert torch.equal(v, ref), k
 
 
 def test_autotuner_times_the_persistent_stage_kernel(tmp_path):
@@ -148,7 +182,7 @@ def test_autotuner_times_the_persistent_stage_kernel(tmp_path):
     cache = tmp_path / "t.txt"
     _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (0, 0, 0)})  # the stage choice is timed
     rep = S.autotune(str(cache))
-    assert "stage N=4 geo=0" in rep and "one persistent kernel" in rep and "separate" in rep, rep
+    assert "stage N=4 geo=0" in rep and all(c.split()[-1] in rep for c in STAGE_CHOICES.values()), rep
     # not offered where it does not apply: mixed orders (several buckets, mortars)
     T = gpu_solver(_box_mixed_orders(), precision=1)
     assert "stage N=" not in T.autotune()

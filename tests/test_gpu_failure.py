@@ -127,3 +127,39 @@ def test_grid_barrier_of_the_persistent_stage_kernel_times_out(tmp_path):
     S.rk_step(qc, gc, w.dt, 1)
     S.check_device()
     assert torch.equal(qc, qa)
+
+
+def test_tile_queue_stage_kernel_wait_times_out(tmp_path):
+    # the one-launch stage kernel with tile queues: block 0's producer stops before its first
+    # viscous tile, so the tiles it claimed never finish. The inviscid tiles that read viscous
+    # results wait on the counter of finished viscous tiles; that bounded wait runs out (site 6)
+    # unless block 0's consumers' wait (site 3) ran out first. The step returns, the queues are
+    # reset, and the next step is exact.
+    import torch
+    from paper_2403_05463_gb300 import dg
+    w = _case(1, n=10)
+    M = oracle_mesh(w)
+    q = oracle_state(w, M)
+    S = gpu_solver(w, precision=1)
+    cache = tmp_path / "queue.txt"
+    with open(cache, "w") as f:
+        for ps, choice in ((0, "0\t0\t0"), (1, "0\t0\t0"), (2, "2\t0\t0")):
+            f.write(f"{torch.cuda.get_device_name(0)}\t{ps}\t4\t0\t{choice}\n")
+    assert "one launch with tile queues" in S.autotune(str(cache))
+    qa, ga = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
+    S.rk_step(qa, ga, w.dt, 2)
+    S.check_device()
+    S.set_wait_limit(polls=1 << 12, stop_tile=0)
+    qb, gb = to_dev(q), torch.zeros_like(ga)
+    t0 = time.perf_counter()
+    S.rk_step(qb, gb, w.dt, 1)
+    with pytest.raises(dg.DGError) as ei:
+        S.check_device()
+    assert time.perf_counter() - t0 < 30.0
+    assert dg.STATUS[ei.value.status] == "DG_ERR_TIMEOUT", str(ei.value)
+    assert any(f"site {k}" in str(ei.value) for k in (1, 3, 6)), str(ei.value)
+    S.set_wait_limit(0, -1)
+    qc, gc = to_dev(q), torch.zeros_like(ga)
+    S.rk_step(qc, gc, w.dt, 2)
+    S.check_device()
+    assert torch.equal(qc, qa)
