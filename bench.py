@@ -138,7 +138,7 @@ def allmax(world, x):
 
 # DRAM traffic of the dominant kernel, from an ncu capture of this workload (committed under
 # profiles/ with the hash of the kernel sources it was taken on); None once the sources differ.
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_inviscid_fp32_mixed_64x64x64_n4.md")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_stage_queue_fp32_mixed_64x64x64_n4.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2403_05463_gb300", "csrc", f)
                   for f in ("dg_kernels_f32.cu", "dg_device.cuh", "dg_internal.h")]
 
@@ -155,8 +155,28 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic(workload, precision, n, kernel):
-    if workload != "mixed_64x64x64_n4" or precision != "fp32" or n is not None or kernel != "inviscid_update":
+def stage_choice(tuning):
+    """The autotuner's choice for an RK stage of one bucket: "separate" launches, one
+    "persistent" kernel with a grid barrier, or one launch with "tile_queues"."""
+    for line in tuning.splitlines():
+        if line.startswith("stage "):
+            head = line.split(" ms")[0]
+            if "tile queues" in head:
+                return "tile_queues"
+            return "persistent" if "persistent kernel" in head else "separate"
+    return "separate"
+
+
+LAUNCH_NAMES = {"separate": "k_inviscid32t (the viscous pass a separate launch)",
+                "persistent": "k_stage32t: viscous + inviscid + RK update, one cooperative launch per stage",
+                "tile_queues": "k_stage32q: viscous + inviscid + RK update, one launch per stage (tile queues)"}
+
+
+def recorded_traffic(workload, precision, n, kernel, launch):
+    """DRAM bytes per launch recorded for the one-launch stage kernel with tile queues on the
+    benchmark workload, while the kernel sources hash to the recorded value."""
+    if workload != "mixed_64x64x64_n4" or precision != "fp32" or n is not None or kernel != "inviscid_update" \
+            or launch != "tile_queues":
         return None
     try:
         text = open(TRAFFIC_RECORD).read()
@@ -521,10 +541,12 @@ def main():
     # step only, and in every step a third update writing traces (ph_bytes are per-stage means:
     # the trace kernel's launch moves 3 x traces, half of it the written traces)
     step_bytes = 3 * sum(ph_bytes.values()) - (1.5 * ph_bytes["traces"] * (args.steps - 1) / max(args.steps, 1))
+    launch = stage_choice(tuning) if tuning != "default" else "separate"
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "launch": LAUNCH_NAMES[launch] if dom == "inviscid_update" else dom,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": ach / NOMINAL_HBM_GBS,
-                "traffic": recorded_traffic(args.workload, args.precision, args.n, dom),
+                "traffic": recorded_traffic(args.workload, args.precision, args.n, dom, launch),
                 "step_frac": step_bytes / (ms_max * 1e-3) / 1e9 / hbm}
     phases = {k: {"ms": ph_ms[k], "algorithmic_gb": ph_bytes[k] / 1e9,
                   "gbs": (ph_bytes[k] / (ph_ms[k] * 1e-3) / 1e9) if ph_ms[k] > 0 else None} for k in ph_ms}
@@ -549,9 +571,7 @@ def main():
             m = re.search(r"one persistent kernel ([0-9.]+) ms, one launch with tile queues ([0-9.]+) ms, "
                           r"separate ([0-9.]+) ms", line)
             if m:
-                chosen = "persistent" if ": one persistent kernel:" in line else \
-                    ("tile_queues" if ": one launch with tile queues:" in line else "separate")
-                out["stage_kernel"] = {"chosen": chosen, "persistent_ms_per_stage": float(m.group(1)),
+                out["stage_kernel"] = {"chosen": stage_choice(line), "persistent_ms_per_stage": float(m.group(1)),
                                        "tile_queues_ms_per_stage": float(m.group(2)),
                                        "separate_ms_per_stage": float(m.group(3))}
 
