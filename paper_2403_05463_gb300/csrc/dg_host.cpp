@@ -1004,7 +1004,8 @@ dg_status rebuild_orders(dg_ctx* c) {
 // pipelined viscous kernel.
 bool stage_fusable(const dg_ctx* c) {
   const DevMesh& M = c->M;
-  if (M.precision != 1 || M.tc || M.split || M.div64 || M.model || M.nodes) return false;
+  // (with the FP64 divergence only the kernel with tile queues applies, see stage_fused)
+  if (M.precision != 1 || M.tc || M.split || M.model || M.nodes) return false;
   if (c->all_buckets.size() != 1 || c->n_mortar_all) return false;
   // (the one-launch kernels use the default tile shapes whatever the separate launches use)
   const Bucket& bi = c->all_buckets[0];
@@ -1022,7 +1023,8 @@ bool stage_fusable(const dg_ctx* c) {
 int stage_fused(const dg_ctx* c) {
   if (!stage_fusable(c)) return 0;
   auto it = c->tuning.find({2, c->all_buckets[0].N, c->all_buckets[0].geo});
-  return it != c->tuning.end() && (it->second[0] == 1 || it->second[0] == 2) ? it->second[0] : 0;
+  const int v = it != c->tuning.end() && (it->second[0] == 1 || it->second[0] == 2) ? it->second[0] : 0;
+  return c->M.div64 && v == 1 ? 0 : v;
 }
 
 cudaError_t launch_stage(const dg_ctx* c, const DevMesh& M, const double* q, double* out, double* g, int stage,
@@ -1960,13 +1962,13 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
           },
           ms_sep);
       float ms_queue = 0.f;
-      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 1, s); }, ms_fused);
+      if (ce == cudaSuccess && !M.div64) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 1, s); }, ms_fused);
       if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 2, s); }, ms_queue);
       // a tie keeps the separate launches (per-pass timing and rooflines stay per kernel): a
       // one-launch form must be at least 1% faster
       int fused = 0;
       float best = ms_sep;
-      if (ce == cudaSuccess && ms_fused < 0.99f * best) fused = 1, best = ms_fused;
+      if (ce == cudaSuccess && !M.div64 && ms_fused < 0.99f * best) fused = 1, best = ms_fused;
       if (ce == cudaSuccess && ms_queue < (fused ? best : 0.99f * best)) fused = 2, best = ms_queue;
       c->tuning[key] = {fused, 0, 0};
       std::snprintf(buf, sizeof buf,

@@ -1840,7 +1840,9 @@ constexpr size_t stage_smem_bound() {
 // viscous pass drains into inviscid work. Overlapped launch: everything waits for the previous
 // launch first. Queue counters: err[8] viscous claims, err[9] inviscid claims, err[10] viscous
 // tiles finished, err[11] blocks finished; the last block resets them for the next launch.
-template <int N, int GEO>
+// VOL: the inviscid pass's volume variant, 0 (FP32 contractions) or 3 (with the FP64 velocity
+// divergence, box elements).
+template <int N, int GEO, int VOL>
 __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value)
     k_stage32q(DevMesh M, Bucket Bv, Bucket Bi, const double* q, double* out, double* g, int stage, int write_tr) {
   extern __shared__ __align__(128) char smc[];
@@ -1886,8 +1888,8 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(smc + PI::oBAR + 56);
   }
-  inviscid_tiles<N, GEO, MODE_RK, EPB, 0, true>(M, Bi, q, out, g, stage, write_tr, smc, 32, Bi.n_indep / EPB, qc + 1,
-                                                qc + 2, nv);
+  inviscid_tiles<N, GEO, MODE_RK, EPB, VOL, true>(M, Bi, q, out, g, stage, write_tr, smc, 32, Bi.n_indep / EPB,
+                                                  qc + 1, qc + 2, nv);
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -1933,13 +1935,14 @@ static cudaError_t launch_stage_n(const DevMesh& M, const Bucket& bv, const Buck
   return cudaLaunchKernelEx(&cfg, k_stage32t<N, GEO>, M, bv, bi, q, out, g, stage, write_tr);
 }
 
-template <int N, int GEO>
+template <int N, int GEO, int VOL>
 static cudaError_t launch_stage_q(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
                                   double* g, int stage, int write_tr, cudaStream_t s) {
   static int per_sm = -1, sms = 0;
   const size_t sm = stage_smem32<N>();
   if (per_sm < 0) {
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32q<N, GEO>, Shape<N>::threads + 32, sm);
+    cudaError_t r =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32q<N, GEO, VOL>, Shape<N>::threads + 32, sm);
     if (r != cudaSuccess) return r;
     int dev = 0;
     if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
@@ -1947,8 +1950,8 @@ static cudaError_t launch_stage_q(const DevMesh& M, const Bucket& bv, const Buck
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
   }
   const int bps = bi.bps > 0 && bi.bps < per_sm ? bi.bps : per_sm;
-  return launch_overlapped(M, k_stage32q<N, GEO>, bps * sms, Shape<N>::threads + 32, sm, s, M, bv, bi, q, out, g,
-                           stage, write_tr);
+  return launch_overlapped(M, k_stage32q<N, GEO, VOL>, bps * sms, Shape<N>::threads + 32, sm, s, M, bv, bi, q, out,
+                           g, stage, write_tr);
 }
 
 cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi, const double* q, double* out,
@@ -1956,9 +1959,13 @@ cudaError_t launch_stage32(const DevMesh& M, const Bucket& bv, const Bucket& bi,
   if (bi.geo > 1 || (bv.count > 0 && (bv.N != bi.N || bv.geo != bi.geo))) return cudaErrorInvalidValue;
   if (!bi.blink || !bi.bmeta || (bv.count > 0 && (!bv.blink || !bv.bmeta))) return cudaErrorInvalidValue;
   DG_SWITCH_N(bi.N, {
-    if (queue)
-      return bi.geo == 0 ? launch_stage_q<NN, 0>(M, bv, bi, q, out, g, stage, write_tr, s)
-                         : launch_stage_q<NN, 1>(M, bv, bi, q, out, g, stage, write_tr, s);
+    if (queue) {
+      if (bi.geo == 0)
+        return M.div64 ? launch_stage_q<NN, 0, 3>(M, bv, bi, q, out, g, stage, write_tr, s)
+                       : launch_stage_q<NN, 0, 0>(M, bv, bi, q, out, g, stage, write_tr, s);
+      return launch_stage_q<NN, 1, 0>(M, bv, bi, q, out, g, stage, write_tr, s);
+    }
+    if (M.div64) return cudaErrorInvalidValue;  // the grid-barrier kernel has no FP64 divergence
     return bi.geo == 0 ? launch_stage_n<NN, 0>(M, bv, bi, q, out, g, stage, write_tr, s)
                        : launch_stage_n<NN, 1>(M, bv, bi, q, out, g, stage, write_tr, s);
   });
@@ -2012,9 +2019,11 @@ static cudaError_t prep32_n() {
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_stage32t<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_stage32q<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((r = cudaFuncSetAttribute(k_stage32q<N, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
-  if ((r = cudaFuncSetAttribute(k_stage32q<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((r = cudaFuncSetAttribute(k_stage32q<N, 0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem32<N>())) != cudaSuccess) return r;
+  if ((r = cudaFuncSetAttribute(k_stage32q<N, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stage_smem32<N>())) != cudaSuccess) return r;
   if ((r = cudaFuncSetAttribute(k_viscous32<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)visc_smem32<N, 0>())) != cudaSuccess) return r;

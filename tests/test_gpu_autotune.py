@@ -148,21 +148,23 @@ def test_persistent_stage_kernel_matches_separate_launches(flags_p, order, tmp_p
     assert rel_l2(out[1][0] - q0, q - q0) <= 1e-4
 
 
-@pytest.mark.parametrize("viscous_shape", [0, 1])
-def test_tile_queue_stage_kernel_chained_steps(viscous_shape, tmp_path):
+@pytest.mark.parametrize("viscous_shape,extra", [(0, {}), (1, {}), (0, {"fp64_divergence": 1})])
+def test_tile_queue_stage_kernel_chained_steps(viscous_shape, extra, tmp_path):
     # regional flags (wall layer and wake NS, most Euler elements independent of the viscous
     # pass), chained steps (the queues are reset by each launch's last block, across graph
     # replays), with overlapped and plain launches; the separate launches may use the other
-    # viscous tile shape, the one-launch kernel always uses the default one
+    # viscous tile shape, the one-launch kernel always uses the default one; and the variant
+    # with the FP64 divergence
     import torch
     w = wl.mixed_64x64x64_n4(n=12)
-    M = oracle_mesh(w)
+    p = dict(w.params, **extra)
+    M = oracle_mesh(w, p)
     q = oracle_state(w, M)
     out = {}
     for fused in (0, 2):
         cache = tmp_path / f"q{fused}.txt"
         _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (viscous_shape, 0, 0), (2, 4, 0): (fused, 0, 0)})
-        S = gpu_solver(w, precision=1)
+        S = gpu_solver(w, precision=1, params=p)
         assert STAGE_CHOICES[fused] in S.autotune(str(cache))
         for overlap in (True, False):
             S.set_launch_overlap(overlap)
