@@ -67,11 +67,19 @@ class ClockSampler:
         os.close(fd)
         cmd = ["nvidia-smi", "-i", str(self.index),
                "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
-               "--format=csv,noheader,nounits", "-lms", "20"]
+               "--format=csv,noheader,nounits", "-lms", "10"]
         try:
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi needs a moment before its first sample: wait for it (at most 3 s), so that
+        # the samples cover the whole timed region that follows
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -506,10 +514,10 @@ def main():
     if args.warmup > 0:
         S.rk_step(q, g, dt, args.warmup, stream=stream)
     torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()  # returns once the sampler has its first sample
     barrier(world)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
