@@ -30,6 +30,12 @@
  * non-positive Jacobian, a bounded wait that timed out) land in a device error word that
  * dg_check_device() and dg_conservation() read.
  *
+ * Streams: one context is one solver; its calls must be ordered (one stream, or streams the
+ * caller orders with events). Its library-owned buffers -- face traces, viscous results, the
+ * tile queues of the one-launch stage kernel, the error word -- are shared by its launches, so
+ * two of its calls running concurrently on unordered streams race. Separate contexts are
+ * independent.
+ *
  * Ownership: descriptors and host arrays passed in are copied; the caller keeps them.
  * Device arrays (q, g, R, xyz) are caller-owned, FP64, contiguous; the library never frees
  * them. Library-owned buffers (traces, geometry, tables) are freed by dg_destroy. The
