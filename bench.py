@@ -582,6 +582,9 @@ def main():
                 out["stage_kernel"] = {"chosen": stage_choice(line), "persistent_ms_per_stage": float(m.group(1)),
                                        "tile_queues_ms_per_stage": float(m.group(2)),
                                        "separate_ms_per_stage": float(m.group(3))}
+                ms = re.search(r"blocks starting with the viscous tiles: ([^)]*)\)", line)
+                if ms:
+                    out["stage_kernel"]["queue_viscous_first_blocks"] = ms.group(1)
 
     if not args.no_extras:
         # mixed vs all-NS and all-Euler on the same mesh and GPU

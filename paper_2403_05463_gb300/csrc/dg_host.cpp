@@ -672,6 +672,8 @@ void apply_tuning(dg_ctx* c) {
     b.tile_alt = it == c->tuning.end() ? 0 : it->second[0];
     b.bps = it == c->tuning.end() ? 0 : it->second[1];
     b.visc_alt = 0;
+    auto st = c->tuning.find({2, b.N, b.geo});
+    b.vsplit = st == c->tuning.end() || st->second[0] != 2 ? 0 : std::min(std::max(st->second[1], 0), 3);
   }
   for (Bucket& b : c->ns_buckets) {
     auto it = c->tuning.find({1, b.N, b.geo});
@@ -1944,9 +1946,10 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
     auto hit = cached.find(key);
     if (hit != cached.end()) {
       c->tuning[key] = hit->second;
-      std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: cached, %s\n", bi.N, bi.geo,
+      std::snprintf(buf, sizeof buf, "stage N=%d geo=%d: cached, %s (split %d)\n", bi.N, bi.geo,
                     hit->second[0] == 2 ? "one launch with tile queues"
-                                        : (hit->second[0] ? "one persistent kernel" : "separate launches"));
+                                        : (hit->second[0] ? "one persistent kernel" : "separate launches"),
+                    hit->second[1]);
       rep += buf;
     } else {
       float ms_sep = 0.f, ms_fused = 0.f;
@@ -1963,20 +1966,33 @@ dg_status dg_autotune(dg_ctx* c, const char* cache_path, char* report, int repor
           ms_sep);
       float ms_queue = 0.f;
       if (ce == cudaSuccess && !M.div64) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 1, s); }, ms_fused);
-      if (ce == cudaSuccess) ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 2, s); }, ms_queue);
+      // the queue kernel with each split of the blocks between the viscous and the inviscid
+      // queue at the start (all blocks start with the viscous one, or k = 1..3 times its share
+      // of the two queues' tiles)
+      int vsplit = 0;
+      Bucket& bq = c->all_buckets[0];
+      for (int v = 0; v < 4 && ce == cudaSuccess; ++v) {
+        if (v > 0 && (c->ns_buckets.empty() || c->ns_buckets[0].count == 0)) break;
+        bq.vsplit = v;
+        float ms = 0.f;
+        ce = timed([&]() { return launch_stage(c, M, tq, tq, tr, 1, 1, 2, s); }, ms);
+        if (v == 0 || ms < ms_queue) ms_queue = ms, vsplit = v;
+      }
+      bq.vsplit = 0;
       // a tie keeps the separate launches (per-pass timing and rooflines stay per kernel): a
       // one-launch form must be at least 1% faster
       int fused = 0;
       float best = ms_sep;
       if (ce == cudaSuccess && !M.div64 && ms_fused < 0.99f * best) fused = 1, best = ms_fused;
       if (ce == cudaSuccess && ms_queue < (fused ? best : 0.99f * best)) fused = 2, best = ms_queue;
-      c->tuning[key] = {fused, 0, 0};
+      c->tuning[key] = {fused, fused == 2 ? vsplit : 0, 0};
+      static const char* split_name[4] = {"all", "1x their share", "2x their share", "3x their share"};
       std::snprintf(buf, sizeof buf,
                     "stage N=%d geo=%d: %s: %.4f ms (one persistent kernel %.4f ms, one launch with tile queues %.4f "
-                    "ms, separate %.4f ms)\n",
+                    "ms, separate %.4f ms; queue kernel: blocks starting with the viscous tiles: %s)\n",
                     bi.N, bi.geo,
                     fused == 2 ? "one launch with tile queues" : (fused ? "one persistent kernel" : "separate launches"),
-                    best, ms_fused, ms_queue, ms_sep);
+                    best, ms_fused, ms_queue, ms_sep, split_name[vsplit]);
       rep += buf;
     }
   }

@@ -156,6 +156,10 @@ struct Bucket {
   // all-element buckets: the first n_indep entries are Euler elements with no NS neighbour and
   // no mortar face (their inviscid pass touches nothing the viscous or mortar passes write)
   int n_indep = 0;
+  // one-launch stage kernel with tile queues: 0, every block starts with the viscous queue; k =
+  // 1..3, the share k * (viscous tiles) / (viscous + independent inviscid tiles) of the grid
+  // does (lowest indices first, at most all) and the others start with the independent tiles
+  int vsplit = 0;
 };
 
 enum StageMode { MODE_RESIDUAL = 0, MODE_RK = 1 };

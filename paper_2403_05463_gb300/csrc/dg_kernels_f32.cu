@@ -1869,7 +1869,15 @@ __global__ void __launch_bounds__(Shape<N>::threads + 32, TmaMinBlocks<N>::value
   }
   __syncthreads();
   const unsigned nv = (unsigned)((Bv.count + EPB - 1) / EPB);
-  if (Bv.count > 0) {
+  // the blocks that start with the viscous queue: all, or a share that follows the flags (the
+  // others begin with independent inviscid tiles, so that both kinds of tiles share the SMs
+  // while the viscous pass runs; without independent tiles every block starts with it)
+  int nvb = (int)gridDim.x;
+  if (Bi.vsplit > 0 && Bi.n_indep >= EPB) {
+    const float share = (float)Bi.vsplit * (float)nv / (float)(nv + (unsigned)(Bi.n_indep / EPB));
+    if (share < 1.f) nvb = max(1, (int)(share * (float)gridDim.x));
+  }
+  if (Bv.count > 0 && (int)blockIdx.x < nvb) {
     // the producer warp returns from here when the viscous queue is empty and goes on to stage
     // inviscid tiles; the consumers return when they have finished their viscous tiles
     const int done = viscous_tiles<N, GEO, EPB, true>(M, Bv, q, smc, 0, qc);

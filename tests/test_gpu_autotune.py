@@ -161,9 +161,11 @@ def test_tile_queue_stage_kernel_chained_steps(viscous_shape, extra, tmp_path):
     M = oracle_mesh(w, p)
     q = oracle_state(w, M)
     out = {}
-    for fused in (0, 2):
-        cache = tmp_path / f"q{fused}.txt"
-        _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (viscous_shape, 0, 0), (2, 4, 0): (fused, 0, 0)})
+    # (stage choice, split): separate launches; the queue kernel with every block starting on
+    # the viscous queue, or 1x / 3x its share of the tiles (the rest start on inviscid tiles)
+    for fused, vsplit in ((0, 0), (2, 0), (2, 1), (2, 3)):
+        cache = tmp_path / f"q{fused}{vsplit}.txt"
+        _forced_cache(cache, {(0, 4, 0): (0, 0, 0), (1, 4, 0): (viscous_shape, 0, 0), (2, 4, 0): (fused, vsplit, 0)})
         S = gpu_solver(w, precision=1, params=p)
         assert STAGE_CHOICES[fused] in S.autotune(str(cache))
         for overlap in (True, False):
@@ -172,8 +174,8 @@ def test_tile_queue_stage_kernel_chained_steps(viscous_shape, extra, tmp_path):
             S.rk_step(qd, gd, 1e-4, 2)
             S.rk_step(qd, gd, 1e-4, 5)
             S.check_device()
-            out[(fused, overlap)] = qd
-    ref = out[(0, True)]
+            out[(fused, vsplit, overlap)] = qd
+    ref = out[(0, 0, True)]
     for k, v in out.items():
         assert torch.equal(v, ref), k
 
