@@ -103,3 +103,36 @@ def test_an_empty_mesh_is_rejected():
     with pytest.raises(dg.DGError) as ei:
         dg.Solver(np.zeros((0, 8), np.int64), np.zeros((0, 8, 3)), 1, PARAMS)
     assert dg.STATUS[ei.value.status] == "DG_ERR_ARG"
+
+
+def _forced(tmp_path, N, stage_choice, vsplit=0):
+    # default tile shapes; the stage form forced (0 separate launches, 2 one launch with tile queues)
+    import torch
+    path = tmp_path / f"stage_{N}_{stage_choice}_{vsplit}.txt"
+    dev = torch.cuda.get_device_name(0)
+    with open(path, "w") as f:
+        for ps, choice in ((0, "0\t0\t0"), (1, "0\t0\t0"), (2, f"{stage_choice}\t{vsplit}\t0")):
+            f.write(f"{dev}\t{ps}\t{N}\t0\t{choice}\n")
+    return str(path)
+
+
+@pytest.mark.parametrize("N", [1, 4, 7])
+@pytest.mark.parametrize("nx,flag", [(1, 1), (1, 0), (2, 1)])
+def test_tile_queue_stage_kernel_on_tiny_meshes(N, nx, flag, tmp_path):
+    # one or two elements with walls: a few tiles against hundreds of persistent blocks, so most
+    # blocks claim no tile at all (an empty tile -1 ends their queue) and the inviscid tiles wait
+    # on one or two viscous ones; chained steps must match the separate launches bitwise
+    import torch
+    desc = _open_box(nx)
+    orders, flags = np.full(nx, N, np.int8), np.full(nx, flag, np.uint8)
+    out = []
+    for choice, vsplit in ((0, 0), (2, 0), (2, 3)):
+        M, S = _pair(desc, orders, flags, PARAMS, 1)
+        rep = S.autotune(_forced(tmp_path, N, choice, vsplit))
+        assert ("tile queues" in rep) == (choice == 2), rep
+        q = _state(M.node_coords())
+        qd, gd = to_dev(q), torch.zeros((4, q.shape[1]), dtype=torch.float64, device="cuda")
+        S.rk_step(qd, gd, 1e-4, 3)
+        S.check_device()
+        out.append(qd)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
