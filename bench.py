@@ -667,7 +667,16 @@ def main():
             M = oracle_mesh(w)
             qh0 = q0.cpu().numpy()
             # the headline's accuracy: the benchmarked residual against the FP64 oracle
-            out["error_vs_oracle"] = sampled_error(M, w, qh0, S.residual(q0).cpu().numpy())
+            out["error_vs_oracle"] = err = sampled_error(M, w, qh0, S.residual(q0).cpu().numpy())
+            if args.precision != "fp64":
+                # which row carries the error, and the configuration that removes it
+                names = ("p", "u", "v", "w")
+                worst = max(range(4), key=lambda v: err["per_var"][v])
+                err["dominant_variable"] = names[worst]
+                if worst == 0:
+                    err["cause"] = ("pressure row: R_p = -c0^2 div u of a nearly divergence-free field is a "
+                                    "small difference of three FP32 directional derivatives; the FP64 "
+                                    "velocity divergence (configs: *_div64) removes it")
             out["configs"] = time_configs(S, w, q0, M, stream, hbm, device=local)
             try:
                 out["cpu_baseline"] = oracle_rate(w, qh0, M=M)
