@@ -256,9 +256,17 @@ def time_configs(S, w, q0, M, stream, hbm, device=0):
         R = S.residual(q0).cpu().numpy()
         q.copy_(q0)
         ms = timed_steps(S, q, g, w.dt, stream, steps)
-        out[f"{w.name}_{prec}" + ("_div64" if extra else "")] = {
-            "ms_per_step": ms, "value": dof * 3 / (ms * 1e-3), "dtype": prec,
-            "fp64_divergence": bool(extra), "error_vs_oracle": sampled_error(M, w, qh, R)}
+        key = f"{w.name}_{prec}" + ("_div64" if extra else "")
+        out[key] = {"ms_per_step": ms, "value": dof * 3 / (ms * 1e-3), "dtype": prec,
+                    "fp64_divergence": bool(extra), "error_vs_oracle": sampled_error(M, w, qh, R)}
+        if prec == "fp64" or (prec == "fp32" and extra):
+            # the mixed-vs-all-NS bar in the FP64 path and in the FP32 mode within 1e-6 of the oracle
+            try:
+                out[key]["comparison"] = flag_comparison(S, w, q0, q, g, stream, steps=steps,
+                                                         reps=3 if prec == "fp32" else 1)
+            except Exception as exc:  # an extra measurement must not cost the headline line
+                S.set_flags(w.flags)
+                out[key]["comparison"] = {"error": str(exc)}
     S.set_params(dict(w.params), precision="fp32")
     del q, g
     for name, make, variants in (("tgv_32x32x32_n5", wl.tgv_32x32x32_n5,
@@ -290,6 +298,27 @@ def time_configs(S, w, q0, M, stream, hbm, device=0):
             Sc.close()
             del qc, g
     return out
+
+
+def flag_comparison(S, w, q0, q, g, stream, steps, reps):
+    """Chained steps with the workload's flags, all NS and all Euler on the same mesh and GPU
+    (each set timed reps times, interleaved; the median of each) and the bar
+    T_mixed <= f T_allNS + (1 - f) T_allEuler."""
+    import numpy as np
+    runs = {"mixed": [], "all_ns": [], "all_euler": []}
+    sets = (("mixed", w.flags), ("all_ns", np.ones(w.n_elem, np.uint8)), ("all_euler", np.zeros(w.n_elem, np.uint8)))
+    for _ in range(reps):
+        for name, fl in sets:
+            S.set_flags(fl)
+            q.copy_(q0)
+            runs[name].append(timed_steps(S, q, g, w.dt, stream, steps, warmup=2))
+    S.set_flags(w.flags)
+    med = {k: statistics.median(v) for k, v in runs.items()}
+    f = w.ns_fraction
+    bar = f * med["all_ns"] + (1 - f) * med["all_euler"]
+    return {"mixed_ms_per_step": med["mixed"], "all_ns_ms_per_step": med["all_ns"],
+            "all_euler_ms_per_step": med["all_euler"], "bar_ms_per_step": bar, "meets_bar": med["mixed"] <= bar,
+            "speedup_vs_all_ns": med["all_ns"] / med["mixed"], "steps": steps, "runs": reps}
 
 
 def oracle_rate(w, q_host, budget_s=12.0, seed=0, M=None):
