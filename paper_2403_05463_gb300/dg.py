@@ -153,10 +153,12 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t, name):
+def _dev_ptr(t, name, device=None):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on {t.device}, the mesh on cuda:{device}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -252,7 +254,7 @@ class Solver:
     def node_coords(self):
         import torch
         xyz = torch.empty((3, self.total_nodes), dtype=torch.float64, device=f"cuda:{self.device}")
-        _check(load().dg_node_coords(self.h, _dev_ptr(xyz, "xyz"), _stream_handle(None)))
+        _check(load().dg_node_coords(self.h, _dev_ptr(xyz, "xyz", self.device), _stream_handle(None)))
         return xyz
 
     def residual(self, q, R=None, stream=None):
@@ -261,14 +263,15 @@ class Solver:
         if R is None:
             R = torch.empty_like(q)
         self._check_state(R, "R")
-        _check(load().dg_residual(self.h, _dev_ptr(q, "q"), _dev_ptr(R, "R"), _stream_handle(stream)))
+        _check(load().dg_residual(self.h, _dev_ptr(q, "q", self.device), _dev_ptr(R, "R", self.device),
+                                  _stream_handle(stream)))
         return R
 
     def rk_step(self, q, g, dt, nsteps=1, t=0.0, stream=None):
         self._check_state(q, "q")
         self._check_state(g, "g")
-        _check(load().dg_rk_step(self.h, _dev_ptr(q, "q"), _dev_ptr(g, "g"), float(t), float(dt), int(nsteps),
-                                 _stream_handle(stream)))
+        _check(load().dg_rk_step(self.h, _dev_ptr(q, "q", self.device), _dev_ptr(g, "g", self.device), float(t),
+                                 float(dt), int(nsteps), _stream_handle(stream)))
 
     def residual_host(self, q, R, stream=None):
         """q, R: host arrays (numpy or pinned CPU tensors), float64 [nvar][total]."""
@@ -287,7 +290,7 @@ class Solver:
     def conservation(self, R, stream=None):
         self._check_state(R, "R")
         out = (ctypes.c_double * 5)()
-        _check(load().dg_conservation(self.h, _dev_ptr(R, "R"), out, _stream_handle(stream)))
+        _check(load().dg_conservation(self.h, _dev_ptr(R, "R", self.device), out, _stream_handle(stream)))
         return np.array(list(out)[:self.nvar])
 
     def conservation_noalloc(self, R, out, stream=None):
@@ -297,7 +300,7 @@ class Solver:
         self._check_state(R, "R")
         if out.numel() < 4:
             raise ValueError("out must hold 4 float64 values")
-        _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R"), _dev_ptr(out, "out"),
+        _check(load().dg_conservation_noalloc(self.h, _dev_ptr(R, "R", self.device), _dev_ptr(out, "out", self.device),
                                               _stream_handle(stream)))
 
     def project_state(self, q_old, stream=None):
@@ -310,7 +313,8 @@ class Solver:
         if q_old.numel() != self.nvar * before:
             raise ValueError(f"q_old must hold [{self.nvar}][{before}] values (the layout before the last set_orders)")
         q_new = torch.empty((self.nvar, self.total_nodes), dtype=torch.float64, device=q_old.device)
-        _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old"), _dev_ptr(q_new, "q_new"),
+        _check(load().dg_project_state(self.h, _dev_ptr(q_old, "q_old", self.device),
+                                       _dev_ptr(q_new, "q_new", self.device),
                                        _stream_handle(stream)))
         return q_new
 
@@ -330,10 +334,11 @@ class Solver:
         f = torch.empty(self.n_elem, dtype=torch.uint8, device=dev) if flags else None
         pb = torch.empty((2, self.n_elem), dtype=torch.float64, device=dev) if pbar else None
         ft = torch.empty((4, self.total_nodes), dtype=torch.float64, device=dev) if features else None
-        _check(load().dg_detect_regions(self.h, _dev_ptr(q, "q"), ctypes.byref(gmm),
+        _check(load().dg_detect_regions(self.h, _dev_ptr(q, "q", self.device), ctypes.byref(gmm),
                                         None if f is None else ctypes.c_void_p(f.data_ptr()),
-                                        None if pb is None else _dev_ptr(pb, "pbar"),
-                                        None if ft is None else _dev_ptr(ft, "features"), _stream_handle(stream)))
+                                        None if pb is None else _dev_ptr(pb, "pbar", self.device),
+                                        None if ft is None else _dev_ptr(ft, "features", self.device),
+                                        _stream_handle(stream)))
         return f, pb, ft
 
     def autotune(self, cache_path=None):
@@ -349,8 +354,8 @@ class Solver:
     def phase_times(self, q, g, dt, reps=3, stream=None):
         """Mean milliseconds per phase over `reps` RK stages (advances q, g)."""
         out = (ctypes.c_double * 5)()
-        _check(load().dg_phase_times(self.h, _dev_ptr(q, "q"), _dev_ptr(g, "g"), float(dt), int(reps), out,
-                                     _stream_handle(stream)))
+        _check(load().dg_phase_times(self.h, _dev_ptr(q, "q", self.device), _dev_ptr(g, "g", self.device), float(dt),
+                                     int(reps), out, _stream_handle(stream)))
         return dict(zip(self.PHASES, list(out)))
 
     def phase_bytes(self):
