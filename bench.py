@@ -336,7 +336,7 @@ def flag_comparison(S, w, q0, q, g, stream, steps, reps):
             "speedup_vs_all_ns": med["all_ns"] / med["mixed"], "steps": steps, "runs": reps}
 
 
-def oracle_rate(w, q_host, budget_s=12.0, seed=0, M=None):
+def oracle_rate(w, q_host, budget_s=20.0, seed=0, M=None):
     """The FP64 oracle as it stands, on the host cores: residual of a random sample of
     elements (each needs its neighbours' BR1 gradients too), DOF of the sample / wall time."""
     import numpy as np
