@@ -118,3 +118,26 @@ def test_project_state_refuses_a_q_old_of_another_layout(monkeypatch):
     S5.params = {"model": 1}
     with pytest.raises(ValueError, match=r"q_old must hold \[5\]\[64\]"):
         S5.project_state(_FakeTensor(4 * 64))  # a four-plane state for the five-plane form
+
+
+def test_product_path_shares_nothing_with_the_oracle():
+    # the library, its binding and its headers neither import, include, link nor load anything
+    # under oracle/, and the oracle includes nothing of the library
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pat = re.compile(r"(import\s+oracle|from\s+oracle|liboracle|dg_oracle|oracle/)")
+    product = [os.path.join(root, "include")] + [os.path.join(root, "paper_2403_05463_gb300")]
+    for top in product:
+        for dirpath, _, files in os.walk(top):
+            if "_build" in dirpath or "__pycache__" in dirpath:
+                continue
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                    text = open(os.path.join(dirpath, f), encoding="utf-8").read()
+                    assert not pat.search(text), os.path.join(dirpath, f)
+    inc = re.compile(r'#include\s+"([^"]+)"')
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith((".c", ".h")):
+            text = open(os.path.join(root, "oracle", f), encoding="utf-8").read()
+            assert all(h.startswith("dg_oracle") for h in inc.findall(text)), f
