@@ -366,7 +366,10 @@ dg_status dg_phase_times(dg_ctx* ctx, double* q_dev, double* g_dev, double dt, i
 /* Algorithmic DRAM bytes of each phase, averaged over the three stages of one Runge-Kutta
  * step, on the current mesh, orders, flags and precision: every value a phase must read or
  * write once (state, RK register, traces, viscous buffers, metric terms), none re-read. The
- * roofline of a phase is these bytes over its mean time from dg_phase_times. */
+ * roofline of a phase is these bytes over its mean time from dg_phase_times. The step is one on
+ * its own, as dg_phase_times runs it: the trace kernel in stage 0, the updates of stages 0 and 1
+ * writing the next stage's traces. In a dg_rk_step call of several steps every update writes
+ * traces (stage 2 those of the next step) and only the first step runs the trace kernel. */
 dg_status dg_phase_bytes(const dg_ctx* ctx, double out_bytes[DG_NPHASES]);
 
 /* Number of kernel launches the last dg_residual / one dg_rk_step step issued, and one step
