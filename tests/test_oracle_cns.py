@@ -530,3 +530,36 @@ def test_gauss_legendre_free_slip_mirror_and_far_field(flags_value):
     v = np.stack([np.full(n, c) for c in FAR["v"]])
     u = _cns_from_primitive(np.full(n, FAR["rho"]), v, np.full(n, FAR["p"]))
     assert np.abs(M.cns_residual(u)).max() < 1e-12
+
+
+@pytest.mark.parametrize("nodes", [0, 1], ids=["lobatto", "legendre"])
+def test_affine_gradient_of_v_and_T_exact_for_polynomials(nodes):
+    # the BR1 gradient of the primitive (v, T) lifts nothing for fields continuous across the
+    # element's faces, and the derivative operators are exact for degree <= N on affine maps:
+    # on the central element of a sheared 3^3 box it equals the exact gradient (v quadratic in
+    # its own coordinate, T linear, rho constant, p = rho T). N = 4, so that on Gauss points the
+    # face values interpolated from the conservative state (rho e of degree 4) are exact too
+    rng = np.random.default_rng(11)
+    n = 3
+    b = np.linspace(0, 1, n + 1)
+    A = np.array([[1.0, 0.3, 0.0], [0.1, 0.9, 0.2], [0.0, -0.2, 1.1]])
+    mesh = wl.box_mesh(n, n, n, b, b, b, warp=lambda x, y, z: tuple(A @ np.stack([x, y, z])))
+    E = n ** 3
+    M = orc.Mesh(mesh.hex, mesh.geom, 1, np.full(E, 4, np.int8), np.ones(E, np.uint8),
+                 _cns_params(nu=1e-3, nodes=nodes))
+    xyz = M.node_coords()
+    C = rng.normal(size=(3, 3))
+    t = rng.normal(size=3) * 0.1
+    rho = np.full(M.total, 1.2)
+    v = np.stack([0.3 * C[c] @ xyz + 0.1 * xyz[c] ** 2 for c in range(3)])
+    T = 1.0 + t @ xyz
+    u = _cns_from_primitive(rho, v, rho * T)
+    e = 13  # the central element: every neighbour carries the same polynomials
+    G = M.cns_element_gradient(u, e)
+    x = xyz[:, M.element_nodes(e)]
+    for c in range(3):
+        for k in range(3):
+            ref = 0.3 * C[c, k] + (0.2 * x[c] if c == k else 0.0)
+            np.testing.assert_allclose(G[c, k], ref, atol=1e-10)
+    for k in range(3):
+        np.testing.assert_allclose(G[3, k], t[k], atol=1e-10)
